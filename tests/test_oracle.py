@@ -1,0 +1,453 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every test here runs on the CPU.  The oracle (oracle.ssamg) is checked
+against closed forms, the paper's worked examples (tests/golden), invariants
+of the Galerkin construction and brute-force assembled-CSR computations in
+oracle.assembled, which shares no code with the stencil implementation.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import problems as P
+from oracle import assembled as C
+from oracle import ssamg as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------
+# Small problems covering one/many parts, odd/even sizes, 2-D, shifted boxes
+# ---------------------------------------------------------------------------
+
+def poisson2d(nx, ny, nine=False, lo=(0, 0)):
+    if nine:
+        offs = [(0, 0, 0)] + [(i, j, 0) for j in (-1, 0, 1) for i in (-1, 0, 1) if (i, j) != (0, 0)]
+        coef = [8.0] + [-1.0] * 8
+    else:
+        offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)]
+        coef = [4.0, -1.0, -1.0, -1.0, -1.0]
+    rng = P.SplitMix64(11)
+    box = ((lo[0], lo[1], 0), (lo[0] + nx - 1, lo[1] + ny - 1, 0))
+    z = np.zeros(0, np.int32)
+    z3 = np.zeros((0, 3), np.int32)
+    return P.Problem(2, [box], np.array(offs, np.int32), [coef], z, z3, z3, z, z3,
+                     np.zeros(0), rng.uniform_pm1(nx * ny).reshape(1, -1), name="poisson2d")
+
+
+def shifted(prob, shifts):
+    """The same matrix with part p's index space moved by shifts[p]."""
+    boxes = []
+    for p, (lo, hi) in enumerate(prob.boxes):
+        s = shifts[p]
+        boxes.append((tuple(lo[d] + s[d] for d in range(3)), tuple(hi[d] + s[d] for d in range(3))))
+    sh = np.array(shifts, np.int32)
+    u_idx = prob.u_idx + sh[prob.u_part] if prob.nnz_u else prob.u_idx
+    u_nb = prob.u_nbor_idx + sh[prob.u_nbor_part] if prob.nnz_u else prob.u_nbor_idx
+    return P.Problem(prob.ndim, boxes, prob.offsets, prob.coef, prob.u_part, u_idx, prob.u_dir,
+                     prob.u_nbor_part, u_nb, prob.u_val, prob.b, name=prob.name + " shifted")
+
+
+def chain(edges, a, seed=5):
+    return P.chain_aniso(edges, np.asarray(a, float), P.SplitMix64(seed), 1)
+
+
+def small_problems():
+    out = [
+        P.laplace7(5),
+        P.laplace7(6),
+        P.multipart_aniso(m=4, layout=(2, 1, 1), seed=7),
+        P.multipart_aniso(m=5, layout=(2, 2, 1), seed=8),
+        P.multipart_aniso(m=3, layout=(2, 2, 2), seed=1),
+        P.var27(n=6, block=2, seed=2),
+        chain([3, 5, 4], [[1, .1, .1], [1, .01, .5], [.2, 1, 1]]),
+        P.diffusion_exp(n=6, seed=4, nfd=2),
+        poisson2d(7, 5),
+        poisson2d(6, 6, nine=True),
+    ]
+    out.append(shifted(P.multipart_aniso(m=4, layout=(2, 1, 1), seed=9), [(-3, 1, 2), (5, -2, 0)]))
+    out.append(shifted(chain([4, 6], [[1, .01, .01], [1, .02, .03]]), [(1, 0, 0), (-1, 3, 1)]))
+    return out
+
+
+SMALL = small_problems()
+IDS = [f"{i}-{p.name}" for i, p in enumerate(SMALL)]
+
+
+# ---------------------------------------------------------------------------
+# Input generator
+# ---------------------------------------------------------------------------
+
+def test_rng_reproducible_and_uniform():
+    a = P.SplitMix64(0).uniform(100000)
+    b = P.SplitMix64(0).uniform(100000)
+    c = P.SplitMix64(1).uniform(100000)
+    assert np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.min() >= 0.0 and a.max() < 1.0
+    assert abs(a.mean() - 0.5) < 5e-3 and abs(a.var() - 1.0 / 12) < 5e-3
+    s = P.SplitMix64(3)
+    s.uniform(10)
+    t = P.SplitMix64(3).uniform(20)
+    assert np.array_equal(s.uniform(10), t[10:])
+    z = P.SplitMix64(4).normal(200001)
+    assert abs(z.mean()) < 1e-2 and abs(z.std() - 1.0) < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# Operator (Section 2): stencil matvec equals the assembled CSR matvec
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prob", SMALL, ids=IDS)
+def test_matvec_matches_assembled(prob):
+    A, _ = C.assemble_problem(prob)
+    lev = O.level0_from_problem(prob)
+    x = P.SplitMix64(99).uniform_pm1(prob.n)
+    assert np.allclose(O.matvec(lev, x), A @ x, rtol=0, atol=1e-13 * abs(A).max())
+    A2, _ = C.assemble_level(lev)
+    assert abs(A - A2).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Coarsening (Section 3.1, Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def test_coupling_sums_closed_form():
+    """Constant 7-point stencil on an n^3 box: c_d = 2 a_d (n-1) n^2."""
+    n = 6
+    prob = P.multipart_aniso(m=n, layout=(1, 1, 1), seed=3)
+    a = prob.extra["a"][0]
+    c = O.coupling_sums(O.level0_from_problem(prob))[0]
+    assert np.allclose(c, 2 * a * (n - 1) * n * n, rtol=1e-14)
+    W = O.grid_spacings(c[None, :], 3)[0]
+    assert np.allclose(W, np.sqrt(a.max() / a), rtol=1e-14)
+
+
+def test_isotropic_direction_cycles():
+    h = O.setup(P.laplace7(8))
+    seq = [lev.dstar[0] for lev in h.levels[:-1]]
+    assert seq == [0, 1, 2] * 3
+    assert h.levels[-1].n == 1
+
+
+def test_tie_break_and_extent():
+    ext = np.array([4, 4, 4])
+    assert O.choose_direction(np.array([1.0, 1.0, 1.0]), ext, 3) == 0
+    assert O.choose_direction(np.array([2.0, 1.0, 1.0]), ext, 3) == 1
+    assert O.choose_direction(np.array([1.0, 2.0, 1.0]), np.array([1, 4, 4]), 3) == 2
+
+
+def test_coarse_boxes_halve_even_cells():
+    lo, hi = np.array([-3, 0, 1]), np.array([4, 5, 1])
+    lo2, hi2 = O.coarsen_box(lo, hi, 0)
+    assert lo2[0] == -1 and hi2[0] == 2          # even cells -2, 0, 2, 4 -> -1..2
+    lo2, hi2 = O.coarsen_box(lo, hi, 1)
+    assert lo2[1] == 0 and hi2[1] == 2           # 0, 2, 4 -> 0..2
+
+
+def test_anisotropic_part_coarsens_strong_direction():
+    # strong coupling along x: W_x smallest until W_x has doubled past W_y, W_z
+    prob = chain([16], [[1.0, 1.0 / 16, 1.0 / 64]])
+    h = O.setup(prob)
+    seq = [lev.dstar[0] for lev in h.levels[:4]]
+    # W = (1, 4, 8): x, x (W_x=2), x (W_x=4 ties y -> x is smaller index) ...
+    assert seq[:3] == [0, 0, 0]
+
+
+# ---------------------------------------------------------------------------
+# Relaxation weight (Section 3.4, Eqs. relax1 and alpha-beta)
+# ---------------------------------------------------------------------------
+
+def test_omega_closed_forms():
+    g = golden("omega_worked_example.json")
+    W = np.array(g["W"])
+    d = O.choose_direction(W, np.array([8, 8, 8]), 3)
+    assert d in g["dstar_candidates"]
+    assert abs(O.relaxation_weight(W, d, 3) - g["omega"]) < 1e-12
+    assert abs(O.relaxation_weight(np.ones(3), 0, 3) - 6.0 / 7.0) < 1e-15
+    assert abs(O.relaxation_weight(np.array([1.0, np.inf, np.inf]), 0, 1) - 2.0 / 3.0) < 1e-15
+    assert abs(O.relaxation_weight(np.array([1.0, 1.0, np.inf]), 1, 2) - 0.8) < 1e-15
+
+
+def test_omega_worked_example_from_matrix():
+    """A problem nearly decoupled in k gives omega = 4/5 at the first levels."""
+    g = golden("omega_worked_example.json")
+    prob = chain([8], [[1.0, 1.0, 1e-9]])
+    h = O.setup(prob)
+    assert h.levels[0].dstar[0] in g["dstar_candidates"]
+    assert abs(h.levels[0].omega[0] - g["omega"]) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Interpolation (Section 3.2, Eq. prolEx)
+# ---------------------------------------------------------------------------
+
+def test_interp_closed_forms_isotropic():
+    h = O.setup(P.laplace7(8))
+    lev = h.levels[0]
+    assert lev.dstar[0] == 0
+    PW, PE = lev.PW[0], lev.PE[0]          # arrays [k, j, i]
+    assert PW[3, 3, 3] == 0.5 and PE[3, 3, 3] == 0.5       # interior fine point
+    assert abs(PW[3, 0, 3] - 1.0 / 3.0) < 1e-15            # next to the j = 0 Dirichlet face
+    assert abs(PW[0, 0, 3] - 1.0 / 4.0) < 1e-15            # two perpendicular faces: 1/(6-2)
+    assert PE[3, 3, 7] == 0.0 and PW[3, 3, 7] == 0.5       # x boundary: physical, no fix
+    assert PW[3, 3, 2] == 0.0 and PE[3, 3, 2] == 0.0       # coarse point
+
+
+def test_interp_golden_example():
+    g = golden("interp_example.json")
+    prob = poisson2d(7, 7, nine=True)
+    h = O.setup(prob)
+    lev, coarse = h.levels[0], h.levels[1]
+    assert lev.dstar[0] == 0
+    r, c, v = lev.P
+    A = sp.coo_matrix((v, (r, c)), shape=(lev.n, coarse.n)).tocsr()
+    nx = 7
+    ncx = coarse.shape(0)[2]
+    for f, cc in g["fine_to_coarse"]:
+        j = 3
+        row = A.getrow(j * nx + f)
+        assert row.nnz == 1 and row.indices[0] == j * ncx + cc and row.data[0] == g["coarse_cell_weight"]
+    fi, fj = g["fine_cell"]
+    row = A.getrow(fj * nx + fi)
+    got = sorted(zip(row.indices.tolist(), row.data.tolist()))
+    want_cols = sorted(cj * ncx + ci for ci, cj in g["interpolates_from_coarse"])
+    assert [c for c, _ in got] == want_cols
+    ex = g["nine_point_laplacian"]
+    assert abs(got[0][1] - ex["PW_interior"]) < 1e-15 and abs(got[1][1] - ex["PE_interior"]) < 1e-15
+
+
+def test_part_boundary_fix_row_sum_one():
+    prob = chain([4, 6], [[1, .01, .01], [1, .02, .03]])
+    h = O.setup(prob)
+    lev = h.levels[0]
+    assert lev.dstar == [0, 0]
+    PW0, PE0 = lev.PW[0], lev.PE[0]
+    # part 0: i = 3 is fine (odd) and sits on the coupled +x face
+    assert np.all(PW0[:, :, 3] == 1.0) and np.all(PE0[:, :, 3] == 0.0)
+    # part 1: i = 0 is coarse; i = 5 is fine on the Dirichlet +x face -> no fix
+    assert np.all(PE0[:, :, 1] < 1.0)
+    assert np.all(lev.PE[1][:, :, 5] == 0.0) and np.all(lev.PW[1][:, :, 5] < 1.0)
+
+
+def _hierarchy_checks(prob):
+    h = O.setup(prob)
+    A, num = C.assemble_problem(prob)
+    for l in range(h.L):
+        fine, coarse = h.levels[l], h.levels[l + 1]
+        Af, numf = C.assemble_level(fine)
+        if l == 0:
+            assert abs(Af - A).max() == 0.0
+        bits = C.row_direction_bits(fine)
+        Pb, _ = C.prolongation_brute(Af, numf, fine.dstar, coarse.lo, coarse.hi, bits)
+        r, c, v = fine.P
+        Po = sp.coo_matrix((v, (r, c)), shape=Pb.shape).tocsr()
+        assert abs(Po - Pb).max() <= 1e-15, f"P mismatch at level {l}"
+        Ac, _ = C.assemble_level(coarse)
+        ref = C.galerkin(Af, Pb)
+        scale = abs(ref).max()
+        assert abs(Ac - ref).max() <= 1e-13 * scale, f"RAP mismatch at level {l}"
+        # Galerkin operators stay symmetric
+        assert abs(Ac - Ac.T).max() <= 1e-14 * scale
+    return h
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=IDS)
+def test_interp_and_galerkin_match_brute_force(prob):
+    _hierarchy_checks(prob)
+
+
+def test_stencil_growth_bounds():
+    g = golden("stencil_growth.json")
+    for case in g["cases"]:
+        prob = poisson2d(9, 9) if case["ndim"] == 2 else P.laplace7(9)
+        h = O.setup(prob)
+        assert len(prob.offsets) == case["fine_entries"]
+        for l, lev in enumerate(h.levels[1:], start=1):
+            nz = [o for o, a in lev.S[0].items() if np.any(a != 0.0)]
+            assert len(nz) <= case["max_coarse_entries"]
+            if case["ndim"] == 3 and l == 1:
+                assert len(nz) <= 15
+        big = max(len([o for o, a in lev.S[0].items() if np.any(a != 0.0)]) for lev in h.levels[1:])
+        assert big == case["max_coarse_entries"]
+
+
+def test_theorem_unstructured_part_stays_on_part_boundaries():
+    """U_c connects only boundary cells of different parts (Section 3.3 Theorem)."""
+    for prob in (P.multipart_aniso(m=6, layout=(2, 2, 2), seed=1),
+                 chain([5, 8, 6], [[.3, 1, .2], [1, .1, .1], [.05, .5, 1]])):
+        h = O.setup(prob)
+        for lev in h.levels:
+            if len(lev.u_row) == 0:
+                continue
+            pr, ijr = lev.locate(lev.u_row)
+            pc, ijc = lev.locate(lev.u_col)
+            assert np.all(pr != pc)
+            for p_arr, ij in ((pr, ijr), (pc, ijc)):
+                for q in np.unique(p_arr):
+                    m = p_arr == q
+                    on_face = np.zeros(m.sum(), bool)
+                    for d in range(3):
+                        on_face |= (ij[m, d] == lev.lo[q][d]) | (ij[m, d] == lev.hi[q][d])
+                    assert on_face.all()
+
+
+def test_zero_row_sum_preserved():
+    """Constant-preserving P keeps zero row sums: A 1 = 0 implies A_c 1 = 0."""
+    n = 7
+    lev_prob = P.laplace7(n)
+    diag = np.zeros((n, n, n))
+    for o in lev_prob.offsets[1:]:
+        diag += O._inside_mask((n, n, n), tuple(int(v) for v in o))
+    lev_prob.coef[0][0] = diag
+    h = O.setup(lev_prob, O.Params(coarse_direct=0))
+    for lev in h.levels:
+        assert np.abs(O.matvec(lev, np.ones(lev.n))).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Relaxation, V-cycle, PCG (Sections 3.4, 3.5, 4)
+# ---------------------------------------------------------------------------
+
+def _dense(prob):
+    A, _ = C.assemble_problem(prob)
+    return A.toarray()
+
+
+@pytest.mark.parametrize("prob", SMALL[:9], ids=IDS[:9])
+def test_pcg_matches_dense_solve(prob):
+    h = O.setup(prob)
+    b = prob.b[0]
+    res = O.pcg(h, b, tol=1e-13, max_iter=300)
+    assert res.converged
+    A = _dense(prob)
+    xs = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) <= max(cond * 1e-13, 1e-12)
+
+
+@pytest.mark.parametrize("prob", SMALL, ids=IDS)
+def test_vcycle_symmetric_positive(prob):
+    for params in (O.Params(), O.Params(relax=1)):
+        h = O.setup(prob, params)
+        r1 = P.SplitMix64(1).uniform_pm1(prob.n)
+        r2 = P.SplitMix64(2).uniform_pm1(prob.n)
+        a = O.vcycle(h, r1) @ r2
+        b = r1 @ O.vcycle(h, r2)
+        assert abs(a - b) <= 1e-11 * (abs(a) + abs(b))
+        assert O.vcycle(h, r1) @ r1 > 0
+
+
+def _vcycle_contraction(h, A, iters=40):
+    """Largest |eigenvalue| of I - V A by power iteration."""
+    e = P.SplitMix64(3).uniform_pm1(A.shape[0])
+    rho = 0.0
+    for _ in range(iters):
+        e2 = e - O.vcycle(h, A @ e)
+        rho = np.linalg.norm(e2) / np.linalg.norm(e)
+        e = e2 / np.linalg.norm(e2)
+    return rho
+
+
+def test_vcycle_converges_on_poisson():
+    """Measured bound (parity unpinned against the paper): the V(1,1) cycle is a
+    contraction on the Poisson problem, and its factor does not grow with n."""
+    rhos = []
+    for n in (6, 10, 14):
+        prob = P.laplace7(n)
+        A, _ = C.assemble_problem(prob)
+        rhos.append(_vcycle_contraction(O.setup(prob), A))
+    assert max(rhos) < 0.8
+    assert rhos[-1] < rhos[0] + 0.15
+
+
+def test_l1_jacobi_convergent():
+    """L1-Jacobi is convergent for SPD A (Section 3.4): rho(I - M^-1 A) < 1."""
+    for prob in (P.var27(n=5, block=2, seed=2), P.multipart_aniso(m=3, layout=(2, 2, 1), seed=4)):
+        h = O.setup(prob, O.Params(relax=1, relax_factor=1.0))
+        A = _dense(prob)
+        M = h.levels[0].Dinv
+        ev = np.linalg.eigvals(np.eye(len(M)) - M[:, None] * A)
+        assert np.abs(ev).max() < 1.0
+
+
+def test_coarsest_is_one_cell_per_part():
+    prob = P.multipart_aniso(m=5, layout=(2, 2, 1), seed=8)
+    h = O.setup(prob)
+    assert h.levels[-1].n == prob.nparts
+
+
+# ---------------------------------------------------------------------------
+# Differentiation (adjoint solve and coefficient gradient)
+# ---------------------------------------------------------------------------
+
+def test_coef_gradient_matches_finite_difference():
+    prob = P.multipart_aniso(m=3, layout=(2, 1, 1), seed=6)
+    A = _dense(prob)
+    b = prob.b[0]
+    xt = P.SplitMix64(7).uniform_pm1(prob.n)
+    x = np.linalg.solve(A, b)
+    lam = np.linalg.solve(A.T, x - xt)
+    lev = O.level0_from_problem(prob)
+    grads = O.coef_gradient(lev, lam, x)
+    # perturb the diagonal coefficient of one cell of part 1
+    cell = (1, 2, 0)   # k, j, i
+    h = 1e-6
+    vals = []
+    for s in (1, -1):
+        pr = P.multipart_aniso(m=3, layout=(2, 1, 1), seed=6)
+        pr.coef[1][0] = pr.coef[1][0].copy()
+        pr.coef[1][0][cell] += s * h
+        xx = np.linalg.solve(_dense(pr), b)
+        vals.append(0.5 * np.sum((xx - xt) ** 2))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - grads[1][(0, 0, 0)][cell]) <= 1e-6 * abs(fd) + 1e-10
+
+
+def test_diffusion_gradient_matches_finite_difference():
+    prob = P.diffusion_exp(n=5, seed=4, nfd=6)
+    g = prob.extra["g"]
+    xt = prob.extra["x_t"]
+    b = prob.b[0]
+
+    def loss(gg):
+        A = _dense(P.diffusion_from_g(gg, b))
+        xx = np.linalg.solve(A, b)
+        return 0.5 * np.sum((xx - xt) ** 2)
+
+    A = _dense(prob)
+    x = np.linalg.solve(A, b)
+    lam = np.linalg.solve(A, x - xt)
+    grad = O.diffusion_exp_gradient(g, lam, x).reshape(-1)
+    for c in prob.extra["fd_cells"]:
+        h = 1e-5
+        gp = g.copy().reshape(-1)
+        gm = g.copy().reshape(-1)
+        gp[c] += h
+        gm[c] -= h
+        fd = (loss(gp.reshape(g.shape)) - loss(gm.reshape(g.shape))) / (2 * h)
+        assert abs(fd - grad[c]) <= 1e-6 * max(abs(fd), 1e-8) + 1e-11
+
+
+def test_adjoint_solve_uses_same_hierarchy():
+    """A is symmetric, so the adjoint system A^T lam = x - x_t is solved with
+    the forward hierarchy; the adjoint identity <lam, A dx> = <A lam, dx> holds."""
+    prob = P.diffusion_exp(n=6, seed=4, nfd=2)
+    h = O.setup(prob)
+    lev = h.levels[0]
+    lam = P.SplitMix64(8).uniform_pm1(prob.n)
+    dx = P.SplitMix64(9).uniform_pm1(prob.n)
+    assert abs(lam @ O.matvec(lev, dx) - O.matvec(lev, lam) @ dx) < 1e-12 * prob.n
+    xt = prob.extra["x_t"]
+    x = O.pcg(h, prob.b[0], tol=1e-13).x
+    lam = O.pcg(h, x - xt, tol=1e-13).x
+    A = _dense(prob)
+    assert np.linalg.norm(A @ lam - (x - xt)) <= 1e-11 * np.linalg.norm(x - xt)
