@@ -1,0 +1,206 @@
+/*
+ * ssamg.h - C ABI of a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of semi-structured algebraic multigrid (SSAMG; Magri, Falgout and
+ * Yang, arXiv 2205.14273).
+ *
+ * Objects follow the paper's semi-structured interface (Section 2): a grid of
+ * parts, each one logically rectangular box of cell-centred indices; a
+ * stencil of offsets shared by the parts, whose coefficients are either
+ * constant over a part or given per cell; and inter-part couplings (the
+ * unstructured matrix U).  A = S + U.
+ *
+ * Conventions for every call:
+ *  - Return value: SSAMG_OK (0) on success, SSAMG_NOT_CONVERGED (1) as a
+ *    warning from the solves, a negative ssamg_status on failure.  A failed
+ *    call leaves its objects unchanged unless stated otherwise.
+ *  - Handles are opaque and owned by the library; *_destroy frees them.
+ *  - Vectors are FP64, parts in order, each part's box with i fastest, then
+ *    j, then k (N = total number of cells).  Pointers marked "device" are
+ *    CUDA device pointers owned by the caller; they are read or written
+ *    asynchronously on the given stream.  Pointers marked "host" are copied
+ *    before the call returns.
+ *  - stream: a cudaStream_t (NULL = legacy default stream).
+ *  - Objects are not thread-safe; use one handle per host thread.
+ */
+#ifndef SSAMG_H
+#define SSAMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssamg_grid_s* ssamg_grid;
+typedef struct ssamg_matrix_s* ssamg_matrix;
+typedef struct ssamg_solver_s* ssamg_solver;
+
+typedef enum {
+  SSAMG_OK = 0,
+  SSAMG_NOT_CONVERGED = 1,   /* iteration limit reached; stats are filled in */
+  SSAMG_ERR_ARG = -1,        /* invalid argument (index, size, box, offset) */
+  SSAMG_ERR_STATE = -2,      /* call out of order (e.g. solve before setup) */
+  SSAMG_ERR_OOM = -3,        /* device or host allocation failed */
+  SSAMG_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+  SSAMG_ERR_BREAKDOWN = -5,  /* PCG breakdown (p.Ap <= 0, NaN/Inf) or a non-SPD coarsest operator */
+  SSAMG_ERR_TIMEOUT = -6,    /* a bounded device wait gave up */
+  SSAMG_ERR_UNSUPPORTED = -7 /* a size limit of this implementation was exceeded */
+} ssamg_status;
+
+/* Human-readable text for a status code (static storage). */
+const char* ssamg_status_string(int status);
+/* Detail of the last failure on the calling host thread (valid until the
+ * next failing call on that thread). */
+const char* ssamg_last_error(void);
+
+/* ---------------------------------------------------------------- grid ---
+ * Section 2 (semi-structured grid): nparts parts with independent index
+ * spaces.  ndim in {1,2,3}; unused dimensions must have lo = hi.
+ * This implementation takes one box per part (the part's bounding box,
+ * Section 3.1 footnote, is then the box itself). */
+int ssamg_grid_create(int ndim, int nparts, ssamg_grid* out);
+/* Inclusive lower and upper corners of the box of `part` (3 ints each). */
+int ssamg_grid_set_box(ssamg_grid g, int part, const int lo[3], const int hi[3]);
+/* Checks that every part has a non-empty box; freezes the grid. */
+int ssamg_grid_assemble(ssamg_grid g);
+/* Total number of cells (valid after assemble), or -1. */
+long long ssamg_grid_num_cells(ssamg_grid g);
+void ssamg_grid_destroy(ssamg_grid g);
+
+/* -------------------------------------------------------------- matrix ---
+ * Section 2 (A = S + U).  offsets: nentries x 3 ints in {-1,0,1}, shared by
+ * all parts (at most 27 entries, each offset at most once).  S(c, c+o) is the
+ * entry's coefficient at c when c+o lies in the part's box and zero
+ * otherwise: connections that leave a part are either a physical boundary
+ * (eliminated) or part of U.  The matrix must be symmetric positive definite
+ * for the solves; symmetry of U is the caller's duty. */
+int ssamg_matrix_create(ssamg_grid g, int nentries, const int* offsets, ssamg_matrix* out);
+/* Entry `entry` of part `part` is `value` at every cell. */
+int ssamg_matrix_set_constant(ssamg_matrix A, int part, int entry, double value);
+/* Entry `entry` of part `part` varies per cell: vals holds the part's cells
+ * in vector order (i fastest).  vals_on_device: 0 = host pointer, 1 = device
+ * pointer; the values are copied either way.  Values of connections that
+ * leave the box are ignored. */
+int ssamg_matrix_set_box_values(ssamg_matrix A, int part, int entry, const double* vals,
+                                int vals_on_device);
+/* Adds n couplings U(row, col) += vals[t] (host arrays, copied).  Row cell:
+ * part[t], absolute index idx[3t..3t+2]; column cell: nbor_part[t],
+ * nbor_idx[3t..3t+2].  dir[3t..3t+2] is the offset through which the row's
+ * cell leaves its part toward the column (one component +-1 for a face
+ * coupling; 0,0,0 for a non-geometric one); it marks the part boundaries that
+ * interpolation must not cross (Section 3.2).  Rows must lie on a face of
+ * their part's box and columns in a different part (the Theorem of Section
+ * 3.3 keeps coarse couplings on part boundaries).  Duplicates are summed. */
+int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int* part, const int* idx,
+                               const int* dir, const int* nbor_part, const int* nbor_idx,
+                               const double* vals);
+/* Validates and uploads the matrix to the device (synchronous on stream). */
+int ssamg_matrix_assemble(ssamg_matrix A, void* stream);
+void ssamg_matrix_destroy(ssamg_matrix A);
+
+/* -------------------------------------------------------------- solver --- */
+typedef struct {
+  int precision;       /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 PCG */
+  int relax;           /* 0: weighted Jacobi (Eq. relax1); 1: L1 Jacobi (Section 3.4) */
+  double relax_factor; /* <= 0: omega_p of Eq. relax1 (relax 0) or 3/2 (relax 1) */
+  int skip;            /* reserved (Section 3.4 "skip"); must be 0 */
+  int max_levels;      /* l_max of Section 3.1 (default 64) */
+  long long s_max;     /* coarsening stops at total size <= s_max; <= 0: number of parts */
+  double tol;          /* PCG stop: ||r||_2 <= tol ||b||_2 (default 1e-8) */
+  int max_iter;        /* PCG iteration limit (default 200) */
+  int coarse_direct;   /* 1: dense Cholesky on the coarsest level; 0: one relaxation sweep (Section 3.5) */
+  int flexible;        /* 1: Polak-Ribiere beta (for the FP32 cycle); 0: Fletcher-Reeves */
+  int use_graph;       /* 1: replay the cycle as a CUDA graph */
+} ssamg_params;
+
+typedef struct {
+  int iterations;
+  int converged;
+  double rel_res;       /* ||r_k|| / ||b|| of the recursive residual */
+  double true_rel_res;  /* ||b - A x|| / ||b|| recomputed at exit (FP64) */
+  int num_levels;
+  long long coarse_size;
+  double operator_complexity; /* sum of stored stencil+U entries over levels / level 0 */
+} ssamg_stats;
+
+/* Fills *p with the defaults listed above. */
+void ssamg_params_default(ssamg_params* p);
+int ssamg_solver_create(const ssamg_params* p, ssamg_solver* out);
+void ssamg_solver_destroy(ssamg_solver s);
+
+/* Builds the hierarchy (Sections 3.1-3.4): per-part coupling sums and
+ * spacings W, Algorithm 1, interpolation (Eq. prolEx), Galerkin coarse
+ * operators (Eq. galerkin) and relaxation diagonals, then factors the
+ * coarsest operator.  The matrix must stay alive until the solver is
+ * destroyed or set up again.  Synchronises `stream`. */
+int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream);
+
+/* PCG preconditioned by one V(1,1) cycle (Section 4), x0 = 0 when
+ * zero_guess != 0, else x holds x0.  b, x: device, nrhs vectors of N
+ * doubles each (solved one after another).  Stops at
+ * ||r|| <= tol ||b||.  st may be NULL (stats of the last right-hand side). */
+int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess,
+                void* stream, ssamg_stats* st);
+/* Same as ssamg_solve with host b and x; the copies are part of the call. */
+int ssamg_solve_host(ssamg_solver s, const double* b, double* x, int nrhs, void* stream,
+                     ssamg_stats* st);
+/* Adjoint solve A^T lambda = g with the forward hierarchy (A is symmetric,
+ * so A^T = A and the same V-cycle applies).  g, lambda: device. */
+int ssamg_adjoint_solve(ssamg_solver s, const double* g, double* lambda, int nrhs, void* stream,
+                        ssamg_stats* st);
+/* dL/da_e(c) = -lambda_c x_{c+o_e} for every entry e and cell c (zero where
+ * c+o_e leaves the box): the gradient of L(x(A)) with respect to the level-0
+ * stencil coefficients, given lambda = A^-T dL/dx.  lambda, x: device, N
+ * doubles.  dcoef: device, nentries x N doubles (entry-major). */
+int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const double* x, double* dcoef,
+                        void* stream);
+/* dL/dg for the 7-point harmonic-mean diffusion operator with kappa = exp(g)
+ * on one part (off-diagonal -2 k_c k_n/(k_c+k_n), diagonal = sum |off| + k_c
+ * per Dirichlet face): dL/dg_c = k_c (sum over interior faces of
+ * -2 k_n^2/(k_c+k_n)^2 (lam_c - lam_n)(x_c - x_n) - lam_c x_c per Dirichlet
+ * face).  g, lambda, x, dg: device, N doubles; part 0 of the solver's grid. */
+int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, const double* lambda,
+                                 const double* x, double* dg, void* stream);
+
+/* One V(1,1) cycle z = M r (device pointers; in the solver's precision). */
+int ssamg_precondition(ssamg_solver s, const double* r, double* z, void* stream);
+/* y = A_l x on level l (FP64, device pointers of the level's size). */
+int ssamg_level_matvec(ssamg_solver s, int level, const double* x, double* y, void* stream);
+
+/* ------------------------------------------------------- introspection ---
+ * For tests and diagnostics (host copies; synchronous). */
+int ssamg_num_levels(ssamg_solver s);
+/* Per level and part: box corners, d* (-1 when the part is not coarsened or
+ * on the coarsest level), omega_p (Eq. relax1), number of stencil entries and
+ * their offsets (nentries x 3 ints, up to 27), offset of the part in the
+ * level vector.  Any output pointer may be NULL. */
+int ssamg_level_part_info(ssamg_solver s, int level, int part, int* lo, int* hi, int* dstar,
+                          double* omega, int* nentries, int* offsets, long long* cell_offset);
+/* Level size and number of U rows and nonzeros. */
+int ssamg_level_sizes(ssamg_solver s, int level, long long* ncells, long long* u_rows,
+                      long long* u_nnz);
+/* Copies level data to host memory:
+ *  what 0: stencil coefficients of (part, entry): ncells(part) doubles
+ *  what 1: P west weights of part (fine points only, see below)
+ *  what 2: P east weights of part
+ *  what 3: smoother diagonal omega M^-1 of the whole level (N_l doubles)
+ *  what 4: U row pointers (u_rows+1 ints)   what 5: U row cells (u_rows ints)
+ *  what 6: U column cells (u_nnz ints)       what 7: U values (u_nnz doubles)
+ *  what 8: U direction bits (u_nnz bytes)
+ * The P weights of a coarsened part are stored for its fine points only: the
+ * box with its d* extent replaced by (n + p) / 2 (p = lo[d*] mod 2), cell
+ * (..., F, ...) being fine cell 2F + 1 - p along d*.  n is the number of
+ * elements the destination holds; it must equal the data size. */
+int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, void* dst,
+                     long long n);
+/* Per-part coupling sums c (n_parts x 3) and spacings W (n_parts x 3) of
+ * Section 3.1 (W = +inf encoded as HUGE_VAL). */
+int ssamg_spacings(ssamg_solver s, double* c, double* W);
+
+/* Host-only check of the run-time division constants the kernels use to
+ * split a linear cell index into (i, j, k): compares against plain division
+ * for `trials` pseudo-random (n, d) pairs.  Returns 0 when all agree. */
+int ssamg_selftest_fastdiv(unsigned long long seed, int trials);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SSAMG_H */

@@ -1,0 +1,1233 @@
+// C ABI of the SSAMG library: grid / matrix / solver objects, the setup
+// driver (Sections 3.1-3.4) and the PCG + V(1,1) solve driver (Section 4).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "ssamg_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Arena: chunked bump allocator.  A setup with the same sizes as the previous
+// one walks the same chunks in the same order and allocates nothing.
+// ---------------------------------------------------------------------------
+void* Arena::alloc(size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  while (cur < chunks.size()) {
+    if (used + bytes <= chunks[cur].second) {
+      void* p = chunks[cur].first + used;
+      used += bytes;
+      return p;
+    }
+    ++cur;
+    used = 0;
+  }
+  size_t sz = std::max(bytes, size_t(64) << 20);
+  char* p = nullptr;
+  if (cudaMalloc(&p, sz) != cudaSuccess) {
+    cudaGetLastError();
+    throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
+  }
+  chunks.push_back({p, sz});
+  cur = chunks.size() - 1;
+  used = bytes;
+  return p;
+}
+
+void Arena::release() {
+  for (auto& c : chunks) cudaFree(c.first);
+  chunks.clear();
+  cur = used = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Objects
+// ---------------------------------------------------------------------------
+struct ssamg_grid_s {
+  int ndim = 3, nparts = 0;
+  std::vector<std::array<int, 3>> lo, hi;
+  std::vector<char> set;
+  bool assembled = false;
+  std::vector<long long> off;  // nparts + 1
+  long long N = 0;
+  long long ncell(int p) const {
+    long long n = 1;
+    for (int d = 0; d < 3; ++d) n *= hi[p][d] - lo[p][d] + 1;
+    return n;
+  }
+};
+
+struct ssamg_matrix_s {
+  ssamg_grid g = nullptr;
+  int nent = 0;
+  int o[SSAMG_MAXE][3];
+  std::vector<std::vector<double>> cval;      // [part][entry]
+  std::vector<std::vector<double*>> tmpvar;   // device values set but not yet packed
+  std::vector<std::vector<char>> isset, isvar;
+  // couplings (host, appended)
+  std::vector<int> c_part, c_idx, c_dir, c_npart, c_nidx;
+  std::vector<double> c_val;
+  // assembled (device)
+  bool assembled = false;
+  double* coef = nullptr;
+  long long ncoef = 0;
+  std::vector<std::vector<long long>> coef_off;  // [part][entry], -1 const
+  int nr = 0;
+  long long nnz = 0;
+  int *u_rows = nullptr, *u_ptr = nullptr, *u_col = nullptr, *u_map = nullptr;
+  double* u_val = nullptr;
+  unsigned char* u_bits = nullptr;
+  std::vector<char> has_u;
+  int version = 0;
+  void free_device() {
+    cudaFree(coef);
+    cudaFree(u_rows);
+    cudaFree(u_ptr);
+    cudaFree(u_col);
+    cudaFree(u_map);
+    cudaFree(u_val);
+    cudaFree(u_bits);
+    coef = nullptr;
+    u_rows = u_ptr = u_col = u_map = nullptr;
+    u_val = nullptr;
+    u_bits = nullptr;
+  }
+  ~ssamg_matrix_s() {
+    free_device();
+    for (auto& v : tmpvar)
+      for (auto* p : v) cudaFree(p);
+  }
+};
+
+struct GraphSet {
+  cudaGraphExec_t pcg = nullptr;
+  cudaGraphExec_t vcycle = nullptr;
+  void reset() {
+    if (pcg) cudaGraphExecDestroy(pcg);
+    if (vcycle) cudaGraphExecDestroy(vcycle);
+    pcg = vcycle = nullptr;
+  }
+};
+
+struct ssamg_solver_s {
+  ssamg_params prm;
+  Arena arena;
+  std::vector<Level> lev;
+  ssamg_matrix A = nullptr;
+  bool ready = false;
+  int ndim = 3;
+  std::vector<double> c, W;  // nparts x 3
+  // coarsest
+  int nL = 0;
+  double* chol = nullptr;
+  // PCG work (FP64, level 0 size)
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
+         *zprev = nullptr, *partial = nullptr, *tres = nullptr;
+  PcgScalars* sc = nullptr;
+  PcgScalars* h_sc = nullptr;  // pinned
+  int* h_int = nullptr;        // pinned scratch
+  double* h_dbl = nullptr;
+  int* d_err = nullptr;
+  int nblk_red = 0;
+  cudaStream_t cs = nullptr;  // capture stream
+  GraphSet graphs;
+  ~ssamg_solver_s() {
+    graphs.reset();
+    if (cs) cudaStreamDestroy(cs);
+    if (h_sc) cudaFreeHost(h_sc);
+    if (h_int) cudaFreeHost(h_int);
+    if (h_dbl) cudaFreeHost(h_dbl);
+  }
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(const SsamgError& e) {
+  g_last_error = e.msg;
+  return e.code;
+}
+
+#define API_BEGIN try {
+#define API_END                                       \
+  }                                                   \
+  catch (const SsamgError& e) { return fail(e); }     \
+  catch (const std::bad_alloc&) { return SSAMG_ERR_OOM; }
+
+inline void argcheck(bool ok, const char* msg) {
+  if (!ok) throw SsamgError{SSAMG_ERR_ARG, msg};
+}
+
+inline long long cdivll(long long a, long long b) { return (a + b - 1) / b; }
+inline int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+inline int ceildiv2(int v) { return -floordiv2(-v); }
+
+template <class T>
+T* aalloc(Arena& a, long long n) {
+  return reinterpret_cast<T*>(a.alloc(sizeof(T) * (size_t)std::max<long long>(n, 1)));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Status strings
+// ---------------------------------------------------------------------------
+extern "C" const char* ssamg_status_string(int s) {
+  switch (s) {
+    case SSAMG_OK: return "ok";
+    case SSAMG_NOT_CONVERGED: return "not converged within max_iter";
+    case SSAMG_ERR_ARG: return "invalid argument";
+    case SSAMG_ERR_STATE: return "call out of order";
+    case SSAMG_ERR_OOM: return "out of memory";
+    case SSAMG_ERR_CUDA: return "CUDA error";
+    case SSAMG_ERR_BREAKDOWN: return "breakdown (non-SPD operator or NaN)";
+    case SSAMG_ERR_TIMEOUT: return "device wait timed out";
+    case SSAMG_ERR_UNSUPPORTED: return "size limit of this implementation exceeded";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* ssamg_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// Grid
+// ---------------------------------------------------------------------------
+extern "C" int ssamg_grid_create(int ndim, int nparts, ssamg_grid* out) {
+  if (!out || ndim < 1 || ndim > 3 || nparts < 1) return SSAMG_ERR_ARG;
+  auto* g = new (std::nothrow) ssamg_grid_s;
+  if (!g) return SSAMG_ERR_OOM;
+  g->ndim = ndim;
+  g->nparts = nparts;
+  g->lo.assign(nparts, {0, 0, 0});
+  g->hi.assign(nparts, {0, 0, 0});
+  g->set.assign(nparts, 0);
+  *out = g;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_grid_set_box(ssamg_grid g, int part, const int lo[3], const int hi[3]) {
+  if (!g || g->assembled) return g ? SSAMG_ERR_STATE : SSAMG_ERR_ARG;
+  if (part < 0 || part >= g->nparts || !lo || !hi) return SSAMG_ERR_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (hi[d] < lo[d]) return SSAMG_ERR_ARG;
+    if (d >= g->ndim && hi[d] != lo[d]) return SSAMG_ERR_ARG;
+  }
+  long long n = 1;
+  for (int d = 0; d < 3; ++d) n *= (long long)hi[d] - lo[d] + 1;
+  if (n > (1ll << 30)) return SSAMG_ERR_UNSUPPORTED;
+  for (int d = 0; d < 3; ++d) {
+    g->lo[part][d] = lo[d];
+    g->hi[part][d] = hi[d];
+  }
+  g->set[part] = 1;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_grid_assemble(ssamg_grid g) {
+  if (!g) return SSAMG_ERR_ARG;
+  for (int p = 0; p < g->nparts; ++p)
+    if (!g->set[p]) return SSAMG_ERR_ARG;
+  g->off.assign(g->nparts + 1, 0);
+  for (int p = 0; p < g->nparts; ++p) g->off[p + 1] = g->off[p] + g->ncell(p);
+  if (g->off.back() >= (1ll << 31)) return SSAMG_ERR_UNSUPPORTED;
+  g->N = g->off.back();
+  g->assembled = true;
+  return SSAMG_OK;
+}
+
+extern "C" long long ssamg_grid_num_cells(ssamg_grid g) {
+  return (g && g->assembled) ? g->N : -1;
+}
+
+extern "C" void ssamg_grid_destroy(ssamg_grid g) { delete g; }
+
+// ---------------------------------------------------------------------------
+// Matrix
+// ---------------------------------------------------------------------------
+extern "C" int ssamg_matrix_create(ssamg_grid g, int nentries, const int* offsets,
+                                   ssamg_matrix* out) {
+  if (!g || !out || !offsets || nentries < 1 || nentries > SSAMG_MAXE) return SSAMG_ERR_ARG;
+  if (!g->assembled) return SSAMG_ERR_STATE;
+  for (int e = 0; e < nentries; ++e) {
+    for (int d = 0; d < 3; ++d) {
+      int v = offsets[3 * e + d];
+      if (v < -1 || v > 1) return SSAMG_ERR_ARG;
+      if (d >= g->ndim && v != 0) return SSAMG_ERR_ARG;
+    }
+    for (int f = 0; f < e; ++f)
+      if (offsets[3 * f] == offsets[3 * e] && offsets[3 * f + 1] == offsets[3 * e + 1] &&
+          offsets[3 * f + 2] == offsets[3 * e + 2])
+        return SSAMG_ERR_ARG;
+  }
+  auto* A = new (std::nothrow) ssamg_matrix_s;
+  if (!A) return SSAMG_ERR_OOM;
+  A->g = g;
+  A->nent = nentries;
+  for (int e = 0; e < nentries; ++e)
+    for (int d = 0; d < 3; ++d) A->o[e][d] = offsets[3 * e + d];
+  A->cval.assign(g->nparts, std::vector<double>(nentries, 0.0));
+  A->tmpvar.assign(g->nparts, std::vector<double*>(nentries, nullptr));
+  A->isset.assign(g->nparts, std::vector<char>(nentries, 0));
+  A->isvar.assign(g->nparts, std::vector<char>(nentries, 0));
+  *out = A;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_matrix_set_constant(ssamg_matrix A, int part, int entry, double value) {
+  if (!A || part < 0 || part >= A->g->nparts || entry < 0 || entry >= A->nent) return SSAMG_ERR_ARG;
+  if (A->tmpvar[part][entry]) {
+    cudaFree(A->tmpvar[part][entry]);
+    A->tmpvar[part][entry] = nullptr;
+  }
+  A->cval[part][entry] = value;
+  A->isvar[part][entry] = 0;
+  A->isset[part][entry] = 1;
+  A->assembled = false;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_matrix_set_box_values(ssamg_matrix A, int part, int entry, const double* vals,
+                                           int vals_on_device) {
+  if (!A || !vals || part < 0 || part >= A->g->nparts || entry < 0 || entry >= A->nent)
+    return SSAMG_ERR_ARG;
+  long long n = A->g->ncell(part);
+  double*& dst = A->tmpvar[part][entry];
+  if (!dst && cudaMalloc(&dst, sizeof(double) * n) != cudaSuccess) {
+    cudaGetLastError();
+    dst = nullptr;
+    return SSAMG_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpy(dst, vals, sizeof(double) * n,
+                             vals_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    g_last_error = cudaGetErrorString(e);
+    return SSAMG_ERR_CUDA;
+  }
+  A->isvar[part][entry] = 1;
+  A->isset[part][entry] = 1;
+  A->assembled = false;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int* part,
+                                          const int* idx, const int* dir, const int* nbor_part,
+                                          const int* nbor_idx, const double* vals) {
+  if (!A || n < 0) return SSAMG_ERR_ARG;
+  if (n == 0) return SSAMG_OK;
+  if (!part || !idx || !dir || !nbor_part || !nbor_idx || !vals) return SSAMG_ERR_ARG;
+  const ssamg_grid g = A->g;
+  for (long long t = 0; t < n; ++t) {
+    int p = part[t], q = nbor_part[t];
+    if (p < 0 || p >= g->nparts || q < 0 || q >= g->nparts || p == q) return SSAMG_ERR_ARG;
+    bool face = false;
+    for (int d = 0; d < 3; ++d) {
+      int a = idx[3 * t + d], b = nbor_idx[3 * t + d];
+      if (a < g->lo[p][d] || a > g->hi[p][d] || b < g->lo[q][d] || b > g->hi[q][d]) return SSAMG_ERR_ARG;
+      if (d < g->ndim && (a == g->lo[p][d] || a == g->hi[p][d])) face = true;
+      int dv = dir[3 * t + d];
+      if (dv < -1 || dv > 1) return SSAMG_ERR_ARG;
+      if (dv > 0 && a != g->hi[p][d]) return SSAMG_ERR_ARG;
+      if (dv < 0 && a != g->lo[p][d]) return SSAMG_ERR_ARG;
+    }
+    if (!face) return SSAMG_ERR_ARG;
+  }
+  A->c_part.insert(A->c_part.end(), part, part + n);
+  A->c_npart.insert(A->c_npart.end(), nbor_part, nbor_part + n);
+  A->c_idx.insert(A->c_idx.end(), idx, idx + 3 * n);
+  A->c_nidx.insert(A->c_nidx.end(), nbor_idx, nbor_idx + 3 * n);
+  A->c_dir.insert(A->c_dir.end(), dir, dir + 3 * n);
+  A->c_val.insert(A->c_val.end(), vals, vals + n);
+  A->assembled = false;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
+  if (!A) return SSAMG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  API_BEGIN
+  const ssamg_grid g = A->g;
+  const int np = g->nparts;
+  for (int p = 0; p < np; ++p)
+    for (int e = 0; e < A->nent; ++e)
+      argcheck(A->isset[p][e], "every stencil entry of every part needs a value");
+  A->free_device();
+  // pack variable entries
+  A->coef_off.assign(np, std::vector<long long>(A->nent, -1));
+  long long n = 0;
+  for (int p = 0; p < np; ++p)
+    for (int e = 0; e < A->nent; ++e)
+      if (A->isvar[p][e]) {
+        A->coef_off[p][e] = n;
+        n += g->ncell(p);
+      }
+  A->ncoef = n;
+  SSAMG_CUDA(cudaMalloc(&A->coef, sizeof(double) * std::max<long long>(n, 1)));
+  for (int p = 0; p < np; ++p)
+    for (int e = 0; e < A->nent; ++e)
+      if (A->isvar[p][e])
+        SSAMG_CUDA(cudaMemcpyAsync(A->coef + A->coef_off[p][e], A->tmpvar[p][e],
+                                   sizeof(double) * g->ncell(p), cudaMemcpyDeviceToDevice, st));
+  // couplings: global (row, col), sorted, duplicates merged
+  long long m = (long long)A->c_val.size();
+  struct E {
+    long long row, col;
+    double v;
+    unsigned char bits;
+  };
+  std::vector<E> es((size_t)m);
+  auto gidx = [&](int p, const int* c) {
+    long long nx = g->hi[p][0] - g->lo[p][0] + 1, ny = g->hi[p][1] - g->lo[p][1] + 1;
+    return g->off[p] + ((long long)(c[2] - g->lo[p][2]) * ny + (c[1] - g->lo[p][1])) * nx +
+           (c[0] - g->lo[p][0]);
+  };
+  for (long long t = 0; t < m; ++t) {
+    E& e = es[(size_t)t];
+    e.row = gidx(A->c_part[t], &A->c_idx[3 * t]);
+    e.col = gidx(A->c_npart[t], &A->c_nidx[3 * t]);
+    e.v = A->c_val[t];
+    e.bits = 0;
+    for (int d = 0; d < 3; ++d) {
+      int dv = A->c_dir[3 * t + d];
+      if (dv > 0) e.bits |= (unsigned char)(1u << (2 * d));
+      if (dv < 0) e.bits |= (unsigned char)(1u << (2 * d + 1));
+    }
+  }
+  std::stable_sort(es.begin(), es.end(), [](const E& a, const E& b) {
+    return a.row != b.row ? a.row < b.row : a.col < b.col;
+  });
+  std::vector<int> rows, ptr, col;
+  std::vector<double> val;
+  std::vector<unsigned char> bits;
+  A->has_u.assign(np, 0);
+  for (size_t t = 0; t < es.size();) {
+    size_t s = t;
+    if (rows.empty() || rows.back() != es[s].row) {
+      rows.push_back((int)es[s].row);
+      ptr.push_back((int)col.size());
+    }
+    double v = 0;
+    unsigned char b = 0;
+    while (t < es.size() && es[t].row == es[s].row && es[t].col == es[s].col) {
+      v += es[t].v;
+      b |= es[t].bits;
+      ++t;
+    }
+    col.push_back((int)es[s].col);
+    val.push_back(v);
+    bits.push_back(b);
+  }
+  ptr.push_back((int)col.size());
+  for (int r : rows) {
+    int p = (int)(std::upper_bound(g->off.begin(), g->off.end(), (long long)r) - g->off.begin()) - 1;
+    A->has_u[p] = 1;
+  }
+  A->nr = (int)rows.size();
+  A->nnz = (long long)col.size();
+  if (A->nr > 0) {
+    SSAMG_CUDA(cudaMalloc(&A->u_rows, sizeof(int) * A->nr));
+    SSAMG_CUDA(cudaMalloc(&A->u_ptr, sizeof(int) * (A->nr + 1)));
+    SSAMG_CUDA(cudaMalloc(&A->u_col, sizeof(int) * A->nnz));
+    SSAMG_CUDA(cudaMalloc(&A->u_val, sizeof(double) * A->nnz));
+    SSAMG_CUDA(cudaMalloc(&A->u_bits, A->nnz));
+    SSAMG_CUDA(cudaMalloc(&A->u_map, sizeof(int) * g->N));
+    SSAMG_CUDA(cudaMemcpyAsync(A->u_rows, rows.data(), sizeof(int) * A->nr, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(A->u_ptr, ptr.data(), sizeof(int) * (A->nr + 1), cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(A->u_col, col.data(), sizeof(int) * A->nnz, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(A->u_val, val.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(A->u_bits, bits.data(), A->nnz, cudaMemcpyHostToDevice, st));
+    Level tmp;
+    tmp.N = g->N;
+    tmp.nr = A->nr;
+    tmp.u_rows = A->u_rows;
+    tmp.u_map = A->u_map;
+    launch_umap_level0(tmp, st);
+  }
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  A->assembled = true;
+  A->version++;
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" void ssamg_matrix_destroy(ssamg_matrix A) { delete A; }
+
+// ---------------------------------------------------------------------------
+// Solver: parameters
+// ---------------------------------------------------------------------------
+extern "C" void ssamg_params_default(ssamg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->precision = 0;
+  p->relax = 0;
+  p->relax_factor = 0.0;
+  p->skip = 0;
+  p->max_levels = 64;
+  p->s_max = 0;
+  p->tol = 1e-8;
+  p->max_iter = 200;
+  p->coarse_direct = 1;
+  p->flexible = 0;
+  p->use_graph = 1;
+}
+
+extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
+  if (!prm || !out) return SSAMG_ERR_ARG;
+  if (prm->precision < 0 || prm->precision > 1 || prm->relax < 0 || prm->relax > 1 ||
+      prm->skip != 0 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
+    return SSAMG_ERR_ARG;
+  auto* s = new (std::nothrow) ssamg_solver_s;
+  if (!s) return SSAMG_ERR_OOM;
+  s->prm = *prm;
+  *out = s;
+  return SSAMG_OK;
+}
+
+extern "C" void ssamg_solver_destroy(ssamg_solver s) { delete s; }
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+namespace {
+
+int choose_direction(const double* Wp, const int* ext, int ndim) {
+  // argmin_d W_pd over dimensions with extent > 1; ties -> smallest index
+  int best = -1;
+  for (int d = 0; d < ndim; ++d)
+    if (ext[d] > 1 && (best < 0 || Wp[d] < Wp[best])) best = d;
+  if (best < 0) {
+    best = 0;
+    for (int d = 1; d < ndim; ++d)
+      if (Wp[d] < Wp[best]) best = d;
+  }
+  return best;
+}
+
+double relaxation_weight(const double* Wp, int dstar, int ndim) {
+  // omega_p = 2 / (3 - beta_p / alpha_p) (Eqs. relax1, alpha-beta)
+  double alpha = 0, inv_d = 0;
+  for (int d = 0; d < ndim; ++d) {
+    double v = std::isfinite(Wp[d]) ? 1.0 / (Wp[d] * Wp[d]) : 0.0;
+    alpha += v;
+    if (d == dstar) inv_d = v;
+  }
+  if (alpha <= 0.0) return 1.0;
+  return 2.0 / (3.0 - (alpha - inv_d) / alpha);
+}
+
+void fill_dpart(DPart& dp, const PartH& h) {
+  std::memset(&dp, 0, sizeof(dp));
+  for (int d = 0; d < 3; ++d) dp.n[d] = h.n[d];
+  dp.ncell = (int)h.ncell;
+  dp.off = h.off;
+  dp.nent = h.nent;
+  dp.dstar = h.dstar;
+  dp.par = h.par;
+  dp.omega = h.omega;
+  dp.has_u = h.has_u;
+  dp.dx = make_fastdiv(h.n[0]);
+  dp.dxy = make_fastdiv(h.n[0] * h.n[1]);
+  std::memset(dp.slot, -1, sizeof(dp.slot));
+  for (int e = 0; e < h.nent; ++e) {
+    for (int d = 0; d < 3; ++d) dp.o[e][d] = (signed char)h.o[e][d];
+    dp.disp[e] = h.o[e][0] + h.o[e][1] * h.n[0] + h.o[e][2] * h.n[0] * h.n[1];
+    dp.coef[e] = h.var[e] ? h.coef_off[e] : -1;
+    dp.cval[e] = h.cval[e];
+    dp.slot[(h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1)] = (signed char)e;
+  }
+  for (int d = 0; d < 3; ++d) dp.nf[d] = h.nf[d];
+  dp.nfine = (int)h.nfine;
+  dp.poff = h.poff;
+  dp.fdx = make_fastdiv(std::max(1, h.nf[0]));
+  dp.fdxy = make_fastdiv(std::max(1, h.nf[0] * h.nf[1]));
+}
+
+void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) {
+  const int np = L.np;
+  L.dparts.assign(np, DPart{});
+  std::vector<int> blk(np + 1, 0), fblk(np + 1, 0), cs(np + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    const PartH& h = L.parts[p];
+    blk[p + 1] = blk[p] + (int)cdivll(h.ncell, SSAMG_BLOCK);
+    fblk[p + 1] = fblk[p] + (int)cdivll(h.nfine, SSAMG_BLOCK);
+    cs[p + 1] = cs[p] + (int)h.ncell;
+  }
+  L.nblk = blk[np];
+  L.nfblk = fblk[np];
+  for (int p = 0; p < np; ++p) {
+    DPart& dp = L.dparts[p];
+    fill_dpart(dp, L.parts[p]);
+    dp.blk0 = blk[p];
+    dp.fblk0 = fblk[p];
+    if (next) {
+      const PartH& c = next->parts[p];
+      dp.coff = c.off;
+      for (int d = 0; d < 3; ++d) dp.cn[d] = c.n[d];
+      dp.cncell = (int)c.ncell;
+      dp.cdx = make_fastdiv(c.n[0]);
+      dp.cdxy = make_fastdiv(c.n[0] * c.n[1]);
+    }
+  }
+  if (!L.d_parts) {
+    L.d_parts = aalloc<DPart>(s->arena, np);
+    L.d_blk = aalloc<int>(s->arena, np + 1);
+    L.d_fblk = aalloc<int>(s->arena, np + 1);
+    L.d_cellstart = aalloc<int>(s->arena, np + 1);
+  }
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_cellstart, cs.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+}
+
+void build_hierarchy(ssamg_solver s, cudaStream_t st) {
+  ssamg_matrix A = s->A;
+  const ssamg_grid g = A->g;
+  const int np = g->nparts;
+  const int ndim = g->ndim;
+  const bool fp32 = s->prm.precision == 1;
+  s->ndim = ndim;
+  s->arena.reset();
+  s->graphs.reset();
+  s->lev.clear();
+  s->lev.reserve((size_t)s->prm.max_levels + 1);
+  s->ready = false;
+
+  if (!s->h_sc) {
+    SSAMG_CUDA(cudaMallocHost(&s->h_sc, sizeof(PcgScalars)));
+    SSAMG_CUDA(cudaMallocHost(&s->h_int, sizeof(int) * 16));
+    SSAMG_CUDA(cudaMallocHost(&s->h_dbl, sizeof(double) * 16));
+  }
+
+  // ---- level 0 from the matrix
+  s->lev.emplace_back();
+  Level& L0 = s->lev[0];
+  L0.np = np;
+  L0.N = g->N;
+  L0.parts.resize(np);
+  for (int p = 0; p < np; ++p) {
+    PartH& h = L0.parts[p];
+    std::memset(&h, 0, sizeof(h));
+    for (int d = 0; d < 3; ++d) {
+      h.lo[d] = g->lo[p][d];
+      h.hi[d] = g->hi[p][d];
+      h.n[d] = h.hi[d] - h.lo[d] + 1;
+    }
+    h.ncell = g->ncell(p);
+    h.off = (int)g->off[p];
+    h.dstar = -1;
+    h.nent = A->nent;
+    for (int e = 0; e < A->nent; ++e) {
+      for (int d = 0; d < 3; ++d) h.o[e][d] = A->o[e][d];
+      h.var[e] = A->isvar[p][e];
+      h.cval[e] = A->cval[p][e];
+      h.coef_off[e] = A->coef_off[p][e];
+    }
+    h.has_u = A->has_u[p];
+  }
+  L0.coef = A->coef;
+  L0.ncoef = A->ncoef;
+  L0.nr = A->nr;
+  L0.nnz = A->nnz;
+  L0.u_rows = A->u_rows;
+  L0.u_ptr = A->u_ptr;
+  L0.u_col = A->u_col;
+  L0.u_val = A->u_val;
+  L0.u_bits = A->u_bits;
+  L0.u_map = A->u_map;
+  upload_level(s, L0, nullptr, st);
+
+  // ---- Section 3.1: coupling sums c and spacings W (one sync)
+  double* d_partial = aalloc<double>(s->arena, 3ll * L0.nblk);
+  double* d_c = aalloc<double>(s->arena, 3ll * np);
+  launch_wsum(L0, d_partial, d_c, st);
+  s->c.assign(3 * np, 0.0);
+  SSAMG_CUDA(cudaMemcpyAsync(s->c.data(), d_c, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  s->W.assign(3 * np, HUGE_VAL);
+  for (int p = 0; p < np; ++p) {
+    double cmax = -HUGE_VAL;
+    for (int d = 0; d < ndim; ++d) cmax = std::max(cmax, s->c[3 * p + d]);
+    for (int d = 0; d < ndim; ++d)
+      if (s->c[3 * p + d] > 0 && cmax > 0) s->W[3 * p + d] = std::sqrt(cmax / s->c[3 * p + d]);
+  }
+
+  // ---- Algorithm 1 on the host: boxes, d* and omega per level
+  long long s_max = s->prm.s_max > 0 ? s->prm.s_max : np;
+  std::vector<double> W = s->W;
+  for (;;) {
+    Level& F = s->lev.back();
+    long long total = 0;
+    bool any_active = false;
+    for (auto& h : F.parts) {
+      total += h.ncell;
+      if (h.ncell > 1) any_active = true;
+    }
+    bool last = total <= s_max || (int)s->lev.size() >= s->prm.max_levels || !any_active;
+    for (int p = 0; p < np; ++p) {
+      PartH& h = F.parts[p];
+      int d = choose_direction(&W[3 * p], h.n, ndim);
+      h.omega = relaxation_weight(&W[3 * p], d, ndim);
+      h.dstar = (!last && h.ncell > 1) ? d : -1;
+    }
+    if (last) break;
+    Level C;
+    C.np = np;
+    C.parts.resize(np);
+    long long off = 0;
+    for (int p = 0; p < np; ++p) {
+      PartH& h = F.parts[p];
+      PartH& c = C.parts[p];
+      std::memset(&c, 0, sizeof(c));
+      for (int d = 0; d < 3; ++d) {
+        c.lo[d] = h.lo[d];
+        c.hi[d] = h.hi[d];
+      }
+      c.has_u = h.has_u;
+      c.dstar = -1;
+      if (h.dstar >= 0) {
+        int d = h.dstar;
+        c.lo[d] = ceildiv2(h.lo[d]);
+        c.hi[d] = floordiv2(h.hi[d]);
+        W[3 * p + d] *= 2.0;
+        h.par = h.lo[d] & 1;
+        for (int q = 0; q < 3; ++q) h.nf[q] = h.n[q];
+        h.nf[d] = (h.n[d] + h.par) >> 1;
+        h.nfine = (long long)h.nf[0] * h.nf[1] * h.nf[2];
+        // coarse stencil: fine offsets projected off d*, times {-1,0,1} along d*
+        bool present[27] = {false};
+        for (int e = 0; e < h.nent; ++e)
+          for (int od = -1; od <= 1; ++od) {
+            int o[3] = {h.o[e][0], h.o[e][1], h.o[e][2]};
+            o[d] = od;
+            present[(o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1)] = true;
+          }
+        c.nent = 0;
+        for (int code = 0; code < 27; ++code)
+          if (present[code]) {
+            c.o[c.nent][0] = code % 3 - 1;
+            c.o[c.nent][1] = (code / 3) % 3 - 1;
+            c.o[c.nent][2] = code / 9 - 1;
+            ++c.nent;
+          }
+      } else {
+        c.nent = h.nent;
+        for (int e = 0; e < h.nent; ++e)
+          for (int d = 0; d < 3; ++d) c.o[e][d] = h.o[e][d];
+      }
+      for (int d = 0; d < 3; ++d) c.n[d] = c.hi[d] - c.lo[d] + 1;
+      c.ncell = (long long)c.n[0] * c.n[1] * c.n[2];
+      c.off = (int)off;
+      off += c.ncell;
+      for (int e = 0; e < c.nent; ++e) c.var[e] = 1;
+    }
+    C.N = off;
+    s->lev.push_back(std::move(C));
+  }
+  const int Lc = (int)s->lev.size() - 1;
+
+  // ---- allocation (one arena walk; identical sizes reuse the same memory)
+  for (int l = 0; l <= Lc; ++l) {
+    Level& L = s->lev[l];
+    if (l > 0) {
+      long long n = 0;
+      for (auto& h : L.parts)
+        for (int e = 0; e < h.nent; ++e) {
+          h.coef_off[e] = n;
+          n += h.ncell;
+        }
+      L.ncoef = n;
+      L.coef = aalloc<double>(s->arena, n);
+    }
+    if (fp32) L.coef32 = aalloc<float>(s->arena, L.ncoef);
+    long long nP = 0;
+    for (auto& h : L.parts) {
+      h.poff = (int)nP;
+      nP += h.nfine;
+    }
+    L.nP = nP;
+    if (l < Lc) {
+      L.Pw = aalloc<double>(s->arena, nP);
+      L.Pe = aalloc<double>(s->arena, nP);
+      if (fp32) {
+        L.Pw32 = aalloc<float>(s->arena, nP);
+        L.Pe32 = aalloc<float>(s->arena, nP);
+      }
+    }
+    L.dinv = aalloc<double>(s->arena, L.N);
+    if (fp32) L.dinv32 = aalloc<float>(s->arena, L.N);
+    size_t w = fp32 ? sizeof(float) : sizeof(double);
+    L.x = s->arena.alloc(w * L.N);
+    L.b = s->arena.alloc(w * L.N);
+    L.r = s->arena.alloc(w * L.N);
+    L.t = s->arena.alloc(w * L.N);
+    bool any_u = false;
+    for (auto& h : L.parts) any_u |= h.has_u != 0;
+    if (l > 0 && any_u) L.u_map = aalloc<int>(s->arena, L.N);
+  }
+  for (int l = 0; l <= Lc; ++l) upload_level(s, s->lev[l], l < Lc ? &s->lev[l + 1] : nullptr, st);
+
+  if (fp32) {
+    launch_to_float(L0.coef, L0.coef32, L0.ncoef, st);
+    if (L0.nnz > 0) {
+      L0.u_val32 = aalloc<float>(s->arena, L0.nnz);
+      launch_to_float(L0.u_val, L0.u_val32, L0.nnz, st);
+    }
+  }
+
+  // ---- per level: P (Eq. prolEx), P^T S P and P^T U P (Eq. galerkin)
+  long long maxN = 0;
+  for (int l = 1; l <= Lc; ++l) maxN = std::max(maxN, s->lev[l].N);
+  int* marker = nullptr;
+  int* scan_tmp = nullptr;
+  if (!s->d_err) s->d_err = aalloc<int>(s->arena, 4);
+  SSAMG_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, st));
+  for (int l = 0; l < Lc; ++l) {
+    Level& F = s->lev[l];
+    Level& C = s->lev[l + 1];
+    launch_interp(F, fp32, st);
+    launch_rap_struct(F, C, fp32, st);
+    if (F.nr > 0) {
+      if (!marker) {
+        marker = aalloc<int>(s->arena, maxN + 1);
+        scan_tmp = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
+      }
+      launch_umark(F, C, marker, st);
+      launch_scan(marker, C.N, scan_tmp, st);
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_int, marker + C.N, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SSAMG_CUDA(cudaStreamSynchronize(st));
+      C.nr = s->h_int[0];
+      C.u_rows = aalloc<int>(s->arena, C.nr);
+      C.u_ptr = aalloc<int>(s->arena, C.nr + 1);
+      launch_urows(C, marker, nullptr, st);
+      if (C.nr > 0) {
+        launch_ucount(F, C, C.u_ptr, s->d_err, st);
+        launch_scan(C.u_ptr, C.nr, scan_tmp, st);
+        SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SSAMG_CUDA(cudaStreamSynchronize(st));
+        C.nnz = s->h_int[0];
+        C.u_col = aalloc<int>(s->arena, C.nnz);
+        C.u_val = aalloc<double>(s->arena, C.nnz);
+        C.u_bits = aalloc<unsigned char>(s->arena, C.nnz);
+        if (fp32) C.u_val32 = aalloc<float>(s->arena, C.nnz);
+        launch_ufill(F, C, fp32, s->d_err, st);
+      }
+    } else {
+      C.nr = 0;
+      C.nnz = 0;
+    }
+  }
+  // has_u may be set on parts whose coarse rows vanished; refresh from U_c
+  for (int l = 1; l <= Lc; ++l) {
+    Level& L = s->lev[l];
+    if (L.nr == 0) {
+      bool changed = false;
+      for (auto& h : L.parts)
+        if (h.has_u) {
+          h.has_u = 0;
+          changed = true;
+        }
+      if (changed) upload_level(s, L, l < Lc ? &s->lev[l + 1] : nullptr, st);
+    }
+  }
+
+  // ---- Section 3.4: smoother diagonals
+  for (int l = 0; l <= Lc; ++l) launch_dinv(s->lev[l], s->prm.relax, s->prm.relax_factor, fp32, st);
+
+  // ---- coarsest level: dense Cholesky (FP64)
+  Level& LL = s->lev[Lc];
+  s->nL = (int)LL.N;
+  if (s->prm.coarse_direct) {
+    if (LL.N > 4096) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "coarsest level too large for the dense solve"};
+    s->chol = aalloc<double>(s->arena, LL.N * LL.N);
+    launch_coarse_assemble(LL, s->chol, st);
+    launch_cholesky((int)LL.N, s->chol, s->d_err + 2, st);
+  }
+  SSAMG_CUDA(cudaMemcpyAsync(s->h_int, s->d_err, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  if (s->h_int[0]) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "coarse coupling row exceeds the candidate limit"};
+  if (s->h_int[2]) throw SsamgError{SSAMG_ERR_BREAKDOWN, "coarsest operator is not positive definite"};
+
+  // ---- PCG work vectors
+  long long N = L0.N;
+  s->b = aalloc<double>(s->arena, N);
+  s->x = aalloc<double>(s->arena, N);
+  s->r = aalloc<double>(s->arena, N);
+  s->z = aalloc<double>(s->arena, N);
+  s->p = aalloc<double>(s->arena, N);
+  s->q = aalloc<double>(s->arena, N);
+  s->zprev = aalloc<double>(s->arena, N);
+  s->nblk_red = reduce_blocks(N);
+  s->partial = aalloc<double>(s->arena, 2ll * std::max<long long>(L0.nblk, s->nblk_red));
+  s->tres = aalloc<double>(s->arena, 2);
+  s->sc = aalloc<PcgScalars>(s->arena, 1);
+  s->ready = true;
+}
+
+// One V(1,1) cycle z = M r (r, z: FP64 level-0 vectors).
+template <class T>
+void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream_t st) {
+  auto& Ls = s->lev;
+  const int Lc = (int)Ls.size() - 1;
+  const bool is_f = sizeof(T) == sizeof(float);
+  const T* b0;
+  if (is_f) {
+    launch_cast_d2f(r_in, (float*)Ls[0].b, Ls[0].N, st);
+    b0 = (const T*)Ls[0].b;
+  } else {
+    b0 = (const T*)r_in;
+  }
+  auto coarse = [&](const T* bl, T* xl) {
+    if (s->prm.coarse_direct)
+      launch_coarse_solve<T>(s->nL, s->chol, bl, xl, st);
+    else
+      launch_relax0<T>(Ls[Lc], bl, xl, st);
+  };
+  if (Lc == 0) {
+    T* out = is_f ? (T*)Ls[0].t : (T*)z_out;
+    coarse(b0, out);
+    if (is_f) launch_cast_f2d((const float*)out, z_out, Ls[0].N, st);
+    return;
+  }
+  const T* b = b0;
+  for (int l = 0; l < Lc; ++l) {
+    T* x = (T*)Ls[l].x;
+    T* r = (T*)Ls[l].r;
+    launch_relax0<T>(Ls[l], b, x, st);
+    launch_residual<T>(Ls[l], x, b, r, st);
+    launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b, st);
+    b = (const T*)Ls[l + 1].b;
+  }
+  coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);
+  const T* e = (const T*)Ls[Lc].x;
+  for (int l = Lc - 1; l >= 0; --l) {
+    launch_prolong<T>(Ls[l], Ls[l + 1], e, (T*)Ls[l].x, st);
+    T* out = (l == 0 && !is_f) ? (T*)z_out : (T*)Ls[l].t;
+    const T* bl = l == 0 ? b0 : (const T*)Ls[l].b;
+    launch_relax<T>(Ls[l], (const T*)Ls[l].x, bl, out, st);
+    e = out;
+  }
+  if (is_f) launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);
+}
+
+void vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st) {
+  if (s->prm.precision == 1)
+    enqueue_vcycle<float>(s, r, z, st);
+  else
+    enqueue_vcycle<double>(s, r, z, st);
+}
+
+// PCG segments.  init: r = b - A x; the first iteration is peeled so that the
+// loop body starts with the V-cycle and ends with the convergence test.
+void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
+  Level& L0 = s->lev[0];
+  long long N = L0.N;
+  double* zp = s->prm.flexible ? s->zprev : nullptr;
+  launch_pcg_init(L0, s->b, s->x, s->r, s->partial, s->sc, st);
+  vcycle(s, s->r, s->z, st);
+  launch_pcg_start(s->r, s->z, s->p, zp, N, s->partial, s->nblk_red, s->sc, st);
+  launch_pcg_alpha(L0, s->p, s->q, s->partial, s->sc, st);
+  launch_pcg_update(s->p, s->q, s->x, s->r, N, s->partial, s->nblk_red, s->sc, h, use_h, st);
+}
+
+void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
+  Level& L0 = s->lev[0];
+  long long N = L0.N;
+  double* zp = s->prm.flexible ? s->zprev : nullptr;
+  vcycle(s, s->r, s->z, st);
+  launch_pcg_beta(s->r, s->z, zp, s->p, N, s->partial, s->nblk_red, s->sc, st);
+  launch_pcg_alpha(L0, s->p, s->q, s->partial, s->sc, st);
+  launch_pcg_update(s->p, s->q, s->x, s->r, N, s->partial, s->nblk_red, s->sc, h, use_h, st);
+}
+
+void build_pcg_graph(ssamg_solver s) {
+  if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  SSAMG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  SSAMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  // head, captured straight into g
+  SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_pcg_head(s, h, 1, s->cs);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  SSAMG_CUDA(cudaStreamGetCaptureInfo(s->cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps));
+  std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+  cudaGraph_t tmp;
+  SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+  // while node: body = one PCG iteration
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  SSAMG_CUDA(cudaGraphAddNode(&cnode, g, tail.data(), nullptr, tail.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_pcg_body(s, h, 1, s->cs);
+  SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+  SSAMG_CUDA(cudaGraphInstantiate(&s->graphs.pcg, g, 0));
+  cudaGraphDestroy(g);
+}
+
+int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
+  PcgScalars init;
+  std::memset(&init, 0, sizeof(init));
+  init.tol = s->prm.tol;
+  init.max_iter = s->prm.max_iter;
+  init.flexible = s->prm.flexible;
+  SSAMG_CUDA(cudaMemcpyAsync(s->sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  if (s->prm.use_graph) {
+    if (!s->graphs.pcg) build_pcg_graph(s);
+    SSAMG_CUDA(cudaGraphLaunch(s->graphs.pcg, st));
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+  } else {
+    enqueue_pcg_head(s, 0, 0, st);
+    for (;;) {
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+      SSAMG_CUDA(cudaStreamSynchronize(st));
+      if (s->h_sc->done) break;
+      enqueue_pcg_body(s, 0, 0, st);
+    }
+  }
+  const PcgScalars& r = *s->h_sc;
+  if (stats) {
+    stats->iterations = r.iter;
+    stats->converged = r.status == 0 && r.rr <= r.tol2bb;
+    stats->rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
+    stats->num_levels = (int)s->lev.size();
+    stats->coarse_size = s->lev.back().N;
+    double nnz0 = 0, nnz = 0;
+    for (size_t l = 0; l < s->lev.size(); ++l) {
+      double n = (double)s->lev[l].nnz;
+      for (auto& h : s->lev[l].parts) n += (double)h.nent * h.ncell;
+      nnz += n;
+      if (l == 0) nnz0 = n;
+    }
+    stats->operator_complexity = nnz / nnz0;
+    launch_true_residual(s->lev[0], s->b, s->x, s->q, s->partial, s->tres, st);
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_dbl, s->tres, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+    stats->true_rel_res = s->h_dbl[0] > 0 ? std::sqrt(s->h_dbl[1] / s->h_dbl[0]) : 0.0;
+  }
+  if (r.status != 0) return r.status;
+  return r.rr <= r.tol2bb ? SSAMG_OK : SSAMG_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
+  if (!s || !A) return SSAMG_ERR_ARG;
+  if (!A->assembled) return SSAMG_ERR_STATE;
+  API_BEGIN
+  s->A = A;
+  build_hierarchy(s, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess,
+                           void* stream, ssamg_stats* st) {
+  if (!s || !b || !x || nrhs < 1) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  cudaStream_t cst = (cudaStream_t)stream;
+  API_BEGIN
+  long long N = s->lev[0].N;
+  int rc = SSAMG_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    SSAMG_CUDA(cudaMemcpyAsync(s->b, b + k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, cst));
+    if (zero_guess)
+      SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, cst));
+    else
+      SSAMG_CUDA(cudaMemcpyAsync(s->x, x + k * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, cst));
+    int r = run_pcg(s, cst, st);
+    SSAMG_CUDA(cudaMemcpyAsync(x + k * N, s->x, sizeof(double) * N, cudaMemcpyDeviceToDevice, cst));
+    if (r < 0) return r;
+    if (r > rc) rc = r;
+  }
+  return rc;
+  API_END
+}
+
+extern "C" int ssamg_solve_host(ssamg_solver s, const double* b, double* x, int nrhs, void* stream,
+                                ssamg_stats* st) {
+  if (!s || !b || !x || nrhs < 1) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  cudaStream_t cst = (cudaStream_t)stream;
+  API_BEGIN
+  long long N = s->lev[0].N;
+  int rc = SSAMG_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    SSAMG_CUDA(cudaMemcpyAsync(s->b, b + k * N, sizeof(double) * N, cudaMemcpyHostToDevice, cst));
+    SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, cst));
+    int r = run_pcg(s, cst, st);
+    SSAMG_CUDA(cudaMemcpyAsync(x + k * N, s->x, sizeof(double) * N, cudaMemcpyDeviceToHost, cst));
+    SSAMG_CUDA(cudaStreamSynchronize(cst));
+    if (r < 0) return r;
+    if (r > rc) rc = r;
+  }
+  return rc;
+  API_END
+}
+
+extern "C" int ssamg_adjoint_solve(ssamg_solver s, const double* g, double* lambda, int nrhs,
+                                   void* stream, ssamg_stats* st) {
+  // A is symmetric (S by the caller's stencil, U by assumption), so the
+  // adjoint system A^T lambda = g is solved with the forward hierarchy.
+  return ssamg_solve(s, g, lambda, nrhs, 1, stream, st);
+}
+
+extern "C" int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const double* x,
+                                   double* dcoef, void* stream) {
+  if (!s || !lambda || !x || !dcoef) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  API_BEGIN
+  launch_coef_gradient(s->lev[0], lambda, x, dcoef, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, const double* lambda,
+                                            const double* x, double* dg, void* stream) {
+  if (!s || !g || !lambda || !x || !dg) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  API_BEGIN
+  launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_precondition(ssamg_solver s, const double* r, double* z, void* stream) {
+  if (!s || !r || !z) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  API_BEGIN
+  vcycle(s, r, z, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_level_matvec(ssamg_solver s, int level, const double* x, double* y,
+                                  void* stream) {
+  if (!s || !x || !y) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  API_BEGIN
+  launch_matvec(s->lev[level], x, y, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+// ---------------------------------------------------------------------------
+// Introspection
+// ---------------------------------------------------------------------------
+extern "C" int ssamg_num_levels(ssamg_solver s) {
+  return (s && s->ready) ? (int)s->lev.size() : SSAMG_ERR_STATE;
+}
+
+extern "C" int ssamg_level_part_info(ssamg_solver s, int level, int part, int* lo, int* hi,
+                                     int* dstar, double* omega, int* nentries, int* offsets,
+                                     long long* cell_offset) {
+  if (!s || !s->ready) return SSAMG_ERR_STATE;
+  if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  const Level& L = s->lev[level];
+  if (part < 0 || part >= L.np) return SSAMG_ERR_ARG;
+  const PartH& h = L.parts[part];
+  for (int d = 0; d < 3; ++d) {
+    if (lo) lo[d] = h.lo[d];
+    if (hi) hi[d] = h.hi[d];
+  }
+  if (dstar) *dstar = h.dstar;
+  if (omega) *omega = h.omega;
+  if (nentries) *nentries = h.nent;
+  if (offsets)
+    for (int e = 0; e < h.nent; ++e)
+      for (int d = 0; d < 3; ++d) offsets[3 * e + d] = h.o[e][d];
+  if (cell_offset) *cell_offset = h.off;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_level_sizes(ssamg_solver s, int level, long long* ncells, long long* u_rows,
+                                 long long* u_nnz) {
+  if (!s || !s->ready) return SSAMG_ERR_STATE;
+  if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  const Level& L = s->lev[level];
+  if (ncells) *ncells = L.N;
+  if (u_rows) *u_rows = L.nr;
+  if (u_nnz) *u_nnz = L.nnz;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, void* dst,
+                                long long n) {
+  if (!s || !s->ready) return SSAMG_ERR_STATE;
+  if (!dst || level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  const Level& L = s->lev[level];
+  API_BEGIN
+  auto copy = [&](const void* src, size_t bytes, long long want) {
+    argcheck(n == want, "destination size does not match the data size");
+    if (want == 0) return;
+    argcheck(src != nullptr, "no such data on this level");
+    SSAMG_CUDA(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  };
+  auto part_ok = [&]() { argcheck(part >= 0 && part < L.np, "part out of range"); };
+  switch (what) {
+    case 0: {
+      part_ok();
+      const PartH& h = L.parts[part];
+      argcheck(entry >= 0 && entry < h.nent, "entry out of range");
+      if (h.var[entry]) {
+        copy(L.coef + h.coef_off[entry], sizeof(double) * h.ncell, h.ncell);
+      } else {
+        argcheck(n == h.ncell, "destination size does not match the data size");
+        std::fill((double*)dst, (double*)dst + n, h.cval[entry]);
+      }
+      break;
+    }
+    case 1:
+    case 2: {
+      part_ok();
+      const PartH& h = L.parts[part];
+      argcheck(h.dstar >= 0, "part is not coarsened at this level");
+      copy((what == 1 ? L.Pw : L.Pe) + h.poff, sizeof(double) * h.nfine, h.nfine);
+      break;
+    }
+    case 3: copy(L.dinv, sizeof(double) * L.N, L.N); break;
+    case 4: copy(L.u_ptr, sizeof(int) * (L.nr + 1), L.nr > 0 ? L.nr + 1 : 0); break;
+    case 5: copy(L.u_rows, sizeof(int) * L.nr, L.nr); break;
+    case 6: copy(L.u_col, sizeof(int) * L.nnz, L.nnz); break;
+    case 7: copy(L.u_val, sizeof(double) * L.nnz, L.nnz); break;
+    case 8: copy(L.u_bits, (size_t)L.nnz, L.nnz); break;
+    default: return SSAMG_ERR_ARG;
+  }
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_spacings(ssamg_solver s, double* c, double* W) {
+  if (!s || !s->ready) return SSAMG_ERR_STATE;
+  if (c) std::copy(s->c.begin(), s->c.end(), c);
+  if (W) std::copy(s->W.begin(), s->W.end(), W);
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_selftest_fastdiv(unsigned long long seed, int trials) {
+  // host check of the division constants against plain division
+  unsigned long long z = seed;
+  for (int t = 0; t < trials; ++t) {
+    z = z * 6364136223846793005ull + 1442695040888963407ull;
+    unsigned d = (unsigned)((z >> 33) % 4000000u) + 1u;
+    z = z * 6364136223846793005ull + 1442695040888963407ull;
+    unsigned n = (unsigned)(z >> 33) & 0x7fffffffu;
+    FastDiv f = make_fastdiv(d);
+    if (fdiv(n, f) != n / d) return 1;
+    if (fdiv(d * (n / d), f) != n / d) return 2;
+  }
+  return 0;
+}

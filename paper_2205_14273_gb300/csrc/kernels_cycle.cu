@@ -1,0 +1,567 @@
+// V(1,1)-cycle kernels (Section 3.4 relaxation, Eq. relax0; Section 3.2
+// restriction R = P^T and prolongation), the FP64 PCG vector kernels
+// (Section 4) and the coefficient-gradient kernels of the adjoint solve.
+#include "kernels_common.cuh"
+
+namespace {
+
+constexpr int NT = SSAMG_BLOCK;
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// x = omega M^-1 b (relaxation from a zero guess).
+template <class T>
+__global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict__ b,
+                         T* __restrict__ x) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < N) x[g] = dinv[g] * b[g];
+}
+
+// r = b - A x
+template <class T>
+__global__ void __launch_bounds__(NT) k_residual(LevelView<T> L, const T* __restrict__ x,
+                                                 const T* __restrict__ b, T* __restrict__ r) {
+  __shared__ DPart sp;
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  int g = sp.off + c;
+  r[g] = b[g] - apply_A(L, sp, x, c, i, j, k);
+}
+
+// xo = x + omega M^-1 (b - A x)
+template <class T>
+__global__ void __launch_bounds__(NT) k_relax(LevelView<T> L, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ xo) {
+  __shared__ DPart sp;
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  int g = sp.off + c;
+  xo[g] = fma(L.dinv[g], b[g] - apply_A(L, sp, x, c, i, j, k), x[g]);
+}
+
+// bc = P^T r, one coarse cell per thread: the anchor (weight 1) and the two
+// fine points beside it along d* (weights PE of the west one, PW of the east).
+template <class T>
+__global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
+                                                 const T* __restrict__ r, T* __restrict__ bc) {
+  __shared__ DPart fp;
+  __shared__ DPart cp;
+  int p = find_part(C.blk, C.np, blockIdx.x);
+  stage_part(fp, F.parts + p);
+  stage_part(cp, C.parts + p);
+  __syncthreads();
+  int cc = (blockIdx.x - cp.blk0) * NT + threadIdx.x;
+  if (cc >= cp.ncell) return;
+  int I[3];
+  cell_coords(cp, cc, I[0], I[1], I[2]);
+  const int d = fp.dstar;
+  T v;
+  if (d < 0) {
+    v = r[fp.off + (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]];
+  } else {
+    int f[3] = {I[0], I[1], I[2]};
+    const int anchor = 2 * I[d] + fp.par;
+    f[d] = anchor;
+    const int sd = (d == 0) ? 1 : (d == 1 ? fp.n[0] : fp.n[0] * fp.n[1]);
+    const int fa = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+    v = r[fa];
+    if (anchor - 1 >= 0) {
+      f[d] = anchor - 1;
+      v = fma(F.Pe[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa - sd], v);
+    }
+    if (anchor + 1 < fp.n[d]) {
+      f[d] = anchor + 1;
+      v = fma(F.Pw[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa + sd], v);
+    }
+  }
+  bc[cp.off + cc] = v;
+}
+
+// x += P ec, one fine cell per thread.
+template <class T>
+__global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
+                                                T* __restrict__ x) {
+  __shared__ DPart fp;
+  int p = find_part(F.blk, F.np, blockIdx.x);
+  stage_part(fp, F.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - fp.blk0) * NT + threadIdx.x;
+  if (c >= fp.ncell) return;
+  int i, j, k;
+  cell_coords(fp, c, i, j, k);
+  int J[2];
+  T w[2];
+  int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+  T v = x[fp.off + c];
+  for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
+  x[fp.off + c] = v;
+}
+
+// Coarsest level: x = (L L^T)^-1 b in FP64 with one warp.
+template <class T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ Lf, const T* __restrict__ b,
+                               T* __restrict__ x) {
+  extern __shared__ double y[];
+  const int l = threadIdx.x;
+  for (int i = 0; i < n; ++i) {
+    const double* ri = Lf + (long long)i * n;
+    double s = 0.0;
+    for (int k = l; k < i; k += 32) s += ri[k] * y[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) y[i] = ((double)b[i] - s) / ri[i];
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int k = i + 1 + l; k < n; k += 32) s += Lf[(long long)k * n + i] * y[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) y[i] = (y[i] - s) / Lf[(long long)i * n + i];
+    __syncwarp();
+  }
+  for (int i = l; i < n; i += 32) x[i] = (T)y[i];
+}
+
+__global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, int n) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[g] = (float)in[g];
+}
+__global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ out, int n) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) out[g] = (double)in[g];
+}
+
+__global__ void __launch_bounds__(NT) k_matvec(LevelView<double> L, const double* __restrict__ x,
+                                               double* __restrict__ y) {
+  __shared__ DPart sp;
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  y[sp.off + c] = apply_A(L, sp, x, c, i, j, k);
+}
+
+// ---------------------------------------------------------------------------
+// PCG (FP64).  Dot products are block partial sums plus a one-block final
+// sum in a fixed order, so results are bitwise reproducible.
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void finish_sums(const double* __restrict__ partial, int nblk,
+                                            double* out) {
+  __shared__ double sh[NT / 32];
+  for (int q = 0; q < K; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += NT) s += partial[(long long)K * b + q];
+    double r = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) out[q] = r;
+  }
+}
+
+// r = b - A x; partial sums of (b.b, r.r)
+__global__ void __launch_bounds__(NT) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
+                                                 const double* __restrict__ x, double* __restrict__ r,
+                                                 double* __restrict__ partial) {
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  double bb = 0.0, rr = 0.0;
+  if (c < sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    int g = sp.off + c;
+    double bv = b[g];
+    double rv = bv - apply_A(L, sp, x, c, i, j, k);
+    r[g] = rv;
+    bb = bv * bv;
+    rr = rv * rv;
+  }
+  double s0 = block_sum<NT>(bb, sh);
+  double s1 = block_sum<NT>(rr, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ partial, int nblk,
+                                                     PcgScalars* sc) {
+  __shared__ double out[2];
+  finish_sums<2>(partial, nblk, out);
+  if (threadIdx.x == 0) {
+    sc->bb = out[0];
+    sc->rr = out[1];
+    sc->tol2bb = sc->tol * sc->tol * out[0];
+    sc->iter = 0;
+    sc->status = 0;
+    sc->done = (out[1] <= sc->tol2bb) ? 1 : 0;
+  }
+}
+
+// p = z (and zprev = z for flexible CG); partial r.z
+__global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
+                                                  const double* __restrict__ z,
+                                                  double* __restrict__ p, double* __restrict__ zprev,
+                                                  long long n, double* __restrict__ partial) {
+  __shared__ double sh[NT / 32];
+  double s = 0.0;
+  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
+    double zv = z[g];
+    p[g] = zv;
+    if (zprev) zprev[g] = zv;
+    s = fma(r[g], zv, s);
+  }
+  double t = block_sum<NT>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__device__ __forceinline__ void set_continue(PcgScalars* sc, cudaGraphConditionalHandle h,
+                                             int use_handle) {
+  if (use_handle) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__ partial, int nblk,
+                                                      PcgScalars* sc) {
+  __shared__ double out[1];
+  finish_sums<1>(partial, nblk, out);
+  if (threadIdx.x == 0 && !sc->done) {
+    sc->rz = out[0];
+    if (!(out[0] > 0.0) || !isfinite(out[0])) {
+      sc->status = SSAMG_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+  }
+}
+
+// partial (r.z, r.zprev) for beta; zprev takes the new z (flexible CG)
+__global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r,
+                                                    const double* __restrict__ z,
+                                                    double* __restrict__ zprev, long long n,
+                                                    double* __restrict__ partial) {
+  __shared__ double sh[NT / 32];
+  double s0 = 0.0, s1 = 0.0;
+  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
+    double rv = r[g], zv = z[g];
+    s0 = fma(rv, zv, s0);
+    if (zprev) {
+      s1 = fma(rv, zprev[g], s1);
+      zprev[g] = zv;
+    }
+  }
+  double t0 = block_sum<NT>(s0, sh);
+  double t1 = block_sum<NT>(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = t0;
+    partial[2 * blockIdx.x + 1] = t1;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ partial, int nblk,
+                                                     PcgScalars* sc) {
+  __shared__ double out[2];
+  finish_sums<2>(partial, nblk, out);
+  if (threadIdx.x == 0 && !sc->done) {
+    double rz = out[0];
+    double num = sc->flexible ? (rz - out[1]) : rz;
+    sc->beta = num / sc->rz;
+    sc->rz = rz;
+    if (!isfinite(rz) || !isfinite(sc->beta)) {
+      sc->status = SSAMG_ERR_BREAKDOWN;
+      sc->done = 1;
+    }
+  }
+}
+
+__global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p, long long n,
+                           const PcgScalars* __restrict__ sc) {
+  if (sc->done) return;
+  double beta = sc->beta;
+  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT)
+    p[g] = fma(beta, p[g], z[g]);
+}
+
+// q = A p; partial p.q
+__global__ void __launch_bounds__(NT) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
+                                                     double* __restrict__ q,
+                                                     double* __restrict__ partial) {
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  int pt = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + pt);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  double s = 0.0;
+  if (c < sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    int g = sp.off + c;
+    double qv = apply_A(L, sp, p, c, i, j, k);
+    q[g] = qv;
+    s = p[g] * qv;
+  }
+  double t = block_sum<NT>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__ partial, int nblk,
+                                                      PcgScalars* sc) {
+  __shared__ double out[1];
+  finish_sums<1>(partial, nblk, out);
+  if (threadIdx.x == 0 && !sc->done) {
+    double pq = out[0];
+    sc->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      sc->status = SSAMG_ERR_BREAKDOWN;
+      sc->done = 1;
+      sc->alpha = 0.0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; partial r.r
+__global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
+                                                   const double* __restrict__ q,
+                                                   double* __restrict__ x, double* __restrict__ r,
+                                                   long long n, double* __restrict__ partial,
+                                                   const PcgScalars* __restrict__ sc) {
+  __shared__ double sh[NT / 32];
+  if (sc->done) return;
+  double alpha = sc->alpha;
+  double s = 0.0;
+  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
+    x[g] = fma(alpha, p[g], x[g]);
+    double rv = fma(-alpha, q[g], r[g]);
+    r[g] = rv;
+    s = fma(rv, rv, s);
+  }
+  double t = block_sum<NT>(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict__ partial, int nblk,
+                                                       PcgScalars* sc, cudaGraphConditionalHandle h,
+                                                       int use_handle) {
+  __shared__ double out[1];
+  bool was_done = sc->done;
+  finish_sums<1>(partial, nblk, out);
+  if (threadIdx.x == 0) {
+    if (!was_done) {
+      sc->rr = out[0];
+      sc->iter += 1;
+      if (!isfinite(out[0])) sc->status = SSAMG_ERR_BREAKDOWN;
+      if (sc->status != 0 || out[0] <= sc->tol2bb || sc->iter >= sc->max_iter) sc->done = 1;
+    }
+    set_continue(sc, h, use_handle);
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ partial, int nblk,
+                                                     double* out) {
+  __shared__ double o2[2];
+  finish_sums<2>(partial, nblk, o2);
+  if (threadIdx.x == 0) {
+    out[0] = o2[0];
+    out[1] = o2[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Differentiation
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
+                                                      const double* __restrict__ lam,
+                                                      const double* __restrict__ x,
+                                                      double* __restrict__ dcoef, long long N) {
+  __shared__ DPart sp;
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  int g = sp.off + c;
+  double l = lam[g];
+  for (int e = 0; e < sp.nent; ++e) {
+    double v = 0.0;
+    if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) v = -l * x[g + sp.disp[e]];
+    dcoef[(long long)e * N + g] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double> L,
+                                                               const double* __restrict__ gg,
+                                                               const double* __restrict__ lam,
+                                                               const double* __restrict__ x,
+                                                               double* __restrict__ dg) {
+  __shared__ DPart sp;
+  stage_part(sp, L.parts);
+  __syncthreads();
+  int c = blockIdx.x * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  const double kc = exp(gg[c]);
+  const double lc = lam[c], xc = x[c];
+  const int nb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  const int st[3] = {1, sp.n[0], sp.n[0] * sp.n[1]};
+  double acc = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    if (inside(sp, i + nb[f][0], j + nb[f][1], k + nb[f][2])) {
+      int cn = c + nb[f][0] * st[0] + nb[f][1] * st[1] + nb[f][2] * st[2];
+      double kn = exp(gg[cn]);
+      double s = kc + kn;
+      double dt = 2.0 * kn * kn / (s * s);
+      acc -= dt * (lc - lam[cn]) * (xc - x[cn]);
+    } else {
+      acc -= lc * xc;
+    }
+  }
+  dg[c] = kc * acc;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class T>
+void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
+  const T* dinv = L.view<T>().dinv;
+  k_relax0<T><<<cdiv(L.N, NT), NT, 0, st>>>((int)L.N, dinv, b, x);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
+  k_residual<T><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
+  k_relax<T><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st) {
+  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st) {
+  (void)Cl;
+  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st) {
+  k_coarse_solve<T><<<1, 32, sizeof(double) * n, st>>>(n, Lfac, b, x);
+  SSAMG_LAUNCH_CHECK();
+}
+
+#define INST(T)                                                                            \
+  template void launch_relax0<T>(const Level&, const T*, T*, cudaStream_t);                \
+  template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
+  template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \
+  template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t); \
+  template void launch_prolong<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
+  template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st) {
+  k_cast_d2f<<<cdiv(n, NT), NT, 0, st>>>(in, out, (int)n);
+  SSAMG_LAUNCH_CHECK();
+}
+void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st) {
+  k_cast_f2d<<<cdiv(n, NT), NT, 0, st>>>(in, out, (int)n);
+  SSAMG_LAUNCH_CHECK();
+}
+void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) {
+  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y);
+  SSAMG_LAUNCH_CHECK();
+}
+
+int reduce_blocks(long long n) {
+  long long nb = (n + NT - 1) / NT;
+  return (int)std::min<long long>(std::max<long long>(nb, 1), 152 * 8);
+}
+
+void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
+                     PcgScalars* sc, cudaStream_t st) {
+  k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_init_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
+                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
+  k_pcg_start<<<nblk, NT, 0, st>>>(r, z, p, zprev, n, partial);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_start_fin<<<1, NT, 0, st>>>(partial, nblk, sc);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
+                     double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
+  k_pcg_dots_rz<<<nblk, NT, 0, st>>>(r, z, zprev, n, partial);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_beta_fin<<<1, NT, 0, st>>>(partial, nblk, sc);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_xpby<<<nblk, NT, 0, st>>>(z, p, n, sc);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
+                      PcgScalars* sc, cudaStream_t st) {
+  k_pcg_spmv_dot<<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_alpha_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,
+                       double* partial, int nblk, PcgScalars* sc, cudaGraphConditionalHandle h,
+                       int use_handle, cudaStream_t st) {
+  k_pcg_update<<<nblk, NT, 0, st>>>(p, q, x, r, n, partial, sc);
+  SSAMG_LAUNCH_CHECK();
+  k_pcg_update_fin<<<1, NT, 0, st>>>(partial, nblk, sc, h, use_handle);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
+                          double* partial, double* out, cudaStream_t st) {
+  k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
+  SSAMG_LAUNCH_CHECK();
+  k_true_res_fin<<<1, NT, 0, st>>>(partial, L.nblk, out);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
+                          cudaStream_t st) {
+  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_diffusion_exp_gradient(const Level& L, const double* g, const double* lam,
+                                   const double* x, double* dg, cudaStream_t st) {
+  k_diffusion_exp_gradient<<<cdiv(L.parts[0].ncell, NT), NT, 0, st>>>(L.view<double>(), g, lam, x, dg);
+  SSAMG_LAUNCH_CHECK();
+}

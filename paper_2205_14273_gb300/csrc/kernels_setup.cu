@@ -1,0 +1,619 @@
+// Setup kernels: coupling sums (Section 3.1), interpolation (Section 3.2,
+// Eq. prolEx), Galerkin coarse operators (Section 3.3, Eq. galerkin),
+// relaxation diagonals (Section 3.4) and the coarsest-level factorisation.
+#include "kernels_common.cuh"
+
+namespace {
+
+constexpr int NT = SSAMG_BLOCK;
+
+// ---------------------------------------------------------------------------
+// K1: per part, c_d = sum over cells of sign(A_C) * (-sum of entries moving
+// along d) (Section 3.1).  Block partials, then one block per part sums them
+// in a fixed order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __restrict__ partial) {
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  double s0 = 0, s1 = 0, s2 = 0;
+  if (c < sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    double sg = 1.0;
+    for (int e = 0; e < sp.nent; ++e)
+      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0 && coef_at(sp, L.coef, e, c) < 0.0)
+        sg = -1.0;
+    for (int e = 0; e < sp.nent; ++e) {
+      if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
+      double a = coef_at(sp, L.coef, e, c);
+      if (sp.o[e][0]) s0 -= a;
+      if (sp.o[e][1]) s1 -= a;
+      if (sp.o[e][2]) s2 -= a;
+    }
+    s0 *= sg; s1 *= sg; s2 *= sg;
+  }
+  double r0 = block_sum<NT>(s0, sh);
+  double r1 = block_sum<NT>(s1, sh);
+  double r2 = block_sum<NT>(s2, sh);
+  if (threadIdx.x == 0) {
+    partial[3 * blockIdx.x + 0] = r0;
+    partial[3 * blockIdx.x + 1] = r1;
+    partial[3 * blockIdx.x + 2] = r2;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_wfinal(const int* __restrict__ blk,
+                                               const double* __restrict__ partial,
+                                               double* __restrict__ c) {
+  __shared__ double sh[NT / 32];
+  int p = blockIdx.x;
+  int b0 = blk[p], b1 = blk[p + 1];
+  for (int d = 0; d < 3; ++d) {
+    double s = 0;
+    for (int b = b0 + threadIdx.x; b < b1; b += NT) s += partial[3 * b + d];
+    double r = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) c[3 * p + d] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: two-point interpolation weights per fine point (Eq. prolEx, sign
+// reading P = -(plane sum)/(centre-plane sum)), with the part-boundary fix.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __restrict__ Pw,
+                                               double* __restrict__ Pe, float* __restrict__ Pw32,
+                                               float* __restrict__ Pe32) {
+  __shared__ DPart sp;
+  int p = find_part(L.fblk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int F = (blockIdx.x - sp.fblk0) * NT + threadIdx.x;
+  if (F >= sp.nfine) return;
+  const int d = sp.dstar;
+  int fc[3];
+  {
+    unsigned q = fdiv((unsigned)F, sp.fdx);
+    fc[0] = F - (int)q * sp.nf[0];
+    fc[2] = (int)fdiv((unsigned)F, sp.fdxy);
+    fc[1] = (int)q - fc[2] * sp.nf[1];
+  }
+  fc[d] = 2 * fc[d] + 1 - sp.par;  // the fine cell
+  const int i = fc[0], j = fc[1], k = fc[2];
+  const int c = (k * sp.n[1] + j) * sp.n[0] + i;
+  double nw = 0, ne = 0, den = 0, diag = 0;
+  for (int e = 0; e < sp.nent; ++e) {
+    if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
+    double a = coef_at(sp, L.coef, e, c);
+    int od = sp.o[e][d];
+    if (od < 0) nw += a;
+    else if (od > 0) ne += a;
+    else den += a;
+    if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += a;
+  }
+  double pw = 0, pe = 0;
+  bool ok = fabs(den) > 1e-300 && ((den > 0) == (diag > 0)) && diag != 0.0;
+  if (ok) {
+    pw = -nw / den;
+    pe = -ne / den;
+  }
+  if (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1)) {
+    int r = L.u_map[sp.off + c];
+    if (r >= 0) {
+      unsigned bits = 0;
+      for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) bits |= L.u_bits[q];
+      if (fc[d] == sp.n[d] - 1 && ((bits >> (2 * d)) & 1u)) { pw = 1.0; pe = 0.0; }
+      if (fc[d] == 0 && ((bits >> (2 * d + 1)) & 1u)) { pw = 0.0; pe = 1.0; }
+    }
+  }
+  Pw[sp.poff + F] = pw;
+  Pe[sp.poff + F] = pe;
+  if (Pw32) {
+    Pw32[sp.poff + F] = (float)pw;
+    Pe32[sp.poff + F] = (float)pe;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: structured Galerkin product P^T S P per coarse cell (Eq. galerkin).
+// For coarse cell I with fine anchor F (2I along d*) and a in {-1,0,1}:
+// f = F + a e_d carries P(f, I) = 1, PE(f) or PW(f); each entry o at f
+// reaches g = f + o, which maps to J = g/2 (coarse point) or to its west and
+// east coarse neighbours with PW(g), PE(g).  The product accumulates into the
+// coarse entry J - I.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelView<double> C,
+                                                   double* __restrict__ ccoef,
+                                                   float* __restrict__ ccoef32) {
+  __shared__ DPart fp;
+  __shared__ DPart cp;
+  int p = find_part(C.blk, C.np, blockIdx.x);
+  stage_part(fp, F.parts + p);
+  stage_part(cp, C.parts + p);
+  __syncthreads();
+  int cc = (blockIdx.x - cp.blk0) * NT + threadIdx.x;
+  if (cc >= cp.ncell) return;
+  int I[3];
+  cell_coords(cp, cc, I[0], I[1], I[2]);
+  double acc[27];
+#pragma unroll
+  for (int t = 0; t < 27; ++t) acc[t] = 0.0;
+  const int d = fp.dstar;
+  if (d < 0) {
+    // part not coarsened at this level: P = I on this part
+    int c = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
+    for (int e = 0; e < fp.nent; ++e) {
+      if (!inside(fp, I[0] + fp.o[e][0], I[1] + fp.o[e][1], I[2] + fp.o[e][2])) continue;
+      int code = (fp.o[e][0] + 1) + 3 * (fp.o[e][1] + 1) + 9 * (fp.o[e][2] + 1);
+      acc[code] += coef_at(fp, F.coef, e, c);
+    }
+  } else {
+    const int anchor = 2 * I[d] + fp.par;
+    for (int a = -1; a <= 1; ++a) {
+      int f[3] = {I[0], I[1], I[2]};
+      f[d] = anchor + a;
+      if (f[d] < 0 || f[d] >= fp.n[d]) continue;
+      const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+      double w1 = 1.0;
+      if (a != 0) {
+        int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
+        w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
+      }
+      if (w1 == 0.0) continue;
+      for (int e = 0; e < fp.nent; ++e) {
+        int g[3] = {f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]};
+        if (!inside(fp, g[0], g[1], g[2])) continue;
+        double v = w1 * coef_at(fp, F.coef, e, fcell);
+        int t = a + fp.o[e][d];
+        int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
+        if ((t & 1) == 0) {
+          ob[d] = t / 2;
+          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
+        } else {
+          int Gi = fp.poff + fine_point_index(fp, g[0], g[1], g[2]);
+          ob[d] = (t - 1) / 2;
+          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pw[Gi];
+          ob[d] = (t + 1) / 2;
+          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pe[Gi];
+        }
+      }
+    }
+  }
+  for (int e = 0; e < cp.nent; ++e) {
+    int code = (cp.o[e][0] + 1) + 3 * (cp.o[e][1] + 1) + 9 * (cp.o[e][2] + 1);
+    double v = acc[code];
+    if (!inside(cp, I[0] + cp.o[e][0], I[1] + cp.o[e][1], I[2] + cp.o[e][2])) v = 0.0;
+    ccoef[cp.coef[e] + cc] = v;
+    if (ccoef32) ccoef32[cp.coef[e] + cc] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: unstructured Galerkin product P^T U P (Eq. galerkin, second term).
+// Rows of U_c are the coarse cells in the P-support of fine U rows (marker +
+// scan); each coarse row gathers the U rows of its <= 3 fine points, spreads
+// every entry over the column's P row, sorts by column and sums duplicates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void locate(const LevelView<double>& L, const DPart* parts, int g,
+                                       int& p, int& i, int& j, int& k) {
+  p = find_part_cell(L.cellstart, L.np, g);
+  const DPart& dp = parts[p];
+  int c = g - dp.off;
+  unsigned q = fdiv((unsigned)c, dp.dx);
+  i = c - (int)q * dp.n[0];
+  k = (int)fdiv((unsigned)c, dp.dxy);
+  j = (int)q - k * dp.n[1];
+}
+
+__global__ void k_umark(LevelView<double> F, int nr, const int* __restrict__ rows,
+                        int* __restrict__ marker) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  int p, i, j, k;
+  locate(F, F.parts, rows[r], p, i, j, k);
+  int J[2];
+  double w[2];
+  int m = p_row(F.parts[p], F.Pw, F.Pe, i, j, k, J, w);
+  for (int t = 0; t < m; ++t) marker[J[t]] = 1;
+}
+
+__global__ void k_urows(int Nc, const int* __restrict__ scan, const int* __restrict__ marker_flag,
+                        int* __restrict__ u_map, int* __restrict__ u_rows) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Nc) return;
+  // marker_flag is the inclusive-minus-exclusive difference: scan[g+1] - scan[g]
+  int s = scan[g];
+  if (scan[g + 1] != s) {
+    u_map[g] = s;
+    u_rows[s] = g;
+  } else {
+    u_map[g] = -1;
+  }
+}
+
+struct UCand {
+  int J;
+  unsigned char bits;
+  double v;
+};
+
+// Gathers and merges the candidates of coarse row R; returns the count (or
+// -1 on overflow).  When out_col is set, writes the merged row.
+__device__ int urow_build(const LevelView<double>& F, const LevelView<double>& C, int R,
+                          const int* __restrict__ crows, int* out_col, double* out_val,
+                          float* out_val32, unsigned char* out_bits) {
+  UCand cand[SSAMG_MAX_UCAND];
+  int nc = 0;
+  int I = crows[R];
+  int p = find_part_cell(C.cellstart, C.np, I);
+  const DPart& fp = F.parts[p];
+  const DPart& cp = C.parts[p];
+  int cl = I - cp.off;
+  int Ic[3];
+  {
+    unsigned q = fdiv((unsigned)cl, cp.dx);
+    Ic[0] = cl - (int)q * cp.n[0];
+    Ic[2] = (int)fdiv((unsigned)cl, cp.dxy);
+    Ic[1] = (int)q - Ic[2] * cp.n[1];
+  }
+  const int d = fp.dstar;
+  for (int a = -1; a <= 1; ++a) {
+    int f[3] = {Ic[0], Ic[1], Ic[2]};
+    double w1 = 1.0;
+    if (d < 0) {
+      if (a != 0) continue;
+    } else {
+      f[d] = 2 * Ic[d] + fp.par + a;
+      if (f[d] < 0 || f[d] >= fp.n[d]) continue;
+      if (a != 0) {
+        int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
+        w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
+      }
+    }
+    int fg = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+    int r = F.u_map[fg];
+    if (r < 0) continue;
+    for (int q = F.u_ptr[r]; q < F.u_ptr[r + 1]; ++q) {
+      int gq, gi, gj, gk;
+      locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
+      int J[2];
+      double w2[2];
+      int m = p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, J, w2);
+      double v = w1 * F.u_val[q];
+      for (int t = 0; t < m; ++t) {
+        if (nc >= SSAMG_MAX_UCAND) return -1;
+        // insertion sort by column; equal columns stay in arrival order
+        int pos = nc;
+        while (pos > 0 && cand[pos - 1].J > J[t]) {
+          cand[pos] = cand[pos - 1];
+          --pos;
+        }
+        cand[pos].J = J[t];
+        cand[pos].v = v * w2[t];
+        cand[pos].bits = F.u_bits[q];
+        ++nc;
+      }
+    }
+  }
+  int nu = 0;
+  int s = 0;
+  while (s < nc) {
+    int e = s;
+    double v = 0.0;
+    unsigned char b = 0;
+    while (e < nc && cand[e].J == cand[s].J) {
+      v += cand[e].v;
+      b |= cand[e].bits;
+      ++e;
+    }
+    if (out_col) {
+      out_col[nu] = cand[s].J;
+      out_val[nu] = v;
+      if (out_val32) out_val32[nu] = (float)v;
+      out_bits[nu] = b;
+    }
+    ++nu;
+    s = e;
+  }
+  return nu;
+}
+
+__global__ void k_ucount(LevelView<double> F, LevelView<double> C, int nrc,
+                         const int* __restrict__ crows, int* __restrict__ counts,
+                         int* __restrict__ err) {
+  int R = blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= nrc) return;
+  int n = urow_build(F, C, R, crows, nullptr, nullptr, nullptr, nullptr);
+  if (n < 0) {
+    atomicOr(err, 1);
+    n = 0;
+  }
+  counts[R] = n;
+}
+
+__global__ void k_ufill(LevelView<double> F, LevelView<double> C, int nrc,
+                        const int* __restrict__ crows, const int* __restrict__ ptr,
+                        int* __restrict__ col, double* __restrict__ val, float* __restrict__ val32,
+                        unsigned char* __restrict__ bits, int* __restrict__ err) {
+  int R = blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= nrc) return;
+  int o = ptr[R];
+  int n = urow_build(F, C, R, crows, col + o, val + o, val32 ? val32 + o : nullptr, bits + o);
+  if (n < 0 || n != ptr[R + 1] - o) atomicOr(err, 2);
+}
+
+__global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ u_map) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nr) u_map[rows[r]] = r;
+}
+
+// ---------------------------------------------------------------------------
+// K5: diagonal of omega M^-1 (Section 3.4).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, double factor,
+                                             double* __restrict__ dinv, float* __restrict__ dinv32) {
+  __shared__ DPart sp;
+  int p = find_part(L.blk, L.np, blockIdx.x);
+  stage_part(sp, L.parts + p);
+  __syncthreads();
+  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
+  if (c >= sp.ncell) return;
+  int i, j, k;
+  cell_coords(sp, c, i, j, k);
+  double v;
+  if (relax == 0) {
+    double diag = 0.0;
+    for (int e = 0; e < sp.nent; ++e)
+      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += coef_at(sp, L.coef, e, c);
+    double w = factor > 0.0 ? factor : sp.omega;
+    v = w / diag;
+  } else {
+    double s = 0.0;
+    for (int e = 0; e < sp.nent; ++e)
+      if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2]))
+        s += fabs(coef_at(sp, L.coef, e, c));
+    if (sp.has_u) {
+      int r = L.u_map[sp.off + c];
+      if (r >= 0)
+        for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) s += fabs(L.u_val[q]);
+    }
+    double w = factor > 0.0 ? factor : 1.5;
+    v = w / s;
+  }
+  dinv[sp.off + c] = v;
+  if (dinv32) dinv32[sp.off + c] = (float)v;
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; t < n; t += (long long)gridDim.x * blockDim.x) out[t] = (float)in[t];
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense assembly and Cholesky (FP64).
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_assemble(LevelView<double> L, double* __restrict__ A) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.N) return;
+  int p = find_part_cell(L.cellstart, L.np, g);
+  const DPart& dp = L.parts[p];
+  int c = g - dp.off;
+  int i, j, k;
+  {
+    unsigned q = fdiv((unsigned)c, dp.dx);
+    i = c - (int)q * dp.n[0];
+    k = (int)fdiv((unsigned)c, dp.dxy);
+    j = (int)q - k * dp.n[1];
+  }
+  double* row = A + (long long)g * L.N;
+  for (int t = 0; t < L.N; ++t) row[t] = 0.0;
+  for (int e = 0; e < dp.nent; ++e) {
+    if (!inside(dp, i + dp.o[e][0], j + dp.o[e][1], k + dp.o[e][2])) continue;
+    row[g + dp.disp[e]] += coef_at(dp, L.coef, e, c);
+  }
+  if (dp.has_u) {
+    int r = L.u_map[g];
+    if (r >= 0)
+      for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) row[L.u_col[q]] += L.u_val[q];
+  }
+}
+
+// Left-looking Cholesky A = L L^T in place (lower triangle), one block.
+// status: 0 ok, 1 not positive definite.
+__global__ void __launch_bounds__(NT) k_cholesky(int n, double* __restrict__ A, int* status) {
+  __shared__ double sh[NT / 32];
+  __shared__ double piv;
+  for (int jj = 0; jj < n; ++jj) {
+    double* rj = A + (long long)jj * n;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < jj; k += NT) s += rj[k] * rj[k];
+    double tot = block_sum<NT>(s, sh);
+    if (threadIdx.x == 0) {
+      double dd = rj[jj] - tot;
+      if (!(dd > 0.0)) {
+        *status = 1;
+        dd = 1.0;
+      }
+      piv = sqrt(dd);
+      rj[jj] = piv;
+    }
+    __syncthreads();
+    for (int i = jj + 1 + threadIdx.x; i < n; i += NT) {
+      double* ri = A + (long long)i * n;
+      double t = ri[jj];
+      for (int k = 0; k < jj; ++k) t -= ri[k] * rj[k];
+      ri[jj] = t / piv;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of ints (three passes; data[n] receives the total).
+// ---------------------------------------------------------------------------
+constexpr int SCAN_ITEMS = 1024;
+
+__global__ void __launch_bounds__(NT) k_scan_reduce(const int* __restrict__ in, long long n,
+                                                    int* __restrict__ sums) {
+  __shared__ int sh[NT];
+  long long base = (long long)blockIdx.x * SCAN_ITEMS;
+  int s = 0;
+  for (int t = threadIdx.x; t < SCAN_ITEMS; t += NT)
+    if (base + t < n) s += in[base + t];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ sums, int nb) {
+  // single block: exclusive scan of nb block sums, sums[nb] = total
+  __shared__ int sh[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int t = base + threadIdx.x;
+    int v = t < nb ? sums[t] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      int u = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += u;
+      __syncthreads();
+    }
+    if (t < nb) sums[t] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void __launch_bounds__(NT) k_scan_apply(int* __restrict__ data, long long n,
+                                                   const int* __restrict__ sums, int nb) {
+  __shared__ int sh[SCAN_ITEMS];
+  long long base = (long long)blockIdx.x * SCAN_ITEMS;
+  for (int t = threadIdx.x; t < SCAN_ITEMS; t += NT) sh[t] = base + t < n ? data[base + t] : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = sums[blockIdx.x];
+    for (int t = 0; t < SCAN_ITEMS; ++t) {
+      int v = sh[t];
+      sh[t] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < SCAN_ITEMS; t += NT)
+    if (base + t < n) data[base + t] = sh[t];
+  if (blockIdx.x == nb - 1 && threadIdx.x == 0) data[n] = sums[nb];
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st) {
+  k_wsum<<<L.nblk, NT, 0, st>>>(L.view<double>(), partial);
+  SSAMG_LAUNCH_CHECK();
+  k_wfinal<<<L.np, NT, 0, st>>>(L.d_blk, partial, c_out);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_interp(const Level& F, bool fp32, cudaStream_t st) {
+  if (F.nfblk == 0) return;
+  k_interp<<<F.nfblk, NT, 0, st>>>(F.view<double>(), F.Pw, F.Pe, fp32 ? F.Pw32 : nullptr,
+                                   fp32 ? F.Pe32 : nullptr);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st) {
+  k_rap_struct<<<Cl.nblk, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
+                                       fp32 ? Cl.coef32 : nullptr);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_umark(const Level& F, const Level& Cl, int* marker, cudaStream_t st) {
+  SSAMG_CUDA(cudaMemsetAsync(marker, 0, sizeof(int) * (Cl.N + 1), st));
+  if (F.nr > 0) {
+    k_umark<<<cdiv(F.nr, NT), NT, 0, st>>>(F.view<double>(), F.nr, F.u_rows, marker);
+    SSAMG_LAUNCH_CHECK();
+  }
+}
+
+void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStream_t st) {
+  k_urows<<<cdiv(Cl.N, NT), NT, 0, st>>>((int)Cl.N, scan, marker, Cl.u_map, Cl.u_rows);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_ucount(const Level& F, const Level& Cl, int* counts, int* err, cudaStream_t st) {
+  if (Cl.nr == 0) return;
+  k_ucount<<<cdiv(Cl.nr, 128), 128, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
+                                             Cl.u_rows, counts, err);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStream_t st) {
+  if (Cl.nr == 0) return;
+  k_ufill<<<cdiv(Cl.nr, 128), 128, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
+                                            Cl.u_rows, Cl.u_ptr, Cl.u_col, Cl.u_val,
+                                            fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, err);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_umap_level0(const Level& L, cudaStream_t st) {
+  SSAMG_CUDA(cudaMemsetAsync(L.u_map, 0xff, sizeof(int) * L.N, st));
+  if (L.nr > 0) {
+    k_umap0<<<cdiv(L.nr, NT), NT, 0, st>>>(L.nr, L.u_rows, L.u_map);
+    SSAMG_LAUNCH_CHECK();
+  }
+}
+
+void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st) {
+  k_dinv<<<L.nblk, NT, 0, st>>>(L.view<double>(), relax, factor, L.dinv, fp32 ? L.dinv32 : nullptr);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {
+  if (n <= 0) return;
+  int nb = (int)std::min<long long>(cdiv(n, NT), 152 * 16);
+  k_to_float<<<nb, NT, 0, st>>>(in, out, n);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_coarse_assemble(const Level& L, double* A, cudaStream_t st) {
+  k_coarse_assemble<<<cdiv(L.N, 64), 64, 0, st>>>(L.view<double>(), A);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_cholesky(int n, double* A, int* status, cudaStream_t st) {
+  k_cholesky<<<1, NT, 0, st>>>(n, A, status);
+  SSAMG_LAUNCH_CHECK();
+}
+
+size_t scan_tmp_ints(long long n) { return (size_t)cdiv(n, SCAN_ITEMS) + 1; }
+
+void launch_scan(int* data, long long n, int* tmp, cudaStream_t st) {
+  if (n <= 0) {
+    SSAMG_CUDA(cudaMemsetAsync(data, 0, sizeof(int), st));
+    return;
+  }
+  int nb = cdiv(n, SCAN_ITEMS);
+  k_scan_reduce<<<nb, NT, 0, st>>>(data, n, tmp);
+  SSAMG_LAUNCH_CHECK();
+  k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);
+  SSAMG_LAUNCH_CHECK();
+  k_scan_apply<<<nb, NT, 0, st>>>(data, n, tmp, nb);
+  SSAMG_LAUNCH_CHECK();
+}

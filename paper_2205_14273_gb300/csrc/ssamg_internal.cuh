@@ -1,0 +1,265 @@
+// Internal structures of the SSAMG library (host and device).
+//
+// Data layout in HBM, per level l:
+//   vectors      one contiguous array of N_l values; parts in order, each
+//                part's box with i fastest, then j, then k.
+//   coefficients one buffer per level; every per-cell (variable) stencil entry
+//                of a part is a contiguous array of the part's cells (SoA,
+//                entry-major); constant entries are a scalar in the part
+//                descriptor.  Levels >= 1 are all variable (Galerkin output).
+//   P            two arrays (west / east weight) over the fine points of the
+//                coarsened parts only (Section 3.2: coarse points carry 1).
+//   U            CSR over the rows that have couplings (row list sorted by
+//                cell), plus a dense cell -> row map that only face cells read.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ssamg.h"
+
+#define SSAMG_MAXE 27
+#define SSAMG_BLOCK 256
+#define SSAMG_MAX_UCAND 128
+
+// ---------------------------------------------------------------------------
+// Division by a run-time constant (round-up multiply-high method of Granlund
+// and Montgomery, PLDI 1994): q = (mulhi(n, m) + n) >> s, exact for every
+// n < 2^31 with s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  unsigned d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d ? d : 1;
+  unsigned s = 0;
+  while ((1ull << s) < f.d) ++s;
+  f.s = s;
+  f.m = (unsigned)((((1ull << 32) * ((1ull << s) - f.d)) / f.d) + 1ull);
+  if (f.d == 1) f.m = 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  return (__umulhi(n, f.m) + n) >> f.s;
+#else
+  return (unsigned)((((unsigned long long)n * f.m >> 32) + n) >> f.s);
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// Per-part, per-level descriptor (device copy).  4-byte multiple, <= 1 KiB so
+// one block can stage it in shared memory with a single pass of 256 threads.
+// ---------------------------------------------------------------------------
+struct DPart {
+  long long coef[SSAMG_MAXE];  // element offset of a variable entry, -1: constant
+  double cval[SSAMG_MAXE];     // value of a constant entry
+  double omega;                // omega_p (Eq. relax1) at this level
+  int n[3];                    // extents along x, y, z
+  int ncell;
+  int off;                     // first cell in the level vector
+  int blk0;                    // first block of cell-wise launches over this level
+  int nent;
+  int dstar;                   // coarsening direction at this level, -1: none
+  int par;                     // lo[dstar] & 1 (parity of local cell 0)
+  int has_u;                   // some cell of the part has U couplings
+  int coff;                    // first cell of the part in the next level vector
+  int cn[3];                   // extents on the next level
+  int cncell;
+  int poff;                    // first fine point in this level's P arrays
+  int nf[3];                   // extents of the fine-point grid
+  int nfine;
+  int fblk0;                   // first block of launches over fine points
+  FastDiv dx, dxy;             // divide by n[0], n[0]*n[1]
+  FastDiv cdx, cdxy;           // same on the next level
+  FastDiv fdx, fdxy;           // same on the fine-point grid
+  int disp[SSAMG_MAXE];        // linear displacement of each entry
+  signed char o[SSAMG_MAXE][3];
+  signed char slot[27];        // entry index of offset code (ox+1)+3(oy+1)+9(oz+1), -1 absent
+  signed char pad_[2];
+};
+static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
+
+// Scalars of one PCG solve (device memory).
+struct PcgScalars {
+  double tol, bb, rr, rz, pq, alpha, beta, tol2bb;
+  int iter, max_iter, status, flexible, done, pad_;
+};
+
+// Views passed to kernels by value.
+template <class T>
+struct LevelView {
+  const DPart* parts;
+  const int* blk;        // np + 1 block starts of cell-wise launches
+  const int* fblk;       // np + 1 block starts of fine-point launches
+  const int* cellstart;  // np + 1 first cells
+  int np;
+  int N;
+  const T* coef;
+  const T* dinv;
+  const T* Pw;
+  const T* Pe;
+  const int* u_map;
+  const int* u_ptr;
+  const int* u_col;
+  const T* u_val;
+  const unsigned char* u_bits;
+};
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct PartH {
+  int lo[3], hi[3], n[3];
+  long long ncell;
+  int off;
+  int dstar, par;
+  double omega;
+  int nent;
+  int o[SSAMG_MAXE][3];
+  int var[SSAMG_MAXE];
+  double cval[SSAMG_MAXE];
+  long long coef_off[SSAMG_MAXE];
+  int nf[3];
+  long long nfine;
+  int poff;
+  int has_u;
+};
+
+struct Arena {
+  std::vector<std::pair<char*, size_t>> chunks;
+  size_t cur = 0, used = 0;
+  void reset() { cur = 0; used = 0; }
+  void* alloc(size_t bytes);  // 256-byte aligned, throws on failure
+  void release();
+  ~Arena() { release(); }
+};
+
+struct Level {
+  int np = 0;
+  long long N = 0;
+  std::vector<PartH> parts;
+  std::vector<DPart> dparts;
+  DPart* d_parts = nullptr;
+  int* d_blk = nullptr;
+  int* d_fblk = nullptr;
+  int* d_cellstart = nullptr;
+  int nblk = 0, nfblk = 0;
+  double* coef = nullptr;
+  float* coef32 = nullptr;
+  long long ncoef = 0;
+  double* Pw = nullptr;
+  double* Pe = nullptr;
+  float* Pw32 = nullptr;
+  float* Pe32 = nullptr;
+  long long nP = 0;
+  double* dinv = nullptr;
+  float* dinv32 = nullptr;
+  int nr = 0;
+  long long nnz = 0;
+  int* u_ptr = nullptr;
+  int* u_rows = nullptr;
+  int* u_col = nullptr;
+  int* u_map = nullptr;
+  double* u_val = nullptr;
+  float* u_val32 = nullptr;
+  unsigned char* u_bits = nullptr;
+  // cycle work vectors (precision of the cycle)
+  void* x = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+  void* t = nullptr;
+
+  template <class T>
+  LevelView<T> view() const;
+};
+
+template <>
+inline LevelView<double> Level::view<double>() const {
+  return LevelView<double>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
+                           u_map, u_ptr, u_col, u_val, u_bits};
+}
+template <>
+inline LevelView<float> Level::view<float>() const {
+  return LevelView<float>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
+                          Pe32, u_map, u_ptr, u_col, u_val32, u_bits};
+}
+
+struct SsamgError {
+  int code;
+  std::string msg;
+};
+
+#define SSAMG_CUDA(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) throw SsamgError{SSAMG_ERR_CUDA, std::string(#call ": ") +       \
+                                                           cudaGetErrorString(e_)};         \
+  } while (0)
+
+#define SSAMG_LAUNCH_CHECK() SSAMG_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels_*.cu)
+// ---------------------------------------------------------------------------
+// setup
+void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st);
+void launch_interp(const Level& F, bool fp32, cudaStream_t st);
+void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st);
+void launch_umark(const Level& F, const Level& Cl, int* marker, cudaStream_t st);
+void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStream_t st);
+void launch_ucount(const Level& F, const Level& Cl, int* counts, int* err, cudaStream_t st);
+void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStream_t st);
+void launch_umap_level0(const Level& L, cudaStream_t st);
+void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st);
+void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
+void launch_coarse_assemble(const Level& L, double* A, cudaStream_t st);
+void launch_cholesky(int n, double* A, int* status, cudaStream_t st);
+// exclusive scan of n ints in place; returns nothing (total at out[n])
+void launch_scan(int* data, long long n, int* tmp, cudaStream_t st);
+size_t scan_tmp_ints(long long n);
+
+// cycle (T = float or double)
+template <class T>
+void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st);
+template <class T>
+void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
+template <class T>
+void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st);
+template <class T>
+void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st);
+template <class T>
+void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st);
+template <class T>
+void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st);
+void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st);
+void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st);
+void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st);
+
+// PCG (FP64)
+void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
+                     PcgScalars* sc, cudaStream_t st);
+void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
+                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
+void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
+                     double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
+void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
+                      PcgScalars* sc, cudaStream_t st);
+void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,
+                       double* partial, int nblk, PcgScalars* sc, cudaGraphConditionalHandle h,
+                       int use_handle, cudaStream_t st);
+void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
+                          double* partial, double* out, cudaStream_t st);
+int reduce_blocks(long long n);
+
+// differentiation
+void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
+                          cudaStream_t st);
+void launch_diffusion_exp_gradient(const Level& L, const double* g, const double* lam,
+                                   const double* x, double* dg, cudaStream_t st);

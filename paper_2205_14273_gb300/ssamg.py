@@ -1,0 +1,362 @@
+"""Python binding of the SSAMG C ABI (include/ssamg.h).
+
+Argument marshalling only: every step of setup and solve runs in the CUDA
+library libssamg.so.  Device vectors are torch CUDA tensors (float64,
+contiguous); streams are torch.cuda.Stream objects or raw cudaStream_t
+integers.  If the library is missing this module raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libssamg.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ssamg.h")
+
+OK = 0
+NOT_CONVERGED = 1
+ERR_ARG = -1
+ERR_STATE = -2
+ERR_OOM = -3
+ERR_CUDA = -4
+ERR_BREAKDOWN = -5
+ERR_TIMEOUT = -6
+ERR_UNSUPPORTED = -7
+
+
+class SsamgError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code}) {last_error()}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("relax", ctypes.c_int),
+                ("relax_factor", ctypes.c_double), ("skip", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("s_max", ctypes.c_longlong),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("coarse_direct", ctypes.c_int), ("flexible", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("num_levels", ctypes.c_int), ("coarse_size", ctypes.c_longlong),
+                ("operator_complexity", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_ll = ctypes.c_longlong
+_d = ctypes.c_double
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "ssamg_status_string": (ctypes.c_char_p, [_i]),
+    "ssamg_last_error": (ctypes.c_char_p, []),
+    "ssamg_grid_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
+    "ssamg_grid_set_box": (_i, [_vp, _i, _ip, _ip]),
+    "ssamg_grid_assemble": (_i, [_vp]),
+    "ssamg_grid_num_cells": (_ll, [_vp]),
+    "ssamg_grid_destroy": (None, [_vp]),
+    "ssamg_matrix_create": (_i, [_vp, _i, _ip, ctypes.POINTER(_vp)]),
+    "ssamg_matrix_set_constant": (_i, [_vp, _i, _i, _d]),
+    "ssamg_matrix_set_box_values": (_i, [_vp, _i, _i, _vp, _i]),
+    "ssamg_matrix_add_couplings": (_i, [_vp, _ll, _ip, _ip, _ip, _ip, _ip, _dp]),
+    "ssamg_matrix_assemble": (_i, [_vp, _vp]),
+    "ssamg_matrix_destroy": (None, [_vp]),
+    "ssamg_params_default": (None, [ctypes.POINTER(Params)]),
+    "ssamg_solver_create": (_i, [ctypes.POINTER(Params), ctypes.POINTER(_vp)]),
+    "ssamg_solver_destroy": (None, [_vp]),
+    "ssamg_setup": (_i, [_vp, _vp, _vp]),
+    "ssamg_solve": (_i, [_vp, _vp, _vp, _i, _i, _vp, ctypes.POINTER(Stats)]),
+    "ssamg_solve_host": (_i, [_vp, _dp, _dp, _i, _vp, ctypes.POINTER(Stats)]),
+    "ssamg_adjoint_solve": (_i, [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(Stats)]),
+    "ssamg_coef_gradient": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ssamg_diffusion_exp_gradient": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "ssamg_precondition": (_i, [_vp, _vp, _vp, _vp]),
+    "ssamg_level_matvec": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "ssamg_num_levels": (_i, [_vp]),
+    "ssamg_level_part_info": (_i, [_vp, _i, _i, _ip, _ip, _ip, _dp, _ip, _ip,
+                                   ctypes.POINTER(_ll)]),
+    "ssamg_level_sizes": (_i, [_vp, _i, ctypes.POINTER(_ll), ctypes.POINTER(_ll),
+                               ctypes.POINTER(_ll)]),
+    "ssamg_level_copy": (_i, [_vp, _i, _i, _i, _i, _vp, _ll]),
+    "ssamg_spacings": (_i, [_vp, _dp, _dp]),
+    "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
+}
+
+
+def header_functions() -> list:
+    """Names of the functions include/ssamg.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssamg_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().ssamg_status_string(code).decode()
+
+
+def last_error() -> str:
+    return lib().ssamg_last_error().decode()
+
+
+def _check(code, what, allow=(OK,)):
+    if code not in allow:
+        raise SsamgError(code, what)
+    return code
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _ints(a) -> ctypes.Array:
+    a = np.ascontiguousarray(a, dtype=np.int32).ravel()
+    return (ctypes.c_int * len(a))(*a.tolist()) if len(a) else (ctypes.c_int * 1)()
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().ssamg_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Grid:
+    """Section 2: parts, each one box of cell-centred indices."""
+
+    def __init__(self, ndim: int, boxes: Sequence):
+        self.h = _vp()
+        _check(lib().ssamg_grid_create(ndim, len(boxes), ctypes.byref(self.h)), "grid_create")
+        for p, (lo, hi) in enumerate(boxes):
+            _check(lib().ssamg_grid_set_box(self.h, p, _ints(lo), _ints(hi)), "grid_set_box")
+        _check(lib().ssamg_grid_assemble(self.h), "grid_assemble")
+        self.ndim = ndim
+        self.boxes = [(tuple(lo), tuple(hi)) for lo, hi in boxes]
+        self.n = lib().ssamg_grid_num_cells(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ssamg_grid_destroy(self.h)
+            self.h = None
+
+
+class Matrix:
+    """Section 2: A = S + U with a stencil shared by the parts."""
+
+    def __init__(self, grid: Grid, offsets):
+        self.grid = grid
+        offs = np.asarray(offsets, np.int32).reshape(-1, 3)
+        self.offsets = offs
+        self.h = _vp()
+        _check(lib().ssamg_matrix_create(grid.h, len(offs), _ints(offs), ctypes.byref(self.h)),
+               "matrix_create")
+
+    def set_constant(self, part: int, entry: int, value: float):
+        _check(lib().ssamg_matrix_set_constant(self.h, part, entry, float(value)), "set_constant")
+
+    def set_box_values(self, part: int, entry: int, vals):
+        if hasattr(vals, "is_cuda") and vals.is_cuda:
+            _check(lib().ssamg_matrix_set_box_values(self.h, part, entry, _dptr(vals), 1),
+                   "set_box_values")
+        else:
+            a = np.ascontiguousarray(vals, dtype=np.float64).ravel()
+            _check(lib().ssamg_matrix_set_box_values(
+                self.h, part, entry, a.ctypes.data_as(_vp), 0), "set_box_values")
+
+    def add_couplings(self, part, idx, direction, nbor_part, nbor_idx, vals):
+        n = len(vals)
+        if n == 0:
+            return
+        v = np.ascontiguousarray(vals, np.float64)
+        _check(lib().ssamg_matrix_add_couplings(
+            self.h, n, _ints(part), _ints(idx), _ints(direction), _ints(nbor_part),
+            _ints(nbor_idx), v.ctypes.data_as(_dp)), "add_couplings")
+
+    def assemble(self, stream=None):
+        _check(lib().ssamg_matrix_assemble(self.h, _stream(stream)), "matrix_assemble")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ssamg_matrix_destroy(self.h)
+            self.h = None
+
+
+def matrix_from_problem(prob, stream=None, device_values=False):
+    """Grid and assembled matrix from a problem description with the fields
+    ndim, boxes, offsets, coef, u_* (see the problems package)."""
+    grid = Grid(prob.ndim, prob.boxes)
+    A = Matrix(grid, prob.offsets)
+    for p in range(len(prob.boxes)):
+        for e in range(len(prob.offsets)):
+            c = prob.coef[p][e]
+            if np.isscalar(c):
+                A.set_constant(p, e, float(c))
+            elif device_values:
+                import torch
+                A.set_box_values(p, e, torch.as_tensor(np.ascontiguousarray(c).ravel(),
+                                                       device="cuda"))
+            else:
+                A.set_box_values(p, e, c)
+    if len(prob.u_val):
+        A.add_couplings(prob.u_part, prob.u_idx, prob.u_dir, prob.u_nbor_part,
+                        prob.u_nbor_idx, prob.u_val)
+    A.assemble(stream)
+    return grid, A
+
+
+class Solver:
+    """SSAMG-preconditioned CG (Sections 3 and 4)."""
+
+    def __init__(self, params: Optional[Params] = None, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        self.h = _vp()
+        _check(lib().ssamg_solver_create(ctypes.byref(self.params), ctypes.byref(self.h)),
+               "solver_create")
+        self.matrix = None
+
+    def setup(self, A: Matrix, stream=None):
+        self.matrix = A
+        _check(lib().ssamg_setup(self.h, A.h, _stream(stream)), "setup")
+
+    def solve(self, b, x, nrhs: int = 1, zero_guess: bool = True, stream=None,
+              allow_not_converged=False) -> Stats:
+        st = Stats()
+        rc = lib().ssamg_solve(self.h, _dptr(b), _dptr(x), nrhs, int(zero_guess),
+                               _stream(stream), ctypes.byref(st))
+        _check(rc, "solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
+        return st
+
+    def solve_nostats(self, b, x, nrhs: int = 1, stream=None) -> int:
+        return _check(lib().ssamg_solve(self.h, _dptr(b), _dptr(x), nrhs, 1, _stream(stream),
+                                         None), "solve", (OK, NOT_CONVERGED))
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, nrhs: int = 1, stream=None,
+                   stats=True) -> Stats:
+        st = Stats()
+        assert b.dtype == np.float64 and x.dtype == np.float64 and x.flags.c_contiguous
+        rc = lib().ssamg_solve_host(self.h, b.ctypes.data_as(_dp), x.ctypes.data_as(_dp), nrhs,
+                                    _stream(stream), ctypes.byref(st) if stats else None)
+        _check(rc, "solve_host", (OK, NOT_CONVERGED))
+        return st
+
+    def adjoint_solve(self, g, lam, nrhs: int = 1, stream=None) -> Stats:
+        st = Stats()
+        _check(lib().ssamg_adjoint_solve(self.h, _dptr(g), _dptr(lam), nrhs, _stream(stream),
+                                         ctypes.byref(st)), "adjoint_solve")
+        return st
+
+    def coef_gradient(self, lam, x, dcoef, stream=None):
+        _check(lib().ssamg_coef_gradient(self.h, _dptr(lam), _dptr(x), _dptr(dcoef),
+                                         _stream(stream)), "coef_gradient")
+
+    def diffusion_exp_gradient(self, g, lam, x, dg, stream=None):
+        _check(lib().ssamg_diffusion_exp_gradient(self.h, _dptr(g), _dptr(lam), _dptr(x),
+                                                  _dptr(dg), _stream(stream)),
+               "diffusion_exp_gradient")
+
+    def precondition(self, r, z, stream=None):
+        _check(lib().ssamg_precondition(self.h, _dptr(r), _dptr(z), _stream(stream)),
+               "precondition")
+
+    def level_matvec(self, level: int, x, y, stream=None):
+        _check(lib().ssamg_level_matvec(self.h, level, _dptr(x), _dptr(y), _stream(stream)),
+               "level_matvec")
+
+    # ---- introspection (host copies)
+    def num_levels(self) -> int:
+        n = lib().ssamg_num_levels(self.h)
+        if n < 0:
+            raise SsamgError(n, "num_levels")
+        return n
+
+    def level_sizes(self, level: int):
+        n, r, z = _ll(), _ll(), _ll()
+        _check(lib().ssamg_level_sizes(self.h, level, ctypes.byref(n), ctypes.byref(r),
+                                       ctypes.byref(z)), "level_sizes")
+        return n.value, r.value, z.value
+
+    def part_info(self, level: int, part: int) -> dict:
+        lo = (ctypes.c_int * 3)()
+        hi = (ctypes.c_int * 3)()
+        ds = ctypes.c_int()
+        om = ctypes.c_double()
+        ne = ctypes.c_int()
+        offs = (ctypes.c_int * 81)()
+        off = _ll()
+        _check(lib().ssamg_level_part_info(self.h, level, part, lo, hi, ctypes.byref(ds),
+                                           ctypes.byref(om), ctypes.byref(ne), offs,
+                                           ctypes.byref(off)), "level_part_info")
+        n = ne.value
+        return {"lo": tuple(lo), "hi": tuple(hi), "dstar": ds.value, "omega": om.value,
+                "offsets": [tuple(offs[3 * e:3 * e + 3]) for e in range(n)],
+                "cell_offset": off.value}
+
+    def level_copy(self, level: int, what: int, part: int = 0, entry: int = 0, n: int = 0,
+                   dtype=np.float64) -> np.ndarray:
+        out = np.zeros(n, dtype)
+        _check(lib().ssamg_level_copy(self.h, level, what, part, entry,
+                                      out.ctypes.data_as(_vp), n), "level_copy")
+        return out
+
+    def spacings(self, nparts: int):
+        c = np.zeros(3 * nparts)
+        W = np.zeros(3 * nparts)
+        _check(lib().ssamg_spacings(self.h, c.ctypes.data_as(_dp), W.ctypes.data_as(_dp)),
+               "spacings")
+        return c.reshape(nparts, 3), W.reshape(nparts, 3)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ssamg_solver_destroy(self.h)
+            self.h = None

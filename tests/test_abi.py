@@ -1,0 +1,104 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/ssamg.h declares, and rejects invalid input before touching CUDA."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+def test_exports_every_declared_function(ssamg_lib):
+    S = ssamg_lib
+    names = S.header_functions()
+    assert len(names) >= 25
+    L = S.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in S._SIGS, f"binding lacks a signature for {n}"
+
+
+def test_fastdiv_constants(ssamg_lib):
+    assert ssamg_lib.lib().ssamg_selftest_fastdiv(12345, 500000) == 0
+    assert ssamg_lib.lib().ssamg_selftest_fastdiv(99, 500000) == 0
+
+
+def test_status_strings(ssamg_lib):
+    S = ssamg_lib
+    for c in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert len(S.status_string(c)) >= 2 and S.status_string(c) != "unknown status"
+
+
+def _grid(S, ndim, boxes):
+    L = S.lib()
+    h = ctypes.c_void_p()
+    assert L.ssamg_grid_create(ndim, len(boxes), ctypes.byref(h)) == 0
+    rcs = [L.ssamg_grid_set_box(h, p, S._ints(lo), S._ints(hi)) for p, (lo, hi) in enumerate(boxes)]
+    return h, rcs
+
+
+def test_grid_validation(ssamg_lib):
+    S = ssamg_lib
+    L = S.lib()
+    h = ctypes.c_void_p()
+    assert L.ssamg_grid_create(4, 1, ctypes.byref(h)) == S.ERR_ARG
+    assert L.ssamg_grid_create(3, 0, ctypes.byref(h)) == S.ERR_ARG
+    g, rcs = _grid(S, 2, [((0, 0, 0), (3, 3, 0)), ((0, 0, 0), (3, 3, 1))])
+    assert rcs == [0, S.ERR_ARG]          # unused dimension must be flat
+    assert L.ssamg_grid_set_box(g, 1, S._ints((2, 0, 0)), S._ints((1, 3, 0))) == S.ERR_ARG
+    assert L.ssamg_grid_assemble(g) == S.ERR_ARG   # part 1 has no box
+    assert L.ssamg_grid_num_cells(g) == -1
+    assert L.ssamg_grid_set_box(g, 1, S._ints((-2, 0, 0)), S._ints((1, 3, 0))) == 0
+    assert L.ssamg_grid_assemble(g) == 0
+    assert L.ssamg_grid_num_cells(g) == 16 + 16
+    assert L.ssamg_grid_set_box(g, 0, S._ints((0, 0, 0)), S._ints((1, 1, 0))) == S.ERR_STATE
+    L.ssamg_grid_destroy(g)
+
+
+def test_matrix_and_coupling_validation(ssamg_lib):
+    S = ssamg_lib
+    L = S.lib()
+    g, _ = _grid(S, 3, [((0, 0, 0), (3, 3, 3)), ((0, 0, 0), (3, 3, 3))])
+    assert L.ssamg_grid_assemble(g) == 0
+    A = ctypes.c_void_p()
+    assert L.ssamg_matrix_create(g, 2, S._ints([0, 0, 0, 2, 0, 0]), ctypes.byref(A)) == S.ERR_ARG
+    assert L.ssamg_matrix_create(g, 2, S._ints([0, 0, 0, 0, 0, 0]), ctypes.byref(A)) == S.ERR_ARG
+    offs = [0, 0, 0, 1, 0, 0, -1, 0, 0]
+    assert L.ssamg_matrix_create(g, 3, S._ints(offs), ctypes.byref(A)) == 0
+    assert L.ssamg_matrix_set_constant(A, 2, 0, 1.0) == S.ERR_ARG
+    assert L.ssamg_matrix_set_constant(A, 0, 3, 1.0) == S.ERR_ARG
+
+    def add(part, idx, d, q, nidx):
+        v = np.array([-1.0])
+        return L.ssamg_matrix_add_couplings(A, 1, S._ints([part]), S._ints(idx), S._ints(d),
+                                            S._ints([q]), S._ints(nidx),
+                                            v.ctypes.data_as(S._dp))
+    assert add(0, (3, 1, 1), (1, 0, 0), 1, (0, 1, 1)) == 0
+    assert add(0, (2, 1, 1), (0, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG   # row not on a face
+    assert add(0, (3, 1, 1), (1, 0, 0), 0, (0, 1, 1)) == S.ERR_ARG   # same part
+    assert add(0, (0, 1, 1), (1, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG   # dir leaves through +x but cell is at lo
+    assert add(0, (3, 1, 1), (1, 0, 0), 1, (4, 1, 1)) == S.ERR_ARG   # column outside its box
+    # every entry of every part needs a value before assembly (no CUDA call yet)
+    assert L.ssamg_matrix_assemble(A, None) == S.ERR_ARG
+    L.ssamg_matrix_destroy(A)
+    L.ssamg_grid_destroy(g)
+
+
+def test_solver_state_errors(ssamg_lib):
+    S = ssamg_lib
+    L = S.lib()
+    p = S.default_params()
+    assert p.tol == 1e-8 and p.max_levels == 64 and p.coarse_direct == 1
+    h = ctypes.c_void_p()
+    bad = S.default_params(precision=2)
+    assert L.ssamg_solver_create(ctypes.byref(bad), ctypes.byref(h)) == S.ERR_ARG
+    assert L.ssamg_solver_create(ctypes.byref(p), ctypes.byref(h)) == 0
+    x = ctypes.c_void_p(16)
+    assert L.ssamg_solve(h, x, x, 1, 1, None, None) == S.ERR_STATE
+    assert L.ssamg_num_levels(h) == S.ERR_STATE
+    g, _ = _grid(S, 3, [((0, 0, 0), (1, 1, 1))])
+    assert L.ssamg_grid_assemble(g) == 0
+    A = ctypes.c_void_p()
+    assert L.ssamg_matrix_create(g, 1, S._ints([0, 0, 0]), ctypes.byref(A)) == 0
+    assert L.ssamg_setup(h, A, None) == S.ERR_STATE     # matrix not assembled
+    L.ssamg_solver_destroy(h)
+    L.ssamg_matrix_destroy(A)
+    L.ssamg_grid_destroy(g)
