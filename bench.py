@@ -1,0 +1,421 @@
+"""SSAMG-PCG benchmark on one GB300 (or N replicas, one per GPU).
+
+Workload (default): 8 parts of 64^3 cells in a 2x2x2 layout (2,097,152
+unknowns), 7-point anisotropic diffusion with per-part (a_x, a_y, a_z) ~
+log-uniform[1e-3, 1] (seed 1), harmonic-mean inter-part couplings, RHS ~
+U[-1,1]; PCG with one SSAMG V(1,1) cycle per iteration from x0 = 0 to a
+1e-8 relative residual.  A step is one SSAMG setup plus one PCG solve, with
+the assembled matrix already resident on the device.  The headline uses the
+FP32 V-cycle inside FP64 PCG; the plain FP64 method is timed the same way and
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica of the workload (no data-path
+collective; barrier and max-over-ranks timing only).  --impl reference times
+the CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import problems as P  # noqa: E402
+
+METRIC = "SSAMG-PCG setup+solve ms, MDOF/s to 1e-8 rel. res., FP32-cycle vs FP64; %HBM"
+WORKLOAD = "8 parts x 64^3 (2x2x2 layout), 7-pt anisotropic diffusion, seed 1"
+L2_BYTES = 129 * 2 ** 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        out["sm_mhz"] = statistics.median(load) if load else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+def fmt(v):
+    if isinstance(v, float):
+        return float(f"{v:.4e}") if 0 < abs(v) < 1e-3 else round(v, 4)
+    return v
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2205_14273_gb300 import ssamg as S
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    S.lib()
+
+    prob = P.config(1)
+    N = prob.n
+    grid, A = S.matrix_from_problem(prob)
+    b = torch.as_tensor(prob.b[0], device=dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def make(precision):
+        return S.Solver(precision=precision, flexible=precision, tol=1e-8, max_iter=500,
+                        use_graph=0 if args.no_graph else 1)
+
+    solvers = {"fp32_cycle": make(1), "fp64": make(0)}
+    if args.only:
+        solvers = {args.only: solvers[args.only]}
+    results = {}
+    for name, sv in solvers.items():
+        # warm-up steps (also builds the arena and the CUDA graph)
+        for _ in range(args.warmup):
+            sv.setup(A)
+            sv.solve(b, x)
+        st = sv.solve(b, x)
+        assert st.converged and st.true_rel_res <= 1.05e-8, (name, st.as_dict())
+        verified = st.as_dict()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush_l2(flush)
+            e0, e1, e2 = ev[k]
+            e0.record(stream)
+            sv.setup(A)
+            e1.record(stream)
+            sv.solve_nostats(b, x)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if ws > 1:
+            dist.barrier()
+        ck = clocks.stop()
+        setup_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+        solve_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+        step_ms = sum(setup_ms) / args.steps + sum(solve_ms) / args.steps
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        if ws > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        results[name] = {
+            "ms_per_step": step_ms,
+            "setup_ms": statistics.median(setup_ms),
+            "solve_ms": statistics.median(solve_ms),
+            "iterations": verified["iterations"],
+            "true_rel_res": verified["true_rel_res"],
+            "levels": verified["num_levels"],
+            "operator_complexity": verified["operator_complexity"],
+            "mdof_s": ws * N / (step_ms * 1e-3) / 1e6,
+            "solve_mdof_s": ws * N / (statistics.median(solve_ms) * 1e-3) / 1e6,
+            "wall_s": wall,
+            "clocks": ck,
+        }
+
+    # ---- dominant-kernel roofline: level-0 FP64 operator apply
+    roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
+
+    # ---- end to end through the C ABI with host buffers (matrix upload,
+    # setup, solve, result read-back)
+    e2e = None if args.no_e2e else end_to_end(S, prob, dev, stream, args)
+
+    head = results.get("fp32_cycle") or results["fp64"]
+    other = results.get("fp64", head)
+    line = {
+        "metric": METRIC,
+        "value": round(head["mdof_s"], 3),
+        "unit": "MDOF/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(head["ms_per_step"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32-cycle/f64-pcg",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": N, "tol": 1e-8, "parallelism": f"replicas{ws}",
+                   "l2": "flushed between steps (write of 2x L2)"},
+        "setup_ms": round(head["setup_ms"], 4),
+        "solve_ms": round(head["solve_ms"], 4),
+        "iterations": head["iterations"],
+        "fp64": {k: fmt(v) for k, v in other.items() if k != "clocks"},
+        "fp32_cycle": {k: fmt(v) for k, v in head.items() if k != "clocks"},
+        "speedup_fp32_cycle_vs_fp64": round(other["ms_per_step"] / head["ms_per_step"], 3),
+        "gpu_launches": None,
+        "roofline": roof,
+        "e2e": e2e,
+        "clocks": head["clocks"],
+    }
+    line["gpu_launches"] = count_launches(next(iter(solvers.values())), head["iterations"])
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def count_launches(sv, iters):
+    """Kernel launches of one setup + solve, counted from the hierarchy shape
+    (setup: per level interpolation, Galerkin, U product, diagonals; solve:
+    5 kernels per level and cycle plus the PCG kernels)."""
+    L = sv.num_levels()
+    nu = sum(1 for l in range(L) if sv.level_sizes(l)[1] > 0)
+    setup = 2 + 2 * (L - 1) + 7 * nu + L + 2 + 1 + 1
+    cycle = 5 * (L - 1) + 1 + 2
+    pcg = 2 + (cycle + 2 + 2 + 2) + iters * (cycle + 3 + 2 + 2)
+    return setup + pcg
+
+
+def kernel_roofline(S, sv, prob, dev, stream, args):
+    import torch
+    N = prob.n
+    peaks = read_peaks()
+    xs = torch.rand(N, dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    for _ in range(5):
+        sv.level_matvec(0, xs, ys)
+    reps = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sv.level_matvec(0, xs, ys)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / reps * 1e-3
+    # algorithmic bytes: x, y, the variable diagonal (8 B each per cell) and
+    # 16 B per coupling (value + column) -- constant off-diagonals are scalars
+    nbytes = 24 * N + 16 * prob.nnz_u
+    flops = 2 * 7 * N + 2 * prob.nnz_u
+    fp64_peak = 1.25e12
+    return {
+        "kernel": "level-0 FP64 SStruct operator apply (k_matvec)",
+        "bound": "alu",
+        "achieved": round(flops / dt / 1e12, 4),
+        "peak": fp64_peak / 1e12,
+        "unit": "TFLOP/s",
+        "frac": round(flops / dt / fp64_peak, 4),
+        "traffic": None,
+        "hbm_gbs": round(nbytes / dt / 1e9, 1),
+        "hbm_frac_of_measured": round(nbytes / dt / 1e9 / peaks.get("hbm_gbs", 6800.0), 4),
+        "us_per_launch": round(dt * 1e6, 3),
+    }
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def end_to_end(S, prob, dev, stream, args):
+    import torch
+    N = prob.n
+    b_pin = torch.from_numpy(prob.b[0].copy()).pin_memory()
+    x_pin = torch.zeros(N, dtype=torch.float64).pin_memory()
+    coef_pin = [[None if np.isscalar(c) else torch.from_numpy(np.ascontiguousarray(c).ravel()).pin_memory()
+                 for c in part] for part in prob.coef]
+    h2d = 8 * N + sum(t.numel() * 8 for part in coef_pin for t in part if t is not None) \
+        + prob.nnz_u * (8 + 4 * 10)
+    d2h = 8 * N
+
+    def step():
+        grid = S.Grid(prob.ndim, prob.boxes)
+        A = S.Matrix(grid, prob.offsets)
+        for p, part in enumerate(prob.coef):
+            for e, c in enumerate(part):
+                if coef_pin[p][e] is None:
+                    A.set_constant(p, e, float(c))
+                else:
+                    A.set_box_values(p, e, coef_pin[p][e].numpy())
+        A.add_couplings(prob.u_part, prob.u_idx, prob.u_dir, prob.u_nbor_part, prob.u_nbor_idx,
+                        prob.u_val)
+        A.assemble(stream)
+        sv = S.Solver(precision=1, flexible=1, tol=1e-8, max_iter=500)
+        sv.setup(A, stream)
+        sv.solve_host(b_pin.numpy(), x_pin.numpy(), stream=stream, stats=False)
+        return sv
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    reps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": round(N / dt / 1e6, 3), "unit": "MDOF/s", "ms_per_step": round(dt * 1e3, 3),
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "includes": "grid+matrix creation from pinned host arrays, assemble, setup, solve, x read-back"}
+
+
+def cpu_baseline(prob, sample_iters=2):
+    """The oracle on the host: full setup plus the first `sample_iters` PCG
+    iterations timed, extrapolated by the oracle's own iteration count."""
+    from oracle import ssamg as O
+    t0 = time.perf_counter()
+    h = O.setup(prob)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.pcg(h, prob.b[0], max_iter=sample_iters)
+    t_it = (time.perf_counter() - t0) / sample_iters
+    iters = O.pcg(h, prob.b[0]).iterations
+    total = t_setup + iters * t_it
+    return {"value": round(prob.n / total / 1e6, 5), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"full setup + {sample_iters} of {iters} PCG iterations timed, extrapolated",
+            "setup_s": round(t_setup, 3), "s_per_iteration": round(t_it, 4),
+            "host": host_info()}
+
+
+def host_info():
+    try:
+        import platform
+        return {"nproc": os.cpu_count(), "machine": platform.machine()}
+    except Exception:
+        return {}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import ssamg as O
+    prob = P.config(1)
+    N = prob.n
+    # the oracle's own iteration count (one full solve, untimed)
+    h = O.setup(prob)
+    iters = O.pcg(h, prob.b[0]).iterations
+    sample_iters = 2
+    for _ in range(args.warmup):
+        O.vcycle(h, prob.b[0])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        h = O.setup(prob)
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.pcg(h, prob.b[0], max_iter=sample_iters)
+        t_it = (time.perf_counter() - t0) / sample_iters
+        times.append(t_setup + iters * t_it)
+    step_s = statistics.median(times)
+    v = N / step_s / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "MDOF/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_s * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": N, "tol": 1e-8, "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(v, 5), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: full setup + {sample_iters} of {iters} PCG iterations, extrapolated"},
+        "e2e": {"value": round(v, 5), "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the solve kernels directly (profilers cannot see kernel "
+                         "nodes of graphs with conditional nodes)")
+    ap.add_argument("--only", choices=["fp32_cycle", "fp64"], default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

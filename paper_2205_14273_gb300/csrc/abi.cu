@@ -537,6 +537,7 @@ void fill_dpart(DPart& dp, const PartH& h) {
     dp.disp[e] = h.o[e][0] + h.o[e][1] * h.n[0] + h.o[e][2] * h.n[0] * h.n[1];
     dp.coef[e] = h.var[e] ? h.coef_off[e] : -1;
     dp.cval[e] = h.cval[e];
+    dp.cval32[e] = (float)h.cval[e];
     dp.slot[(h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1)] = (signed char)e;
   }
   for (int d = 0; d < 3; ++d) dp.nf[d] = h.nf[d];
@@ -552,8 +553,8 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   std::vector<int> blk(np + 1, 0), fblk(np + 1, 0), cs(np + 1, 0);
   for (int p = 0; p < np; ++p) {
     const PartH& h = L.parts[p];
-    blk[p + 1] = blk[p] + (int)cdivll(h.ncell, SSAMG_BLOCK);
-    fblk[p + 1] = fblk[p] + (int)cdivll(h.nfine, SSAMG_BLOCK);
+    blk[p + 1] = blk[p] + (int)cdivll(h.ncell, SSAMG_TILE);
+    fblk[p + 1] = fblk[p] + (int)cdivll(h.nfine, SSAMG_TILE);
     cs[p + 1] = cs[p] + (int)h.ncell;
   }
   L.nblk = blk[np];
@@ -784,7 +785,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   for (int l = 1; l <= Lc; ++l) maxN = std::max(maxN, s->lev[l].N);
   int* marker = nullptr;
   int* scan_tmp = nullptr;
-  if (!s->d_err) s->d_err = aalloc<int>(s->arena, 4);
+  s->d_err = aalloc<int>(s->arena, 4);
   SSAMG_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, st));
   for (int l = 0; l < Lc; ++l) {
     Level& F = s->lev[l];
@@ -849,7 +850,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   }
   SSAMG_CUDA(cudaMemcpyAsync(s->h_int, s->d_err, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   SSAMG_CUDA(cudaStreamSynchronize(st));
-  if (s->h_int[0]) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "coarse coupling row exceeds the candidate limit"};
+  if (s->h_int[0]) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "a coarse coupling row has more than 1024 candidates"};
   if (s->h_int[2]) throw SsamgError{SSAMG_ERR_BREAKDOWN, "coarsest operator is not positive definite"};
 
   // ---- PCG work vectors

@@ -3,6 +3,14 @@
 
 #include "ssamg_internal.cuh"
 
+// Cell-wise launches give each block a tile of SSAMG_TILE consecutive cells of
+// one part; thread t handles cells t, t + SSAMG_BLOCK, ... (coalesced), so
+// per-block work (descriptor staging, reductions) is amortised over
+// SSAMG_CPT cells per thread.
+#define TILE_LOOP(c, first, count)                                                         \
+  for (int c##_m = 0, c = ((int)blockIdx.x - (first)) * SSAMG_TILE + (int)threadIdx.x;     \
+       c##_m < SSAMG_CPT && c < (count); ++c##_m, c += SSAMG_BLOCK)
+
 // Part owning block b of a launch whose per-part block starts are blk[0..np].
 __device__ __forceinline__ int find_part(const int* __restrict__ blk, int np, int b) {
   int lo = 0, hi = np - 1;
@@ -38,10 +46,15 @@ __device__ __forceinline__ bool inside(const DPart& p, int i, int j, int k) {
          (unsigned)k < (unsigned)p.n[2];
 }
 
-template <class T>
-__device__ __forceinline__ T coef_at(const DPart& p, const T* __restrict__ coef, int e, int c) {
+__device__ __forceinline__ double coef_at(const DPart& p, const double* __restrict__ coef, int e,
+                                          int c) {
   long long o = p.coef[e];
-  return o >= 0 ? coef[o + c] : (T)p.cval[e];
+  return o >= 0 ? coef[o + c] : p.cval[e];
+}
+__device__ __forceinline__ float coef_at(const DPart& p, const float* __restrict__ coef, int e,
+                                         int c) {
+  long long o = p.coef[e];
+  return o >= 0 ? coef[o + c] : p.cval32[e];
 }
 
 // (S x)(c) for local cell c = (i, j, k) of part p; x points at the level vector.

@@ -25,12 +25,12 @@ __global__ void __launch_bounds__(NT) k_residual(LevelView<T> L, const T* __rest
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
-  if (c >= sp.ncell) return;
-  int i, j, k;
-  cell_coords(sp, c, i, j, k);
-  int g = sp.off + c;
-  r[g] = b[g] - apply_A(L, sp, x, c, i, j, k);
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    int g = sp.off + c;
+    r[g] = b[g] - apply_A(L, sp, x, c, i, j, k);
+  }
 }
 
 // xo = x + omega M^-1 (b - A x)
@@ -41,12 +41,12 @@ __global__ void __launch_bounds__(NT) k_relax(LevelView<T> L, const T* __restric
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
-  if (c >= sp.ncell) return;
-  int i, j, k;
-  cell_coords(sp, c, i, j, k);
-  int g = sp.off + c;
-  xo[g] = fma(L.dinv[g], b[g] - apply_A(L, sp, x, c, i, j, k), x[g]);
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    int g = sp.off + c;
+    xo[g] = fma(L.dinv[g], b[g] - apply_A(L, sp, x, c, i, j, k), x[g]);
+  }
 }
 
 // bc = P^T r, one coarse cell per thread: the anchor (weight 1) and the two
@@ -60,31 +60,31 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   stage_part(fp, F.parts + p);
   stage_part(cp, C.parts + p);
   __syncthreads();
-  int cc = (blockIdx.x - cp.blk0) * NT + threadIdx.x;
-  if (cc >= cp.ncell) return;
-  int I[3];
-  cell_coords(cp, cc, I[0], I[1], I[2]);
-  const int d = fp.dstar;
-  T v;
-  if (d < 0) {
-    v = r[fp.off + (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]];
-  } else {
-    int f[3] = {I[0], I[1], I[2]};
-    const int anchor = 2 * I[d] + fp.par;
-    f[d] = anchor;
-    const int sd = (d == 0) ? 1 : (d == 1 ? fp.n[0] : fp.n[0] * fp.n[1]);
-    const int fa = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-    v = r[fa];
-    if (anchor - 1 >= 0) {
-      f[d] = anchor - 1;
-      v = fma(F.Pe[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa - sd], v);
+  TILE_LOOP(cc, cp.blk0, cp.ncell) {
+    int I[3];
+    cell_coords(cp, cc, I[0], I[1], I[2]);
+    const int d = fp.dstar;
+    T v;
+    if (d < 0) {
+      v = r[fp.off + (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]];
+    } else {
+      int f[3] = {I[0], I[1], I[2]};
+      const int anchor = 2 * I[d] + fp.par;
+      f[d] = anchor;
+      const int sd = (d == 0) ? 1 : (d == 1 ? fp.n[0] : fp.n[0] * fp.n[1]);
+      const int fa = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+      v = r[fa];
+      if (anchor - 1 >= 0) {
+        f[d] = anchor - 1;
+        v = fma(F.Pe[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa - sd], v);
+      }
+      if (anchor + 1 < fp.n[d]) {
+        f[d] = anchor + 1;
+        v = fma(F.Pw[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa + sd], v);
+      }
     }
-    if (anchor + 1 < fp.n[d]) {
-      f[d] = anchor + 1;
-      v = fma(F.Pw[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], r[fa + sd], v);
-    }
+    bc[cp.off + cc] = v;
   }
-  bc[cp.off + cc] = v;
 }
 
 // x += P ec, one fine cell per thread.
@@ -95,24 +95,34 @@ __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restr
   int p = find_part(F.blk, F.np, blockIdx.x);
   stage_part(fp, F.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - fp.blk0) * NT + threadIdx.x;
-  if (c >= fp.ncell) return;
-  int i, j, k;
-  cell_coords(fp, c, i, j, k);
-  int J[2];
-  T w[2];
-  int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
-  T v = x[fp.off + c];
-  for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
-  x[fp.off + c] = v;
+  TILE_LOOP(c, fp.blk0, fp.ncell) {
+    int i, j, k;
+    cell_coords(fp, c, i, j, k);
+    int J[2];
+    T w[2];
+    int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+    T v = x[fp.off + c];
+    for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
+    x[fp.off + c] = v;
+  }
 }
 
-// Coarsest level: x = (L L^T)^-1 b in FP64 with one warp.
+// Coarsest level: x = (L L^T)^-1 b in FP64 with one warp; small factors are
+// staged in shared memory first (one coalesced load instead of a dependent
+// global load per row).
 template <class T>
-__global__ void k_coarse_solve(int n, const double* __restrict__ Lf, const T* __restrict__ b,
-                               T* __restrict__ x) {
-  extern __shared__ double y[];
+__global__ void k_coarse_solve(int n, const double* __restrict__ Lg, const T* __restrict__ b,
+                               T* __restrict__ x, int staged) {
+  extern __shared__ double sm[];
+  double* y = sm;
+  const double* Lf = Lg;
   const int l = threadIdx.x;
+  if (staged) {
+    double* Ls = sm + n;
+    for (int t = l; t < n * n; t += 32) Ls[t] = Lg[t];
+    __syncwarp();
+    Lf = Ls;
+  }
   for (int i = 0; i < n; ++i) {
     const double* ri = Lf + (long long)i * n;
     double s = 0.0;
@@ -146,11 +156,11 @@ __global__ void __launch_bounds__(NT) k_matvec(LevelView<double> L, const double
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
-  if (c >= sp.ncell) return;
-  int i, j, k;
-  cell_coords(sp, c, i, j, k);
-  y[sp.off + c] = apply_A(L, sp, x, c, i, j, k);
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    y[sp.off + c] = apply_A(L, sp, x, c, i, j, k);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -178,17 +188,16 @@ __global__ void __launch_bounds__(NT) k_pcg_init(LevelView<double> L, const doub
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
   double bb = 0.0, rr = 0.0;
-  if (c < sp.ncell) {
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
     double bv = b[g];
     double rv = bv - apply_A(L, sp, x, c, i, j, k);
     r[g] = rv;
-    bb = bv * bv;
-    rr = rv * rv;
+    bb = fma(bv, bv, bb);
+    rr = fma(rv, rv, rr);
   }
   double s0 = block_sum<NT>(bb, sh);
   double s1 = block_sum<NT>(rr, sh);
@@ -303,15 +312,14 @@ __global__ void __launch_bounds__(NT) k_pcg_spmv_dot(LevelView<double> L, const 
   int pt = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + pt);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
   double s = 0.0;
-  if (c < sp.ncell) {
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
     double qv = apply_A(L, sp, p, c, i, j, k);
     q[g] = qv;
-    s = p[g] * qv;
+    s = fma(p[g], qv, s);
   }
   double t = block_sum<NT>(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
@@ -392,16 +400,16 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
-  if (c >= sp.ncell) return;
-  int i, j, k;
-  cell_coords(sp, c, i, j, k);
-  int g = sp.off + c;
-  double l = lam[g];
-  for (int e = 0; e < sp.nent; ++e) {
-    double v = 0.0;
-    if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) v = -l * x[g + sp.disp[e]];
-    dcoef[(long long)e * N + g] = v;
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    int g = sp.off + c;
+    double l = lam[g];
+    for (int e = 0; e < sp.nent; ++e) {
+      double v = 0.0;
+      if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) v = -l * x[g + sp.disp[e]];
+      dcoef[(long long)e * N + g] = v;
+    }
   }
 }
 
@@ -470,7 +478,9 @@ void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStre
 }
 template <class T>
 void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st) {
-  k_coarse_solve<T><<<1, 32, sizeof(double) * n, st>>>(n, Lfac, b, x);
+  const int staged = (n + n * n) * (int)sizeof(double) <= 40 * 1024;
+  size_t sm = sizeof(double) * (staged ? n + n * n : n);
+  k_coarse_solve<T><<<1, 32, sm, st>>>(n, Lfac, b, x, staged);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -1,6 +1,8 @@
 // Setup kernels: coupling sums (Section 3.1), interpolation (Section 3.2,
 // Eq. prolEx), Galerkin coarse operators (Section 3.3, Eq. galerkin),
 // relaxation diagonals (Section 3.4) and the coarsest-level factorisation.
+#include <climits>
+
 #include "kernels_common.cuh"
 
 namespace {
@@ -18,23 +20,25 @@ __global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __rest
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
   double s0 = 0, s1 = 0, s2 = 0;
-  if (c < sp.ncell) {
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     double sg = 1.0;
     for (int e = 0; e < sp.nent; ++e)
       if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0 && coef_at(sp, L.coef, e, c) < 0.0)
         sg = -1.0;
+    double t0 = 0, t1 = 0, t2 = 0;
     for (int e = 0; e < sp.nent; ++e) {
       if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
       double a = coef_at(sp, L.coef, e, c);
-      if (sp.o[e][0]) s0 -= a;
-      if (sp.o[e][1]) s1 -= a;
-      if (sp.o[e][2]) s2 -= a;
+      if (sp.o[e][0]) t0 -= a;
+      if (sp.o[e][1]) t1 -= a;
+      if (sp.o[e][2]) t2 -= a;
     }
-    s0 *= sg; s1 *= sg; s2 *= sg;
+    s0 += sg * t0;
+    s1 += sg * t1;
+    s2 += sg * t2;
   }
   double r0 = block_sum<NT>(s0, sh);
   double r1 = block_sum<NT>(s1, sh);
@@ -71,49 +75,49 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
   int p = find_part(L.fblk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int F = (blockIdx.x - sp.fblk0) * NT + threadIdx.x;
-  if (F >= sp.nfine) return;
-  const int d = sp.dstar;
-  int fc[3];
-  {
-    unsigned q = fdiv((unsigned)F, sp.fdx);
-    fc[0] = F - (int)q * sp.nf[0];
-    fc[2] = (int)fdiv((unsigned)F, sp.fdxy);
-    fc[1] = (int)q - fc[2] * sp.nf[1];
-  }
-  fc[d] = 2 * fc[d] + 1 - sp.par;  // the fine cell
-  const int i = fc[0], j = fc[1], k = fc[2];
-  const int c = (k * sp.n[1] + j) * sp.n[0] + i;
-  double nw = 0, ne = 0, den = 0, diag = 0;
-  for (int e = 0; e < sp.nent; ++e) {
-    if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
-    double a = coef_at(sp, L.coef, e, c);
-    int od = sp.o[e][d];
-    if (od < 0) nw += a;
-    else if (od > 0) ne += a;
-    else den += a;
-    if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += a;
-  }
-  double pw = 0, pe = 0;
-  bool ok = fabs(den) > 1e-300 && ((den > 0) == (diag > 0)) && diag != 0.0;
-  if (ok) {
-    pw = -nw / den;
-    pe = -ne / den;
-  }
-  if (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1)) {
-    int r = L.u_map[sp.off + c];
-    if (r >= 0) {
-      unsigned bits = 0;
-      for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) bits |= L.u_bits[q];
-      if (fc[d] == sp.n[d] - 1 && ((bits >> (2 * d)) & 1u)) { pw = 1.0; pe = 0.0; }
-      if (fc[d] == 0 && ((bits >> (2 * d + 1)) & 1u)) { pw = 0.0; pe = 1.0; }
+  TILE_LOOP(F, sp.fblk0, sp.nfine) {
+    const int d = sp.dstar;
+    int fc[3];
+    {
+      unsigned q = fdiv((unsigned)F, sp.fdx);
+      fc[0] = F - (int)q * sp.nf[0];
+      fc[2] = (int)fdiv((unsigned)F, sp.fdxy);
+      fc[1] = (int)q - fc[2] * sp.nf[1];
     }
-  }
-  Pw[sp.poff + F] = pw;
-  Pe[sp.poff + F] = pe;
-  if (Pw32) {
-    Pw32[sp.poff + F] = (float)pw;
-    Pe32[sp.poff + F] = (float)pe;
+    fc[d] = 2 * fc[d] + 1 - sp.par;  // the fine cell
+    const int i = fc[0], j = fc[1], k = fc[2];
+    const int c = (k * sp.n[1] + j) * sp.n[0] + i;
+    double nw = 0, ne = 0, den = 0, diag = 0;
+    for (int e = 0; e < sp.nent; ++e) {
+      if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
+      double a = coef_at(sp, L.coef, e, c);
+      int od = sp.o[e][d];
+      if (od < 0) nw += a;
+      else if (od > 0) ne += a;
+      else den += a;
+      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += a;
+    }
+    double pw = 0, pe = 0;
+    bool ok = fabs(den) > 1e-300 && ((den > 0) == (diag > 0)) && diag != 0.0;
+    if (ok) {
+      pw = -nw / den;
+      pe = -ne / den;
+    }
+    if (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1)) {
+      int r = L.u_map[sp.off + c];
+      if (r >= 0) {
+        unsigned bits = 0;
+        for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) bits |= L.u_bits[q];
+        if (fc[d] == sp.n[d] - 1 && ((bits >> (2 * d)) & 1u)) { pw = 1.0; pe = 0.0; }
+        if (fc[d] == 0 && ((bits >> (2 * d + 1)) & 1u)) { pw = 0.0; pe = 1.0; }
+      }
+    }
+    Pw[sp.poff + F] = pw;
+    Pe[sp.poff + F] = pe;
+    if (Pw32) {
+      Pw32[sp.poff + F] = (float)pw;
+      Pe32[sp.poff + F] = (float)pe;
+    }
   }
 }
 
@@ -134,60 +138,60 @@ __global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelVie
   stage_part(fp, F.parts + p);
   stage_part(cp, C.parts + p);
   __syncthreads();
-  int cc = (blockIdx.x - cp.blk0) * NT + threadIdx.x;
-  if (cc >= cp.ncell) return;
-  int I[3];
-  cell_coords(cp, cc, I[0], I[1], I[2]);
-  double acc[27];
-#pragma unroll
-  for (int t = 0; t < 27; ++t) acc[t] = 0.0;
-  const int d = fp.dstar;
-  if (d < 0) {
-    // part not coarsened at this level: P = I on this part
-    int c = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
-    for (int e = 0; e < fp.nent; ++e) {
-      if (!inside(fp, I[0] + fp.o[e][0], I[1] + fp.o[e][1], I[2] + fp.o[e][2])) continue;
-      int code = (fp.o[e][0] + 1) + 3 * (fp.o[e][1] + 1) + 9 * (fp.o[e][2] + 1);
-      acc[code] += coef_at(fp, F.coef, e, c);
-    }
-  } else {
-    const int anchor = 2 * I[d] + fp.par;
-    for (int a = -1; a <= 1; ++a) {
-      int f[3] = {I[0], I[1], I[2]};
-      f[d] = anchor + a;
-      if (f[d] < 0 || f[d] >= fp.n[d]) continue;
-      const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-      double w1 = 1.0;
-      if (a != 0) {
-        int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
-        w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
-      }
-      if (w1 == 0.0) continue;
+  TILE_LOOP(cc, cp.blk0, cp.ncell) {
+    int I[3];
+    cell_coords(cp, cc, I[0], I[1], I[2]);
+    double acc[27];
+  #pragma unroll
+    for (int t = 0; t < 27; ++t) acc[t] = 0.0;
+    const int d = fp.dstar;
+    if (d < 0) {
+      // part not coarsened at this level: P = I on this part
+      int c = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
       for (int e = 0; e < fp.nent; ++e) {
-        int g[3] = {f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]};
-        if (!inside(fp, g[0], g[1], g[2])) continue;
-        double v = w1 * coef_at(fp, F.coef, e, fcell);
-        int t = a + fp.o[e][d];
-        int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
-        if ((t & 1) == 0) {
-          ob[d] = t / 2;
-          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
-        } else {
-          int Gi = fp.poff + fine_point_index(fp, g[0], g[1], g[2]);
-          ob[d] = (t - 1) / 2;
-          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pw[Gi];
-          ob[d] = (t + 1) / 2;
-          acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pe[Gi];
+        if (!inside(fp, I[0] + fp.o[e][0], I[1] + fp.o[e][1], I[2] + fp.o[e][2])) continue;
+        int code = (fp.o[e][0] + 1) + 3 * (fp.o[e][1] + 1) + 9 * (fp.o[e][2] + 1);
+        acc[code] += coef_at(fp, F.coef, e, c);
+      }
+    } else {
+      const int anchor = 2 * I[d] + fp.par;
+      for (int a = -1; a <= 1; ++a) {
+        int f[3] = {I[0], I[1], I[2]};
+        f[d] = anchor + a;
+        if (f[d] < 0 || f[d] >= fp.n[d]) continue;
+        const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+        double w1 = 1.0;
+        if (a != 0) {
+          int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
+          w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
+        }
+        if (w1 == 0.0) continue;
+        for (int e = 0; e < fp.nent; ++e) {
+          int g[3] = {f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]};
+          if (!inside(fp, g[0], g[1], g[2])) continue;
+          double v = w1 * coef_at(fp, F.coef, e, fcell);
+          int t = a + fp.o[e][d];
+          int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
+          if ((t & 1) == 0) {
+            ob[d] = t / 2;
+            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
+          } else {
+            int Gi = fp.poff + fine_point_index(fp, g[0], g[1], g[2]);
+            ob[d] = (t - 1) / 2;
+            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pw[Gi];
+            ob[d] = (t + 1) / 2;
+            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pe[Gi];
+          }
         }
       }
     }
-  }
-  for (int e = 0; e < cp.nent; ++e) {
-    int code = (cp.o[e][0] + 1) + 3 * (cp.o[e][1] + 1) + 9 * (cp.o[e][2] + 1);
-    double v = acc[code];
-    if (!inside(cp, I[0] + cp.o[e][0], I[1] + cp.o[e][1], I[2] + cp.o[e][2])) v = 0.0;
-    ccoef[cp.coef[e] + cc] = v;
-    if (ccoef32) ccoef32[cp.coef[e] + cc] = (float)v;
+    for (int e = 0; e < cp.nent; ++e) {
+      int code = (cp.o[e][0] + 1) + 3 * (cp.o[e][1] + 1) + 9 * (cp.o[e][2] + 1);
+      double v = acc[code];
+      if (!inside(cp, I[0] + cp.o[e][0], I[1] + cp.o[e][1], I[2] + cp.o[e][2])) v = 0.0;
+      ccoef[cp.coef[e] + cc] = v;
+      if (ccoef32) ccoef32[cp.coef[e] + cc] = (float)v;
+    }
   }
 }
 
@@ -234,32 +238,61 @@ __global__ void k_urows(int Nc, const int* __restrict__ scan, const int* __restr
   }
 }
 
-struct UCand {
-  int J;
-  unsigned char bits;
-  double v;
-};
+// Coarse row R of U_c = P^T U P, one warp per row.  The warp gathers the
+// U rows of the coarse cell's fine points (at most 3 along d*), spreads every
+// entry u_fg over P's row of g (at most 2 columns J) into shared memory, and
+// merges equal columns: candidate t is the first of its column if no earlier
+// candidate has the same J; its output slot is the number of first
+// candidates with a smaller J; its value is the sum over its column in
+// generation order (deterministic).
+constexpr int UW = 1024;     // candidates per warp
+constexpr int UWARPS = 2;    // warps (rows) per block
 
-// Gathers and merges the candidates of coarse row R; returns the count (or
-// -1 on overflow).  When out_col is set, writes the merged row.
-__device__ int urow_build(const LevelView<double>& F, const LevelView<double>& C, int R,
-                          const int* __restrict__ crows, int* out_col, double* out_val,
-                          float* out_val32, unsigned char* out_bits) {
-  UCand cand[SSAMG_MAX_UCAND];
-  int nc = 0;
-  int I = crows[R];
-  int p = find_part_cell(C.cellstart, C.np, I);
+__device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+__global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, LevelView<double> C,
+                                                      int nrc, const int* __restrict__ crows,
+                                                      const int* __restrict__ ptr,
+                                                      int* __restrict__ counts,
+                                                      int* __restrict__ col,
+                                                      double* __restrict__ val,
+                                                      float* __restrict__ val32,
+                                                      unsigned char* __restrict__ bits,
+                                                      int* __restrict__ err) {
+  __shared__ int sJ[UWARPS][UW];
+  __shared__ double sV[UWARPS][UW];
+  __shared__ unsigned char sB[UWARPS][UW];
+  __shared__ unsigned char sF[UWARPS][UW];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = blockIdx.x * UWARPS + w;
+  if (R >= nrc) return;
+  int* J = sJ[w];
+  double* V = sV[w];
+  unsigned char* B = sB[w];
+  unsigned char* first = sF[w];
+
+  const int I = crows[R];
+  const int p = find_part_cell(C.cellstart, C.np, I);
   const DPart& fp = F.parts[p];
   const DPart& cp = C.parts[p];
-  int cl = I - cp.off;
   int Ic[3];
   {
+    int cl = I - cp.off;
     unsigned q = fdiv((unsigned)cl, cp.dx);
     Ic[0] = cl - (int)q * cp.n[0];
     Ic[2] = (int)fdiv((unsigned)cl, cp.dxy);
     Ic[1] = (int)q - Ic[2] * cp.n[1];
   }
   const int d = fp.dstar;
+  int n = 0;
   for (int a = -1; a <= 1; ++a) {
     int f[3] = {Ic[0], Ic[1], Ic[2]};
     double w1 = 1.0;
@@ -273,76 +306,79 @@ __device__ int urow_build(const LevelView<double>& F, const LevelView<double>& C
         w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
       }
     }
-    int fg = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-    int r = F.u_map[fg];
-    if (r < 0) continue;
-    for (int q = F.u_ptr[r]; q < F.u_ptr[r + 1]; ++q) {
-      int gq, gi, gj, gk;
-      locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
-      int J[2];
-      double w2[2];
-      int m = p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, J, w2);
-      double v = w1 * F.u_val[q];
-      for (int t = 0; t < m; ++t) {
-        if (nc >= SSAMG_MAX_UCAND) return -1;
-        // insertion sort by column; equal columns stay in arrival order
-        int pos = nc;
-        while (pos > 0 && cand[pos - 1].J > J[t]) {
-          cand[pos] = cand[pos - 1];
-          --pos;
-        }
-        cand[pos].J = J[t];
-        cand[pos].v = v * w2[t];
-        cand[pos].bits = F.u_bits[q];
-        ++nc;
+    const int fg = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+    const int ur = F.u_map[fg];
+    if (ur < 0) continue;
+    const int q0 = F.u_ptr[ur], q1 = F.u_ptr[ur + 1];
+    for (int base = q0; base < q1; base += 32) {
+      const int q = base + lane;
+      int Jt[2] = {0, 0};
+      double w2[2] = {0.0, 0.0};
+      int m = 0;
+      if (q < q1) {
+        int gq, gi, gj, gk;
+        locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
+        m = p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, Jt, w2);
       }
+      int tot;
+      int pos = n + warp_excl_scan(m, lane, tot);
+      if (q < q1) {
+        double v = w1 * F.u_val[q];
+        unsigned char b = F.u_bits[q];
+        for (int t = 0; t < m; ++t)
+          if (pos + t < UW) {
+            J[pos + t] = Jt[t];
+            V[pos + t] = v * w2[t];
+            B[pos + t] = b;
+          }
+      }
+      n += tot;
     }
   }
-  int nu = 0;
-  int s = 0;
-  while (s < nc) {
-    int e = s;
+  if (n > UW) {
+    if (lane == 0) atomicOr(err, 1);
+    if (counts) counts[R] = 0;
+    return;
+  }
+  __syncwarp();
+  int nfirst = 0;
+  for (int t = lane; t < n; t += 32) {
+    const int jt = J[t];
+    bool f1 = true;
+    for (int u = 0; u < t; ++u)
+      if (J[u] == jt) {
+        f1 = false;
+        break;
+      }
+    first[t] = f1;
+    nfirst += f1;
+  }
+  for (int o = 16; o > 0; o >>= 1) nfirst += __shfl_xor_sync(0xffffffffu, nfirst, o);
+  if (counts) {
+    if (lane == 0) counts[R] = nfirst;
+    return;
+  }
+  __syncwarp();
+  const int o0 = ptr[R];
+  for (int t = lane; t < n; t += 32) {
+    if (!first[t]) continue;
+    const int jt = J[t];
+    int slot = 0;
     double v = 0.0;
     unsigned char b = 0;
-    while (e < nc && cand[e].J == cand[s].J) {
-      v += cand[e].v;
-      b |= cand[e].bits;
-      ++e;
+    for (int u = 0; u < n; ++u) {
+      const int ju = J[u];
+      if (first[u] && ju < jt) ++slot;
+      if (ju == jt) {
+        v += V[u];
+        b |= B[u];
+      }
     }
-    if (out_col) {
-      out_col[nu] = cand[s].J;
-      out_val[nu] = v;
-      if (out_val32) out_val32[nu] = (float)v;
-      out_bits[nu] = b;
-    }
-    ++nu;
-    s = e;
+    col[o0 + slot] = jt;
+    val[o0 + slot] = v;
+    if (val32) val32[o0 + slot] = (float)v;
+    bits[o0 + slot] = b;
   }
-  return nu;
-}
-
-__global__ void k_ucount(LevelView<double> F, LevelView<double> C, int nrc,
-                         const int* __restrict__ crows, int* __restrict__ counts,
-                         int* __restrict__ err) {
-  int R = blockIdx.x * blockDim.x + threadIdx.x;
-  if (R >= nrc) return;
-  int n = urow_build(F, C, R, crows, nullptr, nullptr, nullptr, nullptr);
-  if (n < 0) {
-    atomicOr(err, 1);
-    n = 0;
-  }
-  counts[R] = n;
-}
-
-__global__ void k_ufill(LevelView<double> F, LevelView<double> C, int nrc,
-                        const int* __restrict__ crows, const int* __restrict__ ptr,
-                        int* __restrict__ col, double* __restrict__ val, float* __restrict__ val32,
-                        unsigned char* __restrict__ bits, int* __restrict__ err) {
-  int R = blockIdx.x * blockDim.x + threadIdx.x;
-  if (R >= nrc) return;
-  int o = ptr[R];
-  int n = urow_build(F, C, R, crows, col + o, val + o, val32 ? val32 + o : nullptr, bits + o);
-  if (n < 0 || n != ptr[R + 1] - o) atomicOr(err, 2);
 }
 
 __global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ u_map) {
@@ -359,32 +395,32 @@ __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, dou
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  int c = (blockIdx.x - sp.blk0) * NT + threadIdx.x;
-  if (c >= sp.ncell) return;
-  int i, j, k;
-  cell_coords(sp, c, i, j, k);
-  double v;
-  if (relax == 0) {
-    double diag = 0.0;
-    for (int e = 0; e < sp.nent; ++e)
-      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += coef_at(sp, L.coef, e, c);
-    double w = factor > 0.0 ? factor : sp.omega;
-    v = w / diag;
-  } else {
-    double s = 0.0;
-    for (int e = 0; e < sp.nent; ++e)
-      if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2]))
-        s += fabs(coef_at(sp, L.coef, e, c));
-    if (sp.has_u) {
-      int r = L.u_map[sp.off + c];
-      if (r >= 0)
-        for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) s += fabs(L.u_val[q]);
+  TILE_LOOP(c, sp.blk0, sp.ncell) {
+    int i, j, k;
+    cell_coords(sp, c, i, j, k);
+    double v;
+    if (relax == 0) {
+      double diag = 0.0;
+      for (int e = 0; e < sp.nent; ++e)
+        if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += coef_at(sp, L.coef, e, c);
+      double w = factor > 0.0 ? factor : sp.omega;
+      v = w / diag;
+    } else {
+      double s = 0.0;
+      for (int e = 0; e < sp.nent; ++e)
+        if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2]))
+          s += fabs(coef_at(sp, L.coef, e, c));
+      if (sp.has_u) {
+        int r = L.u_map[sp.off + c];
+        if (r >= 0)
+          for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) s += fabs(L.u_val[q]);
+      }
+      double w = factor > 0.0 ? factor : 1.5;
+      v = w / s;
     }
-    double w = factor > 0.0 ? factor : 1.5;
-    v = w / s;
+    dinv[sp.off + c] = v;
+    if (dinv32) dinv32[sp.off + c] = (float)v;
   }
-  dinv[sp.off + c] = v;
-  if (dinv32) dinv32[sp.off + c] = (float)v;
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, long long n) {
@@ -559,16 +595,18 @@ void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStrea
 
 void launch_ucount(const Level& F, const Level& Cl, int* counts, int* err, cudaStream_t st) {
   if (Cl.nr == 0) return;
-  k_ucount<<<cdiv(Cl.nr, 128), 128, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
-                                             Cl.u_rows, counts, err);
+  k_urow<<<cdiv(Cl.nr, UWARPS), 32 * UWARPS, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
+                                                      Cl.u_rows, nullptr, counts, nullptr, nullptr,
+                                                      nullptr, nullptr, err);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStream_t st) {
   if (Cl.nr == 0) return;
-  k_ufill<<<cdiv(Cl.nr, 128), 128, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
-                                            Cl.u_rows, Cl.u_ptr, Cl.u_col, Cl.u_val,
-                                            fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, err);
+  k_urow<<<cdiv(Cl.nr, UWARPS), 32 * UWARPS, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
+                                                      Cl.u_rows, Cl.u_ptr, nullptr, Cl.u_col,
+                                                      Cl.u_val, fp32 ? Cl.u_val32 : nullptr,
+                                                      Cl.u_bits, err);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -23,7 +23,8 @@
 
 #define SSAMG_MAXE 27
 #define SSAMG_BLOCK 256
-#define SSAMG_MAX_UCAND 128
+#define SSAMG_CPT 4
+#define SSAMG_TILE (SSAMG_BLOCK * SSAMG_CPT)
 
 // ---------------------------------------------------------------------------
 // Division by a run-time constant (round-up multiply-high method of Granlund
@@ -60,6 +61,7 @@ __host__ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) 
 struct DPart {
   long long coef[SSAMG_MAXE];  // element offset of a variable entry, -1: constant
   double cval[SSAMG_MAXE];     // value of a constant entry
+  float cval32[SSAMG_MAXE];    // the same rounded to FP32 (converting in the loop would use the FP64 pipe)
   double omega;                // omega_p (Eq. relax1) at this level
   int n[3];                    // extents along x, y, z
   int ncell;
@@ -82,7 +84,7 @@ struct DPart {
   int disp[SSAMG_MAXE];        // linear displacement of each entry
   signed char o[SSAMG_MAXE][3];
   signed char slot[27];        // entry index of offset code (ox+1)+3(oy+1)+9(oz+1), -1 absent
-  signed char pad_[2];
+  signed char pad_[6];
 };
 static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 
