@@ -369,9 +369,15 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
   SSAMG_CUDA(cudaMalloc(&A->coef, sizeof(double) * std::max<long long>(n, 1)));
   for (int p = 0; p < np; ++p)
     for (int e = 0; e < A->nent; ++e)
-      if (A->isvar[p][e])
+      if (A->isvar[p][e]) {
         SSAMG_CUDA(cudaMemcpyAsync(A->coef + A->coef_off[p][e], A->tmpvar[p][e],
                                    sizeof(double) * g->ncell(p), cudaMemcpyDeviceToDevice, st));
+        // S has no connection that leaves the box: store exact zeros there
+        int ext[3] = {g->hi[p][0] - g->lo[p][0] + 1, g->hi[p][1] - g->lo[p][1] + 1,
+                      g->hi[p][2] - g->lo[p][2] + 1};
+        if (A->o[e][0] || A->o[e][1] || A->o[e][2])
+          launch_mask_outside(A->coef + A->coef_off[p][e], ext, A->o[e], st);
+      }
   // couplings: global (row, col), sorted, duplicates merged
   long long m = (long long)A->c_val.size();
   struct E {
@@ -540,6 +546,16 @@ void fill_dpart(DPart& dp, const PartH& h) {
     dp.cval32[e] = (float)h.cval[e];
     dp.slot[(h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1)] = (signed char)e;
   }
+  dp.allvar = 1;
+  dp.varmask = 0;
+  for (int e = 0; e < h.nent; ++e) {
+    if (h.var[e]) dp.varmask |= 1u << e;
+    if (!h.var[e] || h.coef_off[e] != h.coef_off[0] + (long long)e * h.ncell) dp.allvar = 0;
+  }
+  dp.zeroext = dp.allvar;
+  dp.canon27 = h.nent == 27;
+  for (int e = 0; e < h.nent && dp.canon27; ++e)
+    if ((h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1) != e) dp.canon27 = 0;
   for (int d = 0; d < 3; ++d) dp.nf[d] = h.nf[d];
   dp.nfine = (int)h.nfine;
   dp.poff = h.poff;
@@ -547,14 +563,27 @@ void fill_dpart(DPart& dp, const PartH& h) {
   dp.fdxy = make_fastdiv(std::max(1, h.nf[0] * h.nf[1]));
 }
 
+// A vector of n elements of w bytes with `guard` zeroed elements before and
+// after it (stencils on levels whose coefficients vanish outside the box read
+// up to one plane past either end without bounds tests).
+void* padded_vector(ssamg_solver s, size_t w, long long n, long long guard, cudaStream_t st) {
+  char* base = (char*)s->arena.alloc(w * (size_t)(n + 2 * guard));
+  SSAMG_CUDA(cudaMemsetAsync(base, 0, w * (size_t)(n + 2 * guard), st));
+  return base + w * guard;
+}
+
 void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) {
   const int np = L.np;
   L.dparts.assign(np, DPart{});
   std::vector<int> blk(np + 1, 0), fblk(np + 1, 0), cs(np + 1, 0);
+  long long ntot = 0;
+  for (int p = 0; p < np; ++p) ntot += L.parts[p].ncell;
+  L.cpt = ntot >= SSAMG_CPT_MIN_CELLS ? SSAMG_CPT_LARGE : 1;
+  const long long tile = (long long)L.cpt * SSAMG_BLOCK;
   for (int p = 0; p < np; ++p) {
     const PartH& h = L.parts[p];
-    blk[p + 1] = blk[p] + (int)cdivll(h.ncell, SSAMG_TILE);
-    fblk[p + 1] = fblk[p] + (int)cdivll(h.nfine, SSAMG_TILE);
+    blk[p + 1] = blk[p] + (int)cdivll(h.ncell, tile);
+    fblk[p + 1] = fblk[p] + (int)cdivll(h.nfine, tile);
     cs[p + 1] = cs[p] + (int)h.ncell;
   }
   L.nblk = blk[np];
@@ -564,6 +593,7 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     fill_dpart(dp, L.parts[p]);
     dp.blk0 = blk[p];
     dp.fblk0 = fblk[p];
+    dp.cpt = L.cpt;
     if (next) {
       const PartH& c = next->parts[p];
       dp.coff = c.off;
@@ -762,10 +792,12 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     L.dinv = aalloc<double>(s->arena, L.N);
     if (fp32) L.dinv32 = aalloc<float>(s->arena, L.N);
     size_t w = fp32 ? sizeof(float) : sizeof(double);
-    L.x = s->arena.alloc(w * L.N);
-    L.b = s->arena.alloc(w * L.N);
-    L.r = s->arena.alloc(w * L.N);
-    L.t = s->arena.alloc(w * L.N);
+    L.guard = 0;
+    for (auto& h : L.parts) L.guard = std::max<long long>(L.guard, 1 + h.n[0] + (long long)h.n[0] * h.n[1]);
+    L.x = padded_vector(s, w, L.N, L.guard, st);
+    L.b = padded_vector(s, w, L.N, L.guard, st);
+    L.r = padded_vector(s, w, L.N, L.guard, st);
+    L.t = padded_vector(s, w, L.N, L.guard, st);
     bool any_u = false;
     for (auto& h : L.parts) any_u |= h.has_u != 0;
     if (l > 0 && any_u) L.u_map = aalloc<int>(s->arena, L.N);
@@ -836,6 +868,25 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     }
   }
 
+  // ---- row-job data: dense U x buffers and P rows of coupling columns
+  for (int l = 0; l <= Lc; ++l) {
+    Level& L = s->lev[l];
+    L.nublk = (int)cdivll(L.nr, SSAMG_RPB);
+    if (L.nr == 0) continue;
+    L.uy64 = aalloc<double>(s->arena, L.N);
+    SSAMG_CUDA(cudaMemsetAsync(L.uy64, 0, sizeof(double) * L.N, st));
+    if (fp32) {
+      L.uy32 = aalloc<float>(s->arena, L.N);
+      SSAMG_CUDA(cudaMemsetAsync(L.uy32, 0, sizeof(float) * L.N, st));
+    }
+    if (l < Lc) {
+      L.u_pj = aalloc<int>(s->arena, 2 * L.nnz);
+      L.u_pw = aalloc<double>(s->arena, 2 * L.nnz);
+      if (fp32) L.u_pw32 = aalloc<float>(s->arena, 2 * L.nnz);
+      launch_upcols(L, fp32, st);
+    }
+  }
+
   // ---- Section 3.4: smoother diagonals
   for (int l = 0; l <= Lc; ++l) launch_dinv(s->lev[l], s->prm.relax, s->prm.relax_factor, fp32, st);
 
@@ -853,13 +904,14 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   if (s->h_int[0]) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "a coarse coupling row has more than 1024 candidates"};
   if (s->h_int[2]) throw SsamgError{SSAMG_ERR_BREAKDOWN, "coarsest operator is not positive definite"};
 
-  // ---- PCG work vectors
-  long long N = L0.N;
+  // ---- PCG work vectors (the ones the level-0 stencil reads carry guard cells)
+  long long N = s->lev[0].N;
+  long long L0g = s->lev[0].guard;
   s->b = aalloc<double>(s->arena, N);
-  s->x = aalloc<double>(s->arena, N);
+  s->x = (double*)padded_vector(s, sizeof(double), N, L0g, st);
   s->r = aalloc<double>(s->arena, N);
   s->z = aalloc<double>(s->arena, N);
-  s->p = aalloc<double>(s->arena, N);
+  s->p = (double*)padded_vector(s, sizeof(double), N, L0g, st);
   s->q = aalloc<double>(s->arena, N);
   s->zprev = aalloc<double>(s->arena, N);
   s->nblk_red = reduce_blocks(N);
@@ -894,22 +946,25 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
     if (is_f) launch_cast_f2d((const float*)out, z_out, Ls[0].N, st);
     return;
   }
+  // down: pre-relax from zero (with U x for the residual), residual, restrict
   const T* b = b0;
   for (int l = 0; l < Lc; ++l) {
     T* x = (T*)Ls[l].x;
     T* r = (T*)Ls[l].r;
-    launch_relax0<T>(Ls[l], b, x, st);
+    launch_relax0_u<T>(Ls[l], b, x, st);
     launch_residual<T>(Ls[l], x, b, r, st);
     launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b, st);
     b = (const T*)Ls[l + 1].b;
   }
   coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);
+  // up: x + P e into the (now free) residual buffer with U x, post-relax
   const T* e = (const T*)Ls[Lc].x;
   for (int l = Lc - 1; l >= 0; --l) {
-    launch_prolong<T>(Ls[l], Ls[l + 1], e, (T*)Ls[l].x, st);
+    T* xc = (T*)Ls[l].r;
+    launch_prolong_u<T>(Ls[l], e, (const T*)Ls[l].x, xc, st);
     T* out = (l == 0 && !is_f) ? (T*)z_out : (T*)Ls[l].t;
     const T* bl = l == 0 ? b0 : (const T*)Ls[l].b;
-    launch_relax<T>(Ls[l], (const T*)Ls[l].x, bl, out, st);
+    launch_relax<T>(Ls[l], xc, bl, out, st);
     e = out;
   }
   if (is_f) launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);

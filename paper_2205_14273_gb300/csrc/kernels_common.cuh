@@ -3,13 +3,19 @@
 
 #include "ssamg_internal.cuh"
 
-// Cell-wise launches give each block a tile of SSAMG_TILE consecutive cells of
-// one part; thread t handles cells t, t + SSAMG_BLOCK, ... (coalesced), so
-// per-block work (descriptor staging, reductions) is amortised over
-// SSAMG_CPT cells per thread.
-#define TILE_LOOP(c, first, count)                                                         \
-  for (int c##_m = 0, c = ((int)blockIdx.x - (first)) * SSAMG_TILE + (int)threadIdx.x;     \
-       c##_m < SSAMG_CPT && c < (count); ++c##_m, c += SSAMG_BLOCK)
+// Cell-wise launches give each block a tile of P.cpt x SSAMG_BLOCK
+// consecutive cells of one part; thread t handles cells t, t + SSAMG_BLOCK,
+// ... (coalesced).  Large levels use several cells per thread to amortise
+// descriptor staging and FP64 reduction trees; small levels use one, for
+// more warps to hide latency.
+#define TILE_LOOP(c, P)                                                                    \
+  _Pragma("unroll 1") for (int c##_m = 0,                                                  \
+       c = ((int)blockIdx.x - (P).blk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;        \
+       c##_m < (P).cpt && c < (P).ncell; ++c##_m, c += SSAMG_BLOCK)
+#define TILE_LOOP_FINE(c, P)                                                               \
+  _Pragma("unroll 1") for (int c##_m = 0,                                                  \
+       c = ((int)blockIdx.x - (P).fblk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;       \
+       c##_m < (P).cpt && c < (P).nfine; ++c##_m, c += SSAMG_BLOCK)
 
 // Part owning block b of a launch whose per-part block starts are blk[0..np].
 __device__ __forceinline__ int find_part(const int* __restrict__ blk, int np, int b) {
@@ -57,21 +63,114 @@ __device__ __forceinline__ float coef_at(const DPart& p, const float* __restrict
   return o >= 0 ? coef[o + c] : p.cval32[e];
 }
 
-// (S x)(c) for local cell c = (i, j, k) of part p; x points at the level vector.
+// (S x)(c) for local cell c = (i, j, k) of part p; x points at the level
+// vector.  The entry count is uniform over a block, so the dispatch below does
+// not diverge.  Fully unrolled variants (7, 15 and 27 entries) issue all loads
+// of a cell together.  Parts whose entries are all per cell (every coarse
+// level) address entry e as a[e * ncell]; the full 27-point stencil in
+// offset-code order derives offsets and bounds from e at compile time.
+template <class T>
+__device__ __forceinline__ T const_of(const DPart& p, int e);
+template <>
+__device__ __forceinline__ double const_of<double>(const DPart& p, int e) { return p.cval[e]; }
+template <>
+__device__ __forceinline__ float const_of<float>(const DPart& p, int e) { return p.cval32[e]; }
+
+template <class T>
+__device__ __forceinline__ T stencil27_canon(const DPart& p, const T* __restrict__ a,
+                                             const T* __restrict__ xc, int i, int j, int k,
+                                             bool interior) {
+  const int nx = p.n[0], nxy = p.n[0] * p.n[1], s = p.ncell;
+  const bool xm = i > 0, xp = i < p.n[0] - 1, ym = j > 0, yp = j < p.n[1] - 1, zm = k > 0,
+             zp = k < p.n[2] - 1;
+  T acc = (T)0;
+#pragma unroll
+  for (int e = 0; e < 27; ++e) {
+    const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+    const bool ok = interior || ((dx == 0 || (dx < 0 ? xm : xp)) && (dy == 0 || (dy < 0 ? ym : yp)) &&
+                                 (dz == 0 || (dz < 0 ? zm : zp)));
+    if (ok) acc = fma(a[e * s], xc[dx + dy * nx + dz * nxy], acc);
+  }
+  return acc;
+}
+
+template <int K, class T>
+__device__ __forceinline__ T stencil_fixed(const DPart& p, const T* __restrict__ coef,
+                                           const T* __restrict__ xc, int c, int i, int j, int k,
+                                           bool interior) {
+  T acc = (T)0;
+  if (p.allvar) {
+    const T* a = coef + p.coef[0] + c;
+    const int s = p.ncell;
+#pragma unroll
+    for (int e = 0; e < K; ++e)
+      if (interior || inside(p, i + p.o[e][0], j + p.o[e][1], k + p.o[e][2]))
+        acc = fma(a[e * s], xc[p.disp[e]], acc);
+  } else {
+    const unsigned vm = p.varmask;
+#pragma unroll
+    for (int e = 0; e < K; ++e)
+      if (interior || inside(p, i + p.o[e][0], j + p.o[e][1], k + p.o[e][2])) {
+        const T ae = ((vm >> e) & 1u) ? coef[p.coef[e] + c] : const_of<T>(p, e);
+        acc = fma(ae, xc[p.disp[e]], acc);
+      }
+  }
+  return acc;
+}
+
+// Unchecked form: every entry per cell and zero where it leaves the box, and x
+// readable (finite) one plane beyond each end of the level vector, so every
+// cell takes the same path with no bounds tests.
+template <int K, class T>
+__device__ __forceinline__ T stencil_unchecked(const DPart& p, const T* __restrict__ a,
+                                               const T* __restrict__ xc) {
+  const int s = p.ncell;
+  T acc = (T)0;
+#pragma unroll
+  for (int e = 0; e < K; ++e) acc = fma(a[e * s], xc[p.disp[e]], acc);
+  return acc;
+}
+
+template <class T>
+__device__ __forceinline__ T stencil27_unchecked(const DPart& p, const T* __restrict__ a,
+                                                 const T* __restrict__ xc) {
+  const int nx = p.n[0], nxy = p.n[0] * p.n[1], s = p.ncell;
+  T acc = (T)0;
+#pragma unroll
+  for (int e = 0; e < 27; ++e) {
+    const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+    acc = fma(a[e * s], xc[dx + dy * nx + dz * nxy], acc);
+  }
+  return acc;
+}
+
 template <class T>
 __device__ __forceinline__ T stencil_apply(const DPart& p, const T* __restrict__ coef,
                                            const T* __restrict__ x, int c, int i, int j, int k,
-                                           bool interior) {
+                                           bool interior, bool padded) {
   const T* xc = x + p.off + c;
-  T acc = (T)0;
-  if (interior) {
-    for (int e = 0; e < p.nent; ++e) acc = fma(coef_at(p, coef, e, c), xc[p.disp[e]], acc);
-  } else {
-    for (int e = 0; e < p.nent; ++e) {
-      if (inside(p, i + p.o[e][0], j + p.o[e][1], k + p.o[e][2]))
-        acc = fma(coef_at(p, coef, e, c), xc[p.disp[e]], acc);
+  if (p.allvar && p.zeroext && padded) {
+    const T* a = coef + p.coef[0] + c;
+    if (p.canon27) return stencil27_unchecked(p, a, xc);
+    switch (p.nent) {
+      case 7: return stencil_unchecked<7>(p, a, xc);
+      case 15: return stencil_unchecked<15>(p, a, xc);
+      case 27: return stencil_unchecked<27>(p, a, xc);
+      default: break;
     }
   }
+  if (p.canon27 && p.allvar) return stencil27_canon(p, coef + p.coef[0] + c, xc, i, j, k, interior);
+  switch (p.nent) {
+    case 7: return stencil_fixed<7>(p, coef, xc, c, i, j, k, interior);
+    case 15: return stencil_fixed<15>(p, coef, xc, c, i, j, k, interior);
+    case 27: return stencil_fixed<27>(p, coef, xc, c, i, j, k, interior);
+    default: break;
+  }
+  T acc = (T)0;
+#pragma unroll 4
+  for (int e = 0; e < p.nent; ++e)
+    if (interior || inside(p, i + p.o[e][0], j + p.o[e][1], k + p.o[e][2]))
+      acc = fma(coef_at(p, coef, e, c), xc[p.disp[e]], acc);
   return acc;
 }
 
@@ -91,14 +190,31 @@ __device__ __forceinline__ bool is_interior(const DPart& p, int i, int j, int k)
   return i > 0 && i < p.n[0] - 1 && j > 0 && j < p.n[1] - 1 && k > 0 && k < p.n[2] - 1;
 }
 
-// (A x)(c) = (S x + U x)(c).
+// (A x)(c) = (S x)(c) + (U x)(c); the U part comes from L.uy, which a row
+// job filled for this same x (only face cells can have couplings).
 template <class T>
 __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, const T* __restrict__ x,
-                                     int c, int i, int j, int k) {
+                                     int c, int i, int j, int k, bool padded = true) {
   bool interior = is_interior(p, i, j, k);
-  T acc = stencil_apply(p, L.coef, x, c, i, j, k, interior);
-  if (p.has_u && !interior) acc += u_apply(L, x, p.off + c);
+  T acc = stencil_apply(p, L.coef, x, c, i, j, k, interior, padded);
+  if (p.has_u && !interior) acc += L.uy[p.off + c];
   return acc;
+}
+
+// Row job: SSAMG_TPR threads per U row r = blockIdx-relative row; returns
+// sum_q u_q * f(col_q, q) on the quad's lane 0 (all lanes must call).
+template <class T, class F>
+__device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, F&& f) {
+  const int r = rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR;
+  const int l4 = threadIdx.x % SSAMG_TPR;
+  T acc = (T)0;
+  if (r < L.nr) {
+    const int q1 = L.u_ptr[r + 1];
+    for (int q = L.u_ptr[r] + l4; q < q1; q += SSAMG_TPR) acc = fma(L.u_val[q], f(L.u_col[q], q), acc);
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (r < L.nr && l4 == 0) L.uy[L.u_rows[r]] = acc;
 }
 
 // Block-wide sum (deterministic: fixed shuffle tree, then fixed warp order).

@@ -17,15 +17,33 @@ __global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict_
   if (g < N) x[g] = dinv[g] * b[g];
 }
 
+// x = omega M^-1 b on blocks [0, nb); row jobs uy = U x on the rest.
+template <class T>
+__global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T* __restrict__ b,
+                                                 T* __restrict__ x) {
+  if ((int)blockIdx.x < nb) {
+    int g = blockIdx.x * NT + threadIdx.x;
+    if (g < L.N) x[g] = L.dinv[g] * b[g];
+    return;
+  }
+  u_row_job(L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col] * b[col]; });
+}
+
+// uy = U x (row jobs only)
+template <class T>
+__global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__ x) {
+  u_row_job(L, blockIdx.x, [&](int col, int) { return x[col]; });
+}
+
 // r = b - A x
 template <class T>
-__global__ void __launch_bounds__(NT) k_residual(LevelView<T> L, const T* __restrict__ x,
+__global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __restrict__ x,
                                                  const T* __restrict__ b, T* __restrict__ r) {
   __shared__ DPart sp;
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
@@ -35,13 +53,13 @@ __global__ void __launch_bounds__(NT) k_residual(LevelView<T> L, const T* __rest
 
 // xo = x + omega M^-1 (b - A x)
 template <class T>
-__global__ void __launch_bounds__(NT) k_relax(LevelView<T> L, const T* __restrict__ x,
+__global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ xo) {
   __shared__ DPart sp;
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
@@ -60,7 +78,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   stage_part(fp, F.parts + p);
   stage_part(cp, C.parts + p);
   __syncthreads();
-  TILE_LOOP(cc, cp.blk0, cp.ncell) {
+  TILE_LOOP(cc, cp) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
     const int d = fp.dstar;
@@ -87,6 +105,39 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   }
 }
 
+// xout = xin + P ec on the cell tiles; row jobs uy = U xout, where xout at a
+// coupling's column is rebuilt from xin and the column's P row (precomputed
+// at setup), so the two roles need no ordering.
+template <class T>
+__global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
+                                                  const T* __restrict__ xin, T* __restrict__ xout) {
+  __shared__ DPart fp;
+  const int nb = __ldg(F.blk + F.np);
+  if ((int)blockIdx.x >= nb) {
+    u_row_job(F, blockIdx.x - nb, [&](int col, int q) {
+      T v = xin[col];
+      int j0 = F.u_pj[2 * q], j1 = F.u_pj[2 * q + 1];
+      if (j0 >= 0) v = fma(F.u_pw[2 * q], ec[j0], v);
+      if (j1 >= 0) v = fma(F.u_pw[2 * q + 1], ec[j1], v);
+      return v;
+    });
+    return;
+  }
+  int p = find_part(F.blk, F.np, blockIdx.x);
+  stage_part(fp, F.parts + p);
+  __syncthreads();
+  TILE_LOOP(c, fp) {
+    int i, j, k;
+    cell_coords(fp, c, i, j, k);
+    int J[2];
+    T w[2];
+    int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+    T v = xin[fp.off + c];
+    for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
+    xout[fp.off + c] = v;
+  }
+}
+
 // x += P ec, one fine cell per thread.
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
@@ -95,7 +146,7 @@ __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restr
   int p = find_part(F.blk, F.np, blockIdx.x);
   stage_part(fp, F.parts + p);
   __syncthreads();
-  TILE_LOOP(c, fp.blk0, fp.ncell) {
+  TILE_LOOP(c, fp) {
     int i, j, k;
     cell_coords(fp, c, i, j, k);
     int J[2];
@@ -150,16 +201,16 @@ __global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ ou
   if (g < n) out[g] = (double)in[g];
 }
 
-__global__ void __launch_bounds__(NT) k_matvec(LevelView<double> L, const double* __restrict__ x,
-                                               double* __restrict__ y) {
+__global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* __restrict__ x,
+                                               double* __restrict__ y, int padded) {
   __shared__ DPart sp;
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
-    y[sp.off + c] = apply_A(L, sp, x, c, i, j, k);
+    y[sp.off + c] = apply_A(L, sp, x, c, i, j, k, padded != 0);
   }
 }
 
@@ -180,7 +231,7 @@ __device__ __forceinline__ void finish_sums(const double* __restrict__ partial, 
 }
 
 // r = b - A x; partial sums of (b.b, r.r)
-__global__ void __launch_bounds__(NT) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
+__global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
                                                  const double* __restrict__ x, double* __restrict__ r,
                                                  double* __restrict__ partial) {
   __shared__ DPart sp;
@@ -189,7 +240,7 @@ __global__ void __launch_bounds__(NT) k_pcg_init(LevelView<double> L, const doub
   stage_part(sp, L.parts + p);
   __syncthreads();
   double bb = 0.0, rr = 0.0;
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
@@ -304,7 +355,7 @@ __global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p,
 }
 
 // q = A p; partial p.q
-__global__ void __launch_bounds__(NT) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
+__global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
                                                      double* __restrict__ q,
                                                      double* __restrict__ partial) {
   __shared__ DPart sp;
@@ -313,7 +364,7 @@ __global__ void __launch_bounds__(NT) k_pcg_spmv_dot(LevelView<double> L, const 
   stage_part(sp, L.parts + pt);
   __syncthreads();
   double s = 0.0;
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
@@ -400,7 +451,7 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
@@ -456,6 +507,23 @@ void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
+void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
+  int nb = cdiv(L.N, NT);
+  k_relax0_u<T><<<nb + L.nublk, NT, 0, st>>>(L.view<T>(), nb, b, x);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
+  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_uy(const Level& L, const T* x, cudaStream_t st) {
+  if (L.nublk == 0) return;
+  k_uy<T><<<L.nublk, NT, 0, st>>>(L.view<T>(), x);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
   k_residual<T><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r);
   SSAMG_LAUNCH_CHECK();
@@ -486,6 +554,9 @@ void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream
 
 #define INST(T)                                                                            \
   template void launch_relax0<T>(const Level&, const T*, T*, cudaStream_t);                \
+  template void launch_relax0_u<T>(const Level&, const T*, T*, cudaStream_t);              \
+  template void launch_prolong_u<T>(const Level&, const T*, const T*, T*, cudaStream_t);   \
+  template void launch_uy<T>(const Level&, const T*, cudaStream_t);                        \
   template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
   template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \
   template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t); \
@@ -504,7 +575,8 @@ void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st)
   SSAMG_LAUNCH_CHECK();
 }
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) {
-  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y);
+  launch_uy<double>(L, x, st);
+  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -515,6 +587,7 @@ int reduce_blocks(long long n) {
 
 void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
                      PcgScalars* sc, cudaStream_t st) {
+  launch_uy<double>(L, x, st);
   k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
   SSAMG_LAUNCH_CHECK();
   k_pcg_init_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
@@ -541,6 +614,7 @@ void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p,
 
 void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
                       PcgScalars* sc, cudaStream_t st) {
+  launch_uy<double>(L, p, st);
   k_pcg_spmv_dot<<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial);
   SSAMG_LAUNCH_CHECK();
   k_pcg_alpha_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
@@ -558,6 +632,7 @@ void launch_pcg_update(const double* p, const double* q, double* x, double* r, l
 
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
                           double* partial, double* out, cudaStream_t st) {
+  launch_uy<double>(L, x, st);
   k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
   SSAMG_LAUNCH_CHECK();
   k_true_res_fin<<<1, NT, 0, st>>>(partial, L.nblk, out);

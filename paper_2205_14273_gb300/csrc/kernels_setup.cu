@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __rest
   stage_part(sp, L.parts + p);
   __syncthreads();
   double s0 = 0, s1 = 0, s2 = 0;
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     double sg = 1.0;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
   int p = find_part(L.fblk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(F, sp.fblk0, sp.nfine) {
+  TILE_LOOP_FINE(F, sp) {
     const int d = sp.dstar;
     int fc[3];
     {
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelVie
   stage_part(fp, F.parts + p);
   stage_part(cp, C.parts + p);
   __syncthreads();
-  TILE_LOOP(cc, cp.blk0, cp.ncell) {
+  TILE_LOOP(cc, cp) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
     double acc[27];
@@ -381,6 +381,24 @@ __global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, Level
   }
 }
 
+// For every coupling q of level l: the coarse columns and weights of P's row
+// of its column cell (used by the prolongation's row jobs).
+__global__ void k_upcols(LevelView<double> F, long long nnz, int* __restrict__ pj,
+                         double* __restrict__ pw, float* __restrict__ pw32) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  int gq, gi, gj, gk;
+  locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
+  int J[2] = {-1, -1};
+  double w[2] = {0.0, 0.0};
+  p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, J, w);
+  for (int t = 0; t < 2; ++t) {
+    pj[2 * q + t] = J[t];
+    pw[2 * q + t] = w[t];
+    if (pw32) pw32[2 * q + t] = (float)w[t];
+  }
+}
+
 __global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ u_map) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < nr) u_map[rows[r]] = r;
@@ -395,7 +413,7 @@ __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, dou
   int p = find_part(L.blk, L.np, blockIdx.x);
   stage_part(sp, L.parts + p);
   __syncthreads();
-  TILE_LOOP(c, sp.blk0, sp.ncell) {
+  TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     double v;
@@ -420,6 +438,18 @@ __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, dou
     }
     dinv[sp.off + c] = v;
     if (dinv32) dinv32[sp.off + c] = (float)v;
+  }
+}
+
+__global__ void k_mask_outside(double* __restrict__ v, int nx, int ny, int nz, int ox, int oy,
+                               int oz) {
+  long long n = (long long)nx * ny * nz;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    if ((unsigned)(i + ox) >= (unsigned)nx || (unsigned)(j + oy) >= (unsigned)ny ||
+        (unsigned)(k + oz) >= (unsigned)nz)
+      v[c] = 0.0;
   }
 }
 
@@ -610,6 +640,13 @@ void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStre
   SSAMG_LAUNCH_CHECK();
 }
 
+void launch_upcols(const Level& F, bool fp32, cudaStream_t st) {
+  if (F.nnz == 0) return;
+  k_upcols<<<cdiv(F.nnz, NT), NT, 0, st>>>(F.view<double>(), F.nnz, F.u_pj, F.u_pw,
+                                           fp32 ? F.u_pw32 : nullptr);
+  SSAMG_LAUNCH_CHECK();
+}
+
 void launch_umap_level0(const Level& L, cudaStream_t st) {
   SSAMG_CUDA(cudaMemsetAsync(L.u_map, 0xff, sizeof(int) * L.N, st));
   if (L.nr > 0) {
@@ -627,6 +664,13 @@ void launch_to_float(const double* in, float* out, long long n, cudaStream_t st)
   if (n <= 0) return;
   int nb = (int)std::min<long long>(cdiv(n, NT), 152 * 16);
   k_to_float<<<nb, NT, 0, st>>>(in, out, n);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_mask_outside(double* vals, const int n[3], const int o[3], cudaStream_t st) {
+  long long cnt = (long long)n[0] * n[1] * n[2];
+  int nb = (int)std::min<long long>(cdiv(cnt, NT), 152 * 8);
+  k_mask_outside<<<nb, NT, 0, st>>>(vals, n[0], n[1], n[2], o[0], o[1], o[2]);
   SSAMG_LAUNCH_CHECK();
 }
 

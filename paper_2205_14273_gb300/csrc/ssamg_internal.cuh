@@ -23,8 +23,10 @@
 
 #define SSAMG_MAXE 27
 #define SSAMG_BLOCK 256
-#define SSAMG_CPT 4
-#define SSAMG_TILE (SSAMG_BLOCK * SSAMG_CPT)
+#define SSAMG_CPT_LARGE 4         // cells per thread on large levels
+#define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
+#define SSAMG_TPR 4                          // threads per U row in row jobs
+#define SSAMG_RPB (SSAMG_BLOCK / SSAMG_TPR)  // U rows per block
 
 // ---------------------------------------------------------------------------
 // Division by a run-time constant (round-up multiply-high method of Granlund
@@ -78,13 +80,18 @@ struct DPart {
   int nf[3];                   // extents of the fine-point grid
   int nfine;
   int fblk0;                   // first block of launches over fine points
+  int cpt;                     // cells per thread of this level's tiles (tile = cpt x block)
+  int allvar;                  // every entry per cell, entry e at coef[coef[0] + e * ncell + c]
+  int canon27;                 // 27 entries in offset-code order (entry e has code e)
+  unsigned varmask;            // bit e: entry e is per cell
+  int zeroext;                 // per-cell entries are exactly zero where c + o leaves the box
   FastDiv dx, dxy;             // divide by n[0], n[0]*n[1]
   FastDiv cdx, cdxy;           // same on the next level
   FastDiv fdx, fdxy;           // same on the fine-point grid
   int disp[SSAMG_MAXE];        // linear displacement of each entry
   signed char o[SSAMG_MAXE][3];
   signed char slot[27];        // entry index of offset code (ox+1)+3(oy+1)+9(oz+1), -1 absent
-  signed char pad_[6];
+  signed char pad_[2];
 };
 static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 
@@ -112,6 +119,12 @@ struct LevelView {
   const int* u_col;
   const T* u_val;
   const unsigned char* u_bits;
+  const int* u_rows;
+  const int* u_pj;      // per coupling: the (<= 2) coarse columns of P's row of its column cell
+  const T* u_pw;        // and their weights (-1 column: absent)
+  T* uy;                // dense per-cell (U x)(c) of the vector last passed to a row job; 0 off rows
+  int nr;
+  int nublk;            // blocks of row jobs (SSAMG_RPB rows each)
 };
 
 // ---------------------------------------------------------------------------
@@ -145,6 +158,7 @@ struct Arena {
 
 struct Level {
   int np = 0;
+  long long guard = 0;  // zeroed cells before and after every internal level vector
   long long N = 0;
   std::vector<PartH> parts;
   std::vector<DPart> dparts;
@@ -153,6 +167,7 @@ struct Level {
   int* d_fblk = nullptr;
   int* d_cellstart = nullptr;
   int nblk = 0, nfblk = 0;
+  int cpt = 1;
   double* coef = nullptr;
   float* coef32 = nullptr;
   long long ncoef = 0;
@@ -172,6 +187,12 @@ struct Level {
   double* u_val = nullptr;
   float* u_val32 = nullptr;
   unsigned char* u_bits = nullptr;
+  int* u_pj = nullptr;
+  double* u_pw = nullptr;
+  float* u_pw32 = nullptr;
+  double* uy64 = nullptr;
+  float* uy32 = nullptr;
+  int nublk = 0;
   // cycle work vectors (precision of the cycle)
   void* x = nullptr;
   void* b = nullptr;
@@ -185,12 +206,13 @@ struct Level {
 template <>
 inline LevelView<double> Level::view<double>() const {
   return LevelView<double>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
-                           u_map, u_ptr, u_col, u_val, u_bits};
+                           u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
   return LevelView<float>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
-                          Pe32, u_map, u_ptr, u_col, u_val32, u_bits};
+                          Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, uy32,
+                          nr, nublk};
 }
 
 struct SsamgError {
@@ -221,6 +243,8 @@ void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStre
 void launch_umap_level0(const Level& L, cudaStream_t st);
 void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
+// zero the values of a per-cell entry with offset o where c + o leaves the box
+void launch_mask_outside(double* vals, const int n[3], const int o[3], cudaStream_t st);
 void launch_coarse_assemble(const Level& L, double* A, cudaStream_t st);
 void launch_cholesky(int n, double* A, int* status, cudaStream_t st);
 // exclusive scan of n ints in place; returns nothing (total at out[n])
@@ -230,6 +254,16 @@ size_t scan_tmp_ints(long long n);
 // cycle (T = float or double)
 template <class T>
 void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st);
+// x = omega M^-1 b and, in the same launch, uy = U x (row jobs)
+template <class T>
+void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st);
+// xout = xin + P ec and uy = U xout (row jobs)
+template <class T>
+void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st);
+// uy = U x
+template <class T>
+void launch_uy(const Level& L, const T* x, cudaStream_t st);
+void launch_upcols(const Level& F, bool fp32, cudaStream_t st);
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
 template <class T>
@@ -242,6 +276,7 @@ template <class T>
 void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st);
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st);
 void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st);
+// y = A_l x; x may be a caller vector without guard cells
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st);
 
 // PCG (FP64)
