@@ -108,7 +108,9 @@ typedef struct {
   int max_iter;        /* PCG iteration limit (default 200) */
   int coarse_direct;   /* 1: dense Cholesky on the coarsest level; 0: one relaxation sweep (Section 3.5) */
   int flexible;        /* 1: Polak-Ribiere beta (for the FP32 cycle); 0: Fletcher-Reeves */
-  int use_graph;       /* 1: replay the cycle as a CUDA graph */
+  int use_graph;       /* 1: run the PCG iteration loop as one CUDA graph */
+  int use_tail;        /* 1: run the levels of at most 8192 cells (<= 8 parts) in one single-block
+                          launch (default 0: one launch per level and step is faster on GB300) */
 } ssamg_params;
 
 typedef struct {

@@ -124,6 +124,11 @@ struct ssamg_solver_s {
   // coarsest
   int nL = 0;
   double* chol = nullptr;
+  double* cinv = nullptr;      // explicit inverse of the coarsest operator (for the fused tail)
+  int tail_lt = -1;            // first level of the fused coarse tail (-1: none)
+  void* tail_dev = nullptr;    // TailLevel<T> array for levels tail_lt..Lc
+  int tail_blocks = 0;
+  TailBarrier* tail_bar = nullptr;
   // PCG work (FP64, level 0 size)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
          *zprev = nullptr, *partial = nullptr, *tres = nullptr;
@@ -479,6 +484,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->coarse_direct = 1;
   p->flexible = 0;
   p->use_graph = 1;
+  p->use_tail = 0;
 }
 
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
@@ -608,6 +614,34 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     L.d_blk = aalloc<int>(s->arena, np + 1);
     L.d_fblk = aalloc<int>(s->arena, np + 1);
     L.d_cellstart = aalloc<int>(s->arena, np + 1);
+  }
+  {
+    // operator-apply shape shared by all parts (see StencilShape)
+    bool unchecked = true, all27 = true, all7 = true, all15 = true, canon7 = true;
+    static const int c7[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
+                                 {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (const DPart& dp : L.dparts) {
+      unchecked = unchecked && dp.allvar && dp.zeroext;
+      all27 = all27 && dp.canon27;
+      all7 = all7 && dp.nent == 7;
+      all15 = all15 && dp.nent == 15;
+      if (dp.nent != 7) canon7 = false;
+      for (int e = 0; e < 7 && canon7; ++e)
+        for (int d = 0; d < 3; ++d)
+          if (dp.o[e][d] != c7[e][d]) canon7 = false;
+    }
+    L.shape = !unchecked ? (canon7 ? 5 : 0) : all27 ? 3 : all7 ? 1 : all15 ? 2 : 4;
+  }
+  L.pp = std::make_shared<PartsParam>();
+  std::memset(L.pp.get(), 0, sizeof(PartsParam));
+  L.pp->np = np;
+  L.pp->inparam = np <= SSAMG_PARAM_PARTS;
+  if (L.pp->inparam) {
+    for (int p = 0; p <= np; ++p) {
+      L.pp->blk[p] = blk[p];
+      L.pp->fblk[p] = fblk[p];
+    }
+    for (int p = 0; p < np; ++p) L.pp->part[p] = L.dparts[p];
   }
   SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
@@ -898,6 +932,48 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     s->chol = aalloc<double>(s->arena, LL.N * LL.N);
     launch_coarse_assemble(LL, s->chol, st);
     launch_cholesky((int)LL.N, s->chol, s->d_err + 2, st);
+    if (LL.N <= 1024) {
+      s->cinv = aalloc<double>(s->arena, LL.N * LL.N);
+      launch_coarse_inverse((int)LL.N, s->chol, s->cinv, st);
+    }
+  }
+  // ---- fused coarse tail: the trailing levels that fit one block
+  s->tail_lt = -1;
+  s->tail_dev = nullptr;
+  if (s->prm.use_tail && (!s->prm.coarse_direct || s->cinv)) {
+    int lt = Lc;
+    while (lt - 1 >= 0 && s->lev[lt - 1].N <= SSAMG_TAIL_MAX_CELLS &&
+           s->lev[lt - 1].np <= SSAMG_TAIL_MAX_PARTS)
+      --lt;
+    const int maxb = tail_max_blocks();
+    if (lt < Lc && s->lev[lt].np <= SSAMG_TAIL_MAX_PARTS && maxb >= 1) {
+      s->tail_lt = lt;
+      s->tail_blocks = (int)std::min<long long>(
+          std::min<long long>(SSAMG_TAIL_MAX_BLOCKS, maxb),
+          std::max<long long>(1, cdivll(s->lev[lt].N, SSAMG_TAIL_BLOCK)));
+      s->tail_bar = aalloc<TailBarrier>(s->arena, 1);
+      SSAMG_CUDA(cudaMemsetAsync(s->tail_bar, 0, sizeof(TailBarrier), st));
+      const int nt = Lc - lt + 1;
+      if (fp32) {
+        std::vector<TailLevel<float>> tl(nt);
+        for (int l = lt; l <= Lc; ++l)
+          tl[l - lt] = TailLevel<float>{s->lev[l].view<float>(), (float*)s->lev[l].x,
+                                        (float*)s->lev[l].b, (float*)s->lev[l].r,
+                                        (float*)s->lev[l].t};
+        s->tail_dev = s->arena.alloc(sizeof(TailLevel<float>) * nt);
+        SSAMG_CUDA(cudaMemcpyAsync(s->tail_dev, tl.data(), sizeof(TailLevel<float>) * nt,
+                                   cudaMemcpyHostToDevice, st));
+      } else {
+        std::vector<TailLevel<double>> tl(nt);
+        for (int l = lt; l <= Lc; ++l)
+          tl[l - lt] = TailLevel<double>{s->lev[l].view<double>(), (double*)s->lev[l].x,
+                                         (double*)s->lev[l].b, (double*)s->lev[l].r,
+                                         (double*)s->lev[l].t};
+        s->tail_dev = s->arena.alloc(sizeof(TailLevel<double>) * nt);
+        SSAMG_CUDA(cudaMemcpyAsync(s->tail_dev, tl.data(), sizeof(TailLevel<double>) * nt,
+                                   cudaMemcpyHostToDevice, st));
+      }
+    }
   }
   SSAMG_CUDA(cudaMemcpyAsync(s->h_int, s->d_err, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -935,7 +1011,9 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
     b0 = (const T*)r_in;
   }
   auto coarse = [&](const T* bl, T* xl) {
-    if (s->prm.coarse_direct)
+    if (s->prm.coarse_direct && s->cinv)
+      launch_coarse_apply<T>(s->nL, s->cinv, bl, xl, st);
+    else if (s->prm.coarse_direct)
       launch_coarse_solve<T>(s->nL, s->chol, bl, xl, st);
     else
       launch_relax0<T>(Ls[Lc], bl, xl, st);
@@ -946,9 +1024,23 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
     if (is_f) launch_cast_f2d((const float*)out, z_out, Ls[0].N, st);
     return;
   }
+  // levels from tail_lt on run in one fused single-block launch
+  const int lt = s->tail_lt >= 0 ? s->tail_lt : Lc;
+  if (lt == 0) {
+    // the whole cycle fits the tail: it reads b and writes t of level 0
+    if (!is_f)
+      SSAMG_CUDA(cudaMemcpyAsync(Ls[0].b, r_in, sizeof(double) * Ls[0].N, cudaMemcpyDeviceToDevice, st));
+    launch_vtail<T>((const TailLevel<T>*)s->tail_dev, Lc + 1, s->cinv, s->nL, s->prm.coarse_direct,
+                    s->tail_blocks, s->tail_bar, st);
+    if (is_f)
+      launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);
+    else
+      SSAMG_CUDA(cudaMemcpyAsync(z_out, Ls[0].t, sizeof(double) * Ls[0].N, cudaMemcpyDeviceToDevice, st));
+    return;
+  }
   // down: pre-relax from zero (with U x for the residual), residual, restrict
   const T* b = b0;
-  for (int l = 0; l < Lc; ++l) {
+  for (int l = 0; l < lt; ++l) {
     T* x = (T*)Ls[l].x;
     T* r = (T*)Ls[l].r;
     launch_relax0_u<T>(Ls[l], b, x, st);
@@ -956,10 +1048,17 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
     launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b, st);
     b = (const T*)Ls[l + 1].b;
   }
-  coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);
+  const T* e;
+  if (lt < Lc) {
+    launch_vtail<T>((const TailLevel<T>*)s->tail_dev, Lc - lt + 1, s->cinv, s->nL,
+                    s->prm.coarse_direct, s->tail_blocks, s->tail_bar, st);
+    e = (const T*)Ls[lt].t;
+  } else {
+    coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);
+    e = (const T*)Ls[Lc].x;
+  }
   // up: x + P e into the (now free) residual buffer with U x, post-relax
-  const T* e = (const T*)Ls[Lc].x;
-  for (int l = Lc - 1; l >= 0; --l) {
+  for (int l = lt - 1; l >= 0; --l) {
     T* xc = (T*)Ls[l].r;
     launch_prolong_u<T>(Ls[l], e, (const T*)Ls[l].x, xc, st);
     T* out = (l == 0 && !is_f) ? (T*)z_out : (T*)Ls[l].t;
@@ -1051,6 +1150,14 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
       SSAMG_CUDA(cudaStreamSynchronize(st));
       if (s->h_sc->done) break;
       enqueue_pcg_body(s, 0, 0, st);
+    }
+  }
+  if (s->tail_bar) {
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_int, &s->tail_bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+    if (s->h_int[0]) {
+      SSAMG_CUDA(cudaMemsetAsync(&s->tail_bar->err, 0, sizeof(int), st));
+      throw SsamgError{SSAMG_ERR_TIMEOUT, "a grid barrier of the coarse-level kernel timed out"};
     }
   }
   const PcgScalars& r = *s->h_sc;

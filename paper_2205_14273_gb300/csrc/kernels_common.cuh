@@ -32,6 +32,45 @@ __device__ __forceinline__ int find_part_cell(const int* __restrict__ cs, int np
   return find_part(cs, np, g);
 }
 
+// Part of this block (cell tiles, or fine-point tiles when `fine`), staged in
+// shared memory from the kernel parameter when the level has few parts, else
+// from global memory.  All threads call; a barrier follows in the caller.
+__device__ __forceinline__ int block_part(const PartsParam& PP, const int* __restrict__ gblk,
+                                          const DPart* __restrict__ gparts, int np, DPart& sm,
+                                          bool fine) {
+  int p;
+  if (PP.inparam) {
+    const int* b = fine ? PP.fblk : PP.blk;
+    p = 0;
+    while (p + 1 < PP.np && b[p + 1] <= (int)blockIdx.x) ++p;
+    const int* s = reinterpret_cast<const int*>(&PP.part[p]);
+    int* d = reinterpret_cast<int*>(&sm);
+    constexpr int nw = sizeof(DPart) / 4;
+    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = s[t];
+  } else {
+    p = find_part(gblk, np, blockIdx.x);
+    const int* s = reinterpret_cast<const int*>(gparts + p);
+    int* d = reinterpret_cast<int*>(&sm);
+    constexpr int nw = sizeof(DPart) / 4;
+    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
+  }
+  return p;
+}
+
+// The same part of a second level (same part index), into shared memory.
+__device__ __forceinline__ void part_of(const PartsParam& PP, const DPart* __restrict__ gparts,
+                                        int p, DPart& sm) {
+  int* d = reinterpret_cast<int*>(&sm);
+  constexpr int nw = sizeof(DPart) / 4;
+  if (PP.inparam) {
+    const int* s = reinterpret_cast<const int*>(&PP.part[p]);
+    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = s[t];
+  } else {
+    const int* s = reinterpret_cast<const int*>(gparts + p);
+    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
+  }
+}
+
 // Copy one part descriptor into shared memory (all threads of the block call).
 __device__ __forceinline__ void stage_part(DPart& dst, const DPart* __restrict__ src) {
   const int* s = reinterpret_cast<const int*>(src);
@@ -174,6 +213,112 @@ __device__ __forceinline__ T stencil_apply(const DPart& p, const T* __restrict__
   return acc;
 }
 
+// ---------------------------------------------------------------------------
+// Shape-specialised operator apply.  The host picks one shape per level so a
+// kernel instance contains only the variant it runs (small code, no per-part
+// dispatch).  Unchecked shapes need every entry per cell, zero outside the
+// box, and a guard-padded x; the checked shape handles constant entries and
+// caller vectors with branch-free bounds handling (an out-of-box neighbour
+// reads the cell itself and is multiplied by zero).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_interior(const DPart& p, int i, int j, int k) {
+  return i > 0 && i < p.n[0] - 1 && j > 0 && j < p.n[1] - 1 && k > 0 && k < p.n[2] - 1;
+}
+
+enum StencilShape { SH_CHECKED = 0, SH_U7 = 1, SH_U15 = 2, SH_C27 = 3, SH_UGEN = 4, SH_K7 = 5 };
+
+// Checked 7-point stencil in the canonical entry order (centre, -x, +x, -y,
+// +y, -z, +z): directions and bounds are known at compile time; entries may
+// be constant or per cell (uniform per part).
+template <class T>
+__device__ __forceinline__ T stencil7_canon_checked(const DPart& p, const T* __restrict__ coef,
+                                                    const T* __restrict__ xc, int c, int i, int j,
+                                                    int k) {
+  const int nx = p.n[0], nxy = p.n[0] * p.n[1];
+  const bool ok[7] = {true, i > 0, i < p.n[0] - 1, j > 0, j < p.n[1] - 1, k > 0, k < p.n[2] - 1};
+  const int d[7] = {0, -1, 1, -nx, nx, -nxy, nxy};
+  const unsigned vm = p.varmask;
+  T acc = (T)0;
+#pragma unroll
+  for (int e = 0; e < 7; ++e) {
+    const T ae = ((vm >> e) & 1u) ? coef[p.coef[e] + c] : const_of<T>(p, e);
+    const T xv = xc[ok[e] ? d[e] : 0];
+    acc = fma(ae, ok[e] ? xv : (T)0, acc);
+  }
+  return acc;
+}
+
+template <int K, class T>
+__device__ __forceinline__ T stencil_checked_fixed(const DPart& p, const T* __restrict__ coef,
+                                                   const T* __restrict__ xc, int c, int i, int j,
+                                                   int k) {
+  const bool xm = i > 0, xp = i < p.n[0] - 1, ym = j > 0, yp = j < p.n[1] - 1, zm = k > 0,
+             zp = k < p.n[2] - 1;
+  const unsigned vm = p.varmask;
+  T acc = (T)0;
+#pragma unroll
+  for (int e = 0; e < K; ++e) {
+    const int ox = p.o[e][0], oy = p.o[e][1], oz = p.o[e][2];
+    const bool ok = (ox == 0 || (ox < 0 ? xm : xp)) && (oy == 0 || (oy < 0 ? ym : yp)) &&
+                    (oz == 0 || (oz < 0 ? zm : zp));
+    const T ae = ((vm >> e) & 1u) ? coef[p.coef[e] + c] : const_of<T>(p, e);
+    const T xv = xc[ok ? p.disp[e] : 0];
+    acc = fma(ae, ok ? xv : (T)0, acc);
+  }
+  return acc;
+}
+
+template <class T>
+__device__ __forceinline__ T stencil_checked_loop(const DPart& p, const T* __restrict__ coef,
+                                                  const T* __restrict__ xc, int c, int i, int j,
+                                                  int k) {
+  T acc = (T)0;
+#pragma unroll 4
+  for (int e = 0; e < p.nent; ++e) {
+    const bool ok = inside(p, i + p.o[e][0], j + p.o[e][1], k + p.o[e][2]);
+    const T xv = xc[ok ? p.disp[e] : 0];
+    acc = fma(coef_at(p, coef, e, c), ok ? xv : (T)0, acc);
+  }
+  return acc;
+}
+
+template <int SH, class T>
+__device__ __forceinline__ T stencil_sh(const DPart& p, const T* __restrict__ coef,
+                                        const T* __restrict__ x, int c, int i, int j, int k) {
+  const T* xc = x + p.off + c;
+  if constexpr (SH == SH_C27) {
+    return stencil27_unchecked(p, coef + p.coef[0] + c, xc);
+  } else if constexpr (SH == SH_U7) {
+    return stencil_unchecked<7>(p, coef + p.coef[0] + c, xc);
+  } else if constexpr (SH == SH_U15) {
+    return stencil_unchecked<15>(p, coef + p.coef[0] + c, xc);
+  } else if constexpr (SH == SH_K7) {
+    return stencil7_canon_checked(p, coef, xc, c, i, j, k);
+  } else if constexpr (SH == SH_UGEN) {
+    const T* a = coef + p.coef[0] + c;
+    const int s = p.ncell;
+    T acc = (T)0;
+#pragma unroll 4
+    for (int e = 0; e < p.nent; ++e) acc = fma(a[e * s], xc[p.disp[e]], acc);
+    return acc;
+  } else {
+    if (p.nent == 7) return stencil_checked_fixed<7>(p, coef, xc, c, i, j, k);
+    return stencil_checked_loop(p, coef, xc, c, i, j, k);
+  }
+}
+
+// (A x)(g) for local cell c of part p with shape SH; coordinates are only
+// computed where needed (checked shape, or face cells of coupled parts).
+template <int SH, class T>
+__device__ __forceinline__ T apply_A_sh(const LevelView<T>& L, const DPart& p,
+                                        const T* __restrict__ x, int c) {
+  int i = 0, j = 0, k = 0;
+  if (SH == SH_CHECKED || SH == SH_K7 || p.has_u) cell_coords(p, c, i, j, k);
+  T acc = stencil_sh<SH>(p, L.coef, x, c, i, j, k);
+  if (p.has_u && !is_interior(p, i, j, k)) acc += L.uy[p.off + c];
+  return acc;
+}
+
 // (U x)(g) for global cell g (0 when g has no U row).
 template <class T>
 __device__ __forceinline__ T u_apply(const LevelView<T>& L, const T* __restrict__ x, int g) {
@@ -186,9 +331,6 @@ __device__ __forceinline__ T u_apply(const LevelView<T>& L, const T* __restrict_
   return acc;
 }
 
-__device__ __forceinline__ bool is_interior(const DPart& p, int i, int j, int k) {
-  return i > 0 && i < p.n[0] - 1 && j > 0 && j < p.n[1] - 1 && k > 0 && k < p.n[2] - 1;
-}
 
 // (A x)(c) = (S x)(c) + (U x)(c); the U part comes from L.uy, which a row
 // job filled for this same x (only face cells can have couplings).
@@ -201,8 +343,9 @@ __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, cons
   return acc;
 }
 
-// Row job: SSAMG_TPR threads per U row r = blockIdx-relative row; returns
-// sum_q u_q * f(col_q, q) on the quad's lane 0 (all lanes must call).
+// Row job: SSAMG_TPR threads per U row r = blockIdx-relative row; stores
+// sum_q u_q * f(col_q, q) at the row's cell of L.uy (all lanes must call).
+// Each lane takes four entries at a time so that their loads overlap.
 template <class T, class F>
 __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, F&& f) {
   const int r = rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR;
@@ -210,7 +353,20 @@ __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, F&& f) 
   T acc = (T)0;
   if (r < L.nr) {
     const int q1 = L.u_ptr[r + 1];
-    for (int q = L.u_ptr[r] + l4; q < q1; q += SSAMG_TPR) acc = fma(L.u_val[q], f(L.u_col[q], q), acc);
+    int q = L.u_ptr[r] + l4;
+    for (; q + 3 * SSAMG_TPR < q1; q += 4 * SSAMG_TPR) {
+      const int c0 = L.u_col[q], c1 = L.u_col[q + SSAMG_TPR], c2 = L.u_col[q + 2 * SSAMG_TPR],
+                c3 = L.u_col[q + 3 * SSAMG_TPR];
+      const T u0 = L.u_val[q], u1 = L.u_val[q + SSAMG_TPR], u2 = L.u_val[q + 2 * SSAMG_TPR],
+              u3 = L.u_val[q + 3 * SSAMG_TPR];
+      const T v0 = f(c0, q), v1 = f(c1, q + SSAMG_TPR), v2 = f(c2, q + 2 * SSAMG_TPR),
+              v3 = f(c3, q + 3 * SSAMG_TPR);
+      acc = fma(u0, v0, acc);
+      acc = fma(u1, v1, acc);
+      acc = fma(u2, v2, acc);
+      acc = fma(u3, v3, acc);
+    }
+    for (; q < q1; q += SSAMG_TPR) acc = fma(L.u_val[q], f(L.u_col[q], q), acc);
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);

@@ -36,34 +36,30 @@ __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__
 }
 
 // r = b - A x
-template <class T>
+template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __restrict__ x,
-                                                 const T* __restrict__ b, T* __restrict__ r) {
+                                                    const T* __restrict__ b, T* __restrict__ r,
+                                                    const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
-  int p = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + p);
+  block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   TILE_LOOP(c, sp) {
-    int i, j, k;
-    cell_coords(sp, c, i, j, k);
-    int g = sp.off + c;
-    r[g] = b[g] - apply_A(L, sp, x, c, i, j, k);
+    const int g = sp.off + c;
+    r[g] = b[g] - apply_A_sh<SH>(L, sp, x, c);
   }
 }
 
 // xo = x + omega M^-1 (b - A x)
-template <class T>
+template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __restrict__ x,
-                                              const T* __restrict__ b, T* __restrict__ xo) {
+                                                 const T* __restrict__ b, T* __restrict__ xo,
+                                                 const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
-  int p = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + p);
+  block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   TILE_LOOP(c, sp) {
-    int i, j, k;
-    cell_coords(sp, c, i, j, k);
-    int g = sp.off + c;
-    xo[g] = fma(L.dinv[g], b[g] - apply_A(L, sp, x, c, i, j, k), x[g]);
+    const int g = sp.off + c;
+    xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
   }
 }
 
@@ -71,12 +67,11 @@ __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __rest
 // fine points beside it along d* (weights PE of the west one, PW of the east).
 template <class T>
 __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
-                                                 const T* __restrict__ r, T* __restrict__ bc) {
+                                                 const T* __restrict__ r, T* __restrict__ bc, const __grid_constant__ PartsParam PF, const __grid_constant__ PartsParam PC) {
   __shared__ DPart fp;
   __shared__ DPart cp;
-  int p = find_part(C.blk, C.np, blockIdx.x);
-  stage_part(fp, F.parts + p);
-  stage_part(cp, C.parts + p);
+  int p = block_part(PC, C.blk, C.parts, C.np, cp, false);
+  part_of(PF, F.parts, p, fp);
   __syncthreads();
   TILE_LOOP(cc, cp) {
     int I[3];
@@ -110,9 +105,9 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
 // at setup), so the two roles need no ordering.
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
-                                                  const T* __restrict__ xin, T* __restrict__ xout) {
+                                                  const T* __restrict__ xin, T* __restrict__ xout,
+                                                  int nb, const __grid_constant__ PartsParam PP) {
   __shared__ DPart fp;
-  const int nb = __ldg(F.blk + F.np);
   if ((int)blockIdx.x >= nb) {
     u_row_job(F, blockIdx.x - nb, [&](int col, int q) {
       T v = xin[col];
@@ -123,8 +118,7 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
     });
     return;
   }
-  int p = find_part(F.blk, F.np, blockIdx.x);
-  stage_part(fp, F.parts + p);
+  int p = block_part(PP, F.blk, F.parts, F.np, fp, false);
   __syncthreads();
   TILE_LOOP(c, fp) {
     int i, j, k;
@@ -141,10 +135,9 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
 // x += P ec, one fine cell per thread.
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
-                                                T* __restrict__ x) {
+                                                T* __restrict__ x, const __grid_constant__ PartsParam PP) {
   __shared__ DPart fp;
-  int p = find_part(F.blk, F.np, blockIdx.x);
-  stage_part(fp, F.parts + p);
+  int p = block_part(PP, F.blk, F.parts, F.np, fp, false);
   __syncthreads();
   TILE_LOOP(c, fp) {
     int i, j, k;
@@ -192,6 +185,216 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Lg, const T* __
   for (int i = l; i < n; i += 32) x[i] = (T)y[i];
 }
 
+// ---------------------------------------------------------------------------
+// Fused coarse tail: every small level of the V-cycle in one cooperative
+// launch.  The steps are those of the per-level kernels above (pre-relaxation
+// with U x, residual, restriction, coarsest solve, prolongation with U x,
+// post-relaxation); a grid barrier separates them instead of a kernel
+// boundary.  Every thread handles at most a few cells or coupling rows per
+// step, so a step costs one or two dependent memory round trips.
+// ---------------------------------------------------------------------------
+constexpr int TB = SSAMG_TAIL_BLOCK;
+
+// Grid barrier over gridDim.x co-resident blocks (cooperative launch).  Each
+// block's thread 0 adds to one counter with release semantics; block 0 adds
+// 2^31 - (nblocks - 1), the others 1, so the counter's top bit flips exactly
+// when every block has arrived.  Waiters poll with acquire semantics (which
+// also makes the other blocks' writes visible through this SM's L1).  The
+// wait is bounded: after SSAMG_BARRIER_SPINS polls the block records the
+// failure in gb->err and continues, and the solve reports a timeout.
+__device__ __forceinline__ void grid_barrier(TailBarrier* gb) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* ctr = &gb->count;
+    const unsigned nb = (blockIdx.x == 0) ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    unsigned old, cur;
+    asm volatile("atom.add.release.gpu.u32 %0,[%1],%2;" : "=r"(old) : "l"(ctr), "r"(nb) : "memory");
+    unsigned spins = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.u32 %0,[%1];" : "=r"(cur) : "l"(ctr) : "memory");
+      if ((old ^ cur) & 0x80000000u) break;
+      if (++spins > SSAMG_BARRIER_SPINS) {
+        atomicExch(&gb->err, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int tail_part(const int* __restrict__ cs, int np, int g) {
+  int p = 0;
+  while (p + 1 < np && __ldg(cs + p + 1) <= g) ++p;
+  return p;
+}
+
+template <class T>
+__global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ lv, int nlev,
+                                              const double* __restrict__ cinv, int nL,
+                                              int coarse_direct, TailBarrier* gb) {
+  const int tid = blockIdx.x * TB + threadIdx.x;
+  const int nth = gridDim.x * TB;
+  // ---- down
+  for (int l = 0; l + 1 < nlev; ++l) {
+    const TailLevel<T>& F = lv[l];
+    const TailLevel<T>& C = lv[l + 1];
+    const LevelView<T> FL = F.L;
+    T* __restrict__ Fx = F.x;
+    const T* __restrict__ Fb = F.b;
+    for (int g = tid; g < FL.N; g += nth) Fx[g] = FL.dinv[g] * Fb[g];
+    for (int r = tid; r < FL.nr; r += nth) {
+      T acc = (T)0;
+      for (int q = FL.u_ptr[r]; q < FL.u_ptr[r + 1]; ++q) {
+        const int col = FL.u_col[q];
+        acc = fma(FL.u_val[q], FL.dinv[col] * Fb[col], acc);
+      }
+      FL.uy[FL.u_rows[r]] = acc;
+    }
+    grid_barrier(gb);
+    T* __restrict__ Fr = F.r;
+    for (int g = tid; g < FL.N; g += nth) {
+      const DPart& sp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
+      int c = g - sp.off, i, j, k;
+      cell_coords(sp, c, i, j, k);
+      Fr[g] = Fb[g] - apply_A(FL, sp, Fx, c, i, j, k);
+    }
+    grid_barrier(gb);
+    const LevelView<T> CL = C.L;
+    T* __restrict__ Cb = C.b;
+    for (int gc = tid; gc < CL.N; gc += nth) {
+      const int p = tail_part(CL.cellstart, CL.np, gc);
+      const DPart& fp = FL.parts[p];
+      const DPart& cp = CL.parts[p];
+      int cc = gc - cp.off;
+      int I[3];
+      cell_coords(cp, cc, I[0], I[1], I[2]);
+      const int d = fp.dstar;
+      T v;
+      if (d < 0) {
+        v = Fr[fp.off + (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]];
+      } else {
+        int f[3] = {I[0], I[1], I[2]};
+        const int anchor = 2 * I[d] + fp.par;
+        f[d] = anchor;
+        const int sd = (d == 0) ? 1 : (d == 1 ? fp.n[0] : fp.n[0] * fp.n[1]);
+        const int fa = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+        v = Fr[fa];
+        if (anchor - 1 >= 0) {
+          f[d] = anchor - 1;
+          v = fma(FL.Pe[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], Fr[fa - sd], v);
+        }
+        if (anchor + 1 < fp.n[d]) {
+          f[d] = anchor + 1;
+          v = fma(FL.Pw[fp.poff + fine_point_index(fp, f[0], f[1], f[2])], Fr[fa + sd], v);
+        }
+      }
+      Cb[gc] = v;
+    }
+    grid_barrier(gb);
+  }
+  // ---- coarsest level
+  {
+    const TailLevel<T>& Lc = lv[nlev - 1];
+    if (coarse_direct) {
+      for (int i = tid; i < nL; i += nth) {
+        const double* row = cinv + (long long)i * nL;
+        double s0 = 0.0, s1 = 0.0;
+        int jj = 0;
+        for (; jj + 1 < nL; jj += 2) {
+          s0 = fma(row[jj], (double)Lc.b[jj], s0);
+          s1 = fma(row[jj + 1], (double)Lc.b[jj + 1], s1);
+        }
+        if (jj < nL) s0 = fma(row[jj], (double)Lc.b[jj], s0);
+        Lc.x[i] = (T)(s0 + s1);
+      }
+    } else {
+      for (int g = tid; g < Lc.L.N; g += nth) Lc.x[g] = Lc.L.dinv[g] * Lc.b[g];
+    }
+    grid_barrier(gb);
+  }
+  // ---- up
+  const T* e = lv[nlev - 1].x;
+  for (int l = nlev - 2; l >= 0; --l) {
+    const TailLevel<T>& F = lv[l];
+    const LevelView<T> FL = F.L;
+    const T* __restrict__ Fx = F.x;
+    T* __restrict__ Fr = F.r;
+    for (int g = tid; g < FL.N; g += nth) {
+      const DPart& fp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
+      int c = g - fp.off, i, j, k;
+      cell_coords(fp, c, i, j, k);
+      int J[2];
+      T w[2];
+      int m = p_row(fp, FL.Pw, FL.Pe, i, j, k, J, w);
+      T v = Fx[g];
+      for (int t = 0; t < m; ++t) v = fma(w[t], e[J[t]], v);
+      Fr[g] = v;
+    }
+    for (int r = tid; r < FL.nr; r += nth) {
+      T acc = (T)0;
+      for (int q = FL.u_ptr[r]; q < FL.u_ptr[r + 1]; ++q) {
+        const int col = FL.u_col[q];
+        T v = Fx[col];
+        const int j0 = FL.u_pj[2 * q], j1 = FL.u_pj[2 * q + 1];
+        if (j0 >= 0) v = fma(FL.u_pw[2 * q], e[j0], v);
+        if (j1 >= 0) v = fma(FL.u_pw[2 * q + 1], e[j1], v);
+        acc = fma(FL.u_val[q], v, acc);
+      }
+      FL.uy[FL.u_rows[r]] = acc;
+    }
+    grid_barrier(gb);
+    T* __restrict__ Ft = F.t;
+    const T* __restrict__ Fb = F.b;
+    for (int g = tid; g < FL.N; g += nth) {
+      const DPart& sp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
+      int c = g - sp.off, i, j, k;
+      cell_coords(sp, c, i, j, k);
+      Ft[g] = fma(FL.dinv[g], Fb[g] - apply_A(FL, sp, Fr, c, i, j, k), Fr[g]);
+    }
+    grid_barrier(gb);
+    e = Ft;
+  }
+}
+
+// Coarsest level with the explicit inverse: x = A_L^-1 b, one thread per row.
+template <class T>
+__global__ void k_coarse_apply(int n, const double* __restrict__ inv, const T* __restrict__ b,
+                               T* __restrict__ x) {
+  extern __shared__ double sb[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)b[i];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double* row = inv + (long long)i * n;
+    double s0 = 0.0, s1 = 0.0;
+    int jj = 0;
+    for (; jj + 1 < n; jj += 2) {
+      s0 = fma(row[jj], sb[jj], s0);
+      s1 = fma(row[jj + 1], sb[jj + 1], s1);
+    }
+    if (jj < n) s0 = fma(row[jj], sb[jj], s0);
+    x[i] = (T)(s0 + s1);
+  }
+}
+
+// inv = (L L^T)^-1, one thread per column.
+__global__ void k_coarse_inverse(int n, const double* __restrict__ Lf, double* __restrict__ inv) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    // forward: L y = e_j, stored in column j of inv
+    for (int i = 0; i < n; ++i) {
+      double s0 = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s0 -= Lf[(long long)i * n + k] * inv[(long long)k * n + j];
+      inv[(long long)i * n + j] = s0 / Lf[(long long)i * n + i];
+    }
+    // backward: L^T z = y
+    for (int i = n - 1; i >= 0; --i) {
+      double s0 = inv[(long long)i * n + j];
+      for (int k = i + 1; k < n; ++k) s0 -= Lf[(long long)k * n + i] * inv[(long long)k * n + j];
+      inv[(long long)i * n + j] = s0 / Lf[(long long)i * n + i];
+    }
+  }
+}
+
 __global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, int n) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (float)in[g];
@@ -202,15 +405,14 @@ __global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ ou
 }
 
 __global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* __restrict__ x,
-                                               double* __restrict__ y, int padded) {
+                                               double* __restrict__ y, int padded, const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
-  int p = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + p);
+  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
-    y[sp.off + c] = apply_A(L, sp, x, c, i, j, k, padded != 0);
+    y[sp.off + c] = apply_A_sh<SH_CHECKED>(L, sp, x, c);
   }
 }
 
@@ -231,13 +433,13 @@ __device__ __forceinline__ void finish_sums(const double* __restrict__ partial, 
 }
 
 // r = b - A x; partial sums of (b.b, r.r)
+template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
                                                  const double* __restrict__ x, double* __restrict__ r,
-                                                 double* __restrict__ partial) {
+                                                 double* __restrict__ partial, const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int p = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + p);
+  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   double bb = 0.0, rr = 0.0;
   TILE_LOOP(c, sp) {
@@ -245,7 +447,7 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
     double bv = b[g];
-    double rv = bv - apply_A(L, sp, x, c, i, j, k);
+    double rv = bv - apply_A_sh<SH>(L, sp, x, c);
     r[g] = rv;
     bb = fma(bv, bv, bb);
     rr = fma(rv, rv, rr);
@@ -279,6 +481,7 @@ __global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
                                                   long long n, double* __restrict__ partial) {
   __shared__ double sh[NT / 32];
   double s = 0.0;
+#pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
     double zv = z[g];
     p[g] = zv;
@@ -314,6 +517,7 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r
                                                     double* __restrict__ partial) {
   __shared__ double sh[NT / 32];
   double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
     double rv = r[g], zv = z[g];
     s0 = fma(rv, zv, s0);
@@ -350,25 +554,26 @@ __global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p,
                            const PcgScalars* __restrict__ sc) {
   if (sc->done) return;
   double beta = sc->beta;
+#pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT)
     p[g] = fma(beta, p[g], z[g]);
 }
 
 // q = A p; partial p.q
+template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
                                                      double* __restrict__ q,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial, const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int pt = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + pt);
+  int pt = block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   double s = 0.0;
   TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
-    double qv = apply_A(L, sp, p, c, i, j, k);
+    double qv = apply_A_sh<SH>(L, sp, p, c);
     q[g] = qv;
     s = fma(p[g], qv, s);
   }
@@ -403,6 +608,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
   if (sc->done) return;
   double alpha = sc->alpha;
   double s = 0.0;
+#pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
     x[g] = fma(alpha, p[g], x[g]);
     double rv = fma(-alpha, q[g], r[g]);
@@ -446,10 +652,9 @@ __global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ 
 __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
                                                       const double* __restrict__ lam,
                                                       const double* __restrict__ x,
-                                                      double* __restrict__ dcoef, long long N) {
+                                                      double* __restrict__ dcoef, long long N, const __grid_constant__ PartsParam PP) {
   __shared__ DPart sp;
-  int p = find_part(L.blk, L.np, blockIdx.x);
-  stage_part(sp, L.parts + p);
+  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
   __syncthreads();
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -514,7 +719,7 @@ void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
 }
 template <class T>
 void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
-  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout);
+  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout, F.nblk, *F.pp);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -523,25 +728,35 @@ void launch_uy(const Level& L, const T* x, cudaStream_t st) {
   k_uy<T><<<L.nublk, NT, 0, st>>>(L.view<T>(), x);
   SSAMG_LAUNCH_CHECK();
 }
+#define SH_DISPATCH(shape, KCALL)                         \
+  switch (shape) {                                        \
+    case SH_U7: { constexpr int SHV = SH_U7; KCALL; } break;   \
+    case SH_U15: { constexpr int SHV = SH_U15; KCALL; } break; \
+    case SH_C27: { constexpr int SHV = SH_C27; KCALL; } break; \
+    case SH_UGEN: { constexpr int SHV = SH_UGEN; KCALL; } break; \
+    case SH_K7: { constexpr int SHV = SH_K7; KCALL; } break;   \
+    default: { constexpr int SHV = SH_CHECKED; KCALL; } break; \
+  }
+
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
-  k_residual<T><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r);
+  SH_DISPATCH(L.shape, (k_residual<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r, *L.pp)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
-  k_relax<T><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo);
+  SH_DISPATCH(L.shape, (k_relax<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo, *L.pp)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st) {
-  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc);
+  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc, *F.pp, *Cl.pp);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st) {
   (void)Cl;
-  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x);
+  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x, *F.pp);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -552,11 +767,52 @@ void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream
   SSAMG_LAUNCH_CHECK();
 }
 
+template <class T>
+void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st) {
+  k_coarse_apply<T><<<1, 256, sizeof(double) * n, st>>>(n, inv, b, x);
+  SSAMG_LAUNCH_CHECK();
+}
+
+template <class T>
+void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, int coarse_direct,
+                  int nblocks, TailBarrier* gb, cudaStream_t st) {
+  SSAMG_CUDA(cudaMemsetAsync(gb, 0, sizeof(unsigned), st));  // counter (err is sticky)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(TB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SSAMG_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T>, lv, nlev, cinv, nL, coarse_direct, gb));
+}
+
+int tail_max_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vtail<float>, TB, 0);
+  int per2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_vtail<double>, TB, 0);
+  return sms * std::min(per, per2);
+}
+
+void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st) {
+  k_coarse_inverse<<<cdiv(n, 64), 64, 0, st>>>(n, Lfac, inv);
+  SSAMG_LAUNCH_CHECK();
+}
+
 #define INST(T)                                                                            \
   template void launch_relax0<T>(const Level&, const T*, T*, cudaStream_t);                \
   template void launch_relax0_u<T>(const Level&, const T*, T*, cudaStream_t);              \
   template void launch_prolong_u<T>(const Level&, const T*, const T*, T*, cudaStream_t);   \
   template void launch_uy<T>(const Level&, const T*, cudaStream_t);                        \
+  template void launch_vtail<T>(const TailLevel<T>*, int, const double*, int, int, int,      \
+                                TailBarrier*, cudaStream_t);                               \
+  template void launch_coarse_apply<T>(int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
   template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \
   template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t); \
@@ -576,7 +832,7 @@ void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st)
 }
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0);
+  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0, *L.pp);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -588,7 +844,7 @@ int reduce_blocks(long long n) {
 void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
                      PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
+  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial, *L.pp)));
   SSAMG_LAUNCH_CHECK();
   k_pcg_init_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
@@ -615,7 +871,7 @@ void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p,
 void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
                       PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, p, st);
-  k_pcg_spmv_dot<<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial);
+  SH_DISPATCH(L.shape, (k_pcg_spmv_dot<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial, *L.pp)));
   SSAMG_LAUNCH_CHECK();
   k_pcg_alpha_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
@@ -633,7 +889,7 @@ void launch_pcg_update(const double* p, const double* q, double* x, double* r, l
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
                           double* partial, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  k_pcg_init<<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial);
+  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial, *L.pp)));
   SSAMG_LAUNCH_CHECK();
   k_true_res_fin<<<1, NT, 0, st>>>(partial, L.nblk, out);
   SSAMG_LAUNCH_CHECK();
@@ -641,7 +897,7 @@ void launch_true_residual(const Level& L, const double* b, const double* x, doub
 
 void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
                           cudaStream_t st) {
-  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N);
+  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N, *L.pp);
   SSAMG_LAUNCH_CHECK();
 }
 

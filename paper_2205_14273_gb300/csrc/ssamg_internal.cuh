@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -95,6 +96,18 @@ struct DPart {
 };
 static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 
+// Up to SSAMG_PARAM_PARTS part descriptors of a level passed by value as a
+// kernel parameter (constant bank): blocks find and stage their part without
+// a global-memory round trip.  Levels with more parts use the global copies.
+#define SSAMG_PARAM_PARTS 8
+struct PartsParam {
+  int np;
+  int inparam;
+  int blk[SSAMG_PARAM_PARTS + 1];
+  int fblk[SSAMG_PARAM_PARTS + 1];
+  DPart part[SSAMG_PARAM_PARTS];
+};
+
 // Scalars of one PCG solve (device memory).
 struct PcgScalars {
   double tol, bb, rr, rz, pq, alpha, beta, tol2bb;
@@ -125,6 +138,28 @@ struct LevelView {
   T* uy;                // dense per-cell (U x)(c) of the vector last passed to a row job; 0 off rows
   int nr;
   int nublk;            // blocks of row jobs (SSAMG_RPB rows each)
+};
+
+// One level of the fused coarse tail: the level's view and its cycle vectors.
+#define SSAMG_TAIL_MAX_CELLS 32768  // levels at most this large run in the fused tail
+#define SSAMG_TAIL_MAX_PARTS 8
+#define SSAMG_TAIL_BLOCK 256
+#define SSAMG_TAIL_MAX_BLOCKS 128
+#define SSAMG_BARRIER_SPINS (1u << 24)  // ~1 s of polling before a barrier gives up
+
+struct TailBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad_;
+};
+template <class T>
+struct TailLevel {
+  LevelView<T> L;
+  T* x;
+  T* b;
+  T* r;
+  T* t;
 };
 
 // ---------------------------------------------------------------------------
@@ -168,6 +203,8 @@ struct Level {
   int* d_cellstart = nullptr;
   int nblk = 0, nfblk = 0;
   int cpt = 1;
+  int shape = 0;  // StencilShape of the level's operator apply
+  std::shared_ptr<PartsParam> pp;  // host copy of the kernel-parameter descriptors
   double* coef = nullptr;
   float* coef32 = nullptr;
   long long ncoef = 0;
@@ -274,6 +311,15 @@ template <class T>
 void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st);
 template <class T>
 void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st);
+// Levels lt..Lc of the V-cycle in one single-block launch (down sweep from
+// b of level lt, coarsest solve, up sweep; result in t of level lt).
+template <class T>
+void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, int coarse_direct,
+                  int nblocks, TailBarrier* gb, cudaStream_t st);
+int tail_max_blocks();
+void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st);
+template <class T>
+void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st);
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st);
 void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st);
 // y = A_l x; x may be a caller vector without guard cells

@@ -177,23 +177,26 @@ def test_hierarchy_l1_fp32_matches_oracle(S, prob):
 @pytest.mark.parametrize("prob", CASES, ids=CIDS)
 def test_vcycle_and_matvec_match_oracle(S, prob):
     h = O.setup(prob)
-    grid, A, solver = gpu_setup(S, prob)
     r = P.SplitMix64(17).uniform_pm1(prob.n)
     rt = torch.as_tensor(r, device="cuda")
-    z = torch.zeros_like(rt)
-    solver.precondition(rt, z)
     zr = O.vcycle(h, r)
-    assert rel(z.cpu().numpy(), zr) <= OP_TOL
+    # one launch per level and step (default) and the single-block fused tail
+    for tail in (0, 1):
+        grid, A, solver = gpu_setup(S, prob, use_tail=tail)
+        z = torch.zeros_like(rt)
+        solver.precondition(rt, z)
+        assert rel(z.cpu().numpy(), zr) <= OP_TOL, tail
     for l, lev in enumerate(h.levels):
         x = P.SplitMix64(l).uniform_pm1(lev.n)
         y = torch.zeros(lev.n, dtype=torch.float64, device="cuda")
         solver.level_matvec(l, torch.as_tensor(x, device="cuda"), y)
         assert rel(y.cpu().numpy(), O.matvec(lev, x)) <= OP_TOL, l
     # FP32 cycle against the FP64 cycle
-    _, _, s32 = gpu_setup(S, prob, precision=1)
-    z32 = torch.zeros_like(rt)
-    s32.precondition(rt, z32)
-    assert rel(z32.cpu().numpy(), zr) <= 5e-5
+    for tail in (0, 1):
+        _, _, s32 = gpu_setup(S, prob, precision=1, use_tail=tail)
+        z32 = torch.zeros_like(rt)
+        s32.precondition(rt, z32)
+        assert rel(z32.cpu().numpy(), zr) <= 5e-5, tail
 
 
 @pytest.mark.parametrize("prob", CASES, ids=CIDS)
@@ -203,14 +206,14 @@ def test_pcg_matches_oracle(S, prob):
     bt = torch.as_tensor(b, device="cuda")
     tight = O.pcg(h, b, tol=1e-13, max_iter=500)
     at8 = O.pcg(h, b, tol=1e-8)
-    for graph in (1, 0):
-        grid, A, solver = gpu_setup(S, prob, tol=1e-13, max_iter=500, use_graph=graph)
+    for graph, tail in ((1, 1), (0, 0)):
+        grid, A, solver = gpu_setup(S, prob, tol=1e-13, max_iter=500, use_graph=graph, use_tail=tail)
         x = torch.zeros_like(bt)
         st = solver.solve(bt, x)
         assert st.converged
         assert rel(x.cpu().numpy(), tight.x) <= SOL_TOL
         assert st.true_rel_res <= 1e-12
-        _, _, s8 = gpu_setup(S, prob, use_graph=graph)
+        _, _, s8 = gpu_setup(S, prob, use_graph=graph, use_tail=tail)
         x8 = torch.zeros_like(bt)
         st8 = s8.solve(bt, x8)
         assert abs(st8.iterations - at8.iterations) <= 1, (st8.iterations, at8.iterations)
