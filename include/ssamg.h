@@ -197,6 +197,18 @@ int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, v
  * Section 3.1 (W = +inf encoded as HUGE_VAL). */
 int ssamg_spacings(ssamg_solver s, double* c, double* W);
 
+/* Diagnostic timing of one hot-path kernel on `level`: `reps` launches are
+ * captured into a CUDA graph and replayed between CUDA events on `stream`
+ * (after one warm-up replay); *us_per_launch receives the mean time per
+ * launch in microseconds.  kernel: 0 residual, 1 relaxation, 2 pre-relaxation
+ * from zero (with U x), 3 restriction to level+1, 4 prolongation from level+1
+ * (with U x), 5 whole V-cycle (level ignored), 6 the PCG's FP64 level-0
+ * operator apply with its dot product (level ignored).  The kernels work on
+ * the solver's own buffers (their contents are overwritten).  Synchronises
+ * `stream`. */
+int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* us_per_launch,
+                      void* stream);
+
 /* Host-only check of the run-time division constants the kernels use to
  * split a linear cell index into (i, j, k): compares against plain division
  * for `trials` pseudo-random (n, d) pairs.  Returns 0 when all agree. */

@@ -998,14 +998,19 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
 }
 
 // One V(1,1) cycle z = M r (r, z: FP64 level-0 vectors).
+// One V(1,1) cycle z = M r.  With `dots` set, the last post-relaxation also
+// produces the PCG's r.z (and r.zprev) block partials in `dots` and the
+// function returns their block count (0: not fused, compute them apart).
 template <class T>
-void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream_t st) {
+int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream_t st,
+                   double* dots = nullptr, double* zprev = nullptr) {
   auto& Ls = s->lev;
   const int Lc = (int)Ls.size() - 1;
   const bool is_f = sizeof(T) == sizeof(float);
+  const bool fused_in = is_f && Lc > 0 && s->tail_lt != 0;
   const T* b0;
   if (is_f) {
-    launch_cast_d2f(r_in, (float*)Ls[0].b, Ls[0].N, st);
+    if (!fused_in) launch_cast_d2f(r_in, (float*)Ls[0].b, Ls[0].N, st);
     b0 = (const T*)Ls[0].b;
   } else {
     b0 = (const T*)r_in;
@@ -1022,7 +1027,7 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
     T* out = is_f ? (T*)Ls[0].t : (T*)z_out;
     coarse(b0, out);
     if (is_f) launch_cast_f2d((const float*)out, z_out, Ls[0].N, st);
-    return;
+    return 0;
   }
   // levels from tail_lt on run in one fused single-block launch
   const int lt = s->tail_lt >= 0 ? s->tail_lt : Lc;
@@ -1036,14 +1041,17 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
       launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);
     else
       SSAMG_CUDA(cudaMemcpyAsync(z_out, Ls[0].t, sizeof(double) * Ls[0].N, cudaMemcpyDeviceToDevice, st));
-    return;
+    return 0;
   }
   // down: pre-relax from zero (with U x for the residual), residual, restrict
   const T* b = b0;
   for (int l = 0; l < lt; ++l) {
     T* x = (T*)Ls[l].x;
     T* r = (T*)Ls[l].r;
-    launch_relax0_u<T>(Ls[l], b, x, st);
+    if (l == 0 && fused_in)
+      launch_relax0_u_first<T>(Ls[0], r_in, (T*)Ls[0].b, x, st);
+    else
+      launch_relax0_u<T>(Ls[l], b, x, st);
     launch_residual<T>(Ls[l], x, b, r, st);
     launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b, st);
     b = (const T*)Ls[l + 1].b;
@@ -1061,19 +1069,24 @@ void enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStrea
   for (int l = lt - 1; l >= 0; --l) {
     T* xc = (T*)Ls[l].r;
     launch_prolong_u<T>(Ls[l], e, (const T*)Ls[l].x, xc, st);
-    T* out = (l == 0 && !is_f) ? (T*)z_out : (T*)Ls[l].t;
     const T* bl = l == 0 ? b0 : (const T*)Ls[l].b;
+    if (l == 0 && (dots || is_f)) {
+      // straight into the FP64 z (and the PCG dot partials when asked)
+      double* part = dots ? dots : s->partial;
+      launch_relax_final<T>(Ls[0], xc, bl, z_out, r_in, dots ? zprev : nullptr, part, st);
+      return dots ? Ls[0].nblk : 0;
+    }
+    T* out = (l == 0) ? (T*)z_out : (T*)Ls[l].t;
     launch_relax<T>(Ls[l], xc, bl, out, st);
     e = out;
   }
-  if (is_f) launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);
+  return 0;
 }
 
-void vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st) {
-  if (s->prm.precision == 1)
-    enqueue_vcycle<float>(s, r, z, st);
-  else
-    enqueue_vcycle<double>(s, r, z, st);
+int vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st, double* dots = nullptr,
+           double* zprev = nullptr) {
+  if (s->prm.precision == 1) return enqueue_vcycle<float>(s, r, z, st, dots, zprev);
+  return enqueue_vcycle<double>(s, r, z, st, dots, zprev);
 }
 
 // PCG segments.  init: r = b - A x; the first iteration is peeled so that the
@@ -1093,8 +1106,12 @@ void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, c
   Level& L0 = s->lev[0];
   long long N = L0.N;
   double* zp = s->prm.flexible ? s->zprev : nullptr;
-  vcycle(s, s->r, s->z, st);
-  launch_pcg_beta(s->r, s->z, zp, s->p, N, s->partial, s->nblk_red, s->sc, st);
+  // the cycle's last kernel also forms r.z (and r.zprev) for beta
+  const int npart = vcycle(s, s->r, s->z, st, s->partial, zp);
+  if (npart > 0)
+    launch_pcg_beta_from_partials(s->z, s->p, N, s->partial, npart, s->nblk_red, s->sc, st);
+  else
+    launch_pcg_beta(s->r, s->z, zp, s->p, N, s->partial, s->nblk_red, s->sc, st);
   launch_pcg_alpha(L0, s->p, s->q, s->partial, s->sc, st);
   launch_pcg_update(s->p, s->q, s->x, s->r, N, s->partial, s->nblk_red, s->sc, h, use_h, st);
 }
@@ -1378,6 +1395,76 @@ extern "C" int ssamg_spacings(ssamg_solver s, double* c, double* W) {
   if (c) std::copy(s->c.begin(), s->c.end(), c);
   if (W) std::copy(s->W.begin(), s->W.end(), W);
   return SSAMG_OK;
+}
+
+// Times one hot-path kernel: `reps` launches captured into a CUDA graph,
+// replayed once to warm up and once between events on `stream`.
+extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps,
+                                 double* us_per_launch, void* stream) {
+  if (!s || !us_per_launch || reps < 1) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  const int Lc = (int)s->lev.size() - 1;
+  if (level < 0 || level > Lc || ((kernel == 3 || kernel == 4) && level >= Lc)) return SSAMG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  API_BEGIN
+  if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+  Level& L = s->lev[level];
+  const bool f = s->prm.precision == 1;
+  auto one = [&](cudaStream_t cs) {
+    switch (kernel) {
+      case 0:  // residual r = b - A x
+        if (f) launch_residual<float>(L, (const float*)L.x, (const float*)L.b, (float*)L.r, cs);
+        else launch_residual<double>(L, (const double*)L.x, (const double*)L.b, (double*)L.r, cs);
+        break;
+      case 1:  // relaxation t = x + omega M^-1 (b - A x)
+        if (f) launch_relax<float>(L, (const float*)L.x, (const float*)L.b, (float*)L.t, cs);
+        else launch_relax<double>(L, (const double*)L.x, (const double*)L.b, (double*)L.t, cs);
+        break;
+      case 2:  // pre-relaxation from zero with U x
+        if (f) launch_relax0_u<float>(L, (const float*)L.b, (float*)L.x, cs);
+        else launch_relax0_u<double>(L, (const double*)L.b, (double*)L.x, cs);
+        break;
+      case 3:  // restriction to level + 1
+        if (f) launch_restrict<float>(L, s->lev[level + 1], (const float*)L.r, (float*)s->lev[level + 1].b, cs);
+        else launch_restrict<double>(L, s->lev[level + 1], (const double*)L.r, (double*)s->lev[level + 1].b, cs);
+        break;
+      case 4:  // prolongation from level + 1 with U x
+        if (f) launch_prolong_u<float>(L, (const float*)s->lev[level + 1].x, (const float*)L.x, (float*)L.r, cs);
+        else launch_prolong_u<double>(L, (const double*)s->lev[level + 1].x, (const double*)L.x, (double*)L.r, cs);
+        break;
+      case 5:  // whole V-cycle
+        vcycle(s, s->r, s->z, cs);
+        break;
+      case 6:  // FP64 operator apply of the PCG (q = A p with p.q partials)
+        launch_pcg_alpha(s->lev[0], s->p, s->q, s->partial, s->sc, cs);
+        break;
+      default:
+        throw SsamgError{SSAMG_ERR_ARG, "unknown kernel id"};
+    }
+  };
+  cudaGraph_t g;
+  SSAMG_CUDA(cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal));
+  for (int t = 0; t < reps; ++t) one(s->cs);
+  SSAMG_CUDA(cudaStreamEndCapture(s->cs, &g));
+  cudaGraphExec_t ge;
+  SSAMG_CUDA(cudaGraphInstantiate(&ge, g, 0));
+  cudaGraphDestroy(g);
+  cudaEvent_t e0, e1;
+  SSAMG_CUDA(cudaEventCreate(&e0));
+  SSAMG_CUDA(cudaEventCreate(&e1));
+  SSAMG_CUDA(cudaGraphLaunch(ge, st));
+  SSAMG_CUDA(cudaEventRecord(e0, st));
+  SSAMG_CUDA(cudaGraphLaunch(ge, st));
+  SSAMG_CUDA(cudaEventRecord(e1, st));
+  SSAMG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0;
+  SSAMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  *us_per_launch = 1e3 * ms / reps;
+  return SSAMG_OK;
+  API_END
 }
 
 extern "C" int ssamg_selftest_fastdiv(unsigned long long seed, int trials) {

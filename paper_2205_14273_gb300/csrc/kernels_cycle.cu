@@ -29,6 +29,24 @@ __global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T
   u_row_job(L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col] * b[col]; });
 }
 
+// First pre-relaxation of the cycle straight from the FP64 PCG residual:
+// b0 = (T) r, x = omega M^-1 b0 on the cell blocks; uy = U x on the rest.
+template <class T>
+__global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
+                                                       const double* __restrict__ r64,
+                                                       T* __restrict__ b0, T* __restrict__ x) {
+  if ((int)blockIdx.x < nb) {
+    int g = blockIdx.x * NT + threadIdx.x;
+    if (g < L.N) {
+      const T bv = (T)r64[g];
+      b0[g] = bv;
+      x[g] = L.dinv[g] * bv;
+    }
+    return;
+  }
+  u_row_job(L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col] * (T)r64[col]; });
+}
+
 // uy = U x (row jobs only)
 template <class T>
 __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__ x) {
@@ -60,6 +78,41 @@ __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __rest
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
     xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
+  }
+}
+
+// Last post-relaxation of the cycle: t = x + omega M^-1 (b - A x) written as
+// the FP64 preconditioned residual z, with the block partials of r.z and
+// r.zprev (flexible CG; zprev then takes z) for the PCG's beta.
+template <class T, int SH>
+__global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* __restrict__ x,
+                                                       const T* __restrict__ b,
+                                                       double* __restrict__ z,
+                                                       const double* __restrict__ rpcg,
+                                                       double* __restrict__ zprev,
+                                                       double* __restrict__ partial,
+                                                       const __grid_constant__ PartsParam PP) {
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  block_part(PP, L.blk, L.parts, L.np, sp, false);
+  __syncthreads();
+  double s0 = 0.0, s1 = 0.0;
+  TILE_LOOP(c, sp) {
+    const int g = sp.off + c;
+    const double zv = (double)fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
+    z[g] = zv;
+    const double rv = rpcg[g];
+    s0 = fma(rv, zv, s0);
+    if (zprev) {
+      s1 = fma(rv, zprev[g], s1);
+      zprev[g] = zv;
+    }
+  }
+  const double t0 = block_sum<NT>(s0, sh);
+  const double t1 = block_sum<NT>(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = t0;
+    partial[2 * blockIdx.x + 1] = t1;
   }
 }
 
@@ -717,6 +770,29 @@ void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
   k_relax0_u<T><<<nb + L.nublk, NT, 0, st>>>(L.view<T>(), nb, b, x);
   SSAMG_LAUNCH_CHECK();
 }
+#define SH_DISPATCH(shape, KCALL)                         \
+  switch (shape) {                                        \
+    case SH_U7: { constexpr int SHV = SH_U7; KCALL; } break;   \
+    case SH_U15: { constexpr int SHV = SH_U15; KCALL; } break; \
+    case SH_C27: { constexpr int SHV = SH_C27; KCALL; } break; \
+    case SH_UGEN: { constexpr int SHV = SH_UGEN; KCALL; } break; \
+    case SH_K7: { constexpr int SHV = SH_K7; KCALL; } break;   \
+    default: { constexpr int SHV = SH_CHECKED; KCALL; } break; \
+  }
+
+template <class T>
+void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaStream_t st) {
+  int nb = cdiv(L.N, NT);
+  k_relax0_u_first<T><<<nb + L.nublk, NT, 0, st>>>(L.view<T>(), nb, r64, b0, x);
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const double* rpcg,
+                        double* zprev, double* partial, cudaStream_t st) {
+  SH_DISPATCH(L.shape, (k_relax_final<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, z, rpcg,
+                                                                      zprev, partial, *L.pp)));
+  SSAMG_LAUNCH_CHECK();
+}
 template <class T>
 void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
   k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout, F.nblk, *F.pp);
@@ -728,15 +804,6 @@ void launch_uy(const Level& L, const T* x, cudaStream_t st) {
   k_uy<T><<<L.nublk, NT, 0, st>>>(L.view<T>(), x);
   SSAMG_LAUNCH_CHECK();
 }
-#define SH_DISPATCH(shape, KCALL)                         \
-  switch (shape) {                                        \
-    case SH_U7: { constexpr int SHV = SH_U7; KCALL; } break;   \
-    case SH_U15: { constexpr int SHV = SH_U15; KCALL; } break; \
-    case SH_C27: { constexpr int SHV = SH_C27; KCALL; } break; \
-    case SH_UGEN: { constexpr int SHV = SH_UGEN; KCALL; } break; \
-    case SH_K7: { constexpr int SHV = SH_K7; KCALL; } break;   \
-    default: { constexpr int SHV = SH_CHECKED; KCALL; } break; \
-  }
 
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
@@ -809,6 +876,9 @@ void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t 
   template void launch_relax0<T>(const Level&, const T*, T*, cudaStream_t);                \
   template void launch_relax0_u<T>(const Level&, const T*, T*, cudaStream_t);              \
   template void launch_prolong_u<T>(const Level&, const T*, const T*, T*, cudaStream_t);   \
+  template void launch_relax0_u_first<T>(const Level&, const double*, T*, T*, cudaStream_t); \
+  template void launch_relax_final<T>(const Level&, const T*, const T*, double*, const double*, \
+                                      double*, double*, cudaStream_t);                     \
   template void launch_uy<T>(const Level&, const T*, cudaStream_t);                        \
   template void launch_vtail<T>(const TailLevel<T>*, int, const double*, int, int, int,      \
                                 TailBarrier*, cudaStream_t);                               \
@@ -862,7 +932,12 @@ void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p,
                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
   k_pcg_dots_rz<<<nblk, NT, 0, st>>>(r, z, zprev, n, partial);
   SSAMG_LAUNCH_CHECK();
-  k_pcg_beta_fin<<<1, NT, 0, st>>>(partial, nblk, sc);
+  launch_pcg_beta_from_partials(z, p, n, partial, nblk, nblk, sc, st);
+}
+
+void launch_pcg_beta_from_partials(const double* z, double* p, long long n, const double* partial,
+                                   int npart, int nblk, PcgScalars* sc, cudaStream_t st) {
+  k_pcg_beta_fin<<<1, NT, 0, st>>>(partial, npart, sc);
   SSAMG_LAUNCH_CHECK();
   k_pcg_xpby<<<nblk, NT, 0, st>>>(z, p, n, sc);
   SSAMG_LAUNCH_CHECK();

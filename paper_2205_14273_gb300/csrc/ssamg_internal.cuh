@@ -99,7 +99,9 @@ static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 // Up to SSAMG_PARAM_PARTS part descriptors of a level passed by value as a
 // kernel parameter (constant bank): blocks find and stage their part without
 // a global-memory round trip.  Levels with more parts use the global copies.
-#define SSAMG_PARAM_PARTS 8
+#ifndef SSAMG_PARAM_PARTS
+#define SSAMG_PARAM_PARTS 1
+#endif
 struct PartsParam {
   int np;
   int inparam;
@@ -300,6 +302,13 @@ void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaSt
 // uy = U x
 template <class T>
 void launch_uy(const Level& L, const T* x, cudaStream_t st);
+// first pre-relaxation from the FP64 residual (b0 = (T) r) and last
+// post-relaxation into the FP64 z with the PCG's r.z partials (2 per block)
+template <class T>
+void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaStream_t st);
+template <class T>
+void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const double* rpcg,
+                        double* zprev, double* partial, cudaStream_t st);
 void launch_upcols(const Level& F, bool fp32, cudaStream_t st);
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
@@ -332,6 +341,8 @@ void launch_pcg_start(const double* r, const double* z, double* p, double* zprev
                       double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
 void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
+void launch_pcg_beta_from_partials(const double* z, double* p, long long n, const double* partial,
+                                   int npart, int nblk, PcgScalars* sc, cudaStream_t st);
 void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
                       PcgScalars* sc, cudaStream_t st);
 void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,

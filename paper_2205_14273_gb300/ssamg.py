@@ -96,6 +96,7 @@ _SIGS = {
     "ssamg_level_copy": (_i, [_vp, _i, _i, _i, _i, _vp, _ll]),
     "ssamg_spacings": (_i, [_vp, _dp, _dp]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
+    "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
 }
 
 
@@ -157,9 +158,18 @@ def _dptr(t) -> int:
     return t.data_ptr()
 
 
-def _ints(a) -> ctypes.Array:
-    a = np.ascontiguousarray(a, dtype=np.int32).ravel()
-    return (ctypes.c_int * len(a))(*a.tolist()) if len(a) else (ctypes.c_int * 1)()
+class _IntBuf:
+    """A contiguous int32 array kept alive while its pointer is in use."""
+
+    def __init__(self, a):
+        self.a = np.ascontiguousarray(a, dtype=np.int32).ravel()
+        if self.a.size == 0:
+            self.a = np.zeros(1, np.int32)
+        self._as_parameter_ = self.a.ctypes.data_as(_ip)
+
+
+def _ints(a) -> _IntBuf:
+    return _IntBuf(a)
 
 
 def default_params(**kw) -> Params:
@@ -348,6 +358,13 @@ class Solver:
         _check(lib().ssamg_level_copy(self.h, level, what, part, entry,
                                       out.ctypes.data_as(_vp), n), "level_copy")
         return out
+
+    def time_kernel(self, kernel: int, level: int = 0, reps: int = 50, stream=None) -> float:
+        """Mean microseconds per launch of one hot-path kernel (graph replay)."""
+        us = ctypes.c_double()
+        _check(lib().ssamg_time_kernel(self.h, kernel, level, reps, ctypes.byref(us),
+                                       _stream(stream)), "time_kernel")
+        return us.value
 
     def spacings(self, nparts: int):
         c = np.zeros(3 * nparts)
