@@ -187,13 +187,14 @@ def run_ours(args):
             "true_rel_res": verified["true_rel_res"],
             "levels": verified["num_levels"],
             "operator_complexity": verified["operator_complexity"],
+            "launches": int(verified["setup_kernel_launches"] + verified["solve_kernel_launches"]),
             "mdof_s": ws * N / (step_ms * 1e-3) / 1e6,
             "solve_mdof_s": ws * N / (statistics.median(solve_ms) * 1e-3) / 1e6,
             "wall_s": wall,
             "clocks": ck,
         }
 
-    # ---- dominant-kernel roofline: level-0 FP64 operator apply
+    # ---- dominant-kernel roofline (prolongation with U x, FP32 cycle)
     roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
 
     # ---- end to end through the C ABI with host buffers (matrix upload,
@@ -228,7 +229,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": head["clocks"],
     }
-    line["gpu_launches"] = count_launches(next(iter(solvers.values())), head["iterations"])
+    line["gpu_launches"] = head["launches"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
     if rank == 0:
@@ -237,51 +238,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def count_launches(sv, iters):
-    """Kernel launches of one setup + solve, counted from the hierarchy shape
-    (setup: per level interpolation, Galerkin, U product, diagonals; solve:
-    5 kernels per level and cycle plus the PCG kernels)."""
-    L = sv.num_levels()
-    nu = sum(1 for l in range(L) if sv.level_sizes(l)[1] > 0)
-    setup = 2 + 2 * (L - 1) + 7 * nu + L + 2 + 1 + 1
-    cycle = 5 * (L - 1) + 1 + 2
-    pcg = 2 + (cycle + 2 + 2 + 2) + iters * (cycle + 3 + 2 + 2)
-    return setup + pcg
-
-
 def kernel_roofline(S, sv, prob, dev, stream, args):
-    import torch
-    N = prob.n
+    """Roofline of the dominant kernel of the timed step.
+
+    The prolongation with U x (k_prolong_u) has the largest share of the
+    solve (one launch per level and cycle).  achieved = its algorithmic bytes
+    summed over the levels of one V-cycle / the summed launch durations, each
+    measured with CUDA events around graph replays of that launch on this
+    stream.  Bytes per level (FP32 cycle): x in + x out (8 N_l), coarse
+    correction (4 N_{l+1}), P weights (8 per fine point), coupling rows (12 per
+    row: pointer, result) and couplings (36 each: column, value, P row of the
+    column, x and two coarse values).
+    """
     peaks = read_peaks()
-    xs = torch.rand(N, dtype=torch.float64, device=dev)
-    ys = torch.empty_like(xs)
-    for _ in range(5):
-        sv.level_matvec(0, xs, ys)
-    reps = 50
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        sv.level_matvec(0, xs, ys)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    dt = e0.elapsed_time(e1) / reps * 1e-3
-    # algorithmic bytes: x, y, the variable diagonal (8 B each per cell) and
-    # 16 B per coupling (value + column) -- constant off-diagonals are scalars
-    nbytes = 24 * N + 16 * prob.nnz_u
-    flops = 2 * 7 * N + 2 * prob.nnz_u
-    fp64_peak = 1.25e12
+    L = sv.num_levels()
+    sizes = [sv.level_sizes(l) for l in range(L)]
+    tot_us = tot_b = 0.0
+    per_level = []
+    for l in range(L - 1):
+        us = sv.time_kernel(4, l, 50, stream)
+        N, nr, nnz = sizes[l]
+        Nc = sizes[l + 1][0]
+        nbytes = 8 * N + 4 * Nc + 8 * (N - Nc) + 12 * nr + 36 * nnz
+        tot_us += us
+        tot_b += nbytes
+        per_level.append(round(us, 2))
+    nl = L - 1
+    achieved = tot_b / (tot_us * 1e-6) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    # the FP64 level-0 operator apply + dot (the PCG's largest single launch)
+    us_spmv = sv.time_kernel(6, 0, 50, stream)
+    N0 = sizes[0][0]
+    flops = 2 * 8 * N0 + 2 * prob.nnz_u
     return {
-        "kernel": "level-0 FP64 SStruct operator apply (k_matvec)",
-        "bound": "alu",
-        "achieved": round(flops / dt / 1e12, 4),
-        "peak": fp64_peak / 1e12,
-        "unit": "TFLOP/s",
-        "frac": round(flops / dt / fp64_peak, 4),
+        "kernel": "k_prolong_u<float> (prolongation x + P e with U x row jobs), all levels of one V-cycle",
+        "bound": "hbm",
+        "achieved": round(achieved, 1),
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": round(achieved / peak, 4),
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
         "traffic": None,
-        "hbm_gbs": round(nbytes / dt / 1e9, 1),
-        "hbm_frac_of_measured": round(nbytes / dt / 1e9 / peaks.get("hbm_gbs", 6800.0), 4),
-        "us_per_launch": round(dt * 1e6, 3),
+        "bytes_per_launch": int(tot_b / nl),
+        "us_per_launch": round(tot_us / nl, 3),
+        "us_per_level": per_level,
+        "fp64_level0_operator": {
+            "kernel": "k_pcg_spmv_dot (q = A p and p.q, FP64, level 0)",
+            "bound": "alu", "unit": "TFLOP/s",
+            "achieved": round(flops / (us_spmv * 1e-6) / 1e12, 4),
+            "peak": 1.25, "peak_source": "nominal GB300 FP64; 1.255 measured by an FMA probe",
+            "frac": round(flops / (us_spmv * 1e-6) / 1.25e12, 4),
+            "us_per_launch": round(us_spmv, 2),
+            "hbm_gbs": round((24 * N0 + 16 * prob.nnz_u) / (us_spmv * 1e-6) / 1e9, 1)},
     }
 
 

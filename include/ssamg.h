@@ -121,6 +121,8 @@ typedef struct {
   int num_levels;
   long long coarse_size;
   double operator_complexity; /* sum of stored stencil+U entries over levels / level 0 */
+  long long setup_kernel_launches;  /* kernels launched by the last ssamg_setup */
+  long long solve_kernel_launches;  /* kernels run by the PCG of this right-hand side */
 } ssamg_stats;
 
 /* Fills *p with the defaults listed above. */

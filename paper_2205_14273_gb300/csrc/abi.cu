@@ -140,6 +140,7 @@ struct ssamg_solver_s {
   int nblk_red = 0;
   cudaStream_t cs = nullptr;  // capture stream
   GraphSet graphs;
+  long long setup_launches = 0, head_launches = 0, body_launches = 0;
   ~ssamg_solver_s() {
     graphs.reset();
     if (cs) cudaStreamDestroy(cs);
@@ -148,6 +149,8 @@ struct ssamg_solver_s {
     if (h_dbl) cudaFreeHost(h_dbl);
   }
 };
+
+thread_local long long g_ssamg_launches = 0;
 
 namespace {
 
@@ -632,17 +635,6 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     }
     L.shape = !unchecked ? (canon7 ? 5 : 0) : all27 ? 3 : all7 ? 1 : all15 ? 2 : 4;
   }
-  L.pp = std::make_shared<PartsParam>();
-  std::memset(L.pp.get(), 0, sizeof(PartsParam));
-  L.pp->np = np;
-  L.pp->inparam = np <= SSAMG_PARAM_PARTS;
-  if (L.pp->inparam) {
-    for (int p = 0; p <= np; ++p) {
-      L.pp->blk[p] = blk[p];
-      L.pp->fblk[p] = fblk[p];
-    }
-    for (int p = 0; p < np; ++p) L.pp->part[p] = L.dparts[p];
-  }
   SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
@@ -1124,7 +1116,9 @@ void build_pcg_graph(ssamg_solver s) {
   SSAMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
   // head, captured straight into g
   SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  long long c0 = g_ssamg_launches;
   enqueue_pcg_head(s, h, 1, s->cs);
+  s->head_launches = g_ssamg_launches - c0;
   cudaStreamCaptureStatus cst;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
@@ -1142,7 +1136,9 @@ void build_pcg_graph(ssamg_solver s) {
   SSAMG_CUDA(cudaGraphAddNode(&cnode, g, tail.data(), nullptr, tail.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  c0 = g_ssamg_launches;
   enqueue_pcg_body(s, h, 1, s->cs);
+  s->body_launches = g_ssamg_launches - c0;
   SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
   SSAMG_CUDA(cudaGraphInstantiate(&s->graphs.pcg, g, 0));
   cudaGraphDestroy(g);
@@ -1161,12 +1157,16 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
     SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));
   } else {
+    long long c0 = g_ssamg_launches;
     enqueue_pcg_head(s, 0, 0, st);
+    s->head_launches = g_ssamg_launches - c0;
     for (;;) {
       SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
       SSAMG_CUDA(cudaStreamSynchronize(st));
       if (s->h_sc->done) break;
+      c0 = g_ssamg_launches;
       enqueue_pcg_body(s, 0, 0, st);
+      s->body_launches = g_ssamg_launches - c0;
     }
   }
   if (s->tail_bar) {
@@ -1180,6 +1180,8 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
   const PcgScalars& r = *s->h_sc;
   if (stats) {
     stats->iterations = r.iter;
+    stats->setup_kernel_launches = s->setup_launches;
+    stats->solve_kernel_launches = s->head_launches + (long long)(r.iter > 0 ? r.iter - 1 : 0) * s->body_launches;
     stats->converged = r.status == 0 && r.rr <= r.tol2bb;
     stats->rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
     stats->num_levels = (int)s->lev.size();
@@ -1208,7 +1210,9 @@ extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
   if (!A->assembled) return SSAMG_ERR_STATE;
   API_BEGIN
   s->A = A;
+  const long long c0 = g_ssamg_launches;
   build_hierarchy(s, (cudaStream_t)stream);
+  s->setup_launches = g_ssamg_launches - c0;
   return SSAMG_OK;
   API_END
 }

@@ -32,43 +32,26 @@ __device__ __forceinline__ int find_part_cell(const int* __restrict__ cs, int np
   return find_part(cs, np, g);
 }
 
-// Part of this block (cell tiles, or fine-point tiles when `fine`), staged in
-// shared memory from the kernel parameter when the level has few parts, else
-// from global memory.  All threads call; a barrier follows in the caller.
-__device__ __forceinline__ int block_part(const PartsParam& PP, const int* __restrict__ gblk,
-                                          const DPart* __restrict__ gparts, int np, DPart& sm,
-                                          bool fine) {
-  int p;
-  if (PP.inparam) {
-    const int* b = fine ? PP.fblk : PP.blk;
-    p = 0;
-    while (p + 1 < PP.np && b[p + 1] <= (int)blockIdx.x) ++p;
-    const int* s = reinterpret_cast<const int*>(&PP.part[p]);
-    int* d = reinterpret_cast<int*>(&sm);
-    constexpr int nw = sizeof(DPart) / 4;
-    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = s[t];
-  } else {
-    p = find_part(gblk, np, blockIdx.x);
-    const int* s = reinterpret_cast<const int*>(gparts + p);
-    int* d = reinterpret_cast<int*>(&sm);
-    constexpr int nw = sizeof(DPart) / 4;
-    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
-  }
+// Part of this block (cell tiles, or fine-point tiles when `fine` -- the
+// block table passed is then the fine-point one), staged in shared memory
+// from the level's descriptor array.  All threads call; a barrier follows in
+// the caller.
+__device__ __forceinline__ int block_part(const int* __restrict__ gblk,
+                                          const DPart* __restrict__ gparts, int np, DPart& sm) {
+  const int p = find_part(gblk, np, blockIdx.x);
+  const int* s = reinterpret_cast<const int*>(gparts + p);
+  int* d = reinterpret_cast<int*>(&sm);
+  constexpr int nw = sizeof(DPart) / 4;
+  for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
   return p;
 }
 
-// The same part of a second level (same part index), into shared memory.
-__device__ __forceinline__ void part_of(const PartsParam& PP, const DPart* __restrict__ gparts,
-                                        int p, DPart& sm) {
+// Part p of a second level, into shared memory.
+__device__ __forceinline__ void part_of(const DPart* __restrict__ gparts, int p, DPart& sm) {
+  const int* s = reinterpret_cast<const int*>(gparts + p);
   int* d = reinterpret_cast<int*>(&sm);
   constexpr int nw = sizeof(DPart) / 4;
-  if (PP.inparam) {
-    const int* s = reinterpret_cast<const int*>(&PP.part[p]);
-    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = s[t];
-  } else {
-    const int* s = reinterpret_cast<const int*>(gparts + p);
-    for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
-  }
+  for (int t = threadIdx.x; t < nw; t += blockDim.x) d[t] = __ldg(s + t);
 }
 
 // Copy one part descriptor into shared memory (all threads of the block call).

@@ -56,10 +56,9 @@ __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__
 // r = b - A x
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __restrict__ x,
-                                                    const T* __restrict__ b, T* __restrict__ r,
-                                                    const __grid_constant__ PartsParam PP) {
+                                                    const T* __restrict__ b, T* __restrict__ r) {
   __shared__ DPart sp;
-  block_part(PP, L.blk, L.parts, L.np, sp, false);
+  block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
@@ -70,10 +69,9 @@ __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __r
 // xo = x + omega M^-1 (b - A x)
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __restrict__ x,
-                                                 const T* __restrict__ b, T* __restrict__ xo,
-                                                 const __grid_constant__ PartsParam PP) {
+                                                 const T* __restrict__ b, T* __restrict__ xo) {
   __shared__ DPart sp;
-  block_part(PP, L.blk, L.parts, L.np, sp, false);
+  block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
@@ -89,12 +87,11 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
                                                        const T* __restrict__ b,
                                                        double* __restrict__ z,
                                                        const double* __restrict__ rpcg,
-                                                       double* __restrict__ zprev,
-                                                       double* __restrict__ partial,
-                                                       const __grid_constant__ PartsParam PP) {
+                                                       double* __restrict__ zprev, int flex,
+                                                       double* __restrict__ partial) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  block_part(PP, L.blk, L.parts, L.np, sp, false);
+  block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   double s0 = 0.0, s1 = 0.0;
   TILE_LOOP(c, sp) {
@@ -103,7 +100,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
     z[g] = zv;
     const double rv = rpcg[g];
     s0 = fma(rv, zv, s0);
-    if (zprev) {
+    if (flex) {
       s1 = fma(rv, zprev[g], s1);
       zprev[g] = zv;
     }
@@ -120,11 +117,11 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
 // fine points beside it along d* (weights PE of the west one, PW of the east).
 template <class T>
 __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
-                                                 const T* __restrict__ r, T* __restrict__ bc, const __grid_constant__ PartsParam PF, const __grid_constant__ PartsParam PC) {
+                                                 const T* __restrict__ r, T* __restrict__ bc) {
   __shared__ DPart fp;
   __shared__ DPart cp;
-  int p = block_part(PC, C.blk, C.parts, C.np, cp, false);
-  part_of(PF, F.parts, p, fp);
+  int p = block_part(C.blk, C.parts, C.np, cp);
+  part_of(F.parts, p, fp);
   __syncthreads();
   TILE_LOOP(cc, cp) {
     int I[3];
@@ -159,7 +156,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
                                                   const T* __restrict__ xin, T* __restrict__ xout,
-                                                  int nb, const __grid_constant__ PartsParam PP) {
+                                                  int nb) {
   __shared__ DPart fp;
   if ((int)blockIdx.x >= nb) {
     u_row_job(F, blockIdx.x - nb, [&](int col, int q) {
@@ -171,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
     });
     return;
   }
-  int p = block_part(PP, F.blk, F.parts, F.np, fp, false);
+  int p = block_part(F.blk, F.parts, F.np, fp);
   __syncthreads();
   TILE_LOOP(c, fp) {
     int i, j, k;
@@ -188,9 +185,9 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
 // x += P ec, one fine cell per thread.
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
-                                                T* __restrict__ x, const __grid_constant__ PartsParam PP) {
+                                                T* __restrict__ x) {
   __shared__ DPart fp;
-  int p = block_part(PP, F.blk, F.parts, F.np, fp, false);
+  int p = block_part(F.blk, F.parts, F.np, fp);
   __syncthreads();
   TILE_LOOP(c, fp) {
     int i, j, k;
@@ -458,9 +455,9 @@ __global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ ou
 }
 
 __global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* __restrict__ x,
-                                               double* __restrict__ y, int padded, const __grid_constant__ PartsParam PP) {
+                                               double* __restrict__ y, int padded) {
   __shared__ DPart sp;
-  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -489,10 +486,10 @@ __device__ __forceinline__ void finish_sums(const double* __restrict__ partial, 
 template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
                                                  const double* __restrict__ x, double* __restrict__ r,
-                                                 double* __restrict__ partial, const __grid_constant__ PartsParam PP) {
+                                                 double* __restrict__ partial) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   double bb = 0.0, rr = 0.0;
   TILE_LOOP(c, sp) {
@@ -531,14 +528,14 @@ __global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ 
 __global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
                                                   const double* __restrict__ z,
                                                   double* __restrict__ p, double* __restrict__ zprev,
-                                                  long long n, double* __restrict__ partial) {
+                                                  int flex, long long n, double* __restrict__ partial) {
   __shared__ double sh[NT / 32];
   double s = 0.0;
 #pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
     double zv = z[g];
     p[g] = zv;
-    if (zprev) zprev[g] = zv;
+    if (flex) zprev[g] = zv;
     s = fma(r[g], zv, s);
   }
   double t = block_sum<NT>(s, sh);
@@ -566,15 +563,15 @@ __global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__
 // partial (r.z, r.zprev) for beta; zprev takes the new z (flexible CG)
 __global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r,
                                                     const double* __restrict__ z,
-                                                    double* __restrict__ zprev, long long n,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ zprev, int flex,
+                                                    long long n, double* __restrict__ partial) {
   __shared__ double sh[NT / 32];
   double s0 = 0.0, s1 = 0.0;
 #pragma unroll 4
   for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
     double rv = r[g], zv = z[g];
     s0 = fma(rv, zv, s0);
-    if (zprev) {
+    if (flex) {
       s1 = fma(rv, zprev[g], s1);
       zprev[g] = zv;
     }
@@ -616,10 +613,10 @@ __global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p,
 template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
                                                      double* __restrict__ q,
-                                                     double* __restrict__ partial, const __grid_constant__ PartsParam PP) {
+                                                     double* __restrict__ partial) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int pt = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int pt = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   double s = 0.0;
   TILE_LOOP(c, sp) {
@@ -705,9 +702,9 @@ __global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ 
 __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
                                                       const double* __restrict__ lam,
                                                       const double* __restrict__ x,
-                                                      double* __restrict__ dcoef, long long N, const __grid_constant__ PartsParam PP) {
+                                                      double* __restrict__ dcoef, long long N) {
   __shared__ DPart sp;
-  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -789,13 +786,16 @@ void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaS
 template <class T>
 void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const double* rpcg,
                         double* zprev, double* partial, cudaStream_t st) {
+  // zprev may be null (no flexible CG): pass a valid buffer and a flag
+  const int flex = zprev != nullptr;
+  double* zp = flex ? zprev : z;
   SH_DISPATCH(L.shape, (k_relax_final<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, z, rpcg,
-                                                                      zprev, partial, *L.pp)));
+                                                                      zp, flex, partial)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
-  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout, F.nblk, *F.pp);
+  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout, F.nblk);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -807,23 +807,23 @@ void launch_uy(const Level& L, const T* x, cudaStream_t st) {
 
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (k_residual<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r, *L.pp)));
+  SH_DISPATCH(L.shape, (k_residual<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (k_relax<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo, *L.pp)));
+  SH_DISPATCH(L.shape, (k_relax<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st) {
-  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc, *F.pp, *Cl.pp);
+  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st) {
   (void)Cl;
-  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x, *F.pp);
+  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -902,7 +902,7 @@ void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st)
 }
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0, *L.pp);
+  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -914,7 +914,7 @@ int reduce_blocks(long long n) {
 void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
                      PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial, *L.pp)));
+  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial)));
   SSAMG_LAUNCH_CHECK();
   k_pcg_init_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
@@ -922,7 +922,8 @@ void launch_pcg_init(const Level& L, const double* b, const double* x, double* r
 
 void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
                       double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
-  k_pcg_start<<<nblk, NT, 0, st>>>(r, z, p, zprev, n, partial);
+  // zprev may be null (no flexible CG): pass a valid buffer and a flag
+  k_pcg_start<<<nblk, NT, 0, st>>>(r, z, p, zprev ? zprev : p, zprev != nullptr, n, partial);
   SSAMG_LAUNCH_CHECK();
   k_pcg_start_fin<<<1, NT, 0, st>>>(partial, nblk, sc);
   SSAMG_LAUNCH_CHECK();
@@ -930,7 +931,7 @@ void launch_pcg_start(const double* r, const double* z, double* p, double* zprev
 
 void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
-  k_pcg_dots_rz<<<nblk, NT, 0, st>>>(r, z, zprev, n, partial);
+  k_pcg_dots_rz<<<nblk, NT, 0, st>>>(r, z, zprev ? zprev : p, zprev != nullptr, n, partial);
   SSAMG_LAUNCH_CHECK();
   launch_pcg_beta_from_partials(z, p, n, partial, nblk, nblk, sc, st);
 }
@@ -946,7 +947,7 @@ void launch_pcg_beta_from_partials(const double* z, double* p, long long n, cons
 void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
                       PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, p, st);
-  SH_DISPATCH(L.shape, (k_pcg_spmv_dot<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial, *L.pp)));
+  SH_DISPATCH(L.shape, (k_pcg_spmv_dot<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial)));
   SSAMG_LAUNCH_CHECK();
   k_pcg_alpha_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
@@ -964,7 +965,7 @@ void launch_pcg_update(const double* p, const double* q, double* x, double* r, l
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
                           double* partial, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial, *L.pp)));
+  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial)));
   SSAMG_LAUNCH_CHECK();
   k_true_res_fin<<<1, NT, 0, st>>>(partial, L.nblk, out);
   SSAMG_LAUNCH_CHECK();
@@ -972,7 +973,7 @@ void launch_true_residual(const Level& L, const double* b, const double* x, doub
 
 void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
                           cudaStream_t st) {
-  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N, *L.pp);
+  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -14,10 +14,10 @@ constexpr int NT = SSAMG_BLOCK;
 // along d) (Section 3.1).  Block partials, then one block per part sums them
 // in a fixed order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __restrict__ partial, const __grid_constant__ PartsParam PP) {
+__global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __restrict__ partial) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   double s0 = 0, s1 = 0, s2 = 0;
   TILE_LOOP(c, sp) {
@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(NT) k_wfinal(const int* __restrict__ blk,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __restrict__ Pw,
                                                double* __restrict__ Pe, float* __restrict__ Pw32,
-                                               float* __restrict__ Pe32, const __grid_constant__ PartsParam PP) {
+                                               float* __restrict__ Pe32) {
   __shared__ DPart sp;
-  int p = block_part(PP, L.fblk, L.parts, L.np, sp, true);
+  int p = block_part(L.fblk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP_FINE(F, sp) {
     const int d = sp.dstar;
@@ -129,11 +129,11 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelView<double> C,
                                                    double* __restrict__ ccoef,
-                                                   float* __restrict__ ccoef32, const __grid_constant__ PartsParam PF, const __grid_constant__ PartsParam PC) {
+                                                   float* __restrict__ ccoef32) {
   __shared__ DPart fp;
   __shared__ DPart cp;
-  int p = block_part(PC, C.blk, C.parts, C.np, cp, false);
-  part_of(PF, F.parts, p, fp);
+  int p = block_part(C.blk, C.parts, C.np, cp);
+  part_of(F.parts, p, fp);
   __syncthreads();
   TILE_LOOP(cc, cp) {
     int I[3];
@@ -405,9 +405,9 @@ __global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ 
 // K5: diagonal of omega M^-1 (Section 3.4).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, double factor,
-                                             double* __restrict__ dinv, float* __restrict__ dinv32, const __grid_constant__ PartsParam PP) {
+                                             double* __restrict__ dinv, float* __restrict__ dinv32) {
   __shared__ DPart sp;
-  int p = block_part(PP, L.blk, L.parts, L.np, sp, false);
+  int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -587,7 +587,7 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Launchers
 // ---------------------------------------------------------------------------
 void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st) {
-  k_wsum<<<L.nblk, NT, 0, st>>>(L.view<double>(), partial, *L.pp);
+  k_wsum<<<L.nblk, NT, 0, st>>>(L.view<double>(), partial);
   SSAMG_LAUNCH_CHECK();
   k_wfinal<<<L.np, NT, 0, st>>>(L.d_blk, partial, c_out);
   SSAMG_LAUNCH_CHECK();
@@ -596,13 +596,13 @@ void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st
 void launch_interp(const Level& F, bool fp32, cudaStream_t st) {
   if (F.nfblk == 0) return;
   k_interp<<<F.nfblk, NT, 0, st>>>(F.view<double>(), F.Pw, F.Pe, fp32 ? F.Pw32 : nullptr,
-                                   fp32 ? F.Pe32 : nullptr, *F.pp);
+                                   fp32 ? F.Pe32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st) {
   k_rap_struct<<<Cl.nblk, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
-                                       fp32 ? Cl.coef32 : nullptr, *F.pp, *Cl.pp);
+                                       fp32 ? Cl.coef32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -652,7 +652,7 @@ void launch_umap_level0(const Level& L, cudaStream_t st) {
 }
 
 void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st) {
-  k_dinv<<<L.nblk, NT, 0, st>>>(L.view<double>(), relax, factor, L.dinv, fp32 ? L.dinv32 : nullptr, *L.pp);
+  k_dinv<<<L.nblk, NT, 0, st>>>(L.view<double>(), relax, factor, L.dinv, fp32 ? L.dinv32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 

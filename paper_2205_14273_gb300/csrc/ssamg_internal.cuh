@@ -96,20 +96,6 @@ struct DPart {
 };
 static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 
-// Up to SSAMG_PARAM_PARTS part descriptors of a level passed by value as a
-// kernel parameter (constant bank): blocks find and stage their part without
-// a global-memory round trip.  Levels with more parts use the global copies.
-#ifndef SSAMG_PARAM_PARTS
-#define SSAMG_PARAM_PARTS 1
-#endif
-struct PartsParam {
-  int np;
-  int inparam;
-  int blk[SSAMG_PARAM_PARTS + 1];
-  int fblk[SSAMG_PARAM_PARTS + 1];
-  DPart part[SSAMG_PARAM_PARTS];
-};
-
 // Scalars of one PCG solve (device memory).
 struct PcgScalars {
   double tol, bb, rr, rz, pq, alpha, beta, tol2bb;
@@ -206,7 +192,6 @@ struct Level {
   int nblk = 0, nfblk = 0;
   int cpt = 1;
   int shape = 0;  // StencilShape of the level's operator apply
-  std::shared_ptr<PartsParam> pp;  // host copy of the kernel-parameter descriptors
   double* coef = nullptr;
   float* coef32 = nullptr;
   long long ncoef = 0;
@@ -266,7 +251,14 @@ struct SsamgError {
                                                            cudaGetErrorString(e_)};         \
   } while (0)
 
-#define SSAMG_LAUNCH_CHECK() SSAMG_CUDA(cudaGetLastError())
+// Every kernel launch of the library passes through this check, which also
+// counts it (per host thread) for the launch statistics.
+extern thread_local long long g_ssamg_launches;
+#define SSAMG_LAUNCH_CHECK()       \
+  do {                             \
+    ++g_ssamg_launches;            \
+    SSAMG_CUDA(cudaGetLastError()); \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels_*.cu)

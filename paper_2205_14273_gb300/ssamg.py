@@ -49,7 +49,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("num_levels", ctypes.c_int), ("coarse_size", ctypes.c_longlong),
-                ("operator_complexity", ctypes.c_double)]
+                ("operator_complexity", ctypes.c_double),
+                ("setup_kernel_launches", ctypes.c_longlong),
+                ("solve_kernel_launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
