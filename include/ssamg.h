@@ -199,6 +199,33 @@ int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, v
  * Section 3.1 (W = +inf encoded as HUGE_VAL). */
 int ssamg_spacings(ssamg_solver s, double* c, double* W);
 
+/* Blocks whose partial sums fit the static scratch of
+ * ssamg_coupling_sums_noalloc: 3 doubles each, 1.5 MiB of device memory.
+ * A level launch covers 1024 cells per block when the level has 300,000
+ * cells or more (256 below), so levels of up to 67,108,864 cells fit. */
+#define SSAMG_NOALLOC_MAX_BLOCKS 65536
+
+/* Allocation-free form of the per-part coupling sums c of Section 3.1
+ * (sum over the part's cells of sign(a_C) times minus the entries that move
+ * along dimension d), for level `level` of a set-up hierarchy.  The paper has
+ * no counterpart: this variant exists so that the sums can be taken inside a
+ * captured CUDA graph, with no memory allocation and no synchronisation.
+ *   c_dev  device, n_parts(level) x 3 doubles, caller-owned; on level 0 it
+ *          receives the values ssamg_spacings reports, bit for bit.
+ *   stream stream the two kernels are enqueued on; the call returns without
+ *          waiting.
+ * Block partials go to one fixed static device array of
+ * SSAMG_NOALLOC_MAX_BLOCKS x 3 doubles.  A level that needs more blocks is
+ * rejected with SSAMG_ERR_UNSUPPORTED (the message in ssamg_last_error
+ * gives both counts) before anything is enqueued.  Nothing in the scratch
+ * needs to start at zero: every block writes its own partials before the
+ * final sums read them.  ssamg_setup resolves the scratch address once per
+ * device (outside any capture); later calls make no CUDA runtime call that
+ * is illegal during stream capture.  The scratch is shared by every solver
+ * on the device: two calls that may run at the same time (streams with no
+ * ordering between them, or host threads) race on it and give wrong sums. */
+int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* stream);
+
 /* Diagnostic timing of one hot-path kernel on `level`: `reps` launches are
  * captured into a CUDA graph and replayed between CUDA events on `stream`
  * (after one warm-up replay); *us_per_launch receives the mean time per

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 
 #include "ssamg_internal.cuh"
@@ -151,6 +152,22 @@ struct ssamg_solver_s {
 };
 
 thread_local long long g_ssamg_launches = 0;
+
+// Address of the static coupling-sum scratch per device, resolved by setup
+// (outside any stream capture) so that the allocation-free entry makes no
+// capture-illegal runtime call.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_scratch[kMaxDevices] = {};
+
+double* noalloc_scratch() {
+  int dev = 0;
+  SSAMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "device index above 63"};
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_scratch[dev]) g_noalloc_scratch[dev] = wsum_static_scratch();
+  return g_noalloc_scratch[dev];
+}
 
 namespace {
 
@@ -1210,6 +1227,7 @@ extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
   if (!A->assembled) return SSAMG_ERR_STATE;
   API_BEGIN
   s->A = A;
+  noalloc_scratch();
   const long long c0 = g_ssamg_launches;
   build_hierarchy(s, (cudaStream_t)stream);
   s->setup_launches = g_ssamg_launches - c0;
@@ -1399,6 +1417,25 @@ extern "C" int ssamg_spacings(ssamg_solver s, double* c, double* W) {
   if (c) std::copy(s->c.begin(), s->c.end(), c);
   if (W) std::copy(s->W.begin(), s->W.end(), W);
   return SSAMG_OK;
+}
+
+extern "C" int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev,
+                                           void* stream) {
+  if (!s || !c_dev) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  API_BEGIN
+  argcheck(level >= 0 && level < (int)s->lev.size(), "level out of range");
+  const Level& L = s->lev[level];
+  if (L.nblk > SSAMG_NOALLOC_MAX_BLOCKS) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg,
+                  "coupling sums of level %d need %d blocks of scratch; the static scratch holds %d",
+                  level, L.nblk, SSAMG_NOALLOC_MAX_BLOCKS);
+    throw SsamgError{SSAMG_ERR_UNSUPPORTED, msg};
+  }
+  launch_wsum(L, noalloc_scratch(), c_dev, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
 }
 
 // Times one hot-path kernel: `reps` launches captured into a CUDA graph,

@@ -586,6 +586,16 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Block partials of the allocation-free coupling sums: one triple per block
+// of a level launch, every slot written before it is read.
+static __device__ __align__(256) double g_wsum_scratch[3 * SSAMG_NOALLOC_MAX_BLOCKS];
+
+double* wsum_static_scratch() {
+  void* p = nullptr;
+  SSAMG_CUDA(cudaGetSymbolAddress(&p, g_wsum_scratch));
+  return static_cast<double*>(p);
+}
+
 void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st) {
   k_wsum<<<L.nblk, NT, 0, st>>>(L.view<double>(), partial);
   SSAMG_LAUNCH_CHECK();

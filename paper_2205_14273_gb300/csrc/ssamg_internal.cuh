@@ -265,6 +265,9 @@ extern thread_local long long g_ssamg_launches;
 // ---------------------------------------------------------------------------
 // setup
 void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st);
+// Device address of the static block-partial scratch of the allocation-free
+// coupling sums (SSAMG_NOALLOC_MAX_BLOCKS x 3 doubles) on the current device.
+double* wsum_static_scratch();
 void launch_interp(const Level& F, bool fp32, cudaStream_t st);
 void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st);
 void launch_umark(const Level& F, const Level& Cl, int* marker, cudaStream_t st);

@@ -97,6 +97,7 @@ _SIGS = {
                                ctypes.POINTER(_ll)]),
     "ssamg_level_copy": (_i, [_vp, _i, _i, _i, _i, _vp, _ll]),
     "ssamg_spacings": (_i, [_vp, _dp, _dp]),
+    "ssamg_coupling_sums_noalloc": (_i, [_vp, _i, _vp, _vp]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
 }
@@ -374,6 +375,12 @@ class Solver:
         _check(lib().ssamg_spacings(self.h, c.ctypes.data_as(_dp), W.ctypes.data_as(_dp)),
                "spacings")
         return c.reshape(nparts, 3), W.reshape(nparts, 3)
+
+    def coupling_sums_noalloc(self, level: int, c, stream=None):
+        """Per-part coupling sums of `level` into the device tensor c (n_parts
+        x 3 doubles), with no allocation or synchronisation (stream-ordered)."""
+        _check(lib().ssamg_coupling_sums_noalloc(self.h, level, _dptr(c), _stream(stream)),
+               "coupling_sums_noalloc")
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
