@@ -111,6 +111,9 @@ typedef struct {
   int use_graph;       /* 1: run the PCG iteration loop as one CUDA graph */
   int use_tail;        /* 1: run the levels of at most 8192 cells (<= 8 parts) in one single-block
                           launch (default 0: one launch per level and step is faster on GB300) */
+  int use_pdl;         /* 1 (default): launch the solve's kernels with programmatic dependent
+                          launch, so that each kernel is scheduled, and stages its part
+                          descriptors, while its predecessor still runs; 0: plain launches */
 } ssamg_params;
 
 typedef struct {

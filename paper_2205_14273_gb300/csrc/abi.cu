@@ -152,6 +152,16 @@ struct ssamg_solver_s {
 };
 
 thread_local long long g_ssamg_launches = 0;
+thread_local int g_ssamg_pdl = 0;
+
+// Enables programmatic dependent launch for the solve kernels an entry point
+// enqueues (when the solver's parameters ask for it), and restores the
+// previous setting on exit.
+struct PdlScope {
+  int old;
+  explicit PdlScope(int on) : old(g_ssamg_pdl) { g_ssamg_pdl = on; }
+  ~PdlScope() { g_ssamg_pdl = old; }
+};
 
 // Address of the static coupling-sum scratch per device, resolved by setup
 // (outside any stream capture) so that the allocation-free entry makes no
@@ -505,6 +515,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->flexible = 0;
   p->use_graph = 1;
   p->use_tail = 0;
+  p->use_pdl = 1;
 }
 
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
@@ -1241,6 +1252,7 @@ extern "C" int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs,
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -1264,6 +1276,7 @@ extern "C" int ssamg_solve_host(ssamg_solver s, const double* b, double* x, int 
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -1291,6 +1304,7 @@ extern "C" int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const d
   if (!s || !lambda || !x || !dcoef) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   launch_coef_gradient(s->lev[0], lambda, x, dcoef, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1301,6 +1315,7 @@ extern "C" int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, con
   if (!s || !g || !lambda || !x || !dg) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1310,6 +1325,7 @@ extern "C" int ssamg_precondition(ssamg_solver s, const double* r, double* z, vo
   if (!s || !r || !z) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   vcycle(s, r, z, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1321,6 +1337,7 @@ extern "C" int ssamg_level_matvec(ssamg_solver s, int level, const double* x, do
   if (!s->ready) return SSAMG_ERR_STATE;
   if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   launch_matvec(s->lev[level], x, y, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1448,6 +1465,7 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
   if (level < 0 || level > Lc || ((kernel == 3 || kernel == 4) && level >= Lc)) return SSAMG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
   if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
   Level& L = s->lev[level];
   const bool f = s->prm.precision == 1;

@@ -17,6 +17,20 @@
        c = ((int)blockIdx.x - (P).fblk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;       \
        c##_m < (P).cpt && c < (P).nfine; ++c##_m, c += SSAMG_BLOCK)
 
+// Programmatic dependent launch.  The solve's kernels are launched with
+// programmatic stream serialisation: a kernel may be scheduled while its
+// predecessor in the stream is still running, stages what setup wrote (block
+// tables, part descriptors; host copies only), and then waits in pdl_wait()
+// until the predecessor has completed and its writes are visible, before it
+// touches any vector of the solve.  Since every kernel waits before it
+// completes, completion is transitive down the stream.  pdl_trigger() lets
+// the successor be scheduled once every block of this grid has started.
+// Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Part owning block b of a launch whose per-part block starts are blk[0..np].
 __device__ __forceinline__ int find_part(const int* __restrict__ blk, int np, int b) {
   int lo = 0, hi = np - 1;

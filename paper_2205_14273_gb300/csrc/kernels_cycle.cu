@@ -1,6 +1,8 @@
 // V(1,1)-cycle kernels (Section 3.4 relaxation, Eq. relax0; Section 3.2
 // restriction R = P^T and prolongation), the FP64 PCG vector kernels
 // (Section 4) and the coefficient-gradient kernels of the adjoint solve.
+#include <utility>
+
 #include "kernels_common.cuh"
 
 namespace {
@@ -13,6 +15,8 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 template <class T>
 __global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict__ b,
                          T* __restrict__ x) {
+  pdl_trigger();
+  pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < N) x[g] = dinv[g] * b[g];
 }
@@ -21,6 +25,8 @@ __global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict_
 template <class T>
 __global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T* __restrict__ b,
                                                  T* __restrict__ x) {
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < nb) {
     int g = blockIdx.x * NT + threadIdx.x;
     if (g < L.N) x[g] = L.dinv[g] * b[g];
@@ -35,6 +41,8 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
                                                        const double* __restrict__ r64,
                                                        T* __restrict__ b0, T* __restrict__ x) {
+  pdl_trigger();
+  pdl_wait();
   if ((int)blockIdx.x < nb) {
     int g = blockIdx.x * NT + threadIdx.x;
     if (g < L.N) {
@@ -50,6 +58,8 @@ __global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
 // uy = U x (row jobs only)
 template <class T>
 __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__ x) {
+  pdl_trigger();
+  pdl_wait();
   u_row_job(L, blockIdx.x, [&](int col, int) { return x[col]; });
 }
 
@@ -57,9 +67,11 @@ __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __restrict__ x,
                                                     const T* __restrict__ b, T* __restrict__ r) {
+  pdl_trigger();
   __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
     r[g] = b[g] - apply_A_sh<SH>(L, sp, x, c);
@@ -70,9 +82,11 @@ __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __r
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __restrict__ x,
                                                  const T* __restrict__ b, T* __restrict__ xo) {
+  pdl_trigger();
   __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
     xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
@@ -89,10 +103,12 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
                                                        const double* __restrict__ rpcg,
                                                        double* __restrict__ zprev, int flex,
                                                        double* __restrict__ partial) {
+  pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   double s0 = 0.0, s1 = 0.0;
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
@@ -118,11 +134,13 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
 template <class T>
 __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
                                                  const T* __restrict__ r, T* __restrict__ bc) {
+  pdl_trigger();
   __shared__ DPart fp;
   __shared__ DPart cp;
   int p = block_part(C.blk, C.parts, C.np, cp);
   part_of(F.parts, p, fp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(cc, cp) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
@@ -157,8 +175,10 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
                                                   const T* __restrict__ xin, T* __restrict__ xout,
                                                   int nb) {
+  pdl_trigger();
   __shared__ DPart fp;
   if ((int)blockIdx.x >= nb) {
+    pdl_wait();
     u_row_job(F, blockIdx.x - nb, [&](int col, int q) {
       T v = xin[col];
       int j0 = F.u_pj[2 * q], j1 = F.u_pj[2 * q + 1];
@@ -170,6 +190,7 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
   }
   int p = block_part(F.blk, F.parts, F.np, fp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, fp) {
     int i, j, k;
     cell_coords(fp, c, i, j, k);
@@ -186,9 +207,11 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
                                                 T* __restrict__ x) {
+  pdl_trigger();
   __shared__ DPart fp;
   int p = block_part(F.blk, F.parts, F.np, fp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, fp) {
     int i, j, k;
     cell_coords(fp, c, i, j, k);
@@ -207,6 +230,8 @@ __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restr
 template <class T>
 __global__ void k_coarse_solve(int n, const double* __restrict__ Lg, const T* __restrict__ b,
                                T* __restrict__ x, int staged) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ double sm[];
   double* y = sm;
   const double* Lf = Lg;
@@ -411,6 +436,8 @@ __global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ l
 template <class T>
 __global__ void k_coarse_apply(int n, const double* __restrict__ inv, const T* __restrict__ b,
                                T* __restrict__ x) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ double sb[];
   for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = (double)b[i];
   __syncthreads();
@@ -446,19 +473,25 @@ __global__ void k_coarse_inverse(int n, const double* __restrict__ Lf, double* _
 }
 
 __global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, int n) {
+  pdl_trigger();
+  pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (float)in[g];
 }
 __global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ out, int n) {
+  pdl_trigger();
+  pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (double)in[g];
 }
 
 __global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* __restrict__ x,
                                                double* __restrict__ y, int padded) {
+  pdl_trigger();
   __shared__ DPart sp;
   int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
@@ -487,10 +520,12 @@ template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
                                                  const double* __restrict__ x, double* __restrict__ r,
                                                  double* __restrict__ partial) {
+  pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
   int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   double bb = 0.0, rr = 0.0;
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -512,6 +547,8 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
 
 __global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ partial, int nblk,
                                                      PcgScalars* sc) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double out[2];
   finish_sums<2>(partial, nblk, out);
   if (threadIdx.x == 0) {
@@ -529,6 +566,8 @@ __global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
                                                   const double* __restrict__ z,
                                                   double* __restrict__ p, double* __restrict__ zprev,
                                                   int flex, long long n, double* __restrict__ partial) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double sh[NT / 32];
   double s = 0.0;
 #pragma unroll 4
@@ -549,6 +588,8 @@ __device__ __forceinline__ void set_continue(PcgScalars* sc, cudaGraphConditiona
 
 __global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__ partial, int nblk,
                                                       PcgScalars* sc) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double out[1];
   finish_sums<1>(partial, nblk, out);
   if (threadIdx.x == 0 && !sc->done) {
@@ -565,6 +606,8 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r
                                                     const double* __restrict__ z,
                                                     double* __restrict__ zprev, int flex,
                                                     long long n, double* __restrict__ partial) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double sh[NT / 32];
   double s0 = 0.0, s1 = 0.0;
 #pragma unroll 4
@@ -586,6 +629,8 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r
 
 __global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ partial, int nblk,
                                                      PcgScalars* sc) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double out[2];
   finish_sums<2>(partial, nblk, out);
   if (threadIdx.x == 0 && !sc->done) {
@@ -602,6 +647,8 @@ __global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ 
 
 __global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p, long long n,
                            const PcgScalars* __restrict__ sc) {
+  pdl_trigger();
+  pdl_wait();
   if (sc->done) return;
   double beta = sc->beta;
 #pragma unroll 4
@@ -614,10 +661,12 @@ template <int SH>
 __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
                                                      double* __restrict__ q,
                                                      double* __restrict__ partial) {
+  pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
   int pt = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   double s = 0.0;
   TILE_LOOP(c, sp) {
     int i, j, k;
@@ -633,6 +682,8 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, con
 
 __global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__ partial, int nblk,
                                                       PcgScalars* sc) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double out[1];
   finish_sums<1>(partial, nblk, out);
   if (threadIdx.x == 0 && !sc->done) {
@@ -654,6 +705,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
                                                    double* __restrict__ x, double* __restrict__ r,
                                                    long long n, double* __restrict__ partial,
                                                    const PcgScalars* __restrict__ sc) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double sh[NT / 32];
   if (sc->done) return;
   double alpha = sc->alpha;
@@ -672,6 +725,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
 __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict__ partial, int nblk,
                                                        PcgScalars* sc, cudaGraphConditionalHandle h,
                                                        int use_handle) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double out[1];
   bool was_done = sc->done;
   finish_sums<1>(partial, nblk, out);
@@ -688,6 +743,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict_
 
 __global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ partial, int nblk,
                                                      double* out) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double o2[2];
   finish_sums<2>(partial, nblk, o2);
   if (threadIdx.x == 0) {
@@ -703,9 +760,11 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
                                                       const double* __restrict__ lam,
                                                       const double* __restrict__ x,
                                                       double* __restrict__ dcoef, long long N) {
+  pdl_trigger();
   __shared__ DPart sp;
   int p = block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
+  pdl_wait();
   TILE_LOOP(c, sp) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
@@ -724,6 +783,8 @@ __global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double>
                                                                const double* __restrict__ lam,
                                                                const double* __restrict__ x,
                                                                double* __restrict__ dg) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ DPart sp;
   stage_part(sp, L.parts);
   __syncthreads();
@@ -755,16 +816,35 @@ __global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double>
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+namespace {
+// Launch of a solve kernel: with programmatic stream serialisation when the
+// calling entry point enables it (see pdl_wait), else a plain launch.
+template <typename... P, typename... A>
+void launch_k(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = g_ssamg_pdl ? 1 : 0;
+  SSAMG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...));
+}
+}  // namespace
+
 template <class T>
 void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
   const T* dinv = L.view<T>().dinv;
-  k_relax0<T><<<cdiv(L.N, NT), NT, 0, st>>>((int)L.N, dinv, b, x);
+  launch_k(k_relax0<T>, cdiv(L.N, NT), NT, 0, st, (int)L.N, dinv, b, x);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
   int nb = cdiv(L.N, NT);
-  k_relax0_u<T><<<nb + L.nublk, NT, 0, st>>>(L.view<T>(), nb, b, x);
+  launch_k(k_relax0_u<T>, nb + L.nublk, NT, 0, st, L.view<T>(), nb, b, x);
   SSAMG_LAUNCH_CHECK();
 }
 #define SH_DISPATCH(shape, KCALL)                         \
@@ -780,7 +860,7 @@ void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
 template <class T>
 void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaStream_t st) {
   int nb = cdiv(L.N, NT);
-  k_relax0_u_first<T><<<nb + L.nublk, NT, 0, st>>>(L.view<T>(), nb, r64, b0, x);
+  launch_k(k_relax0_u_first<T>, nb + L.nublk, NT, 0, st, L.view<T>(), nb, r64, b0, x);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -789,54 +869,54 @@ void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const
   // zprev may be null (no flexible CG): pass a valid buffer and a flag
   const int flex = zprev != nullptr;
   double* zp = flex ? zprev : z;
-  SH_DISPATCH(L.shape, (k_relax_final<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, z, rpcg,
+  SH_DISPATCH(L.shape, (launch_k(k_relax_final<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, z, rpcg,
                                                                       zp, flex, partial)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
-  k_prolong_u<T><<<F.nblk + F.nublk, NT, 0, st>>>(F.view<T>(), ec, xin, xout, F.nblk);
+  launch_k(k_prolong_u<T>, F.nblk + F.nublk, NT, 0, st, F.view<T>(), ec, xin, xout, F.nblk);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_uy(const Level& L, const T* x, cudaStream_t st) {
   if (L.nublk == 0) return;
-  k_uy<T><<<L.nublk, NT, 0, st>>>(L.view<T>(), x);
+  launch_k(k_uy<T>, L.nublk, NT, 0, st, L.view<T>(), x);
   SSAMG_LAUNCH_CHECK();
 }
 
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (k_residual<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, r)));
+  SH_DISPATCH(L.shape, (launch_k(k_residual<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, r)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (k_relax<T, SHV><<<L.nblk, NT, 0, st>>>(L.view<T>(), x, b, xo)));
+  SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, xo)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st) {
-  k_restrict<T><<<Cl.nblk, NT, 0, st>>>(F.view<T>(), Cl.view<T>(), r, bc);
+  launch_k(k_restrict<T>, Cl.nblk, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st) {
   (void)Cl;
-  k_prolong<T><<<F.nblk, NT, 0, st>>>(F.view<T>(), ec, x);
+  launch_k(k_prolong<T>, F.nblk, NT, 0, st, F.view<T>(), ec, x);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream_t st) {
   const int staged = (n + n * n) * (int)sizeof(double) <= 40 * 1024;
   size_t sm = sizeof(double) * (staged ? n + n * n : n);
-  k_coarse_solve<T><<<1, 32, sm, st>>>(n, Lfac, b, x, staged);
+  launch_k(k_coarse_solve<T>, 1, 32, sm, st, n, Lfac, b, x, staged);
   SSAMG_LAUNCH_CHECK();
 }
 
 template <class T>
 void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st) {
-  k_coarse_apply<T><<<1, 256, sizeof(double) * n, st>>>(n, inv, b, x);
+  launch_k(k_coarse_apply<T>, 1, 256, sizeof(double) * n, st, n, inv, b, x);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -893,16 +973,16 @@ INST(double)
 #undef INST
 
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st) {
-  k_cast_d2f<<<cdiv(n, NT), NT, 0, st>>>(in, out, (int)n);
+  launch_k(k_cast_d2f, cdiv(n, NT), NT, 0, st, in, out, (int)n);
   SSAMG_LAUNCH_CHECK();
 }
 void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st) {
-  k_cast_f2d<<<cdiv(n, NT), NT, 0, st>>>(in, out, (int)n);
+  launch_k(k_cast_f2d, cdiv(n, NT), NT, 0, st, in, out, (int)n);
   SSAMG_LAUNCH_CHECK();
 }
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  k_matvec<<<L.nblk, NT, 0, st>>>(L.view<double>(), x, y, 0);
+  launch_k(k_matvec, L.nblk, NT, 0, st, L.view<double>(), x, y, 0);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -914,71 +994,71 @@ int reduce_blocks(long long n) {
 void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
                      PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r, partial)));
   SSAMG_LAUNCH_CHECK();
-  k_pcg_init_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
+  launch_k(k_pcg_init_fin, 1, NT, 0, st, partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
                       double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
   // zprev may be null (no flexible CG): pass a valid buffer and a flag
-  k_pcg_start<<<nblk, NT, 0, st>>>(r, z, p, zprev ? zprev : p, zprev != nullptr, n, partial);
+  launch_k(k_pcg_start, nblk, NT, 0, st, r, z, p, zprev ? zprev : p, zprev != nullptr, n, partial);
   SSAMG_LAUNCH_CHECK();
-  k_pcg_start_fin<<<1, NT, 0, st>>>(partial, nblk, sc);
+  launch_k(k_pcg_start_fin, 1, NT, 0, st, partial, nblk, sc);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
-  k_pcg_dots_rz<<<nblk, NT, 0, st>>>(r, z, zprev ? zprev : p, zprev != nullptr, n, partial);
+  launch_k(k_pcg_dots_rz, nblk, NT, 0, st, r, z, zprev ? zprev : p, zprev != nullptr, n, partial);
   SSAMG_LAUNCH_CHECK();
   launch_pcg_beta_from_partials(z, p, n, partial, nblk, nblk, sc, st);
 }
 
 void launch_pcg_beta_from_partials(const double* z, double* p, long long n, const double* partial,
                                    int npart, int nblk, PcgScalars* sc, cudaStream_t st) {
-  k_pcg_beta_fin<<<1, NT, 0, st>>>(partial, npart, sc);
+  launch_k(k_pcg_beta_fin, 1, NT, 0, st, partial, npart, sc);
   SSAMG_LAUNCH_CHECK();
-  k_pcg_xpby<<<nblk, NT, 0, st>>>(z, p, n, sc);
+  launch_k(k_pcg_xpby, nblk, NT, 0, st, z, p, n, sc);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
                       PcgScalars* sc, cudaStream_t st) {
   launch_uy<double>(L, p, st);
-  SH_DISPATCH(L.shape, (k_pcg_spmv_dot<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), p, q, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q, partial)));
   SSAMG_LAUNCH_CHECK();
-  k_pcg_alpha_fin<<<1, NT, 0, st>>>(partial, L.nblk, sc);
+  launch_k(k_pcg_alpha_fin, 1, NT, 0, st, partial, L.nblk, sc);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,
                        double* partial, int nblk, PcgScalars* sc, cudaGraphConditionalHandle h,
                        int use_handle, cudaStream_t st) {
-  k_pcg_update<<<nblk, NT, 0, st>>>(p, q, x, r, n, partial, sc);
+  launch_k(k_pcg_update, nblk, NT, 0, st, p, q, x, r, n, partial, sc);
   SSAMG_LAUNCH_CHECK();
-  k_pcg_update_fin<<<1, NT, 0, st>>>(partial, nblk, sc, h, use_handle);
+  launch_k(k_pcg_update_fin, 1, NT, 0, st, partial, nblk, sc, h, use_handle);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
                           double* partial, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (k_pcg_init<SHV><<<L.nblk, NT, 0, st>>>(L.view<double>(), b, x, r, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r, partial)));
   SSAMG_LAUNCH_CHECK();
-  k_true_res_fin<<<1, NT, 0, st>>>(partial, L.nblk, out);
+  launch_k(k_true_res_fin, 1, NT, 0, st, partial, L.nblk, out);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
                           cudaStream_t st) {
-  k_coef_gradient<<<L.nblk, NT, 0, st>>>(L.view<double>(), lam, x, dcoef, L.N);
+  launch_k(k_coef_gradient, L.nblk, NT, 0, st, L.view<double>(), lam, x, dcoef, L.N);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_diffusion_exp_gradient(const Level& L, const double* g, const double* lam,
                                    const double* x, double* dg, cudaStream_t st) {
-  k_diffusion_exp_gradient<<<cdiv(L.parts[0].ncell, NT), NT, 0, st>>>(L.view<double>(), g, lam, x, dg);
+  launch_k(k_diffusion_exp_gradient, cdiv(L.parts[0].ncell, NT), NT, 0, st, L.view<double>(), g, lam, x, dg);
   SSAMG_LAUNCH_CHECK();
 }

@@ -254,6 +254,10 @@ struct SsamgError {
 // Every kernel launch of the library passes through this check, which also
 // counts it (per host thread) for the launch statistics.
 extern thread_local long long g_ssamg_launches;
+// Nonzero while an entry point enqueues solve kernels with programmatic
+// dependent launch (per host thread; set by the entry point, read by the
+// launchers).
+extern thread_local int g_ssamg_pdl;
 #define SSAMG_LAUNCH_CHECK()       \
   do {                             \
     ++g_ssamg_launches;            \

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("s_max", ctypes.c_longlong),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("coarse_direct", ctypes.c_int), ("flexible", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("use_tail", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("use_tail", ctypes.c_int),
+                ("use_pdl", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

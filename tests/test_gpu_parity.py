@@ -357,3 +357,28 @@ def test_diffusion_gradient_matches_oracle_and_fd(S):
         fd = (loss(gp.reshape(g.shape)) - loss(gm.reshape(g.shape))) / (2 * hstep)
         got = dg.cpu().numpy()[c]
         assert abs(fd - got) <= 1e-6 * max(abs(fd), 1e-6), (c, fd, got)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_programmatic_launch_matches_plain_launches(S, prec):
+    """Programmatic dependent launch only changes when kernels are scheduled:
+    every kernel still waits for its predecessor before touching the solve's
+    vectors, so the result is bitwise that of plain launches (graph and host
+    loop alike)."""
+    prob = P.multipart_aniso(m=24, layout=(2, 2, 2), seed=1)
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    runs = []
+    for pdl in (0, 1):
+        for graph in (0, 1):
+            _, _, sv = gpu_setup(S, prob, precision=prec, flexible=prec, use_pdl=pdl,
+                                 use_graph=graph)
+            x = torch.zeros_like(b)
+            st = sv.solve(b, x)
+            assert st.converged
+            z = torch.zeros_like(b)
+            sv.precondition(b, z)
+            runs.append((st.iterations, x.cpu().numpy(), z.cpu().numpy()))
+    for it, x, z in runs[1:]:
+        assert it == runs[0][0]
+        assert np.array_equal(x, runs[0][1])
+        assert np.array_equal(z, runs[0][2])
