@@ -194,6 +194,10 @@ def run_ours(args):
             "clocks": ck,
         }
 
+    if args.levels:
+        for name, sv in solvers.items():
+            level_table(sv, name, stream)
+
     # ---- dominant-kernel roofline (prolongation with U x, FP32 cycle)
     roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
 
@@ -291,6 +295,27 @@ def kernel_roofline(S, sv, prob, dev, stream, args):
             "us_per_launch": round(us_spmv, 2),
             "hbm_gbs": round((24 * N0 + 16 * prob.nnz_u) / (us_spmv * 1e-6) / 1e9, 1)},
     }
+
+
+def level_table(sv, name, stream):
+    """Per-level duration (us) of each cycle kernel, each timed alone as 100
+    graph-replayed launches on the solver's own buffers (stderr)."""
+    kinds = [("relax0_u", 2), ("residual", 0), ("restrict", 3), ("prolong_u", 4),
+             ("relax", 1)]
+    L = sv.num_levels()
+    out = [f"{name}: V-cycle {sv.time_kernel(5, 0, 20, stream):.1f} us, "
+           f"FP64 operator apply {sv.time_kernel(6, 0, 50, stream):.1f} us"]
+    out.append("  lvl        N     nr " + " ".join(f"{k:>11s}" for k, _ in kinds))
+    for l in range(L):
+        n, nr, _ = sv.level_sizes(l)
+        row = []
+        for _, kid in kinds:
+            if kid in (3, 4) and l == L - 1:
+                row.append("-")
+            else:
+                row.append(f"{sv.time_kernel(kid, l, 100, stream):.2f}")
+        out.append(f"  {l:3d} {n:8d} {nr:6d} " + " ".join(f"{v:>11s}" for v in row))
+    print("\n".join(out), file=sys.stderr)
 
 
 def read_peaks():
@@ -418,6 +443,9 @@ def main():
                     help="launch the solve kernels directly (profilers cannot see kernel "
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--only", choices=["fp32_cycle", "fp64"], default=None)
+    ap.add_argument("--levels", action="store_true",
+                    help="also write, to stderr, each cycle kernel's time per level "
+                         "(CUDA-graph replays of that launch alone)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -341,29 +341,51 @@ __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, cons
 }
 
 // Row job: SSAMG_TPR threads per U row r = blockIdx-relative row; stores
-// sum_q u_q * f(col_q, q) at the row's cell of L.uy (all lanes must call).
-// Each lane takes four entries at a time so that their loads overlap.
-template <class T, class F>
-__device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, F&& f) {
+// sum_q u_q * f(col_q, q, s_q) at the row's cell of L.uy, where
+// s_q = pre(col_q, q) is the entry's setup-time data (all lanes must call).
+// The row bounds, each lane's first column and value, and pre() of that
+// entry are loaded before pdl_wait(); so a row of at most SSAMG_TPR entries
+// (the common case) has one dependent load after the wait.  pre() may read
+// only what setup wrote.  Further entries go four per lane at a time so that
+// their loads overlap; the summation order is that of q ascending per lane.
+template <class T, class Pre, class F>
+__device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& pre, F&& f) {
   const int r = rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR;
   const int l4 = threadIdx.x % SSAMG_TPR;
-  T acc = (T)0;
+  int q = 0, q1 = 0, c0 = 0;
+  T u0 = (T)0;
+  decltype(pre(0, 0)) s0{};
   if (r < L.nr) {
-    const int q1 = L.u_ptr[r + 1];
-    int q = L.u_ptr[r] + l4;
+    q = L.u_ptr[r] + l4;
+    q1 = L.u_ptr[r + 1];
+    if (q < q1) {
+      c0 = L.u_col[q];
+      u0 = L.u_val[q];
+      s0 = pre(c0, q);
+    }
+  }
+  pdl_wait();
+  T acc = (T)0;
+  if (q < q1) {
+    acc = fma(u0, f(c0, q, s0), acc);
+    q += SSAMG_TPR;
     for (; q + 3 * SSAMG_TPR < q1; q += 4 * SSAMG_TPR) {
-      const int c0 = L.u_col[q], c1 = L.u_col[q + SSAMG_TPR], c2 = L.u_col[q + 2 * SSAMG_TPR],
-                c3 = L.u_col[q + 3 * SSAMG_TPR];
-      const T u0 = L.u_val[q], u1 = L.u_val[q + SSAMG_TPR], u2 = L.u_val[q + 2 * SSAMG_TPR],
-              u3 = L.u_val[q + 3 * SSAMG_TPR];
-      const T v0 = f(c0, q), v1 = f(c1, q + SSAMG_TPR), v2 = f(c2, q + 2 * SSAMG_TPR),
-              v3 = f(c3, q + 3 * SSAMG_TPR);
-      acc = fma(u0, v0, acc);
+      const int c1 = L.u_col[q], c2 = L.u_col[q + SSAMG_TPR], c3 = L.u_col[q + 2 * SSAMG_TPR],
+                c4 = L.u_col[q + 3 * SSAMG_TPR];
+      const T u1 = L.u_val[q], u2 = L.u_val[q + SSAMG_TPR], u3 = L.u_val[q + 2 * SSAMG_TPR],
+              u4 = L.u_val[q + 3 * SSAMG_TPR];
+      const T v1 = f(c1, q, pre(c1, q)), v2 = f(c2, q + SSAMG_TPR, pre(c2, q + SSAMG_TPR)),
+              v3 = f(c3, q + 2 * SSAMG_TPR, pre(c3, q + 2 * SSAMG_TPR)),
+              v4 = f(c4, q + 3 * SSAMG_TPR, pre(c4, q + 3 * SSAMG_TPR));
       acc = fma(u1, v1, acc);
       acc = fma(u2, v2, acc);
       acc = fma(u3, v3, acc);
+      acc = fma(u4, v4, acc);
     }
-    for (; q < q1; q += SSAMG_TPR) acc = fma(L.u_val[q], f(L.u_col[q], q), acc);
+    for (; q < q1; q += SSAMG_TPR) {
+      const int c = L.u_col[q];
+      acc = fma(L.u_val[q], f(c, q, pre(c, q)), acc);
+    }
   }
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);

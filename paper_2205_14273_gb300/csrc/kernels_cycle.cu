@@ -21,18 +21,22 @@ __global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict_
   if (g < N) x[g] = dinv[g] * b[g];
 }
 
-// x = omega M^-1 b on blocks [0, nb); row jobs uy = U x on the rest.
+// x = omega M^-1 b on blocks [0, nb); row jobs uy = U x on the rest.  The
+// diagonal (setup data) is fetched before the wait for the predecessor.
 template <class T>
 __global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T* __restrict__ b,
                                                  T* __restrict__ x) {
   pdl_trigger();
-  pdl_wait();
   if ((int)blockIdx.x < nb) {
-    int g = blockIdx.x * NT + threadIdx.x;
-    if (g < L.N) x[g] = L.dinv[g] * b[g];
+    const int g = blockIdx.x * NT + threadIdx.x;
+    const T d = g < L.N ? L.dinv[g] : (T)0;
+    pdl_wait();
+    if (g < L.N) x[g] = d * b[g];
     return;
   }
-  u_row_job(L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col] * b[col]; });
+  u_row_job(
+      L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col]; },
+      [&](int col, int, T d) { return d * b[col]; });
 }
 
 // First pre-relaxation of the cycle straight from the FP64 PCG residual:
@@ -42,25 +46,28 @@ __global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
                                                        const double* __restrict__ r64,
                                                        T* __restrict__ b0, T* __restrict__ x) {
   pdl_trigger();
-  pdl_wait();
   if ((int)blockIdx.x < nb) {
-    int g = blockIdx.x * NT + threadIdx.x;
+    const int g = blockIdx.x * NT + threadIdx.x;
+    const T d = g < L.N ? L.dinv[g] : (T)0;
+    pdl_wait();
     if (g < L.N) {
       const T bv = (T)r64[g];
       b0[g] = bv;
-      x[g] = L.dinv[g] * bv;
+      x[g] = d * bv;
     }
     return;
   }
-  u_row_job(L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col] * (T)r64[col]; });
+  u_row_job(
+      L, blockIdx.x - nb, [&](int col, int) { return L.dinv[col]; },
+      [&](int col, int, T d) { return d * (T)r64[col]; });
 }
 
 // uy = U x (row jobs only)
 template <class T>
 __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__ x) {
   pdl_trigger();
-  pdl_wait();
-  u_row_job(L, blockIdx.x, [&](int col, int) { return x[col]; });
+  u_row_job(
+      L, blockIdx.x, [](int, int) { return 0; }, [&](int col, int, int) { return x[col]; });
 }
 
 // r = b - A x
@@ -168,9 +175,17 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   }
 }
 
+// Coarse-side P row of a coupling column (setup data of a row job entry).
+template <class T>
+struct PCol {
+  int j0, j1;
+  T w0, w1;
+};
+
 // xout = xin + P ec on the cell tiles; row jobs uy = U xout, where xout at a
 // coupling's column is rebuilt from xin and the column's P row (precomputed
-// at setup), so the two roles need no ordering.
+// at setup), so the two roles need no ordering.  P rows are setup data and
+// are fetched before the wait for the predecessor.
 template <class T>
 __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
                                                   const T* __restrict__ xin, T* __restrict__ xout,
@@ -178,29 +193,43 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
   pdl_trigger();
   __shared__ DPart fp;
   if ((int)blockIdx.x >= nb) {
-    pdl_wait();
-    u_row_job(F, blockIdx.x - nb, [&](int col, int q) {
-      T v = xin[col];
-      int j0 = F.u_pj[2 * q], j1 = F.u_pj[2 * q + 1];
-      if (j0 >= 0) v = fma(F.u_pw[2 * q], ec[j0], v);
-      if (j1 >= 0) v = fma(F.u_pw[2 * q + 1], ec[j1], v);
-      return v;
-    });
+    u_row_job(
+        F, blockIdx.x - nb,
+        [&](int, int q) {
+          return PCol<T>{F.u_pj[2 * q], F.u_pj[2 * q + 1], F.u_pw[2 * q], F.u_pw[2 * q + 1]};
+        },
+        [&](int col, int, const PCol<T>& pc) {
+          T v = xin[col];
+          if (pc.j0 >= 0) v = fma(pc.w0, ec[pc.j0], v);
+          if (pc.j1 >= 0) v = fma(pc.w1, ec[pc.j1], v);
+          return v;
+        });
     return;
   }
   int p = block_part(F.blk, F.parts, F.np, fp);
   __syncthreads();
+  // the first tile cell's P row (setup data) is fetched before the wait
+  const int cfirst = ((int)blockIdx.x - fp.blk0) * fp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
+  int J[2];
+  T w[2];
+  int m = 0;
+  if (cfirst < fp.ncell) {
+    int i, j, k;
+    cell_coords(fp, cfirst, i, j, k);
+    m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+  }
   pdl_wait();
   TILE_LOOP(c, fp) {
-    int i, j, k;
-    cell_coords(fp, c, i, j, k);
-    int J[2];
-    T w[2];
-    int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+    if (c != cfirst) {
+      int i, j, k;
+      cell_coords(fp, c, i, j, k);
+      m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+    }
     T v = xin[fp.off + c];
     for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
     xout[fp.off + c] = v;
   }
+  (void)p;
 }
 
 // x += P ec, one fine cell per thread.
