@@ -109,11 +109,14 @@ typedef struct {
   int coarse_direct;   /* 1: dense Cholesky on the coarsest level; 0: one relaxation sweep (Section 3.5) */
   int flexible;        /* 1: Polak-Ribiere beta (for the FP32 cycle); 0: Fletcher-Reeves */
   int use_graph;       /* 1: run the PCG iteration loop as one CUDA graph */
-  int use_tail;        /* 1: run the levels of at most 8192 cells (<= 8 parts) in one single-block
-                          launch (default 0: one launch per level and step is faster on GB300) */
+  int use_tail;        /* coarse levels in one launch: 0 (default) one launch per level and step;
+                          1: a cooperative grid over the levels of at most 32,768 cells
+                          (<= 8 parts), with grid barriers; 2: one CTA of 1024 threads over the
+                          levels of at most tail_cells cells (<= 8 parts), with block barriers */
   int use_pdl;         /* 1 (default): launch the solve's kernels with programmatic dependent
                           launch, so that each kernel is scheduled, and stages its part
                           descriptors, while its predecessor still runs; 0: plain launches */
+  int tail_cells;      /* largest level of the use_tail = 2 tail (0: 4096) */
 } ssamg_params;
 
 typedef struct {

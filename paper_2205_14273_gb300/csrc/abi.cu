@@ -129,6 +129,7 @@ struct ssamg_solver_s {
   int tail_lt = -1;            // first level of the fused coarse tail (-1: none)
   void* tail_dev = nullptr;    // TailLevel<T> array for levels tail_lt..Lc
   int tail_blocks = 0;
+  int tail_parts = 0;          // part descriptors of the tail levels (single-CTA tail)
   TailBarrier* tail_bar = nullptr;
   // PCG work (FP64, level 0 size)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
@@ -516,6 +517,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->use_graph = 1;
   p->use_tail = 0;
   p->use_pdl = 1;
+  p->tail_cells = 0;
 }
 
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
@@ -960,26 +962,41 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   // ---- fused coarse tail: the trailing levels that fit one block
   s->tail_lt = -1;
   s->tail_dev = nullptr;
+  s->tail_bar = nullptr;
   if (s->prm.use_tail && (!s->prm.coarse_direct || s->cinv)) {
+    // use_tail 1: cooperative grid over the levels of at most
+    // SSAMG_TAIL_MAX_CELLS cells; 2: one CTA over the levels of at most
+    // tail_cells (default SSAMG_TAIL_CTA_CELLS) cells
+    const bool one = s->prm.use_tail == 2;
+    const long long maxc = one ? (s->prm.tail_cells > 0 ? s->prm.tail_cells : SSAMG_TAIL_CTA_CELLS)
+                               : SSAMG_TAIL_MAX_CELLS;
     int lt = Lc;
-    while (lt - 1 >= 0 && s->lev[lt - 1].N <= SSAMG_TAIL_MAX_CELLS &&
-           s->lev[lt - 1].np <= SSAMG_TAIL_MAX_PARTS)
+    while (lt - 1 >= 0 && s->lev[lt - 1].N <= maxc && s->lev[lt - 1].np <= SSAMG_TAIL_MAX_PARTS)
       --lt;
-    const int maxb = tail_max_blocks();
-    if (lt < Lc && s->lev[lt].np <= SSAMG_TAIL_MAX_PARTS && maxb >= 1) {
+    const int maxb = one ? 1 : tail_max_blocks();
+    s->tail_parts = 0;
+    for (int l = lt; l <= Lc; ++l) s->tail_parts += s->lev[l].np;
+    bool fits = true;
+    if (one && lt < Lc)
+      fits = fp32 ? vtail_one_prepare<float>(Lc - lt + 1, s->tail_parts)
+                  : vtail_one_prepare<double>(Lc - lt + 1, s->tail_parts);
+    if (lt < Lc && fits && s->lev[lt].np <= SSAMG_TAIL_MAX_PARTS && maxb >= 1) {
       s->tail_lt = lt;
-      s->tail_blocks = (int)std::min<long long>(
-          std::min<long long>(SSAMG_TAIL_MAX_BLOCKS, maxb),
-          std::max<long long>(1, cdivll(s->lev[lt].N, SSAMG_TAIL_BLOCK)));
-      s->tail_bar = aalloc<TailBarrier>(s->arena, 1);
-      SSAMG_CUDA(cudaMemsetAsync(s->tail_bar, 0, sizeof(TailBarrier), st));
+      s->tail_blocks = one ? 0
+                           : (int)std::min<long long>(
+                                 std::min<long long>(SSAMG_TAIL_MAX_BLOCKS, maxb),
+                                 std::max<long long>(1, cdivll(s->lev[lt].N, SSAMG_TAIL_BLOCK)));
+      if (!one) {
+        s->tail_bar = aalloc<TailBarrier>(s->arena, 1);
+        SSAMG_CUDA(cudaMemsetAsync(s->tail_bar, 0, sizeof(TailBarrier), st));
+      }
       const int nt = Lc - lt + 1;
       if (fp32) {
         std::vector<TailLevel<float>> tl(nt);
         for (int l = lt; l <= Lc; ++l)
           tl[l - lt] = TailLevel<float>{s->lev[l].view<float>(), (float*)s->lev[l].x,
                                         (float*)s->lev[l].b, (float*)s->lev[l].r,
-                                        (float*)s->lev[l].t};
+                                        (float*)s->lev[l].t, s->lev[l].shape, 0};
         s->tail_dev = s->arena.alloc(sizeof(TailLevel<float>) * nt);
         SSAMG_CUDA(cudaMemcpyAsync(s->tail_dev, tl.data(), sizeof(TailLevel<float>) * nt,
                                    cudaMemcpyHostToDevice, st));
@@ -988,7 +1005,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
         for (int l = lt; l <= Lc; ++l)
           tl[l - lt] = TailLevel<double>{s->lev[l].view<double>(), (double*)s->lev[l].x,
                                          (double*)s->lev[l].b, (double*)s->lev[l].r,
-                                         (double*)s->lev[l].t};
+                                         (double*)s->lev[l].t, s->lev[l].shape, 0};
         s->tail_dev = s->arena.alloc(sizeof(TailLevel<double>) * nt);
         SSAMG_CUDA(cudaMemcpyAsync(s->tail_dev, tl.data(), sizeof(TailLevel<double>) * nt,
                                    cudaMemcpyHostToDevice, st));
@@ -1056,7 +1073,7 @@ int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream
     if (!is_f)
       SSAMG_CUDA(cudaMemcpyAsync(Ls[0].b, r_in, sizeof(double) * Ls[0].N, cudaMemcpyDeviceToDevice, st));
     launch_vtail<T>((const TailLevel<T>*)s->tail_dev, Lc + 1, s->cinv, s->nL, s->prm.coarse_direct,
-                    s->tail_blocks, s->tail_bar, st);
+                    s->tail_blocks, s->tail_bar, st, s->tail_parts);
     if (is_f)
       launch_cast_f2d((const float*)Ls[0].t, z_out, Ls[0].N, st);
     else
@@ -1079,7 +1096,7 @@ int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream
   const T* e;
   if (lt < Lc) {
     launch_vtail<T>((const TailLevel<T>*)s->tail_dev, Lc - lt + 1, s->cinv, s->nL,
-                    s->prm.coarse_direct, s->tail_blocks, s->tail_bar, st);
+                    s->prm.coarse_direct, s->tail_blocks, s->tail_bar, st, s->tail_parts);
     e = (const T*)Ls[lt].t;
   } else {
     coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);

@@ -340,18 +340,18 @@ __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, cons
   return acc;
 }
 
-// Row job: SSAMG_TPR threads per U row r = blockIdx-relative row; stores
-// sum_q u_q * f(col_q, q, s_q) at the row's cell of L.uy, where
-// s_q = pre(col_q, q) is the entry's setup-time data (all lanes must call).
-// The row bounds, each lane's first column and value, and pre() of that
-// entry are loaded before pdl_wait(); so a row of at most SSAMG_TPR entries
-// (the common case) has one dependent load after the wait.  pre() may read
-// only what setup wrote.  Further entries go four per lane at a time so that
+// Sum of one U row: the SSAMG_TPR lanes l4 of a row group compute
+// sum_q u_q * f(col_q, q, s_q) for row r (r >= L.nr: nothing, but the lanes
+// still join the shuffles) and store it at the row's cell of L.uy;
+// s_q = pre(col_q, q) is the entry's setup-time data.  With WAIT, the row
+// bounds, each lane's first column and value, and pre() of that entry are
+// loaded before pdl_wait(); so a row of at most SSAMG_TPR entries (the
+// common case) has one dependent load after the wait.  pre() may read only
+// what setup wrote.  Further entries go four per lane at a time so that
 // their loads overlap; the summation order is that of q ascending per lane.
-template <class T, class Pre, class F>
-__device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& pre, F&& f) {
-  const int r = rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR;
-  const int l4 = threadIdx.x % SSAMG_TPR;
+template <bool WAIT, class T, class Pre, class F>
+__device__ __forceinline__ void u_row_sum(const LevelView<T>& L, int r, int l4, Pre&& pre,
+                                          F&& f) {
   int q = 0, q1 = 0, c0 = 0;
   T u0 = (T)0;
   decltype(pre(0, 0)) s0{};
@@ -364,7 +364,7 @@ __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& p
       s0 = pre(c0, q);
     }
   }
-  pdl_wait();
+  if constexpr (WAIT) pdl_wait();
   T acc = (T)0;
   if (q < q1) {
     acc = fma(u0, f(c0, q, s0), acc);
@@ -390,6 +390,14 @@ __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& p
   acc += __shfl_xor_sync(0xffffffffu, acc, 1);
   acc += __shfl_xor_sync(0xffffffffu, acc, 2);
   if (r < L.nr && l4 == 0) L.uy[L.u_rows[r]] = acc;
+}
+
+// Row job of a launch: block rb's threads take SSAMG_RPB rows, SSAMG_TPR
+// lanes each (all threads must call; waits for the predecessor inside).
+template <class T, class Pre, class F>
+__device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& pre, F&& f) {
+  u_row_sum<true>(L, rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR,
+                  (int)threadIdx.x % SSAMG_TPR, pre, f);
 }
 
 // Block-wide sum (deterministic: fixed shuffle tree, then fixed warp order).

@@ -327,18 +327,70 @@ __device__ __forceinline__ void grid_barrier(TailBarrier* gb) {
   __syncthreads();
 }
 
+// Operator apply of a tail level with the level's stencil shape (the same
+// specialised, unchecked stencils as the per-level kernels).
+template <class T>
+__device__ __forceinline__ T tail_apply(const LevelView<T>& L, const DPart& sp,
+                                        const T* __restrict__ x, int c, int shape) {
+  switch (shape) {
+    case SH_U7: return apply_A_sh<SH_U7>(L, sp, x, c);
+    case SH_U15: return apply_A_sh<SH_U15>(L, sp, x, c);
+    case SH_C27: return apply_A_sh<SH_C27>(L, sp, x, c);
+    case SH_UGEN: return apply_A_sh<SH_UGEN>(L, sp, x, c);
+    case SH_K7: return apply_A_sh<SH_K7>(L, sp, x, c);
+    default: return apply_A_sh<SH_CHECKED>(L, sp, x, c);
+  }
+}
+
 __device__ __forceinline__ int tail_part(const int* __restrict__ cs, int np, int g) {
   int p = 0;
   while (p + 1 < np && __ldg(cs + p + 1) <= g) ++p;
   return p;
 }
 
-template <class T>
-__global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ lv, int nlev,
-                                              const double* __restrict__ cinv, int nL,
-                                              int coarse_direct, TailBarrier* gb) {
-  const int tid = blockIdx.x * TB + threadIdx.x;
-  const int nth = gridDim.x * TB;
+// ONE = true: a single CTA of SSAMG_TAIL_CTA threads runs the tail, with
+// __syncthreads() as the step barrier and the level table staged in shared
+// memory (launched like the other cycle kernels, with programmatic dependent
+// launch).  ONE = false: a cooperative grid with grid_barrier().
+template <class T, bool ONE>
+__global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
+    k_vtail(const TailLevel<T>* __restrict__ lvg, int nlev, const double* __restrict__ cinv,
+            int nL, int coarse_direct, TailBarrier* gb) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const TailLevel<T>* lv = lvg;
+  if constexpr (ONE) {
+    // shared memory: the level table, then every level's part descriptors
+    // (the table's part pointers are redirected there)
+    pdl_trigger();
+    extern __shared__ __align__(16) int tail_smem[];
+    TailLevel<T>* slv = reinterpret_cast<TailLevel<T>*>(tail_smem);
+    const int nw = nlev * (int)(sizeof(TailLevel<T>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(lvg);
+    for (int t = threadIdx.x; t < nw; t += blockDim.x) tail_smem[t] = __ldg(src + t);
+    __syncthreads();
+    DPart* sparts = reinterpret_cast<DPart*>(slv + nlev);
+    constexpr int dw = (int)(sizeof(DPart) / sizeof(int));
+    for (int l = 0; l < nlev; ++l) {
+      const int* ps = reinterpret_cast<const int*>(slv[l].L.parts);
+      int* pd = reinterpret_cast<int*>(sparts);
+      const int n = slv[l].L.np * dw;
+      for (int t = threadIdx.x; t < n; t += blockDim.x) pd[t] = __ldg(ps + t);
+      __syncthreads();
+      if (threadIdx.x == 0) slv[l].L.parts = sparts;
+      sparts += slv[l].L.np;
+    }
+    __syncthreads();
+    lv = slv;
+    pdl_wait();
+  }
+  auto barrier = [&]() {
+    if constexpr (ONE) {
+      __syncthreads();
+    } else {
+      grid_barrier(gb);
+    }
+  };
   // ---- down
   for (int l = 0; l + 1 < nlev; ++l) {
     const TailLevel<T>& F = lv[l];
@@ -347,23 +399,17 @@ __global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ l
     T* __restrict__ Fx = F.x;
     const T* __restrict__ Fb = F.b;
     for (int g = tid; g < FL.N; g += nth) Fx[g] = FL.dinv[g] * Fb[g];
-    for (int r = tid; r < FL.nr; r += nth) {
-      T acc = (T)0;
-      for (int q = FL.u_ptr[r]; q < FL.u_ptr[r + 1]; ++q) {
-        const int col = FL.u_col[q];
-        acc = fma(FL.u_val[q], FL.dinv[col] * Fb[col], acc);
-      }
-      FL.uy[FL.u_rows[r]] = acc;
-    }
-    grid_barrier(gb);
+    for (int base = 0; base < FL.nr; base += nth / SSAMG_TPR)
+      u_row_sum<false>(
+          FL, base + tid / SSAMG_TPR, tid % SSAMG_TPR, [&](int col, int) { return FL.dinv[col]; },
+          [&](int col, int, T d) { return d * Fb[col]; });
+    barrier();
     T* __restrict__ Fr = F.r;
     for (int g = tid; g < FL.N; g += nth) {
       const DPart& sp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
-      int c = g - sp.off, i, j, k;
-      cell_coords(sp, c, i, j, k);
-      Fr[g] = Fb[g] - apply_A(FL, sp, Fx, c, i, j, k);
+      Fr[g] = Fb[g] - tail_apply(FL, sp, Fx, g - sp.off, F.shape);
     }
-    grid_barrier(gb);
+    barrier();
     const LevelView<T> CL = C.L;
     T* __restrict__ Cb = C.b;
     for (int gc = tid; gc < CL.N; gc += nth) {
@@ -395,7 +441,7 @@ __global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ l
       }
       Cb[gc] = v;
     }
-    grid_barrier(gb);
+    barrier();
   }
   // ---- coarsest level
   {
@@ -415,7 +461,7 @@ __global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ l
     } else {
       for (int g = tid; g < Lc.L.N; g += nth) Lc.x[g] = Lc.L.dinv[g] * Lc.b[g];
     }
-    grid_barrier(gb);
+    barrier();
   }
   // ---- up
   const T* e = lv[nlev - 1].x;
@@ -435,28 +481,26 @@ __global__ void __launch_bounds__(TB) k_vtail(const TailLevel<T>* __restrict__ l
       for (int t = 0; t < m; ++t) v = fma(w[t], e[J[t]], v);
       Fr[g] = v;
     }
-    for (int r = tid; r < FL.nr; r += nth) {
-      T acc = (T)0;
-      for (int q = FL.u_ptr[r]; q < FL.u_ptr[r + 1]; ++q) {
-        const int col = FL.u_col[q];
-        T v = Fx[col];
-        const int j0 = FL.u_pj[2 * q], j1 = FL.u_pj[2 * q + 1];
-        if (j0 >= 0) v = fma(FL.u_pw[2 * q], e[j0], v);
-        if (j1 >= 0) v = fma(FL.u_pw[2 * q + 1], e[j1], v);
-        acc = fma(FL.u_val[q], v, acc);
-      }
-      FL.uy[FL.u_rows[r]] = acc;
-    }
-    grid_barrier(gb);
+    for (int base = 0; base < FL.nr; base += nth / SSAMG_TPR)
+      u_row_sum<false>(
+          FL, base + tid / SSAMG_TPR, tid % SSAMG_TPR,
+          [&](int, int q) {
+            return PCol<T>{FL.u_pj[2 * q], FL.u_pj[2 * q + 1], FL.u_pw[2 * q], FL.u_pw[2 * q + 1]};
+          },
+          [&](int col, int, const PCol<T>& pc) {
+            T v = Fx[col];
+            if (pc.j0 >= 0) v = fma(pc.w0, e[pc.j0], v);
+            if (pc.j1 >= 0) v = fma(pc.w1, e[pc.j1], v);
+            return v;
+          });
+    barrier();
     T* __restrict__ Ft = F.t;
     const T* __restrict__ Fb = F.b;
     for (int g = tid; g < FL.N; g += nth) {
       const DPart& sp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
-      int c = g - sp.off, i, j, k;
-      cell_coords(sp, c, i, j, k);
-      Ft[g] = fma(FL.dinv[g], Fb[g] - apply_A(FL, sp, Fr, c, i, j, k), Fr[g]);
+      Ft[g] = fma(FL.dinv[g], Fb[g] - tail_apply(FL, sp, Fr, g - sp.off, F.shape), Fr[g]);
     }
-    grid_barrier(gb);
+    barrier();
     e = Ft;
   }
 }
@@ -950,8 +994,28 @@ void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_
 }
 
 template <class T>
+size_t vtail_one_smem(int nlev, int nparts) {
+  return sizeof(TailLevel<T>) * nlev + sizeof(DPart) * nparts;
+}
+
+template <class T>
+bool vtail_one_prepare(int nlev, int nparts) {
+  const size_t sm = vtail_one_smem<T>(nlev, nparts);
+  if (sm > 200 * 1024) return false;
+  SSAMG_CUDA(cudaFuncSetAttribute(k_vtail<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+  return true;
+}
+
+template <class T>
 void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, int coarse_direct,
-                  int nblocks, TailBarrier* gb, cudaStream_t st) {
+                  int nblocks, TailBarrier* gb, cudaStream_t st, int nparts) {
+  if (nblocks == 0) {  // single CTA
+    launch_k(k_vtail<T, true>, 1, SSAMG_TAIL_CTA, vtail_one_smem<T>(nlev, nparts), st, lv, nlev,
+             cinv, nL, coarse_direct, gb);
+    SSAMG_LAUNCH_CHECK();
+    return;
+  }
   SSAMG_CUDA(cudaMemsetAsync(gb, 0, sizeof(unsigned), st));  // counter (err is sticky)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblocks);
@@ -963,16 +1027,17 @@ void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  SSAMG_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T>, lv, nlev, cinv, nL, coarse_direct, gb));
+  SSAMG_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T, false>, lv, nlev, cinv, nL, coarse_direct, gb));
+  SSAMG_LAUNCH_CHECK();
 }
 
 int tail_max_blocks() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vtail<float>, TB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_vtail<float, false>, TB, 0);
   int per2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_vtail<double>, TB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_vtail<double, false>, TB, 0);
   return sms * std::min(per, per2);
 }
 
@@ -990,7 +1055,8 @@ void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t 
                                       double*, double*, cudaStream_t);                     \
   template void launch_uy<T>(const Level&, const T*, cudaStream_t);                        \
   template void launch_vtail<T>(const TailLevel<T>*, int, const double*, int, int, int,      \
-                                TailBarrier*, cudaStream_t);                               \
+                                TailBarrier*, cudaStream_t, int);                          \
+  template bool vtail_one_prepare<T>(int, int);                                            \
   template void launch_coarse_apply<T>(int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
   template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \

@@ -133,6 +133,8 @@ struct LevelView {
 #define SSAMG_TAIL_MAX_PARTS 8
 #define SSAMG_TAIL_BLOCK 256
 #define SSAMG_TAIL_MAX_BLOCKS 128
+#define SSAMG_TAIL_CTA 1024         // threads of the single-CTA tail
+#define SSAMG_TAIL_CTA_CELLS 4096   // default largest level of the single-CTA tail
 #define SSAMG_BARRIER_SPINS (1u << 24)  // ~1 s of polling before a barrier gives up
 
 struct TailBarrier {
@@ -148,6 +150,8 @@ struct TailLevel {
   T* b;
   T* r;
   T* t;
+  int shape;  // StencilShape of the level's operator apply
+  int pad_;
 };
 
 // ---------------------------------------------------------------------------
@@ -323,7 +327,11 @@ void launch_coarse_solve(int n, const double* Lfac, const T* b, T* x, cudaStream
 // b of level lt, coarsest solve, up sweep; result in t of level lt).
 template <class T>
 void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, int coarse_direct,
-                  int nblocks, TailBarrier* gb, cudaStream_t st);
+                  int nblocks, TailBarrier* gb, cudaStream_t st, int nparts);
+// Allows the single-CTA tail its shared memory (level table + part
+// descriptors); false when they do not fit.
+template <class T>
+bool vtail_one_prepare(int nlev, int nparts);
 int tail_max_blocks();
 void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st);
 template <class T>

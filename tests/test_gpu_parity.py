@@ -180,8 +180,9 @@ def test_vcycle_and_matvec_match_oracle(S, prob):
     r = P.SplitMix64(17).uniform_pm1(prob.n)
     rt = torch.as_tensor(r, device="cuda")
     zr = O.vcycle(h, r)
-    # one launch per level and step (default) and the single-block fused tail
-    for tail in (0, 1):
+    # one launch per level and step (default), the cooperative-grid tail and
+    # the single-CTA tail
+    for tail in (0, 1, 2):
         grid, A, solver = gpu_setup(S, prob, use_tail=tail)
         z = torch.zeros_like(rt)
         solver.precondition(rt, z)
@@ -192,7 +193,7 @@ def test_vcycle_and_matvec_match_oracle(S, prob):
         solver.level_matvec(l, torch.as_tensor(x, device="cuda"), y)
         assert rel(y.cpu().numpy(), O.matvec(lev, x)) <= OP_TOL, l
     # FP32 cycle against the FP64 cycle
-    for tail in (0, 1):
+    for tail in (0, 1, 2):
         _, _, s32 = gpu_setup(S, prob, precision=1, use_tail=tail)
         z32 = torch.zeros_like(rt)
         s32.precondition(rt, z32)
@@ -206,7 +207,7 @@ def test_pcg_matches_oracle(S, prob):
     bt = torch.as_tensor(b, device="cuda")
     tight = O.pcg(h, b, tol=1e-13, max_iter=500)
     at8 = O.pcg(h, b, tol=1e-8)
-    for graph, tail in ((1, 1), (0, 0)):
+    for graph, tail in ((1, 1), (0, 0), (1, 2)):
         grid, A, solver = gpu_setup(S, prob, tol=1e-13, max_iter=500, use_graph=graph, use_tail=tail)
         x = torch.zeros_like(bt)
         st = solver.solve(bt, x)
