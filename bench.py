@@ -303,8 +303,10 @@ def level_table(sv, name, stream):
     kinds = [("relax0_u", 2), ("residual", 0), ("restrict", 3), ("prolong_u", 4),
              ("relax", 1)]
     L = sv.num_levels()
-    out = [f"{name}: V-cycle {sv.time_kernel(5, 0, 20, stream):.1f} us, "
-           f"FP64 operator apply {sv.time_kernel(6, 0, 50, stream):.1f} us"]
+    out = [f"{name}: PCG iteration {sv.time_kernel(7, 0, 20, stream):.1f} us = V-cycle "
+           f"{sv.time_kernel(5, 0, 20, stream):.1f} us + FP64 operator apply "
+           f"{sv.time_kernel(6, 0, 50, stream):.1f} us + vector steps "
+           f"{sv.time_kernel(8, 0, 50, stream):.1f} us (+ U x of p)"]
     out.append("  lvl        N     nr " + " ".join(f"{k:>11s}" for k, _ in kinds))
     for l in range(L):
         n, nr, _ = sv.level_sizes(l)

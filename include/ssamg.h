@@ -238,7 +238,10 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * launch in microseconds.  kernel: 0 residual, 1 relaxation, 2 pre-relaxation
  * from zero (with U x), 3 restriction to level+1, 4 prolongation from level+1
  * (with U x), 5 whole V-cycle (level ignored), 6 the PCG's FP64 level-0
- * operator apply with its dot product (level ignored).  The kernels work on
+ * operator apply with its dot product (level ignored), 7 one whole PCG
+ * iteration, 8 the PCG's vector steps (beta, search direction, alpha, x and
+ * r updates).  Ids 7 and 8 clear the solve's convergence state, so that the
+ * replayed iterations never stop; the next solve starts afresh.  The kernels work on
  * the solver's own buffers (their contents are overwritten).  Synchronises
  * `stream`. */
 int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* us_per_launch,

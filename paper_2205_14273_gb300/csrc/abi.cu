@@ -1514,10 +1514,29 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
       case 6:  // FP64 operator apply of the PCG (q = A p with p.q partials)
         launch_pcg_alpha(s->lev[0], s->p, s->q, s->partial, s->sc, cs);
         break;
+      case 7:  // one PCG iteration (V-cycle, beta, p, q = A p, alpha, x and r)
+        enqueue_pcg_body(s, 0, 0, cs);
+        break;
+      case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
+        launch_pcg_beta_from_partials(s->z, s->p, s->lev[0].N, s->partial, 1, s->nblk_red, s->sc,
+                                      cs);
+        launch_pcg_update(s->p, s->q, s->x, s->r, s->lev[0].N, s->partial, s->nblk_red, s->sc, 0,
+                          0, cs);
+        break;
       default:
         throw SsamgError{SSAMG_ERR_ARG, "unknown kernel id"};
     }
   };
+  if (kernel == 7 || kernel == 8) {
+    // keep the iteration from stopping: no convergence test, no iteration cap
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+    s->h_sc->done = 0;
+    s->h_sc->status = 0;
+    s->h_sc->tol2bb = -1.0;
+    s->h_sc->max_iter = 1 << 30;
+    SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+  }
   cudaGraph_t g;
   SSAMG_CUDA(cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal));
   for (int t = 0; t < reps; ++t) one(s->cs);
