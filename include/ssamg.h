@@ -205,6 +205,43 @@ int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, v
  * Section 3.1 (W = +inf encoded as HUGE_VAL). */
 int ssamg_spacings(ssamg_solver s, double* c, double* W);
 
+/* ---------------------------------------------------------------------------
+ * Batching form (not in the paper, whose solver handles one system): many
+ * independent problems, and several right-hand sides each, solved together.
+ * The problems' parts become the parts of one semi-structured system with no
+ * couplings between problems.  One setup then builds every problem's
+ * hierarchy at once (Algorithm 1 and the Galerkin products act part by part;
+ * the parts of a problem that reaches one cell per part early stay through
+ * the remaining levels, where P is the identity and the coarsest direct solve
+ * stays exact), and every cycle kernel covers all problems in one launch per
+ * level.  PCG (Section 4) runs one instance per problem: its own dot
+ * products, step sizes and stopping test, until every problem has stopped.
+ * ------------------------------------------------------------------------- */
+typedef struct ssamg_batch_s* ssamg_batch;
+
+/* Batch of nprob assembled matrices, each on its own grid; all share the
+ * grid dimension and the stencil (same entries in the same order), else
+ * SSAMG_ERR_UNSUPPORTED.  Values and couplings are copied, so the matrices
+ * may be destroyed afterwards.  prm as for ssamg_solver_create (one setting
+ * for all problems).  Synchronises `stream`. */
+int ssamg_batch_create(int nprob, const ssamg_matrix* A, const ssamg_params* prm, void* stream,
+                       ssamg_batch* out);
+/* Builds the hierarchies of all problems (ssamg_setup on the union). */
+int ssamg_batch_setup(ssamg_batch B, void* stream);
+/* N, the number of unknowns of all problems together (-1 for NULL). */
+long long ssamg_batch_num_cells(ssamg_batch B);
+/* off[0..nprob]: the first unknown of each problem in a batch vector
+ * (off[nprob] = N); problem k's unknowns are in its own grid's order. */
+int ssamg_batch_offsets(ssamg_batch B, long long* off);
+/* Solves A_k x_kj = b_kj for every problem k and right-hand side j from
+ * x0 = 0.  b, x: device, nrhs x N doubles (right-hand side j at j N).
+ * st: NULL or nrhs x nprob stats, entry j nprob + k.  Returns SSAMG_OK when
+ * every instance converged, SSAMG_NOT_CONVERGED when one hit max_iter, else
+ * the first error.  Synchronises `stream` once per right-hand side. */
+int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int nrhs, void* stream,
+                      ssamg_stats* st);
+void ssamg_batch_destroy(ssamg_batch B);
+
 /* Blocks whose partial sums fit the static scratch of
  * ssamg_coupling_sums_noalloc: 3 doubles each, 1.5 MiB of device memory.
  * A level launch covers 1024 cells per block when the level has 300,000

@@ -139,7 +139,13 @@ struct ssamg_solver_s {
   int* h_int = nullptr;        // pinned scratch
   double* h_dbl = nullptr;
   int* d_err = nullptr;
-  int nblk_red = 0;
+  // problems: one, or a batch of independent problems in one hierarchy
+  int nprob = 1;
+  std::vector<int> part_prob;  // problem of each part (empty: all 0)
+  std::vector<long long> prob_cells;  // nprob + 1 first cells of each problem
+  int* pb = nullptr;           // nprob + 1 level-0 block starts of each problem (device)
+  PcgCtl* ctl = nullptr;
+  int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
@@ -627,9 +633,11 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   }
   L.nblk = blk[np];
   L.nfblk = fblk[np];
+  L.hblk = blk;
   for (int p = 0; p < np; ++p) {
     DPart& dp = L.dparts[p];
     fill_dpart(dp, L.parts[p]);
+    dp.prob = s->part_prob.empty() ? 0 : s->part_prob[p];
     dp.blk0 = blk[p];
     dp.fblk0 = fblk[p];
     dp.cpt = L.cpt;
@@ -684,10 +692,19 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->lev.reserve((size_t)s->prm.max_levels + 1);
   s->ready = false;
 
-  if (!s->h_sc) {
-    SSAMG_CUDA(cudaMallocHost(&s->h_sc, sizeof(PcgScalars)));
+  if (!s->part_prob.empty() && (int)s->part_prob.size() != np)
+    throw SsamgError{SSAMG_ERR_ARG, "the problem map does not match the grid's parts"};
+  if (s->h_cap < s->nprob) {
+    if (s->h_sc) cudaFreeHost(s->h_sc);
+    if (s->h_int) cudaFreeHost(s->h_int);
+    if (s->h_dbl) cudaFreeHost(s->h_dbl);
+    s->h_sc = nullptr;
+    s->h_int = nullptr;
+    s->h_dbl = nullptr;
+    SSAMG_CUDA(cudaMallocHost(&s->h_sc, sizeof(PcgScalars) * s->nprob));
     SSAMG_CUDA(cudaMallocHost(&s->h_int, sizeof(int) * 16));
-    SSAMG_CUDA(cudaMallocHost(&s->h_dbl, sizeof(double) * 16));
+    SSAMG_CUDA(cudaMallocHost(&s->h_dbl, sizeof(double) * (2 * s->nprob + 16)));
+    s->h_cap = s->nprob;
   }
 
   // ---- level 0 from the matrix
@@ -1027,10 +1044,25 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->p = (double*)padded_vector(s, sizeof(double), N, L0g, st);
   s->q = aalloc<double>(s->arena, N);
   s->zprev = aalloc<double>(s->arena, N);
-  s->nblk_red = reduce_blocks(N);
-  s->partial = aalloc<double>(s->arena, 2ll * std::max<long long>(L0.nblk, s->nblk_red));
-  s->tres = aalloc<double>(s->arena, 2);
-  s->sc = aalloc<PcgScalars>(s->arena, 1);
+  s->partial = aalloc<double>(s->arena, 2ll * L0.nblk);
+  s->tres = aalloc<double>(s->arena, 2ll * s->nprob);
+  s->sc = aalloc<PcgScalars>(s->arena, s->nprob);
+  s->ctl = aalloc<PcgCtl>(s->arena, 1);
+  SSAMG_CUDA(cudaMemsetAsync(s->ctl, 0, sizeof(PcgCtl), st));
+  {
+    // level-0 block and cell ranges of each problem (parts are problem-ordered)
+    std::vector<int> hpb(s->nprob + 1, L0.nblk);
+    s->prob_cells.assign(s->nprob + 1, N);
+    for (int p = L0.np - 1; p >= 0; --p) {
+      const int k = s->part_prob.empty() ? 0 : s->part_prob[p];
+      hpb[k] = L0.hblk[p];
+      s->prob_cells[k] = L0.parts[p].off;
+    }
+    s->pb = aalloc<int>(s->arena, s->nprob + 1);
+    SSAMG_CUDA(cudaMemcpyAsync(s->pb, hpb.data(), sizeof(int) * (s->nprob + 1),
+                               cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));  // hpb is a host temporary
+  }
   s->ready = true;
 }
 
@@ -1128,29 +1160,31 @@ int vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st, double* 
 
 // PCG segments.  init: r = b - A x; the first iteration is peeled so that the
 // loop body starts with the V-cycle and ends with the convergence test.
+PcgCtx pcg_ctx(ssamg_solver s) { return PcgCtx{s->pb, s->nprob, s->sc, s->ctl, s->partial}; }
+
 void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
   Level& L0 = s->lev[0];
-  long long N = L0.N;
   double* zp = s->prm.flexible ? s->zprev : nullptr;
-  launch_pcg_init(L0, s->b, s->x, s->r, s->partial, s->sc, st);
+  const PcgCtx c = pcg_ctx(s);
+  launch_pcg_init(L0, s->b, s->x, s->r, c, st);
   vcycle(s, s->r, s->z, st);
-  launch_pcg_start(s->r, s->z, s->p, zp, N, s->partial, s->nblk_red, s->sc, st);
-  launch_pcg_alpha(L0, s->p, s->q, s->partial, s->sc, st);
-  launch_pcg_update(s->p, s->q, s->x, s->r, N, s->partial, s->nblk_red, s->sc, h, use_h, st);
+  launch_pcg_start(L0, s->r, s->z, s->p, zp, c, st);
+  launch_pcg_alpha(L0, s->p, s->q, c, st);
+  launch_pcg_update(L0, s->p, s->q, s->x, s->r, c, h, use_h, st);
 }
 
 void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
   Level& L0 = s->lev[0];
-  long long N = L0.N;
   double* zp = s->prm.flexible ? s->zprev : nullptr;
   // the cycle's last kernel also forms r.z (and r.zprev) for beta
+  const PcgCtx c = pcg_ctx(s);
   const int npart = vcycle(s, s->r, s->z, st, s->partial, zp);
   if (npart > 0)
-    launch_pcg_beta_from_partials(s->z, s->p, N, s->partial, npart, s->nblk_red, s->sc, st);
+    launch_pcg_beta_from_partials(L0, s->z, s->p, c, st);
   else
-    launch_pcg_beta(s->r, s->z, zp, s->p, N, s->partial, s->nblk_red, s->sc, st);
-  launch_pcg_alpha(L0, s->p, s->q, s->partial, s->sc, st);
-  launch_pcg_update(s->p, s->q, s->x, s->r, N, s->partial, s->nblk_red, s->sc, h, use_h, st);
+    launch_pcg_beta(L0, s->r, s->z, zp, s->p, c, st);
+  launch_pcg_alpha(L0, s->p, s->q, c, st);
+  launch_pcg_update(L0, s->p, s->q, s->x, s->r, c, h, use_h, st);
 }
 
 void build_pcg_graph(ssamg_solver s) {
@@ -1189,31 +1223,37 @@ void build_pcg_graph(ssamg_solver s) {
   cudaGraphDestroy(g);
 }
 
+// Runs the PCG of every problem of the solver on s->b, s->x (x0 given);
+// stats, when set, receives one entry per problem.  Returns the worst status.
 int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
-  PcgScalars init;
-  std::memset(&init, 0, sizeof(init));
-  init.tol = s->prm.tol;
-  init.max_iter = s->prm.max_iter;
-  init.flexible = s->prm.flexible;
-  SSAMG_CUDA(cudaMemcpyAsync(s->sc, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  const int np = s->nprob;
+  std::vector<PcgScalars> init(np);
+  for (auto& v : init) {
+    std::memset(&v, 0, sizeof(v));
+    v.tol = s->prm.tol;
+    v.max_iter = s->prm.max_iter;
+    v.flexible = s->prm.flexible;
+  }
+  SSAMG_CUDA(cudaMemcpyAsync(s->sc, init.data(), sizeof(PcgScalars) * np, cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));  // init is a host temporary
   if (s->prm.use_graph) {
     if (!s->graphs.pcg) build_pcg_graph(s);
     SSAMG_CUDA(cudaGraphLaunch(s->graphs.pcg, st));
-    SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
-    SSAMG_CUDA(cudaStreamSynchronize(st));
   } else {
     long long c0 = g_ssamg_launches;
     enqueue_pcg_head(s, 0, 0, st);
     s->head_launches = g_ssamg_launches - c0;
     for (;;) {
-      SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_int, &s->ctl->active, sizeof(int), cudaMemcpyDeviceToHost, st));
       SSAMG_CUDA(cudaStreamSynchronize(st));
-      if (s->h_sc->done) break;
+      if (!s->h_int[0]) break;
       c0 = g_ssamg_launches;
       enqueue_pcg_body(s, 0, 0, st);
       s->body_launches = g_ssamg_launches - c0;
     }
   }
+  SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars) * np, cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
   if (s->tail_bar) {
     SSAMG_CUDA(cudaMemcpyAsync(s->h_int, &s->tail_bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -1222,15 +1262,9 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
       throw SsamgError{SSAMG_ERR_TIMEOUT, "a grid barrier of the coarse-level kernel timed out"};
     }
   }
-  const PcgScalars& r = *s->h_sc;
+  int maxit = 0;
+  for (int k = 0; k < np; ++k) maxit = std::max(maxit, s->h_sc[k].iter);
   if (stats) {
-    stats->iterations = r.iter;
-    stats->setup_kernel_launches = s->setup_launches;
-    stats->solve_kernel_launches = s->head_launches + (long long)(r.iter > 0 ? r.iter - 1 : 0) * s->body_launches;
-    stats->converged = r.status == 0 && r.rr <= r.tol2bb;
-    stats->rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
-    stats->num_levels = (int)s->lev.size();
-    stats->coarse_size = s->lev.back().N;
     double nnz0 = 0, nnz = 0;
     for (size_t l = 0; l < s->lev.size(); ++l) {
       double n = (double)s->lev[l].nnz;
@@ -1238,14 +1272,31 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
       nnz += n;
       if (l == 0) nnz0 = n;
     }
-    stats->operator_complexity = nnz / nnz0;
-    launch_true_residual(s->lev[0], s->b, s->x, s->q, s->partial, s->tres, st);
-    SSAMG_CUDA(cudaMemcpyAsync(s->h_dbl, s->tres, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    launch_true_residual(s->lev[0], s->b, s->x, s->q, pcg_ctx(s), s->tres, st);
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_dbl, s->tres, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));
-    stats->true_rel_res = s->h_dbl[0] > 0 ? std::sqrt(s->h_dbl[1] / s->h_dbl[0]) : 0.0;
+    for (int k = 0; k < np; ++k) {
+      const PcgScalars& r = s->h_sc[k];
+      ssamg_stats& o = stats[k];
+      o.iterations = r.iter;
+      o.setup_kernel_launches = s->setup_launches;
+      // the loop runs until the slowest problem stops
+      o.solve_kernel_launches = s->head_launches + (long long)(maxit > 0 ? maxit - 1 : 0) * s->body_launches;
+      o.converged = r.status == 0 && r.rr <= r.tol2bb;
+      o.rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
+      o.num_levels = (int)s->lev.size();
+      o.coarse_size = s->lev.back().N;
+      o.operator_complexity = nnz / nnz0;
+      o.true_rel_res = s->h_dbl[2 * k] > 0 ? std::sqrt(s->h_dbl[2 * k + 1] / s->h_dbl[2 * k]) : 0.0;
+    }
   }
-  if (r.status != 0) return r.status;
-  return r.rr <= r.tol2bb ? SSAMG_OK : SSAMG_NOT_CONVERGED;
+  int rc = SSAMG_OK;
+  for (int k = 0; k < np; ++k) {
+    const PcgScalars& r = s->h_sc[k];
+    if (r.status != 0) return r.status;
+    if (!(r.rr <= r.tol2bb)) rc = SSAMG_NOT_CONVERGED;
+  }
+  return rc;
 }
 
 }  // namespace
@@ -1359,6 +1410,133 @@ extern "C" int ssamg_level_matvec(ssamg_solver s, int level, const double* x, do
   return SSAMG_OK;
   API_END
 }
+
+// ---------------------------------------------------------------------------
+// Batching form: independent problems as the parts of one system
+// ---------------------------------------------------------------------------
+struct ssamg_batch_s {
+  int nprob = 0;
+  ssamg_grid g = nullptr;
+  ssamg_matrix A = nullptr;
+  ssamg_solver s = nullptr;
+  std::vector<long long> off;  // nprob + 1 first unknowns
+  ~ssamg_batch_s() {
+    ssamg_solver_destroy(s);
+    ssamg_matrix_destroy(A);
+    ssamg_grid_destroy(g);
+  }
+};
+
+namespace {
+void check(int rc) {
+  if (rc != SSAMG_OK) throw SsamgError{rc, g_last_error};
+}
+}  // namespace
+
+extern "C" int ssamg_batch_create(int nprob, const ssamg_matrix* A, const ssamg_params* prm,
+                                  void* stream, ssamg_batch* out) {
+  if (!out || !A || nprob < 1) return SSAMG_ERR_ARG;
+  for (int k = 0; k < nprob; ++k) {
+    if (!A[k]) return SSAMG_ERR_ARG;
+    if (!A[k]->assembled) return SSAMG_ERR_STATE;
+  }
+  const ssamg_matrix A0 = A[0];
+  for (int k = 1; k < nprob; ++k) {
+    if (A[k]->g->ndim != A0->g->ndim || A[k]->nent != A0->nent) return SSAMG_ERR_UNSUPPORTED;
+    for (int e = 0; e < A0->nent; ++e)
+      for (int d = 0; d < 3; ++d)
+        if (A[k]->o[e][d] != A0->o[e][d]) return SSAMG_ERR_UNSUPPORTED;
+  }
+  API_BEGIN
+  std::unique_ptr<ssamg_batch_s> B(new ssamg_batch_s);
+  B->nprob = nprob;
+  int total = 0;
+  B->off.assign(nprob + 1, 0);
+  for (int k = 0; k < nprob; ++k) {
+    total += A[k]->g->nparts;
+    B->off[k + 1] = B->off[k] + A[k]->g->N;
+  }
+  // union grid: the problems' parts in problem order
+  check(ssamg_grid_create(A0->g->ndim, total, &B->g));
+  std::vector<int> part_prob;
+  part_prob.reserve(total);
+  for (int k = 0, P = 0; k < nprob; ++k) {
+    const ssamg_grid g = A[k]->g;
+    for (int q = 0; q < g->nparts; ++q, ++P) {
+      check(ssamg_grid_set_box(B->g, P, g->lo[q].data(), g->hi[q].data()));
+      part_prob.push_back(k);
+    }
+  }
+  check(ssamg_grid_assemble(B->g));
+  // union matrix: the same stencil; values copied part by part (device to
+  // device), couplings with their parts renumbered
+  std::vector<int> offs(3 * A0->nent);
+  for (int e = 0; e < A0->nent; ++e)
+    for (int d = 0; d < 3; ++d) offs[3 * e + d] = A0->o[e][d];
+  check(ssamg_matrix_create(B->g, A0->nent, offs.data(), &B->A));
+  for (int k = 0, P = 0; k < nprob; ++k) {
+    const ssamg_matrix M = A[k];
+    for (int q = 0; q < M->g->nparts; ++q, ++P)
+      for (int e = 0; e < M->nent; ++e) {
+        if (M->isvar[q][e])
+          check(ssamg_matrix_set_box_values(B->A, P, e, M->coef + M->coef_off[q][e], 1));
+        else
+          check(ssamg_matrix_set_constant(B->A, P, e, M->cval[q][e]));
+      }
+    const long long nc = (long long)M->c_val.size();
+    if (nc > 0) {
+      std::vector<int> pp(M->c_part), np_(M->c_npart);
+      for (auto& v : pp) v += P - M->g->nparts;
+      for (auto& v : np_) v += P - M->g->nparts;
+      check(ssamg_matrix_add_couplings(B->A, nc, pp.data(), M->c_idx.data(), M->c_dir.data(),
+                                       np_.data(), M->c_nidx.data(), M->c_val.data()));
+    }
+  }
+  check(ssamg_matrix_assemble(B->A, stream));
+  check(ssamg_solver_create(prm, &B->s));
+  B->s->nprob = nprob;
+  B->s->part_prob = std::move(part_prob);
+  *out = B.release();
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_batch_setup(ssamg_batch B, void* stream) {
+  if (!B) return SSAMG_ERR_ARG;
+  return ssamg_setup(B->s, B->A, stream);
+}
+
+extern "C" long long ssamg_batch_num_cells(ssamg_batch B) { return B ? B->off.back() : -1; }
+
+extern "C" int ssamg_batch_offsets(ssamg_batch B, long long* off) {
+  if (!B || !off) return SSAMG_ERR_ARG;
+  std::copy(B->off.begin(), B->off.end(), off);
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int nrhs, void* stream,
+                                 ssamg_stats* st) {
+  if (!B || !b || !x || nrhs < 1) return SSAMG_ERR_ARG;
+  ssamg_solver s = B->s;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  cudaStream_t cst = (cudaStream_t)stream;
+  API_BEGIN
+  PdlScope pdl(s->prm.use_pdl);
+  const long long N = s->lev[0].N;
+  int rc = SSAMG_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    SSAMG_CUDA(cudaMemcpyAsync(s->b, b + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, cst));
+    SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, cst));
+    const int r = run_pcg(s, cst, st ? st + (long long)j * B->nprob : nullptr);
+    SSAMG_CUDA(cudaMemcpyAsync(x + j * N, s->x, sizeof(double) * N, cudaMemcpyDeviceToDevice, cst));
+    if (r < 0) return r;
+    if (r > rc) rc = r;
+  }
+  return rc;
+  API_END
+}
+
+extern "C" void ssamg_batch_destroy(ssamg_batch B) { delete B; }
 
 // ---------------------------------------------------------------------------
 // Introspection
@@ -1512,16 +1690,14 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
         vcycle(s, s->r, s->z, cs);
         break;
       case 6:  // FP64 operator apply of the PCG (q = A p with p.q partials)
-        launch_pcg_alpha(s->lev[0], s->p, s->q, s->partial, s->sc, cs);
+        launch_pcg_alpha(s->lev[0], s->p, s->q, pcg_ctx(s), cs);
         break;
       case 7:  // one PCG iteration (V-cycle, beta, p, q = A p, alpha, x and r)
         enqueue_pcg_body(s, 0, 0, cs);
         break;
       case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
-        launch_pcg_beta_from_partials(s->z, s->p, s->lev[0].N, s->partial, 1, s->nblk_red, s->sc,
-                                      cs);
-        launch_pcg_update(s->p, s->q, s->x, s->r, s->lev[0].N, s->partial, s->nblk_red, s->sc, 0,
-                          0, cs);
+        launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), cs);
+        launch_pcg_update(s->lev[0], s->p, s->q, s->x, s->r, pcg_ctx(s), 0, 0, cs);
         break;
       default:
         throw SsamgError{SSAMG_ERR_ARG, "unknown kernel id"};
@@ -1529,13 +1705,17 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
   };
   if (kernel == 7 || kernel == 8) {
     // keep the iteration from stopping: no convergence test, no iteration cap
-    SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_sc, s->sc, sizeof(PcgScalars) * s->nprob,
+                               cudaMemcpyDeviceToHost, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));
-    s->h_sc->done = 0;
-    s->h_sc->status = 0;
-    s->h_sc->tol2bb = -1.0;
-    s->h_sc->max_iter = 1 << 30;
-    SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->h_sc, sizeof(PcgScalars), cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < s->nprob; ++k) {
+      s->h_sc[k].done = 0;
+      s->h_sc[k].status = 0;
+      s->h_sc[k].tol2bb = -1.0;
+      s->h_sc[k].max_iter = 1 << 30;
+    }
+    SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->h_sc, sizeof(PcgScalars) * s->nprob,
+                               cudaMemcpyHostToDevice, st));
   }
   cudaGraph_t g;
   SSAMG_CUDA(cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal));

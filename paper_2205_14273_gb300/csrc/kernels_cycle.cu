@@ -573,16 +573,21 @@ __global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const dou
 }
 
 // ---------------------------------------------------------------------------
-// PCG (FP64).  Dot products are block partial sums plus a one-block final
-// sum in a fixed order, so results are bitwise reproducible.
+// PCG (FP64), one instance per problem of the solver: a single problem, or a
+// batch of independent problems that share one hierarchy.  Every vector
+// kernel runs over the level-0 cell tiles, so each block belongs to one part
+// and hence one problem (DPart::prob); the level-0 blocks of problem k are
+// pb[k] .. pb[k+1]-1.  A dot product is a partial sum per block plus one
+// final sum per problem in a fixed order (bitwise reproducible).  Once a
+// problem has stopped (sc[k].done) its x and r no longer change.
 // ---------------------------------------------------------------------------
 template <int K>
-__device__ __forceinline__ void finish_sums(const double* __restrict__ partial, int nblk,
+__device__ __forceinline__ void finish_sums(const double* __restrict__ partial, int b0, int b1,
                                             double* out) {
   __shared__ double sh[NT / 32];
   for (int q = 0; q < K; ++q) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += NT) s += partial[(long long)K * b + q];
+    for (int b = b0 + threadIdx.x; b < b1; b += NT) s += partial[(long long)K * b + q];
     double r = block_sum<NT>(s, sh);
     if (threadIdx.x == 0) out[q] = r;
   }
@@ -596,13 +601,11 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int p = block_part(L.blk, L.parts, L.np, sp);
+  block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
   double bb = 0.0, rr = 0.0;
   TILE_LOOP(c, sp) {
-    int i, j, k;
-    cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
     double bv = b[g];
     double rv = bv - apply_A_sh<SH>(L, sp, x, c);
@@ -618,34 +621,40 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
   }
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ partial, int nblk,
-                                                     PcgScalars* sc) {
+// per problem (one block each): ||b||^2, ||r||^2 and the stopping threshold
+__global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ partial,
+                                                     const int* __restrict__ pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[2];
-  finish_sums<2>(partial, nblk, out);
+  const int k = blockIdx.x;
+  finish_sums<2>(partial, pb[k], pb[k + 1], out);
   if (threadIdx.x == 0) {
-    sc->bb = out[0];
-    sc->rr = out[1];
-    sc->tol2bb = sc->tol * sc->tol * out[0];
-    sc->iter = 0;
-    sc->status = 0;
-    sc->done = (out[1] <= sc->tol2bb) ? 1 : 0;
+    PcgScalars& S = sc[k];
+    S.bb = out[0];
+    S.rr = out[1];
+    S.tol2bb = S.tol * S.tol * out[0];
+    S.iter = 0;
+    S.status = 0;
+    S.done = (out[1] <= S.tol2bb) ? 1 : 0;
   }
 }
 
 // p = z (and zprev = z for flexible CG); partial r.z
-__global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
+__global__ void __launch_bounds__(NT) k_pcg_start(LevelView<double> L, const double* __restrict__ r,
                                                   const double* __restrict__ z,
                                                   double* __restrict__ p, double* __restrict__ zprev,
-                                                  int flex, long long n, double* __restrict__ partial) {
+                                                  int flex, double* __restrict__ partial) {
   pdl_trigger();
-  pdl_wait();
+  __shared__ DPart sp;
   __shared__ double sh[NT / 32];
+  block_part(L.blk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
   double s = 0.0;
-#pragma unroll 4
-  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
-    double zv = z[g];
+  TILE_LOOP(c, sp) {
+    const int g = sp.off + c;
+    const double zv = z[g];
     p[g] = zv;
     if (flex) zprev[g] = zv;
     s = fma(r[g], zv, s);
@@ -654,38 +663,44 @@ __global__ void __launch_bounds__(NT) k_pcg_start(const double* __restrict__ r,
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-__device__ __forceinline__ void set_continue(PcgScalars* sc, cudaGraphConditionalHandle h,
+__device__ __forceinline__ void set_continue(int active, cudaGraphConditionalHandle h,
                                              int use_handle) {
-  if (use_handle) cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+  if (use_handle) cudaGraphSetConditional(h, active ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__ partial, int nblk,
-                                                      PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__ partial,
+                                                      const int* __restrict__ pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
-  finish_sums<1>(partial, nblk, out);
-  if (threadIdx.x == 0 && !sc->done) {
-    sc->rz = out[0];
+  const int k = blockIdx.x;
+  finish_sums<1>(partial, pb[k], pb[k + 1], out);
+  PcgScalars& S = sc[k];
+  if (threadIdx.x == 0 && !S.done) {
+    S.rz = out[0];
     if (!(out[0] > 0.0) || !isfinite(out[0])) {
-      sc->status = SSAMG_ERR_BREAKDOWN;
-      sc->done = 1;
+      S.status = SSAMG_ERR_BREAKDOWN;
+      S.done = 1;
     }
   }
 }
 
 // partial (r.z, r.zprev) for beta; zprev takes the new z (flexible CG)
-__global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r,
+__global__ void __launch_bounds__(NT) k_pcg_dots_rz(LevelView<double> L,
+                                                    const double* __restrict__ r,
                                                     const double* __restrict__ z,
                                                     double* __restrict__ zprev, int flex,
-                                                    long long n, double* __restrict__ partial) {
+                                                    double* __restrict__ partial) {
   pdl_trigger();
-  pdl_wait();
+  __shared__ DPart sp;
   __shared__ double sh[NT / 32];
+  block_part(L.blk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
   double s0 = 0.0, s1 = 0.0;
-#pragma unroll 4
-  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
-    double rv = r[g], zv = z[g];
+  TILE_LOOP(c, sp) {
+    const int g = sp.off + c;
+    const double rv = r[g], zv = z[g];
     s0 = fma(rv, zv, s0);
     if (flex) {
       s1 = fma(rv, zprev[g], s1);
@@ -700,33 +715,42 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(const double* __restrict__ r
   }
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ partial, int nblk,
-                                                     PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ partial,
+                                                     const int* __restrict__ pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[2];
-  finish_sums<2>(partial, nblk, out);
-  if (threadIdx.x == 0 && !sc->done) {
+  const int k = blockIdx.x;
+  finish_sums<2>(partial, pb[k], pb[k + 1], out);
+  PcgScalars& S = sc[k];
+  if (threadIdx.x == 0 && !S.done) {
     double rz = out[0];
-    double num = sc->flexible ? (rz - out[1]) : rz;
-    sc->beta = num / sc->rz;
-    sc->rz = rz;
-    if (!isfinite(rz) || !isfinite(sc->beta)) {
-      sc->status = SSAMG_ERR_BREAKDOWN;
-      sc->done = 1;
+    double num = S.flexible ? (rz - out[1]) : rz;
+    S.beta = num / S.rz;
+    S.rz = rz;
+    if (!isfinite(rz) || !isfinite(S.beta)) {
+      S.status = SSAMG_ERR_BREAKDOWN;
+      S.done = 1;
     }
   }
 }
 
-__global__ void k_pcg_xpby(const double* __restrict__ z, double* __restrict__ p, long long n,
-                           const PcgScalars* __restrict__ sc) {
+// p = z + beta p (per problem)
+__global__ void __launch_bounds__(NT) k_pcg_xpby(LevelView<double> L, const double* __restrict__ z,
+                                                 double* __restrict__ p,
+                                                 const PcgScalars* __restrict__ sc) {
   pdl_trigger();
+  __shared__ DPart sp;
+  block_part(L.blk, L.parts, L.np, sp);
+  __syncthreads();
   pdl_wait();
-  if (sc->done) return;
-  double beta = sc->beta;
-#pragma unroll 4
-  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT)
+  const PcgScalars& S = sc[sp.prob];
+  if (S.done) return;
+  const double beta = S.beta;
+  TILE_LOOP(c, sp) {
+    const int g = sp.off + c;
     p[g] = fma(beta, p[g], z[g]);
+  }
 }
 
 // q = A p; partial p.q
@@ -737,13 +761,11 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, con
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  int pt = block_part(L.blk, L.parts, L.np, sp);
+  block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
   double s = 0.0;
   TILE_LOOP(c, sp) {
-    int i, j, k;
-    cell_coords(sp, c, i, j, k);
     int g = sp.off + c;
     double qv = apply_A_sh<SH>(L, sp, p, c);
     q[g] = qv;
@@ -753,41 +775,47 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, con
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__ partial, int nblk,
-                                                      PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__ partial,
+                                                      const int* __restrict__ pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
-  finish_sums<1>(partial, nblk, out);
-  if (threadIdx.x == 0 && !sc->done) {
+  const int k = blockIdx.x;
+  finish_sums<1>(partial, pb[k], pb[k + 1], out);
+  PcgScalars& S = sc[k];
+  if (threadIdx.x == 0 && !S.done) {
     double pq = out[0];
-    sc->pq = pq;
+    S.pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {
-      sc->status = SSAMG_ERR_BREAKDOWN;
-      sc->done = 1;
-      sc->alpha = 0.0;
+      S.status = SSAMG_ERR_BREAKDOWN;
+      S.done = 1;
+      S.alpha = 0.0;
     } else {
-      sc->alpha = sc->rz / pq;
+      S.alpha = S.rz / pq;
     }
   }
 }
 
-// x += alpha p; r -= alpha q; partial r.r
-__global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
+// x += alpha p; r -= alpha q; partial r.r (per problem)
+__global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const double* __restrict__ p,
                                                    const double* __restrict__ q,
                                                    double* __restrict__ x, double* __restrict__ r,
-                                                   long long n, double* __restrict__ partial,
+                                                   double* __restrict__ partial,
                                                    const PcgScalars* __restrict__ sc) {
   pdl_trigger();
-  pdl_wait();
+  __shared__ DPart sp;
   __shared__ double sh[NT / 32];
-  if (sc->done) return;
-  double alpha = sc->alpha;
+  block_part(L.blk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  const PcgScalars& S = sc[sp.prob];
+  if (S.done) return;  // the problem's final sum ignores this block's partial
+  const double alpha = S.alpha;
   double s = 0.0;
-#pragma unroll 4
-  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < n; g += (long long)gridDim.x * NT) {
+  TILE_LOOP(c, sp) {
+    const int g = sp.off + c;
     x[g] = fma(alpha, p[g], x[g]);
-    double rv = fma(-alpha, q[g], r[g]);
+    const double rv = fma(-alpha, q[g], r[g]);
     r[g] = rv;
     s = fma(rv, rv, s);
   }
@@ -795,34 +823,55 @@ __global__ void __launch_bounds__(NT) k_pcg_update(const double* __restrict__ p,
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict__ partial, int nblk,
-                                                       PcgScalars* sc, cudaGraphConditionalHandle h,
+// Per problem: ||r||^2, iteration count and the stopping test.  The last
+// block to finish (ticket counter) sets ctl->active to whether any problem
+// still iterates and, inside the solve graph, the loop condition with it.
+__global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict__ partial,
+                                                       const int* __restrict__ pb, PcgScalars* sc,
+                                                       PcgCtl* ctl, cudaGraphConditionalHandle h,
                                                        int use_handle) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
-  bool was_done = sc->done;
-  finish_sums<1>(partial, nblk, out);
+  __shared__ bool last;
+  const int k = blockIdx.x;
+  PcgScalars& S = sc[k];
+  const bool was_done = S.done;
+  finish_sums<1>(partial, pb[k], pb[k + 1], out);
   if (threadIdx.x == 0) {
     if (!was_done) {
-      sc->rr = out[0];
-      sc->iter += 1;
-      if (!isfinite(out[0])) sc->status = SSAMG_ERR_BREAKDOWN;
-      if (sc->status != 0 || out[0] <= sc->tol2bb || sc->iter >= sc->max_iter) sc->done = 1;
+      S.rr = out[0];
+      S.iter += 1;
+      if (!isfinite(out[0])) S.status = SSAMG_ERR_BREAKDOWN;
+      if (S.status != 0 || out[0] <= S.tol2bb || S.iter >= S.max_iter) S.done = 1;
     }
-    set_continue(sc, h, use_handle);
+    __threadfence();
+    last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    int active = 0;
+    for (int q = 0; q < (int)gridDim.x; ++q)
+      active |= !*reinterpret_cast<volatile const int*>(&sc[q].done);
+    ctl->ticket = 0;
+    ctl->active = active;
+    set_continue(active, h, use_handle);
   }
 }
 
-__global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ partial, int nblk,
-                                                     double* out) {
+// per problem: (||b||^2, ||b - A x||^2)
+__global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ partial,
+                                                     const int* __restrict__ pb,
+                                                     double* __restrict__ out) {
   pdl_trigger();
   pdl_wait();
   __shared__ double o2[2];
-  finish_sums<2>(partial, nblk, o2);
+  const int k = blockIdx.x;
+  finish_sums<2>(partial, pb[k], pb[k + 1], o2);
   if (threadIdx.x == 0) {
-    out[0] = o2[0];
-    out[1] = o2[1];
+    out[2 * k] = o2[0];
+    out[2 * k + 1] = o2[1];
   }
 }
 
@@ -1081,68 +1130,68 @@ void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) 
   SSAMG_LAUNCH_CHECK();
 }
 
-int reduce_blocks(long long n) {
-  long long nb = (n + NT - 1) / NT;
-  return (int)std::min<long long>(std::max<long long>(nb, 1), 152 * 8);
-}
-
-void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
-                     PcgScalars* sc, cudaStream_t st) {
+void launch_pcg_init(const Level& L, const double* b, const double* x, double* r,
+                     const PcgCtx& c, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
+                                 c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_init_fin, 1, NT, 0, st, partial, L.nblk, sc);
+  launch_k(k_pcg_init_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
-                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
+void launch_pcg_start(const Level& L0, const double* r, const double* z, double* p, double* zprev,
+                      const PcgCtx& c, cudaStream_t st) {
   // zprev may be null (no flexible CG): pass a valid buffer and a flag
-  launch_k(k_pcg_start, nblk, NT, 0, st, r, z, p, zprev ? zprev : p, zprev != nullptr, n, partial);
+  launch_k(k_pcg_start, L0.nblk, NT, 0, st, L0.view<double>(), r, z, p, zprev ? zprev : p,
+           zprev != nullptr, c.partial);
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_start_fin, 1, NT, 0, st, partial, nblk, sc);
-  SSAMG_LAUNCH_CHECK();
-}
-
-void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
-                     double* partial, int nblk, PcgScalars* sc, cudaStream_t st) {
-  launch_k(k_pcg_dots_rz, nblk, NT, 0, st, r, z, zprev ? zprev : p, zprev != nullptr, n, partial);
-  SSAMG_LAUNCH_CHECK();
-  launch_pcg_beta_from_partials(z, p, n, partial, nblk, nblk, sc, st);
-}
-
-void launch_pcg_beta_from_partials(const double* z, double* p, long long n, const double* partial,
-                                   int npart, int nblk, PcgScalars* sc, cudaStream_t st) {
-  launch_k(k_pcg_beta_fin, 1, NT, 0, st, partial, npart, sc);
-  SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_xpby, nblk, NT, 0, st, z, p, n, sc);
+  launch_k(k_pcg_start_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
-                      PcgScalars* sc, cudaStream_t st) {
+void launch_pcg_beta(const Level& L0, const double* r, const double* z, double* zprev, double* p,
+                     const PcgCtx& c, cudaStream_t st) {
+  launch_k(k_pcg_dots_rz, L0.nblk, NT, 0, st, L0.view<double>(), r, z, zprev ? zprev : p,
+           zprev != nullptr, c.partial);
+  SSAMG_LAUNCH_CHECK();
+  launch_pcg_beta_from_partials(L0, z, p, c, st);
+}
+
+void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, const PcgCtx& c,
+                                   cudaStream_t st) {
+  launch_k(k_pcg_beta_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
+  SSAMG_LAUNCH_CHECK();
+  launch_k(k_pcg_xpby, L0.nblk, NT, 0, st, L0.view<double>(), z, p, c.sc);
+  SSAMG_LAUNCH_CHECK();
+}
+
+void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& c,
+                      cudaStream_t st) {
   launch_uy<double>(L, p, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q,
+                                 c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_alpha_fin, 1, NT, 0, st, partial, L.nblk, sc);
+  launch_k(k_pcg_alpha_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,
-                       double* partial, int nblk, PcgScalars* sc, cudaGraphConditionalHandle h,
-                       int use_handle, cudaStream_t st) {
-  launch_k(k_pcg_update, nblk, NT, 0, st, p, q, x, r, n, partial, sc);
+void launch_pcg_update(const Level& L0, const double* p, const double* q, double* x, double* r,
+                       const PcgCtx& c, cudaGraphConditionalHandle h, int use_handle,
+                       cudaStream_t st) {
+  launch_k(k_pcg_update, L0.nblk, NT, 0, st, L0.view<double>(), p, q, x, r, c.partial, c.sc);
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_update_fin, 1, NT, 0, st, partial, nblk, sc, h, use_handle);
+  launch_k(k_pcg_update_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc, c.ctl, h, use_handle);
   SSAMG_LAUNCH_CHECK();
 }
 
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
-                          double* partial, double* out, cudaStream_t st) {
+                          const PcgCtx& c, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r, partial)));
+  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
+                                 c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_true_res_fin, 1, NT, 0, st, partial, L.nblk, out);
+  launch_k(k_true_res_fin, c.nprob, NT, 0, st, c.partial, c.pb, out);
   SSAMG_LAUNCH_CHECK();
 }
 

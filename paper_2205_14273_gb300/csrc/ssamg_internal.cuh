@@ -86,6 +86,7 @@ struct DPart {
   int canon27;                 // 27 entries in offset-code order (entry e has code e)
   unsigned varmask;            // bit e: entry e is per cell
   int zeroext;                 // per-cell entries are exactly zero where c + o leaves the box
+  int prob;                    // problem of the part (a batch of independent problems)
   FastDiv dx, dxy;             // divide by n[0], n[0]*n[1]
   FastDiv cdx, cdxy;           // same on the next level
   FastDiv fdx, fdxy;           // same on the fine-point grid
@@ -100,6 +101,23 @@ static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
 struct PcgScalars {
   double tol, bb, rr, rz, pq, alpha, beta, tol2bb;
   int iter, max_iter, status, flexible, done, pad_;
+};
+
+// Loop control of a (batched) PCG solve: the ticket of the per-problem final
+// kernel and whether any problem still iterates.
+struct PcgCtl {
+  unsigned ticket;
+  int active;
+};
+
+// Device state the PCG launchers share: one PcgScalars per problem, the
+// level-0 block range of each problem (pb[0..nprob]) and the block partials.
+struct PcgCtx {
+  const int* pb;
+  int nprob;
+  PcgScalars* sc;
+  PcgCtl* ctl;
+  double* partial;
 };
 
 // Views passed to kernels by value.
@@ -196,6 +214,7 @@ struct Level {
   int nblk = 0, nfblk = 0;
   int cpt = 1;
   int shape = 0;  // StencilShape of the level's operator apply
+  std::vector<int> hblk;  // host copy of the block starts of cell-wise launches
   double* coef = nullptr;
   float* coef32 = nullptr;
   long long ncoef = 0;
@@ -342,22 +361,21 @@ void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st)
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st);
 
 // PCG (FP64)
-void launch_pcg_init(const Level& L, const double* b, const double* x, double* r, double* partial,
-                     PcgScalars* sc, cudaStream_t st);
-void launch_pcg_start(const double* r, const double* z, double* p, double* zprev, long long n,
-                      double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
-void launch_pcg_beta(const double* r, const double* z, double* zprev, double* p, long long n,
-                     double* partial, int nblk, PcgScalars* sc, cudaStream_t st);
-void launch_pcg_beta_from_partials(const double* z, double* p, long long n, const double* partial,
-                                   int npart, int nblk, PcgScalars* sc, cudaStream_t st);
-void launch_pcg_alpha(const Level& L, const double* p, double* q, double* partial,
-                      PcgScalars* sc, cudaStream_t st);
-void launch_pcg_update(const double* p, const double* q, double* x, double* r, long long n,
-                       double* partial, int nblk, PcgScalars* sc, cudaGraphConditionalHandle h,
-                       int use_handle, cudaStream_t st);
+void launch_pcg_init(const Level& L, const double* b, const double* x, double* r,
+                     const PcgCtx& c, cudaStream_t st);
+void launch_pcg_start(const Level& L0, const double* r, const double* z, double* p, double* zprev,
+                      const PcgCtx& c, cudaStream_t st);
+void launch_pcg_beta(const Level& L0, const double* r, const double* z, double* zprev, double* p,
+                     const PcgCtx& c, cudaStream_t st);
+void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, const PcgCtx& c,
+                                   cudaStream_t st);
+void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& c,
+                      cudaStream_t st);
+void launch_pcg_update(const Level& L0, const double* p, const double* q, double* x, double* r,
+                       const PcgCtx& c, cudaGraphConditionalHandle h, int use_handle,
+                       cudaStream_t st);
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
-                          double* partial, double* out, cudaStream_t st);
-int reduce_blocks(long long n);
+                          const PcgCtx& c, double* out, cudaStream_t st);
 
 // differentiation
 void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,

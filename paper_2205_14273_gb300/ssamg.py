@@ -99,6 +99,13 @@ _SIGS = {
     "ssamg_level_copy": (_i, [_vp, _i, _i, _i, _i, _vp, _ll]),
     "ssamg_spacings": (_i, [_vp, _dp, _dp]),
     "ssamg_coupling_sums_noalloc": (_i, [_vp, _i, _vp, _vp]),
+    "ssamg_batch_create": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(Params), _vp,
+                                ctypes.POINTER(_vp)]),
+    "ssamg_batch_setup": (_i, [_vp, _vp]),
+    "ssamg_batch_num_cells": (_ll, [_vp]),
+    "ssamg_batch_offsets": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "ssamg_batch_solve": (_i, [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(Stats)]),
+    "ssamg_batch_destroy": (None, [_vp]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
 }
@@ -386,4 +393,43 @@ class Solver:
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.ssamg_solver_destroy(self.h)
+            self.h = None
+
+
+class Batch:
+    """Many independent problems solved together (the batching form): one
+    setup over all of them, and PCG with one instance per problem."""
+
+    def __init__(self, matrices: Sequence["Matrix"], params: Optional[Params] = None, stream=None,
+                 **kw):
+        self.params = params if params is not None else default_params(**kw)
+        self.matrices = list(matrices)
+        arr = (_vp * len(self.matrices))(*[m.h for m in self.matrices])
+        self.h = _vp()
+        _check(lib().ssamg_batch_create(len(self.matrices), arr, ctypes.byref(self.params),
+                                        _stream(stream), ctypes.byref(self.h)), "batch_create")
+        self.nprob = len(self.matrices)
+
+    def setup(self, stream=None):
+        _check(lib().ssamg_batch_setup(self.h, _stream(stream)), "batch_setup")
+
+    def num_cells(self) -> int:
+        return int(lib().ssamg_batch_num_cells(self.h))
+
+    def offsets(self):
+        off = (_ll * (self.nprob + 1))()
+        _check(lib().ssamg_batch_offsets(self.h, off), "batch_offsets")
+        return [int(v) for v in off]
+
+    def solve(self, b, x, nrhs: int = 1, stream=None, allow_not_converged=False):
+        """b, x: contiguous float64 CUDA tensors of nrhs x N values; returns
+        the nrhs x nprob stats (list of lists)."""
+        st = (Stats * (nrhs * self.nprob))()
+        rc = lib().ssamg_batch_solve(self.h, _dptr(b), _dptr(x), nrhs, _stream(stream), st)
+        _check(rc, "batch_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
+        return [[st[j * self.nprob + k] for k in range(self.nprob)] for j in range(nrhs)]
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ssamg_batch_destroy(self.h)
             self.h = None
