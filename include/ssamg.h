@@ -240,6 +240,10 @@ int ssamg_batch_offsets(ssamg_batch B, long long* off);
  * the first error.  Synchronises `stream` once per right-hand side. */
 int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int nrhs, void* stream,
                       ssamg_stats* st);
+/* The solver the batch runs on (owned by the batch), for the introspection
+ * and timing calls (ssamg_num_levels, ssamg_level_sizes, ssamg_time_kernel
+ * ...); NULL for NULL. */
+ssamg_solver ssamg_batch_solver(ssamg_batch B);
 void ssamg_batch_destroy(ssamg_batch B);
 
 /* Blocks whose partial sums fit the static scratch of

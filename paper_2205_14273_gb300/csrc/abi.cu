@@ -1536,6 +1536,8 @@ extern "C" int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int 
   API_END
 }
 
+extern "C" ssamg_solver ssamg_batch_solver(ssamg_batch B) { return B ? B->s : nullptr; }
+
 extern "C" void ssamg_batch_destroy(ssamg_batch B) { delete B; }
 
 // ---------------------------------------------------------------------------

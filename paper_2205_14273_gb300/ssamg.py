@@ -106,6 +106,7 @@ _SIGS = {
     "ssamg_batch_offsets": (_i, [_vp, ctypes.POINTER(_ll)]),
     "ssamg_batch_solve": (_i, [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(Stats)]),
     "ssamg_batch_destroy": (None, [_vp]),
+    "ssamg_batch_solver": (_vp, [_vp]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
 }
@@ -391,9 +392,9 @@ class Solver:
                "coupling_sums_noalloc")
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
+        if getattr(self, "h", None) and _lib is not None and getattr(self, "_owned", True):
             _lib.ssamg_solver_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Batch:
@@ -428,6 +429,17 @@ class Batch:
         rc = lib().ssamg_batch_solve(self.h, _dptr(b), _dptr(x), nrhs, _stream(stream), st)
         _check(rc, "batch_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return [[st[j * self.nprob + k] for k in range(self.nprob)] for j in range(nrhs)]
+
+    def solver(self) -> "Solver":
+        """The batch's solver (a view owned by the batch) for introspection
+        and kernel timing."""
+        sv = Solver.__new__(Solver)
+        sv.params = self.params
+        sv.h = _vp(lib().ssamg_batch_solver(self.h))
+        sv.matrix = None
+        sv._owned = False  # the batch destroys it
+        sv._owner = self
+        return sv
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
