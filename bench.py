@@ -306,7 +306,9 @@ def level_table(sv, name, stream):
     out = [f"{name}: PCG iteration {sv.time_kernel(7, 0, 20, stream):.1f} us = V-cycle "
            f"{sv.time_kernel(5, 0, 20, stream):.1f} us + FP64 operator apply "
            f"{sv.time_kernel(6, 0, 50, stream):.1f} us + vector steps "
-           f"{sv.time_kernel(8, 0, 50, stream):.1f} us (+ U x of p)"]
+           f"{sv.time_kernel(8, 0, 50, stream):.1f} us (+ U x of p)"
+           + (f"; last relaxation as the PCG runs it {sv.time_kernel(9, 0, 50, stream):.1f} us"
+              if name.startswith("fp32") else "")]
     out.append("  lvl        N     nr " + " ".join(f"{k:>11s}" for k, _ in kinds))
     for l in range(L):
         n, nr, _ = sv.level_sizes(l)
@@ -433,6 +435,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """A fixed case sized for ncu captures (inputs larger than L2, a few GB on
+    the device at most)."""
+    import torch
+
+    from paper_2205_14273_gb300 import ssamg as S
+    rng = P.SplitMix64(5)
+    a = rng.log_uniform(6, 1e-3, 1.0).reshape(2, 3)
+    prob = P.chain_aniso([200, 200], a, rng, 1)
+    grid, A = S.matrix_from_problem(prob)
+    sv = S.Solver(precision=1, flexible=1)
+    sv.setup(A)
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    z = torch.zeros_like(b)
+    for _ in range(3):
+        sv.precondition(b, z)
+    # and three iterations of the flexible PCG (the cycle's PCG-side kernels)
+    sv3 = S.Solver(precision=1, flexible=1, max_iter=3)
+    sv3.setup(A)
+    sv3.solve(b, z, allow_not_converged=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "cells": prob.n,
+                      "levels": sv.num_levels()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,10 +472,18 @@ def main():
                     help="launch the solve kernels directly (profilers cannot see kernel "
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--only", choices=["fp32_cycle", "fp64"], default=None)
+    ap.add_argument("--profile-case", choices=["level0-16M"], default=None,
+                    help="run a fixed small case for profiler captures instead of the bench: "
+                         "level0-16M = two chained 200^3 parts (16M cells, constant anisotropic "
+                         "7-point off-diagonals, per-cell diagonal), FP32 cycle, setup, "
+                         "three V-cycles and three flexible PCG iterations")
     ap.add_argument("--levels", action="store_true",
                     help="also write, to stderr, each cycle kernel's time per level "
                          "(CUDA-graph replays of that launch alone)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -281,7 +281,8 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * (with U x), 5 whole V-cycle (level ignored), 6 the PCG's FP64 level-0
  * operator apply with its dot product (level ignored), 7 one whole PCG
  * iteration, 8 the PCG's vector steps (beta, search direction, alpha, x and
- * r updates).  Ids 7 and 8 clear the solve's convergence state, so that the
+ * r updates), 9 the FP32 cycle's last post-relaxation as the PCG runs it
+ * (FP64 z out, r.z partials).  Ids 7 and 8 clear the solve's convergence state, so that the
  * replayed iterations never stop; the next solve starts afresh.  The kernels work on
  * the solver's own buffers (their contents are overwritten).  Synchronises
  * `stream`. */

@@ -1697,6 +1697,14 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
       case 7:  // one PCG iteration (V-cycle, beta, p, q = A p, alpha, x and r)
         enqueue_pcg_body(s, 0, 0, cs);
         break;
+      case 9:  // the cycle's last post-relaxation as the PCG runs it (FP64 z, dot partials)
+        if (f)
+          launch_relax_final<float>(s->lev[0], (const float*)s->lev[0].r,
+                                    (const float*)s->lev[0].b, s->z, s->r, s->prm.flexible ? s->zprev : nullptr,
+                                    s->partial, cs);
+        else
+          throw SsamgError{SSAMG_ERR_ARG, "kernel 9 times the FP32 cycle's last relaxation"};
+        break;
       case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
         launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), cs);
         launch_pcg_update(s->lev[0], s->p, s->q, s->x, s->r, pcg_ctx(s), 0, 0, cs);

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
                                                        const T* __restrict__ b,
                                                        double* __restrict__ z,
                                                        const double* __restrict__ rpcg,
-                                                       double* __restrict__ zprev, int flex,
+                                                       double* zprev, int flex,
                                                        double* __restrict__ partial) {
   pdl_trigger();
   __shared__ DPart sp;
@@ -119,12 +119,16 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
   double s0 = 0.0, s1 = 0.0;
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
+    // the FP64 operands are fetched with the stencil's, not after it (zprev
+    // is a valid buffer even without flexible CG: z itself, read before its
+    // store and then unused; hence zprev is not declared __restrict__)
+    const double rv = rpcg[g];
+    const double zo = zprev[g];
     const double zv = (double)fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
     z[g] = zv;
-    const double rv = rpcg[g];
     s0 = fma(rv, zv, s0);
     if (flex) {
-      s1 = fma(rv, zprev[g], s1);
+      s1 = fma(rv, zo, s1);
       zprev[g] = zv;
     }
   }
