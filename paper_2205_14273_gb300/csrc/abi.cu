@@ -107,10 +107,18 @@ struct ssamg_matrix_s {
 struct GraphSet {
   cudaGraphExec_t pcg = nullptr;
   cudaGraphExec_t vcycle = nullptr;
+  cudaGraphExec_t rounds = nullptr;  // several right-hand sides in one graph
+  const double* rounds_b = nullptr;   // the user vectors baked into `rounds`
+  double* rounds_x = nullptr;
+  int rounds_n = 0;
   void reset() {
     if (pcg) cudaGraphExecDestroy(pcg);
     if (vcycle) cudaGraphExecDestroy(vcycle);
-    pcg = vcycle = nullptr;
+    if (rounds) cudaGraphExecDestroy(rounds);
+    pcg = vcycle = rounds = nullptr;
+    rounds_b = nullptr;
+    rounds_x = nullptr;
+    rounds_n = 0;
   }
 };
 
@@ -145,12 +153,18 @@ struct ssamg_solver_s {
   std::vector<long long> prob_cells;  // nprob + 1 first cells of each problem
   int* pb = nullptr;           // nprob + 1 level-0 block starts of each problem (device)
   PcgCtl* ctl = nullptr;
+  PcgScalars* sc_init = nullptr;  // nprob starting scalars (tolerance, caps)
+  PcgScalars* sc_hist = nullptr;  // per right-hand side copies of sc (multi-round solves)
+  double* tres_hist = nullptr;    // and of the true residual sums
+  int hist_cap = 0;               // right-hand sides the history holds
   int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
   ~ssamg_solver_s() {
     graphs.reset();
+    if (sc_hist) cudaFree(sc_hist);
+    if (tres_hist) cudaFree(tres_hist);
     if (cs) cudaStreamDestroy(cs);
     if (h_sc) cudaFreeHost(h_sc);
     if (h_int) cudaFreeHost(h_int);
@@ -1050,6 +1064,19 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->ctl = aalloc<PcgCtl>(s->arena, 1);
   SSAMG_CUDA(cudaMemsetAsync(s->ctl, 0, sizeof(PcgCtl), st));
   {
+    std::vector<PcgScalars> init(s->nprob);
+    for (auto& v : init) {
+      std::memset(&v, 0, sizeof(v));
+      v.tol = s->prm.tol;
+      v.max_iter = s->prm.max_iter;
+      v.flexible = s->prm.flexible;
+    }
+    s->sc_init = aalloc<PcgScalars>(s->arena, s->nprob);
+    SSAMG_CUDA(cudaMemcpyAsync(s->sc_init, init.data(), sizeof(PcgScalars) * s->nprob,
+                               cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));  // init is a host temporary
+  }
+  {
     // level-0 block and cell ranges of each problem (parts are problem-ordered)
     std::vector<int> hpb(s->nprob + 1, L0.nblk);
     s->prob_cells.assign(s->nprob + 1, N);
@@ -1223,19 +1250,155 @@ void build_pcg_graph(ssamg_solver s) {
   cudaGraphDestroy(g);
 }
 
+// Per-problem statistics from host copies of the PCG scalars and of the
+// (||b||^2, ||b - A x||^2) pairs.
+void fill_stats(ssamg_solver s, ssamg_stats* stats, const PcgScalars* sc, const double* tres) {
+  const int np = s->nprob;
+  int maxit = 0;
+  for (int k = 0; k < np; ++k) maxit = std::max(maxit, sc[k].iter);
+  double nnz0 = 0, nnz = 0;
+  for (size_t l = 0; l < s->lev.size(); ++l) {
+    double n = (double)s->lev[l].nnz;
+    for (auto& h : s->lev[l].parts) n += (double)h.nent * h.ncell;
+    nnz += n;
+    if (l == 0) nnz0 = n;
+  }
+  for (int k = 0; k < np; ++k) {
+    const PcgScalars& r = sc[k];
+    ssamg_stats& o = stats[k];
+    o.iterations = r.iter;
+    o.setup_kernel_launches = s->setup_launches;
+    // the loop runs until the slowest problem stops
+    o.solve_kernel_launches = s->head_launches + (long long)(maxit > 0 ? maxit - 1 : 0) * s->body_launches;
+    o.converged = r.status == 0 && r.rr <= r.tol2bb;
+    o.rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
+    o.num_levels = (int)s->lev.size();
+    o.coarse_size = s->lev.back().N;
+    o.operator_complexity = nnz / nnz0;
+    o.true_rel_res = tres[2 * k] > 0 ? std::sqrt(tres[2 * k + 1] / tres[2 * k]) : 0.0;
+  }
+}
+
+int worst_status(ssamg_solver s, const PcgScalars* sc) {
+  int rc = SSAMG_OK;
+  for (int k = 0; k < s->nprob; ++k) {
+    if (sc[k].status != 0) return sc[k].status;
+    if (!(sc[k].rr <= sc[k].tol2bb)) rc = SSAMG_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+// One graph for `nrhs` solves in a row (right-hand side j at b + j N, its
+// solution to x + j N): per round, the right-hand side is copied in, x and
+// the scalars reset, the PCG head and its while loop run, and the solution,
+// the scalars and the true-residual sums are copied out to the history.
+void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
+  if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+  const long long N = s->lev[0].N;
+  const int np = s->nprob;
+  cudaGraph_t g;
+  SSAMG_CUDA(cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphNode_t> deps;
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* dp = nullptr;
+  size_t ndp = 0;
+  cudaGraph_t tmp;
+  auto begin = [&](cudaGraph_t gg, const std::vector<cudaGraphNode_t>& d) {
+    SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, gg, d.empty() ? nullptr : d.data(), nullptr,
+                                             d.size(), cudaStreamCaptureModeThreadLocal));
+  };
+  auto end = [&]() {
+    SSAMG_CUDA(cudaStreamGetCaptureInfo(s->cs, &cst, nullptr, nullptr, &dp, nullptr, &ndp));
+    std::vector<cudaGraphNode_t> t(dp, dp + ndp);
+    SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+    return t;
+  };
+  for (int j = 0; j < nrhs; ++j) {
+    cudaGraphConditionalHandle h;
+    SSAMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    begin(g, deps);
+    SSAMG_CUDA(cudaMemcpyAsync(s->b, b + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->cs));
+    SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+    SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->sc_init, sizeof(PcgScalars) * np, cudaMemcpyDeviceToDevice,
+                               s->cs));
+    long long c0 = g_ssamg_launches;
+    enqueue_pcg_head(s, h, 1, s->cs);
+    s->head_launches = g_ssamg_launches - c0;
+    std::vector<cudaGraphNode_t> tail = end();
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    SSAMG_CUDA(cudaGraphAddNode(&cnode, g, tail.data(), nullptr, tail.size(), &cp));
+    begin(cp.conditional.phGraph_out[0], {});
+    c0 = g_ssamg_launches;
+    enqueue_pcg_body(s, h, 1, s->cs);
+    s->body_launches = g_ssamg_launches - c0;
+    end();
+    begin(g, {cnode});
+    SSAMG_CUDA(cudaMemcpyAsync(x + j * N, s->x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->cs));
+    launch_true_residual(s->lev[0], s->b, s->x, s->q, pcg_ctx(s), s->tres_hist + 2ll * j * np,
+                         s->cs);
+    SSAMG_CUDA(cudaMemcpyAsync(s->sc_hist + (long long)j * np, s->sc, sizeof(PcgScalars) * np,
+                               cudaMemcpyDeviceToDevice, s->cs));
+    deps = end();
+  }
+  if (s->graphs.rounds) cudaGraphExecDestroy(s->graphs.rounds);
+  s->graphs.rounds = nullptr;
+  SSAMG_CUDA(cudaGraphInstantiate(&s->graphs.rounds, g, 0));
+  cudaGraphDestroy(g);
+  s->graphs.rounds_b = b;
+  s->graphs.rounds_x = x;
+  s->graphs.rounds_n = nrhs;
+}
+
+// Solves for nrhs right-hand sides (b, x: nrhs x N, device) in one graph
+// launch; stats (nrhs x nprob) as for run_pcg.  One synchronisation.
+int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_t st,
+               ssamg_stats* stats) {
+  const int np = s->nprob;
+  if (s->hist_cap < nrhs) {
+    if (s->sc_hist) cudaFree(s->sc_hist);
+    if (s->tres_hist) cudaFree(s->tres_hist);
+    s->sc_hist = nullptr;
+    s->tres_hist = nullptr;
+    s->hist_cap = 0;
+    SSAMG_CUDA(cudaMalloc(&s->sc_hist, sizeof(PcgScalars) * np * nrhs));
+    SSAMG_CUDA(cudaMalloc(&s->tres_hist, sizeof(double) * 2 * np * nrhs));
+    s->hist_cap = nrhs;
+    if (s->graphs.rounds) cudaGraphExecDestroy(s->graphs.rounds);
+    s->graphs.rounds = nullptr;
+  }
+  if (!s->graphs.rounds || s->graphs.rounds_b != b || s->graphs.rounds_x != x ||
+      s->graphs.rounds_n != nrhs)
+    build_rounds_graph(s, b, x, nrhs);
+  SSAMG_CUDA(cudaGraphLaunch(s->graphs.rounds, st));
+  std::vector<PcgScalars> sc((size_t)np * nrhs);
+  std::vector<double> tres((size_t)2 * np * nrhs);
+  SSAMG_CUDA(cudaMemcpyAsync(sc.data(), s->sc_hist, sizeof(PcgScalars) * np * nrhs,
+                             cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaMemcpyAsync(tres.data(), s->tres_hist, sizeof(double) * 2 * np * nrhs,
+                             cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  int rc = SSAMG_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    if (stats) fill_stats(s, stats + (long long)j * np, sc.data() + (long long)j * np,
+                          tres.data() + 2ll * j * np);
+    const int r = worst_status(s, sc.data() + (long long)j * np);
+    if (r < 0) return r;
+    if (r > rc) rc = r;
+  }
+  return rc;
+}
+
+
 // Runs the PCG of every problem of the solver on s->b, s->x (x0 given);
 // stats, when set, receives one entry per problem.  Returns the worst status.
 int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
   const int np = s->nprob;
-  std::vector<PcgScalars> init(np);
-  for (auto& v : init) {
-    std::memset(&v, 0, sizeof(v));
-    v.tol = s->prm.tol;
-    v.max_iter = s->prm.max_iter;
-    v.flexible = s->prm.flexible;
-  }
-  SSAMG_CUDA(cudaMemcpyAsync(s->sc, init.data(), sizeof(PcgScalars) * np, cudaMemcpyHostToDevice, st));
-  SSAMG_CUDA(cudaStreamSynchronize(st));  // init is a host temporary
+  SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->sc_init, sizeof(PcgScalars) * np, cudaMemcpyDeviceToDevice, st));
   if (s->prm.use_graph) {
     if (!s->graphs.pcg) build_pcg_graph(s);
     SSAMG_CUDA(cudaGraphLaunch(s->graphs.pcg, st));
@@ -1262,41 +1425,13 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
       throw SsamgError{SSAMG_ERR_TIMEOUT, "a grid barrier of the coarse-level kernel timed out"};
     }
   }
-  int maxit = 0;
-  for (int k = 0; k < np; ++k) maxit = std::max(maxit, s->h_sc[k].iter);
   if (stats) {
-    double nnz0 = 0, nnz = 0;
-    for (size_t l = 0; l < s->lev.size(); ++l) {
-      double n = (double)s->lev[l].nnz;
-      for (auto& h : s->lev[l].parts) n += (double)h.nent * h.ncell;
-      nnz += n;
-      if (l == 0) nnz0 = n;
-    }
     launch_true_residual(s->lev[0], s->b, s->x, s->q, pcg_ctx(s), s->tres, st);
     SSAMG_CUDA(cudaMemcpyAsync(s->h_dbl, s->tres, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));
-    for (int k = 0; k < np; ++k) {
-      const PcgScalars& r = s->h_sc[k];
-      ssamg_stats& o = stats[k];
-      o.iterations = r.iter;
-      o.setup_kernel_launches = s->setup_launches;
-      // the loop runs until the slowest problem stops
-      o.solve_kernel_launches = s->head_launches + (long long)(maxit > 0 ? maxit - 1 : 0) * s->body_launches;
-      o.converged = r.status == 0 && r.rr <= r.tol2bb;
-      o.rel_res = r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0;
-      o.num_levels = (int)s->lev.size();
-      o.coarse_size = s->lev.back().N;
-      o.operator_complexity = nnz / nnz0;
-      o.true_rel_res = s->h_dbl[2 * k] > 0 ? std::sqrt(s->h_dbl[2 * k + 1] / s->h_dbl[2 * k]) : 0.0;
-    }
+    fill_stats(s, stats, s->h_sc, s->h_dbl);
   }
-  int rc = SSAMG_OK;
-  for (int k = 0; k < np; ++k) {
-    const PcgScalars& r = s->h_sc[k];
-    if (r.status != 0) return r.status;
-    if (!(r.rr <= r.tol2bb)) rc = SSAMG_NOT_CONVERGED;
-  }
-  return rc;
+  return worst_status(s, s->h_sc);
 }
 
 }  // namespace
@@ -1522,6 +1657,7 @@ extern "C" int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int 
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
   PdlScope pdl(s->prm.use_pdl);
+  if (s->prm.use_graph) return run_rounds(s, b, x, nrhs, cst, st);
   const long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int j = 0; j < nrhs; ++j) {

@@ -110,3 +110,27 @@ def test_batch_rejects_mixed_stencils(S):
     _, A2 = S.matrix_from_problem(c)
     with pytest.raises(S.SsamgError):
         S.Batch([A1, A2])
+
+
+def test_batch_one_graph_matches_host_loop(S):
+    """All right-hand sides in one graph launch (cached per vector pair, and
+    rebuilt for new vectors) give the host-driven rounds' results bitwise."""
+    probs = P.batched(nprob=5, nrhs=3, seed=13, pmax=3, emin=4, emax=11)
+    res = []
+    for graph in (1, 0):
+        _, B = make_batch(S, probs, precision=1, flexible=1, use_graph=graph)
+        off = B.offsets()
+        b = torch.as_tensor(stack_rhs(probs, off, 3), device="cuda").contiguous()
+        x = torch.zeros_like(b)
+        st = B.solve(b, x, 3)
+        x2 = torch.zeros_like(b)
+        st2 = B.solve(b, x2, 3)         # new output vector: the graph is rebuilt
+        x.zero_()
+        st3 = B.solve(b, x, 3)          # same vectors again: the cached graph
+        assert torch.equal(x, x2)
+        its = [[s.iterations for s in row] for row in st]
+        assert its == [[s.iterations for s in row] for row in st2]
+        assert its == [[s.iterations for s in row] for row in st3]
+        res.append((its, x.cpu().numpy()))
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
