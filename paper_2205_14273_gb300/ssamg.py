@@ -312,10 +312,12 @@ class Solver:
         _check(rc, "solve_host", (OK, NOT_CONVERGED))
         return st
 
-    def adjoint_solve(self, g, lam, nrhs: int = 1, stream=None) -> Stats:
+    def adjoint_solve(self, g, lam, nrhs: int = 1, stream=None,
+                      allow_not_converged=False) -> Stats:
         st = Stats()
-        _check(lib().ssamg_adjoint_solve(self.h, _dptr(g), _dptr(lam), nrhs, _stream(stream),
-                                         ctypes.byref(st)), "adjoint_solve")
+        rc = lib().ssamg_adjoint_solve(self.h, _dptr(g), _dptr(lam), nrhs, _stream(stream),
+                                       ctypes.byref(st))
+        _check(rc, "adjoint_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return st
 
     def coef_gradient(self, lam, x, dcoef, stream=None):
