@@ -201,6 +201,13 @@ def run_ours(args):
     # ---- dominant-kernel roofline (prolongation with U x, FP32 cycle)
     roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
 
+    # ---- per-kernel HBM fractions on the large levels, and the other two
+    # full-size workloads
+    peak = read_peaks().get("hbm_gbs", 6800.0)
+    hbm = hbm_by_level(solvers.get("fp32_cycle", next(iter(solvers.values()))),
+                       "8 parts x 64^3", stream, peak)
+    extra = None if args.no_extra_workloads else extra_workloads(S, stream, peak)
+
     # ---- end to end through the C ABI with host buffers (matrix upload,
     # setup, solve, result read-back)
     e2e = None if args.no_e2e else end_to_end(S, prob, dev, stream, args)
@@ -232,7 +239,10 @@ def run_ours(args):
         "roofline": roof,
         "e2e": e2e,
         "clocks": head["clocks"],
+        "hbm_by_level": hbm,
     }
+    if extra is not None:
+        line["other_workloads"] = extra
     line["gpu_launches"] = head["launches"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob)
@@ -320,6 +330,105 @@ def level_table(sv, name, stream):
                 row.append(f"{sv.time_kernel(kid, l, 100, stream):.2f}")
         out.append(f"  {l:3d} {n:8d} {nr:6d} " + " ".join(f"{v:>11s}" for v in row))
     print("\n".join(out), file=sys.stderr)
+
+
+def hbm_by_level(sv, workload, stream, peak, min_cells=1 << 20):
+    """Per-kernel HBM throughput of the FP32 cycle on the levels of at least
+    2^20 cells: algorithmic bytes (each input and output once; w = 4) / the
+    kernel's CUDA-graph launch time, against the measured copy bandwidth."""
+    w = 4
+    L = sv.num_levels()
+    sizes = [sv.level_sizes(l) for l in range(L)]
+    rows = []
+    for l in range(L - 1):
+        N, nr, nnz = sizes[l]
+        if N < min_cells:
+            continue
+        Nc = sizes[l + 1][0]
+        sc = sv.stored_coefficients(l)
+        nbytes = {
+            "relax0_u": (2, 3 * w * N + 12 * nr + 12 * nnz),
+            "residual": (0, w * (sc + 3 * N)),
+            "restrict": (3, w * N + w * Nc + 2 * w * (N - Nc)),
+            "prolong_u": (4, 2 * w * N + w * Nc + 2 * w * (N - Nc) + 12 * nr + 36 * nnz),
+            "relax": (1, w * (sc + 4 * N)),
+        }
+        row = {"level": l, "cells": N, "stored_coefficients": sc}
+        for k, (kid, nb) in nbytes.items():
+            us = sv.time_kernel(kid, l, 50, stream)
+            gbs = nb / (us * 1e-6) / 1e9
+            row[k] = {"us": round(us, 2), "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        rows.append(row)
+    return {"workload": workload, "peak_gbs": peak, "levels": rows}
+
+
+def extra_workloads(S, stream, peak):
+    """The 256^3 27-point workload and the 64-problem batched workload at full
+    size: setup and solve times (one step after a warm-up) in both cycle
+    precisions, and the per-kernel HBM fractions of their large levels."""
+    import torch
+    out = {}
+    prob = P.config(2)
+    grid, A = S.matrix_from_problem(prob)
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    res = {"workload": "1 part 256^3, 27-point variable coefficients, seed 2",
+           "unknowns": prob.n}
+    for prec, name in ((1, "fp32_cycle"), (0, "fp64")):
+        sv = S.Solver(precision=prec, flexible=prec, tol=1e-8, max_iter=500)
+        sv.setup(A)
+        x = torch.zeros_like(b)
+        st = sv.solve(b, x)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        sv.setup(A)
+        e[1].record(stream)
+        sv.solve_nostats(b, x)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        t_s, t_v = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        res[name] = {"setup_ms": round(t_s, 3), "solve_ms": round(t_v, 3),
+                     "iterations": st.iterations, "true_rel_res": fmt(st.true_rel_res),
+                     "levels": st.num_levels,
+                     "mdof_s": round(prob.n / ((t_s + t_v) * 1e-3) / 1e6, 3)}
+        if prec == 1:
+            res["hbm"] = hbm_by_level(sv, res["workload"], stream, peak)
+    out["var27_256"] = res
+    del A, grid
+    probs = P.config(3)
+    mats = [S.matrix_from_problem(p) for p in probs]
+    nrhs = probs[0].b.shape[0]
+    res = {"workload": f"{len(probs)} problems, 1-8 chained parts each, edges 16-96, "
+                       f"{nrhs} right-hand sides, seed 3"}
+    for prec, name in ((1, "fp32_cycle"), (0, "fp64")):
+        B = S.Batch([A for _, A in mats], precision=prec, flexible=prec, tol=1e-8, max_iter=500)
+        off = B.offsets()
+        bh = np.zeros((nrhs, off[-1]))
+        for k, p in enumerate(probs):
+            bh[:, off[k]:off[k + 1]] = p.b
+        bb = torch.as_tensor(bh, device="cuda")
+        xx = torch.zeros_like(bb)
+        B.setup()
+        st = B.solve(bb, xx, nrhs)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        B.setup()
+        e[1].record(stream)
+        st = B.solve(bb, xx, nrhs)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        t_s, t_v = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        its = [s.iterations for row in st for s in row]
+        res["unknowns"] = off[-1]
+        res[name] = {"setup_ms": round(t_s, 3), "solve_ms": round(t_v, 3),
+                     "iterations_max": max(its), "iterations_mean": round(float(np.mean(its)), 2),
+                     "worst_true_rel_res": fmt(max(s.true_rel_res for row in st for s in row)),
+                     "levels": st[0][0].num_levels,
+                     "mdof_s": round(off[-1] * nrhs / ((t_s + t_v) * 1e-3) / 1e6, 3)}
+        if prec == 1:
+            res["hbm"] = hbm_by_level(B.solver(), res["workload"], stream, peak)
+        del B
+    out["batched_64"] = res
+    return out
 
 
 def read_peaks():
@@ -477,6 +586,8 @@ def main():
                          "level0-16M = two chained 200^3 parts (16M cells, constant anisotropic "
                          "7-point off-diagonals, per-cell diagonal), FP32 cycle, setup, "
                          "three V-cycles and three flexible PCG iterations")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the 256^3 27-point and 64-problem batched measurements")
     ap.add_argument("--levels", action="store_true",
                     help="also write, to stderr, each cycle kernel's time per level "
                          "(CUDA-graph replays of that launch alone)")

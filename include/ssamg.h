@@ -201,6 +201,9 @@ int ssamg_level_sizes(ssamg_solver s, int level, long long* ncells, long long* u
  * elements the destination holds; it must equal the data size. */
 int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, void* dst,
                      long long n);
+/* Number of stored per-cell stencil coefficients of a level (constant
+ * entries excluded), for algorithmic-byte counts. */
+int ssamg_level_stored_coefficients(ssamg_solver s, int level, long long* ncoef);
 /* Per-part coupling sums c (n_parts x 3) and spacings W (n_parts x 3) of
  * Section 3.1 (W = +inf encoded as HUGE_VAL). */
 int ssamg_spacings(ssamg_solver s, double* c, double* W);

@@ -1762,6 +1762,14 @@ extern "C" int ssamg_level_copy(ssamg_solver s, int level, int what, int part, i
   API_END
 }
 
+extern "C" int ssamg_level_stored_coefficients(ssamg_solver s, int level, long long* ncoef) {
+  if (!s || !ncoef) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  *ncoef = s->lev[level].ncoef;
+  return SSAMG_OK;
+}
+
 extern "C" int ssamg_spacings(ssamg_solver s, double* c, double* W) {
   if (!s || !s->ready) return SSAMG_ERR_STATE;
   if (c) std::copy(s->c.begin(), s->c.end(), c);

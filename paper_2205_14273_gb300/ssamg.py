@@ -107,6 +107,7 @@ _SIGS = {
     "ssamg_batch_solve": (_i, [_vp, _vp, _vp, _i, _vp, ctypes.POINTER(Stats)]),
     "ssamg_batch_destroy": (None, [_vp]),
     "ssamg_batch_solver": (_vp, [_vp]),
+    "ssamg_level_stored_coefficients": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
 }
@@ -365,6 +366,12 @@ class Solver:
         return {"lo": tuple(lo), "hi": tuple(hi), "dstar": ds.value, "omega": om.value,
                 "offsets": [tuple(offs[3 * e:3 * e + 3]) for e in range(n)],
                 "cell_offset": off.value}
+
+    def stored_coefficients(self, level: int) -> int:
+        v = _ll()
+        _check(lib().ssamg_level_stored_coefficients(self.h, level, ctypes.byref(v)),
+               "level_stored_coefficients")
+        return int(v.value)
 
     def level_copy(self, level: int, what: int, part: int = 0, entry: int = 0, n: int = 0,
                    dtype=np.float64) -> np.ndarray:
