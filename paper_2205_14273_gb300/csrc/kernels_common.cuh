@@ -12,6 +12,14 @@
   _Pragma("unroll 1") for (int c##_m = 0,                                                  \
        c = ((int)blockIdx.x - (P).blk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;        \
        c##_m < (P).cpt && c < (P).ncell; ++c##_m, c += SSAMG_BLOCK)
+// The same tiles with the SSAMG_CPT_LARGE steps unrolled and predicated, so
+// that a thread issues the loads of all its cells before it consumes the
+// first; for kernels light enough in registers (restriction, prolongation).
+#define TILE_LOOP_UNROLLED(c, P)                                                           \
+  _Pragma("unroll") for (int c##_m = 0; c##_m < SSAMG_CPT_LARGE; ++c##_m)                  \
+    if (const int c = ((int)blockIdx.x - (P).blk0) * (P).cpt * SSAMG_BLOCK +               \
+                      (int)threadIdx.x + c##_m * SSAMG_BLOCK;                              \
+        c##_m < (P).cpt && c < (P).ncell)
 #define TILE_LOOP_FINE(c, P)                                                               \
   _Pragma("unroll 1") for (int c##_m = 0,                                                  \
        c = ((int)blockIdx.x - (P).fblk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;       \
@@ -418,9 +426,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // Fine-point index (within the part's P arrays) of local fine cell (i, j, k).
 __device__ __forceinline__ int fine_point_index(const DPart& p, int i, int j, int k) {
-  int c[3] = {i, j, k};
-  c[p.dstar] = (c[p.dstar] + p.par) >> 1;
-  return (c[2] * p.nf[1] + c[1]) * p.nf[0] + c[0];
+  // selects rather than an array indexed by d* (which would live in local memory)
+  const int d = p.dstar;
+  if (d == 0)
+    i = (i + p.par) >> 1;
+  else if (d == 1)
+    j = (j + p.par) >> 1;
+  else
+    k = (k + p.par) >> 1;
+  return (k * p.nf[1] + j) * p.nf[0] + i;
 }
 
 // Linear index on the next level of local coarse cell (i, j, k).
@@ -428,37 +442,60 @@ __device__ __forceinline__ int coarse_index(const DPart& p, int i, int j, int k)
   return p.coff + (k * p.cn[1] + j) * p.cn[0] + i;
 }
 
-// Columns of P's row for local fine cell (i, j, k) of part p (Section 3.2):
-// a coarse point maps to itself with weight 1; a fine point to its west and
-// east coarse neighbours along d* (when inside the box) with PW, PE.
+// P's row for local fine cell (i, j, k) of part p (Section 3.2): a coarse
+// point maps to itself with weight 1; a fine point to its west and east
+// coarse neighbours along d* (when inside the box) with PW, PE.  Columns are
+// coarse-level indices, -1 where absent; j0 is the west (or only) one.
 template <class T>
-__device__ __forceinline__ int p_row(const DPart& p, const T* __restrict__ Pw,
-                                     const T* __restrict__ Pe, int i, int j, int k, int* J, T* w) {
-  if (p.dstar < 0) {
-    J[0] = coarse_index(p, i, j, k);
-    w[0] = (T)1;
-    return 1;
-  }
-  int c[3] = {i, j, k};
+struct PRow {
+  int j0, j1;
+  T w0, w1;
+};
+
+template <class T>
+__device__ __forceinline__ PRow<T> p_row(const DPart& p, const T* __restrict__ Pw,
+                                         const T* __restrict__ Pe, int i, int j, int k) {
+  PRow<T> r{-1, -1, (T)0, (T)0};
   const int d = p.dstar;
-  const int cd = c[d];
-  if (((cd + p.par) & 1) == 0) {
-    c[d] = (cd - p.par) >> 1;
-    J[0] = coarse_index(p, c[0], c[1], c[2]);
-    w[0] = (T)1;
-    return 1;
+  if (d < 0) {
+    r.j0 = coarse_index(p, i, j, k);
+    r.w0 = (T)1;
+    return r;
   }
-  int F = p.poff + fine_point_index(p, i, j, k);
-  int m = 0;
+  // coarse index of (i, j, k) with its d* component replaced by v (selects,
+  // not an array indexed by d*)
+  auto at = [&](int v) {
+    return coarse_index(p, d == 0 ? v : i, d == 1 ? v : j, d == 2 ? v : k);
+  };
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (((cd + p.par) & 1) == 0) {
+    r.j0 = at((cd - p.par) >> 1);
+    r.w0 = (T)1;
+    return r;
+  }
+  const int F = p.poff + fine_point_index(p, i, j, k);
   if (cd - 1 >= 0) {
-    c[d] = (cd - 1 - p.par) >> 1;
-    J[m] = coarse_index(p, c[0], c[1], c[2]);
-    w[m++] = Pw[F];
+    r.j0 = at((cd - 1 - p.par) >> 1);
+    r.w0 = Pw[F];
   }
   if (cd + 1 < p.n[d]) {
-    c[d] = (cd + 1 - p.par) >> 1;
-    J[m] = coarse_index(p, c[0], c[1], c[2]);
-    w[m++] = Pe[F];
+    r.j1 = at((cd + 1 - p.par) >> 1);
+    r.w1 = Pe[F];
   }
-  return m;
+  if (r.j0 < 0) {  // only the east neighbour: keep it first
+    r.j0 = r.j1;
+    r.w0 = r.w1;
+    r.j1 = -1;
+    r.w1 = (T)0;
+  }
+  return r;
+}
+
+// x + P e at one fine cell: the row's terms added west first, as the
+// oracle's P^T / P pair orders them.
+template <class T>
+__device__ __forceinline__ T add_p_row(T v, const PRow<T>& r, const T* __restrict__ ec) {
+  if (r.j0 >= 0) v = fma(r.w0, ec[r.j0], v);
+  if (r.j1 >= 0) v = fma(r.w1, ec[r.j1], v);
+  return v;
 }

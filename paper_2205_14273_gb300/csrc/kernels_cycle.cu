@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   part_of(F.parts, p, fp);
   __syncthreads();
   pdl_wait();
-  TILE_LOOP(cc, cp) {
+  TILE_LOOP_UNROLLED(cc, cp) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
     const int d = fp.dstar;
@@ -214,24 +214,21 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
   __syncthreads();
   // the first tile cell's P row (setup data) is fetched before the wait
   const int cfirst = ((int)blockIdx.x - fp.blk0) * fp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
-  int J[2];
-  T w[2];
-  int m = 0;
+  PRow<T> pr0{-1, -1, (T)0, (T)0};
   if (cfirst < fp.ncell) {
     int i, j, k;
     cell_coords(fp, cfirst, i, j, k);
-    m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+    pr0 = p_row(fp, F.Pw, F.Pe, i, j, k);
   }
   pdl_wait();
-  TILE_LOOP(c, fp) {
+  TILE_LOOP_UNROLLED(c, fp) {
+    PRow<T> pr = pr0;
     if (c != cfirst) {
       int i, j, k;
       cell_coords(fp, c, i, j, k);
-      m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
+      pr = p_row(fp, F.Pw, F.Pe, i, j, k);
     }
-    T v = xin[fp.off + c];
-    for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
-    xout[fp.off + c] = v;
+    xout[fp.off + c] = add_p_row(xin[fp.off + c], pr, ec);
   }
   (void)p;
 }
@@ -248,12 +245,7 @@ __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restr
   TILE_LOOP(c, fp) {
     int i, j, k;
     cell_coords(fp, c, i, j, k);
-    int J[2];
-    T w[2];
-    int m = p_row(fp, F.Pw, F.Pe, i, j, k, J, w);
-    T v = x[fp.off + c];
-    for (int t = 0; t < m; ++t) v = fma(w[t], ec[J[t]], v);
-    x[fp.off + c] = v;
+    x[fp.off + c] = add_p_row(x[fp.off + c], p_row(fp, F.Pw, F.Pe, i, j, k), ec);
   }
 }
 
@@ -478,12 +470,7 @@ __global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
       const DPart& fp = FL.parts[tail_part(FL.cellstart, FL.np, g)];
       int c = g - fp.off, i, j, k;
       cell_coords(fp, c, i, j, k);
-      int J[2];
-      T w[2];
-      int m = p_row(fp, FL.Pw, FL.Pe, i, j, k, J, w);
-      T v = Fx[g];
-      for (int t = 0; t < m; ++t) v = fma(w[t], e[J[t]], v);
-      Fr[g] = v;
+      Fr[g] = add_p_row(Fx[g], p_row(fp, FL.Pw, FL.Pe, i, j, k), e);
     }
     for (int base = 0; base < FL.nr; base += nth / SSAMG_TPR)
       u_row_sum<false>(

@@ -9,6 +9,20 @@ namespace {
 
 constexpr int NT = SSAMG_BLOCK;
 
+// P's row as column and weight arrays J[0..m), w[0..m) (the first the west or
+// only column); returns m.  Unused slots hold -1 and 0.
+template <class T>
+__device__ __forceinline__ int p_row_arrays(const DPart& p, const T* __restrict__ Pw,
+                                            const T* __restrict__ Pe, int i, int j, int k, int* J,
+                                            T* w) {
+  const PRow<T> r = p_row(p, Pw, Pe, i, j, k);
+  J[0] = r.j0;
+  w[0] = r.w0;
+  J[1] = r.j1;
+  w[1] = r.w1;
+  return (r.j0 >= 0) + (r.j1 >= 0);
+}
+
 // ---------------------------------------------------------------------------
 // K1: per part, c_d = sum over cells of sign(A_C) * (-sum of entries moving
 // along d) (Section 3.1).  Block partials, then one block per part sums them
@@ -217,7 +231,7 @@ __global__ void k_umark(LevelView<double> F, int nr, const int* __restrict__ row
   locate(F, F.parts, rows[r], p, i, j, k);
   int J[2];
   double w[2];
-  int m = p_row(F.parts[p], F.Pw, F.Pe, i, j, k, J, w);
+  int m = p_row_arrays(F.parts[p], F.Pw, F.Pe, i, j, k, J, w);
   for (int t = 0; t < m; ++t) marker[J[t]] = 1;
 }
 
@@ -315,7 +329,7 @@ __global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, Level
       if (q < q1) {
         int gq, gi, gj, gk;
         locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
-        m = p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, Jt, w2);
+        m = p_row_arrays(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, Jt, w2);
       }
       int tot;
       int pos = n + warp_excl_scan(m, lane, tot);
@@ -388,7 +402,7 @@ __global__ void k_upcols(LevelView<double> F, long long nnz, int* __restrict__ p
   locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
   int J[2] = {-1, -1};
   double w[2] = {0.0, 0.0};
-  p_row(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, J, w);
+  p_row_arrays(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, J, w);
   for (int t = 0; t < 2; ++t) {
     pj[2 * q + t] = J[t];
     pw[2 * q + t] = w[t];
