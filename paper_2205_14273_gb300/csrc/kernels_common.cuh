@@ -25,7 +25,10 @@
        c = ((int)blockIdx.x - (P).fblk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;       \
        c##_m < (P).cpt && c < (P).nfine; ++c##_m, c += SSAMG_BLOCK)
 
-// Programmatic dependent launch.  The solve's kernels are launched with
+// Programmatic dependent launch.  (Pointer parameters of these kernels are
+// not __restrict__: a const __restrict__ kernel parameter may be read with
+// invariant loads, which the compiler may move above griddepcontrol.wait,
+// before the predecessor has written the data.)  The solve's kernels are launched with
 // programmatic stream serialisation: a kernel may be scheduled while its
 // predecessor in the stream is still running, stages what setup wrote (block
 // tables, part descriptors; host copies only), and then waits in pdl_wait()

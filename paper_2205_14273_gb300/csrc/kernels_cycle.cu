@@ -13,8 +13,8 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // x = omega M^-1 b (relaxation from a zero guess).
 template <class T>
-__global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict__ b,
-                         T* __restrict__ x) {
+__global__ void k_relax0(int N, const T* dinv, const T* b,
+                         T* x) {
   pdl_trigger();
   pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,14 +24,19 @@ __global__ void k_relax0(int N, const T* __restrict__ dinv, const T* __restrict_
 // x = omega M^-1 b on blocks [0, nb); row jobs uy = U x on the rest.  The
 // diagonal (setup data) is fetched before the wait for the predecessor.
 template <class T>
-__global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T* __restrict__ b,
-                                                 T* __restrict__ x) {
+__global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T* b,
+                                                 T* x) {
   pdl_trigger();
   if ((int)blockIdx.x < nb) {
-    const int g = blockIdx.x * NT + threadIdx.x;
-    const T d = g < L.N ? L.dinv[g] : (T)0;
+    // SSAMG_EW cells per thread, strided by the block: all loads in flight
+    const int g0 = blockIdx.x * (NT * SSAMG_EW) + threadIdx.x;
+    T d[SSAMG_EW];
+#pragma unroll
+    for (int m = 0; m < SSAMG_EW; ++m) d[m] = g0 + m * NT < L.N ? L.dinv[g0 + m * NT] : (T)0;
     pdl_wait();
-    if (g < L.N) x[g] = d * b[g];
+#pragma unroll
+    for (int m = 0; m < SSAMG_EW; ++m)
+      if (g0 + m * NT < L.N) x[g0 + m * NT] = d[m] * b[g0 + m * NT];
     return;
   }
   u_row_job(
@@ -43,17 +48,23 @@ __global__ void __launch_bounds__(NT) k_relax0_u(LevelView<T> L, int nb, const T
 // b0 = (T) r, x = omega M^-1 b0 on the cell blocks; uy = U x on the rest.
 template <class T>
 __global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
-                                                       const double* __restrict__ r64,
-                                                       T* __restrict__ b0, T* __restrict__ x) {
+                                                       const double* r64,
+                                                       T* b0, T* x) {
   pdl_trigger();
   if ((int)blockIdx.x < nb) {
-    const int g = blockIdx.x * NT + threadIdx.x;
-    const T d = g < L.N ? L.dinv[g] : (T)0;
+    const int g0 = blockIdx.x * (NT * SSAMG_EW) + threadIdx.x;
+    T d[SSAMG_EW];
+#pragma unroll
+    for (int m = 0; m < SSAMG_EW; ++m) d[m] = g0 + m * NT < L.N ? L.dinv[g0 + m * NT] : (T)0;
     pdl_wait();
-    if (g < L.N) {
-      const T bv = (T)r64[g];
-      b0[g] = bv;
-      x[g] = d * bv;
+#pragma unroll
+    for (int m = 0; m < SSAMG_EW; ++m) {
+      const int g = g0 + m * NT;
+      if (g < L.N) {
+        const T bv = (T)r64[g];
+        b0[g] = bv;
+        x[g] = d[m] * bv;
+      }
     }
     return;
   }
@@ -64,7 +75,7 @@ __global__ void __launch_bounds__(NT) k_relax0_u_first(LevelView<T> L, int nb,
 
 // uy = U x (row jobs only)
 template <class T>
-__global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__ x) {
+__global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* x) {
   pdl_trigger();
   u_row_job(
       L, blockIdx.x, [](int, int) { return 0; }, [&](int col, int, int) { return x[col]; });
@@ -72,8 +83,8 @@ __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* __restrict__
 
 // r = b - A x
 template <class T, int SH>
-__global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __restrict__ x,
-                                                    const T* __restrict__ b, T* __restrict__ r) {
+__global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* x,
+                                                    const T* b, T* r) {
   pdl_trigger();
   __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
@@ -87,8 +98,8 @@ __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* __r
 
 // xo = x + omega M^-1 (b - A x)
 template <class T, int SH>
-__global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __restrict__ x,
-                                                 const T* __restrict__ b, T* __restrict__ xo) {
+__global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* x,
+                                                 const T* b, T* xo) {
   pdl_trigger();
   __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
@@ -104,12 +115,12 @@ __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* __rest
 // the FP64 preconditioned residual z, with the block partials of r.z and
 // r.zprev (flexible CG; zprev then takes z) for the PCG's beta.
 template <class T, int SH>
-__global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* __restrict__ x,
-                                                       const T* __restrict__ b,
-                                                       double* __restrict__ z,
-                                                       const double* __restrict__ rpcg,
+__global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* x,
+                                                       const T* b,
+                                                       double* z,
+                                                       const double* rpcg,
                                                        double* zprev, int flex,
-                                                       double* __restrict__ partial) {
+                                                       double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
     const int g = sp.off + c;
     // the FP64 operands are fetched with the stencil's, not after it (zprev
     // is a valid buffer even without flexible CG: z itself, read before its
-    // store and then unused; hence zprev is not declared __restrict__)
+    // store and then unused)
     const double rv = rpcg[g];
     const double zo = zprev[g];
     const double zv = (double)fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
@@ -144,7 +155,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
 // fine points beside it along d* (weights PE of the west one, PW of the east).
 template <class T>
 __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
-                                                 const T* __restrict__ r, T* __restrict__ bc) {
+                                                 const T* r, T* bc) {
   pdl_trigger();
   __shared__ DPart fp;
   __shared__ DPart cp;
@@ -191,8 +202,8 @@ struct PCol {
 // at setup), so the two roles need no ordering.  P rows are setup data and
 // are fetched before the wait for the predecessor.
 template <class T>
-__global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __restrict__ ec,
-                                                  const T* __restrict__ xin, T* __restrict__ xout,
+__global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* ec,
+                                                  const T* xin, T* xout,
                                                   int nb) {
   pdl_trigger();
   __shared__ DPart fp;
@@ -235,8 +246,8 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* __res
 
 // x += P ec, one fine cell per thread.
 template <class T>
-__global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restrict__ ec,
-                                                T* __restrict__ x) {
+__global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* ec,
+                                                T* x) {
   pdl_trigger();
   __shared__ DPart fp;
   int p = block_part(F.blk, F.parts, F.np, fp);
@@ -253,8 +264,8 @@ __global__ void __launch_bounds__(NT) k_prolong(LevelView<T> F, const T* __restr
 // staged in shared memory first (one coalesced load instead of a dependent
 // global load per row).
 template <class T>
-__global__ void k_coarse_solve(int n, const double* __restrict__ Lg, const T* __restrict__ b,
-                               T* __restrict__ x, int staged) {
+__global__ void k_coarse_solve(int n, const double* Lg, const T* b,
+                               T* x, int staged) {
   pdl_trigger();
   pdl_wait();
   extern __shared__ double sm[];
@@ -350,7 +361,7 @@ __device__ __forceinline__ int tail_part(const int* __restrict__ cs, int np, int
 // launch).  ONE = false: a cooperative grid with grid_barrier().
 template <class T, bool ONE>
 __global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
-    k_vtail(const TailLevel<T>* __restrict__ lvg, int nlev, const double* __restrict__ cinv,
+    k_vtail(const TailLevel<T>* lvg, int nlev, const double* cinv,
             int nL, int coarse_direct, TailBarrier* gb) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
@@ -498,8 +509,8 @@ __global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
 
 // Coarsest level with the explicit inverse: x = A_L^-1 b, one thread per row.
 template <class T>
-__global__ void k_coarse_apply(int n, const double* __restrict__ inv, const T* __restrict__ b,
-                               T* __restrict__ x) {
+__global__ void k_coarse_apply(int n, const double* inv, const T* b,
+                               T* x) {
   pdl_trigger();
   pdl_wait();
   extern __shared__ double sb[];
@@ -536,21 +547,21 @@ __global__ void k_coarse_inverse(int n, const double* __restrict__ Lf, double* _
   }
 }
 
-__global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, int n) {
+__global__ void k_cast_d2f(const double* in, float* out, int n) {
   pdl_trigger();
   pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (float)in[g];
 }
-__global__ void k_cast_f2d(const float* __restrict__ in, double* __restrict__ out, int n) {
+__global__ void k_cast_f2d(const float* in, double* out, int n) {
   pdl_trigger();
   pdl_wait();
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (double)in[g];
 }
 
-__global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* __restrict__ x,
-                                               double* __restrict__ y, int padded) {
+__global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const double* x,
+                                               double* y, int padded) {
   pdl_trigger();
   __shared__ DPart sp;
   int p = block_part(L.blk, L.parts, L.np, sp);
@@ -586,9 +597,9 @@ __device__ __forceinline__ void finish_sums(const double* __restrict__ partial, 
 
 // r = b - A x; partial sums of (b.b, r.r)
 template <int SH>
-__global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* __restrict__ b,
-                                                 const double* __restrict__ x, double* __restrict__ r,
-                                                 double* __restrict__ partial) {
+__global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const double* b,
+                                                 const double* x, double* r,
+                                                 double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -613,8 +624,8 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
 }
 
 // per problem (one block each): ||b||^2, ||r||^2 and the stopping threshold
-__global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ partial,
-                                                     const int* __restrict__ pb, PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* partial,
+                                                     const int* pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[2];
@@ -632,10 +643,10 @@ __global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* __restrict__ 
 }
 
 // p = z (and zprev = z for flexible CG); partial r.z
-__global__ void __launch_bounds__(NT) k_pcg_start(LevelView<double> L, const double* __restrict__ r,
-                                                  const double* __restrict__ z,
-                                                  double* __restrict__ p, double* __restrict__ zprev,
-                                                  int flex, double* __restrict__ partial) {
+__global__ void __launch_bounds__(NT) k_pcg_start(LevelView<double> L, const double* r,
+                                                  const double* z,
+                                                  double* p, double* zprev,
+                                                  int flex, double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -659,8 +670,8 @@ __device__ __forceinline__ void set_continue(int active, cudaGraphConditionalHan
   if (use_handle) cudaGraphSetConditional(h, active ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__ partial,
-                                                      const int* __restrict__ pb, PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* partial,
+                                                      const int* pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
@@ -678,10 +689,10 @@ __global__ void __launch_bounds__(NT) k_pcg_start_fin(const double* __restrict__
 
 // partial (r.z, r.zprev) for beta; zprev takes the new z (flexible CG)
 __global__ void __launch_bounds__(NT) k_pcg_dots_rz(LevelView<double> L,
-                                                    const double* __restrict__ r,
-                                                    const double* __restrict__ z,
-                                                    double* __restrict__ zprev, int flex,
-                                                    double* __restrict__ partial) {
+                                                    const double* r,
+                                                    const double* z,
+                                                    double* zprev, int flex,
+                                                    double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -706,8 +717,8 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(LevelView<double> L,
   }
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ partial,
-                                                     const int* __restrict__ pb, PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* partial,
+                                                     const int* pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[2];
@@ -727,9 +738,9 @@ __global__ void __launch_bounds__(NT) k_pcg_beta_fin(const double* __restrict__ 
 }
 
 // p = z + beta p (per problem)
-__global__ void __launch_bounds__(NT) k_pcg_xpby(LevelView<double> L, const double* __restrict__ z,
-                                                 double* __restrict__ p,
-                                                 const PcgScalars* __restrict__ sc) {
+__global__ void __launch_bounds__(NT) k_pcg_xpby(LevelView<double> L, const double* z,
+                                                 double* p,
+                                                 const PcgScalars* sc) {
   pdl_trigger();
   __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
@@ -746,9 +757,9 @@ __global__ void __launch_bounds__(NT) k_pcg_xpby(LevelView<double> L, const doub
 
 // q = A p; partial p.q
 template <int SH>
-__global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* __restrict__ p,
-                                                     double* __restrict__ q,
-                                                     double* __restrict__ partial) {
+__global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, const double* p,
+                                                     double* q,
+                                                     double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -766,8 +777,8 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, con
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__ partial,
-                                                      const int* __restrict__ pb, PcgScalars* sc) {
+__global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* partial,
+                                                      const int* pb, PcgScalars* sc) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
@@ -788,11 +799,11 @@ __global__ void __launch_bounds__(NT) k_pcg_alpha_fin(const double* __restrict__
 }
 
 // x += alpha p; r -= alpha q; partial r.r (per problem)
-__global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const double* __restrict__ p,
-                                                   const double* __restrict__ q,
-                                                   double* __restrict__ x, double* __restrict__ r,
-                                                   double* __restrict__ partial,
-                                                   const PcgScalars* __restrict__ sc) {
+__global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const double* p,
+                                                   const double* q,
+                                                   double* x, double* r,
+                                                   double* partial,
+                                                   const PcgScalars* sc) {
   pdl_trigger();
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
@@ -817,8 +828,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const do
 // Per problem: ||r||^2, iteration count and the stopping test.  The last
 // block to finish (ticket counter) sets ctl->active to whether any problem
 // still iterates and, inside the solve graph, the loop condition with it.
-__global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict__ partial,
-                                                       const int* __restrict__ pb, PcgScalars* sc,
+__global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* partial,
+                                                       const int* pb, PcgScalars* sc,
                                                        PcgCtl* ctl, cudaGraphConditionalHandle h,
                                                        int use_handle) {
   pdl_trigger();
@@ -852,9 +863,9 @@ __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* __restrict_
 }
 
 // per problem: (||b||^2, ||b - A x||^2)
-__global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ partial,
-                                                     const int* __restrict__ pb,
-                                                     double* __restrict__ out) {
+__global__ void __launch_bounds__(NT) k_true_res_fin(const double* partial,
+                                                     const int* pb,
+                                                     double* out) {
   pdl_trigger();
   pdl_wait();
   __shared__ double o2[2];
@@ -870,9 +881,9 @@ __global__ void __launch_bounds__(NT) k_true_res_fin(const double* __restrict__ 
 // Differentiation
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
-                                                      const double* __restrict__ lam,
-                                                      const double* __restrict__ x,
-                                                      double* __restrict__ dcoef, long long N) {
+                                                      const double* lam,
+                                                      const double* x,
+                                                      double* dcoef, long long N) {
   pdl_trigger();
   __shared__ DPart sp;
   int p = block_part(L.blk, L.parts, L.np, sp);
@@ -892,10 +903,10 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
 }
 
 __global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double> L,
-                                                               const double* __restrict__ gg,
-                                                               const double* __restrict__ lam,
-                                                               const double* __restrict__ x,
-                                                               double* __restrict__ dg) {
+                                                               const double* gg,
+                                                               const double* lam,
+                                                               const double* x,
+                                                               double* dg) {
   pdl_trigger();
   pdl_wait();
   __shared__ DPart sp;
@@ -956,7 +967,7 @@ void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
 }
 template <class T>
 void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
-  int nb = cdiv(L.N, NT);
+  int nb = cdiv(L.N, NT * SSAMG_EW);
   launch_k(k_relax0_u<T>, nb + L.nublk, NT, 0, st, L.view<T>(), nb, b, x);
   SSAMG_LAUNCH_CHECK();
 }
@@ -972,7 +983,7 @@ void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
 
 template <class T>
 void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaStream_t st) {
-  int nb = cdiv(L.N, NT);
+  int nb = cdiv(L.N, NT * SSAMG_EW);
   launch_k(k_relax0_u_first<T>, nb + L.nublk, NT, 0, st, L.view<T>(), nb, r64, b0, x);
   SSAMG_LAUNCH_CHECK();
 }

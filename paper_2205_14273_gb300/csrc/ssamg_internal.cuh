@@ -26,6 +26,7 @@
 #define SSAMG_BLOCK 256
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
+#define SSAMG_EW 4                 // cells per thread of the elementwise pre-relaxation
 #define SSAMG_TPR 4                          // threads per U row in row jobs
 #define SSAMG_RPB (SSAMG_BLOCK / SSAMG_TPR)  // U rows per block
 
