@@ -117,6 +117,10 @@ typedef struct {
                           launch, so that each kernel is scheduled, and stages its part
                           descriptors, while its predecessor still runs; 0: plain launches */
   int tail_cells;      /* largest level of the use_tail = 2 tail (0: 4096) */
+  int use_bricks;      /* 1 (default): residual, relaxation and PCG operator applies on checked
+                          7-point levels (constant entries per part) run over 32 x 8 x 8
+                          bricks, each thread marching a column along z; 0: over the cell
+                          tiles of the other shapes */
 } ssamg_params;
 
 typedef struct {

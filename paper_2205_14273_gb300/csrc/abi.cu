@@ -152,6 +152,7 @@ struct ssamg_solver_s {
   std::vector<int> part_prob;  // problem of each part (empty: all 0)
   std::vector<long long> prob_cells;  // nprob + 1 first cells of each problem
   int* pb = nullptr;           // nprob + 1 level-0 block starts of each problem (device)
+  int* pbb = nullptr;          // the same in brick blocks
   PcgCtl* ctl = nullptr;
   PcgScalars* sc_init = nullptr;  // nprob starting scalars (tolerance, caps)
   PcgScalars* sc_hist = nullptr;  // per right-hand side copies of sc (multi-round solves)
@@ -174,14 +175,22 @@ struct ssamg_solver_s {
 
 thread_local long long g_ssamg_launches = 0;
 thread_local int g_ssamg_pdl = 0;
+thread_local int g_ssamg_bricks = 1;
 
 // Enables programmatic dependent launch for the solve kernels an entry point
 // enqueues (when the solver's parameters ask for it), and restores the
 // previous setting on exit.
 struct PdlScope {
-  int old;
-  explicit PdlScope(int on) : old(g_ssamg_pdl) { g_ssamg_pdl = on; }
-  ~PdlScope() { g_ssamg_pdl = old; }
+  int old, old_b;
+  explicit PdlScope(const ssamg_params& prm)
+      : old(g_ssamg_pdl), old_b(g_ssamg_bricks) {
+    g_ssamg_pdl = prm.use_pdl;
+    g_ssamg_bricks = prm.use_bricks;
+  }
+  ~PdlScope() {
+    g_ssamg_pdl = old;
+    g_ssamg_bricks = old_b;
+  }
 };
 
 // Address of the static coupling-sum scratch per device, resolved by setup
@@ -538,6 +547,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->use_tail = 0;
   p->use_pdl = 1;
   p->tail_cells = 0;
+  p->use_bricks = 1;
 }
 
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
@@ -647,6 +657,16 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   }
   L.nblk = blk[np];
   L.nfblk = fblk[np];
+  // bricks (checked 7-point operator applies)
+  std::vector<int> bblk(np + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    const PartH& h = L.parts[p];
+    const long long nb = cdivll(h.n[0], SSAMG_BRICK_X) * cdivll(h.n[1], SSAMG_BRICK_Y) *
+                         cdivll(h.n[2], SSAMG_BRICK_Z);
+    bblk[p + 1] = bblk[p] + (int)nb;
+  }
+  L.nbblk = bblk[np];
+  L.hbblk = bblk;
   L.hblk = blk;
   for (int p = 0; p < np; ++p) {
     DPart& dp = L.dparts[p];
@@ -654,6 +674,10 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     dp.prob = s->part_prob.empty() ? 0 : s->part_prob[p];
     dp.blk0 = blk[p];
     dp.fblk0 = fblk[p];
+    dp.bblk0 = bblk[p];
+    dp.bb[0] = (int)cdivll(L.parts[p].n[0], SSAMG_BRICK_X);
+    dp.bb[1] = (int)cdivll(L.parts[p].n[1], SSAMG_BRICK_Y);
+    dp.bb[2] = (int)cdivll(L.parts[p].n[2], SSAMG_BRICK_Z);
     dp.cpt = L.cpt;
     if (next) {
       const PartH& c = next->parts[p];
@@ -667,6 +691,7 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   if (!L.d_parts) {
     L.d_parts = aalloc<DPart>(s->arena, np);
     L.d_blk = aalloc<int>(s->arena, np + 1);
+    L.d_bblk = aalloc<int>(s->arena, np + 1);
     L.d_fblk = aalloc<int>(s->arena, np + 1);
     L.d_cellstart = aalloc<int>(s->arena, np + 1);
   }
@@ -689,6 +714,7 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   }
   SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_bblk, bblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_cellstart, cs.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
 }
@@ -1058,7 +1084,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->p = (double*)padded_vector(s, sizeof(double), N, L0g, st);
   s->q = aalloc<double>(s->arena, N);
   s->zprev = aalloc<double>(s->arena, N);
-  s->partial = aalloc<double>(s->arena, 2ll * L0.nblk);
+  s->partial = aalloc<double>(s->arena, 2ll * std::max(L0.nblk, L0.nbblk));
   s->tres = aalloc<double>(s->arena, 2ll * s->nprob);
   s->sc = aalloc<PcgScalars>(s->arena, s->nprob);
   s->ctl = aalloc<PcgCtl>(s->arena, 1);
@@ -1078,15 +1104,19 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   }
   {
     // level-0 block and cell ranges of each problem (parts are problem-ordered)
-    std::vector<int> hpb(s->nprob + 1, L0.nblk);
+    std::vector<int> hpb(s->nprob + 1, L0.nblk), hpbb(s->nprob + 1, L0.nbblk);
     s->prob_cells.assign(s->nprob + 1, N);
     for (int p = L0.np - 1; p >= 0; --p) {
       const int k = s->part_prob.empty() ? 0 : s->part_prob[p];
       hpb[k] = L0.hblk[p];
+      hpbb[k] = L0.hbblk[p];
       s->prob_cells[k] = L0.parts[p].off;
     }
     s->pb = aalloc<int>(s->arena, s->nprob + 1);
+    s->pbb = aalloc<int>(s->arena, s->nprob + 1);
     SSAMG_CUDA(cudaMemcpyAsync(s->pb, hpb.data(), sizeof(int) * (s->nprob + 1),
+                               cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(s->pbb, hpbb.data(), sizeof(int) * (s->nprob + 1),
                                cudaMemcpyHostToDevice, st));
     SSAMG_CUDA(cudaStreamSynchronize(st));  // hpb is a host temporary
   }
@@ -1187,7 +1217,9 @@ int vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st, double* 
 
 // PCG segments.  init: r = b - A x; the first iteration is peeled so that the
 // loop body starts with the V-cycle and ends with the convergence test.
-PcgCtx pcg_ctx(ssamg_solver s) { return PcgCtx{s->pb, s->nprob, s->sc, s->ctl, s->partial}; }
+PcgCtx pcg_ctx(ssamg_solver s) {
+  return PcgCtx{s->pb, s->pbb, s->nprob, s->sc, s->ctl, s->partial};
+}
 
 void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
   Level& L0 = s->lev[0];
@@ -1206,8 +1238,8 @@ void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, c
   // the cycle's last kernel also forms r.z (and r.zprev) for beta
   const PcgCtx c = pcg_ctx(s);
   const int npart = vcycle(s, s->r, s->z, st, s->partial, zp);
-  if (npart > 0)
-    launch_pcg_beta_from_partials(L0, s->z, s->p, c, st);
+  if (npart > 0)  // the last relaxation writes partials per cell-tile block
+    launch_pcg_beta_from_partials(L0, s->z, s->p, c, c.pb, st);
   else
     launch_pcg_beta(L0, s->r, s->z, zp, s->p, c, st);
   launch_pcg_alpha(L0, s->p, s->q, c, st);
@@ -1455,7 +1487,7 @@ extern "C" int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs,
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -1479,7 +1511,7 @@ extern "C" int ssamg_solve_host(ssamg_solver s, const double* b, double* x, int 
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int k = 0; k < nrhs; ++k) {
@@ -1507,7 +1539,7 @@ extern "C" int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const d
   if (!s || !lambda || !x || !dcoef) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   launch_coef_gradient(s->lev[0], lambda, x, dcoef, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1518,7 +1550,7 @@ extern "C" int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, con
   if (!s || !g || !lambda || !x || !dg) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1528,7 +1560,7 @@ extern "C" int ssamg_precondition(ssamg_solver s, const double* r, double* z, vo
   if (!s || !r || !z) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   vcycle(s, r, z, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1540,7 +1572,7 @@ extern "C" int ssamg_level_matvec(ssamg_solver s, int level, const double* x, do
   if (!s->ready) return SSAMG_ERR_STATE;
   if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   launch_matvec(s->lev[level], x, y, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
@@ -1656,7 +1688,7 @@ extern "C" int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int 
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   if (s->prm.use_graph) return run_rounds(s, b, x, nrhs, cst, st);
   const long long N = s->lev[0].N;
   int rc = SSAMG_OK;
@@ -1806,7 +1838,7 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
   if (level < 0 || level > Lc || ((kernel == 3 || kernel == 4) && level >= Lc)) return SSAMG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   API_BEGIN
-  PdlScope pdl(s->prm.use_pdl);
+  PdlScope pdl(s->prm);
   if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
   Level& L = s->lev[level];
   const bool f = s->prm.precision == 1;
@@ -1850,7 +1882,7 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
           throw SsamgError{SSAMG_ERR_ARG, "kernel 9 times the FP32 cycle's last relaxation"};
         break;
       case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
-        launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), cs);
+        launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), s->pb, cs);
         launch_pcg_update(s->lev[0], s->p, s->q, s->x, s->r, pcg_ctx(s), 0, 0, cs);
         break;
       default:

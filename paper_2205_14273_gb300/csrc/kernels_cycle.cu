@@ -151,6 +151,169 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Checked 7-point operator applies over bricks (levels of shape SH_K7: entries
+// [C, -x, +x, -y, +y, -z, +z], some of them constant per part).  A block takes
+// an SSAMG_BRICK_X x _Y x _Z brick of one part and each thread marches one
+// (i, j) column along z, carrying x at k-1 and k in registers: no cell
+// coordinate needs a division, and each x value comes from DRAM once (the
+// in-plane neighbours hit L1).  The operation Op supplies the per-cell inputs
+// of its epilogue (`load`, issued ahead of the stencil's loads, so that a
+// cell costs one memory round trip) and the epilogue (`apply`).  The stencil
+// terms are summed in the order of stencil7_canon_checked, so a cell's A x is
+// bitwise that of the cell-tile kernels.
+// ---------------------------------------------------------------------------
+template <class T, class Op>
+__device__ __forceinline__ void brick7(const LevelView<T>& L, const DPart& sp, const T* x,
+                                       Op& op) {
+  const int bl = (int)blockIdx.x - sp.bblk0;
+  const int bx = bl % sp.bb[0];
+  const int byz = bl / sp.bb[0];
+  const int by = byz % sp.bb[1];
+  const int bz = byz / sp.bb[1];
+  const int nx = sp.n[0], ny = sp.n[1], nz = sp.n[2], nxy = nx * ny;
+  const int i = bx * SSAMG_BRICK_X + (int)threadIdx.x % SSAMG_BRICK_X;
+  const int j = by * SSAMG_BRICK_Y + (int)threadIdx.x / SSAMG_BRICK_X;
+  if (i >= nx || j >= ny) return;
+  const int k0 = bz * SSAMG_BRICK_Z;
+  const int kend = min(k0 + SSAMG_BRICK_Z, nz);
+  const unsigned vm = sp.varmask;
+  const T* xp0 = x + sp.off;
+  const bool bw = i > 0, be = i < nx - 1, bs = j > 0, bn = j < ny - 1;
+  const bool face_ij = !(bw && be && bs && bn);
+  const T c1 = const_of<T>(sp, 1), c2 = const_of<T>(sp, 2), c3 = const_of<T>(sp, 3),
+          c4 = const_of<T>(sp, 4), c5 = const_of<T>(sp, 5), c6 = const_of<T>(sp, 6),
+          c0 = const_of<T>(sp, 0);
+  int c = (k0 * ny + j) * nx + i;
+  T xm = k0 > 0 ? xp0[c - nxy] : (T)0;
+  T xcur = xp0[c];
+#pragma unroll 1
+  for (int k = k0; k < kend; ++k, c += nxy) {
+    const auto in = op.load(sp.off + c);
+    const T xz = k + 1 < nz ? xp0[c + nxy] : (T)0;
+    const T xw = bw ? xp0[c - 1] : (T)0;
+    const T xe = be ? xp0[c + 1] : (T)0;
+    const T xs = bs ? xp0[c - nx] : (T)0;
+    const T xn = bn ? xp0[c + nx] : (T)0;
+    const T a0 = (vm & 1u) ? L.coef[sp.coef[0] + c] : c0;
+    const T a1 = (vm & 2u) ? L.coef[sp.coef[1] + c] : c1;
+    const T a2 = (vm & 4u) ? L.coef[sp.coef[2] + c] : c2;
+    const T a3 = (vm & 8u) ? L.coef[sp.coef[3] + c] : c3;
+    const T a4 = (vm & 16u) ? L.coef[sp.coef[4] + c] : c4;
+    const T a5 = (vm & 32u) ? L.coef[sp.coef[5] + c] : c5;
+    const T a6 = (vm & 64u) ? L.coef[sp.coef[6] + c] : c6;
+    T acc = (T)0;
+    acc = fma(a0, xcur, acc);
+    acc = fma(a1, xw, acc);
+    acc = fma(a2, xe, acc);
+    acc = fma(a3, xs, acc);
+    acc = fma(a4, xn, acc);
+    acc = fma(a5, k > 0 ? xm : (T)0, acc);
+    acc = fma(a6, xz, acc);
+    if (sp.has_u && (face_ij || k == 0 || k == nz - 1)) acc += L.uy[sp.off + c];
+    op.apply(sp.off + c, acc, xcur, in);
+    xm = xcur;
+    xcur = xz;
+  }
+}
+
+template <class T>
+struct ResidualOp {
+  const T* b;
+  T* r;
+  __device__ T load(int g) const { return b[g]; }
+  __device__ void apply(int g, T ax, T, T bv) const { r[g] = bv - ax; }
+};
+
+template <class T>
+struct RelaxOp {
+  const T* b;
+  const T* dinv;
+  T* xo;
+  struct In {
+    T b, d;
+  };
+  __device__ In load(int g) const { return In{b[g], dinv[g]}; }
+  __device__ void apply(int g, T ax, T xg, In in) const { xo[g] = fma(in.d, in.b - ax, xg); }
+};
+
+struct PcgInitOp {
+  const double* b;
+  double* r;
+  double bb, rr;
+  __device__ double load(int g) const { return b[g]; }
+  __device__ void apply(int g, double ax, double, double bv) {
+    const double rv = bv - ax;
+    r[g] = rv;
+    bb = fma(bv, bv, bb);
+    rr = fma(rv, rv, rr);
+  }
+};
+
+struct SpmvDotOp {
+  double* q;
+  double s;
+  __device__ int load(int) const { return 0; }
+  __device__ void apply(int g, double ax, double pg, int) {
+    q[g] = ax;
+    s = fma(pg, ax, s);
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(NT, 6) k7b_residual(LevelView<T> L, const T* x, const T* b, T* r) {
+  pdl_trigger();
+  __shared__ DPart sp;
+  block_part(L.bblk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  ResidualOp<T> op{b, r};
+  brick7(L, sp, x, op);
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT, 6) k7b_relax(LevelView<T> L, const T* x, const T* b, T* xo) {
+  pdl_trigger();
+  __shared__ DPart sp;
+  block_part(L.bblk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  RelaxOp<T> op{b, L.dinv, xo};
+  brick7(L, sp, x, op);
+}
+
+__global__ void __launch_bounds__(NT, 4) k7b_pcg_init(LevelView<double> L, const double* b,
+                                                   const double* x, double* r, double* partial) {
+  pdl_trigger();
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  block_part(L.bblk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  PcgInitOp op{b, r, 0.0, 0.0};
+  brick7(L, sp, x, op);
+  const double s0 = block_sum<NT>(op.bb, sh);
+  const double s1 = block_sum<NT>(op.rr, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+__global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const double* p, double* q,
+                                                   double* partial) {
+  pdl_trigger();
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  block_part(L.bblk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  SpmvDotOp op{q, 0.0};
+  brick7(L, sp, p, op);
+  const double t = block_sum<NT>(op.s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
 // bc = P^T r, one coarse cell per thread: the anchor (weight 1) and the two
 // fine points beside it along d* (weights PE of the west one, PW of the east).
 template <class T>
@@ -959,6 +1122,12 @@ void launch_k(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t
 }
 }  // namespace
 
+bool uses_bricks(const Level& L) { return g_ssamg_bricks && L.shape == SH_K7 && L.nbblk > 0; }
+
+// Level-0 block ranges of the problems for the partials that L's operator
+// apply launches write (brick or cell-tile blocks).
+const int* partial_ranges(const Level& L, const PcgCtx& c) { return uses_bricks(L) ? c.pbb : c.pb; }
+
 template <class T>
 void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
   const T* dinv = L.view<T>().dinv;
@@ -993,8 +1162,10 @@ void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const
   // zprev may be null (no flexible CG): pass a valid buffer and a flag
   const int flex = zprev != nullptr;
   double* zp = flex ? zprev : z;
-  SH_DISPATCH(L.shape, (launch_k(k_relax_final<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, z, rpcg,
-                                                                      zp, flex, partial)));
+  // (on cell tiles also on brick levels: a z-marching brick form of this
+  // FP64-heavy epilogue measured 1.6-4x slower)
+  SH_DISPATCH(L.shape, (launch_k(k_relax_final<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, z,
+                                 rpcg, zp, flex, partial)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -1011,12 +1182,18 @@ void launch_uy(const Level& L, const T* x, cudaStream_t st) {
 
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (launch_k(k_residual<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, r)));
+  if (uses_bricks(L))
+    launch_k(k7b_residual<T>, L.nbblk, NT, 0, st, L.view<T>(), x, b, r);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_residual<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, r)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
-  SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, xo)));
+  if (uses_bricks(L))
+    launch_k(k7b_relax<T>, L.nbblk, NT, 0, st, L.view<T>(), x, b, xo);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, xo)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -1135,10 +1312,13 @@ void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st) 
 void launch_pcg_init(const Level& L, const double* b, const double* x, double* r,
                      const PcgCtx& c, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
-                                 c.partial)));
+  if (uses_bricks(L))
+    launch_k(k7b_pcg_init, L.nbblk, NT, 0, st, L.view<double>(), b, x, r, c.partial);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
+                                   c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_init_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
+  launch_k(k_pcg_init_fin, c.nprob, NT, 0, st, c.partial, partial_ranges(L, c), c.sc);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -1157,12 +1337,12 @@ void launch_pcg_beta(const Level& L0, const double* r, const double* z, double* 
   launch_k(k_pcg_dots_rz, L0.nblk, NT, 0, st, L0.view<double>(), r, z, zprev ? zprev : p,
            zprev != nullptr, c.partial);
   SSAMG_LAUNCH_CHECK();
-  launch_pcg_beta_from_partials(L0, z, p, c, st);
+  launch_pcg_beta_from_partials(L0, z, p, c, c.pb, st);
 }
 
 void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, const PcgCtx& c,
-                                   cudaStream_t st) {
-  launch_k(k_pcg_beta_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
+                                   const int* ranges, cudaStream_t st) {
+  launch_k(k_pcg_beta_fin, c.nprob, NT, 0, st, c.partial, ranges, c.sc);
   SSAMG_LAUNCH_CHECK();
   launch_k(k_pcg_xpby, L0.nblk, NT, 0, st, L0.view<double>(), z, p, c.sc);
   SSAMG_LAUNCH_CHECK();
@@ -1171,10 +1351,13 @@ void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, 
 void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& c,
                       cudaStream_t st) {
   launch_uy<double>(L, p, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q,
-                                 c.partial)));
+  if (uses_bricks(L))
+    launch_k(k7b_spmv_dot, L.nbblk, NT, 0, st, L.view<double>(), p, q, c.partial);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q,
+                                   c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_alpha_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc);
+  launch_k(k_pcg_alpha_fin, c.nprob, NT, 0, st, c.partial, partial_ranges(L, c), c.sc);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -1190,10 +1373,13 @@ void launch_pcg_update(const Level& L0, const double* p, const double* q, double
 void launch_true_residual(const Level& L, const double* b, const double* x, double* r,
                           const PcgCtx& c, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
-  SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
-                                 c.partial)));
+  if (uses_bricks(L))
+    launch_k(k7b_pcg_init, L.nbblk, NT, 0, st, L.view<double>(), b, x, r, c.partial);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
+                                   c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_true_res_fin, c.nprob, NT, 0, st, c.partial, c.pb, out);
+  launch_k(k_true_res_fin, c.nprob, NT, 0, st, c.partial, partial_ranges(L, c), out);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -27,6 +27,11 @@
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
 #define SSAMG_EW 4                 // cells per thread of the elementwise pre-relaxation
+// Bricks of the checked 7-point operator applies: SSAMG_BRICK_X x _Y threads
+// (one column each), marching SSAMG_BRICK_Z cells along z.
+#define SSAMG_BRICK_X 32
+#define SSAMG_BRICK_Y 8
+#define SSAMG_BRICK_Z 8
 #define SSAMG_TPR 4                          // threads per U row in row jobs
 #define SSAMG_RPB (SSAMG_BLOCK / SSAMG_TPR)  // U rows per block
 
@@ -88,6 +93,8 @@ struct DPart {
   unsigned varmask;            // bit e: entry e is per cell
   int zeroext;                 // per-cell entries are exactly zero where c + o leaves the box
   int prob;                    // problem of the part (a batch of independent problems)
+  int bblk0;                   // first block of brick launches over this level
+  int bb[3];                   // bricks along x, y, z (SSAMG_BRICK_X x _Y x _Z cells each)
   FastDiv dx, dxy;             // divide by n[0], n[0]*n[1]
   FastDiv cdx, cdxy;           // same on the next level
   FastDiv fdx, fdxy;           // same on the fine-point grid
@@ -112,9 +119,11 @@ struct PcgCtl {
 };
 
 // Device state the PCG launchers share: one PcgScalars per problem, the
-// level-0 block range of each problem (pb[0..nprob]) and the block partials.
+// level-0 block range of each problem (pb[0..nprob], and pbb[0..nprob] for
+// brick launches) and the block partials.
 struct PcgCtx {
   const int* pb;
+  const int* pbb;  // the same in brick blocks (the level-0 brick launches' partials)
   int nprob;
   PcgScalars* sc;
   PcgCtl* ctl;
@@ -126,6 +135,7 @@ template <class T>
 struct LevelView {
   const DPart* parts;
   const int* blk;        // np + 1 block starts of cell-wise launches
+  const int* bblk;       // np + 1 block starts of brick launches
   const int* fblk;       // np + 1 block starts of fine-point launches
   const int* cellstart;  // np + 1 first cells
   int np;
@@ -210,12 +220,14 @@ struct Level {
   std::vector<DPart> dparts;
   DPart* d_parts = nullptr;
   int* d_blk = nullptr;
+  int* d_bblk = nullptr;
   int* d_fblk = nullptr;
   int* d_cellstart = nullptr;
-  int nblk = 0, nfblk = 0;
+  int nblk = 0, nfblk = 0, nbblk = 0;
   int cpt = 1;
   int shape = 0;  // StencilShape of the level's operator apply
   std::vector<int> hblk;  // host copy of the block starts of cell-wise launches
+  std::vector<int> hbblk; // and of brick launches
   double* coef = nullptr;
   float* coef32 = nullptr;
   long long ncoef = 0;
@@ -253,12 +265,12 @@ struct Level {
 
 template <>
 inline LevelView<double> Level::view<double>() const {
-  return LevelView<double>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
+  return LevelView<double>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
                            u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
-  return LevelView<float>{d_parts, d_blk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
+  return LevelView<float>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
                           Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, uy32,
                           nr, nublk};
 }
@@ -282,6 +294,9 @@ extern thread_local long long g_ssamg_launches;
 // dependent launch (per host thread; set by the entry point, read by the
 // launchers).
 extern thread_local int g_ssamg_pdl;
+// Nonzero while the entry point allows brick launches for checked 7-point
+// levels (per host thread, like g_ssamg_pdl).
+extern thread_local int g_ssamg_bricks;
 #define SSAMG_LAUNCH_CHECK()       \
   do {                             \
     ++g_ssamg_launches;            \
@@ -369,7 +384,11 @@ void launch_pcg_start(const Level& L0, const double* r, const double* z, double*
 void launch_pcg_beta(const Level& L0, const double* r, const double* z, double* zprev, double* p,
                      const PcgCtx& c, cudaStream_t st);
 void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, const PcgCtx& c,
-                                   cudaStream_t st);
+                                   const int* ranges, cudaStream_t st);
+// Whether L's operator applies run over bricks, and the per-problem ranges of
+// the partials those launches write.
+bool uses_bricks(const Level& L);
+const int* partial_ranges(const Level& L, const PcgCtx& c);
 void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& c,
                       cudaStream_t st);
 void launch_pcg_update(const Level& L0, const double* p, const double* q, double* x, double* r,

@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("coarse_direct", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("use_tail", ctypes.c_int),
-                ("use_pdl", ctypes.c_int), ("tail_cells", ctypes.c_int)]
+                ("use_pdl", ctypes.c_int), ("tail_cells", ctypes.c_int),
+                ("use_bricks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
