@@ -411,6 +411,21 @@ extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int
   return SSAMG_OK;
 }
 
+// Order in which a matrix's stencil entries are stored and, on level 0,
+// held by the solver: offset-code order ((ox+1) + 3 (oy+1) + 9 (oz+1)) for a
+// full 27-point stencil (whose specialised kernels expect it), else the
+// user's entry order.
+std::vector<int> storage_order(const ssamg_matrix_s* A) {
+  std::vector<int> order(A->nent);
+  for (int e = 0; e < A->nent; ++e) order[e] = e;
+  if (A->nent == 27)
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      auto code = [&](int e) { return (A->o[e][0] + 1) + 3 * (A->o[e][1] + 1) + 9 * (A->o[e][2] + 1); };
+      return code(a) < code(b);
+    });
+  return order;
+}
+
 extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
   if (!A) return SSAMG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -421,11 +436,13 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
     for (int e = 0; e < A->nent; ++e)
       argcheck(A->isset[p][e], "every stencil entry of every part needs a value");
   A->free_device();
-  // pack variable entries
+  // pack variable entries (a 27-point stencil in offset-code order, so that
+  // a part with every entry per cell is one contiguous array in that order)
   A->coef_off.assign(np, std::vector<long long>(A->nent, -1));
+  const std::vector<int> order = storage_order(A);
   long long n = 0;
   for (int p = 0; p < np; ++p)
-    for (int e = 0; e < A->nent; ++e)
+    for (int e : order)
       if (A->isvar[p][e]) {
         A->coef_off[p][e] = n;
         n += g->ncell(p);
@@ -614,6 +631,7 @@ void fill_dpart(DPart& dp, const PartH& h) {
     dp.cval[e] = h.cval[e];
     dp.cval32[e] = (float)h.cval[e];
     dp.slot[(h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1)] = (signed char)e;
+    dp.uent[e] = (signed char)h.uent[e];
   }
   dp.allvar = 1;
   dp.varmask = 0;
@@ -765,11 +783,14 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     h.off = (int)g->off[p];
     h.dstar = -1;
     h.nent = A->nent;
+    const std::vector<int> order = storage_order(A);
     for (int e = 0; e < A->nent; ++e) {
-      for (int d = 0; d < 3; ++d) h.o[e][d] = A->o[e][d];
-      h.var[e] = A->isvar[p][e];
-      h.cval[e] = A->cval[p][e];
-      h.coef_off[e] = A->coef_off[p][e];
+      const int u = order[e];  // the user's entry held as entry e
+      for (int d = 0; d < 3; ++d) h.o[e][d] = A->o[u][d];
+      h.var[e] = A->isvar[p][u];
+      h.cval[e] = A->cval[p][u];
+      h.coef_off[e] = A->coef_off[p][u];
+      h.uent[e] = u;
     }
     h.has_u = A->has_u[p];
   }
@@ -867,7 +888,10 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       c.ncell = (long long)c.n[0] * c.n[1] * c.n[2];
       c.off = (int)off;
       off += c.ncell;
-      for (int e = 0; e < c.nent; ++e) c.var[e] = 1;
+      for (int e = 0; e < c.nent; ++e) {
+        c.var[e] = 1;
+        c.uent[e] = e;
+      }
     }
     C.N = off;
     s->lev.push_back(std::move(C));

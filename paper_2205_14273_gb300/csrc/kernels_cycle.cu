@@ -1060,7 +1060,7 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
     for (int e = 0; e < sp.nent; ++e) {
       double v = 0.0;
       if (inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) v = -l * x[g + sp.disp[e]];
-      dcoef[(long long)e * N + g] = v;
+      dcoef[(long long)sp.uent[e] * N + g] = v;  // in the user's entry order
     }
   }
 }

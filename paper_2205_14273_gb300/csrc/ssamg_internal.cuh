@@ -101,6 +101,7 @@ struct DPart {
   int disp[SSAMG_MAXE];        // linear displacement of each entry
   signed char o[SSAMG_MAXE][3];
   signed char slot[27];        // entry index of offset code (ox+1)+3(oy+1)+9(oz+1), -1 absent
+  signed char uent[SSAMG_MAXE];  // level 0: the user's index of entry e (gradient output order)
   signed char pad_[2];
 };
 static_assert(sizeof(DPart) % 4 == 0 && sizeof(DPart) <= 1024, "DPart layout");
@@ -197,6 +198,7 @@ struct PartH {
   int var[SSAMG_MAXE];
   double cval[SSAMG_MAXE];
   long long coef_off[SSAMG_MAXE];
+  int uent[SSAMG_MAXE];  // level 0: the user's entry index of entry e (coarse levels: e)
   int nf[3];
   long long nfine;
   int poff;

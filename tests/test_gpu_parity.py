@@ -307,8 +307,11 @@ def test_nan_rhs_is_reported(S):
     assert e.value.code == S.ERR_BREAKDOWN
 
 
-def test_coef_gradient_matches_oracle(S):
-    prob = P.multipart_aniso(m=6, layout=(2, 1, 2), seed=6)
+@pytest.mark.parametrize("prob", [P.multipart_aniso(m=6, layout=(2, 1, 2), seed=6),
+                                  P.var27(n=7, block=3, seed=2)], ids=["aniso", "var27"])
+def test_coef_gradient_matches_oracle(S, prob):
+    """dL/da per stencil entry, in the user's entry order (a 27-point
+    stencil is held internally in offset-code order)."""
     h = O.setup(prob)
     grid, A, solver = gpu_setup(S, prob)
     lam = P.SplitMix64(1).uniform_pm1(prob.n)
