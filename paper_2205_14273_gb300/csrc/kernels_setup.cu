@@ -100,14 +100,30 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
     const int i = fc[0], j = fc[1], k = fc[2];
     const int c = (k * sp.n[1] + j) * sp.n[0] + i;
     double nw = 0, ne = 0, den = 0, diag = 0;
-    for (int e = 0; e < sp.nent; ++e) {
-      if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
-      double a = coef_at(sp, L.coef, e, c);
-      int od = sp.o[e][d];
-      if (od < 0) nw += a;
-      else if (od > 0) ne += a;
-      else den += a;
-      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += a;
+    // entries in batches of IB with predicated loads (in flight together),
+    // summed in entry order as before
+    constexpr int IB = 9;
+    for (int e0 = 0; e0 < sp.nent; e0 += IB) {
+      double av[IB];
+#pragma unroll
+      for (int q = 0; q < IB; ++q) {
+        const int e = e0 + q;
+        const bool ok =
+            e < sp.nent && inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2]);
+        av[q] = ok ? coef_at(sp, L.coef, e, c) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < IB; ++q) {
+        const int e = e0 + q;
+        if (e >= sp.nent) break;
+        if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
+        const double a = av[q];
+        const int od = sp.o[e][d];
+        if (od < 0) nw += a;
+        else if (od > 0) ne += a;
+        else den += a;
+        if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += a;
+      }
     }
     double pw = 0, pe = 0;
     bool ok = fabs(den) > 1e-300 && ((den > 0) == (diag > 0)) && diag != 0.0;
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
 // east coarse neighbours with PW(g), PE(g).  The product accumulates into the
 // coarse entry J - I.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelView<double> C,
+__global__ void __launch_bounds__(NT, 2) k_rap_struct(LevelView<double> F, LevelView<double> C,
                                                    double* __restrict__ ccoef,
                                                    float* __restrict__ ccoef32) {
   __shared__ DPart fp;
@@ -177,21 +193,42 @@ __global__ void __launch_bounds__(NT) k_rap_struct(LevelView<double> F, LevelVie
           w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
         }
         if (w1 == 0.0) continue;
-        for (int e = 0; e < fp.nent; ++e) {
-          int g[3] = {f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]};
-          if (!inside(fp, g[0], g[1], g[2])) continue;
-          double v = w1 * coef_at(fp, F.coef, e, fcell);
-          int t = a + fp.o[e][d];
-          int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
-          if ((t & 1) == 0) {
-            ob[d] = t / 2;
-            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
-          } else {
-            int Gi = fp.poff + fine_point_index(fp, g[0], g[1], g[2]);
-            ob[d] = (t - 1) / 2;
-            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pw[Gi];
-            ob[d] = (t + 1) / 2;
-            acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * F.Pe[Gi];
+        // entries in batches of RB: the batch's coefficient and P-weight loads
+        // are predicated, not branched around, so they are in flight together
+        constexpr int RB = 9;
+        for (int e0 = 0; e0 < fp.nent; e0 += RB) {
+          double cv[RB], pw[RB], pe[RB];
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            const int e = e0 + q;
+            const bool ok = e < fp.nent &&
+                            inside(fp, f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]);
+            const int t = a + (ok ? fp.o[e][d] : 0);
+            const bool odd = ok && (t & 1);
+            const int Gi = odd ? fp.poff + fine_point_index(fp, f[0] + fp.o[e][0],
+                                                            f[1] + fp.o[e][1], f[2] + fp.o[e][2])
+                               : 0;
+            cv[q] = ok ? coef_at(fp, F.coef, e, fcell) : 0.0;
+            pw[q] = odd ? F.Pw[Gi] : 0.0;
+            pe[q] = odd ? F.Pe[Gi] : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            const int e = e0 + q;
+            if (e >= fp.nent) break;
+            if (!inside(fp, f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2])) continue;
+            const double v = w1 * cv[q];
+            const int t = a + fp.o[e][d];
+            int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
+            if ((t & 1) == 0) {
+              ob[d] = t / 2;
+              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
+            } else {
+              ob[d] = (t - 1) / 2;
+              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * pw[q];
+              ob[d] = (t + 1) / 2;
+              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * pe[q];
+            }
           }
         }
       }
