@@ -176,6 +176,15 @@ struct ssamg_solver_s {
 thread_local long long g_ssamg_launches = 0;
 thread_local int g_ssamg_pdl = 0;
 thread_local int g_ssamg_bricks = 1;
+thread_local const PcgScalars* g_ssamg_skip = nullptr;
+
+// While PCG kernels are enqueued: level views carry the problems' scalars,
+// so that the cycle kernels of a stopped problem return at once.
+struct SkipScope {
+  const PcgScalars* old;
+  explicit SkipScope(const PcgScalars* sc) : old(g_ssamg_skip) { g_ssamg_skip = sc; }
+  ~SkipScope() { g_ssamg_skip = old; }
+};
 
 // Enables programmatic dependent launch for the solve kernels an entry point
 // enqueues (when the solver's parameters ask for it), and restores the
@@ -1249,6 +1258,7 @@ void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, c
   Level& L0 = s->lev[0];
   double* zp = s->prm.flexible ? s->zprev : nullptr;
   const PcgCtx c = pcg_ctx(s);
+  SkipScope skip(s->sc);
   launch_pcg_init(L0, s->b, s->x, s->r, c, st);
   vcycle(s, s->r, s->z, st);
   launch_pcg_start(L0, s->r, s->z, s->p, zp, c, st);
@@ -1261,6 +1271,7 @@ void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, c
   double* zp = s->prm.flexible ? s->zprev : nullptr;
   // the cycle's last kernel also forms r.z (and r.zprev) for beta
   const PcgCtx c = pcg_ctx(s);
+  SkipScope skip(s->sc);
   const int npart = vcycle(s, s->r, s->z, st, s->partial, zp);
   if (npart > 0)  // the last relaxation writes partials per cell-tile block
     launch_pcg_beta_from_partials(L0, s->z, s->p, c, c.pb, st);

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* x,
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
     r[g] = b[g] - apply_A_sh<SH>(L, sp, x, c);
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* x,
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
     xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   double s0 = 0.0, s1 = 0.0;
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
@@ -267,6 +270,7 @@ __global__ void __launch_bounds__(NT, 6) k7b_residual(LevelView<T> L, const T* x
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   ResidualOp<T> op{b, r};
   brick7(L, sp, x, op);
 }
@@ -278,6 +282,7 @@ __global__ void __launch_bounds__(NT, 6) k7b_relax(LevelView<T> L, const T* x, c
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   RelaxOp<T> op{b, L.dinv, xo};
   brick7(L, sp, x, op);
 }
@@ -308,6 +313,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   SpmvDotOp op{q, 0.0};
   brick7(L, sp, p, op);
   const double t = block_sum<NT>(op.s, sh);
@@ -326,6 +332,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
   part_of(F.parts, p, fp);
   __syncthreads();
   pdl_wait();
+  if (C.skip && C.skip[cp.prob].done) return;  // problem already stopped
   TILE_LOOP_UNROLLED(cc, cp) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
@@ -395,6 +402,7 @@ __global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* ec,
     pr0 = p_row(fp, F.Pw, F.Pe, i, j, k);
   }
   pdl_wait();
+  if (F.skip && F.skip[fp.prob].done) return;  // problem already stopped
   TILE_LOOP_UNROLLED(c, fp) {
     PRow<T> pr = pr0;
     if (c != cfirst) {

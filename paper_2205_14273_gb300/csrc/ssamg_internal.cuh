@@ -111,6 +111,9 @@ struct PcgScalars {
   double tol, bb, rr, rz, pq, alpha, beta, tol2bb;
   int iter, max_iter, status, flexible, done, pad_;
 };
+// The PCG scalars while a solve's kernels are enqueued (level views carry
+// them, see LevelView::skip), else null (per host thread).
+extern thread_local const PcgScalars* g_ssamg_skip;
 
 // Loop control of a (batched) PCG solve: the ticket of the per-problem final
 // kernel and whether any problem still iterates.
@@ -156,6 +159,9 @@ struct LevelView {
   T* uy;                // dense per-cell (U x)(c) of the vector last passed to a row job; 0 off rows
   int nr;
   int nublk;            // blocks of row jobs (SSAMG_RPB rows each)
+  // inside a PCG solve: the problems' scalars; a block of a problem whose
+  // iteration has stopped leaves its cycle work undone (nothing reads it)
+  const PcgScalars* skip;
 };
 
 // One level of the fused coarse tail: the level's view and its cycle vectors.
@@ -268,13 +274,14 @@ struct Level {
 template <>
 inline LevelView<double> Level::view<double>() const {
   return LevelView<double>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
-                           u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk};
+                           u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk,
+                           g_ssamg_skip};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
   return LevelView<float>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
                           Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, uy32,
-                          nr, nublk};
+                          nr, nublk, g_ssamg_skip};
 }
 
 struct SsamgError {
@@ -299,6 +306,7 @@ extern thread_local int g_ssamg_pdl;
 // Nonzero while the entry point allows brick launches for checked 7-point
 // levels (per host thread, like g_ssamg_pdl).
 extern thread_local int g_ssamg_bricks;
+
 #define SSAMG_LAUNCH_CHECK()       \
   do {                             \
     ++g_ssamg_launches;            \
