@@ -60,6 +60,7 @@ class Params:
     tol: float = 1e-8
     max_iter: int = 200
     coarse_direct: int = 1        # 1: dense Cholesky, 0: one relaxation sweep
+    skip: int = 0                 # 1: the "skip" option of Section 3.4 (see skipped_parts)
 
 
 @dataclass
@@ -563,6 +564,18 @@ def galerkin_unstructured(fine: Level, coarse: Level):
 # Relaxation (Section 3.4)
 # ---------------------------------------------------------------------------
 
+def skipped_parts(dstars, ndim: int, l: int) -> List[bool]:
+    """The "skip" option of Section 3.4: part p does no relaxation at level l
+    when its coarsening direction there equals the one n_d levels above,
+    d*_l = d*_{l - n_d}.  Reading: only actual directions compare (a part
+    left uncoarsened, d* = -1, keeps relaxing), and levels l < n_d always
+    relax."""
+    nparts = len(dstars[l])
+    if l < ndim:
+        return [False] * nparts
+    return [dstars[l][p] >= 0 and dstars[l][p] == dstars[l - ndim][p] for p in range(nparts)]
+
+
 def smoother_inverse(lev: Level, params: Params) -> np.ndarray:
     """The diagonal of omega M^-1 in Eq. relax0.
 
@@ -574,8 +587,11 @@ def smoother_inverse(lev: Level, params: Params) -> np.ndarray:
     l1u = np.zeros(lev.n)
     if params.relax == 1 and len(lev.u_val):
         np.add.at(l1u, lev.u_row, np.abs(lev.u_val))
+    skip = getattr(lev, "skip", None)
     for p in range(lev.nparts):
         dv = lev.part_view(out, p)
+        if skip is not None and skip[p]:
+            continue  # relaxation turned off: omega M^-1 = 0 (x stays 0 / unchanged)
         if params.relax == 0:
             w = params.relax_factor if params.relax_factor > 0 else lev.omega[p]
             dv[...] = w / lev.S[p][(0, 0, 0)]
@@ -628,7 +644,9 @@ def setup(prob, params: Params = Params()) -> Hierarchy:
             coarse.S[p] = galerkin_structured(fine, coarse, p)
         coarse.u_row, coarse.u_col, coarse.u_val, coarse.u_bits = galerkin_unstructured(fine, coarse)
         levels.append(coarse)
-    for lev in levels:
+    for l, lev in enumerate(levels):
+        lev.skip = (skipped_parts(dstars, prob.ndim, l) if params.skip and l < len(dstars)
+                    else [False] * lev.nparts)
         lev.Dinv = smoother_inverse(lev, params)
     h = Hierarchy(levels, params, W0)
     if params.coarse_direct:

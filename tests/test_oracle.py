@@ -451,3 +451,52 @@ def test_adjoint_solve_uses_same_hierarchy():
     lam = O.pcg(h, x - xt, tol=1e-13).x
     A = _dense(prob)
     assert np.linalg.norm(A @ lam - (x - xt)) <= 1e-11 * np.linalg.norm(x - xt)
+
+
+# ---------------------------------------------------------------------------
+# "skip" option (Section 3.4): relaxation off at level l of a part whose
+# coarsening direction equals its direction n_d levels above
+# ---------------------------------------------------------------------------
+def test_skip_isotropic_pattern_closed_form():
+    """Isotropic 3-D: d* cycles x, y, z (ties to the smallest index), so the
+    first n_d = 3 levels relax and every further coarsened level is skipped;
+    the coarsest level (solved directly) is not."""
+    prob = P.laplace7(16)
+    h = O.setup(prob, O.Params(skip=1))
+    L = len(h.levels)
+    assert [lev.dstar[0] for lev in h.levels[:-1]] == [l % 3 for l in range(L - 1)]
+    assert [lev.skip[0] for lev in h.levels] == [l >= 3 and l < L - 1 for l in range(L)]
+
+
+def test_skip_zeroes_only_the_skipped_smoothers():
+    prob = P.multipart_aniso(m=10, layout=(2, 2, 1), seed=1)
+    h0 = O.setup(prob)
+    h1 = O.setup(prob, O.Params(skip=1))
+    nd = prob.ndim
+    assert len(h0.levels) == len(h1.levels)
+    nskip = 0
+    for l, (a, b) in enumerate(zip(h0.levels, h1.levels)):
+        for p in range(a.nparts):
+            for o in a.S[p]:
+                assert np.array_equal(a.S[p][o], b.S[p][o])
+            d0, d1 = a.part_view(a.Dinv, p), b.part_view(b.Dinv, p)
+            if b.skip[p]:
+                nskip += 1
+                assert l >= nd and b.dstar[p] >= 0 and b.dstar[p] == h1.levels[l - nd].dstar[p]
+                assert not d1.any()
+            else:
+                assert np.array_equal(d0, d1)
+    assert nskip > 0
+
+
+def test_skip_preconditioner_is_symmetric_and_converges():
+    prob = P.laplace7(12)
+    h = O.setup(prob, O.Params(skip=1))
+    g = P.SplitMix64(3)
+    r1, r2 = g.uniform_pm1(prob.n), g.uniform_pm1(prob.n)
+    a, b = np.dot(O.vcycle(h, r1), r2), np.dot(r1, O.vcycle(h, r2))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    res = O.pcg(h, prob.b[0], tol=1e-10, max_iter=200)
+    assert res.converged
+    x = np.linalg.solve(_dense(prob), prob.b[0])
+    assert np.abs(res.x - x).max() <= 1e-7 * np.abs(x).max()
