@@ -101,7 +101,10 @@ typedef struct {
   int precision;       /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 PCG */
   int relax;           /* 0: weighted Jacobi (Eq. relax1); 1: L1 Jacobi (Section 3.4) */
   double relax_factor; /* <= 0: omega_p of Eq. relax1 (relax 0) or 3/2 (relax 1) */
-  int skip;            /* reserved (Section 3.4 "skip"); must be 0 */
+  int skip;            /* 1: Section 3.4 "skip": no relaxation on a part at level l >= n_d whose
+                          coarsening direction equals its direction n_d levels above (read
+                          literally: only actual directions compare; the coarsest level is
+                          solved directly); 0 (default): relax on every level */
   int max_levels;      /* l_max of Section 3.1 (default 64) */
   long long s_max;     /* coarsening stops at total size <= s_max; <= 0: number of parts */
   double tol;          /* PCG stop: ||r||_2 <= tol ||b||_2 (default 1e-8) */

@@ -579,7 +579,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
   if (!prm || !out) return SSAMG_ERR_ARG;
   if (prm->precision < 0 || prm->precision > 1 || prm->relax < 0 || prm->relax > 1 ||
-      prm->skip != 0 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
+      prm->skip < 0 || prm->skip > 1 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
     return SSAMG_ERR_ARG;
   auto* s = new (std::nothrow) ssamg_solver_s;
   if (!s) return SSAMG_ERR_OOM;
@@ -630,6 +630,7 @@ void fill_dpart(DPart& dp, const PartH& h) {
   dp.par = h.par;
   dp.omega = h.omega;
   dp.has_u = h.has_u;
+  dp.skip = h.skip;
   dp.dx = make_fastdiv(h.n[0]);
   dp.dxy = make_fastdiv(h.n[0] * h.n[1]);
   std::memset(dp.slot, -1, sizeof(dp.slot));
@@ -906,6 +907,13 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     s->lev.push_back(std::move(C));
   }
   const int Lc = (int)s->lev.size() - 1;
+  // "skip" (Section 3.4): no relaxation on a part at level l >= n_d whose
+  // coarsening direction equals the one n_d levels above (actual directions)
+  for (int l = 0; l <= Lc; ++l)
+    for (int p = 0; p < np; ++p) {
+      PartH& h = s->lev[l].parts[p];
+      h.skip = s->prm.skip && l >= ndim && h.dstar >= 0 && h.dstar == s->lev[l - ndim].parts[p].dstar;
+    }
 
   // ---- allocation (one arena walk; identical sizes reuse the same memory)
   for (int l = 0; l <= Lc; ++l) {

@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, dou
       double w = factor > 0.0 ? factor : 1.5;
       v = w / s;
     }
+    if (sp.skip) v = 0.0;  // relaxation turned off: omega M^-1 = 0
     dinv[sp.off + c] = v;
     if (dinv32) dinv32[sp.off + c] = (float)v;
   }

@@ -93,6 +93,7 @@ struct DPart {
   unsigned varmask;            // bit e: entry e is per cell
   int zeroext;                 // per-cell entries are exactly zero where c + o leaves the box
   int prob;                    // problem of the part (a batch of independent problems)
+  int skip;                    // relaxation turned off at this level (Section 3.4 "skip")
   int bblk0;                   // first block of brick launches over this level
   int bb[3];                   // bricks along x, y, z (SSAMG_BRICK_X x _Y x _Z cells each)
   FastDiv dx, dxy;             // divide by n[0], n[0]*n[1]
@@ -209,6 +210,7 @@ struct PartH {
   long long nfine;
   int poff;
   int has_u;
+  int skip;  // relaxation turned off on this part at this level (Section 3.4 "skip")
 };
 
 struct Arena {

@@ -411,3 +411,23 @@ def test_brick_applies_match_cell_tiles(S, prob, prec):
     assert np.array_equal(zs[0], zs[1])
     assert abs(runs[0][0] - runs[1][0]) <= 1
     assert rel(runs[1][1], runs[0][1]) <= 1e-9
+
+
+@pytest.mark.parametrize("prob", [CASES[i] for i in (0, 13, 20)] + [P.laplace7(16)],
+                         ids=[CIDS[i] for i in (0, 13, 20)] + ["laplace7 16^3"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_skip_option_matches_oracle(S, prob, prec):
+    """Section 3.4 "skip": the hierarchy (skipped parts' smoothers zero), one
+    V-cycle and the PCG iteration count against the oracle with skip on."""
+    h = O.setup(prob, O.Params(skip=1))
+    _, _, sv = gpu_setup(S, prob, skip=1, precision=prec, flexible=prec)
+    if prec == 0:
+        compare_hierarchy(S, prob, sv, h)
+    r = P.SplitMix64(43).uniform_pm1(prob.n)
+    z = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    sv.precondition(torch.as_tensor(r, device="cuda"), z)
+    assert rel(z.cpu().numpy(), O.vcycle(h, r)) <= (OP_TOL if prec == 0 else 5e-5)
+    ref = O.pcg(h, prob.b[0], tol=1e-8)
+    x = torch.zeros_like(z)
+    st = sv.solve(torch.as_tensor(prob.b[0], device="cuda"), x)
+    assert abs(st.iterations - ref.iterations) <= 1, (st.iterations, ref.iterations)
