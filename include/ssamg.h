@@ -258,8 +258,9 @@ void ssamg_batch_destroy(ssamg_batch B);
 
 /* Blocks whose partial sums fit the static scratch of
  * ssamg_coupling_sums_noalloc: 3 doubles each, 1.5 MiB of device memory.
- * A level launch covers 1024 cells per block when the level has 300,000
- * cells or more (256 below), so levels of up to 67,108,864 cells fit. */
+ * Under the built-in tile rule a level launch covers 1024 cells per block
+ * when the level has 300,000 cells or more (256 below), so levels of up to
+ * 67,108,864 cells fit (fewer under a tile table of fewer cells per thread). */
 #define SSAMG_NOALLOC_MAX_BLOCKS 65536
 
 /* Allocation-free form of the per-part coupling sums c of Section 3.1
@@ -291,13 +292,61 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * (with U x), 5 whole V-cycle (level ignored), 6 the PCG's FP64 level-0
  * operator apply with its dot product (level ignored), 7 one whole PCG
  * iteration, 8 the PCG's vector steps (beta, search direction, alpha, x and
- * r updates), 9 the FP32 cycle's last post-relaxation as the PCG runs it
+ * r updates), 9 the cycle's last post-relaxation as the PCG runs it
  * (FP64 z out, r.z partials).  Ids 7 and 8 clear the solve's convergence state, so that the
  * replayed iterations never stop; the next solve starts afresh.  The kernels work on
  * the solver's own buffers (their contents are overwritten).  Synchronises
  * `stream`. */
 int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* us_per_launch,
                       void* stream);
+
+/* ---------------------------------------------------------- tile forms ---
+ * The paper has no counterpart: this is how the kernels map threads to cells.
+ * Every per-level launch covers the level's cells in one tile form, chosen
+ * per level from its cell count n (summed over parts):
+ *   k cells per thread (k = 1 .. 4): blocks of 256 threads over 256 k
+ *     consecutive cells of one part, a thread's cells 256 apart;
+ *   bricks (on levels whose operator is the 7-point stencil with constant
+ *     entries per part, use_bricks set): the residual, relaxation and PCG
+ *     operator applies run over 32 x 8 x 8 bricks, each thread marching a
+ *     column along z; the other kernels keep the cell tiles.
+ * The tile table has one entry per size class c = floor(log2(max(n, 1))),
+ * c = 0 .. SSAMG_TILE_CLASSES - 1: 0 selects the built-in rule (4 cells per
+ * thread from 300,000 cells up, 1 below; bricks where the level allows
+ * them), k alone selects k cells per thread without bricks, and
+ * k | SSAMG_TILE_BRICKS k cells per thread with bricks allowed.  A tile form
+ * decides only which thread computes which cell: every cycle result is the
+ * same bit for bit under any table; the PCG's dot products, summed per
+ * block, round differently. */
+#define SSAMG_TILE_CLASSES 32
+#define SSAMG_TILE_BRICKS 8
+
+/* Sets the solver's tile table from table[SSAMG_TILE_CLASSES] (copied), or
+ * clears it to the built-in rule (table NULL).  It applies from the next
+ * ssamg_setup.  SSAMG_ERR_ARG (table unchanged) on an entry that is not 0,
+ * k or k | SSAMG_TILE_BRICKS with 1 <= k <= 4.  Host only. */
+int ssamg_set_tile_table(ssamg_solver s, const int* table);
+/* Copies the solver's tile table into table[SSAMG_TILE_CLASSES].  Host only. */
+int ssamg_get_tile_table(ssamg_solver s, int* table);
+/* The tile form level `level` of the set-up hierarchy runs with: cells per
+ * thread, and 1 in *bricks when its operator applies run over bricks.
+ * Host only. */
+int ssamg_level_tile(ssamg_solver s, int level, int* cells_per_thread, int* bricks);
+/* Tile autotuner: a grid search over the forms {1, 2, 4} cells per thread,
+ * each with and without bricks.  For each form, applied to every level, it
+ * sets the hierarchy up again from the matrix of the last ssamg_setup and
+ * times per level (as ssamg_time_kernel does, `reps` launches per kernel)
+ * the kernels whose tiles follow that level's form: residual,
+ * post-relaxation and prolongation on the level, restriction onto it, and
+ * on level 0 the PCG's operator apply and vector steps.  Per size class it
+ * keeps the fastest form on the class's largest level when that saves at
+ * least 3% against the built-in rule (else 0), stores the table in the
+ * solver, sets the hierarchy up once more with it, and copies it to table
+ * (SSAMG_TILE_CLASSES ints, or NULL).  Requires a set-up solver; runs on
+ * `stream` and synchronises it; the eight set-ups reuse the solver's device
+ * memory.  On an error the solver keeps its previous table and must be set
+ * up again before the next solve. */
+int ssamg_autotune(ssamg_solver s, int reps, void* stream, int* table);
 
 /* Host-only check of the run-time division constants the kernels use to
  * split a linear cell index into (i, j, k): compares against plain division

@@ -160,6 +160,7 @@ struct ssamg_solver_s {
   int hist_cap = 0;               // right-hand sides the history holds
   int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
+  int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
   ~ssamg_solver_s() {
@@ -669,13 +670,34 @@ void* padded_vector(ssamg_solver s, size_t w, long long n, long long guard, cuda
   return base + w * guard;
 }
 
+// Size class of a level of n cells in the tile table: floor(log2(max(n, 1))).
+int tile_class(long long n) {
+  int c = 0;
+  while (c < SSAMG_TILE_CLASSES - 1 && (2ll << c) <= n) ++c;
+  return c;
+}
+
+long long level_cells(const Level& L) {
+  long long n = 0;
+  for (const PartH& h : L.parts) n += h.ncell;
+  return n;
+}
+
+bool valid_tile(int t) {
+  const int k = t & ~SSAMG_TILE_BRICKS;
+  return t == 0 || (k >= 1 && k <= SSAMG_CPT_LARGE);
+}
+
 void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) {
   const int np = L.np;
   L.dparts.assign(np, DPart{});
   std::vector<int> blk(np + 1, 0), fblk(np + 1, 0), cs(np + 1, 0);
-  long long ntot = 0;
-  for (int p = 0; p < np; ++p) ntot += L.parts[p].ncell;
-  L.cpt = ntot >= SSAMG_CPT_MIN_CELLS ? SSAMG_CPT_LARGE : 1;
+  const long long ntot = level_cells(L);
+  // tile form: the table's entry for the level's size class, else the
+  // built-in rule (SSAMG_CPT_LARGE cells per thread on large levels)
+  const int te = s->tiles[tile_class(ntot)];
+  L.cpt = te ? (te & ~SSAMG_TILE_BRICKS) : ntot >= SSAMG_CPT_MIN_CELLS ? SSAMG_CPT_LARGE : 1;
+  L.bricks = te ? (te & SSAMG_TILE_BRICKS) != 0 : 1;
   const long long tile = (long long)L.cpt * SSAMG_BLOCK;
   for (int p = 0; p < np; ++p) {
     const PartH& h = L.parts[p];
@@ -1511,15 +1533,19 @@ int run_pcg(ssamg_solver s, cudaStream_t st, ssamg_stats* stats) {
 
 }  // namespace
 
+void run_setup(ssamg_solver s, cudaStream_t st) {
+  noalloc_scratch();
+  const long long c0 = g_ssamg_launches;
+  build_hierarchy(s, st);
+  s->setup_launches = g_ssamg_launches - c0;
+}
+
 extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
   if (!s || !A) return SSAMG_ERR_ARG;
   if (!A->assembled) return SSAMG_ERR_STATE;
   API_BEGIN
   s->A = A;
-  noalloc_scratch();
-  const long long c0 = g_ssamg_launches;
-  build_hierarchy(s, (cudaStream_t)stream);
-  s->setup_launches = g_ssamg_launches - c0;
+  run_setup(s, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
 }
@@ -1873,15 +1899,10 @@ extern "C" int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_
 
 // Times one hot-path kernel: `reps` launches captured into a CUDA graph,
 // replayed once to warm up and once between events on `stream`.
-extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps,
-                                 double* us_per_launch, void* stream) {
-  if (!s || !us_per_launch || reps < 1) return SSAMG_ERR_ARG;
-  if (!s->ready) return SSAMG_ERR_STATE;
-  const int Lc = (int)s->lev.size() - 1;
-  if (level < 0 || level > Lc || ((kernel == 3 || kernel == 4) && level >= Lc)) return SSAMG_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  API_BEGIN
-  PdlScope pdl(s->prm);
+// Mean microseconds per launch of `reps` launches of one kernel, captured
+// into a graph and replayed (after one warm-up replay) between events on st.
+// The caller has checked the arguments and set the launch scope.
+double time_kernel_us(ssamg_solver s, int kernel, int level, int reps, cudaStream_t st) {
   if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
   Level& L = s->lev[level];
   const bool f = s->prm.precision == 1;
@@ -1922,7 +1943,9 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
                                     (const float*)s->lev[0].b, s->z, s->r, s->prm.flexible ? s->zprev : nullptr,
                                     s->partial, cs);
         else
-          throw SsamgError{SSAMG_ERR_ARG, "kernel 9 times the FP32 cycle's last relaxation"};
+          launch_relax_final<double>(s->lev[0], (const double*)s->lev[0].r,
+                                     (const double*)s->lev[0].b, s->z, s->r,
+                                     s->prm.flexible ? s->zprev : nullptr, s->partial, cs);
         break;
       case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
         launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), s->pb, cs);
@@ -1966,7 +1989,124 @@ extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaGraphExecDestroy(ge);
-  *us_per_launch = 1e3 * ms / reps;
+  return 1e3 * ms / reps;
+}
+
+extern "C" int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps,
+                                 double* us_per_launch, void* stream) {
+  if (!s || !us_per_launch || reps < 1) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  const int Lc = (int)s->lev.size() - 1;
+  if (level < 0 || level > Lc || ((kernel == 3 || kernel == 4) && level >= Lc)) return SSAMG_ERR_ARG;
+  API_BEGIN
+  PdlScope pdl(s->prm);
+  *us_per_launch = time_kernel_us(s, kernel, level, reps, (cudaStream_t)stream);
+  return SSAMG_OK;
+  API_END
+}
+
+// ------------------------------------------------------------- tile tuning
+
+extern "C" int ssamg_set_tile_table(ssamg_solver s, const int* table) {
+  if (!s) return SSAMG_ERR_ARG;
+  if (table)
+    for (int c = 0; c < SSAMG_TILE_CLASSES; ++c)
+      if (!valid_tile(table[c])) return SSAMG_ERR_ARG;
+  for (int c = 0; c < SSAMG_TILE_CLASSES; ++c) s->tiles[c] = table ? table[c] : 0;
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_get_tile_table(ssamg_solver s, int* table) {
+  if (!s || !table) return SSAMG_ERR_ARG;
+  std::copy(s->tiles, s->tiles + SSAMG_TILE_CLASSES, table);
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_level_tile(ssamg_solver s, int level, int* cells_per_thread, int* bricks) {
+  if (!s || !cells_per_thread || !bricks) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  if (level < 0 || level >= (int)s->lev.size()) return SSAMG_ERR_ARG;
+  PdlScope pdl(s->prm);
+  *cells_per_thread = s->lev[level].cpt;
+  *bricks = uses_bricks(s->lev[level]) ? 1 : 0;
+  return SSAMG_OK;
+}
+
+// Time (us) of the kernels whose tiles follow level l's tile form, as one
+// PCG iteration runs them: the residual, post-relaxation and prolongation on
+// l, the restriction onto l, and on level 0 the PCG's operator apply and
+// vector steps (the pre-relaxation from zero runs on flat element tiles).
+double level_tile_cost(ssamg_solver s, int l, int reps, cudaStream_t st) {
+  const int Lc = (int)s->lev.size() - 1;
+  double t = 0.0;
+  if (l < Lc) {
+    t += time_kernel_us(s, 0, l, reps, st);
+    t += time_kernel_us(s, l == 0 ? 9 : 1, l, reps, st);
+    t += time_kernel_us(s, 4, l, reps, st);
+  }
+  if (l > 0) t += time_kernel_us(s, 3, l - 1, reps, st);
+  if (l == 0) {
+    t += time_kernel_us(s, 6, 0, reps, st);
+    t += time_kernel_us(s, 8, 0, reps, st);
+  }
+  return t;
+}
+
+extern "C" int ssamg_autotune(ssamg_solver s, int reps, void* stream, int* table) {
+  if (!s || reps < 1) return SSAMG_ERR_ARG;
+  if (!s->ready || !s->A) return SSAMG_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int saved[SSAMG_TILE_CLASSES];
+  std::copy(s->tiles, s->tiles + SSAMG_TILE_CLASSES, saved);
+  API_BEGIN
+  // on an error the solver keeps the table it had (and needs a new set-up)
+  struct Restore {
+    ssamg_solver s;
+    const int* saved;
+    bool keep = false;
+    ~Restore() {
+      if (!keep) std::copy(saved, saved + SSAMG_TILE_CLASSES, s->tiles);
+    }
+  } restore{s, saved};
+  PdlScope pdl(s->prm);
+  const int B = SSAMG_TILE_BRICKS;
+  static const int cand[] = {1, 2, 4, 1 | B, 2 | B, 4 | B};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  const int nl = (int)s->lev.size();
+  std::vector<int> cls(nl);
+  for (int l = 0; l < nl; ++l) cls[l] = tile_class(level_cells(s->lev[l]));
+  std::vector<double> def(nl, HUGE_VAL), cost((size_t)nl * nc, HUGE_VAL);
+  // the built-in rule everywhere (the reference point), then each form
+  // everywhere; the hierarchy itself does not depend on the tiles
+  for (int k = -1; k < nc; ++k) {
+    for (int c = 0; c < SSAMG_TILE_CLASSES; ++c) s->tiles[c] = k < 0 ? 0 : cand[k];
+    run_setup(s, st);
+    if ((int)s->lev.size() != nl) throw SsamgError{SSAMG_ERR_STATE, "hierarchy depth changed"};
+    for (int l = 0; l < nl; ++l) {
+      // a brick form on a level that cannot use bricks is its cell form
+      if (k >= 0 && (cand[k] & B) && !uses_bricks(s->lev[l])) continue;
+      const double t = level_tile_cost(s, l, reps, st);
+      if (k < 0) def[l] = t;
+      else cost[(size_t)l * nc + k] = t;
+    }
+  }
+  // per size class, the form of least time on the class's largest level,
+  // kept only when it beats the built-in rule by SSAMG_TUNE_MARGIN
+  int out[SSAMG_TILE_CLASSES] = {};
+  std::vector<char> seen(SSAMG_TILE_CLASSES, 0);
+  for (int l = 0; l < nl; ++l) {
+    if (seen[cls[l]]) continue;
+    seen[cls[l]] = 1;
+    int best = -1;
+    double bt = def[l];
+    for (int k = 0; k < nc; ++k)
+      if (cost[(size_t)l * nc + k] < bt) bt = cost[(size_t)l * nc + (best = k)];
+    if (best >= 0 && bt < SSAMG_TUNE_MARGIN * def[l]) out[cls[l]] = cand[best];
+  }
+  std::copy(out, out + SSAMG_TILE_CLASSES, s->tiles);
+  run_setup(s, st);
+  restore.keep = true;
+  if (table) std::copy(out, out + SSAMG_TILE_CLASSES, table);
   return SSAMG_OK;
   API_END
 }

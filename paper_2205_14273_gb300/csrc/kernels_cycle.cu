@@ -1130,7 +1130,9 @@ void launch_k(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t
 }
 }  // namespace
 
-bool uses_bricks(const Level& L) { return g_ssamg_bricks && L.shape == SH_K7 && L.nbblk > 0; }
+bool uses_bricks(const Level& L) {
+  return g_ssamg_bricks && L.bricks && L.shape == SH_K7 && L.nbblk > 0;
+}
 
 // Level-0 block ranges of the problems for the partials that L's operator
 // apply launches write (brick or cell-tile blocks).

@@ -26,6 +26,7 @@
 #define SSAMG_BLOCK 256
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
+#define SSAMG_TUNE_MARGIN 0.97    // a tuned tile form must save 3% of a level's time
 #define SSAMG_EW 4                 // cells per thread of the elementwise pre-relaxation
 // Bricks of the checked 7-point operator applies: SSAMG_BRICK_X x _Y threads
 // (one column each), marching SSAMG_BRICK_Z cells along z.
@@ -235,6 +236,7 @@ struct Level {
   int* d_cellstart = nullptr;
   int nblk = 0, nfblk = 0, nbblk = 0;
   int cpt = 1;
+  int bricks = 1; // 0: the tile table keeps this level's operator applies on cell tiles
   int shape = 0;  // StencilShape of the level's operator apply
   std::vector<int> hblk;  // host copy of the block starts of cell-wise launches
   std::vector<int> hbblk; // and of brick launches

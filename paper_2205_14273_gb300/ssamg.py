@@ -9,6 +9,7 @@ fallback.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import re
 from typing import Optional, Sequence
@@ -28,6 +29,9 @@ ERR_CUDA = -4
 ERR_BREAKDOWN = -5
 ERR_TIMEOUT = -6
 ERR_UNSUPPORTED = -7
+
+TILE_CLASSES = 32   # entries of a tile table (level size classes floor(log2 n))
+TILE_BRICKS = 8     # tile table bit: bricks allowed on the level
 
 
 class SsamgError(RuntimeError):
@@ -111,6 +115,10 @@ _SIGS = {
     "ssamg_level_stored_coefficients": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
+    "ssamg_set_tile_table": (_i, [_vp, _ip]),
+    "ssamg_get_tile_table": (_i, [_vp, _ip]),
+    "ssamg_level_tile": (_i, [_vp, _i, _ip, _ip]),
+    "ssamg_autotune": (_i, [_vp, _i, _vp, _ip]),
 }
 
 
@@ -388,6 +396,61 @@ class Solver:
                                        _stream(stream)), "time_kernel")
         return us.value
 
+    # ---- tile forms (the tile table and its autotuner)
+    def set_tile_table(self, table=None):
+        """Tile table by level size class (TILE_CLASSES entries: 0, k or
+        k | TILE_BRICKS, 1 <= k <= 4), or None for the built-in rule; it
+        applies from the next setup."""
+        _check(lib().ssamg_set_tile_table(self.h, None if table is None else _ints(table)),
+               "set_tile_table")
+
+    def tile_table(self) -> list:
+        t = (ctypes.c_int * TILE_CLASSES)()
+        _check(lib().ssamg_get_tile_table(self.h, t), "get_tile_table")
+        return list(t)
+
+    def level_tile(self, level: int):
+        """(cells per thread, bricks) of a set-up level."""
+        k, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ssamg_level_tile(self.h, level, ctypes.byref(k), ctypes.byref(b)),
+               "level_tile")
+        return k.value, b.value
+
+    def tile_key(self) -> str:
+        """Cache key of a tuned tile table: the device, the cycle precision
+        and the set-up hierarchy's level sizes."""
+        import torch
+        dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+        sizes = ",".join(str(self.level_sizes(l)[0]) for l in range(self.num_levels()))
+        return f"{dev}|p{self.params.precision}|b{self.params.use_bricks}|{sizes}"
+
+    def autotune(self, reps: int = 30, stream=None, cache: Optional[str] = None,
+                 resetup=None) -> list:
+        """Tile autotuner (ssamg_autotune) on the set-up hierarchy; returns
+        the table, which the solver keeps.  With `cache` (a JSON file), a
+        table stored under tile_key() is taken instead of searching (the
+        hierarchy is set up again with it, by `resetup` or setup() on the
+        last matrix), and a searched table is stored."""
+        key = self.tile_key()
+        data = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                data = json.load(f)
+            if key in data:
+                self.set_tile_table(data[key])
+                (resetup or (lambda: self.setup(self.matrix, stream)))()
+                return list(data[key])
+        t = (ctypes.c_int * TILE_CLASSES)()
+        _check(lib().ssamg_autotune(self.h, reps, _stream(stream), t), "autotune")
+        table = list(t)
+        if cache:
+            data[key] = table
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return table
+
     def spacings(self, nparts: int):
         c = np.zeros(3 * nparts)
         W = np.zeros(3 * nparts)
@@ -439,6 +502,10 @@ class Batch:
         rc = lib().ssamg_batch_solve(self.h, _dptr(b), _dptr(x), nrhs, _stream(stream), st)
         _check(rc, "batch_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return [[st[j * self.nprob + k] for k in range(self.nprob)] for j in range(nrhs)]
+
+    def autotune(self, reps: int = 30, stream=None, cache: Optional[str] = None) -> list:
+        """Tile autotuner on the batch's hierarchy (see Solver.autotune)."""
+        return self.solver().autotune(reps, stream, cache, resetup=lambda: self.setup(stream))
 
     def solver(self) -> "Solver":
         """The batch's solver (a view owned by the batch) for introspection

@@ -102,3 +102,33 @@ def test_solver_state_errors(ssamg_lib):
     L.ssamg_solver_destroy(h)
     L.ssamg_matrix_destroy(A)
     L.ssamg_grid_destroy(g)
+
+
+def test_tile_table_validation(ssamg_lib):
+    """The tile table is host state: valid tables round-trip, an invalid
+    entry is rejected and leaves the table as it was, NULL restores the
+    built-in rule, and the calls that need a hierarchy refuse before setup."""
+    S = ssamg_lib
+    L = S.lib()
+    p = S.default_params()
+    h = ctypes.c_void_p()
+    assert L.ssamg_solver_create(ctypes.byref(p), ctypes.byref(h)) == 0
+    n = S.TILE_CLASSES
+    got = (ctypes.c_int * n)()
+    assert L.ssamg_get_tile_table(h, got) == 0 and list(got) == [0] * n
+    table = [(c % 4 + 1) | (S.TILE_BRICKS if c % 3 == 0 else 0) if c % 5 else 0 for c in range(n)]
+    assert L.ssamg_set_tile_table(h, S._ints(table)) == 0
+    assert L.ssamg_get_tile_table(h, got) == 0 and list(got) == table
+    for bad in (5, -1, S.TILE_BRICKS, S.TILE_BRICKS | 5, 16, 1 | 16):
+        t2 = list(table)
+        t2[7] = bad
+        assert L.ssamg_set_tile_table(h, S._ints(t2)) == S.ERR_ARG, bad
+        assert L.ssamg_get_tile_table(h, got) == 0 and list(got) == table
+    assert L.ssamg_set_tile_table(h, None) == 0
+    assert L.ssamg_get_tile_table(h, got) == 0 and list(got) == [0] * n
+    k, b = ctypes.c_int(), ctypes.c_int()
+    assert L.ssamg_level_tile(h, 0, ctypes.byref(k), ctypes.byref(b)) == S.ERR_STATE
+    assert L.ssamg_autotune(h, 10, None, got) == S.ERR_STATE
+    assert L.ssamg_autotune(h, 0, None, got) == S.ERR_ARG
+    assert L.ssamg_get_tile_table(None, got) == S.ERR_ARG
+    L.ssamg_solver_destroy(h)
