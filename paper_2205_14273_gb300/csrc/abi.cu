@@ -761,6 +761,9 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
           if (dp.o[e][d] != c7[e][d]) canon7 = false;
     }
     L.shape = !unchecked ? (canon7 ? 5 : 0) : all27 ? 3 : all7 ? 1 : all15 ? 2 : 4;
+    L.kvar = 0;
+    for (const DPart& dp : L.dparts)
+      L.kvar = std::max(L.kvar, dp.varmask == 0 ? 0 : dp.varmask == 1u ? 1 : 2);
   }
   SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
 // terms are summed in the order of stencil7_canon_checked, so a cell's A x is
 // bitwise that of the cell-tile kernels.
 // ---------------------------------------------------------------------------
-template <class T, class Op>
+template <class T, int KM, class Op>
 __device__ __forceinline__ void brick7(const LevelView<T>& L, const DPart& sp, const T* x,
                                        Op& op) {
   const int bl = (int)blockIdx.x - sp.bblk0;
@@ -190,21 +190,31 @@ __device__ __forceinline__ void brick7(const LevelView<T>& L, const DPart& sp, c
   int c = (k0 * ny + j) * nx + i;
   T xm = k0 > 0 ? xp0[c - nxy] : (T)0;
   T xcur = xp0[c];
+  T xz = k0 + 1 < nz ? xp0[c + nxy] : (T)0;
+  auto in = op.load(sp.off + c);
+  // KM 0: all entries constant; 1: only the diagonal may vary per cell; 2: any
+  const bool dvar = KM >= 1 && (vm & 1u);
+  T d0 = dvar ? L.coef[sp.coef[0] + c] : c0;
 #pragma unroll 1
   for (int k = k0; k < kend; ++k, c += nxy) {
-    const auto in = op.load(sp.off + c);
-    const T xz = k + 1 < nz ? xp0[c + nxy] : (T)0;
+    // the next cell's streamed inputs (x two planes up, the epilogue's
+    // inputs) are requested before this cell's arithmetic, so that two
+    // cells' DRAM loads are in flight per thread
+    const bool more = k + 1 < kend;
+    const T xz2 = more && k + 2 < nz ? xp0[c + 2 * nxy] : (T)0;
+    const auto in2 = more ? op.load(sp.off + c + nxy) : in;
+    const T d2 = dvar && more ? L.coef[sp.coef[0] + c + nxy] : d0;
     const T xw = bw ? xp0[c - 1] : (T)0;
     const T xe = be ? xp0[c + 1] : (T)0;
     const T xs = bs ? xp0[c - nx] : (T)0;
     const T xn = bn ? xp0[c + nx] : (T)0;
-    const T a0 = (vm & 1u) ? L.coef[sp.coef[0] + c] : c0;
-    const T a1 = (vm & 2u) ? L.coef[sp.coef[1] + c] : c1;
-    const T a2 = (vm & 4u) ? L.coef[sp.coef[2] + c] : c2;
-    const T a3 = (vm & 8u) ? L.coef[sp.coef[3] + c] : c3;
-    const T a4 = (vm & 16u) ? L.coef[sp.coef[4] + c] : c4;
-    const T a5 = (vm & 32u) ? L.coef[sp.coef[5] + c] : c5;
-    const T a6 = (vm & 64u) ? L.coef[sp.coef[6] + c] : c6;
+    const T a0 = d0;
+    const T a1 = (KM == 2 && (vm & 2u)) ? L.coef[sp.coef[1] + c] : c1;
+    const T a2 = (KM == 2 && (vm & 4u)) ? L.coef[sp.coef[2] + c] : c2;
+    const T a3 = (KM == 2 && (vm & 8u)) ? L.coef[sp.coef[3] + c] : c3;
+    const T a4 = (KM == 2 && (vm & 16u)) ? L.coef[sp.coef[4] + c] : c4;
+    const T a5 = (KM == 2 && (vm & 32u)) ? L.coef[sp.coef[5] + c] : c5;
+    const T a6 = (KM == 2 && (vm & 64u)) ? L.coef[sp.coef[6] + c] : c6;
     T acc = (T)0;
     acc = fma(a0, xcur, acc);
     acc = fma(a1, xw, acc);
@@ -217,7 +227,23 @@ __device__ __forceinline__ void brick7(const LevelView<T>& L, const DPart& sp, c
     op.apply(sp.off + c, acc, xcur, in);
     xm = xcur;
     xcur = xz;
+    xz = xz2;
+    in = in2;
+    d0 = d2;
   }
+}
+
+// The instance of a brick kernel for a level's coefficient mode (Level::kvar).
+template <class F>
+F pick_km(int km, F f0, F f1, F f2) {
+  return km == 0 ? f0 : km == 1 ? f1 : f2;
+}
+
+// Resident blocks per SM the brick residual and relaxation are compiled for:
+// as many as fit without register spills.
+template <class T, int KM>
+constexpr int brick_min_blocks() {
+  return sizeof(T) == 8 ? (KM == 2 ? 4 : 5) : (KM == 2 ? 5 : 6);
 }
 
 template <class T>
@@ -263,8 +289,8 @@ struct SpmvDotOp {
   }
 };
 
-template <class T>
-__global__ void __launch_bounds__(NT, 6) k7b_residual(LevelView<T> L, const T* x, const T* b, T* r) {
+template <class T, int KM>
+__global__ void __launch_bounds__(NT, brick_min_blocks<T, KM>()) k7b_residual(LevelView<T> L, const T* x, const T* b, T* r) {
   pdl_trigger();
   __shared__ DPart sp;
   block_part(L.bblk, L.parts, L.np, sp);
@@ -272,11 +298,11 @@ __global__ void __launch_bounds__(NT, 6) k7b_residual(LevelView<T> L, const T* x
   pdl_wait();
   if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   ResidualOp<T> op{b, r};
-  brick7(L, sp, x, op);
+  brick7<T, KM>(L, sp, x, op);
 }
 
-template <class T>
-__global__ void __launch_bounds__(NT, 6) k7b_relax(LevelView<T> L, const T* x, const T* b, T* xo) {
+template <class T, int KM>
+__global__ void __launch_bounds__(NT, brick_min_blocks<T, KM>()) k7b_relax(LevelView<T> L, const T* x, const T* b, T* xo) {
   pdl_trigger();
   __shared__ DPart sp;
   block_part(L.bblk, L.parts, L.np, sp);
@@ -284,9 +310,10 @@ __global__ void __launch_bounds__(NT, 6) k7b_relax(LevelView<T> L, const T* x, c
   pdl_wait();
   if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   RelaxOp<T> op{b, L.dinv, xo};
-  brick7(L, sp, x, op);
+  brick7<T, KM>(L, sp, x, op);
 }
 
+template <int KM>
 __global__ void __launch_bounds__(NT, 4) k7b_pcg_init(LevelView<double> L, const double* b,
                                                    const double* x, double* r, double* partial) {
   pdl_trigger();
@@ -296,7 +323,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_pcg_init(LevelView<double> L, const
   __syncthreads();
   pdl_wait();
   PcgInitOp op{b, r, 0.0, 0.0};
-  brick7(L, sp, x, op);
+  brick7<double, KM>(L, sp, x, op);
   const double s0 = block_sum<NT>(op.bb, sh);
   const double s1 = block_sum<NT>(op.rr, sh);
   if (threadIdx.x == 0) {
@@ -305,6 +332,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_pcg_init(LevelView<double> L, const
   }
 }
 
+template <int KM>
 __global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const double* p, double* q,
                                                    double* partial) {
   pdl_trigger();
@@ -315,7 +343,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const
   pdl_wait();
   if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   SpmvDotOp op{q, 0.0};
-  brick7(L, sp, p, op);
+  brick7<double, KM>(L, sp, p, op);
   const double t = block_sum<NT>(op.s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
@@ -1193,7 +1221,8 @@ void launch_uy(const Level& L, const T* x, cudaStream_t st) {
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st) {
   if (uses_bricks(L))
-    launch_k(k7b_residual<T>, L.nbblk, NT, 0, st, L.view<T>(), x, b, r);
+    launch_k(pick_km(L.kvar, k7b_residual<T, 0>, k7b_residual<T, 1>, k7b_residual<T, 2>), L.nbblk, NT, 0,
+             st, L.view<T>(), x, b, r);
   else
     SH_DISPATCH(L.shape, (launch_k(k_residual<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, r)));
   SSAMG_LAUNCH_CHECK();
@@ -1201,7 +1230,8 @@ void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t 
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st) {
   if (uses_bricks(L))
-    launch_k(k7b_relax<T>, L.nbblk, NT, 0, st, L.view<T>(), x, b, xo);
+    launch_k(pick_km(L.kvar, k7b_relax<T, 0>, k7b_relax<T, 1>, k7b_relax<T, 2>), L.nbblk, NT, 0,
+             st, L.view<T>(), x, b, xo);
   else
     SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, xo)));
   SSAMG_LAUNCH_CHECK();
@@ -1323,7 +1353,8 @@ void launch_pcg_init(const Level& L, const double* b, const double* x, double* r
                      const PcgCtx& c, cudaStream_t st) {
   launch_uy<double>(L, x, st);
   if (uses_bricks(L))
-    launch_k(k7b_pcg_init, L.nbblk, NT, 0, st, L.view<double>(), b, x, r, c.partial);
+    launch_k(pick_km(L.kvar, k7b_pcg_init<0>, k7b_pcg_init<1>, k7b_pcg_init<2>), L.nbblk, NT, 0,
+             st, L.view<double>(), b, x, r, c.partial);
   else
     SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
                                    c.partial)));
@@ -1362,7 +1393,8 @@ void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& 
                       cudaStream_t st) {
   launch_uy<double>(L, p, st);
   if (uses_bricks(L))
-    launch_k(k7b_spmv_dot, L.nbblk, NT, 0, st, L.view<double>(), p, q, c.partial);
+    launch_k(pick_km(L.kvar, k7b_spmv_dot<0>, k7b_spmv_dot<1>, k7b_spmv_dot<2>), L.nbblk, NT, 0,
+             st, L.view<double>(), p, q, c.partial);
   else
     SH_DISPATCH(L.shape, (launch_k(k_pcg_spmv_dot<SHV>, L.nblk, NT, 0, st, L.view<double>(), p, q,
                                    c.partial)));
@@ -1384,7 +1416,8 @@ void launch_true_residual(const Level& L, const double* b, const double* x, doub
                           const PcgCtx& c, double* out, cudaStream_t st) {
   launch_uy<double>(L, x, st);
   if (uses_bricks(L))
-    launch_k(k7b_pcg_init, L.nbblk, NT, 0, st, L.view<double>(), b, x, r, c.partial);
+    launch_k(pick_km(L.kvar, k7b_pcg_init<0>, k7b_pcg_init<1>, k7b_pcg_init<2>), L.nbblk, NT, 0,
+             st, L.view<double>(), b, x, r, c.partial);
   else
     SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
                                    c.partial)));

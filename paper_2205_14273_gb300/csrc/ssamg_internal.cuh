@@ -237,6 +237,7 @@ struct Level {
   int nblk = 0, nfblk = 0, nbblk = 0;
   int cpt = 1;
   int bricks = 1; // 0: the tile table keeps this level's operator applies on cell tiles
+  int kvar = 2;   // per-cell stencil entries: 0 none, 1 only diagonals, 2 others too
   int shape = 0;  // StencilShape of the level's operator apply
   std::vector<int> hblk;  // host copy of the block starts of cell-wise launches
   std::vector<int> hbblk; // and of brick launches
