@@ -1050,7 +1050,11 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   // ---- row-job data: dense U x buffers and P rows of coupling columns
   for (int l = 0; l <= Lc; ++l) {
     Level& L = s->lev[l];
-    L.nublk = (int)cdivll(L.nr, SSAMG_RPB);
+    // lanes per row: the mean row length rounded up to a power of two,
+    // between SSAMG_TPR and SSAMG_TPR_MAX (coarse levels' rows grow long)
+    L.tpr = SSAMG_TPR;
+    while (L.tpr < SSAMG_TPR_MAX && (long long)L.tpr * L.nr < L.nnz) L.tpr *= 2;
+    L.nublk = (int)cdivll(L.nr, SSAMG_BLOCK / L.tpr);
     if (L.nr == 0) continue;
     L.uy64 = aalloc<double>(s->arena, L.N);
     SSAMG_CUDA(cudaMemsetAsync(L.uy64, 0, sizeof(double) * L.N, st));

@@ -351,18 +351,20 @@ __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, cons
   return acc;
 }
 
-// Sum of one U row: the SSAMG_TPR lanes l4 of a row group compute
+// Sum of one U row: the L.tpr lanes l4 of a row group compute
 // sum_q u_q * f(col_q, q, s_q) for row r (r >= L.nr: nothing, but the lanes
 // still join the shuffles) and store it at the row's cell of L.uy;
 // s_q = pre(col_q, q) is the entry's setup-time data.  With WAIT, the row
 // bounds, each lane's first column and value, and pre() of that entry are
-// loaded before pdl_wait(); so a row of at most SSAMG_TPR entries (the
-// common case) has one dependent load after the wait.  pre() may read only
-// what setup wrote.  Further entries go four per lane at a time so that
-// their loads overlap; the summation order is that of q ascending per lane.
+// loaded before pdl_wait(); so a row of at most L.tpr entries (the level
+// picks tpr from its mean row length) has one dependent load after the
+// wait.  pre() may read only what setup wrote.  Further entries go four per
+// lane at a time so that their loads overlap; the summation order is that
+// of q ascending per lane, then a fixed shuffle tree over the lanes.
 template <bool WAIT, class T, class Pre, class F>
 __device__ __forceinline__ void u_row_sum(const LevelView<T>& L, int r, int l4, Pre&& pre,
                                           F&& f) {
+  const int tp = L.tpr;
   int q = 0, q1 = 0, c0 = 0;
   T u0 = (T)0;
   decltype(pre(0, 0)) s0{};
@@ -379,36 +381,36 @@ __device__ __forceinline__ void u_row_sum(const LevelView<T>& L, int r, int l4, 
   T acc = (T)0;
   if (q < q1) {
     acc = fma(u0, f(c0, q, s0), acc);
-    q += SSAMG_TPR;
-    for (; q + 3 * SSAMG_TPR < q1; q += 4 * SSAMG_TPR) {
-      const int c1 = L.u_col[q], c2 = L.u_col[q + SSAMG_TPR], c3 = L.u_col[q + 2 * SSAMG_TPR],
-                c4 = L.u_col[q + 3 * SSAMG_TPR];
-      const T u1 = L.u_val[q], u2 = L.u_val[q + SSAMG_TPR], u3 = L.u_val[q + 2 * SSAMG_TPR],
-              u4 = L.u_val[q + 3 * SSAMG_TPR];
-      const T v1 = f(c1, q, pre(c1, q)), v2 = f(c2, q + SSAMG_TPR, pre(c2, q + SSAMG_TPR)),
-              v3 = f(c3, q + 2 * SSAMG_TPR, pre(c3, q + 2 * SSAMG_TPR)),
-              v4 = f(c4, q + 3 * SSAMG_TPR, pre(c4, q + 3 * SSAMG_TPR));
+    q += tp;
+    for (; q + 3 * tp < q1; q += 4 * tp) {
+      const int c1 = L.u_col[q], c2 = L.u_col[q + tp], c3 = L.u_col[q + 2 * tp],
+                c4 = L.u_col[q + 3 * tp];
+      const T u1 = L.u_val[q], u2 = L.u_val[q + tp], u3 = L.u_val[q + 2 * tp],
+              u4 = L.u_val[q + 3 * tp];
+      const T v1 = f(c1, q, pre(c1, q)), v2 = f(c2, q + tp, pre(c2, q + tp)),
+              v3 = f(c3, q + 2 * tp, pre(c3, q + 2 * tp)),
+              v4 = f(c4, q + 3 * tp, pre(c4, q + 3 * tp));
       acc = fma(u1, v1, acc);
       acc = fma(u2, v2, acc);
       acc = fma(u3, v3, acc);
       acc = fma(u4, v4, acc);
     }
-    for (; q < q1; q += SSAMG_TPR) {
+    for (; q < q1; q += tp) {
       const int c = L.u_col[q];
       acc = fma(L.u_val[q], f(c, q, pre(c, q)), acc);
     }
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  for (int o = 1; o < tp; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (r < L.nr && l4 == 0) L.uy[L.u_rows[r]] = acc;
 }
 
-// Row job of a launch: block rb's threads take SSAMG_RPB rows, SSAMG_TPR
-// lanes each (all threads must call; waits for the predecessor inside).
+// Row job of a launch: block rb's threads take SSAMG_BLOCK / L.tpr rows,
+// L.tpr lanes each (all threads must call; waits for the predecessor inside).
 template <class T, class Pre, class F>
 __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& pre, F&& f) {
-  u_row_sum<true>(L, rb * SSAMG_RPB + (int)threadIdx.x / SSAMG_TPR,
-                  (int)threadIdx.x % SSAMG_TPR, pre, f);
+  const int sh = __ffs(L.tpr) - 1;  // tpr is a power of two
+  u_row_sum<true>(L, rb * (SSAMG_BLOCK >> sh) + ((int)threadIdx.x >> sh),
+                  (int)threadIdx.x & (L.tpr - 1), pre, f);
 }
 
 // Block-wide sum (deterministic: fixed shuffle tree, then fixed warp order).

@@ -605,9 +605,9 @@ __global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
     T* __restrict__ Fx = F.x;
     const T* __restrict__ Fb = F.b;
     for (int g = tid; g < FL.N; g += nth) Fx[g] = FL.dinv[g] * Fb[g];
-    for (int base = 0; base < FL.nr; base += nth / SSAMG_TPR)
+    for (int base = 0; base < FL.nr; base += nth / FL.tpr)
       u_row_sum<false>(
-          FL, base + tid / SSAMG_TPR, tid % SSAMG_TPR, [&](int col, int) { return FL.dinv[col]; },
+          FL, base + tid / FL.tpr, tid % FL.tpr, [&](int col, int) { return FL.dinv[col]; },
           [&](int col, int, T d) { return d * Fb[col]; });
     barrier();
     T* __restrict__ Fr = F.r;
@@ -682,9 +682,9 @@ __global__ void __launch_bounds__(ONE ? SSAMG_TAIL_CTA : TB)
       cell_coords(fp, c, i, j, k);
       Fr[g] = add_p_row(Fx[g], p_row(fp, FL.Pw, FL.Pe, i, j, k), e);
     }
-    for (int base = 0; base < FL.nr; base += nth / SSAMG_TPR)
+    for (int base = 0; base < FL.nr; base += nth / FL.tpr)
       u_row_sum<false>(
-          FL, base + tid / SSAMG_TPR, tid % SSAMG_TPR,
+          FL, base + tid / FL.tpr, tid % FL.tpr,
           [&](int, int q) {
             return PCol<T>{FL.u_pj[2 * q], FL.u_pj[2 * q + 1], FL.u_pw[2 * q], FL.u_pw[2 * q + 1]};
           },

@@ -33,8 +33,8 @@
 #define SSAMG_BRICK_X 32
 #define SSAMG_BRICK_Y 8
 #define SSAMG_BRICK_Z 8
-#define SSAMG_TPR 4                          // threads per U row in row jobs
-#define SSAMG_RPB (SSAMG_BLOCK / SSAMG_TPR)  // U rows per block
+#define SSAMG_TPR 4       // fewest lanes per U row in row jobs
+#define SSAMG_TPR_MAX 16  // most lanes per U row (levels whose rows are long)
 
 // ---------------------------------------------------------------------------
 // Division by a run-time constant (round-up multiply-high method of Granlund
@@ -160,7 +160,8 @@ struct LevelView {
   const T* u_pw;        // and their weights (-1 column: absent)
   T* uy;                // dense per-cell (U x)(c) of the vector last passed to a row job; 0 off rows
   int nr;
-  int nublk;            // blocks of row jobs (SSAMG_RPB rows each)
+  int nublk;            // blocks of row jobs (SSAMG_BLOCK / tpr rows each)
+  int tpr;              // lanes per U row in row jobs (4, 8 or 16)
   // inside a PCG solve: the problems' scalars; a block of a problem whose
   // iteration has stopped leaves its cycle work undone (nothing reads it)
   const PcgScalars* skip;
@@ -266,6 +267,7 @@ struct Level {
   double* uy64 = nullptr;
   float* uy32 = nullptr;
   int nublk = 0;
+  int tpr = SSAMG_TPR;
   // cycle work vectors (precision of the cycle)
   void* x = nullptr;
   void* b = nullptr;
@@ -280,13 +282,13 @@ template <>
 inline LevelView<double> Level::view<double>() const {
   return LevelView<double>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
                            u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk,
-                           g_ssamg_skip};
+                           tpr, g_ssamg_skip};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
   return LevelView<float>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
                           Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, uy32,
-                          nr, nublk, g_ssamg_skip};
+                          nr, nublk, tpr, g_ssamg_skip};
 }
 
 struct SsamgError {
