@@ -120,10 +120,11 @@ typedef struct {
                           launch, so that each kernel is scheduled, and stages its part
                           descriptors, while its predecessor still runs; 0: plain launches */
   int tail_cells;      /* largest level of the use_tail = 2 tail (0: 4096) */
-  int use_bricks;      /* 1 (default): residual, relaxation and PCG operator applies on checked
-                          7-point levels (constant entries per part) run over 32 x 8 x 8
-                          bricks, each thread marching a column along z; 0: over the cell
-                          tiles of the other shapes */
+  int use_bricks;      /* 1 (default): residual, relaxations (also the last one, with the PCG's
+                          dot partials) and PCG operator applies on checked 7-point levels
+                          (some entries constant per part) run over 32 x 8 x 8 bricks, each
+                          thread marching a column along z; 0: over the cell tiles of the
+                          other shapes */
 } ssamg_params;
 
 typedef struct {
@@ -294,7 +295,9 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * iteration, 8 the PCG's vector steps (beta, search direction, alpha, x and
  * r updates), 9 the cycle's last post-relaxation as the PCG runs it
  * (FP64 z out, r.z partials).  Ids 7 and 8 clear the solve's convergence state, so that the
- * replayed iterations never stop; the next solve starts afresh.  The kernels work on
+ * replayed iterations never stop, and run on the vectors the last solve left (time them after a
+ * solve: on vectors that break the iteration down, p.Ap <= 0, the cycle kernels stand idle);
+ * the next solve starts afresh.  The kernels work on
  * the solver's own buffers (their contents are overwritten).  Synchronises
  * `stream`. */
 int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* us_per_launch,
@@ -306,10 +309,10 @@ int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* u
  * per level from its cell count n (summed over parts):
  *   k cells per thread (k = 1 .. 4): blocks of 256 threads over 256 k
  *     consecutive cells of one part, a thread's cells 256 apart;
- *   bricks (on levels whose operator is the 7-point stencil with constant
- *     entries per part, use_bricks set): the residual, relaxation and PCG
- *     operator applies run over 32 x 8 x 8 bricks, each thread marching a
- *     column along z; the other kernels keep the cell tiles.
+ *   bricks (on levels whose operator is the 7-point stencil with some
+ *     entries constant per part, use_bricks set): the residual, relaxations
+ *     and PCG operator applies run over 32 x 8 x 8 bricks, each thread
+ *     marching a column along z; the other kernels keep the cell tiles.
  * The tile table has one entry per size class c = floor(log2(max(n, 1))),
  * c = 0 .. SSAMG_TILE_CLASSES - 1: 0 selects the built-in rule (4 cells per
  * thread from 300,000 cells up, 1 below; bricks where the level allows

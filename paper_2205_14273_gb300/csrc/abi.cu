@@ -1310,8 +1310,8 @@ void enqueue_pcg_body(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, c
   const PcgCtx c = pcg_ctx(s);
   SkipScope skip(s->sc);
   const int npart = vcycle(s, s->r, s->z, st, s->partial, zp);
-  if (npart > 0)  // the last relaxation writes partials per cell-tile block
-    launch_pcg_beta_from_partials(L0, s->z, s->p, c, c.pb, st);
+  if (npart > 0)  // the last relaxation writes partials per block of its tiles
+    launch_pcg_beta_from_partials(L0, s->z, s->p, c, final_ranges(L0, c), st);
   else
     launch_pcg_beta(L0, s->r, s->z, zp, s->p, c, st);
   launch_pcg_alpha(L0, s->p, s->q, c, st);
@@ -1955,7 +1955,8 @@ double time_kernel_us(ssamg_solver s, int kernel, int level, int reps, cudaStrea
                                      s->prm.flexible ? s->zprev : nullptr, s->partial, cs);
         break;
       case 8:  // the PCG's vector steps: beta, p = z + beta p, alpha, x and r updates
-        launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s), s->pb, cs);
+        launch_pcg_beta_from_partials(s->lev[0], s->z, s->p, pcg_ctx(s),
+                                      final_ranges(s->lev[0], pcg_ctx(s)), cs);
         launch_pcg_update(s->lev[0], s->p, s->q, s->x, s->r, pcg_ctx(s), 0, 0, cs);
         break;
       default:

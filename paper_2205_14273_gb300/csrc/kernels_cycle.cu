@@ -289,6 +289,32 @@ struct SpmvDotOp {
   }
 };
 
+// The cycle's last post-relaxation as the PCG runs it (see k_relax_final).
+template <class T>
+struct RelaxFinalOp {
+  const T* b;
+  const T* dinv;
+  double* z;
+  const double* rpcg;
+  double* zprev;
+  int flex;
+  double s0, s1;
+  struct In {
+    T b, d;
+    double r, zo;
+  };
+  __device__ In load(int g) const { return In{b[g], dinv[g], rpcg[g], zprev[g]}; }
+  __device__ void apply(int g, T ax, T xg, In in) {
+    const double zv = (double)fma(in.d, in.b - ax, xg);
+    z[g] = zv;
+    s0 = fma(in.r, zv, s0);
+    if (flex) {
+      s1 = fma(in.r, in.zo, s1);
+      zprev[g] = zv;
+    }
+  }
+};
+
 template <class T, int KM>
 __global__ void __launch_bounds__(NT, brick_min_blocks<T, KM>()) k7b_residual(LevelView<T> L, const T* x, const T* b, T* r) {
   pdl_trigger();
@@ -311,6 +337,27 @@ __global__ void __launch_bounds__(NT, brick_min_blocks<T, KM>()) k7b_relax(Level
   if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
   RelaxOp<T> op{b, L.dinv, xo};
   brick7<T, KM>(L, sp, x, op);
+}
+
+template <class T, int KM>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 5 : 4) k7b_relax_final(LevelView<T> L, const T* x, const T* b,
+                                                      double* z, const double* rpcg,
+                                                      double* zprev, int flex, double* partial) {
+  pdl_trigger();
+  __shared__ DPart sp;
+  __shared__ double sh[NT / 32];
+  block_part(L.bblk, L.parts, L.np, sp);
+  __syncthreads();
+  pdl_wait();
+  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
+  RelaxFinalOp<T> op{b, L.dinv, z, rpcg, zprev, flex, 0.0, 0.0};
+  brick7<T, KM>(L, sp, x, op);
+  const double t0 = block_sum<NT>(op.s0, sh);
+  const double t1 = block_sum<NT>(op.s1, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = t0;
+    partial[2 * blockIdx.x + 1] = t1;
+  }
 }
 
 template <int KM>
@@ -1165,6 +1212,7 @@ bool uses_bricks(const Level& L) {
 // Level-0 block ranges of the problems for the partials that L's operator
 // apply launches write (brick or cell-tile blocks).
 const int* partial_ranges(const Level& L, const PcgCtx& c) { return uses_bricks(L) ? c.pbb : c.pb; }
+const int* final_ranges(const Level& L, const PcgCtx& c) { return uses_bricks(L) ? c.pbb : c.pb; }
 
 template <class T>
 void launch_relax0(const Level& L, const T* b, T* x, cudaStream_t st) {
@@ -1200,10 +1248,12 @@ void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const
   // zprev may be null (no flexible CG): pass a valid buffer and a flag
   const int flex = zprev != nullptr;
   double* zp = flex ? zprev : z;
-  // (on cell tiles also on brick levels: a z-marching brick form of this
-  // FP64-heavy epilogue measured 1.6-4x slower)
-  SH_DISPATCH(L.shape, (launch_k(k_relax_final<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, z,
-                                 rpcg, zp, flex, partial)));
+  if (uses_bricks(L))
+    launch_k(pick_km(L.kvar, k7b_relax_final<T, 0>, k7b_relax_final<T, 1>, k7b_relax_final<T, 2>),
+             L.nbblk, NT, 0, st, L.view<T>(), x, b, z, rpcg, zp, flex, partial);
+  else
+    SH_DISPATCH(L.shape, (launch_k(k_relax_final<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, z,
+                                   rpcg, zp, flex, partial)));
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>

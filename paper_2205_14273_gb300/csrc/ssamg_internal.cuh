@@ -406,6 +406,8 @@ void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, 
 // the partials those launches write.
 bool uses_bricks(const Level& L);
 const int* partial_ranges(const Level& L, const PcgCtx& c);
+// block ranges of the dot partials the cycle's last relaxation writes
+const int* final_ranges(const Level& L, const PcgCtx& c);
 void launch_pcg_alpha(const Level& L, const double* p, double* q, const PcgCtx& c,
                       cudaStream_t st);
 void launch_pcg_update(const Level& L0, const double* p, const double* q, double* x, double* r,
