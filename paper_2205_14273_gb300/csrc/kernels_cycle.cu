@@ -447,7 +447,7 @@ struct PCol {
 // at setup), so the two roles need no ordering.  P rows are setup data and
 // are fetched before the wait for the predecessor.
 template <class T>
-__global__ void __launch_bounds__(NT) k_prolong_u(LevelView<T> F, const T* ec,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 8 : 6) k_prolong_u(LevelView<T> F, const T* ec,
                                                   const T* xin, T* xout,
                                                   int nb) {
   pdl_trigger();
