@@ -62,8 +62,9 @@ __device__ __forceinline__ int find_part_cell(const int* __restrict__ cs, int np
 // from the level's descriptor array.  All threads call; a barrier follows in
 // the caller.
 __device__ __forceinline__ int block_part(const int* __restrict__ gblk,
-                                          const DPart* __restrict__ gparts, int np, DPart& sm) {
-  const int p = find_part(gblk, np, blockIdx.x);
+                                          const DPart* __restrict__ gparts, int np, DPart& sm,
+                                          int tile = -1) {
+  const int p = find_part(gblk, np, tile < 0 ? (int)blockIdx.x : tile);
   const int* s = reinterpret_cast<const int*>(gparts + p);
   int* d = reinterpret_cast<int*>(&sm);
   constexpr int nw = sizeof(DPart) / 4;

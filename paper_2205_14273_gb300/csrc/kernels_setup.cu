@@ -150,14 +150,15 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
 }
 
 // ---------------------------------------------------------------------------
-// K3: structured Galerkin product P^T S P per coarse cell (Eq. galerkin).
+// K3: structured Galerkin product P^T S P (Eq. galerkin), one coarse cell
+// per thread (the form for large levels, where it moves the fine data once).
 // For coarse cell I with fine anchor F (2I along d*) and a in {-1,0,1}:
 // f = F + a e_d carries P(f, I) = 1, PE(f) or PW(f); each entry o at f
 // reaches g = f + o, which maps to J = g/2 (coarse point) or to its west and
 // east coarse neighbours with PW(g), PE(g).  The product accumulates into the
 // coarse entry J - I.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 2) k_rap_struct(LevelView<double> F, LevelView<double> C,
+__global__ void __launch_bounds__(NT, 2) k_rap_cell(LevelView<double> F, LevelView<double> C,
                                                    double* __restrict__ ccoef,
                                                    float* __restrict__ ccoef32) {
   __shared__ DPart fp;
@@ -240,6 +241,85 @@ __global__ void __launch_bounds__(NT, 2) k_rap_struct(LevelView<double> F, Level
       ccoef[cp.coef[e] + cc] = v;
       if (ccoef32) ccoef32[cp.coef[e] + cc] = (float)v;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3 for small levels, one coarse entry per thread (nine terms at most, so
+// the dependent latency of a level is a few loads deep): the block's threads
+// take the cells of a coarse tile and one entry O of the coarse stencil.  For coarse cell I with fine
+// anchor F (2I along d*) and a in {-1,0,1}: f = F + a e_d carries
+// P(f, I) = 1, PE(f) or PW(f); an entry o at f reaches g = f + o, which maps
+// to the coarse offset t/2 (t = a + o_d even: g is a coarse point) or to
+// (t-1)/2 and (t+1)/2 with PW(g) and PE(g) (t odd).  So the entries of f
+// that feed O have o = O off d* and o_d in {-1,0,1}: at most nine terms per
+// coarse entry, summed in registers in the order (a, o_d) ascending.  Block
+// b takes entry b % ne of tile b / ne, so that the ne blocks of a tile run
+// together and share its fine data through L2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_rap_entry(LevelView<double> F, LevelView<double> C,
+                                                  int ne, double* __restrict__ ccoef,
+                                                   float* __restrict__ ccoef32) {
+  __shared__ DPart fp;
+  __shared__ DPart cp;
+  const int tile = (int)blockIdx.x / ne;
+  const int ec = (int)blockIdx.x - tile * ne;
+  int p = block_part(C.blk, C.parts, C.np, cp, tile);
+  part_of(F.parts, p, fp);
+  __syncthreads();
+  if (ec >= cp.nent) return;
+  const int O0 = cp.o[ec][0], O1 = cp.o[ec][1], O2 = cp.o[ec][2];
+  const int d = fp.dstar;
+#pragma unroll 1
+  for (int m = 0, cc = (tile - cp.blk0) * cp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
+       m < cp.cpt && cc < cp.ncell; ++m, cc += SSAMG_BLOCK) {
+    int I[3];
+    cell_coords(cp, cc, I[0], I[1], I[2]);
+    double v = 0.0;
+    if (inside(cp, I[0] + O0, I[1] + O1, I[2] + O2)) {
+      if (d < 0) {
+        // part not coarsened at this level: P = I on this part
+        const int e = fp.slot[(O0 + 1) + 3 * (O1 + 1) + 9 * (O2 + 1)];
+        if (e >= 0 && inside(fp, I[0] + O0, I[1] + O1, I[2] + O2))
+          v = coef_at(fp, F.coef, e, (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]);
+      } else {
+        const int Od = d == 0 ? O0 : d == 1 ? O1 : O2;
+        const int anchor = 2 * I[d] + fp.par;
+        for (int a = -1; a <= 1; ++a) {
+          int f[3] = {I[0], I[1], I[2]};
+          f[d] = anchor + a;
+          if (f[d] < 0 || f[d] >= fp.n[d]) continue;
+          const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+          double w1 = 1.0;
+          if (a != 0) {
+            const int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
+            w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
+          }
+          if (w1 == 0.0) continue;
+#pragma unroll
+          for (int od = -1; od <= 1; ++od) {
+            const int t = a + od;
+            // 0: g is a coarse point; 1: O is g's west coarse neighbour; 2: east
+            const int kind = (t & 1) == 0 ? (t / 2 == Od ? 0 : -1)
+                                          : ((t - 1) / 2 == Od ? 1 : (t + 1) / 2 == Od ? 2 : -1);
+            if (kind < 0) continue;
+            int o[3] = {O0, O1, O2};
+            o[d] = od;
+            const int e = fp.slot[(o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1)];
+            const int g0 = f[0] + o[0], g1 = f[1] + o[1], g2 = f[2] + o[2];
+            if (e < 0 || !inside(fp, g0, g1, g2)) continue;
+            double term = w1 * coef_at(fp, F.coef, e, fcell);
+            if (kind) {
+              const int Gi = fp.poff + fine_point_index(fp, g0, g1, g2);
+              term *= kind == 1 ? F.Pw[Gi] : F.Pe[Gi];
+            }
+            v += term;
+          }
+        }
+      }
+    }
+    ccoef[cp.coef[ec] + cc] = v;
+    if (ccoef32) ccoef32[cp.coef[ec] + cc] = (float)v;
   }
 }
 
@@ -663,8 +743,15 @@ void launch_interp(const Level& F, bool fp32, cudaStream_t st) {
 }
 
 void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st) {
-  k_rap_struct<<<Cl.nblk, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
+  if (Cl.N >= SSAMG_RAP_CELL_MIN) {
+    k_rap_cell<<<Cl.nblk, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
                                        fp32 ? Cl.coef32 : nullptr);
+  } else {
+    int ne = 1;
+    for (const PartH& h : Cl.parts) ne = std::max(ne, h.nent);
+    k_rap_entry<<<Cl.nblk * ne, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), ne, Cl.coef,
+                                             fp32 ? Cl.coef32 : nullptr);
+  }
   SSAMG_LAUNCH_CHECK();
 }
 
