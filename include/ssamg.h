@@ -341,14 +341,18 @@ int ssamg_level_tile(ssamg_solver s, int level, int* cells_per_thread, int* bric
  * times per level (as ssamg_time_kernel does, `reps` launches per kernel)
  * the kernels whose tiles follow that level's form: residual,
  * post-relaxation and prolongation on the level, restriction onto it, and
- * on level 0 the PCG's operator apply and vector steps.  Per size class it
- * keeps the fastest form on the class's largest level when that saves at
- * least 3% against the built-in rule (else 0), stores the table in the
- * solver, sets the hierarchy up once more with it, and copies it to table
- * (SSAMG_TILE_CLASSES ints, or NULL).  Requires a set-up solver; runs on
- * `stream` and synchronises it; the eight set-ups reuse the solver's device
- * memory.  On an error the solver keeps its previous table and must be set
- * up again before the next solve. */
+ * on level 0 the PCG's operator apply and vector steps (on PCG vectors
+ * primed by two iterations for b = 1).  Per size class it keeps the fastest
+ * form on the class's largest level when that saves at least 3% against the
+ * built-in rule (else 0); a table with any entry set is then kept only if a
+ * whole PCG iteration (ssamg_time_kernel id 7) under it is at least 1%
+ * faster than under the built-in rule, else the table is all 0.  The table
+ * is stored in the solver, the hierarchy set up once more with it, and
+ * copied to table (SSAMG_TILE_CLASSES ints, or NULL).  Requires a set-up
+ * solver; runs on `stream` and synchronises it; the set-ups reuse the
+ * solver's device memory; the solver's PCG vectors are overwritten.  On an
+ * error the solver keeps its previous table and must be set up again before
+ * the next solve. */
 int ssamg_autotune(ssamg_solver s, int reps, void* stream, int* table);
 
 /* Host-only check of the run-time division constants the kernels use to

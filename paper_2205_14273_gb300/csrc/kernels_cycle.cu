@@ -799,6 +799,14 @@ __global__ void k_cast_d2f(const double* in, float* out, int n) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g < n) out[g] = (float)in[g];
 }
+__global__ void k_fill(double* x, long long n, double v) {
+  pdl_trigger();
+  pdl_wait();
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n;
+       g += (long long)gridDim.x * blockDim.x)
+    x[g] = v;
+}
+
 __global__ void k_cast_f2d(const float* in, double* out, int n) {
   pdl_trigger();
   pdl_wait();
@@ -1387,6 +1395,10 @@ INST(double)
 
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st) {
   launch_k(k_cast_d2f, cdiv(n, NT), NT, 0, st, in, out, (int)n);
+  SSAMG_LAUNCH_CHECK();
+}
+void launch_fill(double* x, long long n, double v, cudaStream_t st) {
+  launch_k(k_fill, (int)std::min<long long>(cdiv(n, NT), 8 * 152), NT, 0, st, x, n, v);
   SSAMG_LAUNCH_CHECK();
 }
 void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st) {

@@ -27,6 +27,7 @@
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
 #define SSAMG_TUNE_MARGIN 0.97    // a tuned tile form must save 3% of a level's time
+#define SSAMG_TUNE_ITER_MARGIN 0.99  // and the tuned table 1% of a whole PCG iteration
 #define SSAMG_RAP_CELL_MIN 262144  // coarse levels this large take P^T S P one cell per thread
 #define SSAMG_EW 4                 // cells per thread of the elementwise pre-relaxation
 // Bricks of the checked 7-point operator applies: SSAMG_BRICK_X x _Y threads
@@ -391,6 +392,7 @@ template <class T>
 void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st);
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st);
 void launch_cast_f2d(const float* in, double* out, long long n, cudaStream_t st);
+void launch_fill(double* x, long long n, double v, cudaStream_t st);
 // y = A_l x; x may be a caller vector without guard cells
 void launch_matvec(const Level& L, const double* x, double* y, cudaStream_t st);
 
