@@ -316,7 +316,11 @@ def kernel_roofline(S, sv, prob, dev, stream, args):
 
 def level_table(sv, name, stream):
     """Per-level duration (us) of each cycle kernel, each timed alone as 100
-    graph-replayed launches on the solver's own buffers (stderr)."""
+    graph-replayed launches on the solver's own buffers (stderr).  The
+    restriction onto a level above the coarsest also does that level's
+    pre-relaxation (the "restrict" column of level l times the launch that
+    restricts onto l + 1), so the cycle runs the separate pre-relaxation on
+    level 0 only."""
     kinds = [("relax0_u", 2), ("residual", 0), ("restrict", 3), ("prolong_u", 4),
              ("relax", 1)]
     L = sv.num_levels()
@@ -331,7 +335,7 @@ def level_table(sv, name, stream):
         n, nr, _ = sv.level_sizes(l)
         row = []
         for _, kid in kinds:
-            if kid in (3, 4) and l == L - 1:
+            if (kid in (3, 4) and l == L - 1) or (kid == 2 and l > 0):
                 row.append("-")
             else:
                 row.append(f"{sv.time_kernel(kid, l, 100, stream):.2f}")
@@ -353,16 +357,22 @@ def hbm_by_level(sv, workload, stream, peak, min_cells=1 << 20):
         N, nr, nnz = sizes[l]
         if N < min_cells:
             continue
-        Nc = sizes[l + 1][0]
+        Nc, nrc, nnzc = sizes[l + 1]
         sc = sv.stored_coefficients(l)
+        # the restriction onto a level above the coarsest also pre-relaxes it:
+        # omega M^-1 read, x written, and its U x rows (structure, the
+        # columns' restriction rows and diagonals, three fine residuals each)
+        pre = 2 * w * Nc + 12 * nrc + 44 * nnzc if l + 2 < L else 0
         nbytes = {
             "relax0_u": (2, 3 * w * N + 12 * nr + 12 * nnz),
             "residual": (0, w * (sc + 3 * N)),
-            "restrict": (3, w * N + w * Nc + 2 * w * (N - Nc)),
+            "restrict": (3, w * N + w * Nc + 2 * w * (N - Nc) + pre),
             "prolong_u": (4, 2 * w * N + w * Nc + 2 * w * (N - Nc) + 12 * nr + 36 * nnz),
             "relax": (1, w * (sc + 4 * N)),
         }
         row = {"level": l, "cells": N, "stored_coefficients": sc}
+        if l > 0:
+            del nbytes["relax0_u"]  # done by the restriction onto this level
         for k, (kid, nb) in nbytes.items():
             us = sv.time_kernel(kid, l, 50, stream)
             gbs = nb / (us * 1e-6) / 1e9

@@ -1066,8 +1066,14 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       L.u_pj = aalloc<int>(s->arena, 2 * L.nnz);
       L.u_pw = aalloc<double>(s->arena, 2 * L.nnz);
       if (fp32) L.u_pw32 = aalloc<float>(s->arena, 2 * L.nnz);
-      launch_upcols(L, fp32, st);
     }
+    if (l > 0) {
+      // the restriction onto this level also pre-relaxes it (with U x)
+      L.u_rj = aalloc<int>(s->arena, 3 * L.nnz);
+      L.u_rw = aalloc<double>(s->arena, 2 * L.nnz);
+      if (fp32) L.u_rw32 = aalloc<float>(s->arena, 2 * L.nnz);
+    }
+    launch_ucols(l > 0 ? &s->lev[l - 1] : nullptr, L, fp32, st);
   }
 
   // ---- Section 3.4: smoother diagonals
@@ -1239,17 +1245,21 @@ int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream
       SSAMG_CUDA(cudaMemcpyAsync(z_out, Ls[0].t, sizeof(double) * Ls[0].N, cudaMemcpyDeviceToDevice, st));
     return 0;
   }
-  // down: pre-relax from zero (with U x for the residual), residual, restrict
+  // down: pre-relax from zero (with U x for the residual), residual,
+  // restrict; below level 0 the restriction also does the next level's
+  // pre-relaxation (x = omega M^-1 b is pointwise; its row jobs rebuild b at
+  // a coupling's column from the column's restriction row)
   const T* b = b0;
   for (int l = 0; l < lt; ++l) {
     T* x = (T*)Ls[l].x;
     T* r = (T*)Ls[l].r;
     if (l == 0 && fused_in)
       launch_relax0_u_first<T>(Ls[0], r_in, (T*)Ls[0].b, x, st);
-    else
+    else if (l == 0)
       launch_relax0_u<T>(Ls[l], b, x, st);
     launch_residual<T>(Ls[l], x, b, r, st);
-    launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b, st);
+    launch_restrict<T>(Ls[l], Ls[l + 1], r, (T*)Ls[l + 1].b,
+                       l + 1 < lt ? (T*)Ls[l + 1].x : nullptr, st);
     b = (const T*)Ls[l + 1].b;
   }
   const T* e;
@@ -1928,8 +1938,14 @@ double time_kernel_us(ssamg_solver s, int kernel, int level, int reps, cudaStrea
         else launch_relax0_u<double>(L, (const double*)L.b, (double*)L.x, cs);
         break;
       case 3:  // restriction to level + 1
-        if (f) launch_restrict<float>(L, s->lev[level + 1], (const float*)L.r, (float*)s->lev[level + 1].b, cs);
-        else launch_restrict<double>(L, s->lev[level + 1], (const double*)L.r, (double*)s->lev[level + 1].b, cs);
+        // with the next level's pre-relaxation, as the cycle runs it
+        if (f)
+          launch_restrict<float>(L, s->lev[level + 1], (const float*)L.r, (float*)s->lev[level + 1].b,
+                                 level + 2 < (int)s->lev.size() ? (float*)s->lev[level + 1].x : nullptr, cs);
+        else
+          launch_restrict<double>(L, s->lev[level + 1], (const double*)L.r,
+                                  (double*)s->lev[level + 1].b,
+                                  level + 2 < (int)s->lev.size() ? (double*)s->lev[level + 1].x : nullptr, cs);
         break;
       case 4:  // prolongation from level + 1 with U x
         if (f) launch_prolong_u<float>(L, (const float*)s->lev[level + 1].x, (const float*)L.x, (float*)L.r, cs);

@@ -395,14 +395,40 @@ __global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
+// Restriction row of a coupling column (fine cells, side weights) and the
+// column's omega M^-1 (setup data of a row job entry).
+template <class T>
+struct RCol {
+  int j0, j1, j2;
+  T w1, w2, d;
+};
+
 // bc = P^T r, one coarse cell per thread: the anchor (weight 1) and the two
 // fine points beside it along d* (weights PE of the west one, PW of the east).
 template <class T>
 __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
-                                                 const T* r, T* bc) {
+                                                 const T* r, T* bc, T* xc, int nb) {
   pdl_trigger();
   __shared__ DPart fp;
   __shared__ DPart cp;
+  if ((int)blockIdx.x >= nb) {
+    // row jobs of the coarse level's pre-relaxation: uy = U x with
+    // x = omega M^-1 b at each coupling's column, b rebuilt there from the
+    // column's restriction row exactly as the tiles compute it
+    u_row_job(
+        C, blockIdx.x - nb,
+        [&](int col, int q) {
+          return RCol<T>{C.u_rj[3 * q], C.u_rj[3 * q + 1], C.u_rj[3 * q + 2], C.u_rw[2 * q],
+                         C.u_rw[2 * q + 1], C.dinv[col]};
+        },
+        [&](int, int, const RCol<T>& rc) {
+          T v = r[rc.j0];
+          if (rc.j1 >= 0) v = fma(rc.w1, r[rc.j1], v);
+          if (rc.j2 >= 0) v = fma(rc.w2, r[rc.j2], v);
+          return rc.d * v;
+        });
+    return;
+  }
   int p = block_part(C.blk, C.parts, C.np, cp);
   part_of(F.parts, p, fp);
   __syncthreads();
@@ -432,6 +458,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelView<T> F, LevelView<T> C,
       }
     }
     bc[cp.off + cc] = v;
+    if (xc) xc[cp.off + cc] = C.dinv[cp.off + cc] * v;  // pre-relaxation from zero
   }
 }
 
@@ -1295,8 +1322,10 @@ void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
-void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st) {
-  launch_k(k_restrict<T>, Cl.nblk, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc);
+void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, T* xc, cudaStream_t st) {
+  // with xc: also x = omega M^-1 b on the coarse level, and its U x row jobs
+  const int nrow = xc ? Cl.nublk : 0;
+  launch_k(k_restrict<T>, Cl.nblk + nrow, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc, xc, Cl.nblk);
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -1386,7 +1415,7 @@ void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t 
   template void launch_coarse_apply<T>(int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
   template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \
-  template void launch_restrict<T>(const Level&, const Level&, const T*, T*, cudaStream_t); \
+  template void launch_restrict<T>(const Level&, const Level&, const T*, T*, T*, cudaStream_t); \
   template void launch_prolong<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
   template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);
 INST(float)

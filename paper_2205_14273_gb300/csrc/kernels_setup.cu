@@ -511,10 +511,9 @@ __global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, Level
 
 // For every coupling q of level l: the coarse columns and weights of P's row
 // of its column cell (used by the prolongation's row jobs).
-__global__ void k_upcols(LevelView<double> F, long long nnz, int* __restrict__ pj,
-                         double* __restrict__ pw, float* __restrict__ pw32) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nnz) return;
+__device__ __forceinline__ void upcol(const LevelView<double>& F, long long q,
+                                      int* __restrict__ pj, double* __restrict__ pw,
+                                      float* __restrict__ pw32) {
   int gq, gi, gj, gk;
   locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
   int J[2] = {-1, -1};
@@ -525,6 +524,60 @@ __global__ void k_upcols(LevelView<double> F, long long nnz, int* __restrict__ p
     pw[2 * q + t] = w[t];
     if (pw32) pw32[2 * q + t] = (float)w[t];
   }
+}
+
+// Restriction row of each coupling's column cell on a coarse level: the
+// fine cells (centre, -d*, +d* neighbours; -1 absent) and the side weights
+// (PE of the -d* fine point, PW of the +d*), as the restriction applies them.
+__device__ __forceinline__ void urcol(const LevelView<double>& F, const LevelView<double>& C,
+                                      long long q, int* __restrict__ rj, double* __restrict__ rw,
+                                      float* __restrict__ rw32) {
+  int p, I[3];
+  locate(C, C.parts, C.u_col[q], p, I[0], I[1], I[2]);
+  const DPart& fp = F.parts[p];
+  const int d = fp.dstar;
+  int j0, j1 = -1, j2 = -1;
+  double w1 = 0.0, w2 = 0.0;
+  if (d < 0) {
+    j0 = fp.off + (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
+  } else {
+    int f[3] = {I[0], I[1], I[2]};
+    const int anchor = 2 * I[d] + fp.par;
+    f[d] = anchor;
+    const int sd = (d == 0) ? 1 : (d == 1 ? fp.n[0] : fp.n[0] * fp.n[1]);
+    j0 = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
+    if (anchor - 1 >= 0) {
+      f[d] = anchor - 1;
+      j1 = j0 - sd;
+      w1 = F.Pe[fp.poff + fine_point_index(fp, f[0], f[1], f[2])];
+    }
+    if (anchor + 1 < fp.n[d]) {
+      f[d] = anchor + 1;
+      j2 = j0 + sd;
+      w2 = F.Pw[fp.poff + fine_point_index(fp, f[0], f[1], f[2])];
+    }
+  }
+  rj[3 * q] = j0;
+  rj[3 * q + 1] = j1;
+  rj[3 * q + 2] = j2;
+  rw[2 * q] = w1;
+  rw[2 * q + 1] = w2;
+  if (rw32) {
+    rw32[2 * q] = (float)w1;
+    rw32[2 * q + 1] = (float)w2;
+  }
+}
+
+// Setup data of a level's row jobs, per coupling: P's row of its column cell
+// (with pj: the prolongation's U x) and its restriction row from the level
+// above (with rj: the pre-relaxation fused into the restriction onto it).
+__global__ void k_ucols(LevelView<double> Fp, LevelView<double> L, long long nnz,
+                        int* __restrict__ pj, double* __restrict__ pw, float* __restrict__ pw32,
+                        int* __restrict__ rj, double* __restrict__ rw, float* __restrict__ rw32) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  if (pj) upcol(L, q, pj, pw, pw32);
+  if (rj) urcol(Fp, L, q, rj, rw, rw32);
 }
 
 __global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ u_map) {
@@ -785,10 +838,12 @@ void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStre
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_upcols(const Level& F, bool fp32, cudaStream_t st) {
-  if (F.nnz == 0) return;
-  k_upcols<<<cdiv(F.nnz, NT), NT, 0, st>>>(F.view<double>(), F.nnz, F.u_pj, F.u_pw,
-                                           fp32 ? F.u_pw32 : nullptr);
+void launch_ucols(const Level* Fp, const Level& L, bool fp32, cudaStream_t st) {
+  if (L.nnz == 0 || (!L.u_pj && !L.u_rj)) return;
+  k_ucols<<<cdiv(L.nnz, NT), NT, 0, st>>>(Fp ? Fp->view<double>() : L.view<double>(),
+                                         L.view<double>(), L.nnz, L.u_pj, L.u_pw,
+                                         fp32 ? L.u_pw32 : nullptr, L.u_rj, L.u_rw,
+                                         fp32 ? L.u_rw32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -160,6 +160,8 @@ struct LevelView {
   const int* u_rows;
   const int* u_pj;      // per coupling: the (<= 2) coarse columns of P's row of its column cell
   const T* u_pw;        // and their weights (-1 column: absent)
+  const int* u_rj;      // per coupling (levels >= 1): the (<= 3) fine cells of P^T's row of its
+  const T* u_rw;        // column cell (centre, -d*, +d*; -1 absent) and the two side weights
   T* uy;                // dense per-cell (U x)(c) of the vector last passed to a row job; 0 off rows
   int nr;
   int nublk;            // blocks of row jobs (SSAMG_BLOCK / tpr rows each)
@@ -266,6 +268,9 @@ struct Level {
   int* u_pj = nullptr;
   double* u_pw = nullptr;
   float* u_pw32 = nullptr;
+  int* u_rj = nullptr;
+  double* u_rw = nullptr;
+  float* u_rw32 = nullptr;
   double* uy64 = nullptr;
   float* uy32 = nullptr;
   int nublk = 0;
@@ -283,14 +288,14 @@ struct Level {
 template <>
 inline LevelView<double> Level::view<double>() const {
   return LevelView<double>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
-                           u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, uy64, nr, nublk,
-                           tpr, g_ssamg_skip};
+                           u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, u_rj, u_rw, uy64, nr,
+                           nublk, tpr, g_ssamg_skip};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
   return LevelView<float>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
-                          Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, uy32,
-                          nr, nublk, tpr, g_ssamg_skip};
+                          Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, u_rj,
+                          u_rw32, uy32, nr, nublk, tpr, g_ssamg_skip};
 }
 
 struct SsamgError {
@@ -366,13 +371,15 @@ void launch_relax0_u_first(const Level& L, const double* r64, T* b0, T* x, cudaS
 template <class T>
 void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const double* rpcg,
                         double* zprev, double* partial, cudaStream_t st);
-void launch_upcols(const Level& F, bool fp32, cudaStream_t st);
+// row-job setup data of L's couplings: P rows (L.u_pj set) and restriction
+// rows from the level above Fp (L.u_rj set)
+void launch_ucols(const Level* Fp, const Level& L, bool fp32, cudaStream_t st);
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st);
 template <class T>
-void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, cudaStream_t st);
+void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, T* xc, cudaStream_t st);
 template <class T>
 void launch_prolong(const Level& F, const Level& Cl, const T* ec, T* x, cudaStream_t st);
 template <class T>
