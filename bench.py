@@ -205,7 +205,7 @@ def run_ours(args):
         for name, sv in solvers.items():
             level_table(sv, name, stream)
 
-    # ---- dominant-kernel roofline (prolongation with U x, FP32 cycle)
+    # ---- dominant-kernel roofline (restriction with the fused pre-relaxation, FP32 cycle)
     roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
 
     # ---- per-kernel HBM fractions on the large levels, and the other two
@@ -262,56 +262,83 @@ def run_ours(args):
 def kernel_roofline(S, sv, prob, dev, stream, args):
     """Roofline of the dominant kernel of the timed step.
 
-    The prolongation with U x (k_prolong_u) has the largest share of the
-    solve (one launch per level and cycle).  achieved = its algorithmic bytes
-    summed over the levels of one V-cycle / the summed launch durations, each
-    measured with CUDA events around graph replays of that launch on this
-    stream.  Bytes per level (FP32 cycle): x in + x out (8 N_l), coarse
-    correction (4 N_{l+1}), P weights (8 per fine point), coupling rows (12 per
-    row: pointer, result) and couplings (36 each: column, value, P row of the
-    column, x and two coarse values).
+    The restriction (k_restrict, which on every level above the coarsest
+    also does the coarse level's pre-relaxation with its U x row jobs) has
+    the largest share of the step in the launch list, the prolongation with
+    U x (k_prolong_u) the next; both run once per level and cycle.
+    achieved = the kernel's algorithmic bytes summed over the levels of one
+    V-cycle / its summed launch durations, each measured with CUDA events
+    around graph replays of that launch on this stream.  Bytes per level
+    (FP32 cycle, w = 4): restriction: fine residual (w N_l), P weights
+    (2 w per fine point), coarse right-hand side out (w N_{l+1}) and, when
+    fused, omega M^-1 in and x out (2 w N_{l+1}) and the coarse level's
+    coupling rows (12 per row) and couplings (44 each: column, value,
+    restriction row of the column, its diagonal, three fine residuals);
+    prolongation: x in + x out (8 N_l), coarse correction (4 N_{l+1}),
+    P weights (8 per fine point), coupling rows (12 per row) and couplings
+    (36 each: column, value, P row of the column, x and two coarse values).
     """
     peaks = read_peaks()
     L = sv.num_levels()
     sizes = [sv.level_sizes(l) for l in range(L)]
-    tot_us = tot_b = 0.0
-    per_level = []
-    for l in range(L - 1):
-        us = sv.time_kernel(4, l, 50, stream)
+    w = 4
+
+    def restrict_bytes(l):
+        N = sizes[l][0]
+        Nc, nrc, nnzc = sizes[l + 1]
+        pre = 2 * w * Nc + 12 * nrc + 44 * nnzc if l + 2 < L else 0
+        return w * N + w * Nc + 2 * w * (N - Nc) + pre
+
+    def prolong_bytes(l):
         N, nr, nnz = sizes[l]
         Nc = sizes[l + 1][0]
-        nbytes = 8 * N + 4 * Nc + 8 * (N - Nc) + 12 * nr + 36 * nnz
-        tot_us += us
-        tot_b += nbytes
-        per_level.append(round(us, 2))
-    nl = L - 1
-    achieved = tot_b / (tot_us * 1e-6) / 1e9
+        return 8 * N + 4 * Nc + 8 * (N - Nc) + 12 * nr + 36 * nnz
+
     peak = peaks.get("hbm_gbs", 6800.0)
+
+    def over_levels(kid, nbytes, name):
+        tot_us = tot_b = 0.0
+        per_level = []
+        for l in range(L - 1):
+            us = sv.time_kernel(kid, l, 50, stream)
+            tot_us += us
+            tot_b += nbytes(l)
+            per_level.append(round(us, 2))
+        nl = L - 1
+        achieved = tot_b / (tot_us * 1e-6) / 1e9
+        return {
+            "kernel": name,
+            "bound": "hbm",
+            "achieved": round(achieved, 1),
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+            "traffic": None,
+            "bytes_per_launch": int(tot_b / nl),
+            "us_per_launch": round(tot_us / nl, 3),
+            "us_per_level": per_level,
+        }
+
+    out = over_levels(3, restrict_bytes,
+                      "k_restrict<float> (restriction P^T r, with the coarse level's "
+                      "pre-relaxation and U x row jobs), all levels of one V-cycle")
+    out["second_kernel"] = over_levels(
+        4, prolong_bytes,
+        "k_prolong_u<float> (prolongation x + P e with U x row jobs), all levels of one V-cycle")
     # the FP64 level-0 operator apply + dot (the PCG's largest single launch)
     us_spmv = sv.time_kernel(6, 0, 50, stream)
     N0 = sizes[0][0]
     flops = 2 * 8 * N0 + 2 * prob.nnz_u
-    return {
-        "kernel": "k_prolong_u<float> (prolongation x + P e with U x row jobs), all levels of one V-cycle",
-        "bound": "hbm",
-        "achieved": round(achieved, 1),
-        "peak": peak,
-        "unit": "GB/s",
-        "frac": round(achieved / peak, 4),
-        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-        "traffic": None,
-        "bytes_per_launch": int(tot_b / nl),
-        "us_per_launch": round(tot_us / nl, 3),
-        "us_per_level": per_level,
-        "fp64_level0_operator": {
-            "kernel": "k_pcg_spmv_dot (q = A p and p.q, FP64, level 0)",
-            "bound": "alu", "unit": "TFLOP/s",
-            "achieved": round(flops / (us_spmv * 1e-6) / 1e12, 4),
-            "peak": 1.25, "peak_source": "nominal GB300 FP64; 1.255 measured by an FMA probe",
-            "frac": round(flops / (us_spmv * 1e-6) / 1.25e12, 4),
-            "us_per_launch": round(us_spmv, 2),
-            "hbm_gbs": round((24 * N0 + 16 * prob.nnz_u) / (us_spmv * 1e-6) / 1e9, 1)},
-    }
+    out["fp64_level0_operator"] = {
+        "kernel": "k7b_spmv_dot (q = A p and p.q, FP64, level 0 bricks)",
+        "bound": "alu", "unit": "TFLOP/s",
+        "achieved": round(flops / (us_spmv * 1e-6) / 1e12, 4),
+        "peak": 1.25, "peak_source": "nominal GB300 FP64; 1.255 measured by an FMA probe",
+        "frac": round(flops / (us_spmv * 1e-6) / 1.25e12, 4),
+        "us_per_launch": round(us_spmv, 2),
+        "hbm_gbs": round((24 * N0 + 16 * prob.nnz_u) / (us_spmv * 1e-6) / 1e9, 1)}
+    return out
 
 
 def level_table(sv, name, stream):
