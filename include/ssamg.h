@@ -287,20 +287,21 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
 
 /* Diagnostic timing of one hot-path kernel on `level`: `reps` launches are
  * captured into a CUDA graph and replayed between CUDA events on `stream`
- * (after one warm-up replay); *us_per_launch receives the mean time per
- * launch in microseconds.  kernel: 0 residual, 1 relaxation, 2 pre-relaxation
- * from zero (with U x; the cycle runs it on level 0 only), 3 restriction to
- * level+1 (with level+1's pre-relaxation when level+1 is not the coarsest, as
- * the cycle runs it), 4 prolongation from level+1 (with U x), 5 whole V-cycle (level ignored), 6 the PCG's FP64 level-0
- * operator apply with its dot product (level ignored), 7 one whole PCG
- * iteration, 8 the PCG's vector steps (beta, search direction, alpha, x and
- * r updates), 9 the cycle's last post-relaxation as the PCG runs it
- * (FP64 z out, r.z partials).  Ids 7 and 8 clear the solve's convergence state, so that the
- * replayed iterations never stop, and run on the vectors the last solve left (time them after a
- * solve: on vectors that break the iteration down, p.Ap <= 0, the cycle kernels stand idle);
- * the next solve starts afresh.  The kernels work on
- * the solver's own buffers (their contents are overwritten).  Synchronises
- * `stream`. */
+ * (after one warm-up replay); *us_per_launch receives the mean time per launch
+ * in microseconds.  kernel: 0 residual, 1 relaxation, 2 pre-relaxation from
+ * zero (with U x; the cycle runs it on level 0 only), 3 restriction to level+1
+ * (with level+1's pre-relaxation when level+1 is not the coarsest, as the
+ * cycle runs it), 4 prolongation from level+1 (with U x), 5 whole V-cycle
+ * (level ignored), 6 the PCG's FP64 level-0 operator apply with its dot
+ * product (level ignored), 7 one whole PCG iteration, 8 the PCG's vector steps
+ * (beta, search direction, alpha, x and r updates), 9 the cycle's last post-
+ * relaxation as the PCG runs it (FP64 z out, r.z partials).  Ids 7 and 8 clear
+ * the solve's convergence state, so that the replayed iterations never stop,
+ * and run on the vectors the last solve left (time them after a solve: on
+ * vectors that break the iteration down, p.Ap <= 0, the cycle kernels stand
+ * idle); the next solve starts afresh.  The kernels work on the solver's own
+ * buffers (their contents are overwritten).  Synchronises `stream`.
+ */
 int ssamg_time_kernel(ssamg_solver s, int kernel, int level, int reps, double* us_per_launch,
                       void* stream);
 
