@@ -40,6 +40,24 @@ WORKLOAD = "8 parts x 64^3 (2x2x2 layout), 7-pt anisotropic diffusion, seed 1"
 L2_BYTES = 129 * 2 ** 20
 
 
+def max_over_ranks(value, ws, device=None):
+    """The largest of the ranks' values (a replicated job takes as long as its
+    slowest rank); every rank gets it.  One rank: the value itself."""
+    if ws == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mdof_s(n_per_rank, ws, step_ms):
+    """Whole-job throughput of ws replicas of an n_per_rank-unknown step
+    (weak scaling): all ranks' unknowns over the slowest rank's time."""
+    return ws * n_per_rank / (step_ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -179,11 +197,7 @@ def run_ours(args):
         ck = clocks.stop()
         setup_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
         solve_ms = [e1.elapsed_time(e2) for _, e1, e2 in ev]
-        step_ms = sum(setup_ms) / args.steps + sum(solve_ms) / args.steps
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        if ws > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+        step_ms = max_over_ranks(sum(setup_ms) / args.steps + sum(solve_ms) / args.steps, ws, dev)
         results[name] = {
             "ms_per_step": step_ms,
             "setup_ms": statistics.median(setup_ms),
@@ -193,8 +207,8 @@ def run_ours(args):
             "levels": verified["num_levels"],
             "operator_complexity": verified["operator_complexity"],
             "launches": int(verified["setup_kernel_launches"] + verified["solve_kernel_launches"]),
-            "mdof_s": ws * N / (step_ms * 1e-3) / 1e6,
-            "solve_mdof_s": ws * N / (statistics.median(solve_ms) * 1e-3) / 1e6,
+            "mdof_s": job_mdof_s(N, ws, step_ms),
+            "solve_mdof_s": job_mdof_s(N, ws, statistics.median(solve_ms)),
             "wall_s": wall,
             "clocks": ck,
         }
