@@ -132,3 +132,17 @@ def test_tile_table_validation(ssamg_lib):
     assert L.ssamg_autotune(h, 0, None, got) == S.ERR_ARG
     assert L.ssamg_get_tile_table(None, got) == S.ERR_ARG
     L.ssamg_solver_destroy(h)
+
+
+def test_binding_constants_match_the_header(ssamg_lib):
+    """The binding's copies of the header's constants (status codes, tile
+    table size and bit) are the header's values."""
+    import re
+    S = ssamg_lib
+    txt = open(S.HEADER).read()
+    defines = dict(re.findall(r"#define\s+(SSAMG_\w+)\s+(-?\d+)", txt))
+    assert int(defines["SSAMG_TILE_CLASSES"]) == S.TILE_CLASSES
+    assert int(defines["SSAMG_TILE_BRICKS"]) == S.TILE_BRICKS
+    codes = dict(re.findall(r"(SSAMG_(?:OK|NOT_CONVERGED|ERR_\w+))\s*=\s*(-?\d+)", txt))
+    for name, value in codes.items():
+        assert getattr(S, name[len("SSAMG_"):]) == int(value), name
