@@ -436,7 +436,8 @@ def tile_summary(table):
 def extra_workloads(S, stream, peak):
     """The 256^3 27-point workload and the 64-problem batched workload at full
     size: setup and solve times (one step after a warm-up) in both cycle
-    precisions, and the per-kernel HBM fractions of their large levels."""
+    precisions, and the per-kernel HBM fractions of their large levels; and
+    the 128^3 differentiation workload."""
     import torch
     out = {}
     prob = P.config(2)
@@ -511,7 +512,70 @@ def extra_workloads(S, stream, peak):
             res["hbm"] = hbm_by_level(B.solver(), res["workload"], stream, peak)
         del B
     out["batched_64"] = res
+    out["diffusion_128"] = differentiation_workload(S, stream, peak)
     return out
+
+
+def differentiation_workload(S, stream, peak):
+    """The differentiation form at full size (128^3, kappa = exp(g), FP64):
+    setup, forward solve, adjoint solve A lambda = x - x_t on the same
+    hierarchy, and dL/dg, each timed with CUDA events after a warm-up step;
+    the gradient kernels' HBM fractions (k_diffusion_exp_gradient: g, lambda,
+    x in and dL/dg out, 32 B per cell; k_coef_gradient: lambda and x in, the
+    7 entries' dL/da out, 72 B per cell)."""
+    import torch
+    prob = P.config(4)
+    N = prob.n
+    grid, A = S.matrix_from_problem(prob)
+    sv = S.Solver(tol=1e-8, max_iter=500)
+    bt = torch.as_tensor(prob.b[0], device="cuda")
+    xt = torch.as_tensor(prob.extra["x_t"], device="cuda")
+    gt = torch.as_tensor(prob.extra["g"].reshape(-1), device="cuda")
+    x = torch.zeros_like(bt)
+    lam = torch.zeros_like(bt)
+    dg = torch.zeros_like(bt)
+    dcoef = torch.zeros(7 * N, dtype=torch.float64, device="cuda")
+
+    def step(ev=None):
+        mark = (lambda k: ev[k].record(stream)) if ev else (lambda k: None)
+        mark(0)
+        sv.setup(A)
+        mark(1)
+        st_f = sv.solve(bt, x)
+        mark(2)
+        st_a = sv.adjoint_solve(x - xt, lam)
+        mark(3)
+        sv.diffusion_exp_gradient(gt, lam, x, dg)
+        mark(4)
+        return st_f, st_a
+
+    step()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    st_f, st_a = step(ev)
+    torch.cuda.synchronize()
+    t = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+
+    def kernel_us(fn, reps=20):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    us_dg = kernel_us(lambda: sv.diffusion_exp_gradient(gt, lam, x, dg))
+    us_dc = kernel_us(lambda: sv.coef_gradient(lam, x, dcoef))
+    frac = lambda nb, us: round(nb / (us * 1e-6) / 1e9 / peak, 3)
+    return {"workload": "1 part 128^3, 7-point harmonic-mean diffusion, kappa = exp(g), seed 4",
+            "unknowns": N, "precision": "fp64",
+            "setup_ms": round(t[0], 3), "forward_solve_ms": round(t[1], 3),
+            "adjoint_solve_ms": round(t[2], 3), "gradient_ms": round(t[3], 3),
+            "forward_iterations": st_f.iterations, "adjoint_iterations": st_a.iterations,
+            "mdof_s": round(N / (sum(t) * 1e-3) / 1e6, 3),
+            "k_diffusion_exp_gradient": {"us": round(us_dg, 2), "frac_hbm": frac(32 * N, us_dg)},
+            "k_coef_gradient": {"us": round(us_dc, 2), "frac_hbm": frac(72 * N, us_dc)}}
 
 
 def read_peaks():

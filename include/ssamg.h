@@ -174,7 +174,9 @@ int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const double* x, d
  * on one part (off-diagonal -2 k_c k_n/(k_c+k_n), diagonal = sum |off| + k_c
  * per Dirichlet face): dL/dg_c = k_c (sum over interior faces of
  * -2 k_n^2/(k_c+k_n)^2 (lam_c - lam_n)(x_c - x_n) - lam_c x_c per Dirichlet
- * face).  g, lambda, x, dg: device, N doubles; part 0 of the solver's grid. */
+ * face).  g, lambda, x, dg: device, N doubles; part 0 of the solver's grid.
+ * exp(g) is formed once per cell in the solver's PCG work vector q, which
+ * the next solve overwrites anyway. */
 int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, const double* lambda,
                                  const double* x, double* dg, void* stream);
 

@@ -1637,7 +1637,8 @@ extern "C" int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, con
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
   PdlScope pdl(s->prm);
-  launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, (cudaStream_t)stream);
+  // kappa = exp(g) goes to the PCG's q vector (scratch between solves)
+  launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, s->q, (cudaStream_t)stream);
   return SSAMG_OK;
   API_END
 }

@@ -1183,8 +1183,17 @@ __global__ void __launch_bounds__(NT) k_coef_gradient(LevelView<double> L,
   }
 }
 
+// kappa = exp(g), once per cell (FP64 exp is the expensive step on this GPU;
+// the gradient reads each cell's kappa up to seven times).
+__global__ void __launch_bounds__(NT) k_exp(int n, const double* gg, double* kap) {
+  pdl_trigger();
+  pdl_wait();
+  const int c = blockIdx.x * NT + threadIdx.x;
+  if (c < n) kap[c] = exp(gg[c]);
+}
+
 __global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double> L,
-                                                               const double* gg,
+                                                               const double* kap,
                                                                const double* lam,
                                                                const double* x,
                                                                double* dg) {
@@ -1197,22 +1206,27 @@ __global__ void __launch_bounds__(NT) k_diffusion_exp_gradient(LevelView<double>
   if (c >= sp.ncell) return;
   int i, j, k;
   cell_coords(sp, c, i, j, k);
-  const double kc = exp(gg[c]);
+  const double kc = kap[c];
   const double lc = lam[c], xc = x[c];
-  const int nb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
-  const int st[3] = {1, sp.n[0], sp.n[0] * sp.n[1]};
+  const int sx = 1, sy = sp.n[0], sz = sp.n[0] * sp.n[1];
   double acc = 0.0;
-  for (int f = 0; f < 6; ++f) {
-    if (inside(sp, i + nb[f][0], j + nb[f][1], k + nb[f][2])) {
-      int cn = c + nb[f][0] * st[0] + nb[f][1] * st[1] + nb[f][2] * st[2];
-      double kn = exp(gg[cn]);
-      double s = kc + kn;
-      double dt = 2.0 * kn * kn / (s * s);
-      acc -= dt * (lc - lam[cn]) * (xc - x[cn]);
+  // faces -x, +x, -y, +y, -z, +z
+  auto face = [&](bool in, int d) {
+    if (in) {
+      const double kn = kap[c + d];
+      const double s = kc + kn;
+      const double dt = 2.0 * kn * kn / (s * s);
+      acc -= dt * (lc - lam[c + d]) * (xc - x[c + d]);
     } else {
       acc -= lc * xc;
     }
-  }
+  };
+  face(i > 0, -sx);
+  face(i < sp.n[0] - 1, sx);
+  face(j > 0, -sy);
+  face(j < sp.n[1] - 1, sy);
+  face(k > 0, -sz);
+  face(k < sp.n[2] - 1, sz);
   dg[c] = kc * acc;
 }
 
@@ -1524,7 +1538,11 @@ void launch_coef_gradient(const Level& L, const double* lam, const double* x, do
 }
 
 void launch_diffusion_exp_gradient(const Level& L, const double* g, const double* lam,
-                                   const double* x, double* dg, cudaStream_t st) {
-  launch_k(k_diffusion_exp_gradient, cdiv(L.parts[0].ncell, NT), NT, 0, st, L.view<double>(), g, lam, x, dg);
+                                   const double* x, double* dg, double* kap, cudaStream_t st) {
+  const int n = (int)L.parts[0].ncell;
+  launch_k(k_exp, cdiv(n, NT), NT, 0, st, n, g, kap);
+  SSAMG_LAUNCH_CHECK();
+  launch_k(k_diffusion_exp_gradient, cdiv(n, NT), NT, 0, st, L.view<double>(), (const double*)kap,
+           lam, x, dg);
   SSAMG_LAUNCH_CHECK();
 }

@@ -430,4 +430,4 @@ void launch_true_residual(const Level& L, const double* b, const double* x, doub
 void launch_coef_gradient(const Level& L, const double* lam, const double* x, double* dcoef,
                           cudaStream_t st);
 void launch_diffusion_exp_gradient(const Level& L, const double* g, const double* lam,
-                                   const double* x, double* dg, cudaStream_t st);
+                                   const double* x, double* dg, double* kap, cudaStream_t st);
