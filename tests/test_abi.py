@@ -146,3 +146,25 @@ def test_binding_constants_match_the_header(ssamg_lib):
     codes = dict(re.findall(r"(SSAMG_(?:OK|NOT_CONVERGED|ERR_\w+))\s*=\s*(-?\d+)", txt))
     for name, value in codes.items():
         assert getattr(S, name[len("SSAMG_"):]) == int(value), name
+
+
+def test_binding_errors_without_a_hierarchy(ssamg_lib):
+    """The binding raises SsamgError with the library's status for bad
+    parameters, bad tile tables and calls that need a set-up hierarchy."""
+    S = ssamg_lib
+    with pytest.raises(S.SsamgError) as e:
+        S.Solver(precision=2)
+    assert e.value.code == S.ERR_ARG
+    sv = S.Solver()
+    assert sv.tile_table() == [0] * S.TILE_CLASSES
+    with pytest.raises(S.SsamgError) as e:
+        sv.set_tile_table([5] * S.TILE_CLASSES)
+    assert e.value.code == S.ERR_ARG
+    sv.set_tile_table([2 | S.TILE_BRICKS] * S.TILE_CLASSES)
+    assert sv.tile_table() == [2 | S.TILE_BRICKS] * S.TILE_CLASSES
+    sv.set_tile_table(None)
+    assert sv.tile_table() == [0] * S.TILE_CLASSES
+    for call in (lambda: sv.num_levels(), lambda: sv.level_tile(0), lambda: sv.autotune(reps=1)):
+        with pytest.raises(S.SsamgError) as e:
+            call()
+        assert e.value.code == S.ERR_STATE
