@@ -101,10 +101,16 @@ typedef struct {
   int precision;       /* 0: FP64 V-cycle; 1: FP32 V-cycle inside FP64 PCG */
   int relax;           /* 0: weighted Jacobi (Eq. relax1); 1: L1 Jacobi (Section 3.4) */
   double relax_factor; /* <= 0: omega_p of Eq. relax1 (relax 0) or 3/2 (relax 1) */
-  int skip;            /* 1: Section 3.4 "skip": no relaxation on a part at level l >= n_d whose
-                          coarsening direction equals its direction n_d levels above (read
-                          literally: only actual directions compare; the coarsest level is
-                          solved directly); 0 (default): relax on every level */
+  int skip;            /* Section 3.4 "skip" (relaxation turned off on some levels, mimicking
+                          full coarsening).  0 (default): relax on every level.  1: per part,
+                          the levels form rounds of distinct coarsening directions (a round
+                          starts at level 0 and wherever d* repeats a direction of the current
+                          round); only the first level of each round relaxes, so an isotropic
+                          part (d*_l = d*_{l-n_d}) relaxes on levels 0, n_d, 2 n_d, ... and a
+                          part coarsened repeatedly along one direction keeps relaxing there
+                          (Section 4, test case 2); levels where the part is not coarsened
+                          relax.  2: the printed test alone: no relaxation at level l >= n_d
+                          when d*_l = d*_{l-n_d} */
   int max_levels;      /* l_max of Section 3.1 (default 64) */
   long long s_max;     /* coarsening stops at total size <= s_max; <= 0: number of parts */
   double tol;          /* PCG stop: ||r||_2 <= tol ||b||_2 (default 1e-8) */

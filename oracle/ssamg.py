@@ -60,7 +60,8 @@ class Params:
     tol: float = 1e-8
     max_iter: int = 200
     coarse_direct: int = 1        # 1: dense Cholesky, 0: one relaxation sweep
-    skip: int = 0                 # 1: the "skip" option of Section 3.4 (see skipped_parts)
+    skip: int = 0                 # the "skip" option of Section 3.4: 0 off, 1 rounds reading,
+                                  # 2 literal test (see skipped_parts)
 
 
 @dataclass
@@ -564,16 +565,54 @@ def galerkin_unstructured(fine: Level, coarse: Level):
 # Relaxation (Section 3.4)
 # ---------------------------------------------------------------------------
 
-def skipped_parts(dstars, ndim: int, l: int) -> List[bool]:
-    """The "skip" option of Section 3.4: part p does no relaxation at level l
-    when its coarsening direction there equals the one n_d levels above,
-    d*_l = d*_{l - n_d}.  Reading: only actual directions compare (a part
-    left uncoarsened, d* = -1, keeps relaxing), and levels l < n_d always
-    relax."""
+def skipped_parts(dstars, ndim: int, l: int, mode: int = 1) -> List[bool]:
+    """The "skip" option of Section 3.4: which parts do no relaxation at level l.
+
+    The paper states the test d*_l = d*_{l - n_d} and says that the option
+    mimics full coarsening; Section 4 (test case 2) adds that a part coarsened
+    along one direction for its first levels has relaxation skipped only on
+    later levels.  Applied alone at every level, the test would stop an
+    isotropic part from relaxing anywhere below level n_d, which is not full
+    coarsening, and would skip level n_d of a part still coarsening along its
+    strong direction.
+
+    mode 1 (the reading taken): per part, the levels form rounds as full
+    coarsening would: a round starts at level 0 and at every level whose d*
+    already occurs in the current round, so a round holds distinct
+    directions (at most n_d).  A part with d*_l = d*_{l - n_d} throughout
+    (isotropic: x, y, z, x, ...) gets rounds [0, n_d), [n_d, 2 n_d), ...;
+    relaxation stays on the first level of each round and is off on the
+    others, i.e. on levels 0, n_d, 2 n_d, ..., the grids full coarsening
+    visits.  A repeated direction (the strong direction of an anisotropic
+    part) starts a new round at each repetition, so those levels keep
+    relaxing.  A level where the part is not coarsened (d* = -1: one cell, or
+    the coarsest level) relaxes and ends the round.
+
+    mode 2: the test read literally: skip level l >= n_d when d*_l >= 0 and
+    d*_l = d*_{l - n_d}.
+    """
     nparts = len(dstars[l])
-    if l < ndim:
-        return [False] * nparts
-    return [dstars[l][p] >= 0 and dstars[l][p] == dstars[l - ndim][p] for p in range(nparts)]
+    if mode == 2:
+        if l < ndim:
+            return [False] * nparts
+        return [dstars[l][p] >= 0 and dstars[l][p] == dstars[l - ndim][p] for p in range(nparts)]
+    out = []
+    for p in range(nparts):
+        seen = set()
+        skip = False
+        for k in range(l + 1):
+            d = dstars[k][p]
+            if d < 0 or d in seen:
+                seen = set() if d < 0 else {d}
+                skip = False
+            elif not seen:
+                seen = {d}
+                skip = False
+            else:
+                seen.add(d)
+                skip = True
+        out.append(skip)
+    return out
 
 
 def smoother_inverse(lev: Level, params: Params) -> np.ndarray:
@@ -645,7 +684,7 @@ def setup(prob, params: Params = Params()) -> Hierarchy:
         coarse.u_row, coarse.u_col, coarse.u_val, coarse.u_bits = galerkin_unstructured(fine, coarse)
         levels.append(coarse)
     for l, lev in enumerate(levels):
-        lev.skip = (skipped_parts(dstars, prob.ndim, l) if params.skip and l < len(dstars)
+        lev.skip = (skipped_parts(dstars, prob.ndim, l, params.skip) if params.skip and l < len(dstars)
                     else [False] * lev.nparts)
         lev.Dinv = smoother_inverse(lev, params)
     h = Hierarchy(levels, params, W0)

@@ -580,7 +580,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
   if (!prm || !out) return SSAMG_ERR_ARG;
   if (prm->precision < 0 || prm->precision > 1 || prm->relax < 0 || prm->relax > 1 ||
-      prm->skip < 0 || prm->skip > 1 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
+      prm->skip < 0 || prm->skip > 2 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
     return SSAMG_ERR_ARG;
   auto* s = new (std::nothrow) ssamg_solver_s;
   if (!s) return SSAMG_ERR_OOM;
@@ -932,13 +932,33 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     s->lev.push_back(std::move(C));
   }
   const int Lc = (int)s->lev.size() - 1;
-  // "skip" (Section 3.4): no relaxation on a part at level l >= n_d whose
-  // coarsening direction equals the one n_d levels above (actual directions)
-  for (int l = 0; l <= Lc; ++l)
-    for (int p = 0; p < np; ++p) {
+  // "skip" (Section 3.4).  skip = 1: per part, the levels form rounds as
+  // full coarsening would (a round starts at level 0 and at every level whose
+  // d* already occurs in the current round; a level with no d* relaxes and
+  // ends its round); only the first level of a round relaxes.  An isotropic
+  // part (d*_l = d*_{l-n_d}) then relaxes on levels 0, n_d, 2 n_d, ...; a
+  // part coarsened repeatedly along one direction relaxes on each of those
+  // levels.  skip = 2: the printed test alone, no relaxation at l >= n_d
+  // when d*_l = d*_{l-n_d}.
+  for (int p = 0; p < np; ++p) {
+    unsigned seen = 0;  // directions of the current round
+    for (int l = 0; l <= Lc; ++l) {
       PartH& h = s->lev[l].parts[p];
-      h.skip = s->prm.skip && l >= ndim && h.dstar >= 0 && h.dstar == s->lev[l - ndim].parts[p].dstar;
+      h.skip = 0;
+      if (s->prm.skip == 2) {
+        h.skip = l >= ndim && h.dstar >= 0 && h.dstar == s->lev[l - ndim].parts[p].dstar;
+      } else if (s->prm.skip == 1) {
+        if (h.dstar < 0) {
+          seen = 0;
+        } else if (seen == 0 || (seen >> h.dstar) & 1u) {
+          seen = 1u << h.dstar;
+        } else {
+          seen |= 1u << h.dstar;
+          h.skip = 1;
+        }
+      }
     }
+  }
 
   // ---- allocation (one arena walk; identical sizes reuse the same memory)
   for (int l = 0; l <= Lc; ++l) {

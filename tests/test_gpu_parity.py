@@ -416,11 +416,13 @@ def test_brick_applies_match_cell_tiles(S, prob, prec):
 @pytest.mark.parametrize("prob", [CASES[i] for i in (0, 13, 20)] + [P.laplace7(16)],
                          ids=[CIDS[i] for i in (0, 13, 20)] + ["laplace7 16^3"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_skip_option_matches_oracle(S, prob, prec):
-    """Section 3.4 "skip": the hierarchy (skipped parts' smoothers zero), one
+@pytest.mark.parametrize("mode", [1, 2])
+def test_skip_option_matches_oracle(S, prob, prec, mode):
+    """Section 3.4 "skip" (mode 1: rounds of distinct directions; mode 2: the
+    printed test alone): the hierarchy (skipped parts' smoothers zero), one
     V-cycle and the PCG iteration count against the oracle with skip on."""
-    h = O.setup(prob, O.Params(skip=1))
-    _, _, sv = gpu_setup(S, prob, skip=1, precision=prec, flexible=prec)
+    h = O.setup(prob, O.Params(skip=mode))
+    _, _, sv = gpu_setup(S, prob, skip=mode, precision=prec, flexible=prec)
     if prec == 0:
         compare_hierarchy(S, prob, sv, h)
     r = P.SplitMix64(43).uniform_pm1(prob.n)

@@ -379,6 +379,55 @@ def test_l1_jacobi_convergent():
         assert np.abs(ev).max() < 1.0
 
 
+def test_l1_jacobi_closed_form_interior_row():
+    """L1 Jacobi (Section 3.4) with the default factor 3/2 (SSAMG-base,
+    Section 4): an interior row of the 7-point Laplacian (6, -1 x 6) has
+    M_ii = sum_j |A_ij| = 12, so the smoother diagonal is 1.5 / 12 = 0.125;
+    a corner row (three neighbours outside the box) has M_ii = 9: 1/6."""
+    prob = P.laplace7(5)
+    h = O.setup(prob, O.Params(relax=1))
+    D = h.levels[0].part_view(h.levels[0].Dinv, 0)
+    assert D[2, 2, 2] == 0.125
+    assert abs(D[0, 0, 0] - 1.5 / 9.0) <= 1e-16
+    # a given factor replaces 3/2
+    h1 = O.setup(prob, O.Params(relax=1, relax_factor=1.0))
+    assert h1.levels[0].part_view(h1.levels[0].Dinv, 0)[2, 2, 2] == 1.0 / 12.0
+
+
+def test_l1_jacobi_row_sum_includes_couplings():
+    """M_ii sums |A_ij| over the whole row, the couplings U included: two
+    Laplacian parts joined face to face by U = -1 (so that the union is the
+    7-point Laplacian of a 4 x 3 x 3 box).  A face cell (0, 1, 1) of part 0
+    in the middle of the shared face has five in-box entries (6 and four -1)
+    plus one coupling: M_ii = 11 + 1 = 12, diagonal 1.5 / 12."""
+    offs = np.array([(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)],
+                    np.int32)
+    coef = [6.0] + [-1.0] * 6
+    boxes = [((0, 0, 0), (1, 2, 2)), ((0, 0, 0), (1, 2, 2))]
+    rows, idx, dirs, nb, nidx, vals = [], [], [], [], [], []
+    for k in range(3):
+        for j in range(3):
+            # part 0's +x face meets part 1's -x face
+            rows += [0, 1]
+            idx += [(1, j, k), (0, j, k)]
+            dirs += [(1, 0, 0), (-1, 0, 0)]
+            nb += [1, 0]
+            nidx += [(0, j, k), (1, j, k)]
+            vals += [-1.0, -1.0]
+    n = 2 * 18
+    prob = P.Problem(3, boxes, offs, [coef, coef], np.array(rows, np.int32),
+                     np.array(idx, np.int32), np.array(dirs, np.int32), np.array(nb, np.int32),
+                     np.array(nidx, np.int32), np.array(vals), np.ones((1, n)), name="l1pin")
+    h = O.setup(prob, O.Params(relax=1))
+    lev = h.levels[0]
+    D0 = lev.part_view(lev.Dinv, 0)
+    assert D0[1, 1, 1] == 0.125          # (i, j, k) = (1, 1, 1): coupled face cell
+    assert D0[1, 1, 0] == 1.5 / 11.0     # (0, 1, 1): on the physical -x face, five in-box entries
+    # the whole operator agrees with the assembled 7-point Laplacian of the union
+    A = _dense(prob)
+    assert np.allclose(h.levels[0].Dinv, 1.5 / np.abs(A).sum(axis=1), rtol=0, atol=1e-15)
+
+
 def test_coarsest_is_one_cell_per_part():
     prob = P.multipart_aniso(m=5, layout=(2, 2, 1), seed=8)
     h = O.setup(prob)
@@ -454,39 +503,82 @@ def test_adjoint_solve_uses_same_hierarchy():
 
 
 # ---------------------------------------------------------------------------
-# "skip" option (Section 3.4): relaxation off at level l of a part whose
-# coarsening direction equals its direction n_d levels above
+# "skip" option (Section 3.4): relaxation turned off on some levels so that an
+# isotropic part relaxes on the grids full coarsening would visit, while a part
+# still coarsening along its strong direction keeps relaxing (Section 4,
+# test case 2)
 # ---------------------------------------------------------------------------
-def test_skip_isotropic_pattern_closed_form():
-    """Isotropic 3-D: d* cycles x, y, z (ties to the smallest index), so the
-    first n_d = 3 levels relax and every further coarsened level is skipped;
-    the coarsest level (solved directly) is not."""
+def _relaxed_levels(h, p=0):
+    return [l for l, lev in enumerate(h.levels) if not lev.skip[p]]
+
+
+def test_skip_isotropic_relaxes_on_full_coarsening_grids():
+    """Isotropic 3-D: d* cycles x, y, z (ties to the smallest index).  Full
+    coarsening visits the cubes 16^3, 8^3, 4^3, 2^3, 1^3: with skip on, the
+    part relaxes exactly on the levels whose box is a cube (levels 0, 3, 6,
+    9 and the coarsest, 12), and the test d*_l = d*_{l-3} holds on every
+    skipped level from level 3 on."""
     prob = P.laplace7(16)
     h = O.setup(prob, O.Params(skip=1))
     L = len(h.levels)
     assert [lev.dstar[0] for lev in h.levels[:-1]] == [l % 3 for l in range(L - 1)]
-    assert [lev.skip[0] for lev in h.levels] == [l >= 3 and l < L - 1 for l in range(L)]
+    cubes = [l for l, lev in enumerate(h.levels) if len(set(lev.shape(0))) == 1]
+    assert cubes == [0, 3, 6, 9, 12] and L == 13
+    assert _relaxed_levels(h) == cubes
+    for l, lev in enumerate(h.levels):
+        if lev.skip[0] and l >= 3:
+            assert lev.dstar[0] == h.levels[l - 3].dstar[0]
+
+
+def test_skip_anisotropic_part_relaxes_while_direction_repeats():
+    """Test case 2 shape (Section 4): coefficients 100 times larger along i.
+    W = (1, 10, 10), so d* = i on levels 0-3 (W_i doubles to 16 > 10), then
+    j, k, i, j, k, ...  Those first levels keep relaxing; skipping starts
+    once the directions cycle: relaxed levels 0, 1, 2, 3, 6, 9, ..."""
+    a = np.array([[100.0, 1.0, 1.0]])
+    prob = P.chain_aniso([32], a, P.SplitMix64(3), 1)
+    h = O.setup(prob, O.Params(skip=1))
+    ds = [lev.dstar[0] for lev in h.levels[:-1]]
+    assert ds[:9] == [0, 0, 0, 0, 1, 2, 0, 1, 2]
+    rel = _relaxed_levels(h)
+    assert rel[:6] == [0, 1, 2, 3, 6, 9]
+    assert not any(h.levels[l].skip[0] for l in range(4))
+    # the literal test alone would skip level 3 (d*_3 = d*_0 = i)
+    h2 = O.setup(prob, O.Params(skip=2))
+    assert h2.levels[3].skip[0] and not h2.levels[4].skip[0]
+
+
+def test_skip_literal_reading_pattern():
+    """skip = 2, the printed test alone: an isotropic part relaxes on levels
+    0, 1, 2 and the coarsest only."""
+    prob = P.laplace7(16)
+    h = O.setup(prob, O.Params(skip=2))
+    L = len(h.levels)
+    assert [lev.skip[0] for lev in h.levels] == [3 <= l < L - 1 for l in range(L)]
 
 
 def test_skip_zeroes_only_the_skipped_smoothers():
     prob = P.multipart_aniso(m=10, layout=(2, 2, 1), seed=1)
     h0 = O.setup(prob)
-    h1 = O.setup(prob, O.Params(skip=1))
-    nd = prob.ndim
-    assert len(h0.levels) == len(h1.levels)
-    nskip = 0
-    for l, (a, b) in enumerate(zip(h0.levels, h1.levels)):
-        for p in range(a.nparts):
-            for o in a.S[p]:
-                assert np.array_equal(a.S[p][o], b.S[p][o])
-            d0, d1 = a.part_view(a.Dinv, p), b.part_view(b.Dinv, p)
-            if b.skip[p]:
-                nskip += 1
-                assert l >= nd and b.dstar[p] >= 0 and b.dstar[p] == h1.levels[l - nd].dstar[p]
-                assert not d1.any()
-            else:
-                assert np.array_equal(d0, d1)
-    assert nskip > 0
+    for mode in (1, 2):
+        h1 = O.setup(prob, O.Params(skip=mode))
+        nd = prob.ndim
+        assert len(h0.levels) == len(h1.levels)
+        nskip = 0
+        for l, (a, b) in enumerate(zip(h0.levels, h1.levels)):
+            for p in range(a.nparts):
+                for o in a.S[p]:
+                    assert np.array_equal(a.S[p][o], b.S[p][o])
+                d0, d1 = a.part_view(a.Dinv, p), b.part_view(b.Dinv, p)
+                if b.skip[p]:
+                    nskip += 1
+                    assert l >= 1 and b.dstar[p] >= 0
+                    if mode == 2:
+                        assert l >= nd and b.dstar[p] == h1.levels[l - nd].dstar[p]
+                    assert not d1.any()
+                else:
+                    assert np.array_equal(d0, d1)
+        assert nskip > 0
 
 
 def test_skip_preconditioner_is_symmetric_and_converges():

@@ -126,3 +126,52 @@ def test_gradient_sign():
     orig = O.diffusion_exp_gradient
     with patched("diffusion_exp_gradient", lambda g, lam, x: -orig(g, lam, x)):
         _fails(T.test_diffusion_gradient_matches_finite_difference)
+
+
+def _l1_smoother(factor_default, with_u):
+    """The L1 branch of smoother_inverse with a planted mistake."""
+    def fn(lev, params):
+        out = np.zeros(lev.n)
+        l1u = np.zeros(lev.n)
+        if with_u and len(lev.u_val):
+            np.add.at(l1u, lev.u_row, np.abs(lev.u_val))
+        for p in range(lev.nparts):
+            dv = lev.part_view(out, p)
+            w = params.relax_factor if params.relax_factor > 0 else factor_default
+            s = lev.part_view(l1u, p).copy()
+            for a in lev.S[p].values():
+                s += np.abs(a)
+            dv[...] = w / s
+        return out
+    return fn
+
+
+def test_l1_default_factor_one():
+    with patched("smoother_inverse", _l1_smoother(1.0, True)):
+        _fails(T.test_l1_jacobi_closed_form_interior_row)
+
+
+def test_l1_row_sum_without_couplings():
+    with patched("smoother_inverse", _l1_smoother(1.5, False)):
+        _fails(T.test_l1_jacobi_row_sum_includes_couplings)
+
+
+def test_skip_literal_in_place_of_rounds():
+    orig = O.skipped_parts
+    with patched("skipped_parts", lambda ds, nd, l, mode=1: orig(ds, nd, l, 2)):
+        _fails(T.test_skip_isotropic_relaxes_on_full_coarsening_grids)
+    with patched("skipped_parts", lambda ds, nd, l, mode=1: orig(ds, nd, l, 2)):
+        _fails(T.test_skip_anisotropic_part_relaxes_while_direction_repeats)
+
+
+def test_skip_relaxes_on_last_level_of_round():
+    """Relaxation kept on the last level of each round instead of the first."""
+    orig = O.skipped_parts
+
+    def last_of_round(ds, nd, l, mode=1):
+        if mode != 1:
+            return orig(ds, nd, l, mode)
+        nxt = orig(ds, nd, l + 1, 1) if l + 1 < len(ds) else [False] * len(ds[l])
+        return [not n for n in nxt]
+    with patched("skipped_parts", last_of_round):
+        _fails(T.test_skip_isotropic_relaxes_on_full_coarsening_grids)
