@@ -180,7 +180,9 @@ int ssamg_coef_gradient(ssamg_solver s, const double* lambda, const double* x, d
  * on one part (off-diagonal -2 k_c k_n/(k_c+k_n), diagonal = sum |off| + k_c
  * per Dirichlet face): dL/dg_c = k_c (sum over interior faces of
  * -2 k_n^2/(k_c+k_n)^2 (lam_c - lam_n)(x_c - x_n) - lam_c x_c per Dirichlet
- * face).  g, lambda, x, dg: device, N doubles; part 0 of the solver's grid.
+ * face).  g, lambda, x, dg: device, N doubles.  The solver's grid must have
+ * one part and its stencil the seven 7-point offsets (any order), else
+ * SSAMG_ERR_UNSUPPORTED before anything is enqueued.
  * exp(g) is formed once per cell in the solver's PCG work vector q, which
  * the next solve overwrites anyway. */
 int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, const double* lambda,
@@ -194,6 +196,9 @@ int ssamg_level_matvec(ssamg_solver s, int level, const double* x, double* y, vo
 /* ------------------------------------------------------- introspection ---
  * For tests and diagnostics (host copies; synchronous). */
 int ssamg_num_levels(ssamg_solver s);
+/* Number of parts of the set-up hierarchy (every level has the same parts);
+ * SSAMG_ERR_STATE before setup. */
+int ssamg_num_parts(ssamg_solver s);
 /* Per level and part: box corners, d* (-1 when the part is not coarsened or
  * on the coarsest level), omega_p (Eq. relax1), number of stencil entries and
  * their offsets (nentries x 3 ints, up to 27), offset of the part in the
@@ -272,11 +277,13 @@ void ssamg_batch_destroy(ssamg_batch B);
  * 67,108,864 cells fit (fewer under a tile table of fewer cells per thread). */
 #define SSAMG_NOALLOC_MAX_BLOCKS 65536
 
-/* Allocation-free form of the per-part coupling sums c of Section 3.1
- * (sum over the part's cells of sign(a_C) times minus the entries that move
- * along dimension d), for level `level` of a set-up hierarchy.  The paper has
- * no counterpart: this variant exists so that the sums can be taken inside a
- * captured CUDA graph, with no memory allocation and no synchronisation.
+/* Allocation-free form of the per-part coupling sums: for each part and
+ * dimension d, the sum over the part's cells of sign(a_C) times minus the
+ * stencil entries whose offset moves along d, for level `level` of a set-up
+ * hierarchy.  The paper has no counterpart: this variant exists for callers
+ * that cannot allocate device memory where they call it (inside a captured
+ * CUDA graph, or under an allocator they do not control), so it takes no
+ * memory and never synchronises.
  *   c_dev  device, n_parts(level) x 3 doubles, caller-owned; on level 0 it
  *          receives the values ssamg_spacings reports, bit for bit.
  *   stream stream the two kernels are enqueued on; the call returns without
@@ -364,6 +371,16 @@ int ssamg_level_tile(ssamg_solver s, int level, int* cells_per_thread, int* bric
  * error the solver keeps its previous table and must be set up again before
  * the next solve. */
 int ssamg_autotune(ssamg_solver s, int reps, void* stream, int* table);
+
+/* Self-test of the bounded device wait (the grid barrier of the cooperative
+ * coarse-level kernel, use_tail = 1): nblocks (1..8) blocks of one
+ * cooperative launch meet at one barrier that also waits for
+ * extra_arrivals (0..1024) arrivals that never come; each waiting block
+ * polls at most max_polls (1..2^20) times, then gives up and returns.
+ * SSAMG_OK when the barrier completed (extra_arrivals = 0),
+ * SSAMG_ERR_TIMEOUT when a block gave up; the device stays usable either
+ * way.  SSAMG_ERR_ARG outside the ranges.  Synchronises `stream`. */
+int ssamg_selftest_barrier(int nblocks, int extra_arrivals, unsigned max_polls, void* stream);
 
 /* Host-only check of the run-time division constants the kernels use to
  * split a linear cell index into (i, j, k): compares against plain division

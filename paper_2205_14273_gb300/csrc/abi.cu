@@ -139,6 +139,7 @@ struct ssamg_solver_s {
   int tail_blocks = 0;
   int tail_parts = 0;          // part descriptors of the tail levels (single-CTA tail)
   TailBarrier* tail_bar = nullptr;
+  const TailBarrier tail_bar_init{0u, SSAMG_BARRIER_SPINS, 0, 0};  // host source of its set-up copy
   // PCG work (FP64, level 0 size)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
          *zprev = nullptr, *partial = nullptr, *tres = nullptr;
@@ -1141,7 +1142,8 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
                                  std::max<long long>(1, cdivll(s->lev[lt].N, SSAMG_TAIL_BLOCK)));
       if (!one) {
         s->tail_bar = aalloc<TailBarrier>(s->arena, 1);
-        SSAMG_CUDA(cudaMemsetAsync(s->tail_bar, 0, sizeof(TailBarrier), st));
+        SSAMG_CUDA(cudaMemcpyAsync(s->tail_bar, &s->tail_bar_init, sizeof(TailBarrier),
+                                   cudaMemcpyHostToDevice, st));
       }
       const int nt = Lc - lt + 1;
       if (fp32) {
@@ -1656,6 +1658,23 @@ extern "C" int ssamg_diffusion_exp_gradient(ssamg_solver s, const double* g, con
   if (!s || !g || !lambda || !x || !dg) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   API_BEGIN
+  // the kernel differentiates one box with the 7-point stencil's faces
+  const Level& L0 = s->lev[0];
+  if (L0.np != 1)
+    throw SsamgError{SSAMG_ERR_UNSUPPORTED, "the diffusion gradient takes a grid of one part"};
+  {
+    const PartH& h = L0.parts[0];
+    int seen = 0;
+    bool ok = h.nent == 7;
+    for (int e = 0; e < h.nent && ok; ++e) {
+      const int a = std::abs(h.o[e][0]) + std::abs(h.o[e][1]) + std::abs(h.o[e][2]);
+      if (a > 1) ok = false;
+      else seen |= 1 << ((h.o[e][0] + 1) + 3 * (h.o[e][1] + 1) + 9 * (h.o[e][2] + 1));
+    }
+    if (!ok || seen != ((1 << 4) | (1 << 10) | (1 << 12) | (1 << 13) | (1 << 14) | (1 << 16) |
+                        (1 << 22)))
+      throw SsamgError{SSAMG_ERR_UNSUPPORTED, "the diffusion gradient needs the 7-point stencil"};
+  }
   PdlScope pdl(s->prm);
   // kappa = exp(g) goes to the PCG's q vector (scratch between solves)
   launch_diffusion_exp_gradient(s->lev[0], g, lambda, x, dg, s->q, (cudaStream_t)stream);
@@ -1818,6 +1837,10 @@ extern "C" void ssamg_batch_destroy(ssamg_batch B) { delete B; }
 // ---------------------------------------------------------------------------
 // Introspection
 // ---------------------------------------------------------------------------
+extern "C" int ssamg_num_parts(ssamg_solver s) {
+  return (s && s->ready) ? s->lev[0].np : SSAMG_ERR_STATE;
+}
+
 extern "C" int ssamg_num_levels(ssamg_solver s) {
   return (s && s->ready) ? (int)s->lev.size() : SSAMG_ERR_STATE;
 }
@@ -2180,6 +2203,18 @@ extern "C" int ssamg_autotune(ssamg_solver s, int reps, void* stream, int* table
   run_setup(s, st);
   restore.keep = true;
   if (table) std::copy(out, out + SSAMG_TILE_CLASSES, table);
+  return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_selftest_barrier(int nblocks, int extra_arrivals, unsigned max_polls,
+                                      void* stream) {
+  if (nblocks < 1 || nblocks > 8 || extra_arrivals < 0 || extra_arrivals > 1024 ||
+      max_polls < 1 || max_polls > (1u << 20))
+    return SSAMG_ERR_ARG;
+  API_BEGIN
+  const int err = barrier_selftest(nblocks, extra_arrivals, max_polls, (cudaStream_t)stream);
+  if (err) throw SsamgError{SSAMG_ERR_TIMEOUT, "the grid barrier gave up after its poll cap"};
   return SSAMG_OK;
   API_END
 }

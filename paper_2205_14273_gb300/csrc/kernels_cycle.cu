@@ -581,23 +581,26 @@ constexpr int TB = SSAMG_TAIL_BLOCK;
 
 // Grid barrier over gridDim.x co-resident blocks (cooperative launch).  Each
 // block's thread 0 adds to one counter with release semantics; block 0 adds
-// 2^31 - (nblocks - 1), the others 1, so the counter's top bit flips exactly
-// when every block has arrived.  Waiters poll with acquire semantics (which
+// 2^31 - (nblocks - 1 + gb->extra), the others 1, so the counter's top bit
+// flips exactly when every block (and gb->extra further arrivals, 0 outside
+// the self-test) has arrived.  Waiters poll with acquire semantics (which
 // also makes the other blocks' writes visible through this SM's L1).  The
-// wait is bounded: after SSAMG_BARRIER_SPINS polls the block records the
-// failure in gb->err and continues, and the solve reports a timeout.
+// wait is bounded: after gb->cap polls the block records the failure in
+// gb->err and continues, and the caller reports a timeout.
 __device__ __forceinline__ void grid_barrier(TailBarrier* gb) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned* ctr = &gb->count;
-    const unsigned nb = (blockIdx.x == 0) ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    const unsigned cap = *(volatile unsigned*)&gb->cap;
+    const unsigned extra = (unsigned)*(volatile int*)&gb->extra;
+    const unsigned nb = (blockIdx.x == 0) ? 0x80000000u - (gridDim.x - 1u + extra) : 1u;
     unsigned old, cur;
     asm volatile("atom.add.release.gpu.u32 %0,[%1],%2;" : "=r"(old) : "l"(ctr), "r"(nb) : "memory");
     unsigned spins = 0;
     for (;;) {
       asm volatile("ld.acquire.gpu.u32 %0,[%1];" : "=r"(cur) : "l"(ctr) : "memory");
       if ((old ^ cur) & 0x80000000u) break;
-      if (++spins > SSAMG_BARRIER_SPINS) {
+      if (++spins > cap) {
         atomicExch(&gb->err, 1);
         break;
       }
@@ -606,6 +609,9 @@ __device__ __forceinline__ void grid_barrier(TailBarrier* gb) {
   }
   __syncthreads();
 }
+
+// Self-test kernel: every block meets at one grid barrier.
+__global__ void k_barrier_selftest(TailBarrier* gb) { grid_barrier(gb); }
 
 // Operator apply of a tail level with the level's stencil shape (the same
 // specialised, unchecked stencils as the per-level kernels).
@@ -1398,6 +1404,32 @@ void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, 
   cfg.numAttrs = 1;
   SSAMG_CUDA(cudaLaunchKernelEx(&cfg, k_vtail<T, false>, lv, nlev, cinv, nL, coarse_direct, gb));
   SSAMG_LAUNCH_CHECK();
+}
+
+int barrier_selftest(int nblocks, int extra, unsigned cap, cudaStream_t st) {
+  TailBarrier* gb = nullptr;
+  SSAMG_CUDA(cudaMalloc(&gb, sizeof(TailBarrier)));
+  const TailBarrier init{0u, cap, 0, extra};
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(gb, &init, sizeof(init), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_barrier_selftest, gb);
+    if (e == cudaSuccess) ++g_ssamg_launches;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &gb->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(gb);
+  SSAMG_CUDA(e);
+  return err;
 }
 
 int tail_max_blocks() {

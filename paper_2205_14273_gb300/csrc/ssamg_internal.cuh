@@ -178,13 +178,17 @@ struct LevelView {
 #define SSAMG_TAIL_MAX_BLOCKS 128
 #define SSAMG_TAIL_CTA 1024         // threads of the single-CTA tail
 #define SSAMG_TAIL_CTA_CELLS 4096   // default largest level of the single-CTA tail
-#define SSAMG_BARRIER_SPINS (1u << 24)  // ~1 s of polling before a barrier gives up
+#define SSAMG_BARRIER_SPINS (1u << 24)  // default poll cap: ~1 s of polling before a barrier gives up
 
+// Grid barrier state (device memory): the arrival counter, the poll cap
+// after which a waiting block gives up, the sticky failure flag, and arrivals
+// expected beyond the launch's own blocks (0; a self-test sets more, so that
+// the wait cannot complete and must end at the cap).
 struct TailBarrier {
   unsigned count;
-  unsigned gen;
+  unsigned cap;
   int err;
-  int pad_;
+  int extra;
 };
 template <class T>
 struct TailLevel {
@@ -394,6 +398,11 @@ void launch_vtail(const TailLevel<T>* lv, int nlev, const double* cinv, int nL, 
 template <class T>
 bool vtail_one_prepare(int nlev, int nparts);
 int tail_max_blocks();
+// Self-test of the bounded grid barrier: nblocks co-resident blocks meet at
+// one barrier that also waits for `extra` arrivals that never come (when
+// extra > 0), polling at most `cap` times.  Returns the barrier's failure
+// flag (1: a block gave up).  Synchronises st.
+int barrier_selftest(int nblocks, int extra, unsigned cap, cudaStream_t st);
 void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st);
 template <class T>
 void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st);

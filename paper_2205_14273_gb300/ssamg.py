@@ -97,6 +97,7 @@ _SIGS = {
     "ssamg_precondition": (_i, [_vp, _vp, _vp, _vp]),
     "ssamg_level_matvec": (_i, [_vp, _i, _vp, _vp, _vp]),
     "ssamg_num_levels": (_i, [_vp]),
+    "ssamg_num_parts": (_i, [_vp]),
     "ssamg_level_part_info": (_i, [_vp, _i, _i, _ip, _ip, _ip, _dp, _ip, _ip,
                                    ctypes.POINTER(_ll)]),
     "ssamg_level_sizes": (_i, [_vp, _i, ctypes.POINTER(_ll), ctypes.POINTER(_ll),
@@ -114,6 +115,7 @@ _SIGS = {
     "ssamg_batch_solver": (_vp, [_vp]),
     "ssamg_level_stored_coefficients": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
+    "ssamg_selftest_barrier": (_i, [_i, _i, ctypes.c_uint, _vp]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
     "ssamg_set_tile_table": (_i, [_vp, _ip]),
     "ssamg_get_tile_table": (_i, [_vp, _ip]),
@@ -173,10 +175,15 @@ def _stream(stream) -> Optional[int]:
     return int(stream)
 
 
-def _dptr(t) -> int:
-    """Device pointer of a contiguous float64 CUDA tensor."""
-    if not (t.is_cuda and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA tensor")
+def _dptr(t, n: Optional[int] = None, what: str = "vector") -> int:
+    """Device pointer of a contiguous float64 CUDA tensor holding at least n
+    elements (the library reads or writes n doubles there)."""
+    if not (getattr(t, "is_cuda", False) and t.is_contiguous()):
+        raise ValueError(f"{what}: expected a contiguous CUDA tensor")
+    if str(t.dtype) != "torch.float64":
+        raise ValueError(f"{what}: expected float64, got {t.dtype}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what}: {t.numel()} elements, the call uses {n}")
     return t.data_ptr()
 
 
@@ -239,7 +246,10 @@ class Matrix:
 
     def set_box_values(self, part: int, entry: int, vals):
         if hasattr(vals, "is_cuda") and vals.is_cuda:
-            _check(lib().ssamg_matrix_set_box_values(self.h, part, entry, _dptr(vals), 1),
+            lo, hi = self.grid.boxes[part]
+            n = int(np.prod([hi[d] - lo[d] + 1 for d in range(3)]))
+            _check(lib().ssamg_matrix_set_box_values(self.h, part, entry,
+                                                     _dptr(vals, n, "vals"), 1),
                    "set_box_values")
         else:
             a = np.ascontiguousarray(vals, dtype=np.float64).ravel()
@@ -301,22 +311,37 @@ class Solver:
         self.matrix = A
         _check(lib().ssamg_setup(self.h, A.h, _stream(stream)), "setup")
 
+    def _n(self, level: int = 0) -> int:
+        """Cells of a level of the set-up hierarchy (raises before setup)."""
+        return self.level_sizes(level)[0]
+
+    def _nparts(self) -> int:
+        n = lib().ssamg_num_parts(self.h)
+        if n < 0:
+            raise SsamgError(n, "num_parts")
+        return n
+
     def solve(self, b, x, nrhs: int = 1, zero_guess: bool = True, stream=None,
               allow_not_converged=False) -> Stats:
         st = Stats()
-        rc = lib().ssamg_solve(self.h, _dptr(b), _dptr(x), nrhs, int(zero_guess),
-                               _stream(stream), ctypes.byref(st))
+        n = nrhs * self._n()
+        rc = lib().ssamg_solve(self.h, _dptr(b, n, "b"), _dptr(x, n, "x"), nrhs,
+                               int(zero_guess), _stream(stream), ctypes.byref(st))
         _check(rc, "solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return st
 
     def solve_nostats(self, b, x, nrhs: int = 1, stream=None) -> int:
-        return _check(lib().ssamg_solve(self.h, _dptr(b), _dptr(x), nrhs, 1, _stream(stream),
-                                         None), "solve", (OK, NOT_CONVERGED))
+        n = nrhs * self._n()
+        return _check(lib().ssamg_solve(self.h, _dptr(b, n, "b"), _dptr(x, n, "x"), nrhs, 1,
+                                         _stream(stream), None), "solve", (OK, NOT_CONVERGED))
 
     def solve_host(self, b: np.ndarray, x: np.ndarray, nrhs: int = 1, stream=None,
                    stats=True) -> Stats:
         st = Stats()
-        assert b.dtype == np.float64 and x.dtype == np.float64 and x.flags.c_contiguous
+        n = nrhs * self._n()
+        if not (b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous
+                and x.flags.c_contiguous and b.size >= n and x.size >= n):
+            raise ValueError(f"b, x: expected contiguous float64 arrays of {n} elements")
         rc = lib().ssamg_solve_host(self.h, b.ctypes.data_as(_dp), x.ctypes.data_as(_dp), nrhs,
                                     _stream(stream), ctypes.byref(st) if stats else None)
         _check(rc, "solve_host", (OK, NOT_CONVERGED))
@@ -325,27 +350,35 @@ class Solver:
     def adjoint_solve(self, g, lam, nrhs: int = 1, stream=None,
                       allow_not_converged=False) -> Stats:
         st = Stats()
-        rc = lib().ssamg_adjoint_solve(self.h, _dptr(g), _dptr(lam), nrhs, _stream(stream),
-                                       ctypes.byref(st))
+        n = nrhs * self._n()
+        rc = lib().ssamg_adjoint_solve(self.h, _dptr(g, n, "g"), _dptr(lam, n, "lambda"), nrhs,
+                                       _stream(stream), ctypes.byref(st))
         _check(rc, "adjoint_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return st
 
     def coef_gradient(self, lam, x, dcoef, stream=None):
-        _check(lib().ssamg_coef_gradient(self.h, _dptr(lam), _dptr(x), _dptr(dcoef),
-                                         _stream(stream)), "coef_gradient")
+        n = self._n()
+        ne = len(self.part_info(0, 0)["offsets"])
+        _check(lib().ssamg_coef_gradient(self.h, _dptr(lam, n, "lambda"), _dptr(x, n, "x"),
+                                         _dptr(dcoef, ne * n, "dcoef"), _stream(stream)),
+               "coef_gradient")
 
     def diffusion_exp_gradient(self, g, lam, x, dg, stream=None):
-        _check(lib().ssamg_diffusion_exp_gradient(self.h, _dptr(g), _dptr(lam), _dptr(x),
-                                                  _dptr(dg), _stream(stream)),
+        n = self._n()
+        _check(lib().ssamg_diffusion_exp_gradient(self.h, _dptr(g, n, "g"), _dptr(lam, n, "lambda"),
+                                                  _dptr(x, n, "x"), _dptr(dg, n, "dg"),
+                                                  _stream(stream)),
                "diffusion_exp_gradient")
 
     def precondition(self, r, z, stream=None):
-        _check(lib().ssamg_precondition(self.h, _dptr(r), _dptr(z), _stream(stream)),
-               "precondition")
+        n = self._n()
+        _check(lib().ssamg_precondition(self.h, _dptr(r, n, "r"), _dptr(z, n, "z"),
+                                        _stream(stream)), "precondition")
 
     def level_matvec(self, level: int, x, y, stream=None):
-        _check(lib().ssamg_level_matvec(self.h, level, _dptr(x), _dptr(y), _stream(stream)),
-               "level_matvec")
+        n = self._n(level)
+        _check(lib().ssamg_level_matvec(self.h, level, _dptr(x, n, "x"), _dptr(y, n, "y"),
+                                        _stream(stream)), "level_matvec")
 
     # ---- introspection (host copies)
     def num_levels(self) -> int:
@@ -451,7 +484,16 @@ class Solver:
             os.replace(tmp, cache)
         return table
 
-    def spacings(self, nparts: int):
+    def num_parts(self) -> int:
+        return self._nparts()
+
+    def spacings(self, nparts: Optional[int] = None):
+        """Per-part coupling sums c and spacings W (n_parts x 3 each); the part
+        count is the solver's (a given nparts must match it)."""
+        np_solver = self._nparts()
+        if nparts is not None and nparts != np_solver:
+            raise ValueError(f"nparts {nparts} != the solver's {np_solver} parts")
+        nparts = np_solver
         c = np.zeros(3 * nparts)
         W = np.zeros(3 * nparts)
         _check(lib().ssamg_spacings(self.h, c.ctypes.data_as(_dp), W.ctypes.data_as(_dp)),
@@ -461,8 +503,8 @@ class Solver:
     def coupling_sums_noalloc(self, level: int, c, stream=None):
         """Per-part coupling sums of `level` into the device tensor c (n_parts
         x 3 doubles), with no allocation or synchronisation (stream-ordered)."""
-        _check(lib().ssamg_coupling_sums_noalloc(self.h, level, _dptr(c), _stream(stream)),
-               "coupling_sums_noalloc")
+        _check(lib().ssamg_coupling_sums_noalloc(self.h, level, _dptr(c, 3 * self._nparts(), "c"),
+                                                 _stream(stream)), "coupling_sums_noalloc")
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None and getattr(self, "_owned", True):
@@ -499,7 +541,9 @@ class Batch:
         """b, x: contiguous float64 CUDA tensors of nrhs x N values; returns
         the nrhs x nprob stats (list of lists)."""
         st = (Stats * (nrhs * self.nprob))()
-        rc = lib().ssamg_batch_solve(self.h, _dptr(b), _dptr(x), nrhs, _stream(stream), st)
+        n = nrhs * self.num_cells()
+        rc = lib().ssamg_batch_solve(self.h, _dptr(b, n, "b"), _dptr(x, n, "x"), nrhs,
+                                     _stream(stream), st)
         _check(rc, "batch_solve", (OK, NOT_CONVERGED) if allow_not_converged else (OK,))
         return [[st[j * self.nprob + k] for k in range(self.nprob)] for j in range(nrhs)]
 

@@ -168,3 +168,53 @@ def test_binding_errors_without_a_hierarchy(ssamg_lib):
         with pytest.raises(S.SsamgError) as e:
             call()
         assert e.value.code == S.ERR_STATE
+
+
+class _FakeDeviceTensor:
+    """Stands in for a CUDA tensor (no GPU needed): the binding's checks read
+    only these attributes before any pointer reaches the library."""
+
+    def __init__(self, n, dtype="torch.float64", contiguous=True):
+        self.n, self.dtype, self.contig, self.is_cuda = n, dtype, contiguous, True
+
+    def is_contiguous(self):
+        return self.contig
+
+    def numel(self):
+        return self.n
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_binding_checks_device_vectors_before_the_call(ssamg_lib):
+    """A device vector of the wrong dtype, too few elements or not contiguous
+    is refused by the binding, before the library is called."""
+    S = ssamg_lib
+    assert S._dptr(_FakeDeviceTensor(10), 10) == 0x1000
+    assert S._dptr(_FakeDeviceTensor(12), 10) == 0x1000
+    for bad in (_FakeDeviceTensor(10, "torch.float32"), _FakeDeviceTensor(9),
+                _FakeDeviceTensor(10, contiguous=False)):
+        with pytest.raises(ValueError):
+            S._dptr(bad, 10)
+    with pytest.raises(ValueError):
+        S._dptr(np.zeros(10), 10)       # host memory is not a device vector
+
+
+def test_num_parts_needs_a_hierarchy(ssamg_lib):
+    S = ssamg_lib
+    sv = S.Solver()
+    assert S.lib().ssamg_num_parts(sv.h) == S.ERR_STATE
+    assert S.lib().ssamg_num_parts(None) == S.ERR_STATE
+    with pytest.raises(S.SsamgError):
+        sv.spacings()
+
+
+def test_barrier_selftest_argument_ranges(ssamg_lib):
+    """Out-of-range self-test arguments are refused on the host, before any
+    launch (so that no wait can be asked to poll for long)."""
+    S = ssamg_lib
+    L = S.lib()
+    for args in ((0, 0, 10), (9, 0, 10), (2, -1, 10), (2, 1025, 10), (2, 1, 0),
+                 (2, 1, (1 << 20) + 1)):
+        assert L.ssamg_selftest_barrier(*args, None) == S.ERR_ARG, args

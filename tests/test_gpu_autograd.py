@@ -131,3 +131,37 @@ def test_coef_gradient_with_couplings_matches_oracle(AG):
         o = tuple(int(v) for v in o)
         for p in range(prob.nparts):
             assert rel(got[e, cells[p]:cells[p + 1]], ref[p][o].reshape(-1)) <= 1e-9
+
+
+def test_diffusion_gradient_refuses_other_grids(ssamg_lib):
+    """The dL/dg kernel differentiates one box with the 7-point faces: a
+    two-part solver and a 27-point stencil are refused (SSAMG_ERR_UNSUPPORTED)
+    and the output is left as it was; wrong vectors are refused by the
+    binding before the call."""
+    S = ssamg_lib
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    for prob in (P.multipart_aniso(m=4, layout=(2, 1, 1), seed=2), P.var27(n=6, block=2, seed=2)):
+        grid, A = S.matrix_from_problem(prob)
+        sv = S.Solver()
+        sv.setup(A)
+        n = prob.n
+        v = torch.ones(n, dtype=torch.float64, device="cuda")
+        dg = torch.full((n,), 3.0, dtype=torch.float64, device="cuda")
+        with pytest.raises(S.SsamgError) as e:
+            sv.diffusion_exp_gradient(v, v, v, dg)
+        assert e.value.code == S.ERR_UNSUPPORTED
+        torch.cuda.synchronize()
+        assert bool((dg == 3.0).all())
+    prob = P.diffusion_exp(n=6, seed=4, nfd=2)
+    grid, A = S.matrix_from_problem(prob)
+    sv = S.Solver()
+    sv.setup(A)
+    n = prob.n
+    v = torch.ones(n, dtype=torch.float64, device="cuda")
+    for bad in (torch.ones(n, dtype=torch.float32, device="cuda"),
+                torch.ones(n - 1, dtype=torch.float64, device="cuda")):
+        with pytest.raises(ValueError):
+            sv.diffusion_exp_gradient(v, v, v, bad)
+        with pytest.raises(ValueError):
+            sv.solve(bad, torch.zeros(n, dtype=torch.float64, device="cuda"))

@@ -94,3 +94,34 @@ def test_rejects_bad_level(S):
     c = torch.zeros(3, dtype=torch.float64, device="cuda")
     with pytest.raises(Exception):
         sv.coupling_sums_noalloc(sv.num_levels(), c)
+
+
+def test_rejects_level_above_the_scratch(S):
+    """A level whose launch needs more blocks than the static scratch holds
+    is refused before anything is enqueued: one 257 x 256 x 256 part under a
+    tile table of one cell per thread on its size class (2^24) gives
+    16,842,752 / 256 = 65,792 blocks > 65,536."""
+    prob = P.laplace7(1)
+    prob = P.Problem(3, [((0, 0, 0), (256, 255, 255))], prob.offsets, prob.coef,
+                     prob.u_part, prob.u_idx, prob.u_dir, prob.u_nbor_part, prob.u_nbor_idx,
+                     prob.u_val, np.zeros((1, 1)), name="laplace7 257x256x256")
+    grid, A = S.matrix_from_problem(prob)
+    sv = S.Solver()
+    table = [0] * S.TILE_CLASSES
+    table[24] = 1
+    sv.set_tile_table(table)
+    sv.setup(A)
+    assert sv.level_tile(0) == (1, 0)
+    c = torch.full((3,), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.SsamgError) as e:
+        sv.coupling_sums_noalloc(0, c)
+    assert e.value.code == S.ERR_UNSUPPORTED
+    msg = S.last_error()
+    assert "65792" in msg and "65536" in msg, msg
+    torch.cuda.synchronize()
+    assert c.cpu().tolist() == [7.0, 7.0, 7.0]
+    # level 1 (8,421,376 cells, 4 cells per thread) fits
+    c1 = torch.zeros(3, dtype=torch.float64, device="cuda")
+    sv.coupling_sums_noalloc(1, c1)
+    torch.cuda.synchronize()
+    assert np.isfinite(c1.cpu().numpy()).all()
