@@ -118,14 +118,22 @@ typedef struct {
   int coarse_direct;   /* 1: dense Cholesky on the coarsest level; 0: one relaxation sweep (Section 3.5) */
   int flexible;        /* 1: Polak-Ribiere beta (for the FP32 cycle); 0: Fletcher-Reeves */
   int use_graph;       /* 1: run the PCG iteration loop as one CUDA graph */
-  int use_tail;        /* coarse levels in one launch: 0 (default) one launch per level and step;
+  int use_tail;        /* coarse levels in one launch: 0 one launch per level and step;
                           1: a cooperative grid over the levels of at most 32,768 cells
                           (<= 8 parts), with grid barriers; 2: one CTA of 1024 threads over the
-                          levels of at most tail_cells cells (<= 8 parts), with block barriers */
+                          levels of at most tail_cells cells (<= 8 parts), with block barriers;
+                          3 (default): the coarse-level transition of Section 3.5 (hybrid
+                          idea): from the
+                          first level of at most tail_cells cells (default 4096) down, the
+                          levels are assembled at setup (A = S + U as CSR, P, P^T, smoother
+                          diagonal, coarsest inverse) and each V-cycle runs them in one
+                          thread-block cluster with the level vectors in distributed shared
+                          memory (the first tail level is lowered while the tail does not fit
+                          the cluster's shared memory; no tail of two or more levels: as 0) */
   int use_pdl;         /* 1 (default): launch the solve's kernels with programmatic dependent
                           launch, so that each kernel is scheduled, and stages its part
                           descriptors, while its predecessor still runs; 0: plain launches */
-  int tail_cells;      /* largest level of the use_tail = 2 tail (0: 4096) */
+  int tail_cells;      /* largest level of the use_tail = 2 or 3 tail (0: 4096) */
   int use_bricks;      /* 1 (default): residual, relaxations (also the last one, with the PCG's
                           dot partials) and PCG operator applies on checked 7-point levels
                           (some entries constant per part) run over 32 x 8 x 8 bricks, each
@@ -196,6 +204,11 @@ int ssamg_level_matvec(ssamg_solver s, int level, const double* x, double* y, vo
 /* ------------------------------------------------------- introspection ---
  * For tests and diagnostics (host copies; synchronous). */
 int ssamg_num_levels(ssamg_solver s);
+/* Coarse-level transition of use_tail = 3: returns the number of levels it
+ * runs (0: none), with its first level, the CTAs of its cluster and their
+ * shared memory in bytes (-1, 0, 0 when there is none).  SSAMG_ERR_STATE
+ * before setup.  Any output pointer may be NULL. */
+int ssamg_tail_levels(ssamg_solver s, int* first, int* ctas, long long* smem_bytes);
 /* Number of parts of the set-up hierarchy (every level has the same parts);
  * SSAMG_ERR_STATE before setup. */
 int ssamg_num_parts(ssamg_solver s);
@@ -310,7 +323,8 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * (level ignored), 6 the PCG's FP64 level-0 operator apply with its dot
  * product (level ignored), 7 one whole PCG iteration, 8 the PCG's vector steps
  * (beta, search direction, alpha, x and r updates), 9 the cycle's last post-
- * relaxation as the PCG runs it (FP64 z out, r.z partials).  Ids 7 and 8 clear
+ * relaxation as the PCG runs it (FP64 z out, r.z partials), 10 the coarse-level transition's
+ * cluster kernel of use_tail = 3 (level ignored; SSAMG_ERR_STATE without one).  Ids 7 and 8 clear
  * the solve's convergence state, so that the replayed iterations never stop,
  * and run on the vectors the last solve left (time them after a solve: on
  * vectors that break the iteration down, p.Ap <= 0, the cycle kernels stand

@@ -12,7 +12,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libssamg.so")
-SOURCES = ["abi.cu", "kernels_setup.cu", "kernels_cycle.cu"]
+SOURCES = ["abi.cu", "kernels_setup.cu", "kernels_cycle.cu", "kernels_tail.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

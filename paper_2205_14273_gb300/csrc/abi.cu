@@ -139,6 +139,11 @@ struct ssamg_solver_s {
   int tail_blocks = 0;
   int tail_parts = 0;          // part descriptors of the tail levels (single-CTA tail)
   TailBarrier* tail_bar = nullptr;
+  // cluster tail (use_tail = 3): levels ctail.lev[0..nt) from level ctail_lt on
+  int ctail_lt = -1;
+  int ctail_nc = 0;
+  long long ctail_smem = 0;
+  CTailArgs ctail{};
   const TailBarrier tail_bar_init{0u, SSAMG_BARRIER_SPINS, 0, 0};  // host source of its set-up copy
   // PCG work (FP64, level 0 size)
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr,
@@ -572,7 +577,7 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->coarse_direct = 1;
   p->flexible = 0;
   p->use_graph = 1;
-  p->use_tail = 0;
+  p->use_tail = 3;
   p->use_pdl = 1;
   p->tail_cells = 0;
   p->use_bricks = 1;
@@ -581,7 +586,8 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
   if (!prm || !out) return SSAMG_ERR_ARG;
   if (prm->precision < 0 || prm->precision > 1 || prm->relax < 0 || prm->relax > 1 ||
-      prm->skip < 0 || prm->skip > 2 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0)
+      prm->skip < 0 || prm->skip > 2 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0 ||
+      prm->use_tail < 0 || prm->use_tail > 3)
     return SSAMG_ERR_ARG;
   auto* s = new (std::nothrow) ssamg_solver_s;
   if (!s) return SSAMG_ERR_OOM;
@@ -771,6 +777,131 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   SSAMG_CUDA(cudaMemcpyAsync(L.d_bblk, bblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
   SSAMG_CUDA(cudaMemcpyAsync(L.d_cellstart, cs.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+}
+
+// Coarse-level transition run by one cluster (see kernels_tail.cu): picks the
+// first tail level (the first level of at most tail_cells cells whose tail
+// fits the cluster's shared memory), lays out the per-CTA images, and
+// assembles them.  Leaves s->ctail_lt = -1 when no tail of two or more levels
+// fits or the device cannot run the cluster.  Synchronises st.
+void build_ctail(ssamg_solver s, cudaStream_t st) {
+  s->ctail_lt = -1;
+  const int Lc = (int)s->lev.size() - 1;
+  const bool fp32 = s->prm.precision == 1;
+  const bool direct = s->prm.coarse_direct != 0;
+  if (Lc < 1 || (direct && !s->cinv)) return;
+  const long long maxc = s->prm.tail_cells > 0 ? s->prm.tail_cells : SSAMG_CTAIL_CELLS;
+  int lt = Lc;
+  while (lt - 1 >= 1 && s->lev[lt - 1].N <= maxc) --lt;
+  if (lt >= Lc) return;
+  int dev = 0, optin = 0;
+  SSAMG_CUDA(cudaGetDevice(&dev));
+  SSAMG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  // row lengths of every candidate level (one read-back)
+  std::vector<long long> first(Lc + 2, 0);
+  for (int l = lt; l <= Lc; ++l) first[l + 1] = first[l] + s->lev[l].N;
+  int* dlen = aalloc<int>(s->arena, first[Lc + 1] - first[lt]);
+  for (int l = lt; l <= Lc; ++l) launch_ctail_rowlen(s->lev[l], dlen + (first[l] - first[lt]), st);
+  std::vector<int> len(first[Lc + 1] - first[lt]);
+  SSAMG_CUDA(cudaMemcpyAsync(len.data(), dlen, sizeof(int) * len.size(), cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  const size_t w = fp32 ? sizeof(float) : sizeof(double);
+  auto al = [](long long v) { return (v + 15) & ~15ll; };
+  for (int nc : {SSAMG_CTAIL_MAX_CTAS, 8}) {
+    for (int t0 = lt; t0 < Lc; ++t0) {
+      const int nt = Lc - t0 + 1;
+      if (nt > SSAMG_CTAIL_MAX_LEVELS) continue;
+      CTailArgs a{};
+      a.nt = nt;
+      a.direct = direct;
+      a.nL = (int)s->lev[Lc].N;
+      long long vec = 0, ro = 0;
+      bool ok = true;
+      std::vector<long long> cap(nt);
+      // row pointers of every level first, so that one 2-D copy uploads them
+      for (int j = 0; j < nt; ++j) {
+        a.lev[j].S = (int)cdivll(s->lev[t0 + j].N, nc);
+        a.lev[j].o_rowptr = (int)ro;
+        ro += 4ll * (a.lev[j].S + 1);
+      }
+      ro = al(ro);
+      const long long rp_bytes = ro;
+      for (int j = 0; j < nt && ok; ++j) {
+        const Level& L = s->lev[t0 + j];
+        CTailLevel& v = a.lev[j];
+        v.n = (int)L.N;
+        v.S = (int)cdivll(L.N, nc);
+        // lanes per row: as many as leave every row of the slice a group in one pass
+        v.tpr = 1;
+        while (v.tpr < 32 && (long long)v.S * v.tpr * 2 <= SSAMG_CTAIL_THREADS) v.tpr *= 2;
+        if (v.S >= (1 << SSAMG_CTAIL_LOCAL_BITS)) ok = false;
+        long long mx = 0;
+        for (int c = 0; c < nc; ++c) {
+          long long sum = 0;
+          for (long long g = (long long)c * v.S; g < std::min<long long>(L.N, (long long)(c + 1) * v.S); ++g)
+            sum += len[first[t0 + j] - first[lt] + g];
+          mx = std::max(mx, sum);
+        }
+        cap[j] = mx;
+        v.o_x = (int)vec;  vec += al(v.S * w);
+        v.o_b = (int)vec;  vec += al(v.S * w);
+        v.o_r = (int)vec;  vec += al(v.S * w);
+        v.o_col = (int)ro;    ro += al(2 * mx);
+        v.o_val = (int)ro;    ro += al(w * mx);
+        v.o_dinv = (int)ro;   ro += al(w * v.S);
+        v.o_pcol = v.o_pval = v.o_rcol = v.o_rval = v.o_inv = 0;
+        if (j + 1 < nt) {
+          v.o_pcol = (int)ro; ro += al(2ll * 2 * v.S);
+          v.o_pval = (int)ro; ro += al(w * 2 * v.S);
+        }
+        if (j > 0) {
+          v.o_rcol = (int)ro; ro += al(2ll * 3 * v.S);
+          v.o_rval = (int)ro; ro += al(w * 3 * v.S);
+        }
+        if (j + 1 == nt && direct) {
+          v.o_inv = (int)ro; ro += al(8ll * v.S * a.nL);
+        }
+      }
+      if (!ok || vec + ro > optin) continue;
+      a.vec_bytes = (int)vec;
+      a.ro_bytes = ro;
+      const bool can = fp32 ? ctail_prepare<float>(nc, vec + ro) : ctail_prepare<double>(nc, vec + ro);
+      if (!can) break;  // try fewer CTAs
+      // images: zeroed, row pointers from the host, the rest by the fill kernels
+      char* img = (char*)s->arena.alloc((size_t)nc * ro);
+      SSAMG_CUDA(cudaMemsetAsync(img, 0, (size_t)nc * ro, st));
+      std::vector<int> rp((size_t)nc * rp_bytes / 4, 0);
+      for (int j = 0; j < nt; ++j) {
+        const CTailLevel& v = a.lev[j];
+        for (int c = 0; c < nc; ++c) {
+          int* row = rp.data() + ((size_t)c * rp_bytes + v.o_rowptr) / 4;
+          int acc = 0;
+          for (int li = 0; li < v.S; ++li) {
+            row[li] = acc;
+            const long long g = (long long)c * v.S + li;
+            if (g < v.n) acc += len[first[t0 + j] - first[lt] + g];
+          }
+          row[v.S] = acc;
+        }
+      }
+      SSAMG_CUDA(cudaMemcpy2DAsync(img, (size_t)ro, rp.data(), (size_t)rp_bytes, (size_t)rp_bytes,
+                                   nc, cudaMemcpyHostToDevice, st));
+      for (int j = 0; j < nt; ++j) {
+        const int l = t0 + j;
+        launch_ctail_fill(fp32, s->lev[l], j > 0 ? &s->lev[l - 1] : nullptr,
+                          j + 1 < nt ? &s->lev[l + 1] : nullptr,
+                          (j + 1 == nt && direct) ? s->cinv : nullptr, a.nL, a.lev[j],
+                          j > 0 ? a.lev[j - 1].S : 1, j + 1 < nt ? a.lev[j + 1].S : 1, img, ro, st);
+      }
+      SSAMG_CUDA(cudaStreamSynchronize(st));  // rp is a host temporary
+      a.image = img;
+      s->ctail = a;
+      s->ctail_lt = t0;
+      s->ctail_nc = nc;
+      s->ctail_smem = vec + ro;
+      return;
+    }
+  }
 }
 
 void build_hierarchy(ssamg_solver s, cudaStream_t st) {
@@ -1029,7 +1160,16 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
         marker = aalloc<int>(s->arena, maxN + 1);
         scan_tmp = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
       }
-      launch_umark(F, C, marker, st);
+      // P rows of the coupling columns (kept: the prolongation's row jobs use them)
+      F.u_pj = aalloc<int>(s->arena, 2 * F.nnz);
+      F.u_pw = aalloc<double>(s->arena, 2 * F.nnz);
+      if (fp32) F.u_pw32 = aalloc<float>(s->arena, 2 * F.nnz);
+      launch_ucols(nullptr, F, fp32, true, false, st);
+      // P rows of the coupling rows, and the coarse rows they reach
+      int* prI = aalloc<int>(s->arena, 2ll * F.nr);
+      double* prW = aalloc<double>(s->arena, 2ll * F.nr);
+      signed char* prA = aalloc<signed char>(s->arena, 2ll * F.nr);
+      launch_uprow(F, C, prI, prW, prA, marker, st);
       launch_scan(marker, C.N, scan_tmp, st);
       SSAMG_CUDA(cudaMemcpyAsync(s->h_int, marker + C.N, sizeof(int), cudaMemcpyDeviceToHost, st));
       SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -1038,7 +1178,11 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       C.u_ptr = aalloc<int>(s->arena, C.nr + 1);
       launch_urows(C, marker, nullptr, st);
       if (C.nr > 0) {
-        launch_ucount(F, C, C.u_ptr, s->d_err, st);
+        int* fr = aalloc<int>(s->arena, 3ll * C.nr);
+        double* frw = aalloc<double>(s->arena, 3ll * C.nr);
+        int* longrows = aalloc<int>(s->arena, C.nr + 1ll);
+        launch_frows(F, C, prI, prW, prA, fr, frw, st);
+        launch_ucount(F, C, longrows, fr, frw, C.u_ptr, s->d_err, st);
         launch_scan(C.u_ptr, C.nr, scan_tmp, st);
         SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
         SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -1047,7 +1191,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
         C.u_val = aalloc<double>(s->arena, C.nnz);
         C.u_bits = aalloc<unsigned char>(s->arena, C.nnz);
         if (fp32) C.u_val32 = aalloc<float>(s->arena, C.nnz);
-        launch_ufill(F, C, fp32, s->d_err, st);
+        launch_ufill(F, C, longrows, fr, frw, fp32, s->d_err, st);
       }
     } else {
       C.nr = 0;
@@ -1083,18 +1227,14 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       L.uy32 = aalloc<float>(s->arena, L.N);
       SSAMG_CUDA(cudaMemsetAsync(L.uy32, 0, sizeof(float) * L.N, st));
     }
-    if (l < Lc) {
-      L.u_pj = aalloc<int>(s->arena, 2 * L.nnz);
-      L.u_pw = aalloc<double>(s->arena, 2 * L.nnz);
-      if (fp32) L.u_pw32 = aalloc<float>(s->arena, 2 * L.nnz);
-    }
+    // (P rows of the coupling columns, L.u_pj, were made with the level's P^T U P)
     if (l > 0) {
       // the restriction onto this level also pre-relaxes it (with U x)
       L.u_rj = aalloc<int>(s->arena, 3 * L.nnz);
       L.u_rw = aalloc<double>(s->arena, 2 * L.nnz);
       if (fp32) L.u_rw32 = aalloc<float>(s->arena, 2 * L.nnz);
+      launch_ucols(&s->lev[l - 1], L, fp32, false, true, st);
     }
-    launch_ucols(l > 0 ? &s->lev[l - 1] : nullptr, L, fp32, st);
   }
 
   // ---- Section 3.4: smoother diagonals
@@ -1117,7 +1257,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->tail_lt = -1;
   s->tail_dev = nullptr;
   s->tail_bar = nullptr;
-  if (s->prm.use_tail && (!s->prm.coarse_direct || s->cinv)) {
+  if ((s->prm.use_tail == 1 || s->prm.use_tail == 2) && (!s->prm.coarse_direct || s->cinv)) {
     // use_tail 1: cooperative grid over the levels of at most
     // SSAMG_TAIL_MAX_CELLS cells; 2: one CTA over the levels of at most
     // tail_cells (default SSAMG_TAIL_CTA_CELLS) cells
@@ -1171,6 +1311,9 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   SSAMG_CUDA(cudaStreamSynchronize(st));
   if (s->h_int[0]) throw SsamgError{SSAMG_ERR_UNSUPPORTED, "a coarse coupling row has more than 1024 candidates"};
   if (s->h_int[2]) throw SsamgError{SSAMG_ERR_BREAKDOWN, "coarsest operator is not positive definite"};
+  // ---- coarse-level transition in one cluster (use_tail = 3)
+  s->ctail_lt = -1;
+  if (s->prm.use_tail == 3) build_ctail(s, st);
 
   // ---- PCG work vectors (the ones the level-0 stencil reads carry guard cells)
   long long N = s->lev[0].N;
@@ -1253,8 +1396,9 @@ int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream
     if (is_f) launch_cast_f2d((const float*)out, z_out, Ls[0].N, st);
     return 0;
   }
-  // levels from tail_lt on run in one fused single-block launch
-  const int lt = s->tail_lt >= 0 ? s->tail_lt : Lc;
+  // levels from tail_lt on run in one fused single-block launch, or from
+  // ctail_lt on in one cluster
+  const int lt = s->ctail_lt >= 1 ? s->ctail_lt : s->tail_lt >= 0 ? s->tail_lt : Lc;
   if (lt == 0) {
     // the whole cycle fits the tail: it reads b and writes t of level 0
     if (!is_f)
@@ -1285,7 +1429,10 @@ int enqueue_vcycle(ssamg_solver s, const double* r_in, double* z_out, cudaStream
     b = (const T*)Ls[l + 1].b;
   }
   const T* e;
-  if (lt < Lc) {
+  if (lt < Lc && s->ctail_lt == lt) {
+    launch_ctail<T>(s->ctail, s->ctail_nc, s->ctail_smem, (const T*)Ls[lt].b, (T*)Ls[lt].t, st);
+    e = (const T*)Ls[lt].t;
+  } else if (lt < Lc) {
     launch_vtail<T>((const TailLevel<T>*)s->tail_dev, Lc - lt + 1, s->cinv, s->nL,
                     s->prm.coarse_direct, s->tail_blocks, s->tail_bar, st, s->tail_parts);
     e = (const T*)Ls[lt].t;
@@ -1841,6 +1988,15 @@ extern "C" int ssamg_num_parts(ssamg_solver s) {
   return (s && s->ready) ? s->lev[0].np : SSAMG_ERR_STATE;
 }
 
+extern "C" int ssamg_tail_levels(ssamg_solver s, int* first, int* ctas, long long* smem_bytes) {
+  if (!s || !s->ready) return SSAMG_ERR_STATE;
+  const bool on = s->ctail_lt >= 1;
+  if (first) *first = on ? s->ctail_lt : -1;
+  if (ctas) *ctas = on ? s->ctail_nc : 0;
+  if (smem_bytes) *smem_bytes = on ? s->ctail_smem : 0;
+  return on ? s->ctail.nt : 0;
+}
+
 extern "C" int ssamg_num_levels(ssamg_solver s) {
   return (s && s->ready) ? (int)s->lev.size() : SSAMG_ERR_STATE;
 }
@@ -2019,6 +2175,16 @@ double time_kernel_us(ssamg_solver s, int kernel, int level, int reps, cudaStrea
                                       final_ranges(s->lev[0], pcg_ctx(s)), cs);
         launch_pcg_update(s->lev[0], s->p, s->q, s->x, s->r, pcg_ctx(s), 0, 0, cs);
         break;
+      case 10: {  // the coarse-level transition's cluster kernel (levels from ctail_lt on)
+        if (s->ctail_lt < 1) throw SsamgError{SSAMG_ERR_STATE, "no cluster tail in this hierarchy"};
+        Level& T0 = s->lev[s->ctail_lt];
+        if (f)
+          launch_ctail<float>(s->ctail, s->ctail_nc, s->ctail_smem, (const float*)T0.b, (float*)T0.t, cs);
+        else
+          launch_ctail<double>(s->ctail, s->ctail_nc, s->ctail_smem, (const double*)T0.b,
+                               (double*)T0.t, cs);
+        break;
+      }
       default:
         throw SsamgError{SSAMG_ERR_ARG, "unknown kernel id"};
     }

@@ -340,16 +340,71 @@ __device__ __forceinline__ void locate(const LevelView<double>& L, const DPart* 
   j = (int)q - k * dp.n[1];
 }
 
-__global__ void k_umark(LevelView<double> F, int nr, const int* __restrict__ rows,
-                        int* __restrict__ marker) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+// P's row at the cell of every fine coupling row r (Section 3.2): up to two
+// coarse columns I with weights P(f, I) and the position a of f relative to
+// I's anchor along d* (a = 0: f is I's coarse point or its part is not
+// coarsened; +1: I is f's west neighbour; -1: its east neighbour), and the
+// marker of the coarse rows of U_c.
+__global__ void k_uprow(LevelView<double> F, int nr, const int* __restrict__ rows,
+                        int* __restrict__ prI, double* __restrict__ prW,
+                        signed char* __restrict__ prA, int* __restrict__ marker) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nr) return;
   int p, i, j, k;
   locate(F, F.parts, rows[r], p, i, j, k);
-  int J[2];
-  double w[2];
-  int m = p_row_arrays(F.parts[p], F.Pw, F.Pe, i, j, k, J, w);
-  for (int t = 0; t < m; ++t) marker[J[t]] = 1;
+  const DPart& fp = F.parts[p];
+  int I[2] = {-1, -1};
+  double w[2] = {0.0, 0.0};
+  signed char a[2] = {0, 0};
+  const int d = fp.dstar;
+  if (d < 0) {
+    I[0] = coarse_index(fp, i, j, k);
+    w[0] = 1.0;
+  } else {
+    const int cd = d == 0 ? i : (d == 1 ? j : k);
+    auto at = [&](int v) {
+      return coarse_index(fp, d == 0 ? v : i, d == 1 ? v : j, d == 2 ? v : k);
+    };
+    if (((cd + fp.par) & 1) == 0) {
+      I[0] = at((cd - fp.par) >> 1);
+      w[0] = 1.0;
+    } else {
+      const int Fi = fp.poff + fine_point_index(fp, i, j, k);
+      if (cd - 1 >= 0) {
+        I[0] = at((cd - 1 - fp.par) >> 1);
+        w[0] = F.Pw[Fi];
+        a[0] = 1;
+      }
+      if (cd + 1 < fp.n[d]) {
+        I[1] = at((cd + 1 - fp.par) >> 1);
+        w[1] = F.Pe[Fi];
+        a[1] = -1;
+      }
+    }
+  }
+  for (int t = 0; t < 2; ++t) {
+    prI[2 * r + t] = I[t];
+    prW[2 * r + t] = w[t];
+    prA[2 * r + t] = a[t];
+    if (I[t] >= 0) marker[I[t]] = 1;
+  }
+}
+
+// The (at most three) fine coupling rows of each coarse row of U_c, by their
+// position a + 1 along d*, with their weights P(f, I).
+__global__ void k_frows(int nr, const int* __restrict__ prI, const double* __restrict__ prW,
+                        const signed char* __restrict__ prA, const int* __restrict__ cu_map,
+                        int* __restrict__ fr, double* __restrict__ frw) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  for (int t = 0; t < 2; ++t) {
+    const int I = prI[2 * r + t];
+    if (I < 0) continue;
+    const int R = cu_map[I];
+    const int slot = 3 * R + prA[2 * r + t] + 1;
+    fr[slot] = r;
+    frw[slot] = prW[2 * r + t];
+  }
 }
 
 __global__ void k_urows(int Nc, const int* __restrict__ scan, const int* __restrict__ marker_flag,
@@ -367,14 +422,20 @@ __global__ void k_urows(int Nc, const int* __restrict__ scan, const int* __restr
 }
 
 // Coarse row R of U_c = P^T U P, one warp per row.  The warp gathers the
-// U rows of the coarse cell's fine points (at most 3 along d*), spreads every
-// entry u_fg over P's row of g (at most 2 columns J) into shared memory, and
-// merges equal columns: candidate t is the first of its column if no earlier
-// candidate has the same J; its output slot is the number of first
-// candidates with a smaller J; its value is the sum over its column in
-// generation order (deterministic).
-constexpr int UW = 1024;     // candidates per warp
-constexpr int UWARPS = 2;    // warps (rows) per block
+// U rows of the coarse cell's fine points (at most 3 along d*, from the
+// fine-row table fr, in the order a = -1, 0, +1), spreads every entry u_fg
+// over P's row of g (at most 2 columns J, precomputed per coupling in pj, pw)
+// into shared memory as candidates t = 0, 1, ... (generation order), sorts
+// the keys (J, t) with a bitonic network, and merges equal columns: each run
+// of equal J is one entry of the row, its slot the number of runs before it
+// (columns ascending), its value the sum of the run's candidates in
+// generation order (t ascending), so the result does not depend on the
+// warp's schedule.  Two instances: UW = 128 candidates per warp and 8 warps
+// per block for the rows whose candidate bound 2 sum_f len(f) is at most
+// 128, UW = 1024 and 2 warps per block for the others (each instance skips
+// the other's rows).
+constexpr int UW_SMALL = 128, UWARPS_SMALL = 8;
+constexpr int UW_LARGE = 1024, UWARPS_LARGE = 2;
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
   int x = v;
@@ -386,78 +447,80 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
   return x - v;
 }
 
-__global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, LevelView<double> C,
-                                                      int nrc, const int* __restrict__ crows,
-                                                      const int* __restrict__ ptr,
-                                                      int* __restrict__ counts,
-                                                      int* __restrict__ col,
-                                                      double* __restrict__ val,
-                                                      float* __restrict__ val32,
-                                                      unsigned char* __restrict__ bits,
-                                                      int* __restrict__ err) {
-  __shared__ int sJ[UWARPS][UW];
-  __shared__ double sV[UWARPS][UW];
-  __shared__ unsigned char sB[UWARPS][UW];
-  __shared__ unsigned char sF[UWARPS][UW];
+template <int UW, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
+                                                   int* __restrict__ longrows,
+                                                   const int* __restrict__ fr,
+                                                   const double* __restrict__ frw,
+                                                   const int* __restrict__ pj,
+                                                   const double* __restrict__ pw,
+                                                   const int* __restrict__ ptr,
+                                                   int* __restrict__ counts, int* __restrict__ col,
+                                                   double* __restrict__ val,
+                                                   float* __restrict__ val32,
+                                                   unsigned char* __restrict__ bits,
+                                                   int* __restrict__ err) {
+  __shared__ unsigned long long sK[WPB][UW];
+  __shared__ double sV[WPB][UW];
+  __shared__ unsigned char sB[WPB][UW];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = blockIdx.x * UWARPS + w;
-  if (R >= nrc) return;
-  int* J = sJ[w];
+  // the small instance walks the rows (one warp each) and, in the counting
+  // pass, lists the rows it leaves to the large one (longrows[0] = number,
+  // then the rows); the large instance is a fixed grid over that list
+  constexpr bool small = UW == UW_SMALL;
+  const int nlong = small ? 0 : *(volatile int*)longrows;
+  for (int it = blockIdx.x * WPB + w; it < (small ? nrc : nlong); it += gridDim.x * WPB) {
+  const int R = small ? it : longrows[1 + it];
+  unsigned long long* K = sK[w];
   double* V = sV[w];
   unsigned char* B = sB[w];
-  unsigned char* first = sF[w];
-
-  const int I = crows[R];
-  const int p = find_part_cell(C.cellstart, C.np, I);
-  const DPart& fp = F.parts[p];
-  const DPart& cp = C.parts[p];
-  int Ic[3];
-  {
-    int cl = I - cp.off;
-    unsigned q = fdiv((unsigned)cl, cp.dx);
-    Ic[0] = cl - (int)q * cp.n[0];
-    Ic[2] = (int)fdiv((unsigned)cl, cp.dxy);
-    Ic[1] = (int)q - Ic[2] * cp.n[1];
-  }
-  const int d = fp.dstar;
-  int n = 0;
-  for (int a = -1; a <= 1; ++a) {
-    int f[3] = {Ic[0], Ic[1], Ic[2]};
-    double w1 = 1.0;
-    if (d < 0) {
-      if (a != 0) continue;
-    } else {
-      f[d] = 2 * Ic[d] + fp.par + a;
-      if (f[d] < 0 || f[d] >= fp.n[d]) continue;
-      if (a != 0) {
-        int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
-        w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
-      }
+  int ur[3], q0[3], q1[3];
+  double w1[3];
+  int ub = 0;
+  for (int a = 0; a < 3; ++a) {
+    ur[a] = fr[3 * R + a];
+    w1[a] = ur[a] >= 0 ? frw[3 * R + a] : 0.0;
+    q0[a] = q1[a] = 0;
+    if (ur[a] >= 0) {
+      q0[a] = F.u_ptr[ur[a]];
+      q1[a] = F.u_ptr[ur[a] + 1];
+      ub += 2 * (q1[a] - q0[a]);
     }
-    const int fg = fp.off + (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-    const int ur = F.u_map[fg];
-    if (ur < 0) continue;
-    const int q0 = F.u_ptr[ur], q1 = F.u_ptr[ur + 1];
-    for (int base = q0; base < q1; base += 32) {
+  }
+  if (small && ub > UW_SMALL) {
+    if (counts && lane == 0) longrows[1 + atomicAdd(longrows, 1)] = R;
+    continue;
+  }
+  int n = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (ur[a] < 0) continue;
+    for (int base = q0[a]; base < q1[a]; base += 32) {
       const int q = base + lane;
-      int Jt[2] = {0, 0};
+      int Jt[2] = {-1, -1};
       double w2[2] = {0.0, 0.0};
-      int m = 0;
-      if (q < q1) {
-        int gq, gi, gj, gk;
-        locate(F, F.parts, F.u_col[q], gq, gi, gj, gk);
-        m = p_row_arrays(F.parts[gq], F.Pw, F.Pe, gi, gj, gk, Jt, w2);
+      double u = 0.0;
+      unsigned char b = 0;
+      if (q < q1[a]) {
+        Jt[0] = pj[2 * q];
+        Jt[1] = pj[2 * q + 1];
+        w2[0] = pw[2 * q];
+        w2[1] = pw[2 * q + 1];
+        u = F.u_val[q];
+        b = F.u_bits[q];
       }
+      const int m = (Jt[0] >= 0) + (Jt[1] >= 0);
       int tot;
       int pos = n + warp_excl_scan(m, lane, tot);
-      if (q < q1) {
-        double v = w1 * F.u_val[q];
-        unsigned char b = F.u_bits[q];
-        for (int t = 0; t < m; ++t)
-          if (pos + t < UW) {
-            J[pos + t] = Jt[t];
-            V[pos + t] = v * w2[t];
-            B[pos + t] = b;
+      if (q < q1[a]) {
+        const double v = w1[a] * u;
+        for (int t = 0; t < 2; ++t)
+          if (Jt[t] >= 0) {
+            if (pos < UW) {
+              K[pos] = ((unsigned long long)(unsigned)Jt[t] << 10) | (unsigned)pos;
+              V[pos] = v * w2[t];
+              B[pos] = b;
+            }
+            ++pos;
           }
       }
       n += tot;
@@ -466,46 +529,54 @@ __global__ void __launch_bounds__(32 * UWARPS) k_urow(LevelView<double> F, Level
   if (n > UW) {
     if (lane == 0) atomicOr(err, 1);
     if (counts) counts[R] = 0;
-    return;
+    continue;
   }
+  // bitonic sort of the keys (padded to a power of two with the largest key)
+  int m = 32;
+  while (m < n) m <<= 1;
+  for (int t = n + lane; t < m; t += 32) K[t] = ~0ull;
   __syncwarp();
-  int nfirst = 0;
-  for (int t = lane; t < n; t += 32) {
-    const int jt = J[t];
-    bool f1 = true;
-    for (int u = 0; u < t; ++u)
-      if (J[u] == jt) {
-        f1 = false;
-        break;
+  for (int k = 2; k <= m; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < m; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long a = K[i], b = K[l];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            K[i] = b;
+            K[l] = a;
+          }
+        }
       }
-    first[t] = f1;
-    nfirst += f1;
-  }
-  for (int o = 16; o > 0; o >>= 1) nfirst += __shfl_xor_sync(0xffffffffu, nfirst, o);
-  if (counts) {
-    if (lane == 0) counts[R] = nfirst;
-    return;
-  }
-  __syncwarp();
-  const int o0 = ptr[R];
-  for (int t = lane; t < n; t += 32) {
-    if (!first[t]) continue;
-    const int jt = J[t];
-    int slot = 0;
-    double v = 0.0;
-    unsigned char b = 0;
-    for (int u = 0; u < n; ++u) {
-      const int ju = J[u];
-      if (first[u] && ju < jt) ++slot;
-      if (ju == jt) {
-        v += V[u];
-        b |= B[u];
-      }
+      __syncwarp();
     }
-    col[o0 + slot] = jt;
-    val[o0 + slot] = v;
-    if (val32) val32[o0 + slot] = (float)v;
-    bits[o0 + slot] = b;
+  // runs of equal columns: starts, their number and (fill) their slots
+  int o0 = counts ? 0 : ptr[R];
+  int run = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const bool start = i < n && (i == 0 || (K[i] >> 10) != (K[i - 1] >> 10));
+    int tot;
+    const int slot = run + warp_excl_scan(start ? 1 : 0, lane, tot);
+    if (start && !counts) {
+      const unsigned long long J = K[i] >> 10;
+      double v = 0.0;
+      unsigned char b = 0;
+      for (int u = i; u < n && (K[u] >> 10) == J; ++u) {
+        const int t = (int)(K[u] & 1023ull);
+        v += V[t];
+        b |= B[t];
+      }
+      col[o0 + slot] = (int)J;
+      val[o0 + slot] = v;
+      if (val32) val32[o0 + slot] = (float)v;
+      bits[o0 + slot] = b;
+    }
+    run += tot;
+  }
+  if (counts && lane == 0) counts[R] = run;
+  __syncwarp();
   }
 }
 
@@ -744,24 +815,49 @@ __global__ void __launch_bounds__(1024) k_scan_sums(int* __restrict__ sums, int 
   if (threadIdx.x == 0) sums[nb] = carry;
 }
 
+// Block b scans items [b SCAN_ITEMS, (b+1) SCAN_ITEMS) in parallel (four
+// consecutive items per thread, shuffle scan of the thread sums, then the
+// warp sums) and adds the block's offset sums[b] (0 without sums: the
+// single-block case).  The last block writes the total to data[n].
 __global__ void __launch_bounds__(NT) k_scan_apply(int* __restrict__ data, long long n,
                                                    const int* __restrict__ sums, int nb) {
+  static_assert(SCAN_ITEMS == 4 * NT, "four items per thread");
   __shared__ int sh[SCAN_ITEMS];
-  long long base = (long long)blockIdx.x * SCAN_ITEMS;
+  __shared__ int wsum[NT / 32];
+  const long long base = (long long)blockIdx.x * SCAN_ITEMS;
   for (int t = threadIdx.x; t < SCAN_ITEMS; t += NT) sh[t] = base + t < n ? data[base + t] : 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = sums[blockIdx.x];
-    for (int t = 0; t < SCAN_ITEMS; ++t) {
-      int v = sh[t];
-      sh[t] = run;
-      run += v;
-    }
+  const int t4 = 4 * (int)threadIdx.x;
+  const int a0 = sh[t4], a1 = sh[t4 + 1], a2 = sh[t4 + 2], a3 = sh[t4 + 3];
+  const int own = a0 + a1 + a2 + a3;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = own;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < NT / 32 ? wsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < NT / 32) wsum[lane] = v;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int off0 = sums ? sums[blockIdx.x] : 0;
+  const int e = off0 + x - own + (w > 0 ? wsum[w - 1] : 0);
+  sh[t4] = e;
+  sh[t4 + 1] = e + a0;
+  sh[t4 + 2] = e + a0 + a1;
+  sh[t4 + 3] = e + a0 + a1 + a2;
   __syncthreads();
   for (int t = threadIdx.x; t < SCAN_ITEMS; t += NT)
     if (base + t < n) data[base + t] = sh[t];
-  if (blockIdx.x == nb - 1 && threadIdx.x == 0) data[n] = sums[nb];
+  if (blockIdx.x == nb - 1 && threadIdx.x == 0)
+    data[n] = sums ? sums[nb] : wsum[NT / 32 - 1];
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -808,10 +904,21 @@ void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t 
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_umark(const Level& F, const Level& Cl, int* marker, cudaStream_t st) {
+void launch_uprow(const Level& F, const Level& Cl, int* prI, double* prW, signed char* prA,
+                  int* marker, cudaStream_t st) {
   SSAMG_CUDA(cudaMemsetAsync(marker, 0, sizeof(int) * (Cl.N + 1), st));
   if (F.nr > 0) {
-    k_umark<<<cdiv(F.nr, NT), NT, 0, st>>>(F.view<double>(), F.nr, F.u_rows, marker);
+    k_uprow<<<cdiv(F.nr, NT), NT, 0, st>>>(F.view<double>(), F.nr, F.u_rows, prI, prW, prA,
+                                          marker);
+    SSAMG_LAUNCH_CHECK();
+  }
+}
+
+void launch_frows(const Level& F, const Level& Cl, const int* prI, const double* prW,
+                  const signed char* prA, int* fr, double* frw, cudaStream_t st) {
+  SSAMG_CUDA(cudaMemsetAsync(fr, 0xff, sizeof(int) * 3 * (size_t)std::max(Cl.nr, 1), st));
+  if (F.nr > 0 && Cl.nr > 0) {
+    k_frows<<<cdiv(F.nr, NT), NT, 0, st>>>(F.nr, prI, prW, prA, Cl.u_map, fr, frw);
     SSAMG_LAUNCH_CHECK();
   }
 }
@@ -821,28 +928,47 @@ void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStrea
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_ucount(const Level& F, const Level& Cl, int* counts, int* err, cudaStream_t st) {
-  if (Cl.nr == 0) return;
-  k_urow<<<cdiv(Cl.nr, UWARPS), 32 * UWARPS, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
-                                                      Cl.u_rows, nullptr, counts, nullptr, nullptr,
-                                                      nullptr, nullptr, err);
+// Both instances of k_urow: the small one over every row, the large one (a
+// grid of a few blocks per SM) over the rows the counting pass listed.
+void launch_urow(const Level& F, const Level& Cl, int* longrows, const int* fr,
+                 const double* frw, const int* ptr, int* counts, int* col, double* val,
+                 float* val32, unsigned char* bits, int* err, cudaStream_t st) {
+  k_urow<UW_SMALL, UWARPS_SMALL><<<cdiv(Cl.nr, UWARPS_SMALL), 32 * UWARPS_SMALL, 0, st>>>(
+      F.view<double>(), Cl.nr, longrows, fr, frw, F.u_pj, F.u_pw, ptr, counts, col, val, val32,
+      bits, err);
+  SSAMG_LAUNCH_CHECK();
+  int dev = 0, sms = 0;
+  SSAMG_CUDA(cudaGetDevice(&dev));
+  SSAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nb = std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms);
+  k_urow<UW_LARGE, UWARPS_LARGE><<<nb, 32 * UWARPS_LARGE, 0, st>>>(
+      F.view<double>(), Cl.nr, longrows, fr, frw, F.u_pj, F.u_pw, ptr, counts, col, val, val32,
+      bits, err);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStream_t st) {
+void launch_ucount(const Level& F, const Level& Cl, int* longrows, const int* fr,
+                   const double* frw, int* counts, int* err, cudaStream_t st) {
   if (Cl.nr == 0) return;
-  k_urow<<<cdiv(Cl.nr, UWARPS), 32 * UWARPS, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr,
-                                                      Cl.u_rows, Cl.u_ptr, nullptr, Cl.u_col,
-                                                      Cl.u_val, fp32 ? Cl.u_val32 : nullptr,
-                                                      Cl.u_bits, err);
-  SSAMG_LAUNCH_CHECK();
+  SSAMG_CUDA(cudaMemsetAsync(longrows, 0, sizeof(int), st));
+  launch_urow(F, Cl, longrows, fr, frw, nullptr, counts, nullptr, nullptr, nullptr, nullptr,
+              err, st);
 }
 
-void launch_ucols(const Level* Fp, const Level& L, bool fp32, cudaStream_t st) {
-  if (L.nnz == 0 || (!L.u_pj && !L.u_rj)) return;
+void launch_ufill(const Level& F, const Level& Cl, int* longrows, const int* fr,
+                  const double* frw, bool fp32, int* err, cudaStream_t st) {
+  if (Cl.nr == 0) return;
+  launch_urow(F, Cl, longrows, fr, frw, Cl.u_ptr, nullptr, Cl.u_col, Cl.u_val,
+              fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, err, st);
+}
+
+void launch_ucols(const Level* Fp, const Level& L, bool fp32, bool pj, bool rj, cudaStream_t st) {
+  int* dpj = pj ? L.u_pj : nullptr;
+  int* drj = rj ? L.u_rj : nullptr;
+  if (L.nnz == 0 || (!dpj && !drj)) return;
   k_ucols<<<cdiv(L.nnz, NT), NT, 0, st>>>(Fp ? Fp->view<double>() : L.view<double>(),
-                                         L.view<double>(), L.nnz, L.u_pj, L.u_pw,
-                                         fp32 ? L.u_pw32 : nullptr, L.u_rj, L.u_rw,
+                                         L.view<double>(), L.nnz, dpj, L.u_pw,
+                                         fp32 ? L.u_pw32 : nullptr, drj, L.u_rw,
                                          fp32 ? L.u_rw32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
@@ -892,6 +1018,11 @@ void launch_scan(int* data, long long n, int* tmp, cudaStream_t st) {
     return;
   }
   int nb = cdiv(n, SCAN_ITEMS);
+  if (nb == 1) {  // one block scans it all
+    k_scan_apply<<<1, NT, 0, st>>>(data, n, nullptr, 1);
+    SSAMG_LAUNCH_CHECK();
+    return;
+  }
   k_scan_reduce<<<nb, NT, 0, st>>>(data, n, tmp);
   SSAMG_LAUNCH_CHECK();
   k_scan_sums<<<1, 1024, 0, st>>>(tmp, nb);

@@ -180,6 +180,35 @@ struct LevelView {
 #define SSAMG_TAIL_CTA_CELLS 4096   // default largest level of the single-CTA tail
 #define SSAMG_BARRIER_SPINS (1u << 24)  // default poll cap: ~1 s of polling before a barrier gives up
 
+// Coarse-level transition run by one thread-block cluster (kernels_tail.cu):
+// per tail level, the rows are split into slices of S rows, one per CTA; a
+// column index packs the owning CTA (high bits) and the position in its slice
+// (SSAMG_CTAIL_LOCAL_BITS low bits).  Offsets are in bytes: vectors within the
+// CTA's vector region, the rest within its read-only region (its image).
+#define SSAMG_CTAIL_THREADS 512
+#define SSAMG_CTAIL_MAX_LEVELS 32
+#define SSAMG_CTAIL_LOCAL_BITS 12
+#define SSAMG_CTAIL_MAX_CTAS 16
+#define SSAMG_CTAIL_CELLS 4096  // default largest level of the cluster tail
+struct CTailLevel {
+  int n, S;                  // cells, rows per CTA slice
+  int tpr;                   // lanes per CSR row in the operator applies (power of two <= 32)
+  int o_x, o_b, o_r;         // the level's vectors
+  int o_rowptr, o_col, o_val, o_dinv;  // CSR of A = S + U (local row pointers), omega M^-1
+  int o_pcol, o_pval;        // P's row of each fine cell (2 per row), to the next level
+  int o_rcol, o_rval;        // restriction row of each coarse cell (3 per row), from the level above
+  int o_inv;                 // coarsest level: rows of the explicit inverse (FP64)
+};
+struct CTailArgs {
+  const char* image;         // NC images of ro_bytes each
+  long long ro_bytes;
+  int vec_bytes;
+  int nt;                    // tail levels (>= 2)
+  int direct;                // 1: coarsest level by the explicit inverse, 0: one relaxation sweep
+  int nL;                    // cells of the coarsest level
+  CTailLevel lev[SSAMG_CTAIL_MAX_LEVELS];
+};
+
 // Grid barrier state (device memory): the arrival counter, the poll cap
 // after which a waiting block gives up, the sticky failure flag, and arrivals
 // expected beyond the launch's own blocks (0; a self-test sets more, so that
@@ -341,10 +370,21 @@ void launch_wsum(const Level& L, double* partial, double* c_out, cudaStream_t st
 double* wsum_static_scratch();
 void launch_interp(const Level& F, bool fp32, cudaStream_t st);
 void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st);
-void launch_umark(const Level& F, const Level& Cl, int* marker, cudaStream_t st);
+// P^T U P (Section 3.3): P rows of the fine coupling rows (prI, prW, prA: two
+// per row) and the marker of the coarse rows; the coarse rows' fine-row table
+// (fr, frw: three per coarse row); the per-row entry counts and the fill.
+// F.u_pj / F.u_pw (P rows of the coupling columns) must be computed first.
+void launch_uprow(const Level& F, const Level& Cl, int* prI, double* prW, signed char* prA,
+                  int* marker, cudaStream_t st);
 void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStream_t st);
-void launch_ucount(const Level& F, const Level& Cl, int* counts, int* err, cudaStream_t st);
-void launch_ufill(const Level& F, const Level& Cl, bool fp32, int* err, cudaStream_t st);
+void launch_frows(const Level& F, const Level& Cl, const int* prI, const double* prW,
+                  const signed char* prA, int* fr, double* frw, cudaStream_t st);
+// longrows: Cl.nr + 1 ints (the rows of more than 128 candidates, which the
+// counting pass lists for the fill pass).
+void launch_ucount(const Level& F, const Level& Cl, int* longrows, const int* fr,
+                   const double* frw, int* counts, int* err, cudaStream_t st);
+void launch_ufill(const Level& F, const Level& Cl, int* longrows, const int* fr,
+                  const double* frw, bool fp32, int* err, cudaStream_t st);
 void launch_umap_level0(const Level& L, cudaStream_t st);
 void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
@@ -377,7 +417,7 @@ void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const
                         double* zprev, double* partial, cudaStream_t st);
 // row-job setup data of L's couplings: P rows (L.u_pj set) and restriction
 // rows from the level above Fp (L.u_rj set)
-void launch_ucols(const Level* Fp, const Level& L, bool fp32, cudaStream_t st);
+void launch_ucols(const Level* Fp, const Level& L, bool fp32, bool pj, bool rj, cudaStream_t st);
 template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
 template <class T>
@@ -404,6 +444,18 @@ int tail_max_blocks();
 // flag (1: a block gave up).  Synchronises st.
 int barrier_selftest(int nblocks, int extra, unsigned cap, cudaStream_t st);
 void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st);
+// cluster tail (kernels_tail.cu)
+void launch_ctail_rowlen(const Level& L, int* len, cudaStream_t st);
+void launch_ctail_fill(bool fp32, const Level& L, const Level* Fm, const Level* Ln,
+                       const double* inv, int nL, const CTailLevel& lv, int Sm, int Sn,
+                       char* image, long long ro_bytes, cudaStream_t st);
+// Allows the tail kernel nc-CTA clusters and smem bytes of shared memory per
+// CTA; false when the device cannot run such a cluster.
+template <class T>
+bool ctail_prepare(int nc, long long smem);
+template <class T>
+void launch_ctail(const CTailArgs& a, int nc, long long smem, const T* b_top, T* x_top,
+                  cudaStream_t st);
 template <class T>
 void launch_coarse_apply(int n, const double* inv, const T* b, T* x, cudaStream_t st);
 void launch_cast_d2f(const double* in, float* out, long long n, cudaStream_t st);

@@ -98,6 +98,7 @@ _SIGS = {
     "ssamg_level_matvec": (_i, [_vp, _i, _vp, _vp, _vp]),
     "ssamg_num_levels": (_i, [_vp]),
     "ssamg_num_parts": (_i, [_vp]),
+    "ssamg_tail_levels": (_i, [_vp, _ip, _ip, ctypes.POINTER(_ll)]),
     "ssamg_level_part_info": (_i, [_vp, _i, _i, _ip, _ip, _ip, _dp, _ip, _ip,
                                    ctypes.POINTER(_ll)]),
     "ssamg_level_sizes": (_i, [_vp, _i, ctypes.POINTER(_ll), ctypes.POINTER(_ll),
@@ -408,6 +409,17 @@ class Solver:
         return {"lo": tuple(lo), "hi": tuple(hi), "dstar": ds.value, "omega": om.value,
                 "offsets": [tuple(offs[3 * e:3 * e + 3]) for e in range(n)],
                 "cell_offset": off.value}
+
+    def tail_levels(self):
+        """(first level, number of levels) of the coarse-level transition run
+        in one cluster (use_tail = 3); (-1, 0) when there is none."""
+        first, ctas = ctypes.c_int(), ctypes.c_int()
+        smem = _ll()
+        n = lib().ssamg_tail_levels(self.h, ctypes.byref(first), ctypes.byref(ctas),
+                                    ctypes.byref(smem))
+        if n < 0:
+            raise SsamgError(n, "tail_levels")
+        return first.value, n
 
     def stored_coefficients(self, level: int) -> int:
         v = _ll()

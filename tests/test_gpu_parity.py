@@ -180,9 +180,9 @@ def test_vcycle_and_matvec_match_oracle(S, prob):
     r = P.SplitMix64(17).uniform_pm1(prob.n)
     rt = torch.as_tensor(r, device="cuda")
     zr = O.vcycle(h, r)
-    # one launch per level and step (default), the cooperative-grid tail and
-    # the single-CTA tail
-    for tail in (0, 1, 2):
+    # one launch per level and step (default), the cooperative-grid tail, the
+    # single-CTA tail and the assembled coarse levels in one cluster
+    for tail in (0, 1, 2, 3):
         grid, A, solver = gpu_setup(S, prob, use_tail=tail)
         z = torch.zeros_like(rt)
         solver.precondition(rt, z)
@@ -193,7 +193,7 @@ def test_vcycle_and_matvec_match_oracle(S, prob):
         solver.level_matvec(l, torch.as_tensor(x, device="cuda"), y)
         assert rel(y.cpu().numpy(), O.matvec(lev, x)) <= OP_TOL, l
     # FP32 cycle against the FP64 cycle
-    for tail in (0, 1, 2):
+    for tail in (0, 1, 2, 3):
         _, _, s32 = gpu_setup(S, prob, precision=1, use_tail=tail)
         z32 = torch.zeros_like(rt)
         s32.precondition(rt, z32)
@@ -207,7 +207,7 @@ def test_pcg_matches_oracle(S, prob):
     bt = torch.as_tensor(b, device="cuda")
     tight = O.pcg(h, b, tol=1e-13, max_iter=500)
     at8 = O.pcg(h, b, tol=1e-8)
-    for graph, tail in ((1, 1), (0, 0), (1, 2)):
+    for graph, tail in ((1, 1), (0, 0), (1, 2), (1, 3), (0, 3)):
         grid, A, solver = gpu_setup(S, prob, tol=1e-13, max_iter=500, use_graph=graph, use_tail=tail)
         x = torch.zeros_like(bt)
         st = solver.solve(bt, x)
@@ -433,3 +433,46 @@ def test_skip_option_matches_oracle(S, prob, prec, mode):
     x = torch.zeros_like(z)
     st = sv.solve(torch.as_tensor(prob.b[0], device="cuda"), x)
     assert abs(st.iterations - ref.iterations) <= 1, (st.iterations, ref.iterations)
+
+
+@pytest.mark.parametrize("prob", [CASES[i] for i in (0, 2, 5, 13, 14, 15, 18, 19)],
+                         ids=[CIDS[i] for i in (0, 2, 5, 13, 14, 15, 18, 19)])
+@pytest.mark.parametrize("cells", [64, 512, 4096])
+def test_cluster_tail_matches_oracle(S, prob, cells):
+    """The coarse-level transition (use_tail = 3, Section 3.5's hybrid idea):
+    the levels from the first of at most `cells` cells down are assembled
+    (A = S + U, P, P^T, smoother diagonal, coarsest inverse) and run in one
+    thread-block cluster.  The V-cycle is the same operation, so it matches
+    the oracle's at 1e-12 (FP64) and 5e-5 (FP32 cycle); with the relaxation
+    sweep on the coarsest level too; PCG iterations at 1e-8 within one; and
+    the tail really runs (its first level is the first of at most `cells`
+    cells below level 0)."""
+    h = O.setup(prob)
+    r = P.SplitMix64(23).uniform_pm1(prob.n)
+    rt = torch.as_tensor(r, device="cuda")
+    zr = O.vcycle(h, r)
+    sizes = [lev.n for lev in h.levels]
+    want = next((l for l in range(1, len(sizes)) if sizes[l] <= cells), len(sizes) - 1)
+    for prec, tol in ((0, OP_TOL), (1, 5e-5)):
+        _, _, sv = gpu_setup(S, prob, precision=prec, flexible=prec, use_tail=3, tail_cells=cells)
+        first, nlev = sv.tail_levels()
+        if want < len(sizes) - 1:
+            assert first == want and nlev == len(sizes) - want, (first, nlev, sizes)
+        else:
+            assert nlev == 0
+        z = torch.zeros_like(rt)
+        sv.precondition(rt, z)
+        assert rel(z.cpu().numpy(), zr) <= tol, prec
+        z2 = torch.zeros_like(rt)
+        sv.precondition(rt, z2)
+        assert torch.equal(z, z2)   # bit for bit from run to run
+    h0 = O.setup(prob, O.Params(coarse_direct=0))
+    _, _, sv = gpu_setup(S, prob, use_tail=3, tail_cells=cells, coarse_direct=0)
+    z = torch.zeros_like(rt)
+    sv.precondition(rt, z)
+    assert rel(z.cpu().numpy(), O.vcycle(h0, r)) <= OP_TOL
+    ref = O.pcg(h, prob.b[0], tol=1e-8)
+    _, _, sv = gpu_setup(S, prob, precision=1, flexible=1, use_tail=3, tail_cells=cells)
+    x = torch.zeros_like(rt)
+    st = sv.solve(torch.as_tensor(prob.b[0], device="cuda"), x)
+    assert st.converged and abs(st.iterations - ref.iterations) <= 1
