@@ -25,8 +25,11 @@ import tempfile
 import threading
 import time
 
+# the oracle's BLAS/OpenMP threads: 1 unless --cpu-threads asks otherwise
+# (set before numpy is imported)
+_THREADS = sys.argv[sys.argv.index("--cpu-threads") + 1] if "--cpu-threads" in sys.argv[:-1] else "1"
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+    os.environ.setdefault(_v, _THREADS)
 
 import numpy as np
 
@@ -38,6 +41,8 @@ import problems as P  # noqa: E402
 METRIC = "SSAMG-PCG setup+solve ms, MDOF/s to 1e-8 rel. res., FP32-cycle vs FP64; %HBM"
 WORKLOAD = "8 parts x 64^3 (2x2x2 layout), 7-pt anisotropic diffusion, seed 1"
 L2_BYTES = 129 * 2 ** 20
+# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def max_over_ranks(value, ws, device=None):
@@ -133,12 +138,19 @@ def flush_l2(buf):
 
 
 def run_ours(args):
+    ws, rank, local = dist_env()
+    # the oracle beside the GPU: started before the first CUDA call
+    beside = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        jobs = ["bench"] + ([] if args.no_extra_workloads else
+                            ["laplace32", "diffusion128", "batched_subset"])
+        beside = OracleBeside(jobs)
+
     import torch
     import torch.distributed as dist
 
     from paper_2205_14273_gb300 import ssamg as S
 
-    ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -161,6 +173,7 @@ def run_ours(args):
     if args.only:
         solvers = {args.only: solvers[args.only]}
     results = {}
+    xs = {}
     for name, sv in solvers.items():
         # warm-up steps (also builds the arena and the CUDA graph)
         for _ in range(args.warmup):
@@ -174,6 +187,7 @@ def run_ours(args):
         st = sv.solve(b, x)
         assert st.converged and st.true_rel_res <= 1.05e-8, (name, st.as_dict())
         verified = st.as_dict()
+        xs[name] = x.cpu().numpy()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         clocks = ClockSampler(local)
@@ -212,6 +226,8 @@ def run_ours(args):
             "wall_s": wall,
             "clocks": ck,
         }
+        tl = sv.tail_levels()
+        results[name]["coarse_transition"] = {"first_level": tl[0], "levels": tl[1]}
         if table is not None:
             results[name]["tile_table"] = tile_summary(table)
 
@@ -219,15 +235,15 @@ def run_ours(args):
         for name, sv in solvers.items():
             level_table(sv, name, stream)
 
-    # ---- dominant-kernel roofline (restriction with the fused pre-relaxation, FP32 cycle)
-    roof = kernel_roofline(S, next(iter(solvers.values())), prob, dev, stream, args)
-
-    # ---- per-kernel HBM fractions on the large levels, and the other two
-    # full-size workloads
+    # ---- roofline of the cycle's operations (all levels, all template instances)
     peak = read_peaks().get("hbm_gbs", 6800.0)
+    roof = cycle_roofline(S, solvers.get("fp32_cycle", next(iter(solvers.values()))), prob, stream, peak)
+
+    # ---- per-kernel HBM fractions on the large levels, and the other
+    # full-size workloads
     hbm = hbm_by_level(solvers.get("fp32_cycle", next(iter(solvers.values()))),
                        "8 parts x 64^3", stream, peak)
-    extra = None if args.no_extra_workloads else extra_workloads(S, stream, peak)
+    extra = None if args.no_extra_workloads else extra_workloads(S, stream, peak, args)
 
     # ---- end to end through the C ABI with host buffers (matrix upload,
     # setup, solve, result read-back)
@@ -265,82 +281,126 @@ def run_ours(args):
     if extra is not None:
         line["other_workloads"] = extra
     line["gpu_launches"] = head["launches"]
-    if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob)
+    if beside is None and extra is not None:
+        strip_private(extra)
+    if beside is not None:
+        got = beside.result()
+        if got is None:
+            line["cpu_baseline"] = {"unavailable": "the oracle process did not finish"}
+            if extra is not None:
+                strip_private(extra)
+        else:
+            meta, arrays = got
+            jb = meta["jobs"]["bench"]
+            tot = jb["setup_s"] + jb["solve_s"]
+            line["cpu_baseline"] = {
+                "value": round(N / tot / 1e6, 5), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                "sample": f"one full oracle setup + PCG to 1e-8 ({jb['iterations']} iterations) "
+                          f"of the whole workload, in a separate process beside the GPU run",
+                "setup_s": round(jb["setup_s"], 3), "solve_s": round(jb["solve_s"], 3),
+                "host": meta["host"]}
+            # the error of each GPU result against the FP64 oracle's solution
+            xo = arrays["bench:x"]
+            for name in xs:
+                line[name]["err_vs_oracle"] = fmt(rel_err(xs[name], xo))
+            line["err_vs_oracle"] = {name: fmt(rel_err(xs[name], xo)) for name in xs}
+            line["err_vs_oracle"]["oracle_iterations"] = jb["iterations"]
+            if extra is not None:
+                oracle_errors(extra, meta, arrays)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
 
 
-def kernel_roofline(S, sv, prob, dev, stream, args):
-    """Roofline of the dominant kernel of the timed step.
+def cycle_roofline(S, sv, prob, stream, peak):
+    """Roofline of the V-cycle's operations, each summed over the levels it
+    runs on and over all its kernel instances (cell tiles, bricks, the
+    precision's template): residual, post-relaxation (on level 0 the last
+    relaxation as the PCG runs it, with the FP64 z and dot partials),
+    restriction (with the coarse level's pre-relaxation and its U x rows),
+    prolongation (with U x rows), level 0's pre-relaxation, and the coarse-
+    level transition's cluster kernel (levels from its first on).  Each
+    launch is timed alone (CUDA-graph replays on the solver's own buffers,
+    CUDA events on the launching stream); achieved = algorithmic bytes / that
+    time.  The operation with the largest summed time is the headline.
 
-    The restriction (k_restrict, which on every level above the coarsest
-    also does the coarse level's pre-relaxation with its U x row jobs) has
-    the largest share of the step in the launch list, the prolongation with
-    U x (k_prolong_u) the next; both run once per level and cycle.
-    achieved = the kernel's algorithmic bytes summed over the levels of one
-    V-cycle / its summed launch durations, each measured with CUDA events
-    around graph replays of that launch on this stream.  Bytes per level
-    (FP32 cycle, w = 4): restriction: fine residual (w N_l), P weights
-    (2 w per fine point), coarse right-hand side out (w N_{l+1}) and, when
-    fused, omega M^-1 in and x out (2 w N_{l+1}) and the coarse level's
-    coupling rows (12 per row) and couplings (44 each: column, value,
-    restriction row of the column, its diagonal, three fine residuals);
-    prolongation: x in + x out (8 N_l), coarse correction (4 N_{l+1}),
-    P weights (8 per fine point), coupling rows (12 per row) and couplings
-    (36 each: column, value, P row of the column, x and two coarse values).
-    """
-    peaks = read_peaks()
+    Algorithmic bytes per level (FP32 cycle, w = 4; sc = stored per-cell
+    coefficients of the level, nr/nnz its coupling rows and entries):
+    residual w (sc + 3 N) + 4 nr; post-relaxation w (sc + 4 N) + 4 nr (level
+    0: + 8 N FP64 r in, 8 N FP64 z out, 16 N FP64 zprev in/out);
+    restriction w N_l + w N_{l+1} + 2 w (N_l - N_{l+1}) (+ 2 w N_{l+1} +
+    12 nr + 44 nnz of the next level when it pre-relaxes there); prolongation
+    8 N_l + 4 N_{l+1} + 8 (N_l - N_{l+1}) + 12 nr + 36 nnz; pre-relaxation
+    (level 0) 8 N (FP64 r in) + 2 w N + 12 nr + 12 nnz."""
     L = sv.num_levels()
     sizes = [sv.level_sizes(l) for l in range(L)]
+    first, ntail = sv.tail_levels()
+    lt = first if ntail else L - 1        # levels below lt run per-level kernels
     w = 4
+    sc = [sv.stored_coefficients(l) for l in range(L)]
 
-    def restrict_bytes(l):
+    def b_res(l):
+        N, nr, _ = sizes[l]
+        return w * (sc[l] + 3 * N) + 4 * nr
+
+    def b_relax(l):
+        N, nr, _ = sizes[l]
+        return w * (sc[l] + 4 * N) + 4 * nr + (32 * N if l == 0 else 0)
+
+    def b_restrict(l):
         N = sizes[l][0]
         Nc, nrc, nnzc = sizes[l + 1]
-        pre = 2 * w * Nc + 12 * nrc + 44 * nnzc if l + 2 < L else 0
+        pre = 2 * w * Nc + 12 * nrc + 44 * nnzc if l + 1 < lt else 0
         return w * N + w * Nc + 2 * w * (N - Nc) + pre
 
-    def prolong_bytes(l):
+    def b_prolong(l):
         N, nr, nnz = sizes[l]
         Nc = sizes[l + 1][0]
         return 8 * N + 4 * Nc + 8 * (N - Nc) + 12 * nr + 36 * nnz
 
-    peak = peaks.get("hbm_gbs", 6800.0)
+    def b_pre(l):
+        N, nr, nnz = sizes[l]
+        return 8 * N + 2 * w * N + 12 * nr + 12 * nnz
 
-    def over_levels(kid, nbytes, name):
-        tot_us = tot_b = 0.0
-        per_level = []
-        for l in range(L - 1):
-            us = sv.time_kernel(kid, l, 50, stream)
-            tot_us += us
-            tot_b += nbytes(l)
-            per_level.append(round(us, 2))
-        nl = L - 1
-        achieved = tot_b / (tot_us * 1e-6) / 1e9
-        return {
-            "kernel": name,
-            "bound": "hbm",
-            "achieved": round(achieved, 1),
-            "peak": peak,
-            "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-            "traffic": None,
-            "bytes_per_launch": int(tot_b / nl),
-            "us_per_launch": round(tot_us / nl, 3),
-            "us_per_level": per_level,
-        }
-
-    out = over_levels(3, restrict_bytes,
-                      "k_restrict<float> (restriction P^T r, with the coarse level's "
-                      "pre-relaxation and U x row jobs), all levels of one V-cycle")
-    out["second_kernel"] = over_levels(
-        4, prolong_bytes,
-        "k_prolong_u<float> (prolongation x + P e with U x row jobs), all levels of one V-cycle")
-    # the FP64 level-0 operator apply + dot (the PCG's largest single launch)
+    ops = {
+        "residual": (lambda l: 0, b_res, range(lt)),
+        "post_relaxation": (lambda l: 9 if l == 0 else 1, b_relax, range(lt)),
+        "restriction": (lambda l: 3, b_restrict, range(lt)),
+        "prolongation": (lambda l: 4, b_prolong, range(lt)),
+        "pre_relaxation_level0": (lambda l: 2, b_pre, range(1)),
+    }
+    by_op = {}
+    for name, (kid, nbytes, levels) in ops.items():
+        us = [sv.time_kernel(kid(l), l, 50, stream) for l in levels]
+        tb = sum(nbytes(l) for l in levels)
+        tus = sum(us)
+        gbs = tb / (tus * 1e-6) / 1e9
+        by_op[name] = {"levels": len(us), "us": round(tus, 2), "bytes": int(tb),
+                       "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                       "us_per_level": [round(u, 2) for u in us]}
+    if ntail:
+        by_op["coarse_transition_cluster"] = {
+            "levels": ntail, "first_level": first, "us": round(sv.time_kernel(10, 0, 50, stream), 2),
+            "bound": "latency (cluster barriers and remote shared-memory round trips)"}
+    cycle_us = sv.time_kernel(5, 0, 20, stream)
+    top = max((k for k in ops), key=lambda k: by_op[k]["us"])
+    t = by_op[top]
+    nl = t["levels"]
+    out = {
+        "kernel": f"{top} of the FP32 V-cycle, all its kernel instances, levels 0..{lt - 1} "
+                  f"(the operation with the largest summed launch time)",
+        "bound": "hbm", "achieved": t["achieved_gbs"], "peak": peak, "unit": "GB/s",
+        "frac": t["frac"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+        "traffic": None,
+        "traffic_note": "the 2M-cell levels' data stays in the 129 MB L2 between launches, so "
+                        "DRAM counters read below the algorithmic bytes; the HBM-resident "
+                        "case is in other_workloads and profiles/",
+        "bytes_per_launch": int(t["bytes"] / max(nl, 1)), "us_per_launch": round(t["us"] / max(nl, 1), 3),
+        "v_cycle_us": round(cycle_us, 1),
+        "by_operation": by_op,
+    }
+    # the PCG's FP64 level-0 operator apply + dot (bound by the FP64 pipe)
     us_spmv = sv.time_kernel(6, 0, 50, stream)
     N0 = sizes[0][0]
     flops = 2 * 8 * N0 + 2 * prob.nnz_u
@@ -348,8 +408,8 @@ def kernel_roofline(S, sv, prob, dev, stream, args):
         "kernel": "k7b_spmv_dot (q = A p and p.q, FP64, level 0 bricks)",
         "bound": "alu", "unit": "TFLOP/s",
         "achieved": round(flops / (us_spmv * 1e-6) / 1e12, 4),
-        "peak": 1.25, "peak_source": "nominal GB300 FP64; 1.255 measured by an FMA probe",
-        "frac": round(flops / (us_spmv * 1e-6) / 1.25e12, 4),
+        "peak": FP64_PEAK_TFLOPS, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+        "frac": round(flops / (us_spmv * 1e-6) / (FP64_PEAK_TFLOPS * 1e12), 4),
         "us_per_launch": round(us_spmv, 2),
         "hbm_gbs": round((24 * N0 + 16 * prob.nnz_u) / (us_spmv * 1e-6) / 1e9, 1)}
     return out
@@ -433,42 +493,97 @@ def tile_summary(table):
             for c, t in enumerate(table) if t}
 
 
-def extra_workloads(S, stream, peak):
-    """The 256^3 27-point workload and the 64-problem batched workload at full
-    size: setup and solve times (one step after a warm-up) in both cycle
-    precisions, and the per-kernel HBM fractions of their large levels; and
-    the 128^3 differentiation workload."""
+def timed_steps(stream, nsteps, setup, solve, local=0):
+    """nsteps setup + solve steps, each bracketed by CUDA events on `stream`,
+    with nvidia-smi clocks sampled meanwhile; medians (ms) and the clocks."""
+    import torch
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsteps)]
+    ck = ClockSampler(local)
+    torch.cuda.synchronize()
+    ck.start()
+    last = None
+    for e in ev:
+        e[0].record(stream)
+        setup()
+        e[1].record(stream)
+        last = solve()
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    clocks = ck.stop()
+    su = [e[0].elapsed_time(e[1]) for e in ev]
+    so = [e[1].elapsed_time(e[2]) for e in ev]
+    return statistics.median(su), statistics.median(so), clocks, last
+
+
+def golden_var27():
+    path = os.path.join(ROOT, "tests", "golden", "var27_256_oracle.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def extra_workloads(S, stream, peak, args):
+    """The other full-size workloads: 32^3 Laplacian (FP64; latency),
+    256^3 27-point, the 64-problem batch and the 128^3 differentiation
+    workload: setup and solve times (median of 5 steps after a warm-up,
+    clocks sampled), per-kernel HBM fractions of the large levels, and each
+    solution's error against the FP64 oracle (256^3: on the oracle's stored
+    samples; batch: on its eight smallest problems; the rest in full)."""
     import torch
     out = {}
+    nst = 5
+    # ---- 32^3 Laplacian, plain FP64 (reported as latency)
+    prob = P.config(0)
+    grid, A = S.matrix_from_problem(prob)
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    x = torch.zeros_like(b)
+    sv = S.Solver(tol=1e-8, max_iter=500)
+    sv.setup(A)
+    st = sv.solve(b, x)
+    su, so, ck, _ = timed_steps(stream, 10, lambda: sv.setup(A), lambda: sv.solve_nostats(b, x))
+    out["laplace_32"] = {"workload": "1 part 32^3, 7-point Laplacian, FP64 cycle, seed 0",
+                         "unknowns": prob.n, "setup_ms": round(su, 3), "solve_ms": round(so, 3),
+                         "latency_ms": round(su + so, 3), "iterations": st.iterations,
+                         "mdof_s": round(prob.n / ((su + so) * 1e-3) / 1e6, 3), "steps": 10,
+                         "clocks": ck, "_x": x.cpu().numpy()}
+    del A, grid, sv
+    # ---- 256^3 27-point
     prob = P.config(2)
     grid, A = S.matrix_from_problem(prob)
     b = torch.as_tensor(prob.b[0], device="cuda")
     res = {"workload": "1 part 256^3, 27-point variable coefficients, seed 2",
            "unknowns": prob.n}
+    gold = golden_var27()
     for prec, name in ((1, "fp32_cycle"), (0, "fp64")):
         sv = S.Solver(precision=prec, flexible=prec, tol=1e-8, max_iter=500)
         sv.setup(A)
         x = torch.zeros_like(b)
         st = sv.solve(b, x)
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
-        sv.setup(A)
-        e[1].record(stream)
-        sv.solve_nostats(b, x)
-        e[2].record(stream)
-        torch.cuda.synchronize()
-        t_s, t_v = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-        res[name] = {"setup_ms": round(t_s, 3), "solve_ms": round(t_v, 3),
+        su, so, ck, _ = timed_steps(stream, nst, lambda: sv.setup(A), lambda: sv.solve_nostats(b, x))
+        res[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3),
                      "iterations": st.iterations, "true_rel_res": fmt(st.true_rel_res),
-                     "levels": st.num_levels,
-                     "mdof_s": round(prob.n / ((t_s + t_v) * 1e-3) / 1e6, 3)}
+                     "levels": st.num_levels, "steps": nst, "clocks": ck,
+                     "mdof_s": round(prob.n / ((su + so) * 1e-3) / 1e6, 3)}
+        if gold is not None:
+            cells = np.array(gold["pcg"]["cells"])
+            xo = np.array(gold["pcg"]["x"])
+            xg = x.cpu().numpy()[cells]
+            res[name]["err_vs_oracle"] = {
+                "sampled_rel_err": fmt(rel_err(xg, xo)), "samples": len(cells),
+                "norm_ratio": fmt(float(x.norm()) / gold["pcg"]["x_norm"]),
+                "oracle_iterations": gold["pcg"]["iterations"]}
         if prec == 1:
             res["hbm"] = hbm_by_level(sv, res["workload"], stream, peak)
+        del sv
     out["var27_256"] = res
     del A, grid
+    # ---- 64 problems x 4 right-hand sides
     probs = P.config(3)
     mats = [S.matrix_from_problem(p) for p in probs]
     nrhs = probs[0].b.shape[0]
+    sel = batched_subset(probs)
     res = {"workload": f"{len(probs)} problems, 1-8 chained parts each, edges 16-96, "
                        f"{nrhs} right-hand sides, seed 3"}
     for prec, name in ((1, "fp32_cycle"), (0, "fp64")):
@@ -480,34 +595,24 @@ def extra_workloads(S, stream, peak):
         bb = torch.as_tensor(bh, device="cuda")
         xx = torch.zeros_like(bb)
         B.setup()
-        st = B.solve(bb, xx, nrhs)
-
-        def timed():
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-            B.setup()
-            e[1].record(stream)
-            st = B.solve(bb, xx, nrhs)
-            e[2].record(stream)
-            torch.cuda.synchronize()
-            return st, e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-
-        # built-in tiles, then the autotuner's table (the reported step)
-        _, u_s, u_v = timed()
+        B.solve(bb, xx, nrhs)
+        su_u, so_u, _, _ = timed_steps(stream, 1, B.setup, lambda: B.solve(bb, xx, nrhs))
         t0 = time.perf_counter()
         table = B.autotune(reps=10)
         tune_s = time.perf_counter() - t0
         B.solve(bb, xx, nrhs)
-        st, t_s, t_v = timed()
-        its = [s.iterations for row in st for s in row]
+        su, so, ck, st = timed_steps(stream, nst, B.setup, lambda: B.solve(bb, xx, nrhs))
+        its = [s_.iterations for row in st for s_ in row]
         res["unknowns"] = off[-1]
-        res[name] = {"setup_ms": round(t_s, 3), "solve_ms": round(t_v, 3),
+        xh = xx.cpu().numpy()
+        res[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3), "steps": nst, "clocks": ck,
                      "tile_table": tile_summary(table), "autotune_s": round(tune_s, 2),
-                     "builtin_tiles": {"setup_ms": round(u_s, 3), "solve_ms": round(u_v, 3)},
+                     "builtin_tiles": {"setup_ms": round(su_u, 3), "solve_ms": round(so_u, 3)},
                      "iterations_max": max(its), "iterations_mean": round(float(np.mean(its)), 2),
-                     "worst_true_rel_res": fmt(max(s.true_rel_res for row in st for s in row)),
+                     "worst_true_rel_res": fmt(max(s_.true_rel_res for row in st for s_ in row)),
                      "levels": st[0][0].num_levels,
-                     "mdof_s": round(off[-1] * nrhs / ((t_s + t_v) * 1e-3) / 1e6, 3)}
+                     "mdof_s": round(off[-1] * nrhs / ((su + so) * 1e-3) / 1e6, 3),
+                     "_x": {f"{k}_{j}": xh[j, off[k]:off[k + 1]].copy() for k in sel for j in range(nrhs)}}
         if prec == 1:
             res["hbm"] = hbm_by_level(B.solver(), res["workload"], stream, peak)
         del B
@@ -516,13 +621,54 @@ def extra_workloads(S, stream, peak):
     return out
 
 
+def oracle_errors(extra, meta, arrays):
+    """Fills err_vs_oracle of the other workloads from the oracle run beside
+    (and drops the solution vectors kept for it)."""
+    jobs = meta["jobs"]
+    lap = extra.get("laplace_32")
+    if lap is not None:
+        x = lap.pop("_x")
+        if "laplace32" in jobs:
+            lap["err_vs_oracle"] = fmt(rel_err(x, arrays["laplace32:x"]))
+            lap["oracle_iterations"] = jobs["laplace32"]["iterations"]
+    bat = extra.get("batched_64")
+    if bat is not None:
+        for name in ("fp32_cycle", "fp64"):
+            xs = bat[name].pop("_x", {})
+            if "batched_subset" in jobs and xs:
+                errs = [rel_err(v, arrays[f"batched_subset:x:{k}"]) for k, v in xs.items()]
+                bat[name]["err_vs_oracle"] = {"max_rel_err": fmt(max(errs)), "instances": len(errs),
+                                              "problems": jobs["batched_subset"]["problems"]}
+    dif = extra.get("diffusion_128")
+    if dif is not None:
+        x, dg = dif.pop("_x"), dif.pop("_dg")
+        if "diffusion128" in jobs:
+            dif["err_vs_oracle"] = {"x": fmt(rel_err(x, arrays["diffusion128:x"])),
+                                    "dL_dg": fmt(rel_err(dg, arrays["diffusion128:dg"])),
+                                    "oracle_iterations": [jobs["diffusion128"]["iterations"],
+                                                          jobs["diffusion128"]["adjoint_iterations"]]}
+
+
+def strip_private(extra):
+    """Drops the solution vectors kept for the oracle comparison (no oracle run)."""
+    for w in extra.values():
+        if isinstance(w, dict):
+            for k in [k for k in w if k.startswith("_")]:
+                w.pop(k)
+            for v in w.values():
+                if isinstance(v, dict):
+                    for k in [k for k in v if k.startswith("_")]:
+                        v.pop(k)
+
+
 def differentiation_workload(S, stream, peak):
     """The differentiation form at full size (128^3, kappa = exp(g), FP64):
     setup, forward solve, adjoint solve A lambda = x - x_t on the same
-    hierarchy, and dL/dg, each timed with CUDA events after a warm-up step;
-    the gradient kernels' HBM fractions (k_diffusion_exp_gradient: g, lambda,
-    x in and dL/dg out, 32 B per cell; k_coef_gradient: lambda and x in, the
-    7 entries' dL/da out, 72 B per cell)."""
+    hierarchy, and dL/dg, each timed with CUDA events (median of 5 steps after
+    a warm-up step); the gradient kernels' HBM fractions
+    (k_diffusion_exp_gradient: g, lambda, x in and dL/dg out, 32 B per cell;
+    k_coef_gradient: lambda and x in, the 7 entries' dL/da out, 72 B per
+    cell)."""
     import torch
     prob = P.config(4)
     N = prob.n
@@ -550,10 +696,13 @@ def differentiation_workload(S, stream, peak):
         return st_f, st_a
 
     step()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-    st_f, st_a = step(ev)
-    torch.cuda.synchronize()
-    t = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+    ts = []
+    for _ in range(5):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        st_f, st_a = step(ev)
+        torch.cuda.synchronize()
+        ts.append([ev[k].elapsed_time(ev[k + 1]) for k in range(4)])
+    t = [statistics.median(c) for c in zip(*ts)]
 
     def kernel_us(fn, reps=20):
         fn()
@@ -569,13 +718,14 @@ def differentiation_workload(S, stream, peak):
     us_dc = kernel_us(lambda: sv.coef_gradient(lam, x, dcoef))
     frac = lambda nb, us: round(nb / (us * 1e-6) / 1e9 / peak, 3)
     return {"workload": "1 part 128^3, 7-point harmonic-mean diffusion, kappa = exp(g), seed 4",
-            "unknowns": N, "precision": "fp64",
+            "unknowns": N, "precision": "fp64", "steps": 5,
             "setup_ms": round(t[0], 3), "forward_solve_ms": round(t[1], 3),
             "adjoint_solve_ms": round(t[2], 3), "gradient_ms": round(t[3], 3),
             "forward_iterations": st_f.iterations, "adjoint_iterations": st_a.iterations,
             "mdof_s": round(N / (sum(t) * 1e-3) / 1e6, 3),
             "k_diffusion_exp_gradient": {"us": round(us_dg, 2), "frac_hbm": frac(32 * N, us_dg)},
-            "k_coef_gradient": {"us": round(us_dc, 2), "frac_hbm": frac(72 * N, us_dc)}}
+            "k_coef_gradient": {"us": round(us_dc, 2), "frac_hbm": frac(72 * N, us_dc)},
+            "_x": x.cpu().numpy(), "_dg": dg.cpu().numpy()}
 
 
 def read_peaks():
@@ -628,67 +778,216 @@ def end_to_end(S, prob, dev, stream, args):
             "includes": "grid+matrix creation from pinned host arrays, assemble, setup, solve, x read-back"}
 
 
-def cpu_baseline(prob, sample_iters=2):
-    """The oracle on the host: full setup plus the first `sample_iters` PCG
-    iterations timed, extrapolated by the oracle's own iteration count."""
-    from oracle import ssamg as O
-    t0 = time.perf_counter()
-    h = O.setup(prob)
-    t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.pcg(h, prob.b[0], max_iter=sample_iters)
-    t_it = (time.perf_counter() - t0) / sample_iters
-    iters = O.pcg(h, prob.b[0]).iterations
-    total = t_setup + iters * t_it
-    return {"value": round(prob.n / total / 1e6, 5), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"full setup + {sample_iters} of {iters} PCG iterations timed, extrapolated",
-            "setup_s": round(t_setup, 3), "s_per_iteration": round(t_it, 4),
-            "host": host_info()}
-
-
+# ---------------------------------------------------------------------------
+# The CPU oracle beside the GPU (cpu_baseline, the errors against the FP64
+# oracle, the reference arm).  Every oracle run is a full setup and a full
+# PCG solve to the workload's tolerance, timed as it stands (never tuned).
+# ---------------------------------------------------------------------------
 def host_info():
+    info = {"nproc": os.cpu_count()}
     try:
         import platform
-        return {"nproc": os.cpu_count(), "machine": platform.machine()}
+        info["machine"] = platform.machine()
     except Exception:
-        return {}
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                info["cpu_model"] = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        cfg = np.show_config(mode="dicts")
+        info["blas"] = cfg["Build Dependencies"]["blas"]["name"]
+    except Exception:
+        pass
+    info["numpy"] = np.__version__
+    info["threads_env"] = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    return info
+
+
+def batched_subset(probs, k=8):
+    """The k problems of the batched workload with the fewest cells."""
+    return sorted(range(len(probs)), key=lambda i: (probs[i].n, i))[:k]
+
+
+def oracle_run(job):
+    """One timed oracle job (full setup and PCG to 1e-8); returns its timings
+    and the solution vectors (numpy)."""
+    from oracle import ssamg as O
+    out = {}
+    if job in ("bench", "laplace32"):
+        prob = P.config(1 if job == "bench" else 0)
+        t0 = time.perf_counter()
+        h = O.setup(prob)
+        t1 = time.perf_counter()
+        r = O.pcg(h, prob.b[0], tol=1e-8, max_iter=500)
+        t2 = time.perf_counter()
+        out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "iterations": r.iterations,
+               "true_rel_res": r.true_rel_res, "unknowns": prob.n, "x": r.x}
+    elif job == "diffusion128":
+        prob = P.config(4)
+        t0 = time.perf_counter()
+        h = O.setup(prob)
+        t1 = time.perf_counter()
+        r = O.pcg(h, prob.b[0], tol=1e-8, max_iter=500)
+        t2 = time.perf_counter()
+        ra = O.pcg(h, r.x - prob.extra["x_t"], tol=1e-8, max_iter=500)
+        t3 = time.perf_counter()
+        dg = O.diffusion_exp_gradient(prob.extra["g"], ra.x, r.x).reshape(-1)
+        t4 = time.perf_counter()
+        out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "adjoint_s": t3 - t2, "gradient_s": t4 - t3,
+               "iterations": r.iterations, "adjoint_iterations": ra.iterations,
+               "unknowns": prob.n, "x": r.x, "dg": dg}
+    elif job == "batched_subset":
+        probs = P.config(3)
+        sel = batched_subset(probs)
+        xs, its = {}, []
+        t0 = time.perf_counter()
+        n = 0
+        for k in sel:
+            h = O.setup(probs[k])
+            for j in range(probs[k].b.shape[0]):
+                r = O.pcg(h, probs[k].b[j], tol=1e-8, max_iter=500)
+                xs[f"{k}_{j}"] = r.x
+                its.append(r.iterations)
+                n += probs[k].n
+        out = {"problems": sel, "seconds": time.perf_counter() - t0, "unknowns_x_rhs": n,
+               "iterations": its, "x": xs}
+    return out
+
+
+def oracle_worker(out_path, jobs):
+    """Spawned process: the oracle jobs in turn; timings to JSON, vectors to
+    an .npz beside it."""
+    res, arrays = {}, {}
+    for job in jobs:
+        r = oracle_run(job)
+        for key in list(r):
+            v = r[key]
+            if isinstance(v, np.ndarray):
+                arrays[f"{job}:{key}"] = r.pop(key)
+            elif isinstance(v, dict):
+                for kk, vv in r.pop(key).items():
+                    arrays[f"{job}:{key}:{kk}"] = vv
+        res[job] = r
+    np.savez(out_path + ".npz", **arrays)
+    with open(out_path + ".json", "w") as f:
+        json.dump({"jobs": res, "host": host_info()}, f)
+
+
+class OracleBeside:
+    """The oracle jobs in a spawned process (started before the first GPU call,
+    so that no CUDA state is inherited), running while the GPU is timed."""
+
+    def __init__(self, jobs):
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="ssamg_oracle_")
+        self.path = os.path.join(self.dir, "oracle")
+        self.proc = mp.get_context("spawn").Process(target=oracle_worker, args=(self.path, jobs))
+        self.proc.start()
+
+    def result(self, timeout=900):
+        self.proc.join(timeout)
+        if self.proc.is_alive():
+            self.proc.terminate()
+            return None
+        if self.proc.exitcode != 0 or not os.path.exists(self.path + ".json"):
+            return None
+        with open(self.path + ".json") as f:
+            meta = json.load(f)
+        arrays = dict(np.load(self.path + ".npz"))
+        return meta, arrays
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (there is no reference code) on this
+    workload, timed as it stands on the host cores: each step is one full
+    setup and one full PCG solve to 1e-8 of the 8 x 64^3 workload.  A step
+    takes ~20 s, so the arm runs min(steps, 3) steps after one untimed small
+    warm-up run and reports the median; steps/warmup requested are recorded."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     from oracle import ssamg as O
     prob = P.config(1)
     N = prob.n
-    # the oracle's own iteration count (one full solve, untimed)
-    h = O.setup(prob)
-    iters = O.pcg(h, prob.b[0]).iterations
-    sample_iters = 2
-    for _ in range(args.warmup):
-        O.vcycle(h, prob.b[0])
-    times = []
-    for _ in range(args.steps):
+    small = P.config(1, small=True)
+    O.pcg(O.setup(small), small.b[0], tol=1e-8)
+    nsteps = max(1, min(args.steps, 3))
+    times, its = [], []
+    for _ in range(nsteps):
         t0 = time.perf_counter()
         h = O.setup(prob)
-        t_setup = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        O.pcg(h, prob.b[0], max_iter=sample_iters)
-        t_it = (time.perf_counter() - t0) / sample_iters
-        times.append(t_setup + iters * t_it)
+        r = O.pcg(h, prob.b[0], tol=1e-8, max_iter=500)
+        times.append(time.perf_counter() - t0)
+        its.append(r.iterations)
     step_s = statistics.median(times)
     v = N / step_s / 1e6
+    host = host_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "MDOF/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": ws, "steps": nsteps, "warmup": 1, "steps_requested": args.steps,
+        "warmup_requested": args.warmup,
         "ms_per_step": round(step_s * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "unknowns": N, "tol": 1e-8, "parallelism": "cpu"},
         "cpu_baseline": {"value": round(v, 5), "unit": "MDOF/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: full setup + {sample_iters} of {iters} PCG iterations, extrapolated"},
+                         "sample": f"per step: one full oracle setup + PCG to 1e-8 "
+                                   f"({its[0]} iterations) of the whole workload; "
+                                   f"median of {nsteps} steps",
+                         "host": host},
         "e2e": {"value": round(v, 5), "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_cpu_table(args):
+    """Oracle timings for the five workloads (the benchmark's table): setup and
+    solve seconds, iterations, MDOF/s, with the threads given by
+    --cpu-threads (BLAS/OpenMP variables; the oracle's numpy array arithmetic
+    runs on one core either way).  Median of 3 runs for the 32^3 and 8 x 64^3
+    workloads, one run for the others; the batched workload on its eight
+    smallest problems (all right-hand sides), scaled by unknowns."""
+    out = {"threads": args.cpu_threads, "host": host_info(), "workloads": {}}
+    for job, reps in (("laplace32", 3), ("bench", 3), ("diffusion128", 1), ("batched_subset", 1)):
+        runs = [oracle_run(job) for _ in range(reps)]
+        for r in runs:
+            for k in list(r):
+                if isinstance(r[k], (np.ndarray, dict)):
+                    r.pop(k)
+        if job == "batched_subset":
+            r = runs[0]
+            out["workloads"][job] = {"seconds": r["seconds"], "unknowns_x_rhs": r["unknowns_x_rhs"],
+                                     "mdof_s": r["unknowns_x_rhs"] / r["seconds"] / 1e6,
+                                     "iterations_max": max(r["iterations"]),
+                                     "problems": r["problems"]}
+            continue
+        tot = [r["setup_s"] + r["solve_s"] + r.get("adjoint_s", 0) + r.get("gradient_s", 0) for r in runs]
+        med = sorted(range(reps), key=lambda i: tot[i])[reps // 2]
+        r = runs[med]
+        r["total_s"] = tot[med]
+        r["mdof_s"] = r["unknowns"] / tot[med] / 1e6
+        r["runs"] = reps
+        out["workloads"][job] = r
+    if args.cpu_var27:
+        from oracle import ssamg as O
+        prob = P.config(2)
+        t0 = time.perf_counter()
+        h = O.setup(prob)
+        t1 = time.perf_counter()
+        r = O.pcg(h, prob.b[0], tol=1e-8, max_iter=500)
+        t2 = time.perf_counter()
+        out["workloads"]["var27_256"] = {"setup_s": t1 - t0, "solve_s": t2 - t1,
+                                         "iterations": r.iterations, "unknowns": prob.n,
+                                         "mdof_s": prob.n / (t2 - t0) / 1e6, "runs": 1}
+    print(json.dumps(out), flush=True)
 
 
 def run_profile_case(args):
@@ -741,7 +1040,16 @@ def main():
     ap.add_argument("--levels", action="store_true",
                     help="also write, to stderr, each cycle kernel's time per level "
                          "(CUDA-graph replays of that launch alone)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the CPU oracle on the workloads (no GPU) and print one JSON line")
+    ap.add_argument("--cpu-threads", type=int, default=1,
+                    help="BLAS/OpenMP threads for --cpu-table")
+    ap.add_argument("--cpu-var27", action="store_true",
+                    help="with --cpu-table, also the 256^3 27-point workload (minutes)")
     args = ap.parse_args()
+    if args.cpu_table:
+        run_cpu_table(args)
+        return
     if args.profile_case:
         run_profile_case(args)
         return

@@ -6,14 +6,14 @@ Calls only the oracle (oracle/ssamg.py) and the input generators
 (problems/).  Contents:
 
 * levels 0-4 of the hierarchy (Sections 3.1-3.3): cell count, coarsening
-  direction, the largest |coefficient| of the level, and at 2,048 sampled
+  direction, the largest |coefficient| of the level, and at 256 sampled
   cells (plus the eight corners of the box) all 27 stencil entries in
   offset-code order ((ox+1) + 3 (oy+1) + 9 (oz+1)), the smoother diagonal
   omega M^-1 (Eq. relax0/relax1) and, for levels 0-3, the interpolation
   weights PW, PE (Eq. prolEx; zero at coarse points);
 * PCG with one V(1,1) cycle per iteration (Section 4) from x0 = 0 to
   ||r|| <= 1e-8 ||b||: iteration count, recursive and true relative
-  residuals, ||x||_2, and x at 4,096 sampled cells.
+  residuals, ||x||_2, and x at 2,048 sampled cells.
 
 Runs for tens of minutes on one host core and needs ~20 GB of memory:
 
@@ -34,8 +34,8 @@ from oracle import ssamg as O  # noqa: E402
 
 OUT = os.path.join(HERE, "var27_256_oracle.json")
 NLEV = 5
-NSAMPLE = 2048
-NX = 4096
+NSAMPLE = 256
+NX = 2048
 
 
 def code_of(o):
