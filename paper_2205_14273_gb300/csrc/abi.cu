@@ -723,6 +723,9 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     bblk[p + 1] = bblk[p] + (int)nb;
   }
   L.nbblk = bblk[np];
+  L.brick_fill = L.nbblk ? (double)ntot / ((double)L.nbblk * SSAMG_BRICK_X * SSAMG_BRICK_Y *
+                                           SSAMG_BRICK_Z)
+                         : 0.0;
   L.hbblk = bblk;
   L.hblk = blk;
   for (int p = 0; p < np; ++p) {

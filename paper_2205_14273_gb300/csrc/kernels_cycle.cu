@@ -469,6 +469,277 @@ struct PCol {
   T w0, w1;
 };
 
+// ---------------------------------------------------------------------------
+// Restriction and prolongation over bricks.  On levels whose bricks are well
+// filled, a block takes a 32 x 8 x 8 brick of one part and each thread walks
+// one (i, j) column along z.  The code is specialised per coarsening
+// direction D of the part (block-uniform): the row of P (or of P^T) of a
+// cell follows from the column's fixed coordinates and k by running index
+// updates, not from a division per cell.  A column's setup data (P weights,
+// smoother diagonal) is fetched before the wait for the predecessor and the
+// vectors of all its cells are requested before any of them is combined.
+// Each cell's result is computed in the same operation order as the
+// cell-tile kernels above, so the two forms agree bit for bit.
+// ---------------------------------------------------------------------------
+constexpr int RP_Z = SSAMG_BRICK_Z;
+
+// The thread's column (i, j) and first z of its brick; false when the column
+// lies outside the part.  The brick's position comes from shared memory,
+// decoded once per block (bpos[0..2], written by thread 0 of the block).
+__device__ __forceinline__ void rp_brick_origin(const DPart& sp, int* bpos) {
+  if (threadIdx.x == 0) {
+    const int bl = (int)blockIdx.x - sp.bblk0;
+    bpos[0] = bl % sp.bb[0];
+    const int byz = bl / sp.bb[0];
+    bpos[1] = byz % sp.bb[1];
+    bpos[2] = byz / sp.bb[1];
+  }
+}
+__device__ __forceinline__ bool rp_column(const DPart& sp, const int* bpos, int& i, int& j,
+                                          int& k0) {
+  i = bpos[0] * SSAMG_BRICK_X + (int)threadIdx.x % SSAMG_BRICK_X;
+  j = bpos[1] * SSAMG_BRICK_Y + (int)threadIdx.x / SSAMG_BRICK_X;
+  k0 = bpos[2] * SSAMG_BRICK_Z;
+  return i < sp.n[0] && j < sp.n[1];
+}
+
+// Restriction of one column of coarse cells (I0, I1, K0 ..), part coarsened
+// along D (-1: not coarsened).  Side weights and the diagonal are fetched
+// before pdl_wait(); then the residuals of every cell, then the sums.
+template <int D, class T>
+__device__ __forceinline__ void restrict_column(const LevelView<T>& F, const LevelView<T>& C,
+                                                const DPart& fp, const DPart& cp, int I0, int I1,
+                                                int K0, int kend, const T* r, T* bc, T* xc) {
+  const int n0 = fp.n[0], n1 = fp.n[1], nxy = n0 * n1;
+  const int sd = D == 0 ? 1 : D == 1 ? n0 : nxy;
+  // fine anchor of the first cell and its step per coarse k
+  const int a0 = D == 0 ? 2 * I0 + fp.par : I0;
+  const int a1 = D == 1 ? 2 * I1 + fp.par : I1;
+  int fa = fp.off + ((D == 2 ? 2 * K0 + fp.par : K0) * n1 + a1) * n0 + a0;
+  const int dfa = D == 2 ? 2 * nxy : nxy;
+  // fine-point (P array) index of the west side's fine point, its step, and
+  // the east side's offset from it
+  const int nf0 = fp.nf[0], nf1 = fp.nf[1], nfxy = nf0 * nf1;
+  int pw = 0, dpw = 0, pe_off = 0;
+  if (D == 0) {
+    pw = fp.poff + (K0 * nf1 + I1) * nf0 + ((a0 - 1 + fp.par) >> 1);
+    dpw = nfxy;
+    pe_off = 1;
+  } else if (D == 1) {
+    pw = fp.poff + (K0 * nf1 + ((a1 - 1 + fp.par) >> 1)) * nf0 + I0;
+    dpw = nfxy;
+    pe_off = nf0;
+  } else if (D == 2) {
+    pw = fp.poff + (((2 * K0 + fp.par - 1 + fp.par) >> 1) * nf1 + I1) * nf0 + I0;
+    dpw = nfxy;
+    pe_off = nfxy;
+  }
+  const int ad = D == 0 ? a0 : D == 1 ? a1 : 0;
+  const int nd = D == 0 ? n0 : D == 1 ? n1 : fp.n[2];
+  T w1[RP_Z], w2[RP_Z], dv[RP_Z];
+  bool hw[RP_Z], he[RP_Z];
+  int cc0 = cp.off + (K0 * cp.n[1] + I1) * cp.n[0] + I0;
+  const int dcc = cp.n[0] * cp.n[1];
+#pragma unroll
+  for (int t = 0; t < RP_Z; ++t) {
+    const bool in = K0 + t < kend;
+    const int anc = D == 2 ? 2 * (K0 + t) + fp.par : ad;
+    hw[t] = D >= 0 && in && anc - 1 >= 0;
+    he[t] = D >= 0 && in && anc + 1 < nd;
+    w1[t] = hw[t] ? F.Pe[pw + t * dpw] : (T)0;
+    w2[t] = he[t] ? F.Pw[pw + t * dpw + pe_off] : (T)0;
+    dv[t] = (xc && in) ? C.dinv[cc0 + t * dcc] : (T)0;
+  }
+  pdl_wait();
+  if (C.skip && C.skip[cp.prob].done) return;  // problem already stopped
+  T r0[RP_Z], r1[RP_Z], r2[RP_Z];
+#pragma unroll
+  for (int t = 0; t < RP_Z; ++t) {
+    const bool in = K0 + t < kend;
+    const int f = fa + t * dfa;
+    r0[t] = in ? r[f] : (T)0;
+    r1[t] = hw[t] ? r[f - sd] : (T)0;
+    r2[t] = he[t] ? r[f + sd] : (T)0;
+  }
+#pragma unroll
+  for (int t = 0; t < RP_Z; ++t) {
+    if (K0 + t >= kend) break;
+    T v = r0[t];
+    if (hw[t]) v = fma(w1[t], r1[t], v);
+    if (he[t]) v = fma(w2[t], r2[t], v);
+    bc[cc0 + t * dcc] = v;
+    if (xc) xc[cc0 + t * dcc] = dv[t] * v;  // pre-relaxation from zero
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_restrict_b(LevelView<T> F, LevelView<T> C, const T* r,
+                                                   T* bc, T* xc, int nb) {
+  pdl_trigger();
+  __shared__ DPart fp;
+  __shared__ DPart cp;
+  __shared__ int bpos[3];
+  if ((int)blockIdx.x >= nb) {
+    u_row_job(
+        C, blockIdx.x - nb,
+        [&](int col, int q) {
+          return RCol<T>{C.u_rj[3 * q], C.u_rj[3 * q + 1], C.u_rj[3 * q + 2], C.u_rw[2 * q],
+                         C.u_rw[2 * q + 1], C.dinv[col]};
+        },
+        [&](int, int, const RCol<T>& rc) {
+          T v = r[rc.j0];
+          if (rc.j1 >= 0) v = fma(rc.w1, r[rc.j1], v);
+          if (rc.j2 >= 0) v = fma(rc.w2, r[rc.j2], v);
+          return rc.d * v;
+        });
+    return;
+  }
+  const int p = block_part(C.bblk, C.parts, C.np, cp);
+  part_of(F.parts, p, fp);
+  __syncthreads();
+  rp_brick_origin(cp, bpos);
+  __syncthreads();
+  int I0, I1, K0;
+  const bool ok = rp_column(cp, bpos, I0, I1, K0);
+  const int kend = min(K0 + RP_Z, cp.n[2]);
+  if (!ok) {
+    pdl_wait();
+    return;
+  }
+  switch (fp.dstar) {
+    case 0: restrict_column<0>(F, C, fp, cp, I0, I1, K0, kend, r, bc, xc); break;
+    case 1: restrict_column<1>(F, C, fp, cp, I0, I1, K0, kend, r, bc, xc); break;
+    case 2: restrict_column<2>(F, C, fp, cp, I0, I1, K0, kend, r, bc, xc); break;
+    default: restrict_column<-1>(F, C, fp, cp, I0, I1, K0, kend, r, bc, xc); break;
+  }
+}
+
+// Prolongation x_out = x_in + P e of one column of PZ fine cells
+// (i, j, k0 ..), part coarsened along D (-1: not coarsened, P = I).  The
+// prolongation walks half bricks (PZ = RP_Z / 2): fewer registers per
+// thread, twice the blocks, measured faster than whole bricks.
+constexpr int PZ = RP_Z / 2;
+template <int D, class T>
+__device__ __forceinline__ void prolong_column(const LevelView<T>& F, const DPart& fp, int i,
+                                               int j, int k0, int kend, const T* ec,
+                                               const T* xin, T* xout) {
+  const int n0 = fp.n[0], n1 = fp.n[1], nxy = n0 * n1;
+  const int cn0 = fp.cn[0], cn1 = fp.cn[1], cnxy = cn0 * cn1;
+  const int nf0 = fp.nf[0], nf1 = fp.nf[1], nfxy = nf0 * nf1;
+  const int par = fp.par;
+  // per cell: up to two coarse columns and their weights, in p_row's order
+  int j0[PZ], j1[PZ];
+  T w0[PZ], w1[PZ];
+#pragma unroll
+  for (int t = 0; t < PZ; ++t) {
+    const int k = k0 + t;
+    j0[t] = j1[t] = -1;
+    w0[t] = w1[t] = (T)0;
+    if (k >= kend) continue;
+    if (D < 0) {
+      j0[t] = fp.coff + (k * cn1 + j) * cn0 + i;
+      w0[t] = (T)1;
+      continue;
+    }
+    const int cd = D == 0 ? i : D == 1 ? j : k;
+    const int nd = D == 0 ? n0 : D == 1 ? n1 : fp.n[2];
+    // coarse index with the D coordinate replaced by v
+    auto at = [&](int v) {
+      return fp.coff + ((D == 2 ? v : k) * cn1 + (D == 1 ? v : j)) * cn0 + (D == 0 ? v : i);
+    };
+    if (((cd + par) & 1) == 0) {
+      j0[t] = at((cd - par) >> 1);
+      w0[t] = (T)1;
+      continue;
+    }
+    const int Fi = fp.poff + ((D == 2 ? (k + par) >> 1 : k) * nf1 + (D == 1 ? (j + par) >> 1 : j)) * nf0 +
+                   (D == 0 ? (i + par) >> 1 : i);
+    if (cd - 1 >= 0) {
+      j0[t] = at((cd - 1 - par) >> 1);
+      w0[t] = F.Pw[Fi];
+    }
+    if (cd + 1 < nd) {
+      j1[t] = at((cd + 1 - par) >> 1);
+      w1[t] = F.Pe[Fi];
+    }
+    if (j0[t] < 0) {  // only the east neighbour: keep it first
+      j0[t] = j1[t];
+      w0[t] = w1[t];
+      j1[t] = -1;
+      w1[t] = (T)0;
+    }
+  }
+  (void)cnxy;
+  (void)nfxy;
+  pdl_wait();
+  if (F.skip && F.skip[fp.prob].done) return;  // problem already stopped
+  const int c0 = fp.off + (k0 * n1 + j) * n0 + i;
+  T xv[PZ], e0[PZ], e1[PZ];
+#pragma unroll
+  for (int t = 0; t < PZ; ++t) {
+    const bool in = k0 + t < kend;
+    xv[t] = in ? xin[c0 + t * nxy] : (T)0;
+    e0[t] = in && j0[t] >= 0 ? ec[j0[t]] : (T)0;
+    e1[t] = in && j1[t] >= 0 ? ec[j1[t]] : (T)0;
+  }
+#pragma unroll
+  for (int t = 0; t < PZ; ++t) {
+    if (k0 + t >= kend) break;
+    T v = xv[t];
+    if (j0[t] >= 0) v = fma(w0[t], e0[t], v);
+    if (j1[t] >= 0) v = fma(w1[t], e1[t], v);
+    xout[c0 + t * nxy] = v;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_prolong_ub(LevelView<T> F, const T* ec, const T* xin,
+                                                   T* xout, int nb) {
+  pdl_trigger();
+  __shared__ DPart fp;
+  __shared__ int bpos[3];
+  if ((int)blockIdx.x >= nb) {
+    u_row_job(
+        F, blockIdx.x - nb,
+        [&](int, int q) {
+          return PCol<T>{F.u_pj[2 * q], F.u_pj[2 * q + 1], F.u_pw[2 * q], F.u_pw[2 * q + 1]};
+        },
+        [&](int col, int, const PCol<T>& pc) {
+          T v = xin[col];
+          if (pc.j0 >= 0) v = fma(pc.w0, ec[pc.j0], v);
+          if (pc.j1 >= 0) v = fma(pc.w1, ec[pc.j1], v);
+          return v;
+        });
+    return;
+  }
+  // two blocks per brick: block b takes the half (b & 1) of brick b >> 1
+  block_part(F.bblk, F.parts, F.np, fp, (int)blockIdx.x >> 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int bl = ((int)blockIdx.x >> 1) - fp.bblk0;
+    bpos[0] = bl % fp.bb[0];
+    const int byz = bl / fp.bb[0];
+    bpos[1] = byz % fp.bb[1];
+    bpos[2] = byz / fp.bb[1];
+  }
+  __syncthreads();
+  int i, j, k0;
+  const bool ok = rp_column(fp, bpos, i, j, k0);
+  k0 += ((int)blockIdx.x & 1) * PZ;
+  const int kend = min(k0 + PZ, fp.n[2]);
+  if (!ok) {
+    pdl_wait();
+    return;
+  }
+  switch (fp.dstar) {
+    case 0: prolong_column<0>(F, fp, i, j, k0, kend, ec, xin, xout); break;
+    case 1: prolong_column<1>(F, fp, i, j, k0, kend, ec, xin, xout); break;
+    case 2: prolong_column<2>(F, fp, i, j, k0, kend, ec, xin, xout); break;
+    default: prolong_column<-1>(F, fp, i, j, k0, kend, ec, xin, xout); break;
+  }
+}
+
+
 // xout = xin + P ec on the cell tiles; row jobs uy = U xout, where xout at a
 // coupling's column is rebuilt from xin and the column's P row (precomputed
 // at setup), so the two roles need no ordering.  P rows are setup data and
@@ -1260,6 +1531,15 @@ void launch_k(void (*kern)(P...), int grid, int block, size_t smem, cudaStream_t
 }
 }  // namespace
 
+// Restriction onto / prolongation on L over bricks: levels with at least
+// SSAMG_RP_BRICKS bricks (at least a block per SM) that the parts fill
+// to SSAMG_RP_FILL (small or uneven parts leave bricks partly idle), unless
+// the tile table keeps the level on cell tiles.
+bool rp_bricks(const Level& L) {
+  return g_ssamg_bricks && L.bricks && L.nbblk >= SSAMG_RP_BRICKS &&
+         L.brick_fill >= SSAMG_RP_FILL;
+}
+
 bool uses_bricks(const Level& L) {
   return g_ssamg_bricks && L.bricks && L.shape == SH_K7 && L.nbblk > 0;
 }
@@ -1313,7 +1593,12 @@ void launch_relax_final(const Level& L, const T* x, const T* b, double* z, const
 }
 template <class T>
 void launch_prolong_u(const Level& F, const T* ec, const T* xin, T* xout, cudaStream_t st) {
-  launch_k(k_prolong_u<T>, F.nblk + F.nublk, NT, 0, st, F.view<T>(), ec, xin, xout, F.nblk);
+  if (rp_bricks(F)) {
+    launch_k(k_prolong_ub<T>, 2 * F.nbblk + F.nublk, NT, 0, st, F.view<T>(), ec, xin, xout,
+             2 * F.nbblk);
+  } else {
+    launch_k(k_prolong_u<T>, F.nblk + F.nublk, NT, 0, st, F.view<T>(), ec, xin, xout, F.nblk);
+  }
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>
@@ -1345,7 +1630,13 @@ template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, T* xc, cudaStream_t st) {
   // with xc: also x = omega M^-1 b on the coarse level, and its U x row jobs
   const int nrow = xc ? Cl.nublk : 0;
-  launch_k(k_restrict<T>, Cl.nblk + nrow, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc, xc, Cl.nblk);
+  if (rp_bricks(Cl)) {
+    launch_k(k_restrict_b<T>, Cl.nbblk + nrow, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc, xc,
+             Cl.nbblk);
+  } else {
+    launch_k(k_restrict<T>, Cl.nblk + nrow, NT, 0, st, F.view<T>(), Cl.view<T>(), r, bc, xc,
+             Cl.nblk);
+  }
   SSAMG_LAUNCH_CHECK();
 }
 template <class T>

@@ -35,6 +35,8 @@
 #define SSAMG_BRICK_X 32
 #define SSAMG_BRICK_Y 8
 #define SSAMG_BRICK_Z 8
+#define SSAMG_RP_BRICKS 152  // fewest bricks for the restriction / prolongation brick forms
+#define SSAMG_RP_FILL 0.8    // and the least fraction of their brick cells inside the parts
 #define SSAMG_TPR 4       // fewest lanes per U row in row jobs
 #define SSAMG_TPR_MAX 16  // most lanes per U row (levels whose rows are long)
 
@@ -275,6 +277,7 @@ struct Level {
   int nblk = 0, nfblk = 0, nbblk = 0;
   int cpt = 1;
   int bricks = 1; // 0: the tile table keeps this level's operator applies on cell tiles
+  double brick_fill = 0.0;  // cells / (bricks x brick cells): how full the level's bricks are
   int kvar = 2;   // per-cell stencil entries: 0 none, 1 only diagonals, 2 others too
   int shape = 0;  // StencilShape of the level's operator apply
   std::vector<int> hblk;  // host copy of the block starts of cell-wise launches
@@ -476,6 +479,7 @@ void launch_pcg_beta_from_partials(const Level& L0, const double* z, double* p, 
 // Whether L's operator applies run over bricks, and the per-problem ranges of
 // the partials those launches write.
 bool uses_bricks(const Level& L);
+bool rp_bricks(const Level& L);
 const int* partial_ranges(const Level& L, const PcgCtx& c);
 // block ranges of the dot partials the cycle's last relaxation writes
 const int* final_ranges(const Level& L, const PcgCtx& c);
