@@ -1183,7 +1183,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       if (C.nr > 0) {
         int* fr = aalloc<int>(s->arena, 3ll * C.nr);
         double* frw = aalloc<double>(s->arena, 3ll * C.nr);
-        int* longrows = aalloc<int>(s->arena, C.nr + 1ll);
+        int* longrows = aalloc<int>(s->arena, 2 * (C.nr + 1ll));
         launch_frows(F, C, prI, prW, prA, fr, frw, st);
         launch_ucount(F, C, longrows, fr, frw, C.u_ptr, s->d_err, st);
         launch_scan(C.u_ptr, C.nr, scan_tmp, st);

@@ -447,8 +447,99 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
   return x - v;
 }
 
+// Rows of at most UT candidates, one thread per row: the same candidates in
+// the same generation order, sorted by (J, t) by insertion in the thread's
+// own arrays, merged into runs of equal J summed in generation order, so the
+// result is bitwise the warp form's.  Longer rows go to the warp forms: in
+// the counting pass the thread lists them in midrows (midrows[0] = number).
+constexpr int UT = 16;
+__global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
+                                                int* __restrict__ midrows,
+                                                const int* __restrict__ fr,
+                                                const double* __restrict__ frw,
+                                                const int* __restrict__ pj,
+                                                const double* __restrict__ pw,
+                                                const int* __restrict__ ptr,
+                                                int* __restrict__ counts, int* __restrict__ col,
+                                                double* __restrict__ val,
+                                                float* __restrict__ val32,
+                                                unsigned char* __restrict__ bits) {
+  const int R = blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= nrc) return;
+  int ur[3], q0[3], q1[3];
+  double w1[3];
+  int ub = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ur[a] = fr[3 * R + a];
+    w1[a] = ur[a] >= 0 ? frw[3 * R + a] : 0.0;
+    q0[a] = q1[a] = 0;
+    if (ur[a] >= 0) {
+      q0[a] = F.u_ptr[ur[a]];
+      q1[a] = F.u_ptr[ur[a] + 1];
+      ub += 2 * (q1[a] - q0[a]);
+    }
+  }
+  if (ub > UT) {
+    if (counts) midrows[1 + atomicAdd(midrows, 1)] = R;
+    return;
+  }
+  unsigned long long K[UT];
+  double V[UT];
+  unsigned char B[UT];
+  int n = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    for (int q = q0[a]; q < q1[a]; ++q) {
+      const double v = w1[a] * F.u_val[q];
+      const unsigned char b = F.u_bits[q];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int J = pj[2 * q + t];
+        if (J >= 0) {
+          K[n] = ((unsigned long long)(unsigned)J << 10) | (unsigned)n;
+          V[n] = v * pw[2 * q + t];
+          B[n] = b;
+          ++n;
+        }
+      }
+    }
+  for (int i = 1; i < n; ++i) {
+    const unsigned long long key = K[i];
+    int j = i - 1;
+    while (j >= 0 && K[j] > key) {
+      K[j + 1] = K[j];
+      --j;
+    }
+    K[j + 1] = key;
+  }
+  const int o0 = counts ? 0 : ptr[R];
+  int run = 0;
+  for (int i = 0; i < n;) {
+    const unsigned long long J = K[i] >> 10;
+    double v = 0.0;
+    unsigned char b = 0;
+    int u = i;
+    for (; u < n && (K[u] >> 10) == J; ++u) {
+      const int t = (int)(K[u] & 1023ull);
+      v += V[t];
+      b |= B[t];
+    }
+    if (!counts) {
+      col[o0 + run] = (int)J;
+      val[o0 + run] = v;
+      if (val32) val32[o0 + run] = (float)v;
+      bits[o0 + run] = b;
+    }
+    ++run;
+    i = u;
+  }
+  if (counts) counts[R] = run;
+}
+
 template <int UW, int WPB>
 __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
+                                                   const int* __restrict__ midrows,
                                                    int* __restrict__ longrows,
                                                    const int* __restrict__ fr,
                                                    const double* __restrict__ frw,
@@ -464,13 +555,16 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
   __shared__ double sV[WPB][UW];
   __shared__ unsigned char sB[WPB][UW];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the small instance walks the rows (one warp each) and, in the counting
-  // pass, lists the rows it leaves to the large one (longrows[0] = number,
-  // then the rows); the large instance is a fixed grid over that list
+  // both instances are fixed grids over a list of rows (list[0] = number,
+  // then the rows): the small one over the rows the thread form left
+  // (midrows), listing in the counting pass the rows it leaves to the large
+  // one (longrows); the large one over longrows
+  // (midrows null: the small one walks every row instead)
   constexpr bool small = UW == UW_SMALL;
-  const int nlong = small ? 0 : *(volatile int*)longrows;
-  for (int it = blockIdx.x * WPB + w; it < (small ? nrc : nlong); it += gridDim.x * WPB) {
-  const int R = small ? it : longrows[1 + it];
+  const int* list = small ? midrows : longrows;
+  const int nlist = list ? *(volatile const int*)list : nrc;
+  for (int it = blockIdx.x * WPB + w; it < nlist; it += gridDim.x * WPB) {
+  const int R = list ? list[1 + it] : it;
   unsigned long long* K = sK[w];
   double* V = sV[w];
   unsigned char* B = sB[w];
@@ -928,37 +1022,56 @@ void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStrea
   SSAMG_LAUNCH_CHECK();
 }
 
-// Both instances of k_urow: the small one over every row, the large one (a
-// grid of a few blocks per SM) over the rows the counting pass listed.
-void launch_urow(const Level& F, const Level& Cl, int* longrows, const int* fr,
+// The three forms of the coupling-row merge: a thread per row of at most UT
+// candidates over every row, then the warp forms (fixed grids of a few blocks
+// per SM) over the rows the counting pass listed: midrows (more than UT
+// candidates, up to UW_SMALL) and longrows (more than UW_SMALL).  lists:
+// 2 (nr + 1) ints, midrows then longrows.
+// The thread form runs first only where the fine level's coupling rows are
+// short (mean length <= 8/3: three fine rows spread over two columns each
+// then give at most 16 candidates on average); elsewhere the small warp form
+// walks every row.
+bool urow_thread_form(const Level& F) { return 3ll * F.nnz <= 8ll * F.nr; }
+
+void launch_urow(const Level& F, const Level& Cl, int* lists, const int* fr,
                  const double* frw, const int* ptr, int* counts, int* col, double* val,
                  float* val32, unsigned char* bits, int* err, cudaStream_t st) {
-  k_urow<UW_SMALL, UWARPS_SMALL><<<cdiv(Cl.nr, UWARPS_SMALL), 32 * UWARPS_SMALL, 0, st>>>(
-      F.view<double>(), Cl.nr, longrows, fr, frw, F.u_pj, F.u_pw, ptr, counts, col, val, val32,
-      bits, err);
-  SSAMG_LAUNCH_CHECK();
+  const bool thr = urow_thread_form(F);
+  int* midrows = thr ? lists : nullptr;
+  int* longrows = lists + Cl.nr + 1;
   int dev = 0, sms = 0;
   SSAMG_CUDA(cudaGetDevice(&dev));
   SSAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int nb = std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms);
-  k_urow<UW_LARGE, UWARPS_LARGE><<<nb, 32 * UWARPS_LARGE, 0, st>>>(
-      F.view<double>(), Cl.nr, longrows, fr, frw, F.u_pj, F.u_pw, ptr, counts, col, val, val32,
-      bits, err);
+  if (thr) {
+    k_urow_t<<<cdiv(Cl.nr, 256), 256, 0, st>>>(F.view<double>(), Cl.nr, midrows, fr, frw,
+                                                F.u_pj, F.u_pw, ptr, counts, col, val, val32,
+                                                bits);
+    SSAMG_LAUNCH_CHECK();
+  }
+  const int nbs = thr ? std::min(cdiv(Cl.nr, UWARPS_SMALL), 4 * sms) : cdiv(Cl.nr, UWARPS_SMALL);
+  k_urow<UW_SMALL, UWARPS_SMALL><<<nbs, 32 * UWARPS_SMALL, 0,
+                                   st>>>(F.view<double>(), Cl.nr, midrows, longrows, fr, frw,
+                                         F.u_pj, F.u_pw, ptr, counts, col, val, val32, bits, err);
+  SSAMG_LAUNCH_CHECK();
+  k_urow<UW_LARGE, UWARPS_LARGE><<<std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms), 32 * UWARPS_LARGE, 0,
+                                   st>>>(F.view<double>(), Cl.nr, midrows, longrows, fr, frw,
+                                         F.u_pj, F.u_pw, ptr, counts, col, val, val32, bits, err);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_ucount(const Level& F, const Level& Cl, int* longrows, const int* fr,
+void launch_ucount(const Level& F, const Level& Cl, int* lists, const int* fr,
                    const double* frw, int* counts, int* err, cudaStream_t st) {
   if (Cl.nr == 0) return;
-  SSAMG_CUDA(cudaMemsetAsync(longrows, 0, sizeof(int), st));
-  launch_urow(F, Cl, longrows, fr, frw, nullptr, counts, nullptr, nullptr, nullptr, nullptr,
-              err, st);
+  SSAMG_CUDA(cudaMemsetAsync(lists, 0, sizeof(int), st));
+  SSAMG_CUDA(cudaMemsetAsync(lists + Cl.nr + 1, 0, sizeof(int), st));
+  launch_urow(F, Cl, lists, fr, frw, nullptr, counts, nullptr, nullptr, nullptr, nullptr, err,
+              st);
 }
 
-void launch_ufill(const Level& F, const Level& Cl, int* longrows, const int* fr,
+void launch_ufill(const Level& F, const Level& Cl, int* lists, const int* fr,
                   const double* frw, bool fp32, int* err, cudaStream_t st) {
   if (Cl.nr == 0) return;
-  launch_urow(F, Cl, longrows, fr, frw, Cl.u_ptr, nullptr, Cl.u_col, Cl.u_val,
+  launch_urow(F, Cl, lists, fr, frw, Cl.u_ptr, nullptr, Cl.u_col, Cl.u_val,
               fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, err, st);
 }
 

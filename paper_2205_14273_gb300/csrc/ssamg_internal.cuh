@@ -382,8 +382,8 @@ void launch_uprow(const Level& F, const Level& Cl, int* prI, double* prW, signed
 void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStream_t st);
 void launch_frows(const Level& F, const Level& Cl, const int* prI, const double* prW,
                   const signed char* prA, int* fr, double* frw, cudaStream_t st);
-// longrows: Cl.nr + 1 ints (the rows of more than 128 candidates, which the
-// counting pass lists for the fill pass).
+// lists: 2 (Cl.nr + 1) ints (the rows the counting pass lists for the warp
+// forms of the merge, reused by the fill pass).
 void launch_ucount(const Level& F, const Level& Cl, int* longrows, const int* fr,
                    const double* frw, int* counts, int* err, cudaStream_t st);
 void launch_ufill(const Level& F, const Level& Cl, int* longrows, const int* fr,
