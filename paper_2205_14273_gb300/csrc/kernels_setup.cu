@@ -28,35 +28,84 @@ __device__ __forceinline__ int p_row_arrays(const DPart& p, const T* __restrict_
 // along d) (Section 3.1).  Block partials, then one block per part sums them
 // in a fixed order.
 // ---------------------------------------------------------------------------
+// Constant entries (one value over the part) contribute -a_e times the
+// number of the block's cells whose neighbour c + o_e is in the box, each
+// counted with the cell's sign: exact integers (a warp sum per step, kept by
+// the warp's lane 0), multiplied once per block; per-cell entries are summed
+// in FP64 cell by cell.  The diagonal's sign is read from its bits (negative,
+// nonzero, not NaN: the same decision as diag < 0).
 __global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __restrict__ partial) {
   __shared__ DPart sp;
   __shared__ double sh[NT / 32];
+  __shared__ int shc[NT / 32][SSAMG_MAXE];
   int p = block_part(L.blk, L.parts, L.np, sp);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+    for (int e = 0; e < SSAMG_MAXE; ++e) shc[w][e] = 0;
   __syncthreads();
+  int de = -1;  // the diagonal entry (offset 0, 0, 0)
+  bool anyvar = false;
+  for (int e = 0; e < sp.nent; ++e) {
+    if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0)
+      de = e;
+    else if (sp.coef[e] >= 0)
+      anyvar = true;
+  }
   double s0 = 0, s1 = 0, s2 = 0;
-  TILE_LOOP(c, sp) {
-    int i, j, k;
-    cell_coords(sp, c, i, j, k);
-    double sg = 1.0;
-    for (int e = 0; e < sp.nent; ++e)
-      if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0 && coef_at(sp, L.coef, e, c) < 0.0)
-        sg = -1.0;
-    double t0 = 0, t1 = 0, t2 = 0;
-    for (int e = 0; e < sp.nent; ++e) {
-      if (!inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2])) continue;
-      double a = coef_at(sp, L.coef, e, c);
-      if (sp.o[e][0]) t0 -= a;
-      if (sp.o[e][1]) t1 -= a;
-      if (sp.o[e][2]) t2 -= a;
+  const int base = ((int)blockIdx.x - sp.blk0) * sp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
+#pragma unroll 1
+  for (int m = 0; m < sp.cpt; ++m) {
+    const int c = base + m * SSAMG_BLOCK;
+    if (c - lane >= sp.ncell) break;  // the warp's first cell: a warp-uniform exit
+    const bool valid = c < sp.ncell;
+    int i = 0, j = 0, k = 0;
+    bool neg = false;
+    if (valid) {
+      cell_coords(sp, c, i, j, k);
+      if (de >= 0) {
+        const long long bits = __double_as_longlong(coef_at(sp, L.coef, de, c));
+        const long long mag = bits & 0x7fffffffffffffffll;
+        neg = bits < 0 && mag != 0 && mag <= 0x7ff0000000000000ll;
+      }
     }
-    s0 += sg * t0;
-    s1 += sg * t1;
-    s2 += sg * t2;
+    double t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll 1
+    for (int e = 0; e < sp.nent; ++e) {
+      if (e == de) continue;
+      const bool ok = valid && inside(sp, i + sp.o[e][0], j + sp.o[e][1], k + sp.o[e][2]);
+      if (sp.coef[e] >= 0) {
+        if (ok) {
+          const double a = L.coef[sp.coef[e] + c];
+          if (sp.o[e][0]) t0 -= a;
+          if (sp.o[e][1]) t1 -= a;
+          if (sp.o[e][2]) t2 -= a;
+        }
+      } else {
+        const int v = __reduce_add_sync(0xffffffffu, ok ? (neg ? -1 : 1) : 0);
+        if (lane == 0) shc[w][e] += v;
+      }
+    }
+    if (anyvar && valid) {
+      const double sg = neg ? -1.0 : 1.0;
+      s0 += sg * t0;
+      s1 += sg * t1;
+      s2 += sg * t2;
+    }
   }
   double r0 = block_sum<NT>(s0, sh);
   double r1 = block_sum<NT>(s1, sh);
   double r2 = block_sum<NT>(s2, sh);
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int e = 0; e < sp.nent; ++e) {
+      if (e == de || sp.coef[e] >= 0) continue;
+      long long n = 0;
+      for (int q = 0; q < NT / 32; ++q) n += shc[q][e];
+      const double a = sp.cval[e] * (double)n;
+      if (sp.o[e][0]) r0 -= a;
+      if (sp.o[e][1]) r1 -= a;
+      if (sp.o[e][2]) r2 -= a;
+    }
     partial[3 * blockIdx.x + 0] = r0;
     partial[3 * blockIdx.x + 1] = r1;
     partial[3 * blockIdx.x + 2] = r2;
@@ -128,8 +177,9 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
     double pw = 0, pe = 0;
     bool ok = fabs(den) > 1e-300 && ((den > 0) == (diag > 0)) && diag != 0.0;
     if (ok) {
-      pw = -nw / den;
-      pe = -ne / den;
+      const double rd = 1.0 / den;  // one division for both weights
+      pw = -nw * rd;
+      pe = -ne * rd;
     }
     if (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1)) {
       int r = L.u_map[sp.off + c];
@@ -150,176 +200,124 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
 }
 
 // ---------------------------------------------------------------------------
-// K3: structured Galerkin product P^T S P (Eq. galerkin), one coarse cell
-// per thread (the form for large levels, where it moves the fine data once).
-// For coarse cell I with fine anchor F (2I along d*) and a in {-1,0,1}:
-// f = F + a e_d carries P(f, I) = 1, PE(f) or PW(f); each entry o at f
-// reaches g = f + o, which maps to J = g/2 (coarse point) or to its west and
-// east coarse neighbours with PW(g), PE(g).  The product accumulates into the
-// coarse entry J - I.
+// K3, all levels: P^T S P with a thread per (coarse cell, off-d* offset
+// group).  The coarse entries O = (u, v off d*; c along d*), c in {-1,0,1},
+// of one group come only from the fine entries with the same offsets off d*
+// (o_d in {-1,0,1}) at the coarse cell's three fine points f = F + a e_d
+// (F its anchor 2I along d*): the product w_a s_o(f) goes to c = t/2 when
+// t = a + o_d is even (g = f + o is a coarse point) and to (t-1)/2 and
+// (t+1)/2 with PW(g), PE(g) when t is odd.  a and o_d are compile-time, so
+// the group's three sums stay in registers; each sum runs in the order
+// (a, o_d) ascending.  Each fine coefficient is read once per coarse cell.
+// Block b takes group b % 9 of coarse tile b / 9.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 2) k_rap_cell(LevelView<double> F, LevelView<double> C,
-                                                   double* __restrict__ ccoef,
-                                                   float* __restrict__ ccoef32) {
-  __shared__ DPart fp;
-  __shared__ DPart cp;
-  int p = block_part(C.blk, C.parts, C.np, cp);
-  part_of(F.parts, p, fp);
-  __syncthreads();
-  TILE_LOOP(cc, cp) {
-    int I[3];
-    cell_coords(cp, cc, I[0], I[1], I[2]);
-    double acc[27];
-  #pragma unroll
-    for (int t = 0; t < 27; ++t) acc[t] = 0.0;
-    const int d = fp.dstar;
-    if (d < 0) {
-      // part not coarsened at this level: P = I on this part
-      int c = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
-      for (int e = 0; e < fp.nent; ++e) {
-        if (!inside(fp, I[0] + fp.o[e][0], I[1] + fp.o[e][1], I[2] + fp.o[e][2])) continue;
-        int code = (fp.o[e][0] + 1) + 3 * (fp.o[e][1] + 1) + 9 * (fp.o[e][2] + 1);
-        acc[code] += coef_at(fp, F.coef, e, c);
-      }
-    } else {
-      const int anchor = 2 * I[d] + fp.par;
-      for (int a = -1; a <= 1; ++a) {
-        int f[3] = {I[0], I[1], I[2]};
-        f[d] = anchor + a;
-        if (f[d] < 0 || f[d] >= fp.n[d]) continue;
-        const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-        double w1 = 1.0;
-        if (a != 0) {
-          int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
-          w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
-        }
-        if (w1 == 0.0) continue;
-        // entries in batches of RB: the batch's coefficient and P-weight loads
-        // are predicated, not branched around, so they are in flight together
-        constexpr int RB = 9;
-        for (int e0 = 0; e0 < fp.nent; e0 += RB) {
-          double cv[RB], pw[RB], pe[RB];
+// D: the coarsening direction of the part (-1: not coarsened, P = I), a
+// template argument so that the coordinate arrays stay in registers.
+template <int D>
+__device__ __forceinline__ void rap_group_tile(const LevelView<double>& F, const DPart& fp,
+                                               const DPart& cp, int tile, int gu, int gv,
+                                               double* __restrict__ ccoef,
+                                               float* __restrict__ ccoef32) {
+  constexpr int dd = D < 0 ? 0 : D;
+  constexpr int d1 = dd == 0 ? 1 : 0, d2 = dd == 2 ? 1 : 2;
+  // the group's coarse entries (c = -1, 0, 1) and fine entries (o_d = -1, 0, 1)
+  int ce[3], fe[3];
 #pragma unroll
-          for (int q = 0; q < RB; ++q) {
-            const int e = e0 + q;
-            const bool ok = e < fp.nent &&
-                            inside(fp, f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2]);
-            const int t = a + (ok ? fp.o[e][d] : 0);
-            const bool odd = ok && (t & 1);
-            const int Gi = odd ? fp.poff + fine_point_index(fp, f[0] + fp.o[e][0],
-                                                            f[1] + fp.o[e][1], f[2] + fp.o[e][2])
-                               : 0;
-            cv[q] = ok ? coef_at(fp, F.coef, e, fcell) : 0.0;
-            pw[q] = odd ? F.Pw[Gi] : 0.0;
-            pe[q] = odd ? F.Pe[Gi] : 0.0;
-          }
-#pragma unroll
-          for (int q = 0; q < RB; ++q) {
-            const int e = e0 + q;
-            if (e >= fp.nent) break;
-            if (!inside(fp, f[0] + fp.o[e][0], f[1] + fp.o[e][1], f[2] + fp.o[e][2])) continue;
-            const double v = w1 * cv[q];
-            const int t = a + fp.o[e][d];
-            int ob[3] = {fp.o[e][0], fp.o[e][1], fp.o[e][2]};
-            if ((t & 1) == 0) {
-              ob[d] = t / 2;
-              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v;
-            } else {
-              ob[d] = (t - 1) / 2;
-              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * pw[q];
-              ob[d] = (t + 1) / 2;
-              acc[(ob[0] + 1) + 3 * (ob[1] + 1) + 9 * (ob[2] + 1)] += v * pe[q];
-            }
-          }
-        }
-      }
-    }
-    for (int e = 0; e < cp.nent; ++e) {
-      int code = (cp.o[e][0] + 1) + 3 * (cp.o[e][1] + 1) + 9 * (cp.o[e][2] + 1);
-      double v = acc[code];
-      if (!inside(cp, I[0] + cp.o[e][0], I[1] + cp.o[e][1], I[2] + cp.o[e][2])) v = 0.0;
-      ccoef[cp.coef[e] + cc] = v;
-      if (ccoef32) ccoef32[cp.coef[e] + cc] = (float)v;
-    }
+  for (int c = 0; c < 3; ++c) {
+    int o[3];
+    o[dd] = c - 1;
+    o[d1] = gu;
+    o[d2] = gv;
+    const int code = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+    ce[c] = cp.slot[code];
+    fe[c] = fp.slot[code];
   }
-}
-
-// ---------------------------------------------------------------------------
-// K3 for small levels, one coarse entry per thread (nine terms at most, so
-// the dependent latency of a level is a few loads deep): the block's threads
-// take the cells of a coarse tile and one entry O of the coarse stencil.  For coarse cell I with fine
-// anchor F (2I along d*) and a in {-1,0,1}: f = F + a e_d carries
-// P(f, I) = 1, PE(f) or PW(f); an entry o at f reaches g = f + o, which maps
-// to the coarse offset t/2 (t = a + o_d even: g is a coarse point) or to
-// (t-1)/2 and (t+1)/2 with PW(g) and PE(g) (t odd).  So the entries of f
-// that feed O have o = O off d* and o_d in {-1,0,1}: at most nine terms per
-// coarse entry, summed in registers in the order (a, o_d) ascending.  Block
-// b takes entry b % ne of tile b / ne, so that the ne blocks of a tile run
-// together and share its fine data through L2.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_rap_entry(LevelView<double> F, LevelView<double> C,
-                                                  int ne, double* __restrict__ ccoef,
-                                                   float* __restrict__ ccoef32) {
-  __shared__ DPart fp;
-  __shared__ DPart cp;
-  const int tile = (int)blockIdx.x / ne;
-  const int ec = (int)blockIdx.x - tile * ne;
-  int p = block_part(C.blk, C.parts, C.np, cp, tile);
-  part_of(F.parts, p, fp);
-  __syncthreads();
-  if (ec >= cp.nent) return;
-  const int O0 = cp.o[ec][0], O1 = cp.o[ec][1], O2 = cp.o[ec][2];
-  const int d = fp.dstar;
+  if (ce[0] < 0 && ce[1] < 0 && ce[2] < 0) return;
+  const int fstr[3] = {1, fp.n[0], fp.n[0] * fp.n[1]};
 #pragma unroll 1
   for (int m = 0, cc = (tile - cp.blk0) * cp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
        m < cp.cpt && cc < cp.ncell; ++m, cc += SSAMG_BLOCK) {
     int I[3];
     cell_coords(cp, cc, I[0], I[1], I[2]);
-    double v = 0.0;
-    if (inside(cp, I[0] + O0, I[1] + O1, I[2] + O2)) {
-      if (d < 0) {
-        // part not coarsened at this level: P = I on this part
-        const int e = fp.slot[(O0 + 1) + 3 * (O1 + 1) + 9 * (O2 + 1)];
-        if (e >= 0 && inside(fp, I[0] + O0, I[1] + O1, I[2] + O2))
-          v = coef_at(fp, F.coef, e, (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0]);
-      } else {
-        const int Od = d == 0 ? O0 : d == 1 ? O1 : O2;
-        const int anchor = 2 * I[d] + fp.par;
-        for (int a = -1; a <= 1; ++a) {
-          int f[3] = {I[0], I[1], I[2]};
-          f[d] = anchor + a;
-          if (f[d] < 0 || f[d] >= fp.n[d]) continue;
-          const int fcell = (f[2] * fp.n[1] + f[1]) * fp.n[0] + f[0];
-          double w1 = 1.0;
-          if (a != 0) {
-            const int Fi = fp.poff + fine_point_index(fp, f[0], f[1], f[2]);
-            w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
-          }
-          if (w1 == 0.0) continue;
+    double acc[3] = {0.0, 0.0, 0.0};
+    // offsets off d* are fixed within the group
+    const bool off_in = (unsigned)(I[d1] + gu) < (unsigned)fp.n[d1] &&
+                        (unsigned)(I[d2] + gv) < (unsigned)fp.n[d2];
+    if (D < 0) {
+      const int fcell = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0];
 #pragma unroll
-          for (int od = -1; od <= 1; ++od) {
-            const int t = a + od;
-            // 0: g is a coarse point; 1: O is g's west coarse neighbour; 2: east
-            const int kind = (t & 1) == 0 ? (t / 2 == Od ? 0 : -1)
-                                          : ((t - 1) / 2 == Od ? 1 : (t + 1) / 2 == Od ? 2 : -1);
-            if (kind < 0) continue;
-            int o[3] = {O0, O1, O2};
-            o[d] = od;
-            const int e = fp.slot[(o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1)];
-            const int g0 = f[0] + o[0], g1 = f[1] + o[1], g2 = f[2] + o[2];
-            if (e < 0 || !inside(fp, g0, g1, g2)) continue;
-            double term = w1 * coef_at(fp, F.coef, e, fcell);
-            if (kind) {
-              const int Gi = fp.poff + fine_point_index(fp, g0, g1, g2);
-              term *= kind == 1 ? F.Pw[Gi] : F.Pe[Gi];
-            }
-            v += term;
+      for (int c = 0; c < 3; ++c)
+        if (fe[c] >= 0 && off_in && (unsigned)(I[dd] + c - 1) < (unsigned)fp.n[dd])
+          acc[c] = coef_at(fp, F.coef, fe[c], fcell);
+    } else if (off_in) {
+      const int anchor = 2 * I[dd] + fp.par;
+      const int cell0 = (I[2] * fp.n[1] + I[1]) * fp.n[0] + I[0] + (anchor - I[dd]) * fstr[dd];
+      // fine-point index of (f with coordinate x along d*, g off d*): the
+      // fine-point grid halves d* only
+      int q[3] = {I[0], I[1], I[2]};
+      q[d1] += gu;
+      q[d2] += gv;
+      const int nfs[3] = {1, fp.nf[0], fp.nf[0] * fp.nf[1]};
+      const int fp_off = fp.poff + q[d1] * nfs[d1] + q[d2] * nfs[d2];
+      const int fpi0 = fp.poff + I[d1] * nfs[d1] + I[d2] * nfs[d2];
+#pragma unroll
+      for (int a = -1; a <= 1; ++a) {
+        const int fd = anchor + a;
+        if ((unsigned)fd >= (unsigned)fp.n[dd]) continue;
+        const int fcell = cell0 + a * fstr[dd];
+        double w1 = 1.0;
+        if (a != 0) {
+          const int Fi = fpi0 + ((fd + fp.par) >> 1) * nfs[dd];
+          w1 = (a < 0) ? F.Pe[Fi] : F.Pw[Fi];
+        }
+        if (w1 == 0.0) continue;
+#pragma unroll
+        for (int od = -1; od <= 1; ++od) {
+          const int e = fe[od + 1];
+          const int gd = fd + od;
+          if (e < 0 || (unsigned)gd >= (unsigned)fp.n[dd]) continue;
+          const double v = w1 * coef_at(fp, F.coef, e, fcell);
+          const int t = a + od;
+          if ((t & 1) == 0) {
+            acc[t / 2 + 1] += v;
+          } else {
+            const int Gi = fp_off + ((gd + fp.par) >> 1) * nfs[dd];
+            acc[(t - 1) / 2 + 1] += v * F.Pw[Gi];
+            acc[(t + 1) / 2 + 1] += v * F.Pe[Gi];
           }
         }
       }
     }
-    ccoef[cp.coef[ec] + cc] = v;
-    if (ccoef32) ccoef32[cp.coef[ec] + cc] = (float)v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (ce[c] < 0) continue;
+      int O[3];
+      O[dd] = c - 1;
+      O[d1] = gu;
+      O[d2] = gv;
+      const double v = inside(cp, I[0] + O[0], I[1] + O[1], I[2] + O[2]) ? acc[c] : 0.0;
+      ccoef[cp.coef[ce[c]] + cc] = v;
+      if (ccoef32) ccoef32[cp.coef[ce[c]] + cc] = (float)v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_rap_group(LevelView<double> F, LevelView<double> C,
+                                                  double* __restrict__ ccoef,
+                                                  float* __restrict__ ccoef32) {
+  __shared__ DPart fp;
+  __shared__ DPart cp;
+  const int tile = (int)blockIdx.x / 9;
+  const int grp = (int)blockIdx.x - 9 * tile;
+  int p = block_part(C.blk, C.parts, C.np, cp, tile);
+  part_of(F.parts, p, fp);
+  __syncthreads();
+  const int gu = grp % 3 - 1, gv = grp / 3 - 1;
+  switch (fp.dstar) {
+    case 0: rap_group_tile<0>(F, fp, cp, tile, gu, gv, ccoef, ccoef32); break;
+    case 1: rap_group_tile<1>(F, fp, cp, tile, gu, gv, ccoef, ccoef32); break;
+    case 2: rap_group_tile<2>(F, fp, cp, tile, gu, gv, ccoef, ccoef32); break;
+    default: rap_group_tile<-1>(F, fp, cp, tile, gu, gv, ccoef, ccoef32); break;
   }
 }
 
@@ -986,15 +984,8 @@ void launch_interp(const Level& F, bool fp32, cudaStream_t st) {
 }
 
 void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t st) {
-  if (Cl.N >= SSAMG_RAP_CELL_MIN) {
-    k_rap_cell<<<Cl.nblk, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
-                                       fp32 ? Cl.coef32 : nullptr);
-  } else {
-    int ne = 1;
-    for (const PartH& h : Cl.parts) ne = std::max(ne, h.nent);
-    k_rap_entry<<<Cl.nblk * ne, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), ne, Cl.coef,
-                                             fp32 ? Cl.coef32 : nullptr);
-  }
+  k_rap_group<<<Cl.nblk * 9, NT, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.coef,
+                                          fp32 ? Cl.coef32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -28,7 +28,6 @@
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
 #define SSAMG_TUNE_MARGIN 0.97    // a tuned tile form must save 3% of a level's time
 #define SSAMG_TUNE_ITER_MARGIN 0.99  // and the tuned table 1% of a whole PCG iteration
-#define SSAMG_RAP_CELL_MIN 262144  // coarse levels this large take P^T S P one cell per thread
 #define SSAMG_EW 4                 // cells per thread of the elementwise pre-relaxation
 // Bricks of the checked 7-point operator applies: SSAMG_BRICK_X x _Y threads
 // (one column each), marching SSAMG_BRICK_Z cells along z.
