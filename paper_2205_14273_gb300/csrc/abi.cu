@@ -1185,7 +1185,16 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
         double* frw = aalloc<double>(s->arena, 3ll * C.nr);
         int* longrows = aalloc<int>(s->arena, 2 * (C.nr + 1ll));
         launch_frows(F, C, prI, prW, prA, fr, frw, st);
-        launch_ucount(F, C, longrows, fr, frw, C.u_ptr, s->d_err, st);
+        // staging for the sorted rows: a row has at most as many entries as
+        // candidates, and a fine row feeds at most two coarse rows with two
+        // columns per coupling, so 4 nnz of the fine level bound the total
+        UStage ust;
+        ust.toff = aalloc<int>(s->arena, C.nr);
+        ust.cursor = aalloc<int>(s->arena, 1);
+        ust.col = aalloc<int>(s->arena, 4 * F.nnz);
+        ust.val = aalloc<double>(s->arena, 4 * F.nnz);
+        ust.bits = aalloc<unsigned char>(s->arena, 4 * F.nnz);
+        launch_usort(F, C, longrows, fr, frw, C.u_ptr, ust, s->d_err, st);
         launch_scan(C.u_ptr, C.nr, scan_tmp, st);
         SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
         SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -1194,7 +1203,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
         C.u_val = aalloc<double>(s->arena, C.nnz);
         C.u_bits = aalloc<unsigned char>(s->arena, C.nnz);
         if (fp32) C.u_val32 = aalloc<float>(s->arena, C.nnz);
-        launch_ufill(F, C, longrows, fr, frw, fp32, s->d_err, st);
+        launch_ucopy(C, ust, fp32, st);
       }
     } else {
       C.nr = 0;

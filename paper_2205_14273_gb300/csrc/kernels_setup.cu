@@ -448,8 +448,14 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
 // Rows of at most UT candidates, one thread per row: the same candidates in
 // the same generation order, sorted by (J, t) by insertion in the thread's
 // own arrays, merged into runs of equal J summed in generation order, so the
-// result is bitwise the warp form's.  Longer rows go to the warp forms: in
-// the counting pass the thread lists them in midrows (midrows[0] = number).
+// result is bitwise the warp form's.  Longer rows go to the warp forms: the
+// thread lists them in midrows (midrows[0] = number).
+//
+// Every form sorts a row once: it reserves as many staging slots as the row
+// has candidates (a bound on its entries; sum over rows <= 4 nnz of the fine
+// level), writes the merged entries there (toff[R]: the first slot) and their
+// number to counts[R]; k_ucopy moves them to the CSR arrays once the counts
+// are scanned.  The staging order depends on the schedule, the result does not.
 constexpr int UT = 16;
 __global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
                                                 int* __restrict__ midrows,
@@ -457,11 +463,10 @@ __global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
                                                 const double* __restrict__ frw,
                                                 const int* __restrict__ pj,
                                                 const double* __restrict__ pw,
-                                                const int* __restrict__ ptr,
-                                                int* __restrict__ counts, int* __restrict__ col,
-                                                double* __restrict__ val,
-                                                float* __restrict__ val32,
-                                                unsigned char* __restrict__ bits) {
+                                                int* __restrict__ counts, int* __restrict__ toff,
+                                                int* __restrict__ cursor, int* __restrict__ tcol,
+                                                double* __restrict__ tval,
+                                                unsigned char* __restrict__ tbits) {
   const int R = blockIdx.x * blockDim.x + threadIdx.x;
   if (R >= nrc) return;
   int ur[3], q0[3], q1[3];
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
     }
   }
   if (ub > UT) {
-    if (counts) midrows[1 + atomicAdd(midrows, 1)] = R;
+    midrows[1 + atomicAdd(midrows, 1)] = R;
     return;
   }
   unsigned long long K[UT];
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
     }
     K[j + 1] = key;
   }
-  const int o0 = counts ? 0 : ptr[R];
+  const int o0 = n ? atomicAdd(cursor, n) : 0;
   int run = 0;
   for (int i = 0; i < n;) {
     const unsigned long long J = K[i] >> 10;
@@ -523,16 +528,14 @@ __global__ void __launch_bounds__(256) k_urow_t(LevelView<double> F, int nrc,
       v += V[t];
       b |= B[t];
     }
-    if (!counts) {
-      col[o0 + run] = (int)J;
-      val[o0 + run] = v;
-      if (val32) val32[o0 + run] = (float)v;
-      bits[o0 + run] = b;
-    }
+    tcol[o0 + run] = (int)J;
+    tval[o0 + run] = v;
+    tbits[o0 + run] = b;
     ++run;
     i = u;
   }
-  if (counts) counts[R] = run;
+  toff[R] = o0;
+  counts[R] = run;
 }
 
 template <int UW, int WPB>
@@ -543,11 +546,12 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
                                                    const double* __restrict__ frw,
                                                    const int* __restrict__ pj,
                                                    const double* __restrict__ pw,
-                                                   const int* __restrict__ ptr,
-                                                   int* __restrict__ counts, int* __restrict__ col,
-                                                   double* __restrict__ val,
-                                                   float* __restrict__ val32,
-                                                   unsigned char* __restrict__ bits,
+                                                   int* __restrict__ counts,
+                                                   int* __restrict__ toff,
+                                                   int* __restrict__ cursor,
+                                                   int* __restrict__ tcol,
+                                                   double* __restrict__ tval,
+                                                   unsigned char* __restrict__ tbits,
                                                    int* __restrict__ err) {
   __shared__ unsigned long long sK[WPB][UW];
   __shared__ double sV[WPB][UW];
@@ -555,8 +559,8 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // both instances are fixed grids over a list of rows (list[0] = number,
   // then the rows): the small one over the rows the thread form left
-  // (midrows), listing in the counting pass the rows it leaves to the large
-  // one (longrows); the large one over longrows
+  // (midrows), listing the rows it leaves to the large one (longrows); the
+  // large one over longrows
   // (midrows null: the small one walks every row instead)
   constexpr bool small = UW == UW_SMALL;
   const int* list = small ? midrows : longrows;
@@ -580,7 +584,7 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
     }
   }
   if (small && ub > UW_SMALL) {
-    if (counts && lane == 0) longrows[1 + atomicAdd(longrows, 1)] = R;
+    if (lane == 0) longrows[1 + atomicAdd(longrows, 1)] = R;
     continue;
   }
   int n = 0;
@@ -619,8 +623,11 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
     }
   }
   if (n > UW) {
-    if (lane == 0) atomicOr(err, 1);
-    if (counts) counts[R] = 0;
+    if (lane == 0) {
+      atomicOr(err, 1);
+      counts[R] = 0;
+      toff[R] = 0;
+    }
     continue;
   }
   // bitonic sort of the keys (padded to a power of two with the largest key)
@@ -643,15 +650,17 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
       }
       __syncwarp();
     }
-  // runs of equal columns: starts, their number and (fill) their slots
-  int o0 = counts ? 0 : ptr[R];
+  // runs of equal columns: starts, their number and their staging slots
+  int o0 = 0;
+  if (lane == 0 && n) o0 = atomicAdd(cursor, n);
+  o0 = __shfl_sync(0xffffffffu, o0, 0);
   int run = 0;
   for (int base = 0; base < n; base += 32) {
     const int i = base + lane;
     const bool start = i < n && (i == 0 || (K[i] >> 10) != (K[i - 1] >> 10));
     int tot;
     const int slot = run + warp_excl_scan(start ? 1 : 0, lane, tot);
-    if (start && !counts) {
+    if (start) {
       const unsigned long long J = K[i] >> 10;
       double v = 0.0;
       unsigned char b = 0;
@@ -660,14 +669,16 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
         v += V[t];
         b |= B[t];
       }
-      col[o0 + slot] = (int)J;
-      val[o0 + slot] = v;
-      if (val32) val32[o0 + slot] = (float)v;
-      bits[o0 + slot] = b;
+      tcol[o0 + slot] = (int)J;
+      tval[o0 + slot] = v;
+      tbits[o0 + slot] = b;
     }
     run += tot;
   }
-  if (counts && lane == 0) counts[R] = run;
+  if (lane == 0) {
+    counts[R] = run;
+    toff[R] = o0;
+  }
   __syncwarp();
   }
 }
@@ -954,6 +965,28 @@ __global__ void __launch_bounds__(NT) k_scan_apply(int* __restrict__ data, long 
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// The staged rows of U_c into its CSR arrays (ptr: the scanned counts), a
+// warp per row.
+__global__ void __launch_bounds__(256) k_ucopy(int nr, const int* __restrict__ ptr,
+                                               const int* __restrict__ toff,
+                                               const int* __restrict__ tcol,
+                                               const double* __restrict__ tval,
+                                               const unsigned char* __restrict__ tbits,
+                                               int* __restrict__ col, double* __restrict__ val,
+                                               float* __restrict__ val32,
+                                               unsigned char* __restrict__ bits) {
+  const int R = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (R >= nr) return;
+  const int o = ptr[R], n = ptr[R + 1] - o, t = toff[R];
+  for (int i = lane; i < n; i += 32) {
+    const double v = tval[t + i];
+    col[o + i] = tcol[t + i];
+    val[o + i] = v;
+    if (val32) val32[o + i] = (float)v;
+    bits[o + i] = tbits[t + i];
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1015,7 +1048,7 @@ void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStrea
 
 // The three forms of the coupling-row merge: a thread per row of at most UT
 // candidates over every row, then the warp forms (fixed grids of a few blocks
-// per SM) over the rows the counting pass listed: midrows (more than UT
+// per SM) over the rows the form before listed: midrows (more than UT
 // candidates, up to UW_SMALL) and longrows (more than UW_SMALL).  lists:
 // 2 (nr + 1) ints, midrows then longrows.
 // The thread form runs first only where the fine level's coupling rows are
@@ -1024,46 +1057,42 @@ void launch_urows(const Level& Cl, const int* scan, const int* marker, cudaStrea
 // walks every row.
 bool urow_thread_form(const Level& F) { return 3ll * F.nnz <= 8ll * F.nr; }
 
-void launch_urow(const Level& F, const Level& Cl, int* lists, const int* fr,
-                 const double* frw, const int* ptr, int* counts, int* col, double* val,
-                 float* val32, unsigned char* bits, int* err, cudaStream_t st) {
+void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
+                  const double* frw, int* counts, const UStage& t, int* err, cudaStream_t st) {
+  if (Cl.nr == 0) return;
   const bool thr = urow_thread_form(F);
   int* midrows = thr ? lists : nullptr;
   int* longrows = lists + Cl.nr + 1;
+  SSAMG_CUDA(cudaMemsetAsync(lists, 0, sizeof(int), st));
+  SSAMG_CUDA(cudaMemsetAsync(longrows, 0, sizeof(int), st));
+  SSAMG_CUDA(cudaMemsetAsync(t.cursor, 0, sizeof(int), st));
   int dev = 0, sms = 0;
   SSAMG_CUDA(cudaGetDevice(&dev));
   SSAMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (thr) {
     k_urow_t<<<cdiv(Cl.nr, 256), 256, 0, st>>>(F.view<double>(), Cl.nr, midrows, fr, frw,
-                                                F.u_pj, F.u_pw, ptr, counts, col, val, val32,
-                                                bits);
+                                                F.u_pj, F.u_pw, counts, t.toff, t.cursor,
+                                                t.col, t.val, t.bits);
     SSAMG_LAUNCH_CHECK();
   }
   const int nbs = thr ? std::min(cdiv(Cl.nr, UWARPS_SMALL), 4 * sms) : cdiv(Cl.nr, UWARPS_SMALL);
-  k_urow<UW_SMALL, UWARPS_SMALL><<<nbs, 32 * UWARPS_SMALL, 0,
-                                   st>>>(F.view<double>(), Cl.nr, midrows, longrows, fr, frw,
-                                         F.u_pj, F.u_pw, ptr, counts, col, val, val32, bits, err);
+  k_urow<UW_SMALL, UWARPS_SMALL><<<nbs, 32 * UWARPS_SMALL, 0, st>>>(
+      F.view<double>(), Cl.nr, midrows, longrows, fr, frw, F.u_pj, F.u_pw, counts, t.toff,
+      t.cursor, t.col, t.val, t.bits, err);
   SSAMG_LAUNCH_CHECK();
-  k_urow<UW_LARGE, UWARPS_LARGE><<<std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms), 32 * UWARPS_LARGE, 0,
-                                   st>>>(F.view<double>(), Cl.nr, midrows, longrows, fr, frw,
-                                         F.u_pj, F.u_pw, ptr, counts, col, val, val32, bits, err);
+  k_urow<UW_LARGE, UWARPS_LARGE><<<std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms),
+                                   32 * UWARPS_LARGE, 0, st>>>(
+      F.view<double>(), Cl.nr, midrows, longrows, fr, frw, F.u_pj, F.u_pw, counts, t.toff,
+      t.cursor, t.col, t.val, t.bits, err);
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_ucount(const Level& F, const Level& Cl, int* lists, const int* fr,
-                   const double* frw, int* counts, int* err, cudaStream_t st) {
-  if (Cl.nr == 0) return;
-  SSAMG_CUDA(cudaMemsetAsync(lists, 0, sizeof(int), st));
-  SSAMG_CUDA(cudaMemsetAsync(lists + Cl.nr + 1, 0, sizeof(int), st));
-  launch_urow(F, Cl, lists, fr, frw, nullptr, counts, nullptr, nullptr, nullptr, nullptr, err,
-              st);
-}
-
-void launch_ufill(const Level& F, const Level& Cl, int* lists, const int* fr,
-                  const double* frw, bool fp32, int* err, cudaStream_t st) {
-  if (Cl.nr == 0) return;
-  launch_urow(F, Cl, lists, fr, frw, Cl.u_ptr, nullptr, Cl.u_col, Cl.u_val,
-              fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, err, st);
+void launch_ucopy(const Level& Cl, const UStage& t, bool fp32, cudaStream_t st) {
+  if (Cl.nr == 0 || Cl.nnz == 0) return;
+  k_ucopy<<<cdiv(Cl.nr, 8), 256, 0, st>>>(Cl.nr, Cl.u_ptr, t.toff, t.col, t.val, t.bits,
+                                          Cl.u_col, Cl.u_val, fp32 ? Cl.u_val32 : nullptr,
+                                          Cl.u_bits);
+  SSAMG_LAUNCH_CHECK();
 }
 
 void launch_ucols(const Level* Fp, const Level& L, bool fp32, bool pj, bool rj, cudaStream_t st) {

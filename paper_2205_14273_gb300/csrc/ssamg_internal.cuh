@@ -383,10 +383,17 @@ void launch_frows(const Level& F, const Level& Cl, const int* prI, const double*
                   const signed char* prA, int* fr, double* frw, cudaStream_t st);
 // lists: 2 (Cl.nr + 1) ints (the rows the counting pass lists for the warp
 // forms of the merge, reused by the fill pass).
-void launch_ucount(const Level& F, const Level& Cl, int* longrows, const int* fr,
-                   const double* frw, int* counts, int* err, cudaStream_t st);
-void launch_ufill(const Level& F, const Level& Cl, int* longrows, const int* fr,
-                  const double* frw, bool fp32, int* err, cudaStream_t st);
+// Staging of the rows of U_c = P^T U P (sorted once, copied once counted).
+struct UStage {
+  int* toff;    // first staging slot of each coarse row
+  int* cursor;  // next free staging slot
+  int* col;
+  double* val;
+  unsigned char* bits;
+};
+void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
+                  const double* frw, int* counts, const UStage& t, int* err, cudaStream_t st);
+void launch_ucopy(const Level& Cl, const UStage& t, bool fp32, cudaStream_t st);
 void launch_umap_level0(const Level& L, cudaStream_t st);
 void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
