@@ -152,6 +152,8 @@ struct ssamg_solver_s {
   PcgScalars* h_sc = nullptr;  // pinned
   int* h_int = nullptr;        // pinned scratch
   double* h_dbl = nullptr;
+  char* h_up = nullptr;        // pinned staging of the level tables (one copy per set-up)
+  size_t h_up_cap = 0;
   int* d_err = nullptr;
   // problems: one, or a batch of independent problems in one hierarchy
   int nprob = 1;
@@ -177,6 +179,7 @@ struct ssamg_solver_s {
     if (h_sc) cudaFreeHost(h_sc);
     if (h_int) cudaFreeHost(h_int);
     if (h_dbl) cudaFreeHost(h_dbl);
+    if (h_up) cudaFreeHost(h_up);
   }
 };
 
@@ -695,10 +698,23 @@ bool valid_tile(int t) {
   return t == 0 || (k >= 1 && k <= SSAMG_CPT_LARGE);
 }
 
-void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) {
+// Block starts of a level's launches and the first cell of every part (host
+// side of the level's device tables).
+struct LevelTables {
+  std::vector<int> blk, bblk, fblk, cs;
+};
+
+// The host side of a level's tables: part descriptors (L.dparts), tile and
+// brick decomposition, operator-apply shape.  Copies nothing.
+void level_tables(ssamg_solver s, Level& L, const Level* next, LevelTables& t) {
   const int np = L.np;
   L.dparts.assign(np, DPart{});
-  std::vector<int> blk(np + 1, 0), fblk(np + 1, 0), cs(np + 1, 0);
+  std::vector<int>& blk = t.blk;
+  std::vector<int>& fblk = t.fblk;
+  std::vector<int>& cs = t.cs;
+  blk.assign(np + 1, 0);
+  fblk.assign(np + 1, 0);
+  cs.assign(np + 1, 0);
   const long long ntot = level_cells(L);
   // tile form: the table's entry for the level's size class, else the
   // built-in rule (SSAMG_CPT_LARGE cells per thread on large levels)
@@ -715,7 +731,8 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
   L.nblk = blk[np];
   L.nfblk = fblk[np];
   // bricks (checked 7-point operator applies)
-  std::vector<int> bblk(np + 1, 0);
+  std::vector<int>& bblk = t.bblk;
+  bblk.assign(np + 1, 0);
   for (int p = 0; p < np; ++p) {
     const PartH& h = L.parts[p];
     const long long nb = cdivll(h.n[0], SSAMG_BRICK_X) * cdivll(h.n[1], SSAMG_BRICK_Y) *
@@ -748,13 +765,6 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
       dp.cdxy = make_fastdiv(c.n[0] * c.n[1]);
     }
   }
-  if (!L.d_parts) {
-    L.d_parts = aalloc<DPart>(s->arena, np);
-    L.d_blk = aalloc<int>(s->arena, np + 1);
-    L.d_bblk = aalloc<int>(s->arena, np + 1);
-    L.d_fblk = aalloc<int>(s->arena, np + 1);
-    L.d_cellstart = aalloc<int>(s->arena, np + 1);
-  }
   {
     // operator-apply shape shared by all parts (see StencilShape)
     bool unchecked = true, all27 = true, all7 = true, all15 = true, canon7 = true;
@@ -775,11 +785,67 @@ void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) 
     for (const DPart& dp : L.dparts)
       L.kvar = std::max(L.kvar, dp.varmask == 0 ? 0 : dp.varmask == 1u ? 1 : 2);
   }
+}
+
+// One level's tables, copied on their own (level 0 before the coupling sums,
+// and a level whose coupling rows vanished).  The copies are from pageable
+// memory, so they are done when the call returns.
+void upload_level(ssamg_solver s, Level& L, const Level* next, cudaStream_t st) {
+  LevelTables t;
+  level_tables(s, L, next, t);
+  const int np = L.np;
+  if (!L.d_parts) {
+    L.d_parts = aalloc<DPart>(s->arena, np);
+    L.d_blk = aalloc<int>(s->arena, np + 1);
+    L.d_bblk = aalloc<int>(s->arena, np + 1);
+    L.d_fblk = aalloc<int>(s->arena, np + 1);
+    L.d_cellstart = aalloc<int>(s->arena, np + 1);
+  }
   SSAMG_CUDA(cudaMemcpyAsync(L.d_parts, L.dparts.data(), sizeof(DPart) * np, cudaMemcpyHostToDevice, st));
-  SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
-  SSAMG_CUDA(cudaMemcpyAsync(L.d_bblk, bblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
-  SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
-  SSAMG_CUDA(cudaMemcpyAsync(L.d_cellstart, cs.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_blk, t.blk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_bblk, t.bblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_fblk, t.fblk.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(L.d_cellstart, t.cs.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st));
+}
+
+// Every level's tables in one device block, through one pinned staging
+// buffer and one copy.  The buffer is reused by the next set-up, which
+// starts after this one has synchronised the stream.
+void upload_levels(ssamg_solver s, cudaStream_t st) {
+  const int nl = (int)s->lev.size();
+  std::vector<LevelTables> t(nl);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t total = 0;
+  for (int l = 0; l < nl; ++l) {
+    level_tables(s, s->lev[l], l + 1 < nl ? &s->lev[l + 1] : nullptr, t[l]);
+    const size_t np = (size_t)s->lev[l].np;
+    total += al(sizeof(DPart) * np) + 4 * al(sizeof(int) * (np + 1));
+  }
+  if (s->h_up_cap < total) {
+    if (s->h_up) cudaFreeHost(s->h_up);
+    s->h_up = nullptr;
+    s->h_up_cap = 0;
+    SSAMG_CUDA(cudaMallocHost(&s->h_up, total));
+    s->h_up_cap = total;
+  }
+  char* dev = (char*)s->arena.alloc(total);
+  size_t o = 0;
+  auto put = [&](const void* src, size_t bytes) {
+    std::memcpy(s->h_up + o, src, bytes);
+    void* d = dev + o;
+    o += al(bytes);
+    return d;
+  };
+  for (int l = 0; l < nl; ++l) {
+    Level& L = s->lev[l];
+    const size_t np = (size_t)L.np;
+    L.d_parts = (DPart*)put(L.dparts.data(), sizeof(DPart) * np);
+    L.d_blk = (int*)put(t[l].blk.data(), sizeof(int) * (np + 1));
+    L.d_bblk = (int*)put(t[l].bblk.data(), sizeof(int) * (np + 1));
+    L.d_fblk = (int*)put(t[l].fblk.data(), sizeof(int) * (np + 1));
+    L.d_cellstart = (int*)put(t[l].cs.data(), sizeof(int) * (np + 1));
+  }
+  SSAMG_CUDA(cudaMemcpyAsync(dev, s->h_up, o, cudaMemcpyHostToDevice, st));
 }
 
 // Coarse-level transition run by one cluster (see kernels_tail.cu): picks the
@@ -1125,18 +1191,31 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     }
     L.dinv = aalloc<double>(s->arena, L.N);
     if (fp32) L.dinv32 = aalloc<float>(s->arena, L.N);
-    size_t w = fp32 ? sizeof(float) : sizeof(double);
     L.guard = 0;
     for (auto& h : L.parts) L.guard = std::max<long long>(L.guard, 1 + h.n[0] + (long long)h.n[0] * h.n[1]);
-    L.x = padded_vector(s, w, L.N, L.guard, st);
-    L.b = padded_vector(s, w, L.N, L.guard, st);
-    L.r = padded_vector(s, w, L.N, L.guard, st);
-    L.t = padded_vector(s, w, L.N, L.guard, st);
     bool any_u = false;
     for (auto& h : L.parts) any_u |= h.has_u != 0;
     if (l > 0 && any_u) L.u_map = aalloc<int>(s->arena, L.N);
   }
-  for (int l = 0; l <= Lc; ++l) upload_level(s, s->lev[l], l < Lc ? &s->lev[l + 1] : nullptr, st);
+  {
+    // the cycle vectors x, b, r, t of every level (guard cells around each):
+    // one zeroed block
+    const size_t w = fp32 ? sizeof(float) : sizeof(double);
+    auto vb = [&](const Level& L) { return (w * (size_t)(L.N + 2 * L.guard) + 255) & ~(size_t)255; };
+    size_t total = 0;
+    for (int l = 0; l <= Lc; ++l) total += 4 * vb(s->lev[l]);
+    char* base = (char*)s->arena.alloc(total);
+    SSAMG_CUDA(cudaMemsetAsync(base, 0, total, st));
+    for (int l = 0; l <= Lc; ++l) {
+      Level& L = s->lev[l];
+      void** v[4] = {&L.x, &L.b, &L.r, &L.t};
+      for (void** q : v) {
+        *q = base + w * (size_t)L.guard;
+        base += vb(L);
+      }
+    }
+  }
+  upload_levels(s, st);
 
   if (fp32) {
     launch_to_float(L0.coef, L0.coef32, L0.ncoef, st);
@@ -1153,62 +1232,89 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   int* scan_tmp = nullptr;
   s->d_err = aalloc<int>(s->arena, 4);
   SSAMG_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int) * 4, st));
+  // The coupling rows of a coarse level are fixed by the structure alone
+  // (which coarse cells the fine coupling rows' P rows reach), so they are
+  // found one level ahead: each level waits on the host once, for the entry
+  // count of its own U_c and the row count of the next level together.
+  auto mark_rows = [&](const Level& F, const Level& C) {
+    if (!marker) {
+      marker = aalloc<int>(s->arena, maxN + 1);
+      scan_tmp = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
+    }
+    launch_uprow(F, C, nullptr, nullptr, nullptr, marker, st);
+    launch_scan(marker, C.N, scan_tmp, st);
+  };
+  auto make_rows = [&](Level& C, int nr) {
+    C.nr = nr;
+    C.u_rows = aalloc<int>(s->arena, C.nr);
+    C.u_ptr = aalloc<int>(s->arena, C.nr + 1);
+    launch_urows(C, marker, nullptr, st);
+  };
+  if (Lc > 0) {
+    if (L0.nr > 0) {
+      mark_rows(L0, s->lev[1]);
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_int, marker + s->lev[1].N, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+      SSAMG_CUDA(cudaStreamSynchronize(st));
+      make_rows(s->lev[1], s->h_int[0]);
+    } else {
+      s->lev[1].nr = 0;
+    }
+  }
   for (int l = 0; l < Lc; ++l) {
     Level& F = s->lev[l];
     Level& C = s->lev[l + 1];
+    Level* N2 = l + 2 <= Lc ? &s->lev[l + 2] : nullptr;
     launch_interp(F, fp32, st);
     launch_rap_struct(F, C, fp32, st);
-    if (F.nr > 0) {
-      if (!marker) {
-        marker = aalloc<int>(s->arena, maxN + 1);
-        scan_tmp = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
-      }
-      // P rows of the coupling columns (kept: the prolongation's row jobs use them)
-      F.u_pj = aalloc<int>(s->arena, 2 * F.nnz);
-      F.u_pw = aalloc<double>(s->arena, 2 * F.nnz);
-      if (fp32) F.u_pw32 = aalloc<float>(s->arena, 2 * F.nnz);
-      launch_ucols(nullptr, F, fp32, true, false, st);
-      // P rows of the coupling rows, and the coarse rows they reach
-      int* prI = aalloc<int>(s->arena, 2ll * F.nr);
-      double* prW = aalloc<double>(s->arena, 2ll * F.nr);
-      signed char* prA = aalloc<signed char>(s->arena, 2ll * F.nr);
-      launch_uprow(F, C, prI, prW, prA, marker, st);
-      launch_scan(marker, C.N, scan_tmp, st);
-      SSAMG_CUDA(cudaMemcpyAsync(s->h_int, marker + C.N, sizeof(int), cudaMemcpyDeviceToHost, st));
-      SSAMG_CUDA(cudaStreamSynchronize(st));
-      C.nr = s->h_int[0];
-      C.u_rows = aalloc<int>(s->arena, C.nr);
-      C.u_ptr = aalloc<int>(s->arena, C.nr + 1);
-      launch_urows(C, marker, nullptr, st);
-      if (C.nr > 0) {
-        int* fr = aalloc<int>(s->arena, 3ll * C.nr);
-        double* frw = aalloc<double>(s->arena, 3ll * C.nr);
-        int* longrows = aalloc<int>(s->arena, 2 * (C.nr + 1ll));
-        launch_frows(F, C, prI, prW, prA, fr, frw, st);
-        // staging for the sorted rows: a row has at most as many entries as
-        // candidates, and a fine row feeds at most two coarse rows with two
-        // columns per coupling, so 4 nnz of the fine level bound the total
-        UStage ust;
-        ust.toff = aalloc<int>(s->arena, C.nr);
-        ust.cursor = aalloc<int>(s->arena, 1);
-        ust.col = aalloc<int>(s->arena, 4 * F.nnz);
-        ust.val = aalloc<double>(s->arena, 4 * F.nnz);
-        ust.bits = aalloc<unsigned char>(s->arena, 4 * F.nnz);
-        launch_usort(F, C, longrows, fr, frw, C.u_ptr, ust, s->d_err, st);
-        launch_scan(C.u_ptr, C.nr, scan_tmp, st);
-        SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SSAMG_CUDA(cudaStreamSynchronize(st));
-        C.nnz = s->h_int[0];
-        C.u_col = aalloc<int>(s->arena, C.nnz);
-        C.u_val = aalloc<double>(s->arena, C.nnz);
-        C.u_bits = aalloc<unsigned char>(s->arena, C.nnz);
-        if (fp32) C.u_val32 = aalloc<float>(s->arena, C.nnz);
-        launch_ucopy(C, ust, fp32, st);
-      }
-    } else {
-      C.nr = 0;
-      C.nnz = 0;
+    C.nnz = 0;
+    if (N2) N2->nr = 0;
+    if (F.nr == 0) continue;
+    // P rows of the coupling columns (kept: the prolongation's row jobs use them)
+    F.u_pj = aalloc<int>(s->arena, 2 * F.nnz);
+    F.u_pw = aalloc<double>(s->arena, 2 * F.nnz);
+    if (fp32) F.u_pw32 = aalloc<float>(s->arena, 2 * F.nnz);
+    launch_ucols(nullptr, F, fp32, true, false, st);
+    if (C.nr == 0) continue;
+    // P rows of the coupling rows, and the coarse rows they reach
+    int* prI = aalloc<int>(s->arena, 2ll * F.nr);
+    double* prW = aalloc<double>(s->arena, 2ll * F.nr);
+    signed char* prA = aalloc<signed char>(s->arena, 2ll * F.nr);
+    launch_uprow(F, C, prI, prW, prA, nullptr, st);
+    int* fr = aalloc<int>(s->arena, 3ll * C.nr);
+    double* frw = aalloc<double>(s->arena, 3ll * C.nr);
+    int* longrows = aalloc<int>(s->arena, 2 * (C.nr + 1ll));
+    launch_frows(F, C, prI, prW, prA, fr, frw, st);
+    // staging for the sorted rows: a row has at most as many entries as
+    // candidates, and a fine row feeds at most two coarse rows with two
+    // columns per coupling, so 4 nnz of the fine level bound the total
+    UStage ust;
+    ust.toff = aalloc<int>(s->arena, C.nr);
+    ust.cursor = aalloc<int>(s->arena, 1);
+    ust.col = aalloc<int>(s->arena, 4 * F.nnz);
+    ust.val = aalloc<double>(s->arena, 4 * F.nnz);
+    ust.bits = aalloc<unsigned char>(s->arena, 4 * F.nnz);
+    launch_usort(F, C, longrows, fr, frw, C.u_ptr, ust, s->d_err, st);
+    launch_scan(C.u_ptr, C.nr, scan_tmp, st);
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (N2) {
+      mark_rows(C, *N2);
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_int + 1, marker + N2->N, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
     }
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+    C.nnz = s->h_int[0];
+    C.u_col = aalloc<int>(s->arena, C.nnz);
+    C.u_val = aalloc<double>(s->arena, C.nnz);
+    C.u_bits = aalloc<unsigned char>(s->arena, C.nnz);
+    if (fp32) C.u_val32 = aalloc<float>(s->arena, C.nnz);
+    // the restriction onto C also pre-relaxes it (with U x): each coupling's
+    // restriction row, made as the rows are copied
+    C.u_rj = aalloc<int>(s->arena, 3 * C.nnz);
+    C.u_rw = aalloc<double>(s->arena, 2 * C.nnz);
+    if (fp32) C.u_rw32 = aalloc<float>(s->arena, 2 * C.nnz);
+    launch_ucopy(F, C, ust, fp32, st);
+    if (N2) make_rows(*N2, s->h_int[1]);
   }
   // has_u may be set on parts whose coarse rows vanished; refresh from U_c
   for (int l = 1; l <= Lc; ++l) {
@@ -1224,33 +1330,39 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     }
   }
 
-  // ---- row-job data: dense U x buffers and P rows of coupling columns
-  for (int l = 0; l <= Lc; ++l) {
-    Level& L = s->lev[l];
-    // lanes per row: the mean row length rounded up to a power of two,
-    // between SSAMG_TPR and SSAMG_TPR_MAX (coarse levels' rows grow long)
-    L.tpr = SSAMG_TPR;
-    while (L.tpr < SSAMG_TPR_MAX && (long long)L.tpr * L.nr < L.nnz) L.tpr *= 2;
-    L.nublk = (int)cdivll(L.nr, SSAMG_BLOCK / L.tpr);
-    if (L.nr == 0) continue;
-    L.uy64 = aalloc<double>(s->arena, L.N);
-    SSAMG_CUDA(cudaMemsetAsync(L.uy64, 0, sizeof(double) * L.N, st));
-    if (fp32) {
-      L.uy32 = aalloc<float>(s->arena, L.N);
-      SSAMG_CUDA(cudaMemsetAsync(L.uy32, 0, sizeof(float) * L.N, st));
+  // ---- row-job data: dense U x buffers (one zeroed block); the P rows
+  // (u_pj) and restriction rows (u_rj) of the coupling columns were made
+  // with each level's P^T U P
+  {
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    size_t total = 0;
+    for (int l = 0; l <= Lc; ++l) {
+      Level& L = s->lev[l];
+      // lanes per row: the mean row length rounded up to a power of two,
+      // between SSAMG_TPR and SSAMG_TPR_MAX (coarse levels' rows grow long)
+      L.tpr = SSAMG_TPR;
+      while (L.tpr < SSAMG_TPR_MAX && (long long)L.tpr * L.nr < L.nnz) L.tpr *= 2;
+      L.nublk = (int)cdivll(L.nr, SSAMG_BLOCK / L.tpr);
+      if (L.nr > 0) total += al(sizeof(double) * L.N) + (fp32 ? al(sizeof(float) * L.N) : 0);
     }
-    // (P rows of the coupling columns, L.u_pj, were made with the level's P^T U P)
-    if (l > 0) {
-      // the restriction onto this level also pre-relaxes it (with U x)
-      L.u_rj = aalloc<int>(s->arena, 3 * L.nnz);
-      L.u_rw = aalloc<double>(s->arena, 2 * L.nnz);
-      if (fp32) L.u_rw32 = aalloc<float>(s->arena, 2 * L.nnz);
-      launch_ucols(&s->lev[l - 1], L, fp32, false, true, st);
+    if (total > 0) {
+      char* base = (char*)s->arena.alloc(total);
+      SSAMG_CUDA(cudaMemsetAsync(base, 0, total, st));
+      for (int l = 0; l <= Lc; ++l) {
+        Level& L = s->lev[l];
+        if (L.nr == 0) continue;
+        L.uy64 = (double*)base;
+        base += al(sizeof(double) * L.N);
+        if (fp32) {
+          L.uy32 = (float*)base;
+          base += al(sizeof(float) * L.N);
+        }
+      }
     }
   }
 
   // ---- Section 3.4: smoother diagonals
-  for (int l = 0; l <= Lc; ++l) launch_dinv(s->lev[l], s->prm.relax, s->prm.relax_factor, fp32, st);
+  launch_dinv(s->lev, s->prm.relax, s->prm.relax_factor, fp32, st);
 
   // ---- coarsest level: dense Cholesky (FP64)
   Level& LL = s->lev[Lc];

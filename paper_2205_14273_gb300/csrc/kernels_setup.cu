@@ -342,7 +342,8 @@ __device__ __forceinline__ void locate(const LevelView<double>& L, const DPart* 
 // coarse columns I with weights P(f, I) and the position a of f relative to
 // I's anchor along d* (a = 0: f is I's coarse point or its part is not
 // coarsened; +1: I is f's west neighbour; -1: its east neighbour), and the
-// marker of the coarse rows of U_c.
+// marker of the coarse rows of U_c.  Either output may be null: the marker
+// alone needs no weights (it is taken before the level's interpolation).
 __global__ void k_uprow(LevelView<double> F, int nr, const int* __restrict__ rows,
                         int* __restrict__ prI, double* __restrict__ prW,
                         signed char* __restrict__ prA, int* __restrict__ marker) {
@@ -370,21 +371,23 @@ __global__ void k_uprow(LevelView<double> F, int nr, const int* __restrict__ row
       const int Fi = fp.poff + fine_point_index(fp, i, j, k);
       if (cd - 1 >= 0) {
         I[0] = at((cd - 1 - fp.par) >> 1);
-        w[0] = F.Pw[Fi];
+        if (prW) w[0] = F.Pw[Fi];
         a[0] = 1;
       }
       if (cd + 1 < fp.n[d]) {
         I[1] = at((cd + 1 - fp.par) >> 1);
-        w[1] = F.Pe[Fi];
+        if (prW) w[1] = F.Pe[Fi];
         a[1] = -1;
       }
     }
   }
   for (int t = 0; t < 2; ++t) {
-    prI[2 * r + t] = I[t];
-    prW[2 * r + t] = w[t];
-    prA[2 * r + t] = a[t];
-    if (I[t] >= 0) marker[I[t]] = 1;
+    if (prI) {
+      prI[2 * r + t] = I[t];
+      prW[2 * r + t] = w[t];
+      prA[2 * r + t] = a[t];
+    }
+    if (marker && I[t] >= 0) marker[I[t]] = 1;
   }
 }
 
@@ -703,11 +706,11 @@ __device__ __forceinline__ void upcol(const LevelView<double>& F, long long q,
 // Restriction row of each coupling's column cell on a coarse level: the
 // fine cells (centre, -d*, +d* neighbours; -1 absent) and the side weights
 // (PE of the -d* fine point, PW of the +d*), as the restriction applies them.
-__device__ __forceinline__ void urcol(const LevelView<double>& F, const LevelView<double>& C,
-                                      long long q, int* __restrict__ rj, double* __restrict__ rw,
-                                      float* __restrict__ rw32) {
+__device__ __forceinline__ void urcol_at(const LevelView<double>& F, const LevelView<double>& C,
+                                         int col, long long q, int* __restrict__ rj,
+                                         double* __restrict__ rw, float* __restrict__ rw32) {
   int p, I[3];
-  locate(C, C.parts, C.u_col[q], p, I[0], I[1], I[2]);
+  locate(C, C.parts, col, p, I[0], I[1], I[2]);
   const DPart& fp = F.parts[p];
   const int d = fp.dstar;
   int j0, j1 = -1, j2 = -1;
@@ -742,6 +745,12 @@ __device__ __forceinline__ void urcol(const LevelView<double>& F, const LevelVie
   }
 }
 
+__device__ __forceinline__ void urcol(const LevelView<double>& F, const LevelView<double>& C,
+                                      long long q, int* __restrict__ rj, double* __restrict__ rw,
+                                      float* __restrict__ rw32) {
+  urcol_at(F, C, C.u_col[q], q, rj, rw, rw32);
+}
+
 // Setup data of a level's row jobs, per coupling: P's row of its column cell
 // (with pj: the prolongation's U x) and its restriction row from the level
 // above (with rj: the pre-relaxation fused into the restriction onto it).
@@ -762,20 +771,46 @@ __global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ 
 // ---------------------------------------------------------------------------
 // K5: diagonal of omega M^-1 (Section 3.4).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, double factor,
-                                             double* __restrict__ dinv, float* __restrict__ dinv32) {
+// Every level's smoother diagonal in one launch: block b works on the level
+// whose block range holds it (the levels' tile grids one after another).
+struct DinvLevel {
+  const DPart* parts;
+  const int* blk;
+  const double* coef;
+  const int* u_map;
+  const int* u_ptr;
+  const double* u_val;
+  double* dinv;
+  float* dinv32;
+  int np;
+  int b0;  // first block of the level in the launch
+};
+struct DinvArgs {
+  int nl;
+  int relax;
+  double factor;
+  DinvLevel lv[SSAMG_DINV_LEVELS];
+};
+
+__global__ void __launch_bounds__(NT) k_dinv(const __grid_constant__ DinvArgs A) {
   __shared__ DPart sp;
-  int p = block_part(L.blk, L.parts, L.np, sp);
+  int l = 0;
+  while (l + 1 < A.nl && (int)blockIdx.x >= A.lv[l + 1].b0) ++l;
+  const DinvLevel& L = A.lv[l];
+  const int tile = (int)blockIdx.x - L.b0;
+  block_part(L.blk, L.parts, L.np, sp, tile);
   __syncthreads();
-  TILE_LOOP(c, sp) {
+#pragma unroll 1
+  for (int m = 0, c = (tile - sp.blk0) * sp.cpt * SSAMG_BLOCK + (int)threadIdx.x;
+       m < sp.cpt && c < sp.ncell; ++m, c += SSAMG_BLOCK) {
     int i, j, k;
     cell_coords(sp, c, i, j, k);
     double v;
-    if (relax == 0) {
+    if (A.relax == 0) {
       double diag = 0.0;
       for (int e = 0; e < sp.nent; ++e)
         if (sp.o[e][0] == 0 && sp.o[e][1] == 0 && sp.o[e][2] == 0) diag += coef_at(sp, L.coef, e, c);
-      double w = factor > 0.0 ? factor : sp.omega;
+      double w = A.factor > 0.0 ? A.factor : sp.omega;
       v = w / diag;
     } else {
       double s = 0.0;
@@ -787,12 +822,12 @@ __global__ void __launch_bounds__(NT) k_dinv(LevelView<double> L, int relax, dou
         if (r >= 0)
           for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) s += fabs(L.u_val[q]);
       }
-      double w = factor > 0.0 ? factor : 1.5;
+      double w = A.factor > 0.0 ? A.factor : 1.5;
       v = w / s;
     }
     if (sp.skip) v = 0.0;  // relaxation turned off: omega M^-1 = 0
-    dinv[sp.off + c] = v;
-    if (dinv32) dinv32[sp.off + c] = (float)v;
+    L.dinv[sp.off + c] = v;
+    if (L.dinv32) L.dinv32[sp.off + c] = (float)v;
   }
 }
 
@@ -966,24 +1001,31 @@ __global__ void __launch_bounds__(NT) k_scan_apply(int* __restrict__ data, long 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // The staged rows of U_c into its CSR arrays (ptr: the scanned counts), a
-// warp per row.
-__global__ void __launch_bounds__(256) k_ucopy(int nr, const int* __restrict__ ptr,
+// warp per row, and with every entry its restriction row from the level
+// above (the row jobs' data for the pre-relaxation fused into the
+// restriction, as k_ucols makes it).
+__global__ void __launch_bounds__(256) k_ucopy(LevelView<double> F, LevelView<double> C, int nr,
+                                               const int* __restrict__ ptr,
                                                const int* __restrict__ toff,
                                                const int* __restrict__ tcol,
                                                const double* __restrict__ tval,
                                                const unsigned char* __restrict__ tbits,
                                                int* __restrict__ col, double* __restrict__ val,
                                                float* __restrict__ val32,
-                                               unsigned char* __restrict__ bits) {
+                                               unsigned char* __restrict__ bits,
+                                               int* __restrict__ rj, double* __restrict__ rw,
+                                               float* __restrict__ rw32) {
   const int R = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (R >= nr) return;
   const int o = ptr[R], n = ptr[R + 1] - o, t = toff[R];
   for (int i = lane; i < n; i += 32) {
     const double v = tval[t + i];
-    col[o + i] = tcol[t + i];
+    const int J = tcol[t + i];
+    col[o + i] = J;
     val[o + i] = v;
     if (val32) val32[o + i] = (float)v;
     bits[o + i] = tbits[t + i];
+    if (rj) urcol_at(F, C, J, o + i, rj, rw, rw32);
   }
 }
 
@@ -1024,7 +1066,7 @@ void launch_rap_struct(const Level& F, const Level& Cl, bool fp32, cudaStream_t 
 
 void launch_uprow(const Level& F, const Level& Cl, int* prI, double* prW, signed char* prA,
                   int* marker, cudaStream_t st) {
-  SSAMG_CUDA(cudaMemsetAsync(marker, 0, sizeof(int) * (Cl.N + 1), st));
+  if (marker) SSAMG_CUDA(cudaMemsetAsync(marker, 0, sizeof(int) * (Cl.N + 1), st));
   if (F.nr > 0) {
     k_uprow<<<cdiv(F.nr, NT), NT, 0, st>>>(F.view<double>(), F.nr, F.u_rows, prI, prW, prA,
                                           marker);
@@ -1087,11 +1129,12 @@ void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_ucopy(const Level& Cl, const UStage& t, bool fp32, cudaStream_t st) {
+void launch_ucopy(const Level& F, const Level& Cl, const UStage& t, bool fp32, cudaStream_t st) {
   if (Cl.nr == 0 || Cl.nnz == 0) return;
-  k_ucopy<<<cdiv(Cl.nr, 8), 256, 0, st>>>(Cl.nr, Cl.u_ptr, t.toff, t.col, t.val, t.bits,
-                                          Cl.u_col, Cl.u_val, fp32 ? Cl.u_val32 : nullptr,
-                                          Cl.u_bits);
+  k_ucopy<<<cdiv(Cl.nr, 8), 256, 0, st>>>(F.view<double>(), Cl.view<double>(), Cl.nr, Cl.u_ptr,
+                                          t.toff, t.col, t.val, t.bits, Cl.u_col, Cl.u_val,
+                                          fp32 ? Cl.u_val32 : nullptr, Cl.u_bits, Cl.u_rj,
+                                          Cl.u_rw, fp32 ? Cl.u_rw32 : nullptr);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -1114,9 +1157,22 @@ void launch_umap_level0(const Level& L, cudaStream_t st) {
   }
 }
 
-void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st) {
-  k_dinv<<<L.nblk, NT, 0, st>>>(L.view<double>(), relax, factor, L.dinv, fp32 ? L.dinv32 : nullptr);
-  SSAMG_LAUNCH_CHECK();
+void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
+                 cudaStream_t st) {
+  for (size_t l0 = 0; l0 < lev.size(); l0 += SSAMG_DINV_LEVELS) {
+    DinvArgs a{};
+    a.relax = relax;
+    a.factor = factor;
+    int nb = 0;
+    for (size_t l = l0; l < lev.size() && a.nl < SSAMG_DINV_LEVELS; ++l) {
+      const Level& L = lev[l];
+      a.lv[a.nl++] = DinvLevel{L.d_parts, L.d_blk, L.coef, L.u_map, L.u_ptr, L.u_val,
+                               L.dinv, fp32 ? L.dinv32 : nullptr, L.np, nb};
+      nb += L.nblk;
+    }
+    k_dinv<<<nb, NT, 0, st>>>(a);
+    SSAMG_LAUNCH_CHECK();
+  }
 }
 
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {

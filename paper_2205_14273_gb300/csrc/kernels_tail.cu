@@ -39,20 +39,23 @@ __device__ __forceinline__ unsigned short ctail_pack(int g, int S) {
 
 // Row lengths of the tail levels: entries of S inside the box plus the row's
 // couplings.
-__global__ void k_ctail_rowlen(LevelView<double> L, int* __restrict__ len) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_ctail_rowlen(LevelView<double> L, int* __restrict__ len) {
+  // a warp per row: lane e tests entry e
+  const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= L.N) return;
   const int p = find_part_cell(L.cellstart, L.np, g);
   const DPart& dp = L.parts[p];
   int i, j, k;
   cell_coords(dp, g - dp.off, i, j, k);
-  int n = 0;
-  for (int e = 0; e < dp.nent; ++e) n += inside(dp, i + dp.o[e][0], j + dp.o[e][1], k + dp.o[e][2]);
-  if (dp.has_u && L.u_map) {
-    const int r = L.u_map[g];
-    if (r >= 0) n += L.u_ptr[r + 1] - L.u_ptr[r];
+  const bool ok = lane < dp.nent && inside(dp, i + dp.o[lane][0], j + dp.o[lane][1], k + dp.o[lane][2]);
+  int n = __popc(__ballot_sync(0xffffffffu, ok));
+  if (lane == 0) {
+    if (dp.has_u && L.u_map) {
+      const int r = L.u_map[g];
+      if (r >= 0) n += L.u_ptr[r + 1] - L.u_ptr[r];
+    }
+    len[g] = n;
   }
-  len[g] = n;
 }
 
 // Fills the images of one tail level l: for every row g, in the slice of its
@@ -62,12 +65,15 @@ __global__ void k_ctail_rowlen(LevelView<double> L, int* __restrict__ len) {
 // slices) when Fm is given, and the coarsest inverse's row when inv is
 // given.  The row pointers were written by the host.
 template <class T>
-__global__ void k_ctail_fill(LevelView<double> L, const double* __restrict__ dinv64,
+__global__ void __launch_bounds__(256) k_ctail_fill(LevelView<double> L, const double* __restrict__ dinv64,
                              const LevelView<double> Fm, int has_fm, const LevelView<double> Ln,
                              int has_p, const double* __restrict__ inv, int nL,
                              CTailLevel lv, int Sm, int Sn, char* __restrict__ image,
                              long long ro_bytes) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  // a warp per row: the stencil entries one per lane (slots by ballot, in
+  // entry order), the coupling entries strided over the lanes, the rest by
+  // lane 0
+  const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= L.N) return;
   const int owner = g / lv.S, li = g - owner * lv.S;
   char* img = image + owner * ro_bytes;
@@ -80,22 +86,29 @@ __global__ void k_ctail_fill(LevelView<double> L, const double* __restrict__ din
   const int c = g - dp.off;
   int i, j, k;
   cell_coords(dp, c, i, j, k);
-  int q = rowptr[li];
-  for (int e = 0; e < dp.nent; ++e) {
-    if (!inside(dp, i + dp.o[e][0], j + dp.o[e][1], k + dp.o[e][2])) continue;
-    col[q] = ctail_pack(g + dp.disp[e], lv.S);
-    val[q] = (T)coef_at(dp, L.coef, e, c);
-    ++q;
+  const int q0 = rowptr[li];
+  const bool ok = lane < dp.nent && inside(dp, i + dp.o[lane][0], j + dp.o[lane][1], k + dp.o[lane][2]);
+  const unsigned m = __ballot_sync(0xffffffffu, ok);
+  if (ok) {
+    const int q = q0 + __popc(m & ((1u << lane) - 1u));
+    col[q] = ctail_pack(g + dp.disp[lane], lv.S);
+    val[q] = (T)coef_at(dp, L.coef, lane, c);
   }
   if (dp.has_u && L.u_map) {
     const int r = L.u_map[g];
-    if (r >= 0)
-      for (int t = L.u_ptr[r]; t < L.u_ptr[r + 1]; ++t) {
-        col[q] = ctail_pack(L.u_col[t], lv.S);
-        val[q] = (T)L.u_val[t];
-        ++q;
+    if (r >= 0) {
+      const int t0 = L.u_ptr[r], t1 = L.u_ptr[r + 1], q1 = q0 + __popc(m) - t0;
+      for (int t = t0 + lane; t < t1; t += 32) {
+        col[q1 + t] = ctail_pack(L.u_col[t], lv.S);
+        val[q1 + t] = (T)L.u_val[t];
       }
+    }
   }
+  if (inv) {
+    double* iv = reinterpret_cast<double*>(img + lv.o_inv);
+    for (int t = lane; t < nL; t += 32) iv[(long long)li * nL + t] = inv[(long long)g * nL + t];
+  }
+  if (lane != 0) return;
   dv[li] = (T)dinv64[g];
   if (has_p) {
     // P's row of fine cell g (Section 3.2), coarse columns on level l+1
@@ -142,10 +155,6 @@ __global__ void k_ctail_fill(LevelView<double> L, const double* __restrict__ din
     rv[lv.S + li] = f1 >= 0 ? (T)w1 : (T)0;
     rc[2 * lv.S + li] = f2 >= 0 ? ctail_pack(f2, Sm) : 0;
     rv[2 * lv.S + li] = f2 >= 0 ? (T)w2 : (T)0;
-  }
-  if (inv) {
-    double* iv = reinterpret_cast<double*>(img + lv.o_inv);
-    for (int t = 0; t < nL; ++t) iv[(long long)li * nL + t] = inv[(long long)g * nL + t];
   }
 }
 
@@ -347,7 +356,7 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 template <class T>
 bool ctail_query(int nc, long long smem);
 void launch_ctail_rowlen(const Level& L, int* len, cudaStream_t st) {
-  k_ctail_rowlen<<<cdiv(L.N, 256), 256, 0, st>>>(L.view<double>(), len);
+  k_ctail_rowlen<<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), len);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -357,11 +366,11 @@ void launch_ctail_fill(bool fp32, const Level& L, const Level* Fm, const Level* 
   const LevelView<double> fm = Fm ? Fm->view<double>() : L.view<double>();
   const LevelView<double> ln = Ln ? Ln->view<double>() : L.view<double>();
   if (fp32)
-    k_ctail_fill<float><<<cdiv(L.N, 256), 256, 0, st>>>(L.view<double>(), L.dinv, fm, Fm != nullptr,
+    k_ctail_fill<float><<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), L.dinv, fm, Fm != nullptr,
                                                         ln, Ln != nullptr, inv, nL, lv, Sm, Sn,
                                                         image, ro_bytes);
   else
-    k_ctail_fill<double><<<cdiv(L.N, 256), 256, 0, st>>>(L.view<double>(), L.dinv, fm,
+    k_ctail_fill<double><<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), L.dinv, fm,
                                                          Fm != nullptr, ln, Ln != nullptr, inv, nL,
                                                          lv, Sm, Sn, image, ro_bytes);
   SSAMG_LAUNCH_CHECK();

@@ -24,6 +24,7 @@
 
 #define SSAMG_MAXE 27
 #define SSAMG_BLOCK 256
+#define SSAMG_DINV_LEVELS 32  // levels per launch of the smoother-diagonal kernel
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
 #define SSAMG_TUNE_MARGIN 0.97    // a tuned tile form must save 3% of a level's time
@@ -393,9 +394,10 @@ struct UStage {
 };
 void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
                   const double* frw, int* counts, const UStage& t, int* err, cudaStream_t st);
-void launch_ucopy(const Level& Cl, const UStage& t, bool fp32, cudaStream_t st);
+void launch_ucopy(const Level& F, const Level& Cl, const UStage& t, bool fp32, cudaStream_t st);
 void launch_umap_level0(const Level& L, cudaStream_t st);
-void launch_dinv(const Level& L, int relax, double factor, bool fp32, cudaStream_t st);
+void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
+                 cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 // zero the values of a per-cell entry with offset o where c + o leaves the box
 void launch_mask_outside(double* vals, const int n[3], const int o[3], cudaStream_t st);
