@@ -143,7 +143,8 @@ def run_ours(args):
     beside = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         jobs = ["bench"] + ([] if args.no_extra_workloads else
-                            ["laplace32", "diffusion128", "batched_subset"])
+                            ["laplace32", "diffusion128", "batched_subset", "samr128",
+                             "three_point160"])
         beside = OracleBeside(jobs)
 
     import torch
@@ -526,8 +527,10 @@ def golden_var27():
 
 def extra_workloads(S, stream, peak, args):
     """The other full-size workloads: 32^3 Laplacian (FP64; latency),
-    256^3 27-point, the 64-problem batch and the 128^3 differentiation
-    workload: setup and solve times (median of 5 steps after a warm-up,
+    256^3 27-point, the 64-problem batch, the 128^3 differentiation
+    workload and the paper's test cases 3 (three-point intersection,
+    3 x 160^3) and 4 (SAMR, 2 x 128^3): setup and solve times (median of 5
+    steps after a warm-up,
     clocks sampled), per-kernel HBM fractions of the large levels, and each
     solution's error against the FP64 oracle (256^3: on the oracle's stored
     samples; batch: on its eight smallest problems; the rest in full)."""
@@ -618,6 +621,29 @@ def extra_workloads(S, stream, peak, args):
         del B
     out["batched_64"] = res
     out["diffusion_128"] = differentiation_workload(S, stream, peak)
+    # ---- Section 4 test cases 3 (non-Cartesian index maps) and 4 (SAMR)
+    for key, k, text in (("three_point_160", 5, "3 parts 160^3 around a common k edge, rotated "
+                                                "index maps (test case 3), seed 5"),
+                         ("samr_128", 6, "2 parts 128^3: coarse grid with ghost unknowns and a "
+                                         "patch refined by 2 (test case 4), seed 6")):
+        prob = P.config(k)
+        grid, A = S.matrix_from_problem(prob)
+        b = torch.as_tensor(prob.b[0], device="cuda")
+        res = {"workload": text, "unknowns": prob.n}
+        for prec, name in ((1, "fp32_cycle"), (0, "fp64")):
+            sv = S.Solver(precision=prec, flexible=prec, tol=1e-8, max_iter=500)
+            sv.setup(A)
+            x = torch.zeros_like(b)
+            st = sv.solve(b, x)
+            su, so, ck, _ = timed_steps(stream, nst, lambda: sv.setup(A), lambda: sv.solve_nostats(b, x))
+            res[name] = {"setup_ms": round(su, 3), "solve_ms": round(so, 3),
+                         "iterations": st.iterations, "true_rel_res": fmt(st.true_rel_res),
+                         "levels": st.num_levels, "steps": nst, "clocks": ck,
+                         "mdof_s": round(prob.n / ((su + so) * 1e-3) / 1e6, 3),
+                         "_x": x.cpu().numpy()}
+            del sv
+        out[key] = res
+        del A, grid
     return out
 
 
@@ -639,6 +665,16 @@ def oracle_errors(extra, meta, arrays):
                 errs = [rel_err(v, arrays[f"batched_subset:x:{k}"]) for k, v in xs.items()]
                 bat[name]["err_vs_oracle"] = {"max_rel_err": fmt(max(errs)), "instances": len(errs),
                                               "problems": jobs["batched_subset"]["problems"]}
+    for key, job in (("three_point_160", "three_point160"), ("samr_128", "samr128")):
+        w = extra.get(key)
+        if w is None:
+            continue
+        for name in ("fp32_cycle", "fp64"):
+            x = w[name].pop("_x", None)
+            if job in jobs and x is not None:
+                w[name]["err_vs_oracle"] = fmt(rel_err(x, arrays[f"{job}:x"]))
+        if job in jobs:
+            w["oracle_iterations"] = jobs[job]["iterations"]
     dif = extra.get("diffusion_128")
     if dif is not None:
         x, dg = dif.pop("_x"), dif.pop("_dg")
@@ -840,6 +876,15 @@ def oracle_run(job):
         out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "adjoint_s": t3 - t2, "gradient_s": t4 - t3,
                "iterations": r.iterations, "adjoint_iterations": ra.iterations,
                "unknowns": prob.n, "x": r.x, "dg": dg}
+    elif job in ("three_point160", "samr128"):
+        prob = P.config(5 if job == "three_point160" else 6)
+        t0 = time.perf_counter()
+        h = O.setup(prob)
+        t1 = time.perf_counter()
+        r = O.pcg(h, prob.b[0], tol=1e-8, max_iter=500)
+        t2 = time.perf_counter()
+        out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "iterations": r.iterations,
+               "true_rel_res": r.true_rel_res, "unknowns": prob.n, "x": r.x}
     elif job == "batched_subset":
         probs = P.config(3)
         sel = batched_subset(probs)

@@ -86,9 +86,10 @@ int ssamg_matrix_set_box_values(ssamg_matrix A, int part, int entry, const doubl
  * nbor_idx[3t..3t+2].  dir[3t..3t+2] is the offset through which the row's
  * cell leaves its part toward the column (one component +-1 for a face
  * coupling; 0,0,0 for a non-geometric one); it marks the part boundaries that
- * interpolation must not cross (Section 3.2).  Rows must lie on a face of
- * their part's box and columns in a different part (the Theorem of Section
- * 3.3 keeps coarse couplings on part boundaries).  Duplicates are summed. */
+ * interpolation must not cross (Section 3.2).  A row with a nonzero dir
+ * lies on the faces it names; a row with dir 0,0,0 may lie anywhere in its
+ * box (e.g. beside ghost unknowns under a refined patch, Section 4 test case
+ * 4).  Columns lie in a different part.  Duplicates are summed. */
 int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int* part, const int* idx,
                                const int* dir, const int* nbor_part, const int* nbor_idx,
                                const double* vals);

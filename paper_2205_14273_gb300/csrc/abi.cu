@@ -408,17 +408,14 @@ extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int
   for (long long t = 0; t < n; ++t) {
     int p = part[t], q = nbor_part[t];
     if (p < 0 || p >= g->nparts || q < 0 || q >= g->nparts || p == q) return SSAMG_ERR_ARG;
-    bool face = false;
     for (int d = 0; d < 3; ++d) {
       int a = idx[3 * t + d], b = nbor_idx[3 * t + d];
       if (a < g->lo[p][d] || a > g->hi[p][d] || b < g->lo[q][d] || b > g->hi[q][d]) return SSAMG_ERR_ARG;
-      if (d < g->ndim && (a == g->lo[p][d] || a == g->hi[p][d])) face = true;
       int dv = dir[3 * t + d];
       if (dv < -1 || dv > 1) return SSAMG_ERR_ARG;
       if (dv > 0 && a != g->hi[p][d]) return SSAMG_ERR_ARG;
       if (dv < 0 && a != g->lo[p][d]) return SSAMG_ERR_ARG;
     }
-    if (!face) return SSAMG_ERR_ARG;
   }
   A->c_part.insert(A->c_part.end(), part, part + n);
   A->c_npart.insert(A->c_npart.end(), nbor_part, nbor_part + n);
@@ -531,7 +528,16 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
   ptr.push_back((int)col.size());
   for (int r : rows) {
     int p = (int)(std::upper_bound(g->off.begin(), g->off.end(), (long long)r) - g->off.begin()) - 1;
-    A->has_u[p] = 1;
+    // 2 when a row lies inside the box (no face of an active dimension)
+    long long c = r - g->off[p];
+    bool face = false;
+    for (int d = 0; d < 3; ++d) {
+      const long long n = g->hi[p][d] - g->lo[p][d] + 1;
+      const long long a = c % n;
+      c /= n;
+      if (d < g->ndim && (a == 0 || a == n - 1)) face = true;
+    }
+    A->has_u[p] = std::max<char>(A->has_u[p], face ? 1 : 2);
   }
   A->nr = (int)rows.size();
   A->nnz = (long long)col.size();

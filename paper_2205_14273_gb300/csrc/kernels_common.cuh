@@ -318,13 +318,15 @@ __device__ __forceinline__ T stencil_sh(const DPart& p, const T* __restrict__ co
 
 // (A x)(g) for local cell c of part p with shape SH; coordinates are only
 // computed where needed (checked shape, or face cells of coupled parts).
+// has_u: 1 = the part's coupling rows lie on its box faces, 2 = anywhere
+// (rows inside the box, e.g. beside ghost unknowns), so every cell adds U x.
 template <int SH, class T>
 __device__ __forceinline__ T apply_A_sh(const LevelView<T>& L, const DPart& p,
                                         const T* __restrict__ x, int c) {
   int i = 0, j = 0, k = 0;
   if (SH == SH_CHECKED || SH == SH_K7 || p.has_u) cell_coords(p, c, i, j, k);
   T acc = stencil_sh<SH>(p, L.coef, x, c, i, j, k);
-  if (p.has_u && !is_interior(p, i, j, k)) acc += L.uy[p.off + c];
+  if (p.has_u > 1 || (p.has_u && !is_interior(p, i, j, k))) acc += L.uy[p.off + c];
   return acc;
 }
 
@@ -342,13 +344,14 @@ __device__ __forceinline__ T u_apply(const LevelView<T>& L, const T* __restrict_
 
 
 // (A x)(c) = (S x)(c) + (U x)(c); the U part comes from L.uy, which a row
-// job filled for this same x (only face cells can have couplings).
+// job filled for this same x (only face cells can have couplings unless
+// has_u is 2).
 template <class T>
 __device__ __forceinline__ T apply_A(const LevelView<T>& L, const DPart& p, const T* __restrict__ x,
                                      int c, int i, int j, int k, bool padded = true) {
   bool interior = is_interior(p, i, j, k);
   T acc = stencil_apply(p, L.coef, x, c, i, j, k, interior, padded);
-  if (p.has_u && !interior) acc += L.uy[p.off + c];
+  if (p.has_u > 1 || (p.has_u && !interior)) acc += L.uy[p.off + c];
   return acc;
 }
 

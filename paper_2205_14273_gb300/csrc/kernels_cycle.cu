@@ -223,7 +223,7 @@ __device__ __forceinline__ void brick7(const LevelView<T>& L, const DPart& sp, c
     acc = fma(a4, xn, acc);
     acc = fma(a5, k > 0 ? xm : (T)0, acc);
     acc = fma(a6, xz, acc);
-    if (sp.has_u && (face_ij || k == 0 || k == nz - 1)) acc += L.uy[sp.off + c];
+    if (sp.has_u && (sp.has_u > 1 || face_ij || k == 0 || k == nz - 1)) acc += L.uy[sp.off + c];
     op.apply(sp.off + c, acc, xcur, in);
     xm = xcur;
     xcur = xz;

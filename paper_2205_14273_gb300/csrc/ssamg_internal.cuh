@@ -84,7 +84,7 @@ struct DPart {
   int nent;
   int dstar;                   // coarsening direction at this level, -1: none
   int par;                     // lo[dstar] & 1 (parity of local cell 0)
-  int has_u;                   // some cell of the part has U couplings
+  int has_u;                   // 0: no U couplings; 1: rows on the box faces only; 2: rows inside too
   int coff;                    // first cell of the part in the next level vector
   int cn[3];                   // extents on the next level
   int cncell;

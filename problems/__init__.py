@@ -24,6 +24,10 @@ targets:
   batched         many independent multi-part problems chained along x
   diffusion_exp   one part, 7-point diffusion with kappa = exp(g), g smoothed
                   Gaussian noise (differentiable workload)
+  three_point     three cubes around a common k edge, couplings across
+                  rotated index maps (test case 3, non-Cartesian)
+  samr            a coarse part with ghost unknowns under a refined patch of
+                  twice the resolution (test case 4, SAMR)
 """
 from __future__ import annotations
 
@@ -386,9 +390,131 @@ def diffusion_from_g(g: np.ndarray, b: np.ndarray) -> Problem:
                    extra={"g": g})
 
 
+def three_point(m: int = 160, seed: int = 5, nrhs: int = 1) -> Problem:
+    """Three parts of m^3 cells around a common edge along k (test case 3).
+
+    Each part is [0,m-1]^3 in its own index space with the isotropic 7-point
+    Laplacian (6, -1 x 6).  The east face of part p (i = m-1) touches the
+    north face of part q = p+1 mod 3 (j = m-1), the shared edge being each
+    part's (i, j) = (m-1, m-1) corner: cell (m-1, t, k) of p and cell
+    (t, m-1, k) of q are coupled by -1 both ways, so an east connection of p
+    is a north connection of q (the index maps are not Cartesian).  West,
+    south, bottom and top faces are Dirichlet (eliminated), so the diagonal
+    is 6 everywhere.
+    """
+    rng = SplitMix64(seed)
+    boxes = [((0, 0, 0), (m - 1, m - 1, m - 1)) for _ in range(3)]
+    coef = [[6.0] + [-1.0] * 6 for _ in range(3)]
+    kk, tt = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    kk, tt = kk.ravel(), tt.ravel()
+    cnt = m * m
+    east = np.stack([np.full(cnt, m - 1), tt, kk], axis=1)   # (m-1, t, k) of p
+    north = np.stack([tt, np.full(cnt, m - 1), kk], axis=1)  # (t, m-1, k) of q
+    up, ui, ud, uq, uj = [], [], [], [], []
+    for p in range(3):
+        q = (p + 1) % 3
+        up += [np.full(cnt, p), np.full(cnt, q)]
+        ui += [east, north]
+        ud += [np.tile(np.array([1, 0, 0]), (cnt, 1)), np.tile(np.array([0, 1, 0]), (cnt, 1))]
+        uq += [np.full(cnt, q), np.full(cnt, p)]
+        uj += [north, east]
+    uv = np.full(6 * cnt, -1.0)
+    N = 3 * m ** 3
+    b = rng.uniform_pm1(nrhs * N).reshape(nrhs, N)
+    return Problem(3, boxes, STENCIL7.copy(), coef,
+                   np.concatenate(up).astype(np.int32), np.concatenate(ui).astype(np.int32),
+                   np.concatenate(ud).astype(np.int32), np.concatenate(uq).astype(np.int32),
+                   np.concatenate(uj).astype(np.int32), uv, b, name=f"three_point 3x{m}^3")
+
+
+def samr(m: int = 128, seed: int = 6, nrhs: int = 1, cf: float = 2.0 / 3.0) -> Problem:
+    """A structured AMR grid of two parts with m^3 cells each (test case 4).
+
+    Part 0, [0,m-1]^3, is the coarse grid; its cells in the central cube
+    G = [m/4, 3m/4-1]^3 are ghost unknowns (diagonal 1, no off-diagonals, zero
+    right-hand side).  Part 1 refines G by two: [m/2, 3m/2-1]^3 in its own
+    index space, fine cell f under coarse cell f // 2.  Both parts carry the
+    7-point Laplacian (-1 between neighbouring cells of the same part, none
+    into or out of G).  Across the patch boundary each fine face cell is
+    coupled to the coarse cell beside its parent, and each such coarse cell
+    to the four fine cells facing it, by -cf (cf = 2/3) both ways.  Rows of
+    the fine part leave its box through a face; rows of the coarse part lie
+    inside its box beside G (direction 0, 0, 0).  Diagonals: the sum of the
+    row's |off-diagonals| plus 1 per Dirichlet face of the outer box.
+    """
+    assert m % 4 == 0
+    rng = SplitMix64(seed)
+    g0, g1 = m // 4, 3 * m // 4 - 1
+    f0, f1 = 2 * g0, 2 * g1 + 1
+    boxes = [((0, 0, 0), (m - 1, m - 1, m - 1)), ((f0, f0, f0), (f1, f1, f1))]
+    ax = np.arange(m)
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    ghost = ((xx >= g0) & (xx <= g1) & (yy >= g0) & (yy <= g1) & (zz >= g0) & (zz <= g1))
+    # coarse part: -1 between non-ghost neighbours inside the box
+    cdiag = np.zeros((m, m, m))
+    ccoef = []
+    for o in STENCIL7[1:]:
+        ox, oy, oz = (int(v) for v in o)
+        nx, ny, nz = xx + ox, yy + oy, zz + oz
+        inb = (nx >= 0) & (nx < m) & (ny >= 0) & (ny < m) & (nz >= 0) & (nz < m)
+        ng = np.zeros_like(ghost)
+        ng[inb] = ghost[nz[inb], ny[inb], nx[inb]]
+        off = np.where(inb & ~ghost & ~ng, -1.0, 0.0)
+        cdiag += np.where(inb, -off, 1.0)  # a Dirichlet face adds 1
+        cdiag += np.where(inb & ~ghost & ng, 4 * cf, 0.0)  # four fine cells across
+        ccoef.append(off)
+    cdiag = np.where(ghost, 1.0, cdiag)
+    # fine part: -1 inside its box; every face is coupled to the coarse part
+    fdiag = np.full((m, m, m), 6.0)
+    for d in range(3):
+        for side in (0, m - 1):
+            sl = [slice(None)] * 3
+            sl[2 - d] = side
+            fdiag[tuple(sl)] += cf - 1.0
+    up, ui, ud, uq, uj = [], [], [], [], []
+    fa = np.arange(f0, f1 + 1)
+    ca = np.arange(g0, g1 + 1)
+    for d in range(3):
+        for s, fface, cnb in ((-1, f0, g0 - 1), (1, f1, g1 + 1)):
+            # fine rows: face cells, column = the coarse cell beside the parent
+            u1, u2 = np.meshgrid(fa, fa, indexing="ij")
+            u1, u2 = u1.ravel(), u2.ravel()
+            fc = np.zeros((len(u1), 3), np.int64)
+            fc[:, d] = fface
+            fc[:, (d + 1) % 3] = u1
+            fc[:, (d + 2) % 3] = u2
+            cc = fc // 2
+            cc[:, d] = cnb
+            dv = np.zeros((len(u1), 3), np.int64)
+            dv[:, d] = s
+            up.append(np.full(len(u1), 1))
+            ui.append(fc)
+            ud.append(dv)
+            uq.append(np.full(len(u1), 0))
+            uj.append(cc)
+            # coarse rows: the cells beside G, each to its four fine cells
+            up.append(np.full(len(u1), 0))
+            ui.append(cc)
+            ud.append(np.zeros((len(u1), 3), np.int64))
+            uq.append(np.full(len(u1), 1))
+            uj.append(fc)
+    nu = sum(len(x) for x in up)
+    N = 2 * m ** 3
+    b = rng.uniform_pm1(nrhs * N).reshape(nrhs, N)
+    b[:, :m ** 3] *= ~ghost.ravel()
+    coef = [[cdiag] + ccoef, [fdiag] + [-1.0] * 6]
+    return Problem(3, boxes, STENCIL7.copy(), coef,
+                   np.concatenate(up).astype(np.int32), np.concatenate(ui).astype(np.int32),
+                   np.concatenate(ud).astype(np.int32), np.concatenate(uq).astype(np.int32),
+                   np.concatenate(uj).astype(np.int32), np.full(nu, -cf), b,
+                   name=f"samr 2x{m}^3", extra={"ghost": ghost})
+
+
 def config(k: int, small: bool = False) -> Union[Problem, List[Problem]]:
-    """The five workloads at full size (small=False) or at a size the oracle
-    finishes in seconds (small=True) with the same structure and seeds."""
+    """The workloads at full size (small=False) or at a size the oracle
+    finishes in seconds (small=True) with the same structure and seeds:
+    0-4 as listed above, 5 the three-point intersection (3 x 160^3) and 6 the
+    SAMR grid (2 x 128^3) of the paper's test cases 3 and 4."""
     if k == 0:
         return laplace7(16 if small else 32, seed=0)
     if k == 1:
@@ -401,4 +527,8 @@ def config(k: int, small: bool = False) -> Union[Problem, List[Problem]]:
         return batched(nprob=64, nrhs=4, seed=3)
     if k == 4:
         return diffusion_exp(16 if small else 128, seed=4, nfd=8 if small else 32)
+    if k == 5:
+        return three_point(8 if small else 160, seed=5)
+    if k == 6:
+        return samr(8 if small else 128, seed=6)
     raise ValueError(k)

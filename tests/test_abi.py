@@ -72,7 +72,8 @@ def test_matrix_and_coupling_validation(ssamg_lib):
                                             S._ints([q]), S._ints(nidx),
                                             v.ctypes.data_as(S._dp))
     assert add(0, (3, 1, 1), (1, 0, 0), 1, (0, 1, 1)) == 0
-    assert add(0, (2, 1, 1), (0, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG   # row not on a face
+    assert add(0, (2, 1, 1), (1, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG   # leaves through +x, not on that face
+    assert add(0, (2, 1, 1), (0, 0, 0), 1, (0, 1, 1)) == 0            # a non-geometric row may lie inside
     assert add(0, (3, 1, 1), (1, 0, 0), 0, (0, 1, 1)) == S.ERR_ARG   # same part
     assert add(0, (0, 1, 1), (1, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG   # dir leaves through +x but cell is at lo
     assert add(0, (3, 1, 1), (1, 0, 0), 1, (4, 1, 1)) == S.ERR_ARG   # column outside its box

@@ -42,6 +42,8 @@ def cases():
         T.shifted(P.multipart_aniso(m=6, layout=(1, 2, 2), seed=5), [(-5, 3, 1), (2, 2, -3), (0, 0, 0), (7, -1, 2)]),
         T.chain([1, 4], [[1, 1, 1], [1, .5, .2]]),         # a one-cell part
         T.poisson2d(9, 4),
+        P.three_point(9),                                  # rotated index maps (test case 3)
+        P.samr(12),                                        # ghost unknowns, inner rows (test case 4)
     ]
     for k in range(5):
         c = P.config(k, small=True)

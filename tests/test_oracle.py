@@ -76,6 +76,8 @@ def small_problems():
     ]
     out.append(shifted(P.multipart_aniso(m=4, layout=(2, 1, 1), seed=9), [(-3, 1, 2), (5, -2, 0)]))
     out.append(shifted(chain([4, 6], [[1, .01, .01], [1, .02, .03]]), [(1, 0, 0), (-1, 3, 1)]))
+    out.append(P.three_point(4))   # test case 3: rotated index maps between parts
+    out.append(P.samr(4))          # test case 4: ghost unknowns, couplings inside a box
     return out
 
 
@@ -283,7 +285,8 @@ def test_stencil_growth_bounds():
 def test_theorem_unstructured_part_stays_on_part_boundaries():
     """U_c connects only boundary cells of different parts (Section 3.3 Theorem)."""
     for prob in (P.multipart_aniso(m=6, layout=(2, 2, 2), seed=1),
-                 chain([5, 8, 6], [[.3, 1, .2], [1, .1, .1], [.05, .5, 1]])):
+                 chain([5, 8, 6], [[.3, 1, .2], [1, .1, .1], [.05, .5, 1]]),
+                 P.three_point(6)):
         h = O.setup(prob)
         for lev in h.levels:
             if len(lev.u_row) == 0:
@@ -592,3 +595,92 @@ def test_skip_preconditioner_is_symmetric_and_converges():
     assert res.converged
     x = np.linalg.solve(_dense(prob), prob.b[0])
     assert np.abs(res.x - x).max() <= 1e-7 * np.abs(x).max()
+
+
+# ---------------------------------------------------------------------------
+# Section 4 test cases 3 and 4 (non-Cartesian index maps; SAMR ghost unknowns)
+# ---------------------------------------------------------------------------
+
+def _sparse(prob):
+    import scipy.sparse as sp
+    from oracle import assembled as AS
+    A = AS.assemble_problem(prob)
+    return sp.csr_matrix(A[0] if isinstance(A, tuple) else A)
+
+
+@pytest.mark.parametrize("prob", [P.three_point(6), P.samr(8)], ids=["tc3", "tc4"])
+def test_pcg_matches_sparse_direct_solve(prob):
+    """The oracle's SSAMG-PCG reaches the solution of a sparse LU solve."""
+    import scipy.sparse.linalg as sla
+    A = _sparse(prob)
+    assert abs(A - A.T).max() == 0.0
+    h = O.setup(prob)
+    res = O.pcg(h, prob.b[0], tol=1e-13, max_iter=300)
+    assert res.converged
+    xs = sla.spsolve(A.tocsc(), prob.b[0])
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) <= 1e-11
+
+
+def test_three_point_couplings_follow_rotated_maps():
+    """An east connection of part p is a north connection of part p+1: the
+    assembled row of a cell on p's east face reaches the neighbour part's
+    north face cell with the same position t along the shared face."""
+    m = 5
+    prob = P.three_point(m)
+    A = _sparse(prob)
+    n3 = m ** 3
+    for p in range(3):
+        q = (p + 1) % 3
+        for t in range(m):
+            for k in (0, m - 1):
+                row = p * n3 + (k * m + t) * m + (m - 1)        # (m-1, t, k) of p
+                col = q * n3 + (k * m + (m - 1)) * m + t        # (t, m-1, k) of q
+                assert A[row, col] == -1.0 and A[col, row] == -1.0
+    assert np.allclose(A.diagonal(), 6.0)
+
+
+def test_samr_ghost_unknowns_decoupled_on_level_one():
+    """Ghost unknowns are identity rows with zero right-hand side.  On the
+    7-point level 0 the weights toward a ghost coarse point collapse only the
+    (zero) connection into it, so level 1 keeps every ghost coarse point an
+    identity row with no couplings; the solution is 0 there up to the stop
+    tolerance (deeper levels' collapsed corner entries do weight them)."""
+    m = 8
+    prob = P.samr(m)
+    ghost = prob.extra["ghost"]
+    g0, g1 = m // 4, 3 * m // 4 - 1
+    h = O.setup(prob)
+    f, c = h.levels[0], h.levels[1]
+    d = f.dstar[0]
+    assert d >= 0
+    S = c.S[0]
+    nz, ny, nx = c.shape(0)
+    kk, jj, ii = np.meshgrid(*(np.arange(e) for e in (nz, ny, nx)), indexing="ij")
+    I = [ii + c.lo[0][0], jj + c.lo[0][1], kk + c.lo[0][2]]
+    fine = [v.copy() for v in I]
+    fine[d] = 2 * I[d]                                   # the C point of each coarse cell
+    gl = np.ones(I[0].shape, bool)
+    for v in fine:
+        gl &= (v >= g0) & (v <= g1)
+    assert gl.sum() == (m // 2) ** 3 // 2
+    for o, a in S.items():
+        want = 1.0 if o == (0, 0, 0) else 0.0
+        assert np.all(a[gl] == want), o
+    if len(c.u_row):
+        # couplings of ghost coarse points (kept in the pattern through a zero
+        # weight) have zero values
+        pr, ijr = c.locate(c.u_row)
+        for (pp, ij, v) in zip(pr, ijr, c.u_val):
+            if pp == 0:
+                q = list(ij)
+                q[d] = 2 * q[d]
+                if all(g0 <= w <= g1 for w in q):
+                    assert v == 0.0
+    res = O.pcg(h, prob.b[0], tol=1e-10, max_iter=200)
+    assert res.converged
+    xg = res.x[:ghost.size][ghost.ravel()]
+    assert np.abs(xg).max() <= 1e-9 * np.abs(res.x).max()
+    # coarse-part rows of U lie inside the box, beside the ghost cube
+    pr, ijr = f.locate(f.u_row)
+    inside = np.all((ijr > 0) & (ijr < m - 1), axis=1)
+    assert np.all(inside[pr == 0])
