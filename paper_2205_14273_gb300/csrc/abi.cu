@@ -5,11 +5,105 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <unordered_map>
 
 #include "ssamg_internal.cuh"
+
+// ---------------------------------------------------------------------------
+// Device memory pool: blocks freed by matrices and solvers are kept per
+// rounded size and handed to the next allocation of that size, so objects
+// created and destroyed per step (a new matrix and solver every time) do not
+// pay cudaMalloc / cudaFree each time.  Sizes round up to a power of two
+// below 1 MiB and to 2 MiB multiples above.  Callers free only after
+// pool_fence() (a device synchronisation, which cudaFree would have done),
+// so a block is never handed out while a kernel may still use it.  On an
+// allocation failure the cache is released and the allocation retried;
+// ssamg_release_device_cache() returns the cache to the driver.
+// ---------------------------------------------------------------------------
+namespace {
+struct DevPool {
+  std::mutex m;
+  std::multimap<size_t, void*> cache;   // rounded size -> free block
+  std::unordered_map<void*, size_t> live;
+  size_t cached = 0;
+};
+DevPool& dev_pool() {
+  static DevPool* p = new DevPool;  // outlives every object (no order-of-destruction issue)
+  return *p;
+}
+size_t pool_round(size_t b) {
+  if (b <= (size_t(1) << 20)) {
+    size_t r = 512;
+    while (r < b) r <<= 1;
+    return r;
+  }
+  const size_t g = size_t(2) << 20;
+  return (b + g - 1) / g * g;
+}
+void pool_trim(DevPool& P) {
+  for (auto& kv : P.cache) cudaFree(kv.second);
+  P.cache.clear();
+  P.cached = 0;
+}
+}  // namespace
+
+void* pool_alloc(size_t bytes) {
+  DevPool& P = dev_pool();
+  const size_t r = pool_round(std::max<size_t>(bytes, 1));
+  std::lock_guard<std::mutex> lk(P.m);
+  auto it = P.cache.find(r);
+  if (it != P.cache.end()) {
+    void* q = it->second;
+    P.cache.erase(it);
+    P.cached -= r;
+    P.live[q] = r;
+    return q;
+  }
+  void* q = nullptr;
+  if (cudaMalloc(&q, r) != cudaSuccess) {
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    pool_trim(P);
+    if (cudaMalloc(&q, r) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  P.live[q] = r;
+  return q;
+}
+
+void pool_fence() { cudaDeviceSynchronize(); }
+
+void pool_free(void* q) {
+  if (!q) return;
+  DevPool& P = dev_pool();
+  std::lock_guard<std::mutex> lk(P.m);
+  auto it = P.live.find(q);
+  if (it == P.live.end()) return;
+  P.cache.emplace(it->second, q);
+  P.cached += it->second;
+  P.live.erase(it);
+}
+
+extern "C" long long ssamg_release_device_cache(void) {
+  DevPool& P = dev_pool();
+  std::lock_guard<std::mutex> lk(P.m);
+  const long long n = (long long)P.cached;
+  pool_trim(P);
+  return n;
+}
+
+template <class T>
+T* pool_new(long long n) {
+  T* q = (T*)pool_alloc(sizeof(T) * (size_t)std::max<long long>(n, 1));
+  if (!q) throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
+  return q;
+}
 
 // ---------------------------------------------------------------------------
 // Arena: chunked bump allocator.  A setup with the same sizes as the previous
@@ -28,11 +122,8 @@ void* Arena::alloc(size_t bytes) {
     used = 0;
   }
   size_t sz = std::max(bytes, size_t(64) << 20);
-  char* p = nullptr;
-  if (cudaMalloc(&p, sz) != cudaSuccess) {
-    cudaGetLastError();
-    throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
-  }
+  char* p = (char*)pool_alloc(sz);
+  if (!p) throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
   chunks.push_back({p, sz});
   cur = chunks.size() - 1;
   used = bytes;
@@ -40,7 +131,8 @@ void* Arena::alloc(size_t bytes) {
 }
 
 void Arena::release() {
-  for (auto& c : chunks) cudaFree(c.first);
+  if (!chunks.empty()) pool_fence();
+  for (auto& c : chunks) pool_free(c.first);
   chunks.clear();
   cur = used = 0;
 }
@@ -85,22 +177,24 @@ struct ssamg_matrix_s {
   std::vector<char> has_u;
   int version = 0;
   void free_device() {
-    cudaFree(coef);
-    cudaFree(u_rows);
-    cudaFree(u_ptr);
-    cudaFree(u_col);
-    cudaFree(u_map);
-    cudaFree(u_val);
-    cudaFree(u_bits);
+    if (coef || u_rows) pool_fence();
+    pool_free(coef);
+    pool_free(u_rows);
+    pool_free(u_ptr);
+    pool_free(u_col);
+    pool_free(u_map);
+    pool_free(u_val);
+    pool_free(u_bits);
     coef = nullptr;
     u_rows = u_ptr = u_col = u_map = nullptr;
     u_val = nullptr;
     u_bits = nullptr;
   }
   ~ssamg_matrix_s() {
+    pool_fence();
     free_device();
     for (auto& v : tmpvar)
-      for (auto* p : v) cudaFree(p);
+      for (auto* p : v) pool_free(p);
   }
 };
 
@@ -365,7 +459,8 @@ extern "C" int ssamg_matrix_create(ssamg_grid g, int nentries, const int* offset
 extern "C" int ssamg_matrix_set_constant(ssamg_matrix A, int part, int entry, double value) {
   if (!A || part < 0 || part >= A->g->nparts || entry < 0 || entry >= A->nent) return SSAMG_ERR_ARG;
   if (A->tmpvar[part][entry]) {
-    cudaFree(A->tmpvar[part][entry]);
+    pool_fence();
+    pool_free(A->tmpvar[part][entry]);
     A->tmpvar[part][entry] = nullptr;
   }
   A->cval[part][entry] = value;
@@ -381,11 +476,7 @@ extern "C" int ssamg_matrix_set_box_values(ssamg_matrix A, int part, int entry, 
     return SSAMG_ERR_ARG;
   long long n = A->g->ncell(part);
   double*& dst = A->tmpvar[part][entry];
-  if (!dst && cudaMalloc(&dst, sizeof(double) * n) != cudaSuccess) {
-    cudaGetLastError();
-    dst = nullptr;
-    return SSAMG_ERR_OOM;
-  }
+  if (!dst && !(dst = (double*)pool_alloc(sizeof(double) * n))) return SSAMG_ERR_OOM;
   cudaError_t e = cudaMemcpy(dst, vals, sizeof(double) * n,
                              vals_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -464,7 +555,7 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
         n += g->ncell(p);
       }
   A->ncoef = n;
-  SSAMG_CUDA(cudaMalloc(&A->coef, sizeof(double) * std::max<long long>(n, 1)));
+  A->coef = pool_new<double>(n);
   for (int p = 0; p < np; ++p)
     for (int e = 0; e < A->nent; ++e)
       if (A->isvar[p][e]) {
@@ -476,89 +567,57 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
         if (A->o[e][0] || A->o[e][1] || A->o[e][2])
           launch_mask_outside(A->coef + A->coef_off[p][e], ext, A->o[e], st);
       }
-  // couplings: global (row, col), sorted, duplicates merged
-  long long m = (long long)A->c_val.size();
-  struct E {
-    long long row, col;
-    double v;
-    unsigned char bits;
-  };
-  std::vector<E> es((size_t)m);
-  auto gidx = [&](int p, const int* c) {
-    long long nx = g->hi[p][0] - g->lo[p][0] + 1, ny = g->hi[p][1] - g->lo[p][1] + 1;
-    return g->off[p] + ((long long)(c[2] - g->lo[p][2]) * ny + (c[1] - g->lo[p][1])) * nx +
-           (c[0] - g->lo[p][0]);
-  };
-  for (long long t = 0; t < m; ++t) {
-    E& e = es[(size_t)t];
-    e.row = gidx(A->c_part[t], &A->c_idx[3 * t]);
-    e.col = gidx(A->c_npart[t], &A->c_nidx[3 * t]);
-    e.v = A->c_val[t];
-    e.bits = 0;
-    for (int d = 0; d < 3; ++d) {
-      int dv = A->c_dir[3 * t + d];
-      if (dv > 0) e.bits |= (unsigned char)(1u << (2 * d));
-      if (dv < 0) e.bits |= (unsigned char)(1u << (2 * d + 1));
-    }
-  }
-  std::stable_sort(es.begin(), es.end(), [](const E& a, const E& b) {
-    return a.row != b.row ? a.row < b.row : a.col < b.col;
-  });
-  std::vector<int> rows, ptr, col;
-  std::vector<double> val;
-  std::vector<unsigned char> bits;
+  // couplings: global (row, col) and direction bits per coupling here,
+  // O(m); the CSR (rows ascending, columns ascending, duplicates summed in
+  // input order) on the device
+  const long long m = (long long)A->c_val.size();
   A->has_u.assign(np, 0);
-  for (size_t t = 0; t < es.size();) {
-    size_t s = t;
-    if (rows.empty() || rows.back() != es[s].row) {
-      rows.push_back((int)es[s].row);
-      ptr.push_back((int)col.size());
+  A->nr = 0;
+  A->nnz = 0;
+  if (m > 0) {
+    std::vector<int> crow((size_t)m), ccol((size_t)m);
+    std::vector<unsigned char> cbits((size_t)m);
+    auto gidx = [&](int p, const int* c) {
+      long long nx = g->hi[p][0] - g->lo[p][0] + 1, ny = g->hi[p][1] - g->lo[p][1] + 1;
+      return g->off[p] + ((long long)(c[2] - g->lo[p][2]) * ny + (c[1] - g->lo[p][1])) * nx +
+             (c[0] - g->lo[p][0]);
+    };
+    for (long long t = 0; t < m; ++t) {
+      const int p = A->c_part[t];
+      const int* c = &A->c_idx[3 * t];
+      crow[t] = (int)gidx(p, c);
+      ccol[t] = (int)gidx(A->c_npart[t], &A->c_nidx[3 * t]);
+      unsigned char bt = 0;
+      bool face = false;
+      for (int d = 0; d < 3; ++d) {
+        const int dv = A->c_dir[3 * t + d];
+        if (dv > 0) bt |= (unsigned char)(1u << (2 * d));
+        if (dv < 0) bt |= (unsigned char)(1u << (2 * d + 1));
+        if (d < g->ndim && (c[d] == g->lo[p][d] || c[d] == g->hi[p][d])) face = true;
+      }
+      cbits[t] = bt;
+      // 2 when a row lies inside the box (no face of an active dimension)
+      A->has_u[p] = std::max<char>(A->has_u[p], face ? 1 : 2);
     }
-    double v = 0;
-    unsigned char b = 0;
-    while (t < es.size() && es[t].row == es[s].row && es[t].col == es[s].col) {
-      v += es[t].v;
-      b |= es[t].bits;
-      ++t;
-    }
-    col.push_back((int)es[s].col);
-    val.push_back(v);
-    bits.push_back(b);
-  }
-  ptr.push_back((int)col.size());
-  for (int r : rows) {
-    int p = (int)(std::upper_bound(g->off.begin(), g->off.end(), (long long)r) - g->off.begin()) - 1;
-    // 2 when a row lies inside the box (no face of an active dimension)
-    long long c = r - g->off[p];
-    bool face = false;
-    for (int d = 0; d < 3; ++d) {
-      const long long n = g->hi[p][d] - g->lo[p][d] + 1;
-      const long long a = c % n;
-      c /= n;
-      if (d < g->ndim && (a == 0 || a == n - 1)) face = true;
-    }
-    A->has_u[p] = std::max<char>(A->has_u[p], face ? 1 : 2);
-  }
-  A->nr = (int)rows.size();
-  A->nnz = (long long)col.size();
-  if (A->nr > 0) {
-    SSAMG_CUDA(cudaMalloc(&A->u_rows, sizeof(int) * A->nr));
-    SSAMG_CUDA(cudaMalloc(&A->u_ptr, sizeof(int) * (A->nr + 1)));
-    SSAMG_CUDA(cudaMalloc(&A->u_col, sizeof(int) * A->nnz));
-    SSAMG_CUDA(cudaMalloc(&A->u_val, sizeof(double) * A->nnz));
-    SSAMG_CUDA(cudaMalloc(&A->u_bits, A->nnz));
-    SSAMG_CUDA(cudaMalloc(&A->u_map, sizeof(int) * g->N));
-    SSAMG_CUDA(cudaMemcpyAsync(A->u_rows, rows.data(), sizeof(int) * A->nr, cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(A->u_ptr, ptr.data(), sizeof(int) * (A->nr + 1), cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(A->u_col, col.data(), sizeof(int) * A->nnz, cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(A->u_val, val.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(A->u_bits, bits.data(), A->nnz, cudaMemcpyHostToDevice, st));
-    Level tmp;
-    tmp.N = g->N;
-    tmp.nr = A->nr;
-    tmp.u_rows = A->u_rows;
-    tmp.u_map = A->u_map;
-    launch_umap_level0(tmp, st);
+    int* drow = pool_new<int>(m);
+    int* dcol = pool_new<int>(m);
+    double* dval = pool_new<double>(m);
+    unsigned char* dbits = pool_new<unsigned char>(m);
+    SSAMG_CUDA(cudaMemcpyAsync(drow, crow.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(dcol, ccol.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(dval, A->c_val.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(dbits, cbits.data(), m, cudaMemcpyHostToDevice, st));
+    // outputs sized by the bound m (the row and entry counts come back below)
+    A->u_rows = pool_new<int>(m);
+    A->u_ptr = pool_new<int>(m + 1);
+    A->u_col = pool_new<int>(m);
+    A->u_val = pool_new<double>(m);
+    A->u_bits = pool_new<unsigned char>(m);
+    A->u_map = pool_new<int>(g->N);
+    UAssemble ua{(int)g->N, m, drow, dcol, dval, dbits, A->u_rows, A->u_ptr,
+                 A->u_col, A->u_val, A->u_bits, A->u_map};
+    launch_uassemble(ua, &A->nr, &A->nnz, st);  // synchronises st
+    for (void* q : {(void*)drow, (void*)dcol, (void*)dval, (void*)dbits}) pool_free(q);
   }
   SSAMG_CUDA(cudaStreamSynchronize(st));
   A->assembled = true;

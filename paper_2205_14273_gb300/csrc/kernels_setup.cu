@@ -763,11 +763,6 @@ __global__ void k_ucols(LevelView<double> Fp, LevelView<double> L, long long nnz
   if (rj) urcol(Fp, L, q, rj, rw, rw32);
 }
 
-__global__ void k_umap0(int nr, const int* __restrict__ rows, int* __restrict__ u_map) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nr) u_map[rows[r]] = r;
-}
-
 // ---------------------------------------------------------------------------
 // K5: diagonal of omega M^-1 (Section 3.4).
 // ---------------------------------------------------------------------------
@@ -1029,6 +1024,89 @@ __global__ void __launch_bounds__(256) k_ucopy(LevelView<double> F, LevelView<do
   }
 }
 
+// ---------------------------------------------------------------------------
+// Level-0 coupling rows from the user's m (row, col, value, bits) tuples: a
+// counting sort by row, then per row the entries ordered by (column, input
+// position), equal columns summed in input order with their direction bits
+// OR'ed; rows ascending, columns ascending within a row.
+// ---------------------------------------------------------------------------
+__global__ void k_ua_count(long long m, const int* __restrict__ row, int* __restrict__ cnt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) atomicAdd(cnt + row[t], 1);
+}
+
+__global__ void k_ua_scatter(long long m, const int* __restrict__ row,
+                             const int* __restrict__ start, int* __restrict__ fill,
+                             int* __restrict__ perm) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const int r = row[t];
+  perm[start[r] + atomicAdd(fill + r, 1)] = (int)t;
+}
+
+__global__ void k_ua_rows(int N, const int* __restrict__ start, int* __restrict__ perm,
+                          const int* __restrict__ col, int* __restrict__ uniq,
+                          int* __restrict__ flag) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= N) return;
+  const int s0 = start[g], n = start[g + 1] - s0;
+  if (n == 0) {
+    uniq[g] = 0;
+    flag[g] = 0;
+    return;
+  }
+  int* pr = perm + s0;
+  // insertion sort by (column, input position): rows hold a few entries
+  for (int i = 1; i < n; ++i) {
+    const int t = pr[i], ct = col[t];
+    int j = i - 1;
+    while (j >= 0 && (col[pr[j]] > ct || (col[pr[j]] == ct && pr[j] > t))) {
+      pr[j + 1] = pr[j];
+      --j;
+    }
+    pr[j + 1] = t;
+  }
+  int u = 1;
+  for (int i = 1; i < n; ++i) u += col[pr[i]] != col[pr[i - 1]];
+  uniq[g] = u;
+  flag[g] = 1;
+}
+
+__global__ void k_ua_fill(int N, const int* __restrict__ start, const int* __restrict__ perm,
+                          const int* __restrict__ col, const double* __restrict__ val,
+                          const unsigned char* __restrict__ bits, const int* __restrict__ uoff,
+                          const int* __restrict__ roff, int* __restrict__ u_rows,
+                          int* __restrict__ u_ptr, int* __restrict__ u_col,
+                          double* __restrict__ u_val, unsigned char* __restrict__ u_bits,
+                          int* __restrict__ u_map) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) u_ptr[roff[N]] = uoff[N];
+  if (g >= N) return;
+  const int r = roff[g];
+  if (roff[g + 1] == r) {
+    u_map[g] = -1;
+    return;
+  }
+  u_map[g] = r;
+  u_rows[r] = g;
+  int q = uoff[g];
+  u_ptr[r] = q;
+  const int s0 = start[g], s1 = start[g + 1];
+  for (int i = s0; i < s1;) {
+    const int c = col[perm[i]];
+    double v = 0.0;
+    unsigned char b = 0;
+    for (; i < s1 && col[perm[i]] == c; ++i) {
+      v += val[perm[i]];
+      b |= bits[perm[i]];
+    }
+    u_col[q] = c;
+    u_val[q] = v;
+    u_bits[q] = b;
+    ++q;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1149,13 +1227,6 @@ void launch_ucols(const Level* Fp, const Level& L, bool fp32, bool pj, bool rj, 
   SSAMG_LAUNCH_CHECK();
 }
 
-void launch_umap_level0(const Level& L, cudaStream_t st) {
-  SSAMG_CUDA(cudaMemsetAsync(L.u_map, 0xff, sizeof(int) * L.N, st));
-  if (L.nr > 0) {
-    k_umap0<<<cdiv(L.nr, NT), NT, 0, st>>>(L.nr, L.u_rows, L.u_map);
-    SSAMG_LAUNCH_CHECK();
-  }
-}
 
 void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
                  cudaStream_t st) {
@@ -1218,4 +1289,45 @@ void launch_scan(int* data, long long n, int* tmp, cudaStream_t st) {
   SSAMG_LAUNCH_CHECK();
   k_scan_apply<<<nb, NT, 0, st>>>(data, n, tmp, nb);
   SSAMG_LAUNCH_CHECK();
+}
+
+void launch_uassemble(const UAssemble& a, int* nr, long long* nnz, cudaStream_t st) {
+  const int N = a.N;
+  int* cnt = (int*)pool_alloc(sizeof(int) * ((size_t)N + 1));
+  int* fill = (int*)pool_alloc(sizeof(int) * (size_t)N);
+  int* perm = (int*)pool_alloc(sizeof(int) * (size_t)a.m);
+  int* uniq = (int*)pool_alloc(sizeof(int) * ((size_t)N + 1));
+  int* flag = (int*)pool_alloc(sizeof(int) * ((size_t)N + 1));
+  int* tmp = (int*)pool_alloc(sizeof(int) * (scan_tmp_ints((long long)N + 1) + 1));
+  int* tot = (int*)pool_alloc(sizeof(int) * 2);
+  if (!cnt || !fill || !perm || !uniq || !flag || !tmp || !tot) {
+    pool_fence();
+    for (void* q : {(void*)cnt, (void*)fill, (void*)perm, (void*)uniq, (void*)flag, (void*)tmp, (void*)tot})
+      pool_free(q);
+    throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
+  }
+  SSAMG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)N + 1), st));
+  SSAMG_CUDA(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)N, st));
+  const int mb = cdiv(a.m, NT);
+  k_ua_count<<<mb, NT, 0, st>>>(a.m, a.row, cnt);
+  SSAMG_LAUNCH_CHECK();
+  launch_scan(cnt, N, tmp, st);
+  k_ua_scatter<<<mb, NT, 0, st>>>(a.m, a.row, cnt, fill, perm);
+  SSAMG_LAUNCH_CHECK();
+  k_ua_rows<<<cdiv(N, NT), NT, 0, st>>>(N, cnt, perm, a.col, uniq, flag);
+  SSAMG_LAUNCH_CHECK();
+  launch_scan(uniq, N, tmp, st);
+  launch_scan(flag, N, tmp, st);
+  k_ua_fill<<<cdiv(N, NT), NT, 0, st>>>(N, cnt, perm, a.col, a.val, a.bits, uniq, flag, a.u_rows,
+                                        a.u_ptr, a.u_col, a.u_val, a.u_bits, a.u_map);
+  SSAMG_LAUNCH_CHECK();
+  SSAMG_CUDA(cudaMemcpyAsync(tot, flag + N, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  SSAMG_CUDA(cudaMemcpyAsync(tot + 1, uniq + N, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  int h[2] = {0, 0};
+  SSAMG_CUDA(cudaMemcpyAsync(h, tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  SSAMG_CUDA(cudaStreamSynchronize(st));
+  *nr = h[0];
+  *nnz = h[1];
+  for (void* q : {(void*)cnt, (void*)fill, (void*)perm, (void*)uniq, (void*)flag, (void*)tmp, (void*)tot})
+    pool_free(q);
 }

@@ -395,7 +395,6 @@ struct UStage {
 void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
                   const double* frw, int* counts, const UStage& t, int* err, cudaStream_t st);
 void launch_ucopy(const Level& F, const Level& Cl, const UStage& t, bool fp32, cudaStream_t st);
-void launch_umap_level0(const Level& L, cudaStream_t st);
 void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
                  cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
@@ -405,6 +404,29 @@ void launch_coarse_assemble(const Level& L, double* A, cudaStream_t st);
 void launch_cholesky(int n, double* A, int* status, cudaStream_t st);
 // exclusive scan of n ints in place; returns nothing (total at out[n])
 void launch_scan(int* data, long long n, int* tmp, cudaStream_t st);
+// Device memory pool (abi.cu): blocks are cached per rounded size; free a
+// block only after pool_fence() once no kernel can still use it.
+void* pool_alloc(size_t bytes);
+void pool_free(void* p);
+void pool_fence();
+// Level-0 coupling CSR (kernels_setup.cu): m tuples in, rows ascending,
+// columns ascending per row, duplicates summed in input order; the outputs
+// hold at least m entries (N + 1 for u_map's N).  Synchronises st.
+struct UAssemble {
+  int N;
+  long long m;
+  const int* row;
+  const int* col;
+  const double* val;
+  const unsigned char* bits;
+  int* u_rows;
+  int* u_ptr;
+  int* u_col;
+  double* u_val;
+  unsigned char* u_bits;
+  int* u_map;
+};
+void launch_uassemble(const UAssemble& a, int* nr, long long* nnz, cudaStream_t st);
 size_t scan_tmp_ints(long long n);
 
 // cycle (T = float or double)

@@ -74,6 +74,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "ssamg_status_string": (ctypes.c_char_p, [_i]),
     "ssamg_last_error": (ctypes.c_char_p, []),
+    "ssamg_release_device_cache": (ctypes.c_longlong, []),
     "ssamg_grid_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
     "ssamg_grid_set_box": (_i, [_vp, _i, _ip, _ip]),
     "ssamg_grid_assemble": (_i, [_vp]),

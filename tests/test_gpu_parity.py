@@ -478,3 +478,55 @@ def test_cluster_tail_matches_oracle(S, prob, cells):
     x = torch.zeros_like(rt)
     st = sv.solve(torch.as_tensor(prob.b[0], device="cuda"), x)
     assert st.converged and abs(st.iterations - ref.iterations) <= 1
+
+
+def _split_couplings(prob, seed=11):
+    """The same matrix with every coupling given twice (value halves, exact)
+    and the coupling list shuffled."""
+    import dataclasses
+    m = prob.nnz_u
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(2 * m)
+    rep = lambda a: np.concatenate([a, a])[perm]
+    return dataclasses.replace(prob, u_part=rep(prob.u_part), u_idx=rep(prob.u_idx),
+                               u_dir=rep(prob.u_dir), u_nbor_part=rep(prob.u_nbor_part),
+                               u_nbor_idx=rep(prob.u_nbor_idx), u_val=rep(prob.u_val * 0.5))
+
+
+@pytest.mark.parametrize("prob", [P.multipart_aniso(m=7, layout=(2, 2, 1), seed=3), P.samr(8),
+                                  P.three_point(5)], ids=["aniso4", "samr", "tc3"])
+def test_duplicate_and_unordered_couplings_assemble_the_same_rows(S, prob):
+    """Matrix assembly sorts couplings by row and column and sums duplicates:
+    a shuffled list with every coupling split in two exact halves gives the
+    same level-0 coupling rows, bit for bit, and the same hierarchy."""
+    _, _, sv1 = gpu_setup(S, prob)
+    _, _, sv2 = gpu_setup(S, _split_couplings(prob))
+    u1 = gpu_level(S, sv1, 0, prob.nparts)["U"]
+    u2 = gpu_level(S, sv2, 0, prob.nparts)["U"]
+    assert u1 == u2 and len(u1) > 0
+    for l in range(1, sv1.num_levels()):
+        a = gpu_level(S, sv1, l, prob.nparts)
+        b = gpu_level(S, sv2, l, prob.nparts)
+        assert a["U"] == b["U"]
+        for pa, pb in zip(a["parts"], b["parts"]):
+            for o in pa["S"]:
+                assert np.array_equal(pa["S"][o], pb["S"][o])
+
+
+def test_device_cache_release_after_objects(S):
+    """Objects destroyed leave their device memory to the pool; releasing it
+    returns the cached bytes, a second release returns nothing, and a new
+    matrix and solver still work afterwards."""
+    import gc
+    prob = P.multipart_aniso(m=6, layout=(2, 1, 1), seed=1)
+    for _ in range(2):
+        _, _, sv = gpu_setup(S, prob)
+        del sv
+        gc.collect()
+    torch.cuda.synchronize()
+    first = S.lib().ssamg_release_device_cache()
+    assert first > 0
+    assert S.lib().ssamg_release_device_cache() == 0
+    h = O.setup(prob)
+    _, _, sv = gpu_setup(S, prob)
+    compare_hierarchy(S, prob, sv, h)
