@@ -417,16 +417,21 @@ __device__ __forceinline__ void u_row_job(const LevelView<T>& L, int rb, Pre&& p
                   (int)threadIdx.x & (L.tpr - 1), pre, f);
 }
 
-// Block-wide sum (deterministic: fixed shuffle tree, then fixed warp order).
+// Block-wide sum (deterministic: fixed order).  sh holds NT doubles.  The
+// threads' values go through shared memory and one warp adds them: lane l
+// sums values l, l + 32, ... in order, then a fixed shuffle tree.  FP64 adds
+// run at 1/64 of the FP32 rate on this GPU, so a shuffle tree in every warp
+// (5 adds per thread) cost as much as the kernels' own FP64 work when each
+// thread holds a few cells; this takes NT/32 - 1 + 5 adds in one warp.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
+  sh[threadIdx.x] = v;
   __syncthreads();
   double r = 0.0;
-  if (w == 0) {
-    r = (l < NT / 32) ? sh[l] : 0.0;
+  if (threadIdx.x < 32) {
+    r = sh[threadIdx.x];
+#pragma unroll
+    for (int q = 1; q < NT / 32; ++q) r += sh[threadIdx.x + 32 * q];
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   __syncthreads();

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(NT, 4) k_relax_final(LevelView<T> L, const T* 
                                                        double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 5 : 4) k7b_relax_final(Le
                                                       double* zprev, int flex, double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_pcg_init(LevelView<double> L, const
                                                    const double* x, double* r, double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(NT, 4) k7b_spmv_dot(LevelView<double> L, const
                                                    double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.bblk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -1144,7 +1144,7 @@ __global__ void __launch_bounds__(NT, 4) k_matvec(LevelView<double> L, const dou
 template <int K>
 __device__ __forceinline__ void finish_sums(const double* __restrict__ partial, int b0, int b1,
                                             double* out) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   for (int q = 0; q < K; ++q) {
     double s = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += NT) s += partial[(long long)K * b + q];
@@ -1160,7 +1160,7 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
                                                  double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -1207,7 +1207,7 @@ __global__ void __launch_bounds__(NT) k_pcg_start(LevelView<double> L, const dou
                                                   int flex, double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -1253,7 +1253,7 @@ __global__ void __launch_bounds__(NT) k_pcg_dots_rz(LevelView<double> L,
                                                     double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -1320,7 +1320,7 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_spmv_dot(LevelView<double> L, con
                                                      double* partial) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
@@ -1364,7 +1364,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const do
                                                    const PcgScalars* sc) {
   pdl_trigger();
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();

@@ -36,7 +36,7 @@ __device__ __forceinline__ int p_row_arrays(const DPart& p, const T* __restrict_
 // nonzero, not NaN: the same decision as diag < 0).
 __global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __restrict__ partial) {
   __shared__ DPart sp;
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   __shared__ int shc[NT / 32][SSAMG_MAXE];
   int p = block_part(L.blk, L.parts, L.np, sp);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_wsum(LevelView<double> L, double* __rest
 __global__ void __launch_bounds__(NT) k_wfinal(const int* __restrict__ blk,
                                                const double* __restrict__ partial,
                                                double* __restrict__ c) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   int p = blockIdx.x;
   int b0 = blk[p], b1 = blk[p + 1];
   for (int d = 0; d < 3; ++d) {
@@ -875,7 +875,7 @@ __global__ void k_coarse_assemble(LevelView<double> L, double* __restrict__ A) {
 // Left-looking Cholesky A = L L^T in place (lower triangle), one block.
 // status: 0 ok, 1 not positive definite.
 __global__ void __launch_bounds__(NT) k_cholesky(int n, double* __restrict__ A, int* status) {
-  __shared__ double sh[NT / 32];
+  __shared__ double sh[NT];
   __shared__ double piv;
   for (int jj = 0; jj < n; ++jj) {
     double* rj = A + (long long)jj * n;
