@@ -304,11 +304,19 @@ __device__ __forceinline__ T stencil_sh(const DPart& p, const T* __restrict__ co
   } else if constexpr (SH == SH_K7) {
     return stencil7_canon_checked(p, coef, xc, c, i, j, k);
   } else if constexpr (SH == SH_UGEN) {
+    // parts of one level with different stencils (e.g. semicoarsened in
+    // different directions): the unrolled form of each part's size, chosen
+    // per part (uniform over a block), so that every entry's loads are in
+    // flight together; the same entry order as a plain loop
     const T* a = coef + p.coef[0] + c;
-    const int s = p.ncell;
+    if (p.canon27) return stencil27_unchecked(p, a, xc);
+    if (p.nent == 15) return stencil_unchecked<15>(p, a, xc);
+    if (p.nent == 7) return stencil_unchecked<7>(p, a, xc);
+    const int s = p.ncell, n = p.nent;
     T acc = (T)0;
-#pragma unroll 4
-    for (int e = 0; e < p.nent; ++e) acc = fma(a[e * s], xc[p.disp[e]], acc);
+#pragma unroll
+    for (int e = 0; e < SSAMG_MAXE; ++e)
+      if (e < n) acc = fma(a[e * s], xc[p.disp[e]], acc);
     return acc;
   } else {
     if (p.nent == 7) return stencil_checked_fixed<7>(p, coef, xc, c, i, j, k);
