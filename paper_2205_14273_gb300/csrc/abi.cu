@@ -262,6 +262,8 @@ struct ssamg_solver_s {
   int hist_cap = 0;               // right-hand sides the history holds
   int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
+  cudaStream_t ss = nullptr;  // setup side stream (structured Galerkin products)
+  cudaEvent_t ev_p = nullptr, ev_rap = nullptr;
   int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
@@ -270,6 +272,9 @@ struct ssamg_solver_s {
     if (sc_hist) cudaFree(sc_hist);
     if (tres_hist) cudaFree(tres_hist);
     if (cs) cudaStreamDestroy(cs);
+    if (ss) cudaStreamDestroy(ss);
+    if (ev_p) cudaEventDestroy(ev_p);
+    if (ev_rap) cudaEventDestroy(ev_rap);
     if (h_sc) cudaFreeHost(h_sc);
     if (h_int) cudaFreeHost(h_int);
     if (h_dbl) cudaFreeHost(h_dbl);
@@ -1326,12 +1331,25 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       s->lev[1].nr = 0;
     }
   }
+  // The structured Galerkin product of a level needs only P (the
+  // interpolation just before it) and nothing of the coupling chain that
+  // follows, so it runs on a side stream beside that chain; the next level's
+  // interpolation (which reads the coarse stencil) waits for it.
+  if (!s->ss) {
+    SSAMG_CUDA(cudaStreamCreateWithFlags(&s->ss, cudaStreamNonBlocking));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_p, cudaEventDisableTiming));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rap, cudaEventDisableTiming));
+  }
   for (int l = 0; l < Lc; ++l) {
     Level& F = s->lev[l];
     Level& C = s->lev[l + 1];
     Level* N2 = l + 2 <= Lc ? &s->lev[l + 2] : nullptr;
+    if (l > 0) SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_rap, 0));
     launch_interp(F, fp32, st);
-    launch_rap_struct(F, C, fp32, st);
+    SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
+    SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_p, 0));
+    launch_rap_struct(F, C, fp32, s->ss);
+    SSAMG_CUDA(cudaEventRecord(s->ev_rap, s->ss));
     C.nnz = 0;
     if (N2) N2->nr = 0;
     if (F.nr == 0) continue;
@@ -1381,6 +1399,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     launch_ucopy(F, C, ust, fp32, st);
     if (N2) make_rows(*N2, s->h_int[1]);
   }
+  if (Lc > 0) SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_rap, 0));
   // has_u may be set on parts whose coarse rows vanished; refresh from U_c
   for (int l = 1; l <= Lc; ++l) {
     Level& L = s->lev[l];
