@@ -263,7 +263,7 @@ struct ssamg_solver_s {
   int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
   cudaStream_t ss = nullptr;  // setup side stream (structured Galerkin products)
-  cudaEvent_t ev_p = nullptr, ev_rap = nullptr;
+  cudaEvent_t ev_p = nullptr, ev_rap = nullptr, ev_rows = nullptr, ev_mark = nullptr;
   int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
@@ -275,6 +275,8 @@ struct ssamg_solver_s {
     if (ss) cudaStreamDestroy(ss);
     if (ev_p) cudaEventDestroy(ev_p);
     if (ev_rap) cudaEventDestroy(ev_rap);
+    if (ev_rows) cudaEventDestroy(ev_rows);
+    if (ev_mark) cudaEventDestroy(ev_mark);
     if (h_sc) cudaFreeHost(h_sc);
     if (h_int) cudaFreeHost(h_int);
     if (h_dbl) cudaFreeHost(h_dbl);
@@ -1306,13 +1308,22 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   // (which coarse cells the fine coupling rows' P rows reach), so they are
   // found one level ahead: each level waits on the host once, for the entry
   // count of its own U_c and the row count of the next level together.
-  auto mark_rows = [&](const Level& F, const Level& C) {
+  int* scan_tmp2 = nullptr;  // the side stream's scan scratch
+  if (!s->ss) {
+    SSAMG_CUDA(cudaStreamCreateWithFlags(&s->ss, cudaStreamNonBlocking));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_p, cudaEventDisableTiming));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rap, cudaEventDisableTiming));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rows, cudaEventDisableTiming));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_mark, cudaEventDisableTiming));
+  }
+  auto mark_rows = [&](const Level& F, const Level& C, cudaStream_t ms) {
     if (!marker) {
       marker = aalloc<int>(s->arena, maxN + 1);
       scan_tmp = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
+      scan_tmp2 = aalloc<int>(s->arena, (long long)scan_tmp_ints(maxN + 1) + 1);
     }
-    launch_uprow(F, C, nullptr, nullptr, nullptr, marker, st);
-    launch_scan(marker, C.N, scan_tmp, st);
+    launch_uprow(F, C, nullptr, nullptr, nullptr, marker, ms);
+    launch_scan(marker, C.N, ms == st ? scan_tmp : scan_tmp2, ms);
   };
   auto make_rows = [&](Level& C, int nr) {
     C.nr = nr;
@@ -1322,28 +1333,34 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   };
   if (Lc > 0) {
     if (L0.nr > 0) {
-      mark_rows(L0, s->lev[1]);
+      mark_rows(L0, s->lev[1], st);
       SSAMG_CUDA(cudaMemcpyAsync(s->h_int, marker + s->lev[1].N, sizeof(int),
                                  cudaMemcpyDeviceToHost, st));
       SSAMG_CUDA(cudaStreamSynchronize(st));
       make_rows(s->lev[1], s->h_int[0]);
+      SSAMG_CUDA(cudaEventRecord(s->ev_rows, st));
     } else {
       s->lev[1].nr = 0;
     }
   }
-  // The structured Galerkin product of a level needs only P (the
-  // interpolation just before it) and nothing of the coupling chain that
-  // follows, so it runs on a side stream beside that chain; the next level's
-  // interpolation (which reads the coarse stencil) waits for it.
-  if (!s->ss) {
-    SSAMG_CUDA(cudaStreamCreateWithFlags(&s->ss, cudaStreamNonBlocking));
-    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_p, cudaEventDisableTiming));
-    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rap, cudaEventDisableTiming));
-  }
+  // Two kinds of work of a level run on a side stream beside the coupling
+  // chain on st: the marking of the next level's coupling rows (it needs
+  // only this coarse level's rows and the geometry; the host waits for its
+  // row count through ev_mark) and the structured Galerkin product (it needs
+  // only P, the interpolation just before it; the next level's
+  // interpolation, which reads the coarse stencil, waits for it).
   for (int l = 0; l < Lc; ++l) {
     Level& F = s->lev[l];
     Level& C = s->lev[l + 1];
     Level* N2 = l + 2 <= Lc ? &s->lev[l + 2] : nullptr;
+    const bool mark = N2 && F.nr > 0 && C.nr > 0;
+    if (mark) {
+      SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_rows, 0));
+      mark_rows(C, *N2, s->ss);
+      SSAMG_CUDA(cudaMemcpyAsync(s->h_int + 1, marker + N2->N, sizeof(int),
+                                 cudaMemcpyDeviceToHost, s->ss));
+      SSAMG_CUDA(cudaEventRecord(s->ev_mark, s->ss));
+    }
     if (l > 0) SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_rap, 0));
     launch_interp(F, fp32, st);
     SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
@@ -1380,12 +1397,8 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     launch_usort(F, C, longrows, fr, frw, C.u_ptr, ust, s->d_err, st);
     launch_scan(C.u_ptr, C.nr, scan_tmp, st);
     SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (N2) {
-      mark_rows(C, *N2);
-      SSAMG_CUDA(cudaMemcpyAsync(s->h_int + 1, marker + N2->N, sizeof(int),
-                                 cudaMemcpyDeviceToHost, st));
-    }
     SSAMG_CUDA(cudaStreamSynchronize(st));
+    if (mark) SSAMG_CUDA(cudaEventSynchronize(s->ev_mark));
     C.nnz = s->h_int[0];
     C.u_col = aalloc<int>(s->arena, C.nnz);
     C.u_val = aalloc<double>(s->arena, C.nnz);
@@ -1397,7 +1410,10 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     C.u_rw = aalloc<double>(s->arena, 2 * C.nnz);
     if (fp32) C.u_rw32 = aalloc<float>(s->arena, 2 * C.nnz);
     launch_ucopy(F, C, ust, fp32, st);
-    if (N2) make_rows(*N2, s->h_int[1]);
+    if (N2) {
+      make_rows(*N2, s->h_int[1]);
+      SSAMG_CUDA(cudaEventRecord(s->ev_rows, st));
+    }
   }
   if (Lc > 0) SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_rap, 0));
   // has_u may be set on parts whose coarse rows vanished; refresh from U_c
