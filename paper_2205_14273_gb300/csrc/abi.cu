@@ -263,7 +263,8 @@ struct ssamg_solver_s {
   int h_cap = 0;               // problems the pinned buffers hold
   cudaStream_t cs = nullptr;  // capture stream
   cudaStream_t ss = nullptr;  // setup side stream (structured Galerkin products)
-  cudaEvent_t ev_p = nullptr, ev_rap = nullptr, ev_rows = nullptr, ev_mark = nullptr;
+  cudaEvent_t ev_p = nullptr, ev_rap = nullptr, ev_rows = nullptr, ev_mark = nullptr,
+              ev_uc = nullptr;
   int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
@@ -277,6 +278,7 @@ struct ssamg_solver_s {
     if (ev_rap) cudaEventDestroy(ev_rap);
     if (ev_rows) cudaEventDestroy(ev_rows);
     if (ev_mark) cudaEventDestroy(ev_mark);
+    if (ev_uc) cudaEventDestroy(ev_uc);
     if (h_sc) cudaFreeHost(h_sc);
     if (h_int) cudaFreeHost(h_int);
     if (h_dbl) cudaFreeHost(h_dbl);
@@ -1315,6 +1317,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rap, cudaEventDisableTiming));
     SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_rows, cudaEventDisableTiming));
     SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_mark, cudaEventDisableTiming));
+    SSAMG_CUDA(cudaEventCreateWithFlags(&s->ev_uc, cudaEventDisableTiming));
   }
   auto mark_rows = [&](const Level& F, const Level& C, cudaStream_t ms) {
     if (!marker) {
@@ -1365,16 +1368,20 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     launch_interp(F, fp32, st);
     SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
     SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_p, 0));
+    if (F.nr > 0) {
+      // P rows of the coupling columns (kept: the prolongation's row jobs
+      // use them), on the side stream too; the merge waits for them
+      F.u_pj = aalloc<int>(s->arena, 2 * F.nnz);
+      F.u_pw = aalloc<double>(s->arena, 2 * F.nnz);
+      if (fp32) F.u_pw32 = aalloc<float>(s->arena, 2 * F.nnz);
+      launch_ucols(nullptr, F, fp32, true, false, s->ss);
+      SSAMG_CUDA(cudaEventRecord(s->ev_uc, s->ss));
+    }
     launch_rap_struct(F, C, fp32, s->ss);
     SSAMG_CUDA(cudaEventRecord(s->ev_rap, s->ss));
     C.nnz = 0;
     if (N2) N2->nr = 0;
     if (F.nr == 0) continue;
-    // P rows of the coupling columns (kept: the prolongation's row jobs use them)
-    F.u_pj = aalloc<int>(s->arena, 2 * F.nnz);
-    F.u_pw = aalloc<double>(s->arena, 2 * F.nnz);
-    if (fp32) F.u_pw32 = aalloc<float>(s->arena, 2 * F.nnz);
-    launch_ucols(nullptr, F, fp32, true, false, st);
     if (C.nr == 0) continue;
     // P rows of the coupling rows, and the coarse rows they reach
     int* prI = aalloc<int>(s->arena, 2ll * F.nr);
@@ -1394,6 +1401,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     ust.col = aalloc<int>(s->arena, 4 * F.nnz);
     ust.val = aalloc<double>(s->arena, 4 * F.nnz);
     ust.bits = aalloc<unsigned char>(s->arena, 4 * F.nnz);
+    SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_uc, 0));
     launch_usort(F, C, longrows, fr, frw, C.u_ptr, ust, s->d_err, st);
     launch_scan(C.u_ptr, C.nr, scan_tmp, st);
     SSAMG_CUDA(cudaMemcpyAsync(s->h_int, C.u_ptr + C.nr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1462,7 +1470,11 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   }
 
   // ---- Section 3.4: smoother diagonals
-  launch_dinv(s->lev, s->prm.relax, s->prm.relax_factor, fp32, st);
+  // on the side stream, beside the coarsest factor (which does not read them)
+  SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
+  SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_p, 0));
+  launch_dinv(s->lev, s->prm.relax, s->prm.relax_factor, fp32, s->ss);
+  SSAMG_CUDA(cudaEventRecord(s->ev_rap, s->ss));
 
   // ---- coarsest level: dense Cholesky (FP64)
   Level& LL = s->lev[Lc];
@@ -1477,6 +1489,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
       launch_coarse_inverse((int)LL.N, s->chol, s->cinv, st);
     }
   }
+  SSAMG_CUDA(cudaStreamWaitEvent(st, s->ev_rap, 0));
   // ---- fused coarse tail: the trailing levels that fit one block
   s->tail_lt = -1;
   s->tail_dev = nullptr;
