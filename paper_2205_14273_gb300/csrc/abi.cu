@@ -944,7 +944,11 @@ void build_ctail(ssamg_solver s, cudaStream_t st) {
   std::vector<long long> first(Lc + 2, 0);
   for (int l = lt; l <= Lc; ++l) first[l + 1] = first[l] + s->lev[l].N;
   int* dlen = aalloc<int>(s->arena, first[Lc + 1] - first[lt]);
-  for (int l = lt; l <= Lc; ++l) launch_ctail_rowlen(s->lev[l], dlen + (first[l] - first[lt]), st);
+  {
+    std::vector<int*> lens;
+    for (int l = lt; l <= Lc; ++l) lens.push_back(dlen + (first[l] - first[lt]));
+    launch_ctail_rowlen(s->lev, lt, Lc, lens.data(), st);
+  }
   std::vector<int> len(first[Lc + 1] - first[lt]);
   SSAMG_CUDA(cudaMemcpyAsync(len.data(), dlen, sizeof(int) * len.size(), cudaMemcpyDeviceToHost, st));
   SSAMG_CUDA(cudaStreamSynchronize(st));
@@ -1029,13 +1033,7 @@ void build_ctail(ssamg_solver s, cudaStream_t st) {
       }
       SSAMG_CUDA(cudaMemcpy2DAsync(img, (size_t)ro, rp.data(), (size_t)rp_bytes, (size_t)rp_bytes,
                                    nc, cudaMemcpyHostToDevice, st));
-      for (int j = 0; j < nt; ++j) {
-        const int l = t0 + j;
-        launch_ctail_fill(fp32, s->lev[l], j > 0 ? &s->lev[l - 1] : nullptr,
-                          j + 1 < nt ? &s->lev[l + 1] : nullptr,
-                          (j + 1 == nt && direct) ? s->cinv : nullptr, a.nL, a.lev[j],
-                          j > 0 ? a.lev[j - 1].S : 1, j + 1 < nt ? a.lev[j + 1].S : 1, img, ro, st);
-      }
+      launch_ctail_fill(fp32, s->lev, t0, a, direct ? s->cinv : nullptr, img, ro, st);
       SSAMG_CUDA(cudaStreamSynchronize(st));  // rp is a host temporary
       a.image = img;
       s->ctail = a;
@@ -1352,6 +1350,11 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   // row count through ev_mark) and the structured Galerkin product (it needs
   // only P, the interpolation just before it; the next level's
   // interpolation, which reads the coarse stencil, waits for it).
+  // Level 0's operator is final already: its smoother diagonal (the largest
+  // of them) runs on the side stream beside the whole level loop.
+  SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
+  SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_p, 0));
+  launch_dinv(s->lev, 0, 0, s->prm.relax, s->prm.relax_factor, fp32, s->ss);
   for (int l = 0; l < Lc; ++l) {
     Level& F = s->lev[l];
     Level& C = s->lev[l + 1];
@@ -1470,10 +1473,11 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   }
 
   // ---- Section 3.4: smoother diagonals
-  // on the side stream, beside the coarsest factor (which does not read them)
+  // (level 0's were launched before the level loop) on the side stream,
+  // beside the coarsest factor, which does not read them
   SSAMG_CUDA(cudaEventRecord(s->ev_p, st));
   SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_p, 0));
-  launch_dinv(s->lev, s->prm.relax, s->prm.relax_factor, fp32, s->ss);
+  if (Lc > 0) launch_dinv(s->lev, 1, Lc, s->prm.relax, s->prm.relax_factor, fp32, s->ss);
   SSAMG_CUDA(cudaEventRecord(s->ev_rap, s->ss));
 
   // ---- coarsest level: dense Cholesky (FP64)

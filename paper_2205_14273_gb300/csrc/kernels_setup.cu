@@ -1228,14 +1228,14 @@ void launch_ucols(const Level* Fp, const Level& L, bool fp32, bool pj, bool rj, 
 }
 
 
-void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
-                 cudaStream_t st) {
-  for (size_t l0 = 0; l0 < lev.size(); l0 += SSAMG_DINV_LEVELS) {
+void launch_dinv(const std::vector<Level>& lev, int first, int last, int relax, double factor,
+                 bool fp32, cudaStream_t st) {
+  for (int l0 = first; l0 <= last; l0 += SSAMG_DINV_LEVELS) {
     DinvArgs a{};
     a.relax = relax;
     a.factor = factor;
     int nb = 0;
-    for (size_t l = l0; l < lev.size() && a.nl < SSAMG_DINV_LEVELS; ++l) {
+    for (int l = l0; l <= last && a.nl < SSAMG_DINV_LEVELS; ++l) {
       const Level& L = lev[l];
       a.lv[a.nl++] = DinvLevel{L.d_parts, L.d_blk, L.coef, L.u_map, L.u_ptr, L.u_val,
                                L.dinv, fp32 ? L.dinv32 : nullptr, L.np, nb};

@@ -39,9 +39,10 @@ __device__ __forceinline__ unsigned short ctail_pack(int g, int S) {
 
 // Row lengths of the tail levels: entries of S inside the box plus the row's
 // couplings.
-__global__ void __launch_bounds__(256) k_ctail_rowlen(LevelView<double> L, int* __restrict__ len) {
-  // a warp per row: lane e tests entry e
-  const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+// Row lengths of one level, a warp per row: lane e tests entry e.
+__device__ __forceinline__ void ctail_rowlen_row(const LevelView<double>& L, int* __restrict__ len,
+                                                 int g) {
+  const int lane = threadIdx.x & 31;
   if (g >= L.N) return;
   const int p = find_part_cell(L.cellstart, L.np, g);
   const DPart& dp = L.parts[p];
@@ -58,22 +59,56 @@ __global__ void __launch_bounds__(256) k_ctail_rowlen(LevelView<double> L, int* 
   }
 }
 
+// Every candidate level in one launch: block b works on the level whose
+// block range holds it (8 rows per block).
+struct CTailRowlenArgs {
+  int nl;
+  int b0[SSAMG_CTAIL_MAX_LEVELS + 1];
+  int* len[SSAMG_CTAIL_MAX_LEVELS];
+  LevelView<double> lv[SSAMG_CTAIL_MAX_LEVELS];
+};
+__global__ void __launch_bounds__(256) k_ctail_rowlen(const __grid_constant__ CTailRowlenArgs A) {
+  int l = 0;
+  while (l + 1 < A.nl && (int)blockIdx.x >= A.b0[l + 1]) ++l;
+  const int g = ((int)blockIdx.x - A.b0[l]) * 8 + (int)(threadIdx.x >> 5);
+  ctail_rowlen_row(A.lv[l], A.len[l], g);
+}
+
 // Fills the images of one tail level l: for every row g, in the slice of its
 // owning CTA: its CSR entries (columns packed in this level's slices), the
 // smoother diagonal, P's row (columns packed in level l+1's slices) when
 // has_p, the restriction row from level l-1 (columns packed in l-1's
 // slices) when Fm is given, and the coarsest inverse's row when inv is
 // given.  The row pointers were written by the host.
+// One tail level's share of a fill launch.
+struct CTailFillLevel {
+  LevelView<double> L, fm, ln;
+  const double* dinv;
+  const double* inv;
+  CTailLevel lv;
+  int has_fm, has_p, Sm, Sn;
+};
+struct CTailFillArgs {
+  int nl, nL;
+  long long ro_bytes;
+  char* image;
+  int b0[SSAMG_CTAIL_MAX_LEVELS + 1];
+  CTailFillLevel lev[SSAMG_CTAIL_MAX_LEVELS];
+};
+
 template <class T>
-__global__ void __launch_bounds__(256) k_ctail_fill(LevelView<double> L, const double* __restrict__ dinv64,
-                             const LevelView<double> Fm, int has_fm, const LevelView<double> Ln,
-                             int has_p, const double* __restrict__ inv, int nL,
-                             CTailLevel lv, int Sm, int Sn, char* __restrict__ image,
-                             long long ro_bytes) {
+__device__ __forceinline__ void ctail_fill_row(const LevelView<double>& L,
+                                               const double* __restrict__ dinv64,
+                                               const LevelView<double>& Fm, int has_fm,
+                                               const LevelView<double>& Ln, int has_p,
+                                               const double* __restrict__ inv, int nL,
+                                               const CTailLevel& lv, int Sm, int Sn,
+                                               char* __restrict__ image, long long ro_bytes,
+                                               int g) {
   // a warp per row: the stencil entries one per lane (slots by ballot, in
   // entry order), the coupling entries strided over the lanes, the rest by
   // lane 0
-  const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   if (g >= L.N) return;
   const int owner = g / lv.S, li = g - owner * lv.S;
   char* img = image + owner * ro_bytes;
@@ -156,6 +191,17 @@ __global__ void __launch_bounds__(256) k_ctail_fill(LevelView<double> L, const d
     rc[2 * lv.S + li] = f2 >= 0 ? ctail_pack(f2, Sm) : 0;
     rv[2 * lv.S + li] = f2 >= 0 ? (T)w2 : (T)0;
   }
+}
+
+// Every tail level's images in one launch (8 rows per block).
+template <class T>
+__global__ void __launch_bounds__(256) k_ctail_fill(const __grid_constant__ CTailFillArgs A) {
+  int l = 0;
+  while (l + 1 < A.nl && (int)blockIdx.x >= A.b0[l + 1]) ++l;
+  const CTailFillLevel& v = A.lev[l];
+  const int g = ((int)blockIdx.x - A.b0[l]) * 8 + (int)(threadIdx.x >> 5);
+  ctail_fill_row<T>(v.L, v.dinv, v.fm, v.has_fm, v.ln, v.has_p, v.inv, A.nL, v.lv, v.Sm, v.Sn,
+                    A.image, A.ro_bytes, g);
 }
 
 // Cluster-wide barrier between the tail's steps.  The non-aligned forms of
@@ -355,24 +401,55 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------
 template <class T>
 bool ctail_query(int nc, long long smem);
-void launch_ctail_rowlen(const Level& L, int* len, cudaStream_t st) {
-  k_ctail_rowlen<<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), len);
-  SSAMG_LAUNCH_CHECK();
+void launch_ctail_rowlen(const std::vector<Level>& lev, int first, int last, int* const* len,
+                         cudaStream_t st) {
+  for (int l0 = first; l0 <= last; l0 += SSAMG_CTAIL_MAX_LEVELS) {
+    CTailRowlenArgs a{};
+    int nb = 0;
+    for (int l = l0; l <= last && a.nl < SSAMG_CTAIL_MAX_LEVELS; ++l) {
+      a.b0[a.nl] = nb;
+      a.len[a.nl] = len[l - first];
+      a.lv[a.nl] = lev[l].view<double>();
+      ++a.nl;
+      nb += cdiv(lev[l].N, 8);
+    }
+    a.b0[a.nl] = nb;
+    if (nb == 0) continue;
+    k_ctail_rowlen<<<nb, 256, 0, st>>>(a);
+    SSAMG_LAUNCH_CHECK();
+  }
 }
 
-void launch_ctail_fill(bool fp32, const Level& L, const Level* Fm, const Level* Ln,
-                       const double* inv, int nL, const CTailLevel& lv, int Sm, int Sn,
-                       char* image, long long ro_bytes, cudaStream_t st) {
-  const LevelView<double> fm = Fm ? Fm->view<double>() : L.view<double>();
-  const LevelView<double> ln = Ln ? Ln->view<double>() : L.view<double>();
+void launch_ctail_fill(bool fp32, const std::vector<Level>& lev, int t0, const CTailArgs& ta,
+                       const double* inv, char* image, long long ro_bytes, cudaStream_t st) {
+  const int nt = ta.nt;
+  CTailFillArgs a{};
+  a.nl = nt;
+  a.nL = ta.nL;
+  a.ro_bytes = ro_bytes;
+  a.image = image;
+  int nb = 0;
+  for (int j = 0; j < nt; ++j) {
+    const Level& L = lev[t0 + j];
+    CTailFillLevel& v = a.lev[j];
+    v.L = L.view<double>();
+    v.fm = j > 0 ? lev[t0 + j - 1].view<double>() : v.L;
+    v.ln = j + 1 < nt ? lev[t0 + j + 1].view<double>() : v.L;
+    v.has_fm = j > 0;
+    v.has_p = j + 1 < nt;
+    v.dinv = L.dinv;
+    v.inv = (j + 1 == nt) ? inv : nullptr;
+    v.lv = ta.lev[j];
+    v.Sm = j > 0 ? ta.lev[j - 1].S : 1;
+    v.Sn = j + 1 < nt ? ta.lev[j + 1].S : 1;
+    a.b0[j] = nb;
+    nb += cdiv(L.N, 8);
+  }
+  a.b0[nt] = nb;
   if (fp32)
-    k_ctail_fill<float><<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), L.dinv, fm, Fm != nullptr,
-                                                        ln, Ln != nullptr, inv, nL, lv, Sm, Sn,
-                                                        image, ro_bytes);
+    k_ctail_fill<float><<<nb, 256, 0, st>>>(a);
   else
-    k_ctail_fill<double><<<cdiv(L.N, 8), 256, 0, st>>>(L.view<double>(), L.dinv, fm,
-                                                         Fm != nullptr, ln, Ln != nullptr, inv, nL,
-                                                         lv, Sm, Sn, image, ro_bytes);
+    k_ctail_fill<double><<<nb, 256, 0, st>>>(a);
   SSAMG_LAUNCH_CHECK();
 }
 

@@ -395,8 +395,9 @@ struct UStage {
 void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
                   const double* frw, int* counts, const UStage& t, int* err, cudaStream_t st);
 void launch_ucopy(const Level& F, const Level& Cl, const UStage& t, bool fp32, cudaStream_t st);
-void launch_dinv(const std::vector<Level>& lev, int relax, double factor, bool fp32,
-                 cudaStream_t st);
+// Smoother diagonals of levels first..last in one launch (per SSAMG_DINV_LEVELS).
+void launch_dinv(const std::vector<Level>& lev, int first, int last, int relax, double factor,
+                 bool fp32, cudaStream_t st);
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 // zero the values of a per-cell entry with offset o where c + o leaves the box
 void launch_mask_outside(double* vals, const int n[3], const int o[3], cudaStream_t st);
@@ -478,10 +479,12 @@ int tail_max_blocks();
 int barrier_selftest(int nblocks, int extra, unsigned cap, cudaStream_t st);
 void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t st);
 // cluster tail (kernels_tail.cu)
-void launch_ctail_rowlen(const Level& L, int* len, cudaStream_t st);
-void launch_ctail_fill(bool fp32, const Level& L, const Level* Fm, const Level* Ln,
-                       const double* inv, int nL, const CTailLevel& lv, int Sm, int Sn,
-                       char* image, long long ro_bytes, cudaStream_t st);
+// Row lengths of levels first..last (len[l - first]: N_l ints each) and the
+// images of the tail levels t0 .. t0 + ta.nt - 1, each in one launch.
+void launch_ctail_rowlen(const std::vector<Level>& lev, int first, int last, int* const* len,
+                         cudaStream_t st);
+void launch_ctail_fill(bool fp32, const std::vector<Level>& lev, int t0, const CTailArgs& ta,
+                       const double* inv, char* image, long long ro_bytes, cudaStream_t st);
 // Allows the tail kernel nc-CTA clusters and smem bytes of shared memory per
 // CTA; false when the device cannot run such a cluster.
 template <class T>
