@@ -50,10 +50,11 @@ const char* ssamg_status_string(int status);
 /* Detail of the last failure on the calling host thread (valid until the
  * next failing call on that thread). */
 const char* ssamg_last_error(void);
-/* Device memory that destroyed matrices and solvers left to the library's
- * pool (kept per rounded size and reused by the next objects, so that
- * creating them per step costs no cudaMalloc / cudaFree) is returned to the
- * driver.  Returns the number of bytes released.  Never fails. */
+/* Device memory and pinned host buffers that destroyed matrices and solvers
+ * left to the library's pools (kept per rounded size and reused by the next
+ * objects, so that creating them per step costs no cudaMalloc / cudaFree /
+ * cudaMallocHost) are returned to the driver.  Returns the number of device
+ * bytes released.  Never fails. */
 long long ssamg_release_device_cache(void);
 
 /* ---------------------------------------------------------------- grid ---

@@ -90,11 +90,65 @@ void pool_free(void* q) {
   P.live.erase(it);
 }
 
+
+// Pinned host buffers of destroyed solvers are kept the same way (per
+// rounded size): cudaMallocHost costs far more than a small set-up step.
+namespace {
+struct HostPool {
+  std::mutex m;
+  std::multimap<size_t, void*> cache;
+  std::unordered_map<void*, size_t> live;
+};
+HostPool& host_pool() {
+  static HostPool* p = new HostPool;
+  return *p;
+}
+}  // namespace
+
+void* pinned_alloc(size_t bytes) {
+  HostPool& P = host_pool();
+  const size_t r = pool_round(std::max<size_t>(bytes, 1));
+  std::lock_guard<std::mutex> lk(P.m);
+  auto it = P.cache.find(r);
+  void* q = nullptr;
+  if (it != P.cache.end()) {
+    q = it->second;
+    P.cache.erase(it);
+  } else if (cudaMallocHost(&q, r) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  P.live[q] = r;
+  return q;
+}
+
+// Only after the work that reads or writes the buffer has finished.
+void pinned_free(void* q) {
+  if (!q) return;
+  HostPool& P = host_pool();
+  std::lock_guard<std::mutex> lk(P.m);
+  auto it = P.live.find(q);
+  if (it == P.live.end()) return;
+  P.cache.emplace(it->second, q);
+  P.live.erase(it);
+}
+
+template <class T>
+T* pinned_new(long long n) {
+  T* q = (T*)pinned_alloc(sizeof(T) * (size_t)std::max<long long>(n, 1));
+  if (!q) throw SsamgError{SSAMG_ERR_OOM, "pinned host allocation failed"};
+  return q;
+}
+
 extern "C" long long ssamg_release_device_cache(void) {
   DevPool& P = dev_pool();
   std::lock_guard<std::mutex> lk(P.m);
   const long long n = (long long)P.cached;
   pool_trim(P);
+  HostPool& H = host_pool();
+  std::lock_guard<std::mutex> lh(H.m);
+  for (auto& kv : H.cache) cudaFreeHost(kv.second);
+  H.cache.clear();
   return n;
 }
 
@@ -279,10 +333,11 @@ struct ssamg_solver_s {
     if (ev_rows) cudaEventDestroy(ev_rows);
     if (ev_mark) cudaEventDestroy(ev_mark);
     if (ev_uc) cudaEventDestroy(ev_uc);
-    if (h_sc) cudaFreeHost(h_sc);
-    if (h_int) cudaFreeHost(h_int);
-    if (h_dbl) cudaFreeHost(h_dbl);
-    if (h_up) cudaFreeHost(h_up);
+    if (h_sc || h_int || h_dbl || h_up) pool_fence();
+    pinned_free(h_sc);
+    pinned_free(h_int);
+    pinned_free(h_dbl);
+    pinned_free(h_up);
   }
 };
 
@@ -896,10 +951,10 @@ void upload_levels(ssamg_solver s, cudaStream_t st) {
     total += al(sizeof(DPart) * np) + 4 * al(sizeof(int) * (np + 1));
   }
   if (s->h_up_cap < total) {
-    if (s->h_up) cudaFreeHost(s->h_up);
+    pinned_free(s->h_up);
     s->h_up = nullptr;
     s->h_up_cap = 0;
-    SSAMG_CUDA(cudaMallocHost(&s->h_up, total));
+    s->h_up = pinned_new<char>((long long)total);
     s->h_up_cap = total;
   }
   char* dev = (char*)s->arena.alloc(total);
@@ -1061,15 +1116,15 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   if (!s->part_prob.empty() && (int)s->part_prob.size() != np)
     throw SsamgError{SSAMG_ERR_ARG, "the problem map does not match the grid's parts"};
   if (s->h_cap < s->nprob) {
-    if (s->h_sc) cudaFreeHost(s->h_sc);
-    if (s->h_int) cudaFreeHost(s->h_int);
-    if (s->h_dbl) cudaFreeHost(s->h_dbl);
+    pinned_free(s->h_sc);
+    pinned_free(s->h_int);
+    pinned_free(s->h_dbl);
     s->h_sc = nullptr;
     s->h_int = nullptr;
     s->h_dbl = nullptr;
-    SSAMG_CUDA(cudaMallocHost(&s->h_sc, sizeof(PcgScalars) * s->nprob));
-    SSAMG_CUDA(cudaMallocHost(&s->h_int, sizeof(int) * 16));
-    SSAMG_CUDA(cudaMallocHost(&s->h_dbl, sizeof(double) * (2 * s->nprob + 16)));
+    s->h_sc = pinned_new<PcgScalars>(s->nprob);
+    s->h_int = pinned_new<int>(16);
+    s->h_dbl = pinned_new<double>(2 * s->nprob + 16);
     s->h_cap = s->nprob;
   }
 
