@@ -245,6 +245,17 @@ int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, v
 /* Number of stored per-cell stencil coefficients of a level (constant
  * entries excluded), for algorithmic-byte counts. */
 int ssamg_level_stored_coefficients(ssamg_solver s, int level, long long* ncoef);
+/* Representative grid spacings given by the user (Section 3.1: an option
+ * PFMG offers, used only for coarsening): W is n_parts x 3 host doubles
+ * (part-major, x y z), each > 0 (+inf: never coarsen along that dimension;
+ * unused dimensions are ignored), copied.  From the next ssamg_setup on,
+ * Algorithm 1 and the relaxation weights of Eq. relax1 take them instead of
+ * the spacings computed from the coupling sums; W = NULL (or nparts = 0)
+ * returns to the computed ones.  SSAMG_ERR_ARG for a NaN, zero or negative
+ * value; the next setup fails with SSAMG_ERR_ARG when nparts does not match
+ * the matrix's grid. */
+int ssamg_set_spacings(ssamg_solver s, int nparts, const double* W);
+
 /* Per-part coupling sums c (n_parts x 3) and spacings W (n_parts x 3) of
  * Section 3.1 (W = +inf encoded as HUGE_VAL). */
 int ssamg_spacings(ssamg_solver s, double* c, double* W);

@@ -62,6 +62,8 @@ class Params:
     coarse_direct: int = 1        # 1: dense Cholesky, 0: one relaxation sweep
     skip: int = 0                 # the "skip" option of Section 3.4: 0 off, 1 rounds reading,
                                   # 2 literal test (see skipped_parts)
+    spacings: Optional[np.ndarray] = None  # user "representative grid spacings" (n_parts x 3),
+                                  # used for coarsening instead of W from the coefficients (3.1)
 
 
 @dataclass
@@ -278,6 +280,17 @@ def grid_spacings(c: np.ndarray, ndim: int) -> np.ndarray:
         for d in range(ndim):
             if c[p, d] > 0 and cmax > 0:
                 W[p, d] = math.sqrt(cmax / c[p, d])
+    return W
+
+
+def user_spacings(W, prob) -> np.ndarray:
+    """Representative grid spacings given by the user (Section 3.1: an option
+    kept from PFMG, used only for coarsening): n_parts x 3, positive or +inf;
+    dimensions >= ndim are +inf."""
+    W = np.array(W, dtype=float).reshape(prob.nparts, 3)
+    if np.any(np.isnan(W)) or np.any(W <= 0):
+        raise ValueError("spacings must be positive (or +inf)")
+    W[:, prob.ndim:] = np.inf
     return W
 
 
@@ -661,7 +674,7 @@ def coarse_operator_dense(lev: Level) -> np.ndarray:
 def setup(prob, params: Params = Params()) -> Hierarchy:
     lev0 = level0_from_problem(prob)
     c = coupling_sums(lev0)
-    W0 = grid_spacings(c, prob.ndim)
+    W0 = grid_spacings(c, prob.ndim) if params.spacings is None else user_spacings(params.spacings, prob)
     s_max = params.s_max if params.s_max > 0 else prob.nparts
     boxes, dstars, omegas = coarsen_plan(W0, lev0.lo, lev0.hi, prob.ndim, s_max, params.max_levels)
     levels = [lev0]

@@ -320,6 +320,7 @@ struct ssamg_solver_s {
   cudaEvent_t ev_p = nullptr, ev_rap = nullptr, ev_rows = nullptr, ev_mark = nullptr,
               ev_uc = nullptr;
   int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
+  std::vector<double> user_W;  // user spacings (3 per part), empty: from the coupling sums
   GraphSet graphs;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
   ~ssamg_solver_s() {
@@ -1177,11 +1178,20 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   SSAMG_CUDA(cudaMemcpyAsync(s->c.data(), d_c, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, st));
   SSAMG_CUDA(cudaStreamSynchronize(st));
   s->W.assign(3 * np, HUGE_VAL);
-  for (int p = 0; p < np; ++p) {
-    double cmax = -HUGE_VAL;
-    for (int d = 0; d < ndim; ++d) cmax = std::max(cmax, s->c[3 * p + d]);
-    for (int d = 0; d < ndim; ++d)
-      if (s->c[3 * p + d] > 0 && cmax > 0) s->W[3 * p + d] = std::sqrt(cmax / s->c[3 * p + d]);
+  if (!s->user_W.empty()) {
+    // representative grid spacings given by the user (Section 3.1), used
+    // for coarsening instead of the ones from the coupling sums
+    if ((int)s->user_W.size() != 3 * np)
+      throw SsamgError{SSAMG_ERR_ARG, "the spacings do not match the grid's parts"};
+    for (int p = 0; p < np; ++p)
+      for (int d = 0; d < ndim; ++d) s->W[3 * p + d] = s->user_W[3 * p + d];
+  } else {
+    for (int p = 0; p < np; ++p) {
+      double cmax = -HUGE_VAL;
+      for (int d = 0; d < ndim; ++d) cmax = std::max(cmax, s->c[3 * p + d]);
+      for (int d = 0; d < ndim; ++d)
+        if (s->c[3 * p + d] > 0 && cmax > 0) s->W[3 * p + d] = std::sqrt(cmax / s->c[3 * p + d]);
+    }
   }
 
   // ---- Algorithm 1 on the host: boxes, d* and omega per level
@@ -2679,6 +2689,19 @@ extern "C" int ssamg_selftest_barrier(int nblocks, int extra_arrivals, unsigned 
   if (err) throw SsamgError{SSAMG_ERR_TIMEOUT, "the grid barrier gave up after its poll cap"};
   return SSAMG_OK;
   API_END
+}
+
+extern "C" int ssamg_set_spacings(ssamg_solver s, int nparts, const double* W) {
+  if (!s || nparts < 0) return SSAMG_ERR_ARG;
+  if (!W || nparts == 0) {
+    s->user_W.clear();
+    return SSAMG_OK;
+  }
+  for (int t = 0; t < 3 * nparts; ++t)
+    if (!(W[t] > 0.0)) return SSAMG_ERR_ARG;  // NaN, zero or negative
+  s->user_W.assign(W, W + 3 * nparts);
+  s->ready = false;
+  return SSAMG_OK;
 }
 
 extern "C" int ssamg_selftest_fastdiv(unsigned long long seed, int trials) {

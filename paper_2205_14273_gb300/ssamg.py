@@ -117,6 +117,7 @@ _SIGS = {
     "ssamg_batch_solver": (_vp, [_vp]),
     "ssamg_level_stored_coefficients": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
+    "ssamg_set_spacings": (_i, [_vp, _i, _dp]),
     "ssamg_selftest_barrier": (_i, [_i, _i, ctypes.c_uint, _vp]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
     "ssamg_set_tile_table": (_i, [_vp, _ip]),
@@ -512,6 +513,17 @@ class Solver:
         _check(lib().ssamg_spacings(self.h, c.ctypes.data_as(_dp), W.ctypes.data_as(_dp)),
                "spacings")
         return c.reshape(nparts, 3), W.reshape(nparts, 3)
+
+    def set_spacings(self, W=None):
+        """User representative grid spacings (n_parts x 3, > 0 or inf) used
+        for coarsening from the next setup on; None returns to the ones
+        computed from the coupling sums."""
+        if W is None:
+            _check(lib().ssamg_set_spacings(self.h, 0, None), "set_spacings")
+            return
+        a = np.ascontiguousarray(W, dtype=np.float64).reshape(-1, 3)
+        _check(lib().ssamg_set_spacings(self.h, a.shape[0], a.ctypes.data_as(_dp)),
+               "set_spacings")
 
     def coupling_sums_noalloc(self, level: int, c, stream=None):
         """Per-part coupling sums of `level` into the device tensor c (n_parts

@@ -530,3 +530,38 @@ def test_device_cache_release_after_objects(S):
     h = O.setup(prob)
     _, _, sv = gpu_setup(S, prob)
     compare_hierarchy(S, prob, sv, h)
+
+
+@pytest.mark.parametrize("prob,W", [
+    (P.multipart_aniso(m=11, layout=(2, 2, 2), seed=1), np.ones((8, 3))),
+    (P.laplace7(13), np.array([[1.0, 1.0, 0.5]])),
+    (P.three_point(7), np.array([[1.0, np.inf, 1.0], [0.5, 1.0, 1.0], [1.0, 1.0, 1.0]])),
+], ids=["aniso8-isotropic-W", "cube-W", "tc3-W"])
+def test_user_spacings_match_oracle(S, prob, W):
+    """Representative grid spacings given by the user (Section 3.1) replace
+    the computed ones in Algorithm 1 and Eq. relax1, on both sides."""
+    h = O.setup(prob, O.Params(spacings=W))
+    grid, A = S.matrix_from_problem(prob)
+    sv = S.Solver()
+    sv.set_spacings(W)
+    sv.setup(A)
+    compare_hierarchy(S, prob, sv, h)   # W compared with the oracle's W0: the user's
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    x = torch.zeros_like(b)
+    st = sv.solve(b, x)
+    ref = O.pcg(h, prob.b[0], tol=1e-8)
+    assert abs(st.iterations - ref.iterations) <= 1
+    # back to the computed spacings
+    sv.set_spacings(None)
+    sv.setup(A)
+    compare_hierarchy(S, prob, sv, O.setup(prob))
+
+
+def test_user_spacings_rejected(S):
+    grid, A = S.matrix_from_problem(P.laplace7(6))
+    sv = S.Solver()
+    with pytest.raises(S.SsamgError):
+        sv.set_spacings(np.array([[1.0, float("nan"), 1.0]]))
+    sv.set_spacings(np.ones((2, 3)))          # one part in the grid
+    with pytest.raises(S.SsamgError):
+        sv.setup(A)

@@ -684,3 +684,36 @@ def test_samr_ghost_unknowns_decoupled_on_level_one():
     pr, ijr = f.locate(f.u_row)
     inside = np.all((ijr > 0) & (ijr < m - 1), axis=1)
     assert np.all(inside[pr == 0])
+
+
+# ---------------------------------------------------------------------------
+# Representative grid spacings given by the user (Section 3.1)
+# ---------------------------------------------------------------------------
+
+def test_user_spacings_drive_the_coarsening_directions():
+    """With W = (1, 1, 1/2) on a cube, Algorithm 1 takes the smallest spacing
+    (z) first; doubling it ties all three, so x (smallest index) follows, then
+    y, then z again: z, x, y, z, x, y, ...  The weight of Eq. relax1 at level 0
+    is 2 / (3 - beta/alpha) with 1/W^2 = (1, 1, 4): alpha = 6, beta = 2,
+    omega = 3/4.  Without spacings the isotropic cube cycles x, y, z."""
+    prob = P.laplace7(16)
+    h = O.setup(prob, O.Params(spacings=np.array([[1.0, 1.0, 0.5]])))
+    ds = [lev.dstar[0] for lev in h.levels[:6]]
+    assert ds == [2, 0, 1, 2, 0, 1]
+    assert abs(h.levels[0].omega[0] - 0.75) < 1e-15
+    h0 = O.setup(prob)
+    assert [lev.dstar[0] for lev in h0.levels[:3]] == [0, 1, 2]
+
+
+def test_user_spacings_infinite_dimension_is_coarsened_last():
+    """An infinite spacing is never the argmin while another dimension can
+    still be halved: y is coarsened only once x and z are down to one cell."""
+    prob = P.laplace7(8)
+    h = O.setup(prob, O.Params(spacings=np.array([[1.0, np.inf, 1.0]])))
+    ds = [lev.dstar[0] for lev in h.levels]
+    first_y = ds.index(1)
+    ext = h.levels[first_y].hi[0] - h.levels[first_y].lo[0] + 1
+    assert ext[0] == 1 and ext[2] == 1 and 1 not in ds[:first_y]
+    assert ds[:first_y] == [0, 2, 0, 2, 0, 2]
+    with pytest.raises(ValueError):
+        O.setup(prob, O.Params(spacings=np.array([[1.0, 0.0, 1.0]])))
