@@ -245,6 +245,14 @@ int ssamg_level_copy(ssamg_solver s, int level, int what, int part, int entry, v
 /* Number of stored per-cell stencil coefficients of a level (constant
  * entries excluded), for algorithmic-byte counts. */
 int ssamg_level_stored_coefficients(ssamg_solver s, int level, long long* ncoef);
+/* Residual history of the last solved right-hand side of `problem` (0 for a
+ * single system; a batch's problem index otherwise): rel[k] = ||r_k|| / ||b||
+ * of the PCG's recursive residual for k = 0 .. iterations, at most n values
+ * (host array).  Returns the number written (>= 0), or SSAMG_ERR_STATE
+ * before a setup, SSAMG_ERR_ARG for a bad problem index or pointer.  Call
+ * once the solve's stream has completed (synchronous copies). */
+int ssamg_residual_history(ssamg_solver s, int problem, double* rel, int n);
+
 /* Representative grid spacings given by the user (Section 3.1: an option
  * PFMG offers, used only for coarsening): W is n_parts x 3 host doubles
  * (part-major, x y z), each > 0 (+inf: never coarsen along that dimension;

@@ -310,6 +310,7 @@ struct ssamg_solver_s {
   int* pb = nullptr;           // nprob + 1 level-0 block starts of each problem (device)
   int* pbb = nullptr;          // the same in brick blocks
   PcgCtl* ctl = nullptr;
+  double* hist = nullptr;      // residual history: nprob x (max_iter + 1) squared norms
   PcgScalars* sc_init = nullptr;  // nprob starting scalars (tolerance, caps)
   PcgScalars* sc_hist = nullptr;  // per right-hand side copies of sc (multi-round solves)
   double* tres_hist = nullptr;    // and of the true residual sums
@@ -1635,6 +1636,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->tres = aalloc<double>(s->arena, 2ll * s->nprob);
   s->sc = aalloc<PcgScalars>(s->arena, s->nprob);
   s->ctl = aalloc<PcgCtl>(s->arena, 1);
+  s->hist = aalloc<double>(s->arena, (long long)s->nprob * (s->prm.max_iter + 1));
   SSAMG_CUDA(cudaMemsetAsync(s->ctl, 0, sizeof(PcgCtl), st));
   {
     std::vector<PcgScalars> init(s->nprob);
@@ -1773,7 +1775,8 @@ int vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st, double* 
 // PCG segments.  init: r = b - A x; the first iteration is peeled so that the
 // loop body starts with the V-cycle and ends with the convergence test.
 PcgCtx pcg_ctx(ssamg_solver s) {
-  return PcgCtx{s->pb, s->pbb, s->nprob, s->sc, s->ctl, s->partial};
+  return PcgCtx{s->pb, s->pbb, s->nprob, s->sc, s->ctl, s->partial, s->hist,
+                s->prm.max_iter + 1};
 }
 
 void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
@@ -2688,6 +2691,24 @@ extern "C" int ssamg_selftest_barrier(int nblocks, int extra_arrivals, unsigned 
   const int err = barrier_selftest(nblocks, extra_arrivals, max_polls, (cudaStream_t)stream);
   if (err) throw SsamgError{SSAMG_ERR_TIMEOUT, "the grid barrier gave up after its poll cap"};
   return SSAMG_OK;
+  API_END
+}
+
+extern "C" int ssamg_residual_history(ssamg_solver s, int problem, double* rel, int n) {
+  if (!s || !rel || n < 0) return SSAMG_ERR_ARG;
+  if (!s->ready) return SSAMG_ERR_STATE;
+  if (problem < 0 || problem >= s->nprob) return SSAMG_ERR_ARG;
+  API_BEGIN
+  PcgScalars sc;
+  SSAMG_CUDA(cudaMemcpy(&sc, s->sc + problem, sizeof(sc), cudaMemcpyDeviceToHost));
+  const int stride = s->prm.max_iter + 1;
+  const int m = std::min(n, std::min(sc.iter, s->prm.max_iter) + 1);
+  if (m <= 0) return 0;
+  std::vector<double> h((size_t)m);
+  SSAMG_CUDA(cudaMemcpy(h.data(), s->hist + (long long)problem * stride, sizeof(double) * m,
+                        cudaMemcpyDeviceToHost));
+  for (int k = 0; k < m; ++k) rel[k] = sc.bb > 0 ? std::sqrt(h[k] / sc.bb) : 0.0;
+  return m;
   API_END
 }
 

@@ -1183,7 +1183,8 @@ __global__ void __launch_bounds__(NT, 4) k_pcg_init(LevelView<double> L, const d
 
 // per problem (one block each): ||b||^2, ||r||^2 and the stopping threshold
 __global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* partial,
-                                                     const int* pb, PcgScalars* sc) {
+                                                     const int* pb, PcgScalars* sc,
+                                                     double* hist, int hstride) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[2];
@@ -1195,6 +1196,7 @@ __global__ void __launch_bounds__(NT) k_pcg_init_fin(const double* partial,
     S.rr = out[1];
     S.tol2bb = S.tol * S.tol * out[0];
     S.iter = 0;
+    if (hist) hist[(long long)k * hstride] = out[1];
     S.status = 0;
     S.done = (out[1] <= S.tol2bb) ? 1 : 0;
   }
@@ -1389,7 +1391,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(LevelView<double> L, const do
 __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* partial,
                                                        const int* pb, PcgScalars* sc,
                                                        PcgCtl* ctl, cudaGraphConditionalHandle h,
-                                                       int use_handle) {
+                                                       int use_handle, double* hist,
+                                                       int hstride) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
@@ -1402,6 +1405,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* partial,
     if (!was_done) {
       S.rr = out[0];
       S.iter += 1;
+      if (hist && S.iter < hstride) hist[(long long)k * hstride + S.iter] = out[0];
       if (!isfinite(out[0])) S.status = SSAMG_ERR_BREAKDOWN;
       if (S.status != 0 || out[0] <= S.tol2bb || S.iter >= S.max_iter) S.done = 1;
     }
@@ -1787,7 +1791,8 @@ void launch_pcg_init(const Level& L, const double* b, const double* x, double* r
     SH_DISPATCH(L.shape, (launch_k(k_pcg_init<SHV>, L.nblk, NT, 0, st, L.view<double>(), b, x, r,
                                    c.partial)));
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_init_fin, c.nprob, NT, 0, st, c.partial, partial_ranges(L, c), c.sc);
+  launch_k(k_pcg_init_fin, c.nprob, NT, 0, st, c.partial, partial_ranges(L, c), c.sc, c.hist,
+           c.hstride);
   SSAMG_LAUNCH_CHECK();
 }
 
@@ -1836,7 +1841,8 @@ void launch_pcg_update(const Level& L0, const double* p, const double* q, double
                        cudaStream_t st) {
   launch_k(k_pcg_update, L0.nblk, NT, 0, st, L0.view<double>(), p, q, x, r, c.partial, c.sc);
   SSAMG_LAUNCH_CHECK();
-  launch_k(k_pcg_update_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc, c.ctl, h, use_handle);
+  launch_k(k_pcg_update_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc, c.ctl, h, use_handle,
+           c.hist, c.hstride);
   SSAMG_LAUNCH_CHECK();
 }
 

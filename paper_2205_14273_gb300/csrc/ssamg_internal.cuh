@@ -138,6 +138,8 @@ struct PcgCtx {
   PcgScalars* sc;
   PcgCtl* ctl;
   double* partial;
+  double* hist;    // per problem ||r_k||^2, k = 0..hstride-1 (residual history)
+  int hstride;
 };
 
 // Views passed to kernels by value.

@@ -118,6 +118,7 @@ _SIGS = {
     "ssamg_level_stored_coefficients": (_i, [_vp, _i, ctypes.POINTER(_ll)]),
     "ssamg_selftest_fastdiv": (_i, [ctypes.c_ulonglong, _i]),
     "ssamg_set_spacings": (_i, [_vp, _i, _dp]),
+    "ssamg_residual_history": (_i, [_vp, _i, _dp, _i]),
     "ssamg_selftest_barrier": (_i, [_i, _i, ctypes.c_uint, _vp]),
     "ssamg_time_kernel": (_i, [_vp, _i, _i, _i, _dp, _vp]),
     "ssamg_set_tile_table": (_i, [_vp, _ip]),
@@ -513,6 +514,15 @@ class Solver:
         _check(lib().ssamg_spacings(self.h, c.ctypes.data_as(_dp), W.ctypes.data_as(_dp)),
                "spacings")
         return c.reshape(nparts, 3), W.reshape(nparts, 3)
+
+    def residual_history(self, problem: int = 0, n: Optional[int] = None):
+        """||r_k|| / ||b|| of the last solve, k = 0 .. iterations."""
+        n = n if n is not None else 100000
+        out = np.zeros(n)
+        m = lib().ssamg_residual_history(self.h, problem, out.ctypes.data_as(_dp), n)
+        if m < 0:
+            _check(m, "residual_history")
+        return out[:m]
 
     def set_spacings(self, W=None):
         """User representative grid spacings (n_parts x 3, > 0 or inf) used

@@ -565,3 +565,23 @@ def test_user_spacings_rejected(S):
     sv.set_spacings(np.ones((2, 3)))          # one part in the grid
     with pytest.raises(S.SsamgError):
         sv.setup(A)
+
+
+@pytest.mark.parametrize("prob", [P.multipart_aniso(m=11, layout=(2, 2, 2), seed=1),
+                                  P.samr(8)], ids=["aniso8", "samr"])
+def test_residual_history_matches_oracle(S, prob):
+    """||r_k|| / ||b|| of every iteration (FP64 cycle) against the oracle's
+    PCG history: the same iteration count, each value to 1e-9 relative (the
+    recursive residuals of two FP64 runs that differ in summation order)."""
+    grid, A, sv = gpu_setup(S, prob, tol=1e-8)
+    b = torch.as_tensor(prob.b[0], device="cuda")
+    x = torch.zeros_like(b)
+    st = sv.solve(b, x)
+    hist = sv.residual_history()
+    ref = O.pcg(O.setup(prob), prob.b[0], tol=1e-8)
+    assert len(hist) == st.iterations + 1 == len(ref.history)
+    assert hist[0] == pytest.approx(1.0, rel=1e-14)
+    assert abs(hist[-1] - st.rel_res) <= 1e-15 * max(st.rel_res, 1e-300) * 10
+    h = np.array(ref.history)
+    assert np.all(np.abs(hist - h) <= 1e-9 * h + 1e-300)
+    assert S.lib().ssamg_residual_history(sv.h, 1, None, 4) == S.ERR_ARG
