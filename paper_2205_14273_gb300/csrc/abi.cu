@@ -11,7 +11,25 @@
 #include <numeric>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ssamg_internal.cuh"
+
+// NVTX range around a scope (entry points, set-up stages and levels): seen by
+// profilers that record NVTX, a few nanoseconds otherwise.
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* prefix, int k) {
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%s %d", prefix, k);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Device memory pool: blocks freed by matrices and solvers are kept per
@@ -601,6 +619,7 @@ std::vector<int> storage_order(const ssamg_matrix_s* A) {
 
 extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
   if (!A) return SSAMG_ERR_ARG;
+  NvtxRange nv("ssamg_matrix_assemble");
   cudaStream_t st = (cudaStream_t)stream;
   API_BEGIN
   const ssamg_grid g = A->g;
@@ -1425,6 +1444,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
     Level& F = s->lev[l];
     Level& C = s->lev[l + 1];
     Level* N2 = l + 2 <= Lc ? &s->lev[l + 2] : nullptr;
+    NvtxRange nvl("ssamg setup level", l);
     const bool mark = N2 && F.nr > 0 && C.nr > 0;
     if (mark) {
       SSAMG_CUDA(cudaStreamWaitEvent(s->ss, s->ev_rows, 0));
@@ -1620,7 +1640,10 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   if (s->h_int[2]) throw SsamgError{SSAMG_ERR_BREAKDOWN, "coarsest operator is not positive definite"};
   // ---- coarse-level transition in one cluster (use_tail = 3)
   s->ctail_lt = -1;
-  if (s->prm.use_tail == 3) build_ctail(s, st);
+  if (s->prm.use_tail == 3) {
+    NvtxRange nvt("ssamg setup transition");
+    build_ctail(s, st);
+  }
 
   // ---- PCG work vectors (the ones the level-0 stencil reads carry guard cells)
   long long N = s->lev[0].N;
@@ -2036,6 +2059,7 @@ void run_setup(ssamg_solver s, cudaStream_t st) {
 }
 
 extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
+  NvtxRange nv("ssamg_setup");
   if (!s || !A) return SSAMG_ERR_ARG;
   if (!A->assembled) return SSAMG_ERR_STATE;
   API_BEGIN
@@ -2047,6 +2071,7 @@ extern "C" int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream) {
 
 extern "C" int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess,
                            void* stream, ssamg_stats* st) {
+  NvtxRange nv("ssamg_solve");
   if (!s || !b || !x || nrhs < 1) return SSAMG_ERR_ARG;
   if (!s->ready) return SSAMG_ERR_STATE;
   cudaStream_t cst = (cudaStream_t)stream;
@@ -2251,6 +2276,7 @@ extern "C" int ssamg_batch_create(int nprob, const ssamg_matrix* A, const ssamg_
 }
 
 extern "C" int ssamg_batch_setup(ssamg_batch B, void* stream) {
+  NvtxRange nv("ssamg_batch_setup");
   if (!B) return SSAMG_ERR_ARG;
   return ssamg_setup(B->s, B->A, stream);
 }
@@ -2265,6 +2291,7 @@ extern "C" int ssamg_batch_offsets(ssamg_batch B, long long* off) {
 
 extern "C" int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int nrhs, void* stream,
                                  ssamg_stats* st) {
+  NvtxRange nv("ssamg_batch_solve");
   if (!B || !b || !x || nrhs < 1) return SSAMG_ERR_ARG;
   ssamg_solver s = B->s;
   if (!s->ready) return SSAMG_ERR_STATE;
