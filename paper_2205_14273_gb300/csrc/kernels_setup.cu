@@ -431,12 +431,11 @@ __global__ void k_urows(int Nc, const int* __restrict__ scan, const int* __restr
 // of equal J is one entry of the row, its slot the number of runs before it
 // (columns ascending), its value the sum of the run's candidates in
 // generation order (t ascending), so the result does not depend on the
-// warp's schedule.  Two instances: UW = 128 candidates per warp and 8 warps
-// per block for the rows whose candidate bound 2 sum_f len(f) is at most
-// 128, UW = 1024 and 2 warps per block for the others (each instance skips
-// the other's rows).
+// warp's schedule.  Instantiated with UW = 128 candidates per warp and 8
+// warps per block for the rows whose candidate bound 2 sum_f len(f) is at
+// most 128; longer rows go to the block form (k_urow_blk).
 constexpr int UW_SMALL = 128, UWARPS_SMALL = 8;
-constexpr int UW_LARGE = 1024, UWARPS_LARGE = 2;
+constexpr int UW_LARGE = 1024;  // candidates of a row in the block form (k_urow_blk)
 
 __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total) {
   int x = v;
@@ -683,6 +682,167 @@ __global__ void __launch_bounds__(32 * WPB) k_urow(LevelView<double> F, int nrc,
     toff[R] = o0;
   }
   __syncwarp();
+  }
+}
+
+// Block-wide exclusive scan of one int per thread (NTB threads); total in
+// `total`.  All threads must call.
+template <int NTB>
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < NTB / 32 ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < NTB / 32) sh[lane] = t;  // inclusive warp-total prefix
+  }
+  __syncthreads();
+  total = sh[NTB / 32 - 1];
+  const int before = w > 0 ? sh[w - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// Rows of more than UW_SMALL candidates (up to UW_LARGE), a block of NTB
+// threads per row: the same candidates in the same generation order (the
+// positions by a block scan over the entries' candidate counts), the same
+// keys (J, t) sorted by a bitonic network over the whole block, the same
+// runs summed in generation order by their first thread: bitwise the warp
+// form's rows, with the sort's stages spread over NTB threads instead of 32.
+constexpr int UBLK = 256;
+__global__ void __launch_bounds__(UBLK) k_urow_blk(LevelView<double> F,
+                                                   const int* __restrict__ longrows,
+                                                   const int* __restrict__ fr,
+                                                   const double* __restrict__ frw,
+                                                   const int* __restrict__ pj,
+                                                   const double* __restrict__ pw,
+                                                   int* __restrict__ counts,
+                                                   int* __restrict__ toff,
+                                                   int* __restrict__ cursor,
+                                                   int* __restrict__ tcol,
+                                                   double* __restrict__ tval,
+                                                   unsigned char* __restrict__ tbits,
+                                                   int* __restrict__ err) {
+  __shared__ unsigned long long K[UW_LARGE];
+  __shared__ double V[UW_LARGE];
+  __shared__ unsigned char B[UW_LARGE];
+  __shared__ int sh[UBLK / 32];
+  __shared__ int s_o0;
+  const int tid = threadIdx.x;
+  const int nlist = *(volatile const int*)longrows;
+  for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+    const int R = longrows[1 + it];
+    int ur[3], q0[3], q1[3];
+    double w1[3];
+    for (int a = 0; a < 3; ++a) {
+      ur[a] = fr[3 * R + a];
+      w1[a] = ur[a] >= 0 ? frw[3 * R + a] : 0.0;
+      q0[a] = q1[a] = 0;
+      if (ur[a] >= 0) {
+        q0[a] = F.u_ptr[ur[a]];
+        q1[a] = F.u_ptr[ur[a] + 1];
+      }
+    }
+    int n = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (ur[a] < 0) continue;
+      for (int base = q0[a]; base < q1[a]; base += UBLK) {
+        const int q = base + tid;
+        int Jt[2] = {-1, -1};
+        double w2[2] = {0.0, 0.0};
+        double u = 0.0;
+        unsigned char b = 0;
+        if (q < q1[a]) {
+          Jt[0] = pj[2 * q];
+          Jt[1] = pj[2 * q + 1];
+          w2[0] = pw[2 * q];
+          w2[1] = pw[2 * q + 1];
+          u = F.u_val[q];
+          b = F.u_bits[q];
+        }
+        const int m = (Jt[0] >= 0) + (Jt[1] >= 0);
+        int tot;
+        int pos = n + block_excl_scan<UBLK>(m, sh, tot);
+        if (q < q1[a]) {
+          const double v = w1[a] * u;
+          for (int t = 0; t < 2; ++t)
+            if (Jt[t] >= 0) {
+              if (pos < UW_LARGE) {
+                K[pos] = ((unsigned long long)(unsigned)Jt[t] << 10) | (unsigned)pos;
+                V[pos] = v * w2[t];
+                B[pos] = b;
+              }
+              ++pos;
+            }
+        }
+        n += tot;
+      }
+    }
+    if (n > UW_LARGE) {
+      if (tid == 0) {
+        atomicOr(err, 1);
+        counts[R] = 0;
+        toff[R] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    int m = 32;
+    while (m < n) m <<= 1;
+    for (int t = n + tid; t < m; t += UBLK) K[t] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < m; i += UBLK) {
+          const int l = i ^ j;
+          if (l > i) {
+            const unsigned long long x = K[i], y = K[l];
+            if ((x > y) == ((i & k) == 0)) {
+              K[i] = y;
+              K[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (tid == 0) s_o0 = n ? atomicAdd(cursor, n) : 0;
+    __syncthreads();
+    const int o0 = s_o0;
+    int run = 0;
+    for (int base = 0; base < n; base += UBLK) {
+      const int i = base + tid;
+      const bool start = i < n && (i == 0 || (K[i] >> 10) != (K[i - 1] >> 10));
+      int tot;
+      const int slot = run + block_excl_scan<UBLK>(start ? 1 : 0, sh, tot);
+      if (start) {
+        const unsigned long long J = K[i] >> 10;
+        double v = 0.0;
+        unsigned char b = 0;
+        for (int u = i; u < n && (K[u] >> 10) == J; ++u) {
+          const int t = (int)(K[u] & 1023ull);
+          v += V[t];
+          b |= B[t];
+        }
+        tcol[o0 + slot] = (int)J;
+        tval[o0 + slot] = v;
+        tbits[o0 + slot] = b;
+      }
+      run += tot;
+    }
+    if (tid == 0) {
+      counts[R] = run;
+      toff[R] = o0;
+    }
+    __syncthreads();
   }
 }
 
@@ -1200,10 +1360,9 @@ void launch_usort(const Level& F, const Level& Cl, int* lists, const int* fr,
       F.view<double>(), Cl.nr, midrows, longrows, fr, frw, F.u_pj, F.u_pw, counts, t.toff,
       t.cursor, t.col, t.val, t.bits, err);
   SSAMG_LAUNCH_CHECK();
-  k_urow<UW_LARGE, UWARPS_LARGE><<<std::min(cdiv(Cl.nr, UWARPS_LARGE), 4 * sms),
-                                   32 * UWARPS_LARGE, 0, st>>>(
-      F.view<double>(), Cl.nr, midrows, longrows, fr, frw, F.u_pj, F.u_pw, counts, t.toff,
-      t.cursor, t.col, t.val, t.bits, err);
+k_urow_blk<<<std::min(Cl.nr, 2 * sms), UBLK, 0, st>>>(F.view<double>(), longrows, fr, frw,
+                                                        F.u_pj, F.u_pw, counts, t.toff, t.cursor,
+                                                        t.col, t.val, t.bits, err);
   SSAMG_LAUNCH_CHECK();
 }
 
