@@ -234,8 +234,13 @@ struct ssamg_matrix_s {
   std::vector<std::vector<double*>> tmpvar;   // device values set but not yet packed
   std::vector<std::vector<char>> isset, isvar;
   // couplings (host, appended)
-  std::vector<int> c_part, c_idx, c_dir, c_npart, c_nidx;
+  // couplings as added: global row and column cell, direction bits (bit 2d:
+  // +d, 2d+1: -d), value; and per part 1 / 2 once a row lies on a face /
+  // inside the box
+  std::vector<int> c_row, c_col;
+  std::vector<unsigned char> c_bits;
   std::vector<double> c_val;
+  std::vector<char> c_hasu;
   // assembled (device)
   bool assembled = false;
   double* coef = nullptr;
@@ -580,24 +585,84 @@ extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int
   if (n == 0) return SSAMG_OK;
   if (!part || !idx || !dir || !nbor_part || !nbor_idx || !vals) return SSAMG_ERR_ARG;
   const ssamg_grid g = A->g;
-  for (long long t = 0; t < n; ++t) {
-    int p = part[t], q = nbor_part[t];
-    if (p < 0 || p >= g->nparts || q < 0 || q >= g->nparts || p == q) return SSAMG_ERR_ARG;
+  const int np = g->nparts;
+  // validated and converted in one pass into the tail; a rejected call
+  // leaves the matrix as it was
+  const size_t m0 = A->c_val.size();
+  A->c_row.resize(m0 + n);
+  A->c_col.resize(m0 + n);
+  A->c_bits.resize(m0 + n);
+  A->c_val.resize(m0 + n);
+  std::vector<char> hasu(A->c_hasu);
+  hasu.resize(np, 0);
+  // the parts' boxes and first cells in local arrays (the loop's stores do
+  // not alias them)
+  std::vector<int> lo(3 * np), hi(3 * np);
+  std::vector<long long> off(np);
+  for (int p = 0; p < np; ++p) {
     for (int d = 0; d < 3; ++d) {
-      int a = idx[3 * t + d], b = nbor_idx[3 * t + d];
-      if (a < g->lo[p][d] || a > g->hi[p][d] || b < g->lo[q][d] || b > g->hi[q][d]) return SSAMG_ERR_ARG;
-      int dv = dir[3 * t + d];
-      if (dv < -1 || dv > 1) return SSAMG_ERR_ARG;
-      if (dv > 0 && a != g->hi[p][d]) return SSAMG_ERR_ARG;
-      if (dv < 0 && a != g->lo[p][d]) return SSAMG_ERR_ARG;
+      lo[3 * p + d] = g->lo[p][d];
+      hi[3 * p + d] = g->hi[p][d];
     }
+    off[p] = g->off[p];
   }
-  A->c_part.insert(A->c_part.end(), part, part + n);
-  A->c_npart.insert(A->c_npart.end(), nbor_part, nbor_part + n);
-  A->c_idx.insert(A->c_idx.end(), idx, idx + 3 * n);
-  A->c_nidx.insert(A->c_nidx.end(), nbor_idx, nbor_idx + 3 * n);
-  A->c_dir.insert(A->c_dir.end(), dir, dir + 3 * n);
-  A->c_val.insert(A->c_val.end(), vals, vals + n);
+  const int ndim = g->ndim;
+  const int* LO = lo.data();
+  const int* HI = hi.data();
+  const long long* OFF = off.data();
+  int* crow = A->c_row.data() + m0;
+  int* ccol = A->c_col.data() + m0;
+  unsigned char* cbits = A->c_bits.data() + m0;
+  double* cval = A->c_val.data() + m0;
+  char* hu = hasu.data();
+  auto gidx = [&](int p, const int* c) {
+    const int* l = LO + 3 * p;
+    const int* h = HI + 3 * p;
+    const long long nx = h[0] - l[0] + 1, ny = h[1] - l[1] + 1;
+    return OFF[p] + ((long long)(c[2] - l[2]) * ny + (c[1] - l[1])) * nx + (c[0] - l[0]);
+  };
+  bool ok = true;
+  for (long long t = 0; t < n; ++t) {
+    const int p = part[t], q = nbor_part[t];
+    if (p < 0 || p >= np || q < 0 || q >= np || p == q) {
+      ok = false;
+      break;
+    }
+    const int* a = idx + 3 * t;
+    const int* b = nbor_idx + 3 * t;
+    const int* dv = dir + 3 * t;
+    const int* lp = LO + 3 * p;
+    const int* hp = HI + 3 * p;
+    const int* lq = LO + 3 * q;
+    const int* hq = HI + 3 * q;
+    unsigned bt = 0;
+    bool face = false, bad = false;
+    for (int d = 0; d < 3; ++d) {
+      bad |= a[d] < lp[d] || a[d] > hp[d] || b[d] < lq[d] || b[d] > hq[d] || dv[d] < -1 ||
+             dv[d] > 1 || (dv[d] > 0 && a[d] != hp[d]) || (dv[d] < 0 && a[d] != lp[d]);
+      bt |= (dv[d] > 0 ? 1u << (2 * d) : 0u) | (dv[d] < 0 ? 1u << (2 * d + 1) : 0u);
+      face |= d < ndim && (a[d] == lp[d] || a[d] == hp[d]);
+    }
+    if (bad) {
+      ok = false;
+      break;
+    }
+    crow[t] = (int)gidx(p, a);
+    ccol[t] = (int)gidx(q, b);
+    cbits[t] = (unsigned char)bt;
+    cval[t] = vals[t];
+    // 2 when a row lies inside the box (no face of an active dimension)
+    const char hv = face ? 1 : 2;
+    if (hu[p] < hv) hu[p] = hv;
+  }
+  if (!ok) {
+    A->c_row.resize(m0);
+    A->c_col.resize(m0);
+    A->c_bits.resize(m0);
+    A->c_val.resize(m0);
+    return SSAMG_ERR_ARG;
+  }
+  A->c_hasu.swap(hasu);
   A->assembled = false;
   return SSAMG_OK;
 }
@@ -657,41 +722,18 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
   // input order) on the device
   const long long m = (long long)A->c_val.size();
   A->has_u.assign(np, 0);
+  for (int p = 0; p < np && p < (int)A->c_hasu.size(); ++p) A->has_u[p] = A->c_hasu[p];
   A->nr = 0;
   A->nnz = 0;
   if (m > 0) {
-    std::vector<int> crow((size_t)m), ccol((size_t)m);
-    std::vector<unsigned char> cbits((size_t)m);
-    auto gidx = [&](int p, const int* c) {
-      long long nx = g->hi[p][0] - g->lo[p][0] + 1, ny = g->hi[p][1] - g->lo[p][1] + 1;
-      return g->off[p] + ((long long)(c[2] - g->lo[p][2]) * ny + (c[1] - g->lo[p][1])) * nx +
-             (c[0] - g->lo[p][0]);
-    };
-    for (long long t = 0; t < m; ++t) {
-      const int p = A->c_part[t];
-      const int* c = &A->c_idx[3 * t];
-      crow[t] = (int)gidx(p, c);
-      ccol[t] = (int)gidx(A->c_npart[t], &A->c_nidx[3 * t]);
-      unsigned char bt = 0;
-      bool face = false;
-      for (int d = 0; d < 3; ++d) {
-        const int dv = A->c_dir[3 * t + d];
-        if (dv > 0) bt |= (unsigned char)(1u << (2 * d));
-        if (dv < 0) bt |= (unsigned char)(1u << (2 * d + 1));
-        if (d < g->ndim && (c[d] == g->lo[p][d] || c[d] == g->hi[p][d])) face = true;
-      }
-      cbits[t] = bt;
-      // 2 when a row lies inside the box (no face of an active dimension)
-      A->has_u[p] = std::max<char>(A->has_u[p], face ? 1 : 2);
-    }
     int* drow = pool_new<int>(m);
     int* dcol = pool_new<int>(m);
     double* dval = pool_new<double>(m);
     unsigned char* dbits = pool_new<unsigned char>(m);
-    SSAMG_CUDA(cudaMemcpyAsync(drow, crow.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(dcol, ccol.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(drow, A->c_row.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(dcol, A->c_col.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
     SSAMG_CUDA(cudaMemcpyAsync(dval, A->c_val.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
-    SSAMG_CUDA(cudaMemcpyAsync(dbits, cbits.data(), m, cudaMemcpyHostToDevice, st));
+    SSAMG_CUDA(cudaMemcpyAsync(dbits, A->c_bits.data(), m, cudaMemcpyHostToDevice, st));
     // outputs sized by the bound m (the row and entry counts come back below)
     A->u_rows = pool_new<int>(m);
     A->u_ptr = pool_new<int>(m + 1);
@@ -2257,13 +2299,22 @@ extern "C" int ssamg_batch_create(int nprob, const ssamg_matrix* A, const ssamg_
         else
           check(ssamg_matrix_set_constant(B->A, P, e, M->cval[q][e]));
       }
+    // couplings: the problem's cells shifted by its first cell in the union
     const long long nc = (long long)M->c_val.size();
     if (nc > 0) {
-      std::vector<int> pp(M->c_part), np_(M->c_npart);
-      for (auto& v : pp) v += P - M->g->nparts;
-      for (auto& v : np_) v += P - M->g->nparts;
-      check(ssamg_matrix_add_couplings(B->A, nc, pp.data(), M->c_idx.data(), M->c_dir.data(),
-                                       np_.data(), M->c_nidx.data(), M->c_val.data()));
+      ssamg_matrix U = B->A;
+      const int shift = (int)B->off[k];
+      for (long long t = 0; t < nc; ++t) {
+        U->c_row.push_back(M->c_row[t] + shift);
+        U->c_col.push_back(M->c_col[t] + shift);
+      }
+      U->c_bits.insert(U->c_bits.end(), M->c_bits.begin(), M->c_bits.end());
+      U->c_val.insert(U->c_val.end(), M->c_val.begin(), M->c_val.end());
+      U->c_hasu.resize(B->g->nparts, 0);
+      const int p0 = P - M->g->nparts;
+      for (int q = 0; q < M->g->nparts && q < (int)M->c_hasu.size(); ++q)
+        U->c_hasu[p0 + q] = std::max(U->c_hasu[p0 + q], M->c_hasu[q]);
+      U->assembled = false;
     }
   }
   check(ssamg_matrix_assemble(B->A, stream));
