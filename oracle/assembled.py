@@ -50,8 +50,18 @@ class Numbering:
         return self.start[p] + ((c[2] - lo[2]) * ny + (c[1] - lo[1])) * nx + (c[0] - lo[0])
 
 
+def _in_part(prob, p, c):
+    """Cell c of part p's bounding box belongs to the part (one of its boxes)."""
+    boxes = prob.part_boxes[p] if getattr(prob, "part_boxes", None) else None
+    if boxes is None:
+        return True
+    return any(all(lo[d] <= c[d] <= hi[d] for d in range(3)) for lo, hi in boxes)
+
+
 def assemble_problem(prob):
-    """A = S + U of a problems.Problem as CSR, by loops over cells and entries."""
+    """A = S + U of a problems.Problem as CSR, by loops over cells and entries
+    (a part of several boxes over its bounding box: cells outside the boxes
+    are rows of the identity, connections to them are dropped)."""
     num = Numbering([b[0] for b in prob.boxes], [b[1] for b in prob.boxes])
     rows, cols, vals = [], [], []
     for p in range(prob.nparts):
@@ -60,9 +70,14 @@ def assemble_problem(prob):
         ny = hi[1] - lo[1] + 1
         for c in _cells(lo, hi):
             loc = (c[0] - lo[0], c[1] - lo[1], c[2] - lo[2])
+            if not _in_part(prob, p, c):
+                rows.append(num.index(p, c))
+                cols.append(num.index(p, c))
+                vals.append(1.0)
+                continue
             for e, o in enumerate(prob.offsets):
                 nb = (c[0] + int(o[0]), c[1] + int(o[1]), c[2] + int(o[2]))
-                if not num.inside(p, nb):
+                if not num.inside(p, nb) or not _in_part(prob, p, nb):
                     continue
                 co = prob.coef[p][e]
                 v = float(co) if np.isscalar(co) else float(co[loc[2], loc[1], loc[0]])
@@ -160,9 +175,9 @@ def prolongation_brute(A, num, dstar, coarse_lo, coarse_hi, bits):
             pw, pe = -sw / den, -se / den
         else:
             pw = pe = 0.0
-        if c[d] == num.his[p][d] and (bits[g] >> (2 * d)) & 1:
+        if (bits[g] >> (2 * d)) & 1:
             pw, pe = 1.0, 0.0
-        if c[d] == num.los[p][d] and (bits[g] >> (2 * d + 1)) & 1:
+        if (bits[g] >> (2 * d + 1)) & 1:
             pw, pe = 0.0, 1.0
         for J_d, w in (((c[d] - 1) // 2, pw), ((c[d] + 1) // 2, pe)):
             if coarse_lo[p][d] <= J_d <= coarse_hi[p][d]:

@@ -3,8 +3,10 @@
 Conventions (the readings of the paper this oracle takes):
 
 * Grid (Section 2): part p is one box [lo, hi] (inclusive, absolute indices
-  in the part's own index space).  Arrays are indexed [k, j, i]; vectors are
-  part-major with i fastest.
+  in the part's own index space), or a group of boxes held over their
+  bounding box [lo, hi] with the cells outside them decoupled (diagonal 1,
+  no connections).  Arrays are indexed [k, j, i]; vectors are part-major
+  with i fastest.
 * S (Section 2): S(c, c+o) = a_o(c) when c+o lies inside the part box, zero
   otherwise (physical boundaries are eliminated; connections across parts
   live in U).
@@ -17,9 +19,10 @@ Conventions (the readings of the paper this oracle takes):
 * Interpolation sign (Eq. prolEx, printed without a minus sign): P_W =
   -(sum of the -1 plane) / (sum of the centre plane), P_E likewise, which
   gives weights in [0, 1] for M-matrices.
-* Part-boundary fix (Section 3.2): a fine point whose neighbour along +-d* is
-  outside the box and whose U row carries the matching direction bit gets 0
-  on that side and 1 on the other side (row sum one).
+* Part-boundary fix (Section 3.2): a fine point whose U row carries the
+  direction bit +d* (-d*), i.e. whose neighbour that way lies outside its
+  part and across a coupled part boundary, gets 0 on that side and 1 on the
+  other side (row sum one).
 * Coarsening stop (Section 3.1): the coarsest level is the first whose total
   size is <= s_max, or level l_max - 1, or the first with every part at one
   cell.
@@ -176,20 +179,49 @@ def _unit(d, s=1):
 # Level 0 from a problem description (Section 2: A = S + U)
 # ---------------------------------------------------------------------------
 
+def part_active(prob, p, shp) -> np.ndarray:
+    """Cells of part p's bounding box that belong to the part (Section 2: a
+    part is a group of boxes); all of them for a one-box part."""
+    boxes = prob.part_boxes[p] if getattr(prob, "part_boxes", None) else None
+    m = np.zeros(shp, bool)
+    if boxes is None:
+        m[...] = True
+        return m
+    lo = prob.boxes[p][0]
+    zz, yy, xx = np.meshgrid(*(np.arange(n) + l for n, l in zip(shp, (lo[2], lo[1], lo[0]))),
+                             indexing="ij")
+    for blo, bhi in boxes:
+        m |= ((xx >= blo[0]) & (xx <= bhi[0]) & (yy >= blo[1]) & (yy <= bhi[1]) &
+              (zz >= blo[2]) & (zz <= bhi[2]))
+    return m
+
+
 def level0_from_problem(prob) -> Level:
-    """S with out-of-box connections dropped, U with duplicates summed."""
+    """S with out-of-box connections dropped, U with duplicates summed.
+
+    A part of several boxes is held over its bounding box: connections from
+    or to a cell outside its boxes are dropped and such a cell is a decoupled
+    unknown (diagonal 1), as the paper's ghost unknowns (Section 4, test case
+    4); stencil connections between the part's boxes stay (interpolation
+    within a part crosses its box faces)."""
     lo = [np.array(b[0], np.int64) for b in prob.boxes]
     hi = [np.array(b[1], np.int64) for b in prob.boxes]
     S = []
     for p in range(prob.nparts):
         e = hi[p] - lo[p] + 1
         shp = (int(e[2]), int(e[1]), int(e[0]))
+        act = part_active(prob, p, shp)
         sp = {}
         for ei, o in enumerate(prob.offsets):
             o = tuple(int(v) for v in o)
             c = prob.coef[p][ei]
             arr = np.full(shp, float(c)) if np.isscalar(c) else np.array(c, np.float64).reshape(shp)
             arr = np.where(_inside_mask(shp, o), arr, 0.0)
+            if not act.all():
+                if o == (0, 0, 0):
+                    arr = np.where(act, arr, 1.0)
+                else:
+                    arr = np.where(act & _shift(act, o), arr, 0.0)
             sp[o] = sp.get(o, 0.0) + arr
         S.append(sp)
     lev = Level(prob.ndim, lo, hi, S)
@@ -412,11 +444,12 @@ def interpolation(lev: Level, p: int, d: int):
     bshape = [1, 1, 1]
     bshape[ax] = shp[ax]
     fine = np.broadcast_to((idx % 2 == 1).reshape(bshape), shp)
-    at_lo = np.broadcast_to((idx == lev.lo[p][d]).reshape(bshape), shp)
-    at_hi = np.broadcast_to((idx == lev.hi[p][d]).reshape(bshape), shp)
     bits = _face_bits(lev, p)
-    cross_e = fine & at_hi & ((bits >> (2 * d)) & 1).astype(bool)
-    cross_w = fine & at_lo & ((bits >> (2 * d + 1)) & 1).astype(bool)
+    # a row's bit +d (-d) says that it leaves its part through +d (-d): on
+    # the box face for a one-box part, also beside a hole for a part of
+    # several boxes
+    cross_e = fine & ((bits >> (2 * d)) & 1).astype(bool)
+    cross_w = fine & ((bits >> (2 * d + 1)) & 1).astype(bool)
     PE = np.where(cross_e, 0.0, PE)
     PW = np.where(cross_e, 1.0, PW)
     PW = np.where(cross_w, 0.0, PW)

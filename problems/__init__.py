@@ -28,6 +28,8 @@ targets:
                   rotated index maps (test case 3, non-Cartesian)
   samr            a coarse part with ghost unknowns under a refined patch of
                   twice the resolution (test case 4, SAMR)
+  multibox        an L-shaped part of two boxes around a cube part filling
+                  its notch (a part of several boxes, Section 2)
 """
 from __future__ import annotations
 
@@ -123,6 +125,12 @@ class Problem:
     b: np.ndarray
     name: str = ""
     extra: dict = field(default_factory=dict)
+    # parts made of several boxes (Section 2): part_boxes[p] lists the boxes
+    # (lo, hi) of part p, boxes[p] being their bounding box; None (or None
+    # for a part) means the part is its bounding box.  Coefficient arrays and
+    # right-hand sides cover the bounding box; cells outside the part's boxes
+    # carry no connections (their values are ignored).
+    part_boxes: Optional[List[Optional[List[Tuple[Tuple[int, int, int], Tuple[int, int, int]]]]]] = None
 
     @property
     def nparts(self) -> int:
@@ -508,6 +516,69 @@ def samr(m: int = 128, seed: int = 6, nrhs: int = 1, cf: float = 2.0 / 3.0) -> P
                    np.concatenate(ud).astype(np.int32), np.concatenate(uq).astype(np.int32),
                    np.concatenate(uj).astype(np.int32), np.full(nu, -cf), b,
                    name=f"samr 2x{m}^3", extra={"ghost": ghost})
+
+
+def box_mask(shape_zyx, lo, boxes) -> np.ndarray:
+    """Cells of a bounding box (shape (nz, ny, nx), corner lo) that lie in
+    any of `boxes`."""
+    nz, ny, nx = shape_zyx
+    zz, yy, xx = np.meshgrid(np.arange(nz) + lo[2], np.arange(ny) + lo[1],
+                             np.arange(nx) + lo[0], indexing="ij")
+    m = np.zeros(shape_zyx, bool)
+    for blo, bhi in boxes:
+        m |= ((xx >= blo[0]) & (xx <= bhi[0]) & (yy >= blo[1]) & (yy <= bhi[1]) &
+              (zz >= blo[2]) & (zz <= bhi[2]))
+    return m
+
+
+def multibox(m: int = 64, seed: int = 7, nrhs: int = 1) -> Problem:
+    """Two parts (Section 2, a part of several boxes, as Part 4 of Fig. ssgrid).
+
+    Part 0 is L-shaped: boxes [0, 2m-1] x [0, m-1] x [0, m-1] and
+    [0, m-1] x [m, 2m-1] x [0, m-1], bounding box [0, 2m-1]^2 x [0, m-1]; its
+    notch [m, 2m-1]^2 x [0, m-1] is filled by part 1, [0, m-1]^3 in its own
+    index space (cell (i, j, k) of part 1 sits at (m + i, m + j, k) of part
+    0's index space).  Both parts carry the 7-point Laplacian (6, -1 x 6)
+    between cells of the same part; facing cells of the two parts are coupled
+    by -1 both ways, the rows of part 0 leaving it through +x (the notch's
+    west face) or +y (its south face) from inside its bounding box.  Other
+    faces are Dirichlet: the diagonal stays 6.
+    """
+    rng = SplitMix64(seed)
+    b0 = [((0, 0, 0), (2 * m - 1, m - 1, m - 1)), ((0, m, 0), (m - 1, 2 * m - 1, m - 1))]
+    boxes = [((0, 0, 0), (2 * m - 1, 2 * m - 1, m - 1)), ((0, 0, 0), (m - 1, m - 1, m - 1))]
+    up, ui, ud, uq, uj = [], [], [], [], []
+    t, k = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    t, k = t.ravel(), k.ravel()
+    cnt = m * m
+    for d in (0, 1):
+        # part 0 cells just outside the notch along d, part 1's cells on its face
+        c0 = np.zeros((cnt, 3), np.int64)
+        c0[:, d] = m - 1
+        c0[:, 1 - d] = m + t
+        c0[:, 2] = k
+        c1 = np.zeros((cnt, 3), np.int64)
+        c1[:, d] = 0
+        c1[:, 1 - d] = t
+        c1[:, 2] = k
+        dv = np.zeros((cnt, 3), np.int64)
+        dv[:, d] = 1
+        up += [np.zeros(cnt), np.ones(cnt)]
+        ui += [c0, c1]
+        ud += [dv, -dv]
+        uq += [np.ones(cnt), np.zeros(cnt)]
+        uj += [c1, c0]
+    N0 = 4 * m ** 3
+    N = N0 + m ** 3
+    b = rng.uniform_pm1(nrhs * N).reshape(nrhs, N)
+    act = box_mask((m, 2 * m, 2 * m), (0, 0, 0), b0).ravel()
+    b[:, :N0] *= act
+    coef = [[6.0] + [-1.0] * 6, [6.0] + [-1.0] * 6]
+    return Problem(3, boxes, STENCIL7.copy(), coef,
+                   np.concatenate(up).astype(np.int32), np.concatenate(ui).astype(np.int32),
+                   np.concatenate(ud).astype(np.int32), np.concatenate(uq).astype(np.int32),
+                   np.concatenate(uj).astype(np.int32), np.full(4 * cnt, -1.0), b,
+                   name=f"multibox L(2 boxes)+{m}^3", part_boxes=[b0, None])
 
 
 def config(k: int, small: bool = False) -> Union[Problem, List[Problem]]:

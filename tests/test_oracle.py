@@ -78,6 +78,7 @@ def small_problems():
     out.append(shifted(chain([4, 6], [[1, .01, .01], [1, .02, .03]]), [(1, 0, 0), (-1, 3, 1)]))
     out.append(P.three_point(4))   # test case 3: rotated index maps between parts
     out.append(P.samr(4))          # test case 4: ghost unknowns, couplings inside a box
+    out.append(P.multibox(4))      # a part of two boxes (L shape) around a cube part
     return out
 
 
@@ -717,3 +718,102 @@ def test_user_spacings_infinite_dimension_is_coarsened_last():
     assert ds[:first_y] == [0, 2, 0, 2, 0, 2]
     with pytest.raises(ValueError):
         O.setup(prob, O.Params(spacings=np.array([[1.0, 0.0, 1.0]])))
+
+
+# ---------------------------------------------------------------------------
+# Parts of several boxes (Section 2), held over their bounding box
+# ---------------------------------------------------------------------------
+
+def test_boxes_tiling_their_bounding_box_give_the_one_box_hierarchy():
+    """Two boxes that tile a cube are the cube: every operator of every level
+    equals the one-box problem's (the stencil connects the boxes of a part)."""
+    import dataclasses
+    one = P.laplace7(6)
+    two = dataclasses.replace(one, part_boxes=[[((0, 0, 0), (2, 5, 5)), ((3, 0, 0), (5, 5, 5))]])
+    h1, h2 = O.setup(one), O.setup(two)
+    assert len(h1.levels) == len(h2.levels)
+    for a, b in zip(h1.levels, h2.levels):
+        assert a.dstar == b.dstar
+        for o in a.S[0]:
+            assert np.array_equal(a.S[0][o], b.S[0][o])
+    assert np.array_equal(O.pcg(h1, one.b[0], tol=1e-10).x, O.pcg(h2, two.b[0], tol=1e-10).x)
+
+
+def _multibox_true_system(prob):
+    """The L-shaped problem over its parts' own cells only (no bounding box):
+    the 7-point Laplacian between cells of the same part, the couplings of
+    the problem, Dirichlet elsewhere; returned with the map to the bounding-box
+    numbering."""
+    import scipy.sparse as sp
+    nz, ny, nx = prob.shape(0)
+    act0 = P.box_mask((nz, ny, nx), prob.boxes[0][0], prob.part_boxes[0]).ravel()
+    n0 = act0.size
+    n1 = int(np.prod(prob.shape(1)))
+    full = np.concatenate([np.flatnonzero(act0), n0 + np.arange(n1)])
+    pos = -np.ones(n0 + n1, np.int64)
+    pos[full] = np.arange(full.size)
+    rows, cols, vals = [], [], []
+
+    def cell(p, i, j, k):
+        if p == 0:
+            return (k * ny + j) * nx + i if 0 <= i < nx and 0 <= j < ny and 0 <= k < nz and act0[(k * ny + j) * nx + i] else -1
+        m = prob.shape(1)[0]
+        return n0 + (k * m + j) * m + i if all(0 <= v < m for v in (i, j, k)) else -1
+
+    for p, (dims) in ((0, (nx, ny, nz)), (1, prob.shape(1)[::-1])):
+        for k in range(dims[2]):
+            for j in range(dims[1]):
+                for i in range(dims[0]):
+                    g = cell(p, i, j, k)
+                    if g < 0:
+                        continue
+                    rows.append(pos[g]); cols.append(pos[g]); vals.append(6.0)
+                    for o in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                        h = cell(p, i + o[0], j + o[1], k + o[2])
+                        if h >= 0:
+                            rows.append(pos[g]); cols.append(pos[h]); vals.append(-1.0)
+    for t in range(prob.nnz_u):
+        a = cell(int(prob.u_part[t]), *prob.u_idx[t])
+        b = cell(int(prob.u_nbor_part[t]), *prob.u_nbor_idx[t])
+        rows.append(pos[a]); cols.append(pos[b]); vals.append(float(prob.u_val[t]))
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(full.size, full.size))
+    return A, full
+
+
+def test_multibox_solution_is_the_true_systems():
+    """The bounding-box form solves the same system on the part's cells: the
+    oracle's PCG matches a sparse LU solve of the L-shaped problem assembled
+    over the parts' own cells only; the cells of the notch stay ~0."""
+    import scipy.sparse.linalg as sla
+    prob = P.multibox(4)
+    A, full = _multibox_true_system(prob)
+    assert abs(A - A.T).max() == 0.0
+    xs = sla.spsolve(A.tocsc(), prob.b[0][full])
+    h = O.setup(prob)
+    res = O.pcg(h, prob.b[0], tol=1e-13, max_iter=300)
+    assert res.converged
+    assert np.linalg.norm(res.x[full] - xs) / np.linalg.norm(xs) <= 1e-11
+    hole = np.setdiff1d(np.arange(prob.n), full)
+    assert np.abs(res.x[hole]).max() <= 1e-12
+
+
+def test_multibox_fix_beside_the_notch():
+    """Interpolation stays inside the part: the fine points of part 0 whose
+    +x neighbour is in the notch (coupled to part 1) get (PW, PE) = (1, 0)
+    (Section 3.2), while the fine points between its two boxes keep the
+    stencil weights (1/2, 1/2 for the isotropic Laplacian away from faces)."""
+    m = 4
+    prob = P.multibox(m)
+    h = O.setup(prob)
+    lev = h.levels[0]
+    assert lev.dstar[0] == 0
+    PW, PE = O.interpolation(lev, 0, 0)
+    x = m - 1                         # odd: a fine point along x
+    for y in range(m, 2 * m):
+        for k in range(m):
+            assert PW[k, y, x] == 1.0 and PE[k, y, x] == 0.0
+    # x = 1, y = m - 1 (box A) and y = m (box B) are interior along x and y
+    # apart from the z faces: k = 1..m-2
+    for y in (m - 1, m):
+        for k in range(1, m - 1):
+            assert PW[k, y, 1] == 0.5 and PE[k, y, 1] == 0.5
