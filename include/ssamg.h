@@ -65,6 +65,17 @@ long long ssamg_release_device_cache(void);
 int ssamg_grid_create(int ndim, int nparts, ssamg_grid* out);
 /* Inclusive lower and upper corners of the box of `part` (3 ints each). */
 int ssamg_grid_set_box(ssamg_grid g, int part, const int lo[3], const int hi[3]);
+/* Another box of `part` (after its ssamg_grid_set_box; Section 2: a part is
+ * a group of boxes in one index space, at most 16).  The part is held over
+ * the bounding box of its boxes: vectors and coefficient arrays of the part
+ * cover the bounding box (i fastest); cells outside the boxes are decoupled
+ * unknowns (diagonal 1, no stencil connection into or out of them, values
+ * given for them ignored), so the solution there is the right-hand side's
+ * value and every other cell is solved exactly as the group of boxes.
+ * Stencil connections between the part's boxes are kept (interpolation
+ * crosses them).  SSAMG_ERR_ARG for a box with hi < lo, before set_box or
+ * after assemble; SSAMG_ERR_UNSUPPORTED beyond 16 boxes or 2^30 cells. */
+int ssamg_grid_add_box(ssamg_grid g, int part, const int lo[3], const int hi[3]);
 /* Checks that every part has a non-empty box; freezes the grid. */
 int ssamg_grid_assemble(ssamg_grid g);
 /* Total number of cells (valid after assemble), or -1. */
@@ -93,9 +104,11 @@ int ssamg_matrix_set_box_values(ssamg_matrix A, int part, int entry, const doubl
  * cell leaves its part toward the column (one component +-1 for a face
  * coupling; 0,0,0 for a non-geometric one); it marks the part boundaries that
  * interpolation must not cross (Section 3.2).  A row with a nonzero dir
- * lies on the faces it names; a row with dir 0,0,0 may lie anywhere in its
- * box (e.g. beside ghost unknowns under a refined patch, Section 4 test case
- * 4).  Columns lie in a different part.  Duplicates are summed. */
+ * leaves its part that way: the neighbour through dir lies outside the part
+ * (outside its box, or outside the boxes of a part of several); a row with
+ * dir 0,0,0 may lie anywhere in its part (e.g. beside ghost unknowns under a
+ * refined patch, Section 4 test case 4).  Rows and columns lie in their
+ * parts' boxes, columns in a different part.  Duplicates are summed. */
 int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int* part, const int* idx,
                                const int* dir, const int* nbor_part, const int* nbor_idx,
                                const double* vals);

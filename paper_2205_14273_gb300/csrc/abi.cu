@@ -214,8 +214,24 @@ void Arena::release() {
 // ---------------------------------------------------------------------------
 struct ssamg_grid_s {
   int ndim = 3, nparts = 0;
-  std::vector<std::array<int, 3>> lo, hi;
+  std::vector<std::array<int, 3>> lo, hi;  // each part's (bounding) box
   std::vector<char> set;
+  // a part of several boxes (Section 2): its boxes (lo, hi), empty for a
+  // one-box part; the part is held over their bounding box lo..hi
+  std::vector<std::vector<std::array<int, 6>>> boxes;
+  bool in_part(int p, const int* c) const {
+    if (boxes[p].empty()) return true;
+    for (const auto& b : boxes[p])
+      if (c[0] >= b[0] && c[0] <= b[3] && c[1] >= b[1] && c[1] <= b[4] && c[2] >= b[2] &&
+          c[2] <= b[5])
+        return true;
+    return false;
+  }
+  bool in_box(int p, const int* c) const {
+    for (int d = 0; d < 3; ++d)
+      if (c[d] < lo[p][d] || c[d] > hi[p][d]) return false;
+    return true;
+  }
   bool assembled = false;
   std::vector<long long> off;  // nparts + 1
   long long N = 0;
@@ -473,6 +489,7 @@ extern "C" int ssamg_grid_create(int ndim, int nparts, ssamg_grid* out) {
   g->lo.assign(nparts, {0, 0, 0});
   g->hi.assign(nparts, {0, 0, 0});
   g->set.assign(nparts, 0);
+  g->boxes.assign(nparts, {});
   *out = g;
   return SSAMG_OK;
 }
@@ -492,6 +509,32 @@ extern "C" int ssamg_grid_set_box(ssamg_grid g, int part, const int lo[3], const
     g->hi[part][d] = hi[d];
   }
   g->set[part] = 1;
+  g->boxes[part].clear();
+  return SSAMG_OK;
+}
+
+extern "C" int ssamg_grid_add_box(ssamg_grid g, int part, const int lo[3], const int hi[3]) {
+  if (!g || g->assembled) return g ? SSAMG_ERR_STATE : SSAMG_ERR_ARG;
+  if (part < 0 || part >= g->nparts || !lo || !hi || !g->set[part]) return SSAMG_ERR_ARG;
+  if ((int)g->boxes[part].size() >= SSAMG_MAX_PART_BOXES) return SSAMG_ERR_UNSUPPORTED;
+  for (int d = 0; d < 3; ++d) {
+    if (hi[d] < lo[d]) return SSAMG_ERR_ARG;
+    if (d >= g->ndim && (lo[d] != g->lo[part][d] || hi[d] != g->hi[part][d])) return SSAMG_ERR_ARG;
+  }
+  std::array<int, 3> nlo = g->lo[part], nhi = g->hi[part];
+  for (int d = 0; d < 3; ++d) {
+    nlo[d] = std::min(nlo[d], lo[d]);
+    nhi[d] = std::max(nhi[d], hi[d]);
+  }
+  long long n = 1;
+  for (int d = 0; d < 3; ++d) n *= (long long)nhi[d] - nlo[d] + 1;
+  if (n > (1ll << 30)) return SSAMG_ERR_UNSUPPORTED;
+  if (g->boxes[part].empty())  // the box given by set_box is the first
+    g->boxes[part].push_back({g->lo[part][0], g->lo[part][1], g->lo[part][2], g->hi[part][0],
+                              g->hi[part][1], g->hi[part][2]});
+  g->boxes[part].push_back({lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]});
+  g->lo[part] = nlo;
+  g->hi[part] = nhi;
   return SSAMG_OK;
 }
 
@@ -639,9 +682,20 @@ extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int
     bool face = false, bad = false;
     for (int d = 0; d < 3; ++d) {
       bad |= a[d] < lp[d] || a[d] > hp[d] || b[d] < lq[d] || b[d] > hq[d] || dv[d] < -1 ||
-             dv[d] > 1 || (dv[d] > 0 && a[d] != hp[d]) || (dv[d] < 0 && a[d] != lp[d]);
+             dv[d] > 1;
       bt |= (dv[d] > 0 ? 1u << (2 * d) : 0u) | (dv[d] < 0 ? 1u << (2 * d + 1) : 0u);
       face |= d < ndim && (a[d] == lp[d] || a[d] == hp[d]);
+    }
+    if (!bad) {
+      // a nonzero direction leaves the row's part: the neighbour that way
+      // lies outside its box, or outside the boxes of a part of several
+      for (int d = 0; d < 3 && !bad; ++d) {
+        if (dv[d] == 0) continue;
+        int nb[3] = {a[0], a[1], a[2]};
+        nb[d] += dv[d];
+        bad = g->in_box(p, nb) && g->in_part(p, nb);
+      }
+      bad = bad || !g->in_part(p, a) || !g->in_part(q, b);
     }
     if (bad) {
       ok = false;
@@ -693,6 +747,19 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
     for (int e = 0; e < A->nent; ++e)
       argcheck(A->isset[p][e], "every stencil entry of every part needs a value");
   A->free_device();
+  // a part of several boxes: every entry per cell over the bounding box (the
+  // constants spread), masked below
+  for (int p = 0; p < np; ++p) {
+    if (g->boxes[p].empty()) continue;
+    for (int e = 0; e < A->nent; ++e)
+      if (!A->isvar[p][e]) {
+        double*& dst = A->tmpvar[p][e];
+        if (!dst && !(dst = (double*)pool_alloc(sizeof(double) * g->ncell(p))))
+          throw SsamgError{SSAMG_ERR_OOM, "device allocation failed"};
+        launch_fill(dst, g->ncell(p), A->cval[p][e], st);
+        A->isvar[p][e] = 1;
+      }
+  }
   // pack variable entries (a 27-point stencil in offset-code order, so that
   // a part with every entry per cell is one contiguous array in that order)
   A->coef_off.assign(np, std::vector<long long>(A->nent, -1));
@@ -716,6 +783,16 @@ extern "C" int ssamg_matrix_assemble(ssamg_matrix A, void* stream) {
                       g->hi[p][2] - g->lo[p][2] + 1};
         if (A->o[e][0] || A->o[e][1] || A->o[e][2])
           launch_mask_outside(A->coef + A->coef_off[p][e], ext, A->o[e], st);
+        if (!g->boxes[p].empty()) {
+          // cells outside the part's boxes: decoupled (diagonal 1), and no
+          // connection into them
+          PartBoxes pb{};
+          pb.n = (int)g->boxes[p].size();
+          for (int b = 0; b < pb.n; ++b)
+            for (int t = 0; t < 6; ++t)
+              pb.b[b][t] = g->boxes[p][b][t] - g->lo[p][t % 3];
+          launch_mask_part(A->coef + A->coef_off[p][e], ext, A->o[e], pb, st);
+        }
       }
   // couplings: global (row, col) and direction bits per coupling here,
   // O(m); the CSR (rows ascending, columns ascending, duplicates summed in

@@ -181,13 +181,16 @@ __global__ void __launch_bounds__(NT) k_interp(LevelView<double> L, double* __re
       pw = -nw * rd;
       pe = -ne * rd;
     }
-    if (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1)) {
+    // part-boundary fix: a row's bit +d* (-d*) says that it leaves its part
+    // that way (on the box face; beside a hole too when rows lie inside the
+    // box, has_u = 2)
+    if (sp.has_u > 1 || (sp.has_u && (fc[d] == 0 || fc[d] == sp.n[d] - 1))) {
       int r = L.u_map[sp.off + c];
       if (r >= 0) {
         unsigned bits = 0;
         for (int q = L.u_ptr[r]; q < L.u_ptr[r + 1]; ++q) bits |= L.u_bits[q];
-        if (fc[d] == sp.n[d] - 1 && ((bits >> (2 * d)) & 1u)) { pw = 1.0; pe = 0.0; }
-        if (fc[d] == 0 && ((bits >> (2 * d + 1)) & 1u)) { pw = 0.0; pe = 1.0; }
+        if ((bits >> (2 * d)) & 1u) { pw = 1.0; pe = 0.0; }
+        if ((bits >> (2 * d + 1)) & 1u) { pw = 0.0; pe = 1.0; }
       }
     }
     Pw[sp.poff + F] = pw;
@@ -1267,6 +1270,30 @@ __global__ void k_ua_fill(int N, const int* __restrict__ start, const int* __res
   }
 }
 
+__device__ __forceinline__ bool in_boxes(const PartBoxes& pb, int i, int j, int k) {
+  for (int b = 0; b < pb.n; ++b)
+    if (i >= pb.b[b][0] && i <= pb.b[b][3] && j >= pb.b[b][1] && j <= pb.b[b][4] &&
+        k >= pb.b[b][2] && k <= pb.b[b][5])
+      return true;
+  return false;
+}
+
+__global__ void k_mask_part(double* __restrict__ v, int nx, int ny, int nz, int ox, int oy, int oz,
+                            const __grid_constant__ PartBoxes pb) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    const bool act = in_boxes(pb, i, j, k);
+    if (ox == 0 && oy == 0 && oz == 0) {
+      if (!act) v[c] = 1.0;
+    } else if (!act || !in_boxes(pb, i + ox, j + oy, k + oz)) {
+      v[c] = 0.0;
+    }
+  }
+}
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1490,3 +1517,12 @@ void launch_uassemble(const UAssemble& a, int* nr, long long* nnz, cudaStream_t 
   for (void* q : {(void*)cnt, (void*)fill, (void*)perm, (void*)uniq, (void*)flag, (void*)tmp, (void*)tot})
     pool_free(q);
 }
+
+void launch_mask_part(double* vals, const int n[3], const int o[3], const PartBoxes& pb,
+                      cudaStream_t st) {
+  const long long cells = (long long)n[0] * n[1] * n[2];
+  const int nb = (int)std::min<long long>(cdiv(cells, NT), 152 * 16);
+  k_mask_part<<<nb, NT, 0, st>>>(vals, n[0], n[1], n[2], o[0], o[1], o[2], pb);
+  SSAMG_LAUNCH_CHECK();
+}
+

@@ -25,6 +25,7 @@
 #define SSAMG_MAXE 27
 #define SSAMG_BLOCK 256
 #define SSAMG_DINV_LEVELS 32  // levels per launch of the smoother-diagonal kernel
+#define SSAMG_MAX_PART_BOXES 16  // boxes of one part (ssamg_grid_add_box)
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
 #define SSAMG_TUNE_MARGIN 0.97    // a tuned tile form must save 3% of a level's time
@@ -403,6 +404,17 @@ void launch_dinv(const std::vector<Level>& lev, int first, int last, int relax, 
 void launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 // zero the values of a per-cell entry with offset o where c + o leaves the box
 void launch_mask_outside(double* vals, const int n[3], const int o[3], cudaStream_t st);
+// The boxes of a part of several boxes, relative to its bounding box's
+// corner: b[t] = (lo x, y, z, hi x, y, z).
+struct PartBoxes {
+  int n;
+  int b[SSAMG_MAX_PART_BOXES][6];
+};
+// Entry with offset o of a part held over its bounding box (extents n):
+// the diagonal (o = 0) becomes 1 at cells outside the boxes, any other entry
+// 0 where the cell or its neighbour c + o is outside them.
+void launch_mask_part(double* vals, const int n[3], const int o[3], const PartBoxes& pb,
+                      cudaStream_t st);
 void launch_coarse_assemble(const Level& L, double* A, cudaStream_t st);
 void launch_cholesky(int n, double* A, int* status, cudaStream_t st);
 // exclusive scan of n ints in place; returns nothing (total at out[n])

@@ -77,6 +77,7 @@ _SIGS = {
     "ssamg_release_device_cache": (ctypes.c_longlong, []),
     "ssamg_grid_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
     "ssamg_grid_set_box": (_i, [_vp, _i, _ip, _ip]),
+    "ssamg_grid_add_box": (_i, [_vp, _i, _ip, _ip]),
     "ssamg_grid_assemble": (_i, [_vp]),
     "ssamg_grid_num_cells": (_ll, [_vp]),
     "ssamg_grid_destroy": (None, [_vp]),
@@ -216,13 +217,22 @@ def default_params(**kw) -> Params:
 
 
 class Grid:
-    """Section 2: parts, each one box of cell-centred indices."""
+    """Section 2: parts of cell-centred indices, each one box, or a group of
+    boxes (part_boxes[p], held over their bounding box)."""
 
-    def __init__(self, ndim: int, boxes: Sequence):
+    def __init__(self, ndim: int, boxes: Sequence, part_boxes=None):
         self.h = _vp()
         _check(lib().ssamg_grid_create(ndim, len(boxes), ctypes.byref(self.h)), "grid_create")
         for p, (lo, hi) in enumerate(boxes):
-            _check(lib().ssamg_grid_set_box(self.h, p, _ints(lo), _ints(hi)), "grid_set_box")
+            group = part_boxes[p] if part_boxes is not None else None
+            if group:
+                (blo, bhi), rest = group[0], group[1:]
+                _check(lib().ssamg_grid_set_box(self.h, p, _ints(blo), _ints(bhi)), "grid_set_box")
+                for blo, bhi in rest:
+                    _check(lib().ssamg_grid_add_box(self.h, p, _ints(blo), _ints(bhi)),
+                           "grid_add_box")
+            else:
+                _check(lib().ssamg_grid_set_box(self.h, p, _ints(lo), _ints(hi)), "grid_set_box")
         _check(lib().ssamg_grid_assemble(self.h), "grid_assemble")
         self.ndim = ndim
         self.boxes = [(tuple(lo), tuple(hi)) for lo, hi in boxes]
@@ -281,7 +291,7 @@ class Matrix:
 def matrix_from_problem(prob, stream=None, device_values=False):
     """Grid and assembled matrix from a problem description with the fields
     ndim, boxes, offsets, coef, u_* (see the problems package)."""
-    grid = Grid(prob.ndim, prob.boxes)
+    grid = Grid(prob.ndim, prob.boxes, getattr(prob, "part_boxes", None))
     A = Matrix(grid, prob.offsets)
     for p in range(len(prob.boxes)):
         for e in range(len(prob.offsets)):

@@ -219,3 +219,33 @@ def test_barrier_selftest_argument_ranges(ssamg_lib):
     for args in ((0, 0, 10), (9, 0, 10), (2, -1, 10), (2, 1025, 10), (2, 1, 0),
                  (2, 1, (1 << 20) + 1)):
         assert L.ssamg_selftest_barrier(*args, None) == S.ERR_ARG, args
+
+
+def test_grid_add_box_validation(ssamg_lib):
+    """A part of several boxes: add_box after set_box only, the bounding box
+    grows, couplings must leave the part (the notch is outside it)."""
+    S = ssamg_lib
+    L = S.lib()
+    g = ctypes.c_void_p()
+    assert L.ssamg_grid_create(3, 2, ctypes.byref(g)) == 0
+    assert L.ssamg_grid_add_box(g, 0, S._ints([0, 4, 0]), S._ints([3, 7, 3])) == S.ERR_ARG  # no set_box yet
+    assert L.ssamg_grid_set_box(g, 0, S._ints([0, 0, 0]), S._ints([7, 3, 3])) == 0
+    assert L.ssamg_grid_add_box(g, 0, S._ints([0, 4, 0]), S._ints([3, 7, 3])) == 0
+    assert L.ssamg_grid_add_box(g, 0, S._ints([2, 2, 2]), S._ints([1, 1, 1])) == S.ERR_ARG   # hi < lo
+    assert L.ssamg_grid_set_box(g, 1, S._ints([0, 0, 0]), S._ints([3, 3, 3])) == 0
+    assert L.ssamg_grid_assemble(g) == 0
+    assert L.ssamg_grid_num_cells(g) == 8 * 8 * 4 + 4 ** 3     # the bounding box and the cube
+    assert L.ssamg_grid_add_box(g, 1, S._ints([0, 0, 0]), S._ints([1, 1, 1])) == S.ERR_STATE
+    A = ctypes.c_void_p()
+    offs = [0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1]
+    assert L.ssamg_matrix_create(g, 7, S._ints(offs), ctypes.byref(A)) == 0
+
+    def add(part, idx, d, q, nidx):
+        v = np.array([-1.0])
+        return L.ssamg_matrix_add_couplings(A, 1, S._ints([part]), S._ints(idx), S._ints(d),
+                                            S._ints([q]), S._ints(nidx), v.ctypes.data_as(S._dp))
+    assert add(0, (3, 5, 1), (1, 0, 0), 1, (0, 1, 1)) == 0         # beside the notch, leaves through +x
+    assert add(0, (2, 5, 1), (1, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG  # +x neighbour is in the part
+    assert add(0, (5, 5, 1), (0, 0, 0), 1, (0, 1, 1)) == S.ERR_ARG  # the row is in the notch
+    L.ssamg_matrix_destroy(A)
+    L.ssamg_grid_destroy(g)

@@ -44,6 +44,7 @@ def cases():
         T.poisson2d(9, 4),
         P.three_point(9),                                  # rotated index maps (test case 3)
         P.samr(12),                                        # ghost unknowns, inner rows (test case 4)
+        P.multibox(9),                                     # a part of two boxes (Section 2)
     ]
     for k in range(5):
         c = P.config(k, small=True)
