@@ -144,7 +144,7 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         jobs = ["bench"] + ([] if args.no_extra_workloads else
                             ["laplace32", "diffusion128", "batched_subset", "samr128",
-                             "three_point160"])
+                             "three_point160", "multibox96"])
         beside = OracleBeside(jobs)
 
     import torch
@@ -625,7 +625,10 @@ def extra_workloads(S, stream, peak, args):
     for key, k, text in (("three_point_160", 5, "3 parts 160^3 around a common k edge, rotated "
                                                 "index maps (test case 3), seed 5"),
                          ("samr_128", 6, "2 parts 128^3: coarse grid with ghost unknowns and a "
-                                         "patch refined by 2 (test case 4), seed 6")):
+                                         "patch refined by 2 (test case 4), seed 6"),
+                         ("multibox_96", 7, "an L-shaped part of two boxes (3 x 96^3 cells, held "
+                                            "over its 192 x 192 x 96 bounding box) around a 96^3 "
+                                            "part, seed 7")):
         prob = P.config(k)
         grid, A = S.matrix_from_problem(prob)
         b = torch.as_tensor(prob.b[0], device="cuda")
@@ -665,7 +668,8 @@ def oracle_errors(extra, meta, arrays):
                 errs = [rel_err(v, arrays[f"batched_subset:x:{k}"]) for k, v in xs.items()]
                 bat[name]["err_vs_oracle"] = {"max_rel_err": fmt(max(errs)), "instances": len(errs),
                                               "problems": jobs["batched_subset"]["problems"]}
-    for key, job in (("three_point_160", "three_point160"), ("samr_128", "samr128")):
+    for key, job in (("three_point_160", "three_point160"), ("samr_128", "samr128"),
+                     ("multibox_96", "multibox96")):
         w = extra.get(key)
         if w is None:
             continue
@@ -876,8 +880,8 @@ def oracle_run(job):
         out = {"setup_s": t1 - t0, "solve_s": t2 - t1, "adjoint_s": t3 - t2, "gradient_s": t4 - t3,
                "iterations": r.iterations, "adjoint_iterations": ra.iterations,
                "unknowns": prob.n, "x": r.x, "dg": dg}
-    elif job in ("three_point160", "samr128"):
-        prob = P.config(5 if job == "three_point160" else 6)
+    elif job in ("three_point160", "samr128", "multibox96"):
+        prob = P.config({"three_point160": 5, "samr128": 6, "multibox96": 7}[job])
         t0 = time.perf_counter()
         h = O.setup(prob)
         t1 = time.perf_counter()

@@ -585,7 +585,8 @@ def config(k: int, small: bool = False) -> Union[Problem, List[Problem]]:
     """The workloads at full size (small=False) or at a size the oracle
     finishes in seconds (small=True) with the same structure and seeds:
     0-4 as listed above, 5 the three-point intersection (3 x 160^3) and 6 the
-    SAMR grid (2 x 128^3) of the paper's test cases 3 and 4."""
+    SAMR grid (2 x 128^3) of the paper's test cases 3 and 4, 7 a part of two
+    boxes (an L of 3 x 96^3 cells) around a 96^3 part."""
     if k == 0:
         return laplace7(16 if small else 32, seed=0)
     if k == 1:
@@ -602,4 +603,6 @@ def config(k: int, small: bool = False) -> Union[Problem, List[Problem]]:
         return three_point(8 if small else 160, seed=5)
     if k == 6:
         return samr(8 if small else 128, seed=6)
+    if k == 7:
+        return multibox(4 if small else 96, seed=7)
     raise ValueError(k)
