@@ -445,12 +445,16 @@ def level_table(sv, name, stream):
     print("\n".join(out), file=sys.stderr)
 
 
-def hbm_by_level(sv, workload, stream, peak, min_cells=1 << 20):
+def hbm_by_level(sv, workload, stream, peak, min_cells=1 << 20, nrhs=1):
     """Per-kernel HBM throughput of the FP32 cycle on the levels of at least
     2^20 cells: algorithmic bytes (each input and output once; w = 4) / the
     kernel's CUDA-graph launch time (50 replayed launches on the solver's own
     buffers), against the measured copy bandwidth.  Launches moving less than
-    ~3/4 of L2 are flagged l2_resident."""
+    ~3/4 of L2 are flagged l2_resident.  With nrhs > 1 (after a batch solve of
+    that many right-hand sides together), the residual and relaxation of
+    cell-tile levels are also timed as the solve runs them, every right-hand
+    side in one launch: the coefficients counted once, the vectors nrhs
+    times."""
     w = 4
     L = sv.num_levels()
     sizes = [sv.level_sizes(l) for l in range(L)]
@@ -484,6 +488,13 @@ def hbm_by_level(sv, workload, stream, peak, min_cells=1 << 20):
                 # the 129 MB L2: the fraction is of the HBM copy rate, the
                 # bytes are mostly served by L2
                 row[k]["l2_resident"] = True
+        if nrhs > 1 and not sv.level_tile(l)[1]:
+            for k, kid, nb in (("residual_rhs_together", 11, w * (sc + 3 * N * nrhs)),
+                               ("relax_rhs_together", 12, w * (sc + 4 * N * nrhs))):
+                us = sv.time_kernel(kid, l, 50, stream)
+                gbs = nb / (us * 1e-6) / 1e9
+                row[k] = {"rhs": nrhs, "us": round(us, 2), "us_per_rhs": round(us / nrhs, 2),
+                          "gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
         rows.append(row)
     return {"workload": workload, "peak_gbs": peak, "levels": rows}
 
@@ -617,7 +628,21 @@ def extra_workloads(S, stream, peak, args):
                      "mdof_s": round(off[-1] * nrhs / ((su + so) * 1e-3) / 1e6, 3),
                      "_x": {f"{k}_{j}": xh[j, off[k]:off[k + 1]].copy() for k in sel for j in range(nrhs)}}
         if prec == 1:
-            res["hbm"] = hbm_by_level(B.solver(), res["workload"], stream, peak)
+            res["hbm"] = hbm_by_level(B.solver(), res["workload"], stream, peak, nrhs=nrhs)
+            # the same batch and tile table with the right-hand sides one
+            # after another (each its own PCG loop inside the one graph)
+            B2 = S.Batch([A for _, A in mats], precision=prec, flexible=prec, tol=1e-8,
+                         max_iter=500, rhs_together=0)
+            B2.solver().set_tile_table(table)
+            B2.setup()
+            x2 = torch.zeros_like(bb)
+            B2.solve(bb, x2, nrhs)
+            su2, so2, _, st2 = timed_steps(stream, nst, B2.setup, lambda: B2.solve(bb, x2, nrhs))
+            res[name]["rhs_one_after_another"] = {
+                "setup_ms": round(su2, 3), "solve_ms": round(so2, 3), "steps": nst,
+                "solutions_bitwise_equal": bool(torch.equal(xx, x2)),
+                "mdof_s": round(off[-1] * nrhs / ((su2 + so2) * 1e-3) / 1e6, 3)}
+            del B2, x2
         del B
     out["batched_64"] = res
     out["diffusion_128"] = differentiation_workload(S, stream, peak)

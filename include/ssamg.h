@@ -159,6 +159,13 @@ typedef struct {
                           (some entries constant per part) run over 32 x 8 x 8 bricks, each
                           thread marching a column along z; 0: over the cell tiles of the
                           other shapes */
+  int rhs_together;    /* ssamg_batch_solve with several right-hand sides and use_graph:
+                          1 (default) one PCG loop for all of them, each cycle step enqueued
+                          per right-hand side except the residual and relaxation on cell-tile
+                          levels, which take every right-hand side in one launch (the blocks
+                          of a tile side by side, so its stencil coefficients are read from
+                          HBM once); 0: the right-hand sides one after another in one graph.
+                          Both give the same results; use_tail 1 or 2 always takes 0 */
 } ssamg_params;
 
 typedef struct {
@@ -313,7 +320,10 @@ int ssamg_batch_offsets(ssamg_batch B, long long* off);
  * x0 = 0.  b, x: device, nrhs x N doubles (right-hand side j at j N).
  * st: NULL or nrhs x nprob stats, entry j nprob + k.  Returns SSAMG_OK when
  * every instance converged, SSAMG_NOT_CONVERGED when one hit max_iter, else
- * the first error.  Synchronises `stream` once per right-hand side. */
+ * the first error.  With use_graph, all right-hand sides run in one graph
+ * launch (together or one after another, see rhs_together) and `stream` is
+ * synchronised once; without, once per right-hand side.  The residual
+ * history (ssamg_residual_history) is the last right-hand side's. */
 int ssamg_batch_solve(ssamg_batch B, const double* b, double* x, int nrhs, void* stream,
                       ssamg_stats* st);
 /* The solver the batch runs on (owned by the batch), for the introspection
@@ -363,7 +373,9 @@ int ssamg_coupling_sums_noalloc(ssamg_solver s, int level, double* c_dev, void* 
  * product (level ignored), 7 one whole PCG iteration, 8 the PCG's vector steps
  * (beta, search direction, alpha, x and r updates), 9 the cycle's last post-
  * relaxation as the PCG runs it (FP64 z out, r.z partials), 10 the coarse-level transition's
- * cluster kernel of use_tail = 3 (level ignored; SSAMG_ERR_STATE without one).  Ids 7 and 8 clear
+ * cluster kernel of use_tail = 3 (level ignored; SSAMG_ERR_STATE without one), 11 and 12 the
+ * residual and the relaxation of every right-hand side of the last batch solve in one launch
+ * (rhs_together; cell-tile levels above the tail, SSAMG_ERR_STATE elsewhere).  Ids 7 and 8 clear
  * the solve's convergence state, so that the replayed iterations never stop,
  * and run on the vectors the last solve left (time them after a solve: on
  * vectors that break the iteration down, p.Ap <= 0, the cycle kernels stand

@@ -9,6 +9,7 @@
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include <nvtx3/nvToolsExt.h>
@@ -309,6 +310,29 @@ struct GraphSet {
   }
 };
 
+// Copies of the per-solve vectors for right-hand sides solved together: on
+// every level whose cycle vectors the per-level kernels use, and for the
+// FP64 PCG, R slices of each vector (guard cells around each slice), the
+// slices of one vector `stride` elements apart; per right-hand side a
+// block-partial buffer, the problems' scalars (contiguous: right-hand side
+// j's at sc + j nprob) and a residual history.
+struct RhsSet {
+  int R = 0;
+  int nlev = 0;                       // levels 0..nlev-1 carry slices
+  std::vector<long long> stride;      // per level, elements between slices
+  std::vector<char*> x, b, r, t;      // per level: the first slice
+  std::vector<float*> uy32;           // per level: the first U x slice (or none)
+  std::vector<double*> uy64;
+  long long stride0 = 0;              // the FP64 PCG vectors
+  double *pb = nullptr, *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr,
+         *pq = nullptr, *pzprev = nullptr;
+  double* partial = nullptr;
+  long long partial_len = 0;
+  PcgScalars* sc = nullptr;
+  double* hist = nullptr;
+  long long hist_len = 0;
+};
+
 struct ssamg_solver_s {
   ssamg_params prm;
   Arena arena;
@@ -362,6 +386,10 @@ struct ssamg_solver_s {
   int tiles[SSAMG_TILE_CLASSES] = {};  // tile table by level size class (0: built-in rule)
   std::vector<double> user_W;  // user spacings (3 per part), empty: from the coupling sums
   GraphSet graphs;
+  RhsSet rhs;
+  // scalars whose done flags decide the solve loop (null: sc, nprob)
+  const PcgScalars* any_sc = nullptr;
+  int any_n = 0;
   long long setup_launches = 0, head_launches = 0, body_launches = 0;
   ~ssamg_solver_s() {
     graphs.reset();
@@ -657,57 +685,79 @@ extern "C" int ssamg_matrix_add_couplings(ssamg_matrix A, long long n, const int
   int* ccol = A->c_col.data() + m0;
   unsigned char* cbits = A->c_bits.data() + m0;
   double* cval = A->c_val.data() + m0;
-  char* hu = hasu.data();
   auto gidx = [&](int p, const int* c) {
     const int* l = LO + 3 * p;
     const int* h = HI + 3 * p;
     const long long nx = h[0] - l[0] + 1, ny = h[1] - l[1] + 1;
     return OFF[p] + ((long long)(c[2] - l[2]) * ny + (c[1] - l[1])) * nx + (c[0] - l[0]);
   };
-  bool ok = true;
-  for (long long t = 0; t < n; ++t) {
-    const int p = part[t], q = nbor_part[t];
-    if (p < 0 || p >= np || q < 0 || q >= np || p == q) {
-      ok = false;
-      break;
-    }
-    const int* a = idx + 3 * t;
-    const int* b = nbor_idx + 3 * t;
-    const int* dv = dir + 3 * t;
-    const int* lp = LO + 3 * p;
-    const int* hp = HI + 3 * p;
-    const int* lq = LO + 3 * q;
-    const int* hq = HI + 3 * q;
-    unsigned bt = 0;
-    bool face = false, bad = false;
-    for (int d = 0; d < 3; ++d) {
-      bad |= a[d] < lp[d] || a[d] > hp[d] || b[d] < lq[d] || b[d] > hq[d] || dv[d] < -1 ||
-             dv[d] > 1;
-      bt |= (dv[d] > 0 ? 1u << (2 * d) : 0u) | (dv[d] < 0 ? 1u << (2 * d + 1) : 0u);
-      face |= d < ndim && (a[d] == lp[d] || a[d] == hp[d]);
-    }
-    if (!bad) {
-      // a nonzero direction leaves the row's part: the neighbour that way
-      // lies outside its box, or outside the boxes of a part of several
-      for (int d = 0; d < 3 && !bad; ++d) {
-        if (dv[d] == 0) continue;
-        int nb[3] = {a[0], a[1], a[2]};
-        nb[d] += dv[d];
-        bad = g->in_box(p, nb) && g->in_part(p, nb);
+  // One chunk of couplings [t0, t1): converts them into the tail and raises
+  // its own part flags in hu; false at the first invalid coupling.
+  auto convert = [&](long long t0, long long t1, char* hu) {
+    for (long long t = t0; t < t1; ++t) {
+      const int p = part[t], q = nbor_part[t];
+      if (p < 0 || p >= np || q < 0 || q >= np || p == q) return false;
+      const int* a = idx + 3 * t;
+      const int* b = nbor_idx + 3 * t;
+      const int* dv = dir + 3 * t;
+      const int* lp = LO + 3 * p;
+      const int* hp = HI + 3 * p;
+      const int* lq = LO + 3 * q;
+      const int* hq = HI + 3 * q;
+      unsigned bt = 0;
+      bool face = false, bad = false;
+      for (int d = 0; d < 3; ++d) {
+        bad |= a[d] < lp[d] || a[d] > hp[d] || b[d] < lq[d] || b[d] > hq[d] || dv[d] < -1 ||
+               dv[d] > 1;
+        bt |= (dv[d] > 0 ? 1u << (2 * d) : 0u) | (dv[d] < 0 ? 1u << (2 * d + 1) : 0u);
+        face |= d < ndim && (a[d] == lp[d] || a[d] == hp[d]);
       }
-      bad = bad || !g->in_part(p, a) || !g->in_part(q, b);
+      if (!bad) {
+        // a nonzero direction leaves the row's part: the neighbour that way
+        // lies outside its box, or outside the boxes of a part of several
+        for (int d = 0; d < 3 && !bad; ++d) {
+          if (dv[d] == 0) continue;
+          int nb[3] = {a[0], a[1], a[2]};
+          nb[d] += dv[d];
+          bad = g->in_box(p, nb) && g->in_part(p, nb);
+        }
+        bad = bad || !g->in_part(p, a) || !g->in_part(q, b);
+      }
+      if (bad) return false;
+      crow[t] = (int)gidx(p, a);
+      ccol[t] = (int)gidx(q, b);
+      cbits[t] = (unsigned char)bt;
+      cval[t] = vals[t];
+      // 2 when a row lies inside the box (no face of an active dimension)
+      const char hv = face ? 1 : 2;
+      if (hu[p] < hv) hu[p] = hv;
     }
-    if (bad) {
-      ok = false;
-      break;
+    return true;
+  };
+  // large calls in chunks on host threads (every coupling is written by one
+  // thread; the part flags are merged by maximum, so the result does not
+  // depend on the split)
+  const long long chunk = 16384;
+  const int nth = (int)std::max<long long>(
+      1, std::min<long long>({(long long)std::max(1u, std::thread::hardware_concurrency()),
+                              (long long)SSAMG_HOST_THREADS, n / chunk}));
+  bool ok = true;
+  if (nth == 1) {
+    ok = convert(0, n, hasu.data());
+  } else {
+    std::vector<std::vector<char>> hus(nth, std::vector<char>(np, 0));
+    std::vector<char> oks(nth, 1);
+    std::vector<std::thread> th;
+    th.reserve(nth);
+    for (int i = 0; i < nth; ++i)
+      th.emplace_back([&, i] {
+        oks[i] = convert(n * i / nth, n * (i + 1) / nth, hus[i].data());
+      });
+    for (auto& t : th) t.join();
+    for (int i = 0; i < nth; ++i) {
+      ok = ok && oks[i];
+      for (int p = 0; p < np; ++p) hasu[p] = std::max(hasu[p], hus[i][p]);
     }
-    crow[t] = (int)gidx(p, a);
-    ccol[t] = (int)gidx(q, b);
-    cbits[t] = (unsigned char)bt;
-    cval[t] = vals[t];
-    // 2 when a row lies inside the box (no face of an active dimension)
-    const char hv = face ? 1 : 2;
-    if (hu[p] < hv) hu[p] = hv;
   }
   if (!ok) {
     A->c_row.resize(m0);
@@ -853,13 +903,14 @@ extern "C" void ssamg_params_default(ssamg_params* p) {
   p->use_pdl = 1;
   p->tail_cells = 0;
   p->use_bricks = 1;
+  p->rhs_together = 1;
 }
 
 extern "C" int ssamg_solver_create(const ssamg_params* prm, ssamg_solver* out) {
   if (!prm || !out) return SSAMG_ERR_ARG;
   if (prm->precision < 0 || prm->precision > 1 || prm->relax < 0 || prm->relax > 1 ||
       prm->skip < 0 || prm->skip > 2 || prm->max_levels < 1 || prm->tol < 0 || prm->max_iter < 0 ||
-      prm->use_tail < 0 || prm->use_tail > 3)
+      prm->use_tail < 0 || prm->use_tail > 3 || prm->rhs_together < 0 || prm->rhs_together > 1)
     return SSAMG_ERR_ARG;
   auto* s = new (std::nothrow) ssamg_solver_s;
   if (!s) return SSAMG_ERR_OOM;
@@ -1249,6 +1300,7 @@ void build_hierarchy(ssamg_solver s, cudaStream_t st) {
   s->ndim = ndim;
   s->arena.reset();
   s->graphs.reset();
+  s->rhs = RhsSet{};
   s->lev.clear();
   s->lev.reserve((size_t)s->prm.max_levels + 1);
   s->ready = false;
@@ -1918,7 +1970,8 @@ int vcycle(ssamg_solver s, const double* r, double* z, cudaStream_t st, double* 
 // loop body starts with the V-cycle and ends with the convergence test.
 PcgCtx pcg_ctx(ssamg_solver s) {
   return PcgCtx{s->pb, s->pbb, s->nprob, s->sc, s->ctl, s->partial, s->hist,
-                s->prm.max_iter + 1};
+                s->prm.max_iter + 1, s->any_sc ? s->any_sc : s->sc,
+                s->any_sc ? s->any_n : s->nprob};
 }
 
 void enqueue_pcg_head(ssamg_solver s, cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
@@ -2088,6 +2141,381 @@ void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
   s->graphs.rounds_n = nrhs;
 }
 
+// ---- Right-hand sides solved together --------------------------------------
+// One PCG loop runs every right-hand side of a batch: each step of the cycle
+// is enqueued for right-hand side 0, 1, ... in turn (its vectors swapped into
+// the solver), except the residual and the relaxation on cell-tile levels,
+// which take all right-hand sides in one launch with the blocks of a tile
+// side by side, so that the tile's stencil coefficients come from HBM once
+// and from L2 for the others.  Every right-hand side computes what it would
+// alone, in the same order.
+
+// First level of the coarse tail the host-side cycle stops at (as in
+// enqueue_vcycle).
+int cycle_tail_level(ssamg_solver s) {
+  const int Lc = (int)s->lev.size() - 1;
+  return s->ctail_lt >= 1 ? s->ctail_lt : s->tail_lt >= 0 ? s->tail_lt : Lc;
+}
+
+// Whether the right-hand sides can share launches: a cycle with levels above
+// its tail and no fused grid-barrier tail (whose level table holds one set of
+// vectors).
+bool rhs_together_ok(ssamg_solver s) {
+  const int Lc = (int)s->lev.size() - 1;
+  return Lc > 0 && s->tail_lt < 0 && cycle_tail_level(s) > 0;
+}
+
+struct RhsSaved {
+  double *b, *x, *r, *z, *p, *q, *zprev, *partial, *hist;
+  PcgScalars* sc;
+  std::vector<void*> x_, b_, r_, t_;
+  std::vector<float*> uy32;
+  std::vector<double*> uy64;
+};
+
+// Slices for R right-hand sides (kept until the next set-up); zeroed on st.
+void alloc_rhs(ssamg_solver s, int R, cudaStream_t st) {
+  RhsSet& M = s->rhs;
+  if (M.R == R) return;
+  const bool fp32 = s->prm.precision == 1;
+  const size_t w = fp32 ? sizeof(float) : sizeof(double);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  auto slab = [](long long n, long long guard) { return (n + 2 * guard + 63) / 64 * 64; };
+  RhsSet N;
+  N.R = R;
+  N.nlev = cycle_tail_level(s) + 1;
+  N.stride.resize(N.nlev);
+  size_t total = 0;
+  for (int l = 0; l < N.nlev; ++l) {
+    const Level& L = s->lev[l];
+    N.stride[l] = slab(L.N, L.guard);
+    total += 4 * al(w * N.stride[l] * R);
+    if (L.nr > 0) total += al(8 * N.stride[l] * R) + (fp32 ? al(4 * N.stride[l] * R) : 0);
+  }
+  const Level& L0 = s->lev[0];
+  N.stride0 = slab(L0.N, L0.guard);  // equal to stride[0] (element counts)
+  total += 7 * al(8 * N.stride0 * R);
+  N.partial_len = 2ll * std::max(L0.nblk, L0.nbblk);
+  total += al(8 * N.partial_len * R);
+  total += al(sizeof(PcgScalars) * (size_t)s->nprob * R);
+  N.hist_len = (long long)s->nprob * (s->prm.max_iter + 1);
+  total += al(8 * N.hist_len * R);
+  char* base = (char*)s->arena.alloc(total);
+  SSAMG_CUDA(cudaMemsetAsync(base, 0, total, st));
+  auto take = [&](size_t bytes) {
+    char* p = base;
+    base += al(bytes);
+    return p;
+  };
+  N.x.resize(N.nlev);
+  N.b.resize(N.nlev);
+  N.r.resize(N.nlev);
+  N.t.resize(N.nlev);
+  N.uy32.assign(N.nlev, nullptr);
+  N.uy64.assign(N.nlev, nullptr);
+  for (int l = 0; l < N.nlev; ++l) {
+    const Level& L = s->lev[l];
+    const size_t g = w * L.guard;
+    N.x[l] = take(w * N.stride[l] * R) + g;
+    N.b[l] = take(w * N.stride[l] * R) + g;
+    N.r[l] = take(w * N.stride[l] * R) + g;
+    N.t[l] = take(w * N.stride[l] * R) + g;
+    if (L.nr > 0) {
+      N.uy64[l] = (double*)take(8 * N.stride[l] * R);
+      if (fp32) N.uy32[l] = (float*)take(4 * N.stride[l] * R);
+    }
+  }
+  double** pv[7] = {&N.pb, &N.px, &N.pr, &N.pz, &N.pp, &N.pq, &N.pzprev};
+  for (double** q : pv) *q = (double*)take(8 * N.stride0 * R) + L0.guard;
+  N.partial = (double*)take(8 * N.partial_len * R);
+  N.sc = (PcgScalars*)take(sizeof(PcgScalars) * (size_t)s->nprob * R);
+  N.hist = (double*)take(8 * N.hist_len * R);
+  M = std::move(N);
+}
+
+RhsSaved save_rhs(ssamg_solver s) {
+  RhsSaved o{s->b, s->x, s->r, s->z, s->p, s->q, s->zprev, s->partial, s->hist, s->sc,
+             {}, {}, {}, {}, {}, {}};
+  for (int l = 0; l < s->rhs.nlev; ++l) {
+    const Level& L = s->lev[l];
+    o.x_.push_back(L.x);
+    o.b_.push_back(L.b);
+    o.r_.push_back(L.r);
+    o.t_.push_back(L.t);
+    o.uy32.push_back(L.uy32);
+    o.uy64.push_back(L.uy64);
+  }
+  return o;
+}
+
+void restore_rhs(ssamg_solver s, const RhsSaved& o) {
+  s->b = o.b;
+  s->x = o.x;
+  s->r = o.r;
+  s->z = o.z;
+  s->p = o.p;
+  s->q = o.q;
+  s->zprev = o.zprev;
+  s->partial = o.partial;
+  s->hist = o.hist;
+  s->sc = o.sc;
+  for (int l = 0; l < s->rhs.nlev; ++l) {
+    Level& L = s->lev[l];
+    L.x = o.x_[l];
+    L.b = o.b_[l];
+    L.r = o.r_[l];
+    L.t = o.t_[l];
+    L.uy32 = o.uy32[l];
+    L.uy64 = o.uy64[l];
+  }
+}
+
+// Right-hand side j's slices into the solver (and its scalars into the
+// level views' skip pointer).
+void use_rhs(ssamg_solver s, int j) {
+  const RhsSet& M = s->rhs;
+  const bool fp32 = s->prm.precision == 1;
+  const size_t w = fp32 ? sizeof(float) : sizeof(double);
+  const long long o0 = j * M.stride0;
+  s->b = M.pb + o0;
+  s->x = M.px + o0;
+  s->r = M.pr + o0;
+  s->z = M.pz + o0;
+  s->p = M.pp + o0;
+  s->q = M.pq + o0;
+  s->zprev = M.pzprev + o0;
+  s->partial = M.partial + j * M.partial_len;
+  s->hist = M.hist + j * M.hist_len;
+  s->sc = M.sc + (long long)j * s->nprob;
+  for (int l = 0; l < M.nlev; ++l) {
+    Level& L = s->lev[l];
+    const long long o = j * M.stride[l];
+    L.x = M.x[l] + w * o;
+    L.b = M.b[l] + w * o;
+    L.r = M.r[l] + w * o;
+    L.t = M.t[l] + w * o;
+    L.uy32 = M.uy32[l] ? M.uy32[l] + o : nullptr;
+    L.uy64 = M.uy64[l] ? M.uy64[l] + o : nullptr;
+  }
+  g_ssamg_skip = s->sc;
+}
+
+// The V(1,1) cycle z_j = M r_j of every right-hand side j (r, z: the PCG
+// slices).  With `dots`, the last relaxation also forms each right-hand
+// side's r.z (and r.zprev) partials in its own buffer; returns their block
+// count as enqueue_vcycle does.
+template <class T>
+int enqueue_vcycle_rhs(ssamg_solver s, bool dots, cudaStream_t st) {
+  const RhsSet& M = s->rhs;
+  const int R = M.R;
+  auto& Ls = s->lev;
+  const int Lc = (int)Ls.size() - 1;
+  const bool is_f = sizeof(T) == sizeof(float);
+  const bool fused_in = is_f && s->tail_lt != 0;
+  const int lt = cycle_tail_level(s);
+  const bool ctail = lt < Lc && s->ctail_lt == lt;
+  auto each = [&](auto&& f) {
+    for (int j = 0; j < R; ++j) {
+      use_rhs(s, j);
+      f();
+    }
+    use_rhs(s, 0);
+  };
+  // right-hand side's level-0 cycle right-hand side (slice of the current one)
+  auto b0 = [&]() { return is_f ? (const T*)Ls[0].b : (const T*)s->r; };
+  auto coarse = [&](const T* bl, T* xl) {
+    if (s->prm.coarse_direct && s->cinv)
+      launch_coarse_apply<T>(s->nL, s->cinv, bl, xl, st);
+    else if (s->prm.coarse_direct)
+      launch_coarse_solve<T>(s->nL, s->chol, bl, xl, st);
+    else
+      launch_relax0<T>(Ls[Lc], bl, xl, st);
+  };
+  for (int l = 0; l < lt; ++l) {
+    if (l == 0)
+      each([&] {
+        if (fused_in) {
+          launch_relax0_u_first<T>(Ls[0], s->r, (T*)Ls[0].b, (T*)Ls[0].x, st);
+        } else {
+          if (is_f) launch_cast_d2f(s->r, (float*)Ls[0].b, Ls[0].N, st);
+          launch_relax0_u<T>(Ls[0], b0(), (T*)Ls[0].x, st);
+        }
+      });
+    if (!uses_bricks(Ls[l])) {
+      use_rhs(s, 0);
+      launch_residual_rhs<T>(Ls[l], R, M.stride[l], s->nprob, (const T*)Ls[l].x,
+                             l == 0 ? b0() : (const T*)Ls[l].b, (T*)Ls[l].r, st);
+    } else {
+      each([&] {
+        launch_residual<T>(Ls[l], (const T*)Ls[l].x, l == 0 ? b0() : (const T*)Ls[l].b,
+                           (T*)Ls[l].r, st);
+      });
+    }
+    each([&] {
+      launch_restrict<T>(Ls[l], Ls[l + 1], (const T*)Ls[l].r, (T*)Ls[l + 1].b,
+                         l + 1 < lt ? (T*)Ls[l + 1].x : nullptr, st);
+    });
+  }
+  each([&] {
+    if (ctail)
+      launch_ctail<T>(s->ctail, s->ctail_nc, s->ctail_smem, (const T*)Ls[lt].b, (T*)Ls[lt].t, st);
+    else
+      coarse((const T*)Ls[Lc].b, (T*)Ls[Lc].x);
+  });
+  // the correction prolongated to level l comes from level l + 1's output
+  auto e_of = [&](int l) {
+    if (l + 1 == lt) return ctail ? (const T*)Ls[lt].t : (const T*)Ls[Lc].x;
+    return (const T*)Ls[l + 1].t;
+  };
+  for (int l = lt - 1; l >= 0; --l) {
+    each([&] { launch_prolong_u<T>(Ls[l], e_of(l), (const T*)Ls[l].x, (T*)Ls[l].r, st); });
+    if (l == 0 && (dots || is_f)) {
+      each([&] {
+        launch_relax_final<T>(Ls[0], (const T*)Ls[0].r, b0(), s->z, s->r,
+                              dots ? s->zprev : nullptr, s->partial, st);
+      });
+      return dots ? Ls[0].nblk : 0;
+    }
+    if (!uses_bricks(Ls[l])) {
+      use_rhs(s, 0);
+      T* out = l == 0 ? (T*)s->z : (T*)Ls[l].t;
+      launch_relax_rhs<T>(Ls[l], R, M.stride[l], s->nprob, (const T*)Ls[l].r,
+                          l == 0 ? b0() : (const T*)Ls[l].b, out, st);
+    } else {
+      each([&] {
+        T* out = l == 0 ? (T*)s->z : (T*)Ls[l].t;
+        launch_relax<T>(Ls[l], (const T*)Ls[l].r, l == 0 ? b0() : (const T*)Ls[l].b, out, st);
+      });
+    }
+  }
+  return 0;
+}
+
+int vcycle_rhs(ssamg_solver s, bool dots, cudaStream_t st) {
+  if (s->prm.precision == 1) return enqueue_vcycle_rhs<float>(s, dots, st);
+  return enqueue_vcycle_rhs<double>(s, dots, st);
+}
+
+// PCG head and loop body of every right-hand side (as enqueue_pcg_head /
+// enqueue_pcg_body; the scalar steps per right-hand side, the cycle shared).
+void enqueue_pcg_head_rhs(ssamg_solver s, cudaGraphConditionalHandle h, cudaStream_t st) {
+  const int R = s->rhs.R;
+  Level& L0 = s->lev[0];
+  for (int j = 0; j < R; ++j) {
+    use_rhs(s, j);
+    launch_pcg_init(L0, s->b, s->x, s->r, pcg_ctx(s), st);
+  }
+  vcycle_rhs(s, false, st);
+  for (int j = 0; j < R; ++j) {
+    use_rhs(s, j);
+    const PcgCtx c = pcg_ctx(s);
+    launch_pcg_start(L0, s->r, s->z, s->p, s->prm.flexible ? s->zprev : nullptr, c, st);
+    launch_pcg_alpha(L0, s->p, s->q, c, st);
+    launch_pcg_update(L0, s->p, s->q, s->x, s->r, c, h, 1, st);
+  }
+}
+
+void enqueue_pcg_body_rhs(ssamg_solver s, cudaGraphConditionalHandle h, cudaStream_t st) {
+  const int R = s->rhs.R;
+  Level& L0 = s->lev[0];
+  const int npart = vcycle_rhs(s, true, st);
+  for (int j = 0; j < R; ++j) {
+    use_rhs(s, j);
+    const PcgCtx c = pcg_ctx(s);
+    double* zp = s->prm.flexible ? s->zprev : nullptr;
+    if (npart > 0)
+      launch_pcg_beta_from_partials(L0, s->z, s->p, c, final_ranges(L0, c), st);
+    else
+      launch_pcg_beta(L0, s->r, s->z, zp, s->p, c, st);
+    launch_pcg_alpha(L0, s->p, s->q, c, st);
+    launch_pcg_update(L0, s->p, s->q, s->x, s->r, c, h, 1, st);
+  }
+}
+
+// One graph for nrhs right-hand sides solved together (right-hand side j at
+// b + j N, its solution to x + j N): the right-hand sides are copied in and
+// x and the scalars reset, the shared PCG head and while loop run, and the
+// solutions, scalars and true-residual sums are copied out to the history
+// (the last right-hand side's residual history and scalars to the solver's).
+void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
+  if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
+  const long long N = s->lev[0].N;
+  const int np = s->nprob;
+  const RhsSaved saved = save_rhs(s);
+  SkipScope skip(s->rhs.sc);
+  s->any_sc = s->rhs.sc;
+  s->any_n = nrhs * np;
+  cudaGraph_t g = nullptr;
+  try {
+    SSAMG_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    SSAMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* dp = nullptr;
+    size_t ndp = 0;
+    cudaGraph_t tmp;
+    SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < nrhs; ++j) {
+      use_rhs(s, j);
+      SSAMG_CUDA(cudaMemcpyAsync(s->b, b + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                 s->cs));
+      SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+      SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->sc_init, sizeof(PcgScalars) * np,
+                                 cudaMemcpyDeviceToDevice, s->cs));
+    }
+    long long c0 = g_ssamg_launches;
+    enqueue_pcg_head_rhs(s, h, s->cs);
+    s->head_launches = g_ssamg_launches - c0;
+    SSAMG_CUDA(cudaStreamGetCaptureInfo(s->cs, &cst, nullptr, nullptr, &dp, nullptr, &ndp));
+    std::vector<cudaGraphNode_t> tail(dp, dp + ndp);
+    SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    SSAMG_CUDA(cudaGraphAddNode(&cnode, g, tail.data(), nullptr, tail.size(), &cp));
+    SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, cp.conditional.phGraph_out[0], nullptr,
+                                             nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    c0 = g_ssamg_launches;
+    enqueue_pcg_body_rhs(s, h, s->cs);
+    s->body_launches = g_ssamg_launches - c0;
+    SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+    SSAMG_CUDA(cudaStreamBeginCaptureToGraph(s->cs, g, &cnode, nullptr, 1,
+                                             cudaStreamCaptureModeThreadLocal));
+    for (int j = 0; j < nrhs; ++j) {
+      use_rhs(s, j);
+      SSAMG_CUDA(cudaMemcpyAsync(x + j * N, s->x, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                 s->cs));
+      launch_true_residual(s->lev[0], s->b, s->x, s->q, pcg_ctx(s), s->tres_hist + 2ll * j * np,
+                           s->cs);
+      SSAMG_CUDA(cudaMemcpyAsync(s->sc_hist + (long long)j * np, s->sc, sizeof(PcgScalars) * np,
+                                 cudaMemcpyDeviceToDevice, s->cs));
+    }
+    SSAMG_CUDA(cudaMemcpyAsync(saved.hist, s->hist, sizeof(double) * s->rhs.hist_len,
+                               cudaMemcpyDeviceToDevice, s->cs));
+    SSAMG_CUDA(cudaMemcpyAsync(saved.sc, s->sc, sizeof(PcgScalars) * np,
+                               cudaMemcpyDeviceToDevice, s->cs));
+    SSAMG_CUDA(cudaStreamEndCapture(s->cs, &tmp));
+    if (s->graphs.rounds) cudaGraphExecDestroy(s->graphs.rounds);
+    s->graphs.rounds = nullptr;
+    SSAMG_CUDA(cudaGraphInstantiate(&s->graphs.rounds, g, 0));
+  } catch (...) {
+    restore_rhs(s, saved);
+    s->any_sc = nullptr;
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  restore_rhs(s, saved);
+  s->any_sc = nullptr;
+  cudaGraphDestroy(g);
+  s->graphs.rounds_b = b;
+  s->graphs.rounds_x = x;
+  s->graphs.rounds_n = nrhs;
+}
+
 // Solves for nrhs right-hand sides (b, x: nrhs x N, device) in one graph
 // launch; stats (nrhs x nprob) as for run_pcg.  One synchronisation.
 int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_t st,
@@ -2106,8 +2534,14 @@ int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_
     s->graphs.rounds = nullptr;
   }
   if (!s->graphs.rounds || s->graphs.rounds_b != b || s->graphs.rounds_x != x ||
-      s->graphs.rounds_n != nrhs)
-    build_rounds_graph(s, b, x, nrhs);
+      s->graphs.rounds_n != nrhs) {
+    if (nrhs > 1 && s->prm.rhs_together && rhs_together_ok(s)) {
+      alloc_rhs(s, nrhs, st);
+      build_rhs_graph(s, b, x, nrhs);
+    } else {
+      build_rounds_graph(s, b, x, nrhs);
+    }
+  }
   SSAMG_CUDA(cudaGraphLaunch(s->graphs.rounds, st));
   std::vector<PcgScalars> sc((size_t)np * nrhs);
   std::vector<double> tres((size_t)2 * np * nrhs);
@@ -2647,6 +3081,26 @@ double time_kernel_us(ssamg_solver s, int kernel, int level, int reps, cudaStrea
         else
           launch_ctail<double>(s->ctail, s->ctail_nc, s->ctail_smem, (const double*)T0.b,
                                (double*)T0.t, cs);
+        break;
+      }
+      case 11:    // residual of every right-hand side of the last batch solve, one launch
+      case 12: {  // relaxation likewise (cell-tile levels above the tail)
+        const RhsSet& M = s->rhs;
+        if (M.R < 2 || level >= M.nlev || uses_bricks(L))
+          throw SsamgError{SSAMG_ERR_STATE, "no right-hand sides solved together on this level"};
+        const RhsSaved saved = save_rhs(s);
+        SkipScope none(nullptr);
+        use_rhs(s, 0);
+        g_ssamg_skip = nullptr;  // every instance takes part
+        const long long vs = M.stride[level];
+        if (kernel == 11) {
+          if (f) launch_residual_rhs<float>(L, M.R, vs, s->nprob, (const float*)L.x, (const float*)L.b, (float*)L.r, cs);
+          else launch_residual_rhs<double>(L, M.R, vs, s->nprob, (const double*)L.x, (const double*)L.b, (double*)L.r, cs);
+        } else {
+          if (f) launch_relax_rhs<float>(L, M.R, vs, s->nprob, (const float*)L.x, (const float*)L.b, (float*)L.t, cs);
+          else launch_relax_rhs<double>(L, M.R, vs, s->nprob, (const double*)L.x, (const double*)L.b, (double*)L.t, cs);
+        }
+        restore_rhs(s, saved);
         break;
       }
       default:

@@ -8,9 +8,11 @@
 // ... (coalesced).  Large levels use several cells per thread to amortise
 // descriptor staging and FP64 reduction trees; small levels use one, for
 // more warps to hide latency.
-#define TILE_LOOP(c, P)                                                                    \
+#define TILE_LOOP(c, P) TILE_LOOP_AT(c, P, (int)blockIdx.x)
+// The same for tile block B (launches of several right-hand sides).
+#define TILE_LOOP_AT(c, P, B)                                                              \
   _Pragma("unroll 1") for (int c##_m = 0,                                                  \
-       c = ((int)blockIdx.x - (P).blk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;        \
+       c = ((B) - (P).blk0) * (P).cpt * SSAMG_BLOCK + (int)threadIdx.x;                    \
        c##_m < (P).cpt && c < (P).ncell; ++c##_m, c += SSAMG_BLOCK)
 // The same tiles with the SSAMG_CPT_LARGE steps unrolled and predicated, so
 // that a thread issues the loads of all its cells before it consumes the
@@ -336,6 +338,97 @@ __device__ __forceinline__ T apply_A_sh(const LevelView<T>& L, const DPart& p,
   T acc = stencil_sh<SH>(p, L.coef, x, c, i, j, k);
   if (p.has_u > 1 || (p.has_u && !is_interior(p, i, j, k))) acc += L.uy[p.off + c];
   return acc;
+}
+
+// The unchecked shapes for R right-hand sides at once: each stencil
+// coefficient is loaded once and multiplies the R vectors' neighbours (x of
+// right-hand side q at x + q vs); each right-hand side's sum takes the
+// entries in the single form's order, so acc[q] is bitwise what
+// stencil_sh gives for x + q vs.
+template <int K, int R, class T>
+__device__ __forceinline__ void stencil_unchecked_r(const DPart& p, const T* __restrict__ a,
+                                                    const T* __restrict__ xc, long long vs,
+                                                    T* acc) {
+  const int s = p.ncell;
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = (T)0;
+#pragma unroll
+  for (int e = 0; e < K; ++e) {
+    const T ae = a[e * s];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = fma(ae, xc[q * vs + p.disp[e]], acc[q]);
+  }
+}
+
+template <int R, class T>
+__device__ __forceinline__ void stencil27_unchecked_r(const DPart& p, const T* __restrict__ a,
+                                                      const T* __restrict__ xc, long long vs,
+                                                      T* acc) {
+  const int nx = p.n[0], nxy = p.n[0] * p.n[1], s = p.ncell;
+#pragma unroll
+  for (int q = 0; q < R; ++q) acc[q] = (T)0;
+#pragma unroll
+  for (int e = 0; e < 27; ++e) {
+    const int dx = e % 3 - 1, dy = (e / 3) % 3 - 1, dz = e / 9 - 1;
+    const T ae = a[e * s];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] = fma(ae, xc[q * vs + dx + dy * nx + dz * nxy], acc[q]);
+  }
+}
+
+// Shapes with a several-right-hand-side form: every entry per cell.
+__host__ __device__ constexpr bool shape_has_rhs_form(int sh) {
+  return sh == SH_U7 || sh == SH_U15 || sh == SH_C27 || sh == SH_UGEN;
+}
+
+template <int SH, int R, class T>
+__device__ __forceinline__ void stencil_sh_r(const DPart& p, const T* __restrict__ coef,
+                                             const T* __restrict__ x, int c, long long vs,
+                                             T* acc) {
+  const T* xc = x + p.off + c;
+  const T* a = coef + p.coef[0] + c;
+  if constexpr (SH == SH_C27) {
+    stencil27_unchecked_r<R>(p, a, xc, vs, acc);
+  } else if constexpr (SH == SH_U7) {
+    stencil_unchecked_r<7, R>(p, a, xc, vs, acc);
+  } else if constexpr (SH == SH_U15) {
+    stencil_unchecked_r<15, R>(p, a, xc, vs, acc);
+  } else {
+    static_assert(SH == SH_UGEN, "no several-right-hand-side form of this shape");
+    if (p.canon27) {
+      stencil27_unchecked_r<R>(p, a, xc, vs, acc);
+    } else if (p.nent == 15) {
+      stencil_unchecked_r<15, R>(p, a, xc, vs, acc);
+    } else if (p.nent == 7) {
+      stencil_unchecked_r<7, R>(p, a, xc, vs, acc);
+    } else {
+      const int s = p.ncell, n = p.nent;
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc[q] = (T)0;
+#pragma unroll
+      for (int e = 0; e < SSAMG_MAXE; ++e)
+        if (e < n) {
+          const T ae = a[e * s];
+#pragma unroll
+          for (int q = 0; q < R; ++q) acc[q] = fma(ae, xc[q * vs + p.disp[e]], acc[q]);
+        }
+    }
+  }
+}
+
+// (A x_q)(c) for R right-hand sides (x_q = x + q vs, U x_q likewise in uy),
+// each bitwise apply_A_sh's value.
+template <int SH, int R, class T>
+__device__ __forceinline__ void apply_A_sh_r(const LevelView<T>& L, const DPart& p,
+                                             const T* __restrict__ x, int c, long long vs,
+                                             T* acc) {
+  int i = 0, j = 0, k = 0;
+  if (p.has_u) cell_coords(p, c, i, j, k);
+  stencil_sh_r<SH, R>(p, L.coef, x, c, vs, acc);
+  if (p.has_u > 1 || (p.has_u && !is_interior(p, i, j, k))) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] += L.uy[p.off + c + q * vs];
+  }
 }
 
 // (U x)(g) for global cell g (0 when g has no U row).

@@ -82,34 +82,104 @@ __global__ void __launch_bounds__(NT) k_uy(LevelView<T> L, const T* x) {
 }
 
 // r = b - A x
+// (with L.nrhs > 1: that many right-hand sides, the blocks of one tile side
+// by side, so that the tile's coefficients are read from HBM once)
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_residual(LevelView<T> L, const T* x,
                                                     const T* b, T* r) {
   pdl_trigger();
   __shared__ DPart sp;
-  block_part(L.blk, L.parts, L.np, sp);
+  int bid = blockIdx.x, j = 0;
+  if (L.nrhs > 1) {
+    bid = (int)blockIdx.x / L.nrhs;
+    j = (int)blockIdx.x - bid * L.nrhs;
+  }
+  block_part(L.blk, L.parts, L.np, sp, bid);
   __syncthreads();
+  if (j > 0) {
+    const long long o = j * L.vstride;
+    x += o;
+    b += o;
+    r += o;
+    if (L.uy) L.uy += o;
+  }
   pdl_wait();
-  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
-  TILE_LOOP(c, sp) {
+  if (L.skip && L.skip[sp.prob + j * L.skip_stride].done) return;  // problem already stopped
+  TILE_LOOP_AT(c, sp, bid) {
     const int g = sp.off + c;
     r[g] = b[g] - apply_A_sh<SH>(L, sp, x, c);
   }
 }
 
 // xo = x + omega M^-1 (b - A x)
+// (several right-hand sides per launch as k_residual)
 template <class T, int SH>
 __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* x,
                                                  const T* b, T* xo) {
   pdl_trigger();
   __shared__ DPart sp;
+  int bid = blockIdx.x, j = 0;
+  if (L.nrhs > 1) {
+    bid = (int)blockIdx.x / L.nrhs;
+    j = (int)blockIdx.x - bid * L.nrhs;
+  }
+  block_part(L.blk, L.parts, L.np, sp, bid);
+  __syncthreads();
+  if (j > 0) {
+    const long long o = j * L.vstride;
+    x += o;
+    b += o;
+    xo += o;
+    if (L.uy) L.uy += o;
+  }
+  pdl_wait();
+  if (L.skip && L.skip[sp.prob + j * L.skip_stride].done) return;  // problem already stopped
+  TILE_LOOP_AT(c, sp, bid) {
+    const int g = sp.off + c;
+    xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
+  }
+}
+
+// r = b - A x and xo = x + omega M^-1 (b - A x) for R right-hand sides per
+// thread (shapes with every entry per cell): the coefficients of a cell are
+// loaded once for all of them.  Right-hand side q's vectors (and U x) lie
+// q L.vstride elements after the first's, its scalars q L.skip_stride after
+// the first's; a right-hand side whose problem has stopped is not written.
+// (blocks per SM: the general shape's per-part dispatch and the FP64 forms
+// need 64 registers to run without spilling, the fixed FP32 shapes fit in
+// 48; measured on the batched workload's levels)
+template <class T, int SH>
+constexpr int rhs_min_blocks() {
+  return (SH == SH_UGEN || sizeof(T) == 8) ? 4 : 5;
+}
+template <class T, int SH, int R, bool RELAX>
+__global__ void __launch_bounds__(NT, rhs_min_blocks<T, SH>()) k_cycle_r(LevelView<T> L, const T* x, const T* b,
+                                                   T* out) {
+  pdl_trigger();
+  __shared__ DPart sp;
   block_part(L.blk, L.parts, L.np, sp);
   __syncthreads();
   pdl_wait();
-  if (L.skip && L.skip[sp.prob].done) return;  // problem already stopped
+  const long long vs = L.vstride;
+  unsigned act = 0;
+#pragma unroll
+  for (int q = 0; q < R; ++q)
+    if (!L.skip || !L.skip[sp.prob + q * L.skip_stride].done) act |= 1u << q;
+  if (!act) return;  // every right-hand side of the problem stopped
   TILE_LOOP(c, sp) {
     const int g = sp.off + c;
-    xo[g] = fma(L.dinv[g], b[g] - apply_A_sh<SH>(L, sp, x, c), x[g]);
+    T acc[R];
+    apply_A_sh_r<SH, R>(L, sp, x, c, vs, acc);
+    const T dv = RELAX ? L.dinv[g] : (T)0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (!((act >> q) & 1u)) continue;
+      const long long o = g + q * vs;
+      if (RELAX)
+        out[o] = fma(dv, b[o] - acc[q], x[o]);
+      else
+        out[o] = b[o] - acc[q];
+    }
   }
 }
 
@@ -1392,7 +1462,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* partial,
                                                        const int* pb, PcgScalars* sc,
                                                        PcgCtl* ctl, cudaGraphConditionalHandle h,
                                                        int use_handle, double* hist,
-                                                       int hstride) {
+                                                       int hstride, const PcgScalars* any_sc,
+                                                       int any_n) {
   pdl_trigger();
   pdl_wait();
   __shared__ double out[1];
@@ -1415,9 +1486,11 @@ __global__ void __launch_bounds__(NT) k_pcg_update_fin(const double* partial,
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
+    // any problem of any right-hand side solved together (the last
+    // right-hand side's launch sees them all updated and decides)
     int active = 0;
-    for (int q = 0; q < (int)gridDim.x; ++q)
-      active |= !*reinterpret_cast<volatile const int*>(&sc[q].done);
+    for (int q = 0; q < any_n; ++q)
+      active |= !*reinterpret_cast<volatile const int*>(&any_sc[q].done);
     ctl->ticket = 0;
     ctl->active = active;
     set_continue(active, h, use_handle);
@@ -1565,6 +1638,14 @@ void launch_relax0_u(const Level& L, const T* b, T* x, cudaStream_t st) {
   launch_k(k_relax0_u<T>, nb + L.nublk, NT, 0, st, L.view<T>(), nb, b, x);
   SSAMG_LAUNCH_CHECK();
 }
+// one group of g right-hand sides (g = 1 .. SSAMG_RHS_GROUP) of shape SHC
+#define RHS_GROUP_LAUNCH(SHC)                                                               \
+  switch (g) {                                                                             \
+    case 1: launch_k(k_cycle_r<T, SHC, 1, RELAX>, L.nblk, NT, 0, st, v, xg, bg, og); break; \
+    case 2: launch_k(k_cycle_r<T, SHC, 2, RELAX>, L.nblk, NT, 0, st, v, xg, bg, og); break; \
+    case 3: launch_k(k_cycle_r<T, SHC, 3, RELAX>, L.nblk, NT, 0, st, v, xg, bg, og); break; \
+    default: launch_k(k_cycle_r<T, SHC, 4, RELAX>, L.nblk, NT, 0, st, v, xg, bg, og); break; \
+  }
 #define SH_DISPATCH(shape, KCALL)                         \
   switch (shape) {                                        \
     case SH_U7: { constexpr int SHV = SH_U7; KCALL; } break;   \
@@ -1629,6 +1710,57 @@ void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st
   else
     SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk, NT, 0, st, L.view<T>(), x, b, xo)));
   SSAMG_LAUNCH_CHECK();
+}
+// R right-hand sides (cell-tile levels only): vectors and U x of right-hand
+// side j at + j vstride, its scalars at skip + j skip_stride.  Shapes with
+// every entry per cell take up to SSAMG_RHS_GROUP right-hand sides per thread
+// (one launch per group); the others one launch with R blocks per tile, side
+// by side, so that a tile's coefficients come from HBM once.
+template <class T, bool RELAX>
+void launch_cycle_rhs(const Level& L, int R, long long vstride, int skip_stride, const T* x,
+                      const T* b, T* out, cudaStream_t st) {
+  if (shape_has_rhs_form(L.shape)) {
+    for (int j0 = 0; j0 < R; j0 += SSAMG_RHS_GROUP) {
+      const int g = std::min(SSAMG_RHS_GROUP, R - j0);
+      LevelView<T> v = L.view<T>();
+      v.vstride = vstride;
+      v.skip_stride = skip_stride;
+      const long long o = (long long)j0 * vstride;
+      if (v.uy) v.uy += o;
+      if (v.skip) v.skip += (long long)j0 * skip_stride;
+      const T* xg = x + o;
+      const T* bg = b + o;
+      T* og = out + o;
+      switch (L.shape) {
+        case SH_U7: RHS_GROUP_LAUNCH(SH_U7); break;
+        case SH_U15: RHS_GROUP_LAUNCH(SH_U15); break;
+        case SH_C27: RHS_GROUP_LAUNCH(SH_C27); break;
+        default: RHS_GROUP_LAUNCH(SH_UGEN); break;
+      }
+      SSAMG_LAUNCH_CHECK();
+    }
+    return;
+  }
+  LevelView<T> v = L.view<T>();
+  v.nrhs = R;
+  v.vstride = vstride;
+  v.skip_stride = skip_stride;
+  if constexpr (RELAX) {
+    SH_DISPATCH(L.shape, (launch_k(k_relax<T, SHV>, L.nblk * R, NT, 0, st, v, x, b, out)));
+  } else {
+    SH_DISPATCH(L.shape, (launch_k(k_residual<T, SHV>, L.nblk * R, NT, 0, st, v, x, b, out)));
+  }
+  SSAMG_LAUNCH_CHECK();
+}
+template <class T>
+void launch_residual_rhs(const Level& L, int R, long long vstride, int skip_stride, const T* x,
+                         const T* b, T* r, cudaStream_t st) {
+  launch_cycle_rhs<T, false>(L, R, vstride, skip_stride, x, b, r, st);
+}
+template <class T>
+void launch_relax_rhs(const Level& L, int R, long long vstride, int skip_stride, const T* x,
+                      const T* b, T* xo, cudaStream_t st) {
+  launch_cycle_rhs<T, true>(L, R, vstride, skip_stride, x, b, xo, st);
 }
 template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, T* xc, cudaStream_t st) {
@@ -1756,6 +1888,10 @@ void launch_coarse_inverse(int n, const double* Lfac, double* inv, cudaStream_t 
   template void launch_coarse_apply<T>(int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_residual<T>(const Level&, const T*, const T*, T*, cudaStream_t);    \
   template void launch_relax<T>(const Level&, const T*, const T*, T*, cudaStream_t);       \
+  template void launch_residual_rhs<T>(const Level&, int, long long, int, const T*, const T*, \
+                                       T*, cudaStream_t);                                    \
+  template void launch_relax_rhs<T>(const Level&, int, long long, int, const T*, const T*,    \
+                                    T*, cudaStream_t);                                       \
   template void launch_restrict<T>(const Level&, const Level&, const T*, T*, T*, cudaStream_t); \
   template void launch_prolong<T>(const Level&, const Level&, const T*, T*, cudaStream_t);  \
   template void launch_coarse_solve<T>(int, const double*, const T*, T*, cudaStream_t);
@@ -1842,7 +1978,7 @@ void launch_pcg_update(const Level& L0, const double* p, const double* q, double
   launch_k(k_pcg_update, L0.nblk, NT, 0, st, L0.view<double>(), p, q, x, r, c.partial, c.sc);
   SSAMG_LAUNCH_CHECK();
   launch_k(k_pcg_update_fin, c.nprob, NT, 0, st, c.partial, c.pb, c.sc, c.ctl, h, use_handle,
-           c.hist, c.hstride);
+           c.hist, c.hstride, (const PcgScalars*)c.any_sc, c.any_n);
   SSAMG_LAUNCH_CHECK();
 }
 

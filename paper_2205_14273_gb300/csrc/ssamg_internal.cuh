@@ -25,6 +25,8 @@
 #define SSAMG_MAXE 27
 #define SSAMG_BLOCK 256
 #define SSAMG_DINV_LEVELS 32  // levels per launch of the smoother-diagonal kernel
+#define SSAMG_RHS_GROUP 4  // right-hand sides one thread of the several-right-hand-side cycle kernels takes
+#define SSAMG_HOST_THREADS 16  // host threads of the coupling conversion of one call
 #define SSAMG_MAX_PART_BOXES 16  // boxes of one part (ssamg_grid_add_box)
 #define SSAMG_CPT_LARGE 4         // cells per thread on large levels
 #define SSAMG_CPT_MIN_CELLS 300000  // levels smaller than this use one cell per thread
@@ -141,6 +143,10 @@ struct PcgCtx {
   double* partial;
   double* hist;    // per problem ||r_k||^2, k = 0..hstride-1 (residual history)
   int hstride;
+  // the scalars whose done flags decide whether the solve goes on: sc and
+  // nprob, or those of every right-hand side solved together
+  const PcgScalars* any_sc;
+  int any_n;
 };
 
 // Views passed to kernels by value.
@@ -174,6 +180,13 @@ struct LevelView {
   // inside a PCG solve: the problems' scalars; a block of a problem whose
   // iteration has stopped leaves its cycle work undone (nothing reads it)
   const PcgScalars* skip;
+  // right-hand sides one launch takes together (1 elsewhere): block b works
+  // on tile b / nrhs for right-hand side j = b % nrhs, whose vectors and U x
+  // lie vstride elements after those of j - 1 and whose scalars skip_stride
+  // entries after them
+  int nrhs;
+  int skip_stride;
+  long long vstride;
 };
 
 // One level of the fused coarse tail: the level's view and its cycle vectors.
@@ -328,13 +341,13 @@ template <>
 inline LevelView<double> Level::view<double>() const {
   return LevelView<double>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef, dinv, Pw, Pe,
                            u_map, u_ptr, u_col, u_val, u_bits, u_rows, u_pj, u_pw, u_rj, u_rw, uy64, nr,
-                           nublk, tpr, g_ssamg_skip};
+                           nublk, tpr, g_ssamg_skip, 1, 0, 0};
 }
 template <>
 inline LevelView<float> Level::view<float>() const {
   return LevelView<float>{d_parts, d_blk, d_bblk, d_fblk, d_cellstart, np, (int)N, coef32, dinv32, Pw32,
                           Pe32, u_map, u_ptr, u_col, u_val32, u_bits, u_rows, u_pj, u_pw32, u_rj,
-                          u_rw32, uy32, nr, nublk, tpr, g_ssamg_skip};
+                          u_rw32, uy32, nr, nublk, tpr, g_ssamg_skip, 1, 0, 0};
 }
 
 struct SsamgError {
@@ -470,6 +483,13 @@ template <class T>
 void launch_residual(const Level& L, const T* x, const T* b, T* r, cudaStream_t st);
 template <class T>
 void launch_relax(const Level& L, const T* x, const T* b, T* xo, cudaStream_t st);
+// the same for R right-hand sides in one launch (cell-tile levels only)
+template <class T>
+void launch_residual_rhs(const Level& L, int R, long long vstride, int skip_stride, const T* x,
+                         const T* b, T* r, cudaStream_t st);
+template <class T>
+void launch_relax_rhs(const Level& L, int R, long long vstride, int skip_stride, const T* x,
+                      const T* b, T* xo, cudaStream_t st);
 template <class T>
 void launch_restrict(const Level& F, const Level& Cl, const T* r, T* bc, T* xc, cudaStream_t st);
 template <class T>

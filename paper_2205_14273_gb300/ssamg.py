@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
                 ("coarse_direct", ctypes.c_int), ("flexible", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("use_tail", ctypes.c_int),
                 ("use_pdl", ctypes.c_int), ("tail_cells", ctypes.c_int),
-                ("use_bricks", ctypes.c_int)]
+                ("use_bricks", ctypes.c_int), ("rhs_together", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

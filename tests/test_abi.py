@@ -83,6 +83,46 @@ def test_matrix_and_coupling_validation(ssamg_lib):
     L.ssamg_grid_destroy(g)
 
 
+def test_large_coupling_calls_split_over_threads(ssamg_lib):
+    """A call of many couplings is converted in chunks on host threads: a
+    valid call is accepted whole, one invalid coupling deep inside a large
+    call rejects all of it, and the matrix takes later calls as before."""
+    S = ssamg_lib
+    L = S.lib()
+    g, _ = _grid(S, 3, [((0, 0, 0), (15, 15, 15)), ((16, 0, 0), (31, 15, 15))])
+    assert L.ssamg_grid_assemble(g) == 0
+    A = ctypes.c_void_p()
+    offs = [0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1]
+    assert L.ssamg_matrix_create(g, 7, S._ints(offs), ctypes.byref(A)) == 0
+    # the +x face of part 0 against the -x face of part 1, repeated (repeats
+    # are summed at assembly): 40,960 couplings
+    j, k = np.meshgrid(np.arange(16), np.arange(16), indexing="ij")
+    face = np.stack([np.full(256, 15), j.ravel(), k.ravel()], 1)
+    idx = np.tile(face, (160, 1)).astype(np.int32)
+    n = len(idx)
+    nidx = idx.copy()
+    nidx[:, 0] = 16
+    part = np.zeros(n, np.int32)
+    nbor = np.ones(n, np.int32)
+    d = np.tile(np.array([[1, 0, 0]], np.int32), (n, 1))
+    v = np.full(n, -0.25)
+
+    def add(idx_, d_):
+        return L.ssamg_matrix_add_couplings(
+            A, n, S._ints(part), S._ints(idx_.ravel()), S._ints(d_.ravel()), S._ints(nbor),
+            S._ints(nidx.ravel()), v.ctypes.data_as(S._dp))
+    assert add(idx, d) == 0
+    bad = idx.copy()
+    bad[n - 900, 0] = 14  # leaves through +x but is not on that face
+    assert add(bad, d) == S.ERR_ARG
+    bad_dir = d.copy()
+    bad_dir[7] = (2, 0, 0)  # direction components are -1, 0 or 1
+    assert add(idx, bad_dir) == S.ERR_ARG
+    assert add(idx, d) == 0
+    L.ssamg_matrix_destroy(A)
+    L.ssamg_grid_destroy(g)
+
+
 def test_solver_state_errors(ssamg_lib):
     S = ssamg_lib
     L = S.lib()

@@ -134,3 +134,36 @@ def test_batch_one_graph_matches_host_loop(S):
         res.append((its, x.cpu().numpy()))
     assert res[0][0] == res[1][0]
     assert np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("prec,use_tail,bricks,kind", [
+    (1, 3, 1, "7pt"), (0, 3, 1, "7pt"), (1, 0, 1, "7pt"), (1, 3, 0, "7pt"),
+    (0, 0, 0, "7pt"), (1, 3, 1, "27pt"), (0, 0, 1, "27pt"), (1, 2, 1, "7pt")])
+def test_rhs_together_matches_one_after_another(S, prec, use_tail, bricks, kind):
+    """Right-hand sides solved in one PCG loop (the residual and relaxation
+    of cell-tile levels taking all of them per launch) give each right-hand
+    side's one-after-another results bitwise: solutions, iteration counts,
+    residuals and the last right-hand side's residual history."""
+    if kind == "7pt":
+        probs = P.batched(nprob=4, nrhs=3, seed=17, pmax=3, emin=4, emax=12)
+    else:
+        probs = [P.var27(n=n, block=3, seed=20 + n, nrhs=3) for n in (7, 9, 6)]
+    res = []
+    for together in (1, 0):
+        _, B = make_batch(S, probs, precision=prec, flexible=prec, use_tail=use_tail,
+                          tail_cells=256, use_bricks=bricks, rhs_together=together)
+        off = B.offsets()
+        b = torch.as_tensor(stack_rhs(probs, off, 3), device="cuda").contiguous()
+        x = torch.zeros_like(b)
+        st = B.solve(b, x, 3)
+        its = [[(s.iterations, s.rel_res, s.true_rel_res) for s in row] for row in st]
+        hist = [B.solver().residual_history(k) for k in range(len(probs))]
+        res.append((its, x.cpu().numpy(), hist, st[0][0].solve_kernel_launches))
+    # together, one loop enqueues every right-hand side's steps (a fused
+    # single-CTA tail, where the batch has one, takes them one after another)
+    if use_tail != 2:
+        assert res[0][3] > res[1][3]
+    assert res[0][0] == res[1][0]
+    assert np.array_equal(res[0][1], res[1][1])
+    for h0, h1 in zip(res[0][2], res[1][2]):
+        assert np.array_equal(h0, h1)
