@@ -145,12 +145,13 @@ __global__ void __launch_bounds__(NT, 4) k_relax(LevelView<T> L, const T* x,
 // loaded once for all of them.  Right-hand side q's vectors (and U x) lie
 // q L.vstride elements after the first's, its scalars q L.skip_stride after
 // the first's; a right-hand side whose problem has stopped is not written.
-// (blocks per SM: the general shape's per-part dispatch and the FP64 forms
-// need 64 registers to run without spilling, the fixed FP32 shapes fit in
-// 48; measured on the batched workload's levels)
+// (blocks per SM, measured on the batched workload's levels with four
+// right-hand sides: the fixed shapes run best with 64 registers, 4 blocks;
+// the general shape's per-part dispatch with 48, 5 blocks, although it then
+// spills a few words: 729 vs 921 us on a 15-point level of 18M cells)
 template <class T, int SH>
 constexpr int rhs_min_blocks() {
-  return (SH == SH_UGEN || sizeof(T) == 8) ? 4 : 5;
+  return (SH == SH_UGEN && sizeof(T) == 4) ? 5 : 4;
 }
 template <class T, int SH, int R, bool RELAX>
 __global__ void __launch_bounds__(NT, rhs_min_blocks<T, SH>()) k_cycle_r(LevelView<T> L, const T* x, const T* b,
