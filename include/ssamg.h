@@ -165,7 +165,8 @@ typedef struct {
                           levels, which take every right-hand side in one launch (the blocks
                           of a tile side by side, so its stencil coefficients are read from
                           HBM once); 0: the right-hand sides one after another in one graph.
-                          Both give the same results; use_tail 1 or 2 always takes 0 */
+                          Both give the same results; a hierarchy with the fused tail of
+                          use_tail 1 or 2 always takes 0 */
 } ssamg_params;
 
 typedef struct {

@@ -317,7 +317,8 @@ struct GraphSet {
 // block-partial buffer, the problems' scalars (contiguous: right-hand side
 // j's at sc + j nprob) and a residual history.
 struct RhsSet {
-  int R = 0;
+  int R = 0;                          // right-hand sides of the current solve
+  int cap = 0;                        // slices allocated (>= R)
   int nlev = 0;                       // levels 0..nlev-1 carry slices
   std::vector<long long> stride;      // per level, elements between slices
   std::vector<char*> x, b, r, t;      // per level: the first slice
@@ -2173,16 +2174,20 @@ struct RhsSaved {
   std::vector<double*> uy64;
 };
 
-// Slices for R right-hand sides (kept until the next set-up); zeroed on st.
+// Slices for R right-hand sides (kept until the next set-up, and reused by
+// solves of as many right-hand sides or fewer); zeroed on st.
 void alloc_rhs(ssamg_solver s, int R, cudaStream_t st) {
   RhsSet& M = s->rhs;
-  if (M.R == R) return;
+  if (M.cap >= R) {
+    M.R = R;
+    return;
+  }
   const bool fp32 = s->prm.precision == 1;
   const size_t w = fp32 ? sizeof(float) : sizeof(double);
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   auto slab = [](long long n, long long guard) { return (n + 2 * guard + 63) / 64 * 64; };
   RhsSet N;
-  N.R = R;
+  N.R = N.cap = R;
   N.nlev = cycle_tail_level(s) + 1;
   N.stride.resize(N.nlev);
   size_t total = 0;
