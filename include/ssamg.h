@@ -195,8 +195,10 @@ int ssamg_setup(ssamg_solver s, ssamg_matrix A, void* stream);
 
 /* PCG preconditioned by one V(1,1) cycle (Section 4), x0 = 0 when
  * zero_guess != 0, else x holds x0.  b, x: device, nrhs vectors of N
- * doubles each (solved one after another).  Stops at
- * ||r|| <= tol ||b||.  st may be NULL (stats of the last right-hand side). */
+ * doubles each.  With use_graph and nrhs > 1, all right-hand sides run in
+ * one graph launch as ssamg_batch_solve runs them (rhs_together); else one
+ * after another.  Stops at ||r|| <= tol ||b||.  st may be NULL (stats of
+ * the last right-hand side). */
 int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess,
                 void* stream, ssamg_stats* st);
 /* Same as ssamg_solve with host b and x; the copies are part of the call. */

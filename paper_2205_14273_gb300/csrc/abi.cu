@@ -299,6 +299,7 @@ struct GraphSet {
   const double* rounds_b = nullptr;   // the user vectors baked into `rounds`
   double* rounds_x = nullptr;
   int rounds_n = 0;
+  int rounds_zero = 1;                // 1: x0 = 0 baked in, 0: x0 read from x
   void reset() {
     if (pcg) cudaGraphExecDestroy(pcg);
     if (vcycle) cudaGraphExecDestroy(vcycle);
@@ -2080,7 +2081,7 @@ int worst_status(ssamg_solver s, const PcgScalars* sc) {
 // solution to x + j N): per round, the right-hand side is copied in, x and
 // the scalars reset, the PCG head and its while loop run, and the solution,
 // the scalars and the true-residual sums are copied out to the history.
-void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
+void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess) {
   if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
   const long long N = s->lev[0].N;
   const int np = s->nprob;
@@ -2106,7 +2107,11 @@ void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
     SSAMG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
     begin(g, deps);
     SSAMG_CUDA(cudaMemcpyAsync(s->b, b + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->cs));
-    SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+    if (zero_guess)
+      SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+    else
+      SSAMG_CUDA(cudaMemcpyAsync(s->x, x + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                 s->cs));
     SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->sc_init, sizeof(PcgScalars) * np, cudaMemcpyDeviceToDevice,
                                s->cs));
     long long c0 = g_ssamg_launches;
@@ -2140,6 +2145,7 @@ void build_rounds_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
   s->graphs.rounds_b = b;
   s->graphs.rounds_x = x;
   s->graphs.rounds_n = nrhs;
+  s->graphs.rounds_zero = zero_guess;
 }
 
 // ---- Right-hand sides solved together --------------------------------------
@@ -2442,7 +2448,7 @@ void enqueue_pcg_body_rhs(ssamg_solver s, cudaGraphConditionalHandle h, cudaStre
 // x and the scalars reset, the shared PCG head and while loop run, and the
 // solutions, scalars and true-residual sums are copied out to the history
 // (the last right-hand side's residual history and scalars to the solver's).
-void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
+void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs, int zero_guess) {
   if (!s->cs) SSAMG_CUDA(cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking));
   const long long N = s->lev[0].N;
   const int np = s->nprob;
@@ -2465,7 +2471,11 @@ void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
       use_rhs(s, j);
       SSAMG_CUDA(cudaMemcpyAsync(s->b, b + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
                                  s->cs));
-      SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+      if (zero_guess)
+        SSAMG_CUDA(cudaMemsetAsync(s->x, 0, sizeof(double) * N, s->cs));
+      else
+        SSAMG_CUDA(cudaMemcpyAsync(s->x, x + j * N, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                   s->cs));
       SSAMG_CUDA(cudaMemcpyAsync(s->sc, s->sc_init, sizeof(PcgScalars) * np,
                                  cudaMemcpyDeviceToDevice, s->cs));
     }
@@ -2519,12 +2529,13 @@ void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs) {
   s->graphs.rounds_b = b;
   s->graphs.rounds_x = x;
   s->graphs.rounds_n = nrhs;
+  s->graphs.rounds_zero = zero_guess;
 }
 
 // Solves for nrhs right-hand sides (b, x: nrhs x N, device) in one graph
 // launch; stats (nrhs x nprob) as for run_pcg.  One synchronisation.
 int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_t st,
-               ssamg_stats* stats) {
+               ssamg_stats* stats, int zero_guess = 1) {
   const int np = s->nprob;
   if (s->hist_cap < nrhs) {
     if (s->sc_hist) cudaFree(s->sc_hist);
@@ -2539,12 +2550,12 @@ int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_
     s->graphs.rounds = nullptr;
   }
   if (!s->graphs.rounds || s->graphs.rounds_b != b || s->graphs.rounds_x != x ||
-      s->graphs.rounds_n != nrhs) {
+      s->graphs.rounds_n != nrhs || s->graphs.rounds_zero != zero_guess) {
     if (nrhs > 1 && s->prm.rhs_together && rhs_together_ok(s)) {
       alloc_rhs(s, nrhs, st);
-      build_rhs_graph(s, b, x, nrhs);
+      build_rhs_graph(s, b, x, nrhs, zero_guess);
     } else {
-      build_rounds_graph(s, b, x, nrhs);
+      build_rounds_graph(s, b, x, nrhs, zero_guess);
     }
   }
   SSAMG_CUDA(cudaGraphLaunch(s->graphs.rounds, st));
@@ -2555,6 +2566,14 @@ int run_rounds(ssamg_solver s, const double* b, double* x, int nrhs, cudaStream_
   SSAMG_CUDA(cudaMemcpyAsync(tres.data(), s->tres_hist, sizeof(double) * 2 * np * nrhs,
                              cudaMemcpyDeviceToHost, st));
   SSAMG_CUDA(cudaStreamSynchronize(st));
+  if (s->tail_bar) {
+    SSAMG_CUDA(cudaMemcpyAsync(s->h_int, &s->tail_bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SSAMG_CUDA(cudaStreamSynchronize(st));
+    if (s->h_int[0]) {
+      SSAMG_CUDA(cudaMemsetAsync(&s->tail_bar->err, 0, sizeof(int), st));
+      throw SsamgError{SSAMG_ERR_TIMEOUT, "a grid barrier of the coarse-level kernel timed out"};
+    }
+  }
   int rc = SSAMG_OK;
   for (int j = 0; j < nrhs; ++j) {
     if (stats) fill_stats(s, stats + (long long)j * np, sc.data() + (long long)j * np,
@@ -2635,6 +2654,13 @@ extern "C" int ssamg_solve(ssamg_solver s, const double* b, double* x, int nrhs,
   cudaStream_t cst = (cudaStream_t)stream;
   API_BEGIN
   PdlScope pdl(s->prm);
+  if (nrhs > 1 && s->prm.use_graph) {
+    // every right-hand side in one graph launch; st: the last one's stats
+    std::vector<ssamg_stats> all(st ? (size_t)nrhs * s->nprob : 0);
+    const int r = run_rounds(s, b, x, nrhs, cst, st ? all.data() : nullptr, zero_guess ? 1 : 0);
+    if (st) std::copy(all.end() - s->nprob, all.end(), st);
+    return r;
+  }
   long long N = s->lev[0].N;
   int rc = SSAMG_OK;
   for (int k = 0; k < nrhs; ++k) {

@@ -586,3 +586,33 @@ def test_residual_history_matches_oracle(S, prob):
     h = np.array(ref.history)
     assert np.all(np.abs(hist - h) <= 1e-9 * h + 1e-300)
     assert S.lib().ssamg_residual_history(sv.h, 1, None, 4) == S.ERR_ARG
+
+
+@pytest.mark.parametrize("kind", ["27pt", "7pt"])
+def test_solve_several_rhs_one_graph(S, kind):
+    """ssamg_solve with several right-hand sides runs them in one graph
+    launch (together where the hierarchy allows it), from zero or from given
+    initial guesses: each solution bitwise that of its own solve, and within
+    1e-9 of the oracle's."""
+    if kind == "27pt":
+        prob = P.var27(n=24, block=4, seed=31, nrhs=3)
+    else:
+        prob = P.multipart_aniso(m=16, layout=(2, 1, 2), seed=5, nrhs=3)
+    grid, A, solver = gpu_setup(S, prob, precision=1, flexible=1, tol=1e-12)
+    n = prob.n
+    bt = torch.as_tensor(np.ascontiguousarray(prob.b.reshape(-1)), device="cuda")
+    x0 = torch.as_tensor(P.SplitMix64(9).uniform_pm1(3 * n) * 1e-2, device="cuda")
+    for zero in (True, False):
+        x = torch.zeros_like(bt) if zero else x0.clone()
+        st = solver.solve(bt, x, nrhs=3, zero_guess=zero)
+        assert st.converged
+        for k in range(3):
+            xk = torch.zeros(n, dtype=torch.float64, device="cuda") if zero \
+                else x0[k * n:(k + 1) * n].clone()
+            sk = solver.solve(bt[k * n:(k + 1) * n].contiguous(), xk, zero_guess=zero)
+            assert torch.equal(x[k * n:(k + 1) * n], xk), (zero, k)
+        assert sk.iterations == st.iterations  # the last right-hand side's stats
+    h = O.setup(prob)
+    for k in range(3):
+        ref = O.pcg(h, prob.b[k], tol=1e-12).x
+        assert rel(x[k * n:(k + 1) * n].cpu().numpy(), ref) <= 1e-9
