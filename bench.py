@@ -43,6 +43,9 @@ WORKLOAD = "8 parts x 64^3 (2x2x2 layout), 7-pt anisotropic diffusion, seed 1"
 L2_BYTES = 129 * 2 ** 20
 # FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64-pipe instructions per cell of dL/dg (exp(g), then six faces with a
+# division each), counted by ncu on the 128^3 case
+FP64_INSTS_PER_CELL_DG = 15 + 102
 
 
 def max_over_ranks(value, ws, device=None):
@@ -788,7 +791,15 @@ def differentiation_workload(S, stream, peak):
             "adjoint_solve_ms": round(t[2], 3), "gradient_ms": round(t[3], 3),
             "forward_iterations": st_f.iterations, "adjoint_iterations": st_a.iterations,
             "mdof_s": round(N / (sum(t) * 1e-3) / 1e6, 3),
-            "k_diffusion_exp_gradient": {"us": round(us_dg, 2), "frac_hbm": frac(32 * N, us_dg)},
+            "k_diffusion_exp_gradient": {
+                "us": round(us_dg, 2), "frac_hbm": frac(32 * N, us_dg),
+                # bound by the FP64 pipe: FP64-pipe instructions per cell
+                # counted by ncu (15 in k_exp, 102 in the gradient kernel)
+                # against 2 per SM per clock (152 SMs, 2.07 GHz)
+                "bound": "fp64",
+                "fp64_pipe_insts_per_cell": FP64_INSTS_PER_CELL_DG,
+                "frac_fp64_pipe": round(FP64_INSTS_PER_CELL_DG * N / (us_dg * 1e-6)
+                                        / (FP64_PEAK_TFLOPS * 1e12 / 2), 3)},
             "k_coef_gradient": {"us": round(us_dc, 2), "frac_hbm": frac(72 * N, us_dc)},
             "_x": x.cpu().numpy(), "_dg": dg.cpu().numpy()}
 
@@ -1070,6 +1081,25 @@ def run_profile_case(args):
     import torch
 
     from paper_2205_14273_gb300 import ssamg as S
+    if args.profile_case == "diffusion-128":
+        # the differentiation workload's gradient kernels (FP64, 128^3):
+        # forward and adjoint solve, then dL/dg three times
+        prob = P.config(4)
+        grid, A = S.matrix_from_problem(prob)
+        sv = S.Solver(tol=1e-8, max_iter=500, use_graph=0)
+        sv.setup(A)
+        b = torch.as_tensor(prob.b[0], device="cuda")
+        x = torch.zeros_like(b)
+        lam = torch.zeros_like(b)
+        dg = torch.zeros_like(b)
+        sv.solve(b, x)
+        sv.adjoint_solve(x - torch.as_tensor(prob.extra["x_t"], device="cuda"), lam)
+        g = torch.as_tensor(prob.extra["g"].reshape(-1), device="cuda")
+        for _ in range(3):
+            sv.diffusion_exp_gradient(g, lam, x, dg)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "cells": prob.n}))
+        return
     rng = P.SplitMix64(5)
     a = rng.log_uniform(6, 1e-3, 1.0).reshape(2, 3)
     prob = P.chain_aniso([200, 200], a, rng, 1)
@@ -1101,11 +1131,13 @@ def main():
                     help="launch the solve kernels directly (profilers cannot see kernel "
                          "nodes of graphs with conditional nodes)")
     ap.add_argument("--only", choices=["fp32_cycle", "fp64"], default=None)
-    ap.add_argument("--profile-case", choices=["level0-16M"], default=None,
+    ap.add_argument("--profile-case", choices=["level0-16M", "diffusion-128"], default=None,
                     help="run a fixed small case for profiler captures instead of the bench: "
                          "level0-16M = two chained 200^3 parts (16M cells, constant anisotropic "
                          "7-point off-diagonals, per-cell diagonal), FP32 cycle, setup, "
-                         "three V-cycles and three flexible PCG iterations")
+                         "three V-cycles and three flexible PCG iterations; diffusion-128 = the "
+                         "128^3 differentiation workload, forward and adjoint solve, three "
+                         "dL/dg evaluations")
     ap.add_argument("--no-extra-workloads", action="store_true",
                     help="skip the 256^3 27-point and 64-problem batched measurements")
     ap.add_argument("--autotune", action="store_true",
