@@ -2518,6 +2518,13 @@ void build_rhs_graph(ssamg_solver s, const double* b, double* x, int nrhs, int z
     s->graphs.rounds = nullptr;
     SSAMG_CUDA(cudaGraphInstantiate(&s->graphs.rounds, g, 0));
   } catch (...) {
+    // leave the capture stream usable: end a capture the error interrupted
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t part = nullptr;
+      cudaStreamEndCapture(s->cs, &part);
+      if (part) cudaGraphDestroy(part);
+    }
     restore_rhs(s, saved);
     s->any_sc = nullptr;
     if (g) cudaGraphDestroy(g);

@@ -131,6 +131,9 @@ def test_solver_state_errors(ssamg_lib):
     h = ctypes.c_void_p()
     bad = S.default_params(precision=2)
     assert L.ssamg_solver_create(ctypes.byref(bad), ctypes.byref(h)) == S.ERR_ARG
+    assert p.rhs_together == 1
+    bad = S.default_params(rhs_together=2)
+    assert L.ssamg_solver_create(ctypes.byref(bad), ctypes.byref(h)) == S.ERR_ARG
     assert L.ssamg_solver_create(ctypes.byref(p), ctypes.byref(h)) == 0
     x = ctypes.c_void_p(16)
     assert L.ssamg_solve(h, x, x, 1, 1, None, None) == S.ERR_STATE
