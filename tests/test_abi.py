@@ -192,6 +192,36 @@ def test_binding_constants_match_the_header(ssamg_lib):
         assert getattr(S, name[len("SSAMG_"):]) == int(value), name
 
 
+def _header_struct(txt, name):
+    """(type, field) pairs of `typedef struct { ... } name;` in the header,
+    comments removed."""
+    import re
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", txt).group(1)
+    fields = []
+    for decl in body.split(";"):
+        words = decl.split()
+        if words:
+            fields.append((" ".join(words[:-1]), words[-1]))
+    return fields
+
+
+def test_binding_structs_match_the_header(ssamg_lib):
+    """The ctypes copies of ssamg_params and ssamg_stats have the header's
+    fields in the header's order and with its C types (a field added on one
+    side only would shift every later one)."""
+    import ctypes as C
+    S = ssamg_lib
+    txt = open(S.HEADER).read()
+    ctype = {"int": C.c_int, "double": C.c_double, "long long": C.c_longlong}
+    for name, cls in (("ssamg_params", S.Params), ("ssamg_stats", S.Stats)):
+        want = _header_struct(txt, name)
+        got = [(f, t) for f, t in cls._fields_]
+        assert [f for _, f in want] == [f for f, _ in got], name
+        for (ct, f), (_, t) in zip(want, got):
+            assert ctype[ct] is t, (name, f)
+
+
 def test_binding_errors_without_a_hierarchy(ssamg_lib):
     """The binding raises SsamgError with the library's status for bad
     parameters, bad tile tables and calls that need a set-up hierarchy."""
